@@ -1,0 +1,155 @@
+"""CPU oracle of the bulk hash-table operations -- TEST INFRASTRUCTURE.
+
+Only the tests, `__graft_entry__.smoke()` and the CPU-baseline leg of `bench.py` may
+import this package.  The GPU library never calls it and shares no code with it.
+
+`oracle.cpp` implements the plain definitions over std::unordered_map (single-value,
+Sec. IV-B3..IV-B5 of the paper) and std::unordered_multimap (multi-value, Sec. IV-B4);
+this module compiles it with g++ and wraps it with ctypes over numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+FLAG_DUPLICATE_KEY = 1
+FLAG_INVALID_KEY = 2
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.cpp into liboracle.so next to it (portable flags: x86 and Arm)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
+        lib.oracle_create.restype = vp
+        lib.oracle_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.oracle_destroy.argtypes = [vp]
+        lib.oracle_insert.restype = u32
+        lib.oracle_insert.argtypes = [vp, vp, vp, u64]
+        lib.oracle_retrieve.restype = u32
+        lib.oracle_retrieve.argtypes = [vp, vp, u64, vp, vp]
+        lib.oracle_erase.restype = u32
+        lib.oracle_erase.argtypes = [vp, vp, u64]
+        lib.oracle_count_values.restype = u32
+        lib.oracle_count_values.argtypes = [vp, vp, u64, vp]
+        lib.oracle_retrieve_multi.restype = u32
+        lib.oracle_retrieve_multi.argtypes = [vp, vp, u64, vp, vp]
+        lib.oracle_size.restype = u64
+        lib.oracle_size.argtypes = [vp]
+        lib.oracle_num_keys.restype = u64
+        lib.oracle_num_keys.argtypes = [vp]
+        lib.oracle_reserve.argtypes = [vp, u64]
+        _lib = lib
+    return _lib
+
+
+def _dt(nbytes: int):
+    return np.uint32 if nbytes == 4 else np.uint64
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class _Base:
+    kind = -1
+
+    def __init__(self, key_bytes: int = 4, value_bytes: int = 4):
+        self._lib = _load()
+        self.kb, self.vb = key_bytes, value_bytes
+        self.kdt, self.vdt = _dt(key_bytes), _dt(value_bytes)
+        self._h = self._lib.oracle_create(self.kind, key_bytes, value_bytes)
+        if not self._h:
+            raise ValueError("unsupported key/value widths")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.oracle_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _keys(self, keys):
+        return np.ascontiguousarray(keys, dtype=self.kdt)
+
+    def insert(self, keys, values) -> int:
+        k = self._keys(keys)
+        v = np.ascontiguousarray(values, dtype=self.vdt)
+        assert k.size == v.size
+        return int(self._lib.oracle_insert(self._h, _ptr(k), _ptr(v), k.size))
+
+    def erase(self, keys) -> int:
+        k = self._keys(keys)
+        return int(self._lib.oracle_erase(self._h, _ptr(k), k.size))
+
+    def size(self) -> int:
+        return int(self._lib.oracle_size(self._h))
+
+    def num_keys(self) -> int:
+        return int(self._lib.oracle_num_keys(self._h))
+
+    def reserve(self, n: int):
+        self._lib.oracle_reserve(self._h, int(n))
+
+
+class SingleValue(_Base):
+    """std::unordered_map<K, V> with the single-value semantics of Sec. IV-B."""
+    kind = 0
+
+    def retrieve(self, keys):
+        k = self._keys(keys)
+        out = np.empty(k.size, dtype=self.vdt)
+        found = np.empty(k.size, dtype=np.uint8)
+        flags = int(self._lib.oracle_retrieve(self._h, _ptr(k), k.size, _ptr(out), _ptr(found)))
+        return out, found, flags
+
+
+class MultiValue(_Base):
+    """std::unordered_multimap<K, V> with the multi-value semantics of Sec. IV-B4."""
+    kind = 1
+
+    def count_values(self, keys):
+        k = self._keys(keys)
+        offs = np.empty(k.size + 1, dtype=np.uint64)
+        flags = int(self._lib.oracle_count_values(self._h, _ptr(k), k.size, _ptr(offs)))
+        return offs, flags
+
+    def retrieve_multi(self, keys, offsets):
+        k = self._keys(keys)
+        offs = np.ascontiguousarray(offsets, dtype=np.uint64)
+        assert offs.size == k.size + 1
+        out = np.empty(int(offs[-1]), dtype=self.vdt)
+        flags = int(self._lib.oracle_retrieve_multi(self._h, _ptr(k), k.size, _ptr(offs), _ptr(out)))
+        return out, flags
+
+
+def sorted_segments(values: np.ndarray, offsets: np.ndarray) -> np.ndarray:
+    """Sort every CSR segment in place-independent form (values compared as multisets)."""
+    out = np.array(values, copy=True)
+    offs = np.asarray(offsets, dtype=np.int64)
+    n = offs.size - 1
+    if n <= 0 or out.size == 0:
+        return out
+    seg = np.repeat(np.arange(n, dtype=np.int64), np.diff(offs))
+    order = np.lexsort((out, seg))
+    return out[order]

@@ -1,0 +1,264 @@
+// CPU oracle for the bulk hash-table operations.  TEST INFRASTRUCTURE ONLY: the tests,
+// the package's smoke check and the bench's CPU-baseline leg load it; the library
+// itself never does.  It shares no code, header or constant generator with the CUDA
+// path.
+//
+// What it computes is the plain definition of each operation, over the C++ standard
+// library's associative containers (no blocking, no reordering):
+//
+//   * single-value table (Sec. IV, "SingleValueHashTable": each key occurs once)
+//       insert   : key absent -> M[k] = v; key present -> M[k] = v and the duplicate-key
+//                  warning of Sec. IV-B3 is raised (the stored value is overwritten).
+//       retrieve : M[k] if present (Sec. IV-B4), else NOT_FOUND = all ones, found = 0.
+//       erase    : removes k if present (Sec. IV-B5); an absent key is a no-op.
+//       size     : number of live keys; load factor = size / capacity (Sec. II).
+//   * multi-value table (Sec. IV, "MultiValueHashTable": a key may occur many times)
+//       insert        : always appends (k, v) (multiset semantics).
+//       count_values  : per query, the number of values of that key; offsets are the
+//                       exclusive prefix sum with n+1 entries (Sec. IV-B4).
+//       retrieve_multi: query i's values are written to out[offsets[i] .. offsets[i+1]);
+//                       their order inside a segment is unspecified.
+//       erase         : removes every value of the key.
+//
+// Sentinel keys (0 = empty marker k_e, all ones = tombstone k_t, Sec. IV-B1 and
+// IV-B5) cannot be stored: they are skipped and reported with the INVALID_KEY flag.
+// Flag bits match the meaning (not the code) of the library's device status word.
+#include <cstdint>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+constexpr uint32_t F_DUPLICATE = 1u;
+constexpr uint32_t F_INVALID = 2u;
+
+template <class K>
+bool is_sentinel(K k) { return k == K(0) || k == K(~K(0)); }
+
+template <class K, class V>
+struct SV {
+  std::unordered_map<K, V> m;
+
+  uint32_t insert(const K* keys, const V* vals, uint64_t n) {
+    uint32_t f = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+      if (is_sentinel(keys[i])) { f |= F_INVALID; continue; }
+      auto it = m.find(keys[i]);
+      if (it == m.end()) {
+        m.emplace(keys[i], vals[i]);
+      } else {
+        it->second = vals[i];
+        f |= F_DUPLICATE;
+      }
+    }
+    return f;
+  }
+  uint32_t retrieve(const K* keys, uint64_t n, V* out, uint8_t* found) const {
+    uint32_t f = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+      if (is_sentinel(keys[i])) f |= F_INVALID;
+      auto it = is_sentinel(keys[i]) ? m.end() : m.find(keys[i]);
+      bool hit = it != m.end();
+      out[i] = hit ? it->second : V(~V(0));
+      if (found) found[i] = hit ? 1 : 0;
+    }
+    return f;
+  }
+  uint32_t erase(const K* keys, uint64_t n) {
+    uint32_t f = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+      if (is_sentinel(keys[i])) { f |= F_INVALID; continue; }
+      m.erase(keys[i]);
+    }
+    return f;
+  }
+};
+
+template <class K, class V>
+struct MV {
+  std::unordered_multimap<K, V> m;
+
+  uint32_t insert(const K* keys, const V* vals, uint64_t n) {
+    uint32_t f = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+      if (is_sentinel(keys[i])) { f |= F_INVALID; continue; }
+      m.emplace(keys[i], vals[i]);
+    }
+    return f;
+  }
+  uint32_t count_values(const K* keys, uint64_t n, uint64_t* offsets) const {
+    uint32_t f = 0;
+    uint64_t run = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+      offsets[i] = run;
+      if (is_sentinel(keys[i])) { f |= F_INVALID; continue; }
+      run += m.count(keys[i]);
+    }
+    offsets[n] = run;
+    return f;
+  }
+  uint32_t retrieve_multi(const K* keys, uint64_t n, const uint64_t* offsets, V* out) const {
+    uint32_t f = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+      if (is_sentinel(keys[i])) { f |= F_INVALID; continue; }
+      uint64_t o = offsets[i];
+      auto range = m.equal_range(keys[i]);
+      for (auto it = range.first; it != range.second; ++it) {
+        if (o < offsets[i + 1]) out[o] = it->second;
+        ++o;
+      }
+    }
+    return f;
+  }
+  uint32_t erase(const K* keys, uint64_t n) {
+    uint32_t f = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+      if (is_sentinel(keys[i])) { f |= F_INVALID; continue; }
+      m.erase(keys[i]);
+    }
+    return f;
+  }
+};
+
+// A tagged handle so one C entry point serves every key/value width.
+struct Handle {
+  int kind;  // 0 = single-value, 1 = multi-value
+  int kb, vb;
+  void* impl;
+};
+
+template <template <class, class> class T, class F>
+auto dispatch(Handle* h, F&& f) {
+  if (h->kb == 4 && h->vb == 4) return f(static_cast<T<uint32_t, uint32_t>*>(h->impl));
+  if (h->kb == 8 && h->vb == 8) return f(static_cast<T<uint64_t, uint64_t>*>(h->impl));
+  if (h->kb == 8 && h->vb == 4) return f(static_cast<T<uint64_t, uint32_t>*>(h->impl));
+  return f(static_cast<T<uint32_t, uint64_t>*>(h->impl));
+}
+
+template <template <class, class> class T>
+void* make(int kb, int vb) {
+  if (kb == 4 && vb == 4) return new T<uint32_t, uint32_t>();
+  if (kb == 8 && vb == 8) return new T<uint64_t, uint64_t>();
+  if (kb == 8 && vb == 4) return new T<uint64_t, uint32_t>();
+  return new T<uint32_t, uint64_t>();
+}
+
+bool valid_widths(int kb, int vb) { return (kb == 4 || kb == 8) && (vb == 4 || vb == 8); }
+
+}  // namespace
+
+extern "C" {
+
+void* oracle_create(int kind, int key_bytes, int value_bytes) {
+  if (!valid_widths(key_bytes, value_bytes) || (kind != 0 && kind != 1)) return nullptr;
+  auto* h = new Handle{kind, key_bytes, value_bytes, nullptr};
+  h->impl = kind == 0 ? make<SV>(key_bytes, value_bytes) : make<MV>(key_bytes, value_bytes);
+  return h;
+}
+
+void oracle_destroy(void* p) {
+  auto* h = static_cast<Handle*>(p);
+  if (!h) return;
+  if (h->kind == 0) dispatch<SV>(h, [](auto* t) { delete t; return 0; });
+  else dispatch<MV>(h, [](auto* t) { delete t; return 0; });
+  delete h;
+}
+
+uint32_t oracle_insert(void* p, const void* keys, const void* vals, uint64_t n) {
+  auto* h = static_cast<Handle*>(p);
+  if (h->kind == 0)
+    return dispatch<SV>(h, [&](auto* t) {
+      using M = std::remove_pointer_t<decltype(t)>;
+      using K = typename decltype(M::m)::key_type;
+      using V = typename decltype(M::m)::mapped_type;
+      return t->insert(static_cast<const K*>(keys), static_cast<const V*>(vals), n);
+    });
+  return dispatch<MV>(h, [&](auto* t) {
+    using M = std::remove_pointer_t<decltype(t)>;
+    using K = typename decltype(M::m)::key_type;
+    using V = typename decltype(M::m)::mapped_type;
+    return t->insert(static_cast<const K*>(keys), static_cast<const V*>(vals), n);
+  });
+}
+
+// Single-value only.
+uint32_t oracle_retrieve(void* p, const void* keys, uint64_t n, void* out, uint8_t* found) {
+  auto* h = static_cast<Handle*>(p);
+  if (h->kind != 0) return 0xFFFFFFFFu;
+  return dispatch<SV>(h, [&](auto* t) {
+    using M = std::remove_pointer_t<decltype(t)>;
+    using K = typename decltype(M::m)::key_type;
+    using V = typename decltype(M::m)::mapped_type;
+    return t->retrieve(static_cast<const K*>(keys), n, static_cast<V*>(out), found);
+  });
+}
+
+uint32_t oracle_erase(void* p, const void* keys, uint64_t n) {
+  auto* h = static_cast<Handle*>(p);
+  if (h->kind == 0)
+    return dispatch<SV>(h, [&](auto* t) {
+      using M = std::remove_pointer_t<decltype(t)>;
+      using K = typename decltype(M::m)::key_type;
+      return t->erase(static_cast<const K*>(keys), n);
+    });
+  return dispatch<MV>(h, [&](auto* t) {
+    using M = std::remove_pointer_t<decltype(t)>;
+    using K = typename decltype(M::m)::key_type;
+    return t->erase(static_cast<const K*>(keys), n);
+  });
+}
+
+// Multi-value only.
+uint32_t oracle_count_values(void* p, const void* keys, uint64_t n, uint64_t* offsets) {
+  auto* h = static_cast<Handle*>(p);
+  if (h->kind != 1) return 0xFFFFFFFFu;
+  return dispatch<MV>(h, [&](auto* t) {
+    using M = std::remove_pointer_t<decltype(t)>;
+    using K = typename decltype(M::m)::key_type;
+    return t->count_values(static_cast<const K*>(keys), n, offsets);
+  });
+}
+
+uint32_t oracle_retrieve_multi(void* p, const void* keys, uint64_t n, const uint64_t* offsets,
+                               void* out) {
+  auto* h = static_cast<Handle*>(p);
+  if (h->kind != 1) return 0xFFFFFFFFu;
+  return dispatch<MV>(h, [&](auto* t) {
+    using M = std::remove_pointer_t<decltype(t)>;
+    using K = typename decltype(M::m)::key_type;
+    using V = typename decltype(M::m)::mapped_type;
+    return t->retrieve_multi(static_cast<const K*>(keys), n, offsets, static_cast<V*>(out));
+  });
+}
+
+uint64_t oracle_size(void* p) {
+  auto* h = static_cast<Handle*>(p);
+  if (h->kind == 0) return dispatch<SV>(h, [](auto* t) { return (uint64_t)t->m.size(); });
+  return dispatch<MV>(h, [](auto* t) { return (uint64_t)t->m.size(); });
+}
+
+// Number of distinct live keys (equals size for a single-value table).
+uint64_t oracle_num_keys(void* p) {
+  auto* h = static_cast<Handle*>(p);
+  if (h->kind == 0) return dispatch<SV>(h, [](auto* t) { return (uint64_t)t->m.size(); });
+  return dispatch<MV>(h, [](auto* t) {
+    uint64_t c = 0;
+    for (auto it = t->m.begin(); it != t->m.end();) {
+      auto r = t->m.equal_range(it->first);
+      ++c;
+      it = r.second;
+    }
+    return c;
+  });
+}
+
+// Reserve buckets for n elements (a plain std::unordered_map::reserve); used by the
+// CPU-baseline timing so rehashing is not what gets measured.
+void oracle_reserve(void* p, uint64_t n) {
+  auto* h = static_cast<Handle*>(p);
+  if (h->kind == 0) dispatch<SV>(h, [&](auto* t) { t->m.reserve(n); return 0; });
+  else dispatch<MV>(h, [&](auto* t) { t->m.reserve(n); return 0; });
+}
+
+}  // extern "C"

@@ -1,0 +1,211 @@
+"""Pins of the CPU oracle to things other than itself (no GPU needed).
+
+* brute force: a list of (key, value) pairs searched by linear scan, written
+  independently of the oracle, on tiny random operation sequences that mix insert,
+  duplicate insert, erase, re-insert after erase and sentinel keys;
+* invariants of the paper's definitions (every inserted key found, absent keys
+  NOT_FOUND, size = distinct live keys, MV counts sum to the inserts, offsets are the
+  exclusive prefix sum with offsets[n] = total);
+* the paper's multi-value benchmark invariant (Sec. V-C): keys from 1..n/r queried over
+  1..n return exactly n values;
+* hand-derived worked examples under tests/golden/ (each line cites its section).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import wc_inputs
+from tests.golden_fixtures import run_mv, run_sv
+
+NF32 = 0xFFFFFFFF
+
+
+class BruteSV:
+    """Single-value semantics by linear scan over a list of pairs."""
+
+    def __init__(self, kmax):
+        self.pairs = []
+        self.kmax = kmax
+
+    def _find(self, k):
+        for i, (kk, _) in enumerate(self.pairs):
+            if kk == k:
+                return i
+        return -1
+
+    def insert(self, ks, vs):
+        f = 0
+        for k, v in zip(ks, vs):
+            if k == 0 or k == self.kmax:
+                f |= 2
+                continue
+            i = self._find(k)
+            if i < 0:
+                self.pairs.append((k, v))
+            else:
+                self.pairs[i] = (k, v)
+                f |= 1
+        return f
+
+    def erase(self, ks):
+        f = 0
+        for k in ks:
+            if k == 0 or k == self.kmax:
+                f |= 2
+                continue
+            i = self._find(k)
+            if i >= 0:
+                self.pairs.pop(i)
+        return f
+
+    def retrieve(self, ks, nf):
+        out, found, f = [], [], 0
+        for k in ks:
+            if k == 0 or k == self.kmax:
+                f |= 2
+            i = -1 if (k == 0 or k == self.kmax) else self._find(k)
+            out.append(self.pairs[i][1] if i >= 0 else nf)
+            found.append(1 if i >= 0 else 0)
+        return out, found, f
+
+
+class BruteMV:
+    def __init__(self, kmax):
+        self.pairs = []
+        self.kmax = kmax
+
+    def insert(self, ks, vs):
+        for k, v in zip(ks, vs):
+            if k != 0 and k != self.kmax:
+                self.pairs.append((k, v))
+
+    def erase(self, ks):
+        drop = {k for k in ks}
+        self.pairs = [(k, v) for (k, v) in self.pairs if k not in drop]
+
+    def values_of(self, k):
+        return sorted(v for (kk, v) in self.pairs if kk == k)
+
+
+@pytest.mark.parametrize("kb,vb", [(4, 4), (8, 8), (8, 4)])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_sv_oracle_matches_brute_force(kb, vb, seed):
+    kmax = (1 << (8 * kb)) - 1
+    vmax = (1 << (8 * vb)) - 1
+    kdt = np.uint32 if kb == 4 else np.uint64
+    vdt = np.uint32 if vb == 4 else np.uint64
+    rng = np.random.default_rng(seed)
+    o = oracle.SingleValue(kb, vb)
+    b = BruteSV(kmax)
+    universe = np.array([0, kmax] + list(rng.integers(1, kmax, 40, dtype=np.uint64)), dtype=np.uint64)
+    for step in range(60):
+        op = rng.integers(0, 3)
+        m = int(rng.integers(0, 12))
+        ks = universe[rng.integers(0, universe.size, m)].astype(kdt)
+        if op == 0:
+            vs = rng.integers(0, vmax, m, dtype=np.uint64, endpoint=True).astype(vdt)
+            # the oracle applies a batch in call order; so does the brute force
+            assert o.insert(ks, vs) == b.insert([int(x) for x in ks], [int(x) for x in vs])
+        elif op == 1:
+            assert o.erase(ks) == b.erase([int(x) for x in ks])
+        else:
+            out, found, f = o.retrieve(ks)
+            bo, bf, bfl = b.retrieve([int(x) for x in ks], vmax)
+            assert [int(x) for x in out] == bo
+            assert [int(x) for x in found] == bf
+            assert f == bfl
+        assert o.size() == len(b.pairs)
+
+
+@pytest.mark.parametrize("kb,vb", [(4, 4), (8, 4), (8, 8)])
+@pytest.mark.parametrize("seed", [4, 5])
+def test_mv_oracle_matches_brute_force(kb, vb, seed):
+    kmax = (1 << (8 * kb)) - 1
+    kdt = np.uint32 if kb == 4 else np.uint64
+    vdt = np.uint32 if vb == 4 else np.uint64
+    rng = np.random.default_rng(seed)
+    o = oracle.MultiValue(kb, vb)
+    b = BruteMV(kmax)
+    universe = np.array([0, kmax] + list(rng.integers(1, 1000, 15)), dtype=np.uint64)
+    for step in range(40):
+        op = rng.integers(0, 3)
+        m = int(rng.integers(0, 16))
+        ks = universe[rng.integers(0, universe.size, m)].astype(kdt)
+        if op == 0:
+            vs = rng.integers(0, 50, m).astype(vdt)  # small range: equal values repeat
+            o.insert(ks, vs)
+            b.insert([int(x) for x in ks], [int(x) for x in vs])
+        elif op == 1 and rng.random() < 0.3:
+            o.erase(ks)
+            b.erase([int(x) for x in ks])
+        else:
+            offs, _ = o.count_values(ks)
+            out, _ = o.retrieve_multi(ks, offs)
+            assert int(offs[0]) == 0
+            for i, k in enumerate(ks):
+                seg = sorted(int(x) for x in out[int(offs[i]):int(offs[i + 1])])
+                want = [] if int(k) in (0, kmax) else b.values_of(int(k))
+                assert seg == want
+        assert o.size() == len(b.pairs)
+
+
+def test_sv_invariants_random_batch():
+    d = wc_inputs.sv_insert_retrieve_u32(11, 50_000, 20_000, 20_000)
+    o = oracle.SingleValue(4, 4)
+    assert o.insert(d["keys"], d["values"]) == 0
+    assert o.size() == d["keys"].size
+    out, found, _ = o.retrieve(d["queries"])
+    pres = d["q_src"] >= 0
+    assert found[pres].all() and not found[~pres].any()
+    assert (out[pres] == d["values"][d["q_src"][pres]]).all()
+    assert (out[~pres] == NF32).all()
+    # erase half, the rest stays; size = distinct live keys
+    o.erase(d["keys"][::2])
+    assert o.size() == d["keys"].size - d["keys"][::2].size
+    out, found, _ = o.retrieve(d["keys"])
+    assert not found[::2].any() and found[1::2].all()
+    assert (out[1::2] == d["values"][1::2]).all()
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 8, 64])
+def test_mv_paper_invariant_total_equals_n(r):
+    """Sec. V-C: n keys drawn from 1..n/r, queried over 1..n -> exactly n values."""
+    n = 4096
+    d = wc_inputs.mv_uniform_r(100 + r, n, r)
+    o = oracle.MultiValue(8, 4)
+    o.insert(d["keys"], d["values"])
+    offs, _ = o.count_values(d["queries"])
+    assert int(offs[-1]) == n
+    assert np.all(np.diff(offs.astype(np.int64)) >= 0)
+    out, _ = o.retrieve_multi(d["queries"], offs)
+    # every inserted value comes back exactly once (values are the insert indices)
+    assert np.array_equal(np.sort(out), np.arange(n, dtype=np.uint32))
+    # and each lands in its own key's segment
+    seg_of = np.repeat(np.arange(n), np.diff(offs.astype(np.int64)))
+    assert np.array_equal(d["queries"][seg_of], d["keys"][out])
+
+
+def test_mv_counts_sum_to_inserts_zipf():
+    d = wc_inputs.mv_zipf_u64(9, 1 << 12, 1 << 15, 1 << 10)
+    o = oracle.MultiValue(8, 4)
+    o.insert(d["keys"], d["values"])
+    assert o.size() == d["keys"].size
+    offs, _ = o.count_values(d["queries"])
+    assert int(offs[-1]) == d["keys"].size  # the universe covers every inserted key
+    assert o.num_keys() == np.unique(d["keys"]).size
+
+
+def test_golden_sv_worked_example():
+    assert run_sv("sv_ops.txt", lambda: oracle.SingleValue(4, 4)) >= 10
+
+
+def test_golden_mv_worked_example():
+    assert run_mv("mv_ops.txt", lambda: oracle.MultiValue(8, 4)) >= 8
+
+
+def test_sentinels_are_rejected():
+    o = oracle.SingleValue(8, 8)
+    f = o.insert(np.array([0, 2 ** 64 - 1, 3], dtype=np.uint64), np.array([1, 2, 3], dtype=np.uint64))
+    assert f == oracle.FLAG_INVALID_KEY and o.size() == 1
