@@ -1,0 +1,213 @@
+/*
+ * wc.h -- C ABI of a GB300-native (sm_103a) library of bulk open-addressing GPU hash
+ * tables, after WarpCore (Juenger et al., "WarpCore: A Library for fast Hash Tables on
+ * GPUs", 2020).
+ *
+ * Conventions for every call below
+ *   - Pointers named d_* are device pointers (global memory of the table's device).
+ *     Pointers named h_* are host pointers.  The caller owns every key, value, output
+ *     and offset buffer; the library owns a table's slot array, value pool and the few
+ *     device words (status, counters) it allocates at create time.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Bulk operations are asynchronous with respect to the host; only calls that hand a
+ *     value back to the host (wc_size, wc_load_factor, wc_get_status, wc_count_values with
+ *     h_total != NULL) synchronise `stream` (Sec. IV-D of the paper).
+ *   - Keys and values are unsigned integers of `key_bytes` / `value_bytes` width, packed
+ *     densely (element i at byte offset i * width).  Input arrays must be aligned to
+ *     their element width.
+ *   - Sentinels: key 0 marks an empty slot and the all-ones key marks a tombstone
+ *     (Sec. IV-B1 and IV-B5).  They cannot be stored: an input holding one is skipped
+ *     and raises WC_FLAG_INVALID_KEY in the device status word.
+ *   - Errors the host can see (bad arguments, allocation failure, an op the table kind
+ *     does not support, a CUDA launch error) are returned at once as wc_status.
+ *     Conditions found on the device accumulate as bits of the table's status word
+ *     (WC_FLAG_*), read with wc_get_status.
+ *   - A table is not thread-safe across host threads.  Operations of the same kind may
+ *     overlap on different streams; a write (insert, erase) must not overlap any other
+ *     kind of operation on the same table (Sec. IV-D).
+ */
+#ifndef WC_H_
+#define WC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wc_table wc_table;
+
+typedef enum {
+  WC_OK = 0,
+  WC_ERR_INVALID_ARG = 1,   /* null pointer, bad width, n too large, misaligned buffer */
+  WC_ERR_OUT_OF_MEMORY = 2, /* cudaMalloc failed at create time */
+  WC_ERR_FULL = 3,          /* reported by wc_get_status when PROBE_LIMIT was raised */
+  WC_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+  WC_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out (queue path) */
+  WC_ERR_UNSUPPORTED = 6    /* the operation does not exist for this table kind */
+} wc_status;
+
+/* Bits of the device status word (see wc_get_status). */
+enum {
+  WC_FLAG_DUPLICATE_KEY = 1,  /* single-value insert met a key already stored (Sec. IV-B3);
+                                 the stored value was overwritten */
+  WC_FLAG_INVALID_KEY = 2,    /* an input key was a sentinel (0 or all ones) */
+  WC_FLAG_PROBE_LIMIT = 4,    /* an insert visited every window without a free slot */
+  WC_FLAG_POOL_EXHAUSTED = 8, /* multi-value insert ran out of value-pool space */
+  WC_FLAG_COUNT_OVERFLOW = 16,/* a multi-value key would exceed 2^28 - 1 values */
+  WC_FLAG_QUEUE_TIMEOUT = 32  /* the batched executor gave up waiting (bounded wait) */
+};
+
+enum { WC_SINGLE_VALUE = 0, WC_MULTI_VALUE = 1 };
+
+/* Table configuration.
+ *   kind                 WC_SINGLE_VALUE or WC_MULTI_VALUE.
+ *   key_bytes/value_bytes  single-value: 4/4 (key and value packed in one 64-bit slot
+ *                        word, claimed by one 64-bit CAS, Sec. IV-B1) or 8/8 (one 16-byte
+ *                        slot claimed by one 128-bit CAS).  multi-value: key 4 or 8,
+ *                        value 4 or 8 (keys are stored once in a 16-byte key-store slot
+ *                        next to a handle to their values, Sec. IV-C).
+ *   window_width         slots per probing window W (the inner linear-probing window of
+ *                        the cooperative probing scheme, Sec. IV-B2).  Windows are
+ *                        aligned to W slots.  0 = the library default for the widths.
+ *                        Allowed: 4, 8, 16, 32 (8-byte slots); 2, 4, 8, 16 (16-byte slots).
+ *   min_capacity         requested slots (key-store slots for multi-value).  The table
+ *                        holds capacity = p * W slots with p the smallest prime
+ *                        >= ceil(min_capacity / W), so the outer double-hashing sequence
+ *                        over the p windows visits every window once (Sec. IV-B2).
+ *                        p must stay below 2^32.
+ *   value_pool_capacity  multi-value only: value elements in the pool (headers of
+ *                        repeat-insert segments included); at most 2^35.
+ *   seed                 seeds the two hash functions of the outer probing scheme.
+ *   device               CUDA device ordinal the table lives on.
+ *   l2_persist           1 = launch this table's kernels with an L2 access-policy window
+ *                        marking the slot array persisting (useful when it fits in L2).
+ */
+typedef struct {
+  int32_t kind;
+  int32_t key_bytes;
+  int32_t value_bytes;
+  int32_t window_width;
+  int32_t device;
+  int32_t l2_persist;
+  uint64_t min_capacity;
+  uint64_t value_pool_capacity;
+  uint64_t seed;
+} wc_table_config;
+
+/* Sizes of a created table (host copy; no device access). */
+typedef struct {
+  uint64_t capacity;        /* slots (key-store slots for multi-value) = windows * W */
+  uint64_t windows;         /* p, prime */
+  uint64_t slot_bytes;      /* 8 or 16 */
+  uint64_t table_bytes;     /* bytes of the slot array */
+  uint64_t pool_capacity;   /* multi-value value-pool elements (0 for single-value) */
+  uint64_t device_bytes;    /* every device byte the table owns */
+  int32_t window_width;     /* W */
+  int32_t kind;
+} wc_table_info;
+
+/* Launch shape of one operation class.  group_size = lanes that probe one key together
+ * (the cooperative group of Sec. IV-B2; W / group_size slots per lane, walked
+ * consecutively by each lane, Sec. IV-B2 "fixed window with variable CG size");
+ * block_threads = CUDA block size; blocks_per_sm = resident blocks per SM the grid is
+ * sized for (0 = the occupancy limit). */
+typedef struct {
+  int32_t group_size;
+  int32_t block_threads;
+  int32_t blocks_per_sm;
+} wc_launch;
+
+enum { WC_OP_INSERT = 0, WC_OP_RETRIEVE = 1, WC_OP_ERASE = 2, WC_OP_COUNT = 3, WC_OP__N = 4 };
+
+/* ---- lifecycle ------------------------------------------------------------------ */
+
+/* Plan a table's geometry without a device: p = smallest prime >= ceil(min_capacity/W),
+ * capacity = p * W (Sec. IV-B2, c = p * 32 generalised to c = p * W).  Host only.
+ * Returns WC_ERR_INVALID_ARG for W outside 1..64 or p >= 2^32. */
+wc_status wc_plan_capacity(uint64_t min_capacity, int32_t window_width, uint64_t* h_windows,
+                           uint64_t* h_capacity);
+
+/* Create a table on cfg->device: allocates and clears (every slot = empty key) its slot
+ * array, value pool and status/counter words.  Synchronous.  *out is owned by the caller
+ * and released with wc_table_destroy. */
+wc_status wc_table_create(wc_table** out, const wc_table_config* cfg);
+
+/* Free everything the table owns.  The caller must make sure no work on it is pending. */
+wc_status wc_table_destroy(wc_table* t);
+
+/* Reset to empty on `stream`: every slot back to the empty key, counters, status word
+ * and value-pool cursor to zero (Sec. IV-B1: slots start as k_e). */
+wc_status wc_table_clear(wc_table* t, void* stream);
+
+wc_status wc_table_get_info(const wc_table* t, wc_table_info* h_out);
+
+/* Override the launch shape of one operation class (see wc_launch); the autotuner in
+ * the Python package calls this.  group_size must divide W and give 8..64 bytes per lane
+ * (or be 1..32 with W / group_size slots per lane <= 8).  Host only. */
+wc_status wc_table_set_launch(wc_table* t, int32_t op, const wc_launch* launch);
+wc_status wc_table_get_launch(const wc_table* t, int32_t op, wc_launch* h_out);
+
+/* ---- bulk operations (Sec. IV-B3 .. IV-B5) ----------------------------------------- */
+
+/* Insert n pairs (d_keys[i], d_values[i]).  Single-value: a new key claims the earliest
+ * free or tombstoned slot of its probing sequence with one CAS of the packed pair
+ * (Sec. IV-B2 steps 1-7); a key already present gets its value overwritten and raises
+ * WC_FLAG_DUPLICATE_KEY (Sec. IV-B3).  If the same key occurs several times in one
+ * batch, the stored value is one of that batch's values for it.  Multi-value: every
+ * pair is appended (Sec. IV-B4); values of one call are stored contiguously per key in
+ * the value pool (a bucket of exactly that call's count, linked to the key's earlier
+ * buckets, Sec. IV-C with lambda = 1, s0 = count).  n < 2^32. */
+wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint64_t n,
+                    void* stream);
+
+/* Single-value retrieve (Sec. IV-B4): d_values_out[i] = value of d_keys[i], or all ones
+ * (NOT_FOUND) when absent; d_found_or_null[i] = 1/0 when the mask is given (a stored value
+ * may itself be all ones).  Probing stops at the key or at the first window holding an
+ * empty slot.  Multi-value tables return WC_ERR_UNSUPPORTED. */
+wc_status wc_retrieve(wc_table* t, const void* d_keys, uint64_t n, void* d_values_out,
+                      uint8_t* d_found_or_null, void* stream);
+
+/* Erase (Sec. IV-B5): the key's slot becomes a tombstone; absent keys are a no-op.
+ * Multi-value: removes every value of the key (its pool space is not reused). */
+wc_status wc_erase(wc_table* t, const void* d_keys, uint64_t n, void* stream);
+
+/* Multi-value counting pass (Sec. IV-B4): d_offsets[0..n] (n+1 uint64, caller-allocated)
+ * receives the exclusive prefix sum of the per-query value counts, so query i's values
+ * go to [d_offsets[i], d_offsets[i+1]) and d_offsets[n] is the total.  If h_total_or_null
+ * is given the call synchronises `stream` and stores the total there.  Sentinel
+ * queries count 0.  Single-value tables return WC_ERR_UNSUPPORTED. */
+wc_status wc_count_values(wc_table* t, const void* d_keys, uint64_t n, uint64_t* d_offsets,
+                          uint64_t* h_total_or_null, void* stream);
+
+/* Multi-value retrieve into CSR form (Sec. IV-B4): writes the values of query i to
+ * d_values_out[d_offsets[i] .. d_offsets[i+1]), with d_offsets from wc_count_values on
+ * the same keys and an unchanged table.  The order of values inside a segment is
+ * unspecified.  d_values_out holds d_offsets[n] elements of value_bytes. */
+wc_status wc_retrieve_multi(wc_table* t, const void* d_keys, uint64_t n,
+                            const uint64_t* d_offsets, void* d_values_out, void* stream);
+
+/* ---- metrics (blocking) ---------------------------------------------------------- */
+
+/* Single-value: live keys.  Multi-value: stored key-value pairs.  Synchronises stream. */
+wc_status wc_size(wc_table* t, uint64_t* h_out, void* stream);
+
+/* Multi-value: distinct live keys.  Single-value: same as wc_size. */
+wc_status wc_num_keys(wc_table* t, uint64_t* h_out, void* stream);
+
+/* Load factor alpha = live keys / capacity (key-store load for multi-value, Sec. II).
+ * Single-value tables have storage density rho = alpha (Sec. IV-C). */
+wc_status wc_load_factor(wc_table* t, double* h_out, void* stream);
+
+/* Read the device status word (WC_FLAG_* bits accumulated since the last clear); with
+ * clear != 0 it is reset to 0 afterwards.  Synchronises stream. */
+wc_status wc_get_status(wc_table* t, uint32_t* h_flags, int32_t clear, void* stream);
+
+/* Static description of a status code. */
+const char* wc_status_string(wc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WC_H_ */

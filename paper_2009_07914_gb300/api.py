@@ -1,0 +1,152 @@
+"""Python functions with the names of the C ABI (include/wc.h).
+
+Each function marshals its arguments (tensor -> device address, stream -> handle,
+ctypes out-parameters) and calls the library once.  Tables are opaque integer handles.
+Buffers are torch tensors of any 4- or 8-byte integer dtype: the library reads their
+bytes, so uint32 keys may travel as int32 tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _binding as B
+from ._binding import (WC_MULTI_VALUE, WC_SINGLE_VALUE, WcLaunch, WcTableConfig, WcTableInfo, check, lib, ptr,
+                       stream_handle)
+
+__all__ = [
+    "wc_plan_capacity", "wc_table_create", "wc_table_destroy", "wc_table_clear", "wc_table_get_info",
+    "wc_table_set_launch", "wc_table_get_launch", "wc_insert", "wc_retrieve", "wc_erase", "wc_count_values",
+    "wc_retrieve_multi", "wc_size", "wc_num_keys", "wc_load_factor", "wc_get_status", "wc_status_string",
+]
+
+
+def _n_of(n, t: torch.Tensor | None, width: int | None = None) -> int:
+    if n is None:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("n is required when the keys are a raw address")
+        n = t.numel()
+    if isinstance(t, torch.Tensor):
+        if t.numel() < n:
+            raise ValueError("buffer holds %d elements, n = %d" % (t.numel(), n))
+        if width is not None and t.numel() and t.element_size() != width:
+            raise ValueError("element width %d, table expects %d" % (t.element_size(), width))
+        if t.numel() and not t.is_cuda:
+            raise ValueError("device buffers must be CUDA tensors")
+    return int(n)
+
+
+def wc_status_string(code: int) -> str:
+    return B.status_string(code)
+
+
+def wc_plan_capacity(min_capacity: int, window_width: int) -> tuple[int, int]:
+    p, c = ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib().wc_plan_capacity(int(min_capacity), int(window_width), ctypes.byref(p), ctypes.byref(c)),
+          "wc_plan_capacity")
+    return int(p.value), int(c.value)
+
+
+def wc_table_create(kind: int = WC_SINGLE_VALUE, key_bytes: int = 4, value_bytes: int = 4, min_capacity: int = 1024,
+                    window_width: int = 0, value_pool_capacity: int = 0, seed: int = 0x5EED_C0DE,
+                    device: int | None = None, l2_persist: bool = False) -> int:
+    if device is None:
+        device = torch.cuda.current_device()
+    cfg = WcTableConfig(kind=kind, key_bytes=key_bytes, value_bytes=value_bytes, window_width=window_width,
+                        device=device, l2_persist=1 if l2_persist else 0, min_capacity=int(min_capacity),
+                        value_pool_capacity=int(value_pool_capacity), seed=int(seed) & (2 ** 64 - 1))
+    h = ctypes.c_void_p()
+    check(lib().wc_table_create(ctypes.byref(h), ctypes.byref(cfg)), "wc_table_create")
+    return int(h.value)
+
+
+def wc_table_destroy(t: int):
+    check(lib().wc_table_destroy(t), "wc_table_destroy")
+
+
+def wc_table_clear(t: int, stream=None):
+    check(lib().wc_table_clear(t, stream_handle(stream)), "wc_table_clear")
+
+
+def wc_table_get_info(t: int) -> dict:
+    info = WcTableInfo()
+    check(lib().wc_table_get_info(t, ctypes.byref(info)), "wc_table_get_info")
+    return {f: getattr(info, f) for f, _ in WcTableInfo._fields_}
+
+
+def wc_table_set_launch(t: int, op: int, group_size: int, block_threads: int = 256, blocks_per_sm: int = 0):
+    lc = WcLaunch(group_size=group_size, block_threads=block_threads, blocks_per_sm=blocks_per_sm)
+    check(lib().wc_table_set_launch(t, op, ctypes.byref(lc)), "wc_table_set_launch")
+
+
+def wc_table_get_launch(t: int, op: int) -> dict:
+    lc = WcLaunch()
+    check(lib().wc_table_get_launch(t, op, ctypes.byref(lc)), "wc_table_get_launch")
+    return {f: getattr(lc, f) for f, _ in WcLaunch._fields_}
+
+
+def wc_insert(t: int, keys, values, n: int | None = None, stream=None):
+    n = _n_of(n, keys)
+    _n_of(n, values)
+    check(lib().wc_insert(t, ptr(keys), ptr(values), n, stream_handle(stream)), "wc_insert")
+
+
+def wc_retrieve(t: int, keys, values_out, found_out=None, n: int | None = None, stream=None):
+    n = _n_of(n, keys)
+    _n_of(n, values_out)
+    if found_out is not None:
+        _n_of(n, found_out, 1)
+    check(lib().wc_retrieve(t, ptr(keys), n, ptr(values_out), ptr(found_out), stream_handle(stream)),
+          "wc_retrieve")
+
+
+def wc_erase(t: int, keys, n: int | None = None, stream=None):
+    n = _n_of(n, keys)
+    check(lib().wc_erase(t, ptr(keys), n, stream_handle(stream)), "wc_erase")
+
+
+def wc_count_values(t: int, keys, offsets_out, n: int | None = None, want_total: bool = True, stream=None):
+    """Fills offsets_out[0..n] (n+1 uint64); returns the total if want_total (blocking)."""
+    n = _n_of(n, keys)
+    _n_of(n + 1, offsets_out, 8)
+    total = ctypes.c_uint64()
+    check(lib().wc_count_values(t, ptr(keys), n, ptr(offsets_out), ctypes.byref(total) if want_total else None,
+                                stream_handle(stream)), "wc_count_values")
+    return int(total.value) if want_total else None
+
+
+def wc_retrieve_multi(t: int, keys, offsets, values_out, n: int | None = None, stream=None):
+    n = _n_of(n, keys)
+    _n_of(n + 1, offsets, 8)
+    check(lib().wc_retrieve_multi(t, ptr(keys), n, ptr(offsets), ptr(values_out), stream_handle(stream)),
+          "wc_retrieve_multi")
+
+
+def _read_u64(fn, t, stream, where):
+    v = ctypes.c_uint64()
+    check(fn(t, ctypes.byref(v), stream_handle(stream)), where)
+    return int(v.value)
+
+
+def wc_size(t: int, stream=None) -> int:
+    return _read_u64(lib().wc_size, t, stream, "wc_size")
+
+
+def wc_num_keys(t: int, stream=None) -> int:
+    return _read_u64(lib().wc_num_keys, t, stream, "wc_num_keys")
+
+
+def wc_load_factor(t: int, stream=None) -> float:
+    v = ctypes.c_double()
+    check(lib().wc_load_factor(t, ctypes.byref(v), stream_handle(stream)), "wc_load_factor")
+    return float(v.value)
+
+
+def wc_get_status(t: int, clear: bool = False, stream=None) -> int:
+    v = ctypes.c_uint32()
+    check(lib().wc_get_status(t, ctypes.byref(v), 1 if clear else 0, stream_handle(stream)), "wc_get_status")
+    return int(v.value)
+
+
+__all__ += ["WC_SINGLE_VALUE", "WC_MULTI_VALUE"]

@@ -1,0 +1,432 @@
+// The C ABI of include/wc.h: table lifecycle, geometry planning, argument checks and
+// dispatch to the kernel families.  Host code only.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "wc.h"
+#include "wc_internal.h"
+
+namespace wc {
+
+bool sv_p32_shape_ok(int W, int G);
+bool sv_p64_shape_ok(int W, int G);
+cudaError_t sv_p32_launch(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n, void* out,
+                          uint8_t* found, cudaStream_t s);
+cudaError_t sv_p64_launch(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n, void* out,
+                          uint8_t* found, cudaStream_t s);
+
+namespace {
+
+constexpr uint64_t kAlign = 256;
+constexpr uint64_t kMaxPool = 1ull << 35;
+constexpr uint64_t kMaxBatch = (1ull << 32) - 1;
+
+uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// Trial division: exact for every 64-bit input, fast for the < 2^32 range used here.
+bool is_prime(uint64_t x) {
+  if (x < 2) return false;
+  if (x % 2 == 0) return x == 2;
+  if (x % 3 == 0) return x == 3;
+  for (uint64_t d = 5; d * d <= x; d += 6)
+    if (x % d == 0 || x % (d + 2) == 0) return false;
+  return true;
+}
+
+uint64_t next_prime(uint64_t x) {
+  if (x <= 2) return 2;
+  uint64_t c = x | 1;
+  while (!is_prime(c)) c += 2;
+  return c;
+}
+
+bool slot_layout(const wc_table_config& c, uint64_t* slot_bytes) {
+  if (c.kind == WC_SINGLE_VALUE) {
+    if (c.key_bytes == 4 && c.value_bytes == 4) { *slot_bytes = 8; return true; }
+    if (c.key_bytes == 8 && c.value_bytes == 8) { *slot_bytes = 16; return true; }
+    return false;
+  }
+  if (c.kind == WC_MULTI_VALUE) {
+    if ((c.key_bytes == 4 || c.key_bytes == 8) && (c.value_bytes == 4 || c.value_bytes == 8)) {
+      *slot_bytes = 16;
+      return true;
+    }
+  }
+  return false;
+}
+
+bool window_ok(uint64_t slot_bytes, int W) {
+  if (slot_bytes == 8) return W == 4 || W == 8 || W == 16 || W == 32;
+  return W == 2 || W == 4 || W == 8 || W == 16;
+}
+
+bool shape_ok(const wc_table* t, int op, int G) {
+  const int W = static_cast<int>(t->W);
+  if (t->slot_bytes == 8) return sv_p32_shape_ok(W, G);
+  if (t->cfg.kind == WC_MULTI_VALUE && op == WC_OP_INSERT) return G == 1;  // aggregation kernels
+  return sv_p64_shape_ok(W, G);
+}
+
+// Default lanes per key: 32 bytes of the window per lane (one 256-bit load), else the
+// whole window in fewer bytes.
+int default_group(uint64_t slot_bytes, int W) {
+  const int per_lane = static_cast<int>(32 / slot_bytes);
+  return std::max(1, W / per_lane);
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+wc_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return WC_OK;
+  if (e == cudaErrorMemoryAllocation) return WC_ERR_OUT_OF_MEMORY;
+  return WC_ERR_CUDA;
+}
+
+// Bulk ops run on the table's device; restore the caller's device afterwards.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool aligned(const void* p, uint64_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace
+
+TableDesc desc_of(const wc_table* t) {
+  TableDesc d;
+  d.slots = t->d_slots;
+  d.seed = t->cfg.seed;
+  d.status = t->d_status;
+  d.size = t->d_size;
+  d.nkeys = t->d_nkeys;
+  d.p = static_cast<uint32_t>(t->windows);
+  d.W = static_cast<uint32_t>(t->W);
+  return d;
+}
+
+PoolDesc pool_of(const wc_table* t) {
+  PoolDesc p;
+  p.pool = t->d_pool;
+  p.cursor = t->d_cursor;
+  p.pending = t->d_pending;
+  p.capacity = t->pool_capacity;
+  p.value_bytes = t->cfg.value_bytes;
+  return p;
+}
+
+cudaLaunchAttribute* l2_attr(const wc_table* t, cudaLaunchAttribute* storage, unsigned* count) {
+  if (t == nullptr || t->l2_window_bytes == 0) {
+    *count = 0;
+    return nullptr;
+  }
+  storage[0].id = cudaLaunchAttributeAccessPolicyWindow;
+  storage[0].val.accessPolicyWindow.base_ptr = t->d_slots;
+  storage[0].val.accessPolicyWindow.num_bytes = t->l2_window_bytes;
+  storage[0].val.accessPolicyWindow.hitRatio = t->l2_hit_ratio;
+  storage[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+  storage[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+  *count = 1;
+  return storage;
+}
+
+int sm_count_of(int device) {
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n < 1) n = 1;
+  return n;
+}
+
+cudaError_t sv_launch(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n, void* out,
+                      uint8_t* found, cudaStream_t s) {
+  if (t->slot_bytes == 8) return sv_p32_launch(t, op, keys, vals, n, out, found, s);
+  return sv_p64_launch(t, op, keys, vals, n, out, found, s);
+}
+
+}  // namespace wc
+
+using namespace wc;
+
+extern "C" {
+
+const char* wc_status_string(wc_status s) {
+  switch (s) {
+    case WC_OK: return "ok";
+    case WC_ERR_INVALID_ARG: return "invalid argument";
+    case WC_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case WC_ERR_FULL: return "table full (probe limit reached)";
+    case WC_ERR_CUDA: return "CUDA runtime error";
+    case WC_ERR_TIMEOUT: return "bounded device wait timed out";
+    case WC_ERR_UNSUPPORTED: return "operation not supported for this table kind";
+  }
+  return "unknown status";
+}
+
+wc_status wc_plan_capacity(uint64_t min_capacity, int32_t window_width, uint64_t* h_windows,
+                           uint64_t* h_capacity) {
+  if (window_width < 1 || window_width > 64 || h_windows == nullptr || h_capacity == nullptr)
+    return WC_ERR_INVALID_ARG;
+  const uint64_t W = static_cast<uint64_t>(window_width);
+  const uint64_t want = std::max<uint64_t>(1, (min_capacity + W - 1) / W);
+  if (want >= (1ull << 32)) return WC_ERR_INVALID_ARG;
+  const uint64_t p = next_prime(want);
+  if (p >= (1ull << 32)) return WC_ERR_INVALID_ARG;
+  *h_windows = p;
+  *h_capacity = p * W;
+  return WC_OK;
+}
+
+wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
+  if (out == nullptr || cfg == nullptr) return WC_ERR_INVALID_ARG;
+  *out = nullptr;
+  uint64_t slot_bytes = 0;
+  if (!slot_layout(*cfg, &slot_bytes)) return WC_ERR_INVALID_ARG;
+  int W = cfg->window_width;
+  if (W == 0) W = slot_bytes == 8 ? 8 : 4;
+  if (!window_ok(slot_bytes, W)) return WC_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) return WC_ERR_CUDA;
+  const bool mv = cfg->kind == WC_MULTI_VALUE;
+  if (mv && cfg->value_pool_capacity > kMaxPool) return WC_ERR_INVALID_ARG;
+
+  uint64_t p = 0, cap = 0;
+  if (wc_plan_capacity(cfg->min_capacity, W, &p, &cap) != WC_OK) return WC_ERR_INVALID_ARG;
+
+  wc_table* t = new (std::nothrow) wc_table();
+  if (t == nullptr) return WC_ERR_OUT_OF_MEMORY;
+  t->cfg = *cfg;
+  t->cfg.window_width = W;
+  t->device = cfg->device;
+  t->windows = p;
+  t->W = static_cast<uint64_t>(W);
+  t->capacity = cap;
+  t->slot_bytes = slot_bytes;
+  t->table_bytes = cap * slot_bytes;
+  t->pool_capacity = mv ? cfg->value_pool_capacity : 0;
+
+  DeviceGuard guard(t->device);
+  t->sm_count = sm_count_of(t->device);
+
+  // One allocation: [slots | meta 256 B | pending (MV) | scan partials (MV) | pool (MV)]
+  const uint64_t off_meta = align_up(t->table_bytes, kAlign);
+  const uint64_t off_pending = off_meta + kAlign;
+  const uint64_t pending_bytes = mv ? align_up(cap * 4, kAlign) : 0;
+  const uint64_t off_partials = off_pending + pending_bytes;
+  t->partials_cap = mv ? scan_partials_needed(kMaxBatch + 1) : 0;
+  const uint64_t partial_bytes = align_up(t->partials_cap * 8, kAlign);
+  const uint64_t off_pool = off_partials + partial_bytes;
+  const uint64_t pool_bytes = align_up(t->pool_capacity * static_cast<uint64_t>(cfg->value_bytes), kAlign);
+  t->device_bytes = off_pool + pool_bytes;
+
+  if (cudaMalloc(&t->d_block, t->device_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete t;
+    return WC_ERR_OUT_OF_MEMORY;
+  }
+  char* base = static_cast<char*>(t->d_block);
+  t->d_slots = base;
+  t->d_status = reinterpret_cast<uint32_t*>(base + off_meta);
+  t->d_size = reinterpret_cast<unsigned long long*>(base + off_meta + 8);
+  t->d_nkeys = reinterpret_cast<unsigned long long*>(base + off_meta + 16);
+  t->d_cursor = reinterpret_cast<unsigned long long*>(base + off_meta + 24);
+  t->d_pending = mv ? reinterpret_cast<uint32_t*>(base + off_pending) : nullptr;
+  t->d_partials = mv ? reinterpret_cast<uint64_t*>(base + off_partials) : nullptr;
+  t->d_pool = mv ? static_cast<void*>(base + off_pool) : nullptr;
+
+  for (int op = 0; op < WC_OP__N; ++op) {
+    t->launch[op].group_size = default_group(slot_bytes, W);
+    t->launch[op].block_threads = 256;
+    t->launch[op].blocks_per_sm = 0;
+  }
+  if (mv) t->launch[WC_OP_INSERT].group_size = 1;
+
+  if (cfg->l2_persist) {
+    int max_persist = 0, max_window = 0;
+    cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, t->device);
+    cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, t->device);
+    if (max_persist > 0 && max_window > 0) {
+      const size_t persist = std::min<size_t>(t->table_bytes, static_cast<size_t>(max_persist));
+      size_t cur = 0;
+      cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+      if (cur < persist) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, persist);
+      cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+      t->l2_window_bytes = std::min<size_t>(t->table_bytes, static_cast<size_t>(max_window));
+      t->l2_hit_ratio = std::min(1.0f, static_cast<float>(cur) / static_cast<float>(t->l2_window_bytes));
+    }
+    cudaGetLastError();
+  }
+
+  t->clear_bytes = off_partials;
+  if (cudaMemset(t->d_block, 0, t->clear_bytes) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    cudaFree(t->d_block);
+    delete t;
+    return WC_ERR_CUDA;
+  }
+  *out = t;
+  return WC_OK;
+}
+
+wc_status wc_table_destroy(wc_table* t) {
+  if (t == nullptr) return WC_ERR_INVALID_ARG;
+  DeviceGuard guard(t->device);
+  cudaError_t e = cudaFree(t->d_block);
+  delete t;
+  return cuda_status(e);
+}
+
+wc_status wc_table_clear(wc_table* t, void* stream) {
+  if (t == nullptr) return WC_ERR_INVALID_ARG;
+  DeviceGuard guard(t->device);
+  return cuda_status(cudaMemsetAsync(t->d_block, 0, t->clear_bytes, as_stream(stream)));
+}
+
+wc_status wc_table_get_info(const wc_table* t, wc_table_info* h_out) {
+  if (t == nullptr || h_out == nullptr) return WC_ERR_INVALID_ARG;
+  h_out->capacity = t->capacity;
+  h_out->windows = t->windows;
+  h_out->slot_bytes = t->slot_bytes;
+  h_out->table_bytes = t->table_bytes;
+  h_out->pool_capacity = t->pool_capacity;
+  h_out->device_bytes = t->device_bytes;
+  h_out->window_width = static_cast<int32_t>(t->W);
+  h_out->kind = t->cfg.kind;
+  return WC_OK;
+}
+
+wc_status wc_table_set_launch(wc_table* t, int32_t op, const wc_launch* launch) {
+  if (t == nullptr || launch == nullptr || op < 0 || op >= WC_OP__N) return WC_ERR_INVALID_ARG;
+  const int b = launch->block_threads;
+  if (b < 32 || b > 256 || b % 32 != 0 || launch->blocks_per_sm < 0 || launch->blocks_per_sm > 64)
+    return WC_ERR_INVALID_ARG;
+  if (!shape_ok(t, op, launch->group_size)) return WC_ERR_INVALID_ARG;
+  t->launch[op] = *launch;
+  return WC_OK;
+}
+
+wc_status wc_table_get_launch(const wc_table* t, int32_t op, wc_launch* h_out) {
+  if (t == nullptr || h_out == nullptr || op < 0 || op >= WC_OP__N) return WC_ERR_INVALID_ARG;
+  *h_out = t->launch[op];
+  return WC_OK;
+}
+
+static wc_status check_bulk(const wc_table* t, const void* keys, uint64_t n) {
+  if (t == nullptr) return WC_ERR_INVALID_ARG;
+  if (n > kMaxBatch) return WC_ERR_INVALID_ARG;
+  if (n > 0 && keys == nullptr) return WC_ERR_INVALID_ARG;
+  if (n > 0 && !aligned(keys, static_cast<uint64_t>(t->cfg.key_bytes))) return WC_ERR_INVALID_ARG;
+  return WC_OK;
+}
+
+wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint64_t n, void* stream) {
+  wc_status st = check_bulk(t, d_keys, n);
+  if (st != WC_OK) return st;
+  if (n > 0 && (d_values == nullptr || !aligned(d_values, static_cast<uint64_t>(t->cfg.value_bytes))))
+    return WC_ERR_INVALID_ARG;
+  if (n == 0) return WC_OK;
+  DeviceGuard guard(t->device);
+  if (t->cfg.kind == WC_MULTI_VALUE) return cuda_status(mv_insert(t, d_keys, d_values, n, as_stream(stream)));
+  return cuda_status(sv_launch(t, WC_OP_INSERT, d_keys, d_values, n, nullptr, nullptr, as_stream(stream)));
+}
+
+wc_status wc_retrieve(wc_table* t, const void* d_keys, uint64_t n, void* d_values_out, uint8_t* d_found_or_null,
+                      void* stream) {
+  wc_status st = check_bulk(t, d_keys, n);
+  if (st != WC_OK) return st;
+  if (t->cfg.kind != WC_SINGLE_VALUE) return WC_ERR_UNSUPPORTED;
+  if (n > 0 && (d_values_out == nullptr || !aligned(d_values_out, static_cast<uint64_t>(t->cfg.value_bytes))))
+    return WC_ERR_INVALID_ARG;
+  if (n == 0) return WC_OK;
+  DeviceGuard guard(t->device);
+  return cuda_status(
+      sv_launch(t, WC_OP_RETRIEVE, d_keys, nullptr, n, d_values_out, d_found_or_null, as_stream(stream)));
+}
+
+wc_status wc_erase(wc_table* t, const void* d_keys, uint64_t n, void* stream) {
+  wc_status st = check_bulk(t, d_keys, n);
+  if (st != WC_OK) return st;
+  if (n == 0) return WC_OK;
+  DeviceGuard guard(t->device);
+  if (t->cfg.kind == WC_MULTI_VALUE) return cuda_status(mv_erase(t, d_keys, n, as_stream(stream)));
+  return cuda_status(sv_launch(t, WC_OP_ERASE, d_keys, nullptr, n, nullptr, nullptr, as_stream(stream)));
+}
+
+wc_status wc_count_values(wc_table* t, const void* d_keys, uint64_t n, uint64_t* d_offsets,
+                          uint64_t* h_total_or_null, void* stream) {
+  wc_status st = check_bulk(t, d_keys, n);
+  if (st != WC_OK) return st;
+  if (t->cfg.kind != WC_MULTI_VALUE) return WC_ERR_UNSUPPORTED;
+  if (d_offsets == nullptr || !aligned(d_offsets, 8)) return WC_ERR_INVALID_ARG;
+  DeviceGuard guard(t->device);
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = mv_count(t, d_keys, n, d_offsets, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (h_total_or_null != nullptr) {
+    e = cudaMemcpyAsync(h_total_or_null, d_offsets + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  return cuda_status(e);
+}
+
+wc_status wc_retrieve_multi(wc_table* t, const void* d_keys, uint64_t n, const uint64_t* d_offsets,
+                            void* d_values_out, void* stream) {
+  wc_status st = check_bulk(t, d_keys, n);
+  if (st != WC_OK) return st;
+  if (t->cfg.kind != WC_MULTI_VALUE) return WC_ERR_UNSUPPORTED;
+  if (d_offsets == nullptr || !aligned(d_offsets, 8)) return WC_ERR_INVALID_ARG;
+  if (d_values_out != nullptr && !aligned(d_values_out, static_cast<uint64_t>(t->cfg.value_bytes)))
+    return WC_ERR_INVALID_ARG;
+  if (n == 0) return WC_OK;
+  DeviceGuard guard(t->device);
+  return cuda_status(mv_retrieve_multi(t, d_keys, n, d_offsets, d_values_out, as_stream(stream)));
+}
+
+static wc_status read_counter(wc_table* t, const void* dptr, size_t bytes, void* host, void* stream) {
+  if (t == nullptr || host == nullptr) return WC_ERR_INVALID_ARG;
+  DeviceGuard guard(t->device);
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = cudaMemcpyAsync(host, dptr, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_status(e);
+}
+
+wc_status wc_size(wc_table* t, uint64_t* h_out, void* stream) {
+  if (t == nullptr) return WC_ERR_INVALID_ARG;
+  return read_counter(t, t->d_size, sizeof(uint64_t), h_out, stream);
+}
+
+wc_status wc_num_keys(wc_table* t, uint64_t* h_out, void* stream) {
+  if (t == nullptr) return WC_ERR_INVALID_ARG;
+  return read_counter(t, t->cfg.kind == WC_MULTI_VALUE ? t->d_nkeys : t->d_size, sizeof(uint64_t), h_out, stream);
+}
+
+wc_status wc_load_factor(wc_table* t, double* h_out, void* stream) {
+  if (t == nullptr || h_out == nullptr) return WC_ERR_INVALID_ARG;
+  uint64_t live = 0;
+  wc_status st = wc_num_keys(t, &live, stream);
+  if (st != WC_OK) return st;
+  *h_out = static_cast<double>(live) / static_cast<double>(t->capacity);
+  return WC_OK;
+}
+
+wc_status wc_get_status(wc_table* t, uint32_t* h_flags, int32_t clear, void* stream) {
+  if (t == nullptr || h_flags == nullptr) return WC_ERR_INVALID_ARG;
+  wc_status st = read_counter(t, t->d_status, sizeof(uint32_t), h_flags, stream);
+  if (st != WC_OK || !clear) return st;
+  DeviceGuard guard(t->device);
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = cudaMemsetAsync(t->d_status, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_status(e);
+}
+
+}  // extern "C"

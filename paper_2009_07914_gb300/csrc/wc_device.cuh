@@ -1,0 +1,222 @@
+// Device-side building blocks shared by every kernel of the library: slot layouts, the
+// outer probing scheme, window loads, group votes and status accounting.
+//
+// Probing (Sec. IV-B2, cooperative probing scheme): the table is p windows of W slots,
+// p prime.  A key visits windows w_j = (w_0 + j * step) mod p, j = 0..p-1 (outer
+// double hashing; step in [1, p-1] and p prime make the sequence visit every window
+// exactly once), and inside a window all W slots at once (inner linear probing).  A
+// group of G lanes reads one window together: lane r holds slots [r*S, r*S + S) with
+// S = W / G, so slot order inside a window is (lane, sub-slot) order.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wc {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+// Device status-word bits (same values as WC_FLAG_* of the public header).
+enum : uint32_t {
+  kFlagDuplicate = 1u,
+  kFlagInvalid = 2u,
+  kFlagProbeLimit = 4u,
+  kFlagPoolExhausted = 8u,
+  kFlagCountOverflow = 16u,
+  kFlagQueueTimeout = 32u,
+};
+
+// MurmurHash3's 64-bit finalizer "fmix64" (A. Appleby, public domain): an invertible
+// avalanche mix.  h1 and h2 of the outer double hashing are its two 32-bit halves.
+__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+// w_0 = floor(h1 * p / 2^32), step = 1 + floor(h2 * (p - 1) / 2^32); requires p >= 2.
+__device__ __forceinline__ void probe_init(uint64_t key, uint64_t seed, uint32_t p, uint32_t& w,
+                                           uint32_t& step) {
+  const uint64_t h = fmix64(key ^ seed);
+  w = __umulhi(static_cast<uint32_t>(h >> 32), p);
+  step = 1u + __umulhi(static_cast<uint32_t>(h), p - 1u);
+}
+
+// (w + step) mod p for w, step < p < 2^32 (the u32 sum may wrap).
+__device__ __forceinline__ uint32_t probe_next(uint32_t w, uint32_t step, uint32_t p) {
+  uint32_t x = w + step;
+  if (x < w || x >= p) x -= p;
+  return x;
+}
+
+// ---- vector loads that bypass L1 (L2 is the coherence point for CAS) ----------------
+
+__device__ __forceinline__ void ldcg1(const void* p, unsigned long long (&u)[1]) {
+  asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(u[0]) : "l"(p));
+}
+__device__ __forceinline__ void ldcg2(const void* p, unsigned long long* u) {
+  asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(u[0]), "=l"(u[1]) : "l"(p));
+}
+__device__ __forceinline__ void ldcg4(const void* p, unsigned long long* u) {
+  asm volatile("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];"
+               : "=l"(u[0]), "=l"(u[1]), "=l"(u[2]), "=l"(u[3])
+               : "l"(p));
+}
+
+// Load N 64-bit words (N in 1, 2, 4, 8; address aligned to min(8N, 32) bytes).
+template <int N>
+__device__ __forceinline__ void load_words(const unsigned long long* p, unsigned long long (&u)[N]) {
+  if constexpr (N == 1) {
+    ldcg1(p, u);
+  } else if constexpr (N == 2) {
+    ldcg2(p, u);
+  } else if constexpr (N == 4) {
+    ldcg4(p, u);
+  } else {
+    static_assert(N % 4 == 0, "word count");
+#pragma unroll
+    for (int i = 0; i < N; i += 4) ldcg4(p + i, u + i);
+  }
+}
+
+// ---- slot layouts ---------------------------------------------------------------------
+
+// Packed array-of-structs slot (Sec. IV-B1): a uint32 key in the low half and a uint32
+// value in the high half of one 64-bit word, so one 64-bit CAS stores both.
+struct LayoutP32 {
+  using Key = uint32_t;
+  using Val = uint32_t;
+  struct Slot {
+    unsigned long long w;
+  };
+  static constexpr int kWords = 1;
+  static constexpr Key kEmpty = 0u;
+  static constexpr Key kTomb = 0xffffffffu;
+  static constexpr Val kNotFound = 0xffffffffu;
+  __device__ static Key key(const Slot& s) { return static_cast<uint32_t>(s.w); }
+  __device__ static Val val(const Slot& s) { return static_cast<uint32_t>(s.w >> 32); }
+  __device__ static Slot make(Key k, Val v) { return Slot{(static_cast<unsigned long long>(v) << 32) | k}; }
+  __device__ static Slot tomb() { return Slot{0xffffffffull}; }
+  __device__ static Slot from_words(const unsigned long long* u) { return Slot{u[0]}; }
+  __device__ static bool cas(Slot* p, const Slot& e, const Slot& d) {
+    return atomicCAS(&p->w, e.w, d.w) == e.w;
+  }
+  __device__ static void store_val(Slot* p, Val v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(reinterpret_cast<uint32_t*>(&p->w) + 1), "r"(v)
+                 : "memory");
+  }
+  __device__ static Slot shfl(const Slot& s, int src) { return Slot{__shfl_sync(kFull, s.w, src)}; }
+};
+
+// 16-byte array-of-structs slot {uint64 key, uint64 value}, claimed with one 128-bit CAS
+// (atom.cas.b128, sm_90 and later).  The paper's GV100 had only 64-bit CAS and had to
+// swap the key first and store the value afterwards (Sec. II, hazard (1) of Sec. IV-D);
+// one 16-byte CAS stores the pair at once.
+struct LayoutP64 {
+  using Key = unsigned long long;
+  using Val = unsigned long long;
+  struct Slot {
+    unsigned long long k, v;
+  };
+  static constexpr int kWords = 2;
+  static constexpr Key kEmpty = 0ull;
+  static constexpr Key kTomb = ~0ull;
+  static constexpr Val kNotFound = ~0ull;
+  __device__ static Key key(const Slot& s) { return s.k; }
+  __device__ static Val val(const Slot& s) { return s.v; }
+  __device__ static Slot make(Key k, Val v) { return Slot{k, v}; }
+  __device__ static Slot tomb() { return Slot{~0ull, 0ull}; }
+  __device__ static Slot from_words(const unsigned long long* u) { return Slot{u[0], u[1]}; }
+  __device__ static bool cas(Slot* p, const Slot& e, const Slot& d) {
+    unsigned long long olo, ohi;
+    asm volatile(
+        "{\n\t.reg .b128 e, d, o;\n\t"
+        "mov.b128 e, {%2, %3};\n\t"
+        "mov.b128 d, {%4, %5};\n\t"
+        "atom.global.cas.b128 o, [%6], e, d;\n\t"
+        "mov.b128 {%0, %1}, o;\n\t}"
+        : "=l"(olo), "=l"(ohi)
+        : "l"(e.k), "l"(e.v), "l"(d.k), "l"(d.v), "l"(p)
+        : "memory");
+    return olo == e.k && ohi == e.v;
+  }
+  __device__ static void store_val(Slot* p, Val v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(&p->v), "l"(v) : "memory");
+  }
+  __device__ static Slot shfl(const Slot& s, int src) {
+    return Slot{__shfl_sync(kFull, s.k, src), __shfl_sync(kFull, s.v, src)};
+  }
+};
+
+// S consecutive slots of one lane.
+template <class L, int S>
+__device__ __forceinline__ void load_slots(const typename L::Slot* p, typename L::Slot (&s)[S]) {
+  unsigned long long u[S * L::kWords];
+  load_words<S * L::kWords>(reinterpret_cast<const unsigned long long*>(p), u);
+#pragma unroll
+  for (int i = 0; i < S; ++i) s[i] = L::from_words(u + i * L::kWords);
+}
+
+// s[i] selected without dynamic register indexing.
+template <class L, int S>
+__device__ __forceinline__ typename L::Slot pick(const typename L::Slot (&s)[S], int i) {
+  typename L::Slot x = s[0];
+#pragma unroll
+  for (int k = 1; k < S; ++k)
+    if (i == k) x = s[k];
+  return x;
+}
+
+// My group's G bits of a warp ballot.
+template <int G>
+__device__ __forceinline__ uint32_t group_bits(uint32_t ballot, int gbase) {
+  if constexpr (G == 32) {
+    return ballot;
+  } else {
+    return (ballot >> gbase) & ((1u << G) - 1u);
+  }
+}
+
+template <int G>
+__device__ __forceinline__ uint32_t group_vote(bool pred, int gbase) {
+  if constexpr (G == 1) {
+    return pred ? 1u : 0u;
+  } else {
+    return group_bits<G>(__ballot_sync(kFull, pred), gbase);
+  }
+}
+
+// Hand each idle group of the warp the next input position of the warp's range
+// [next, end).  `next` is warp-uniform and advances by the number of idle groups.
+// Positions go to idle groups in lane order, so a warp reads its inputs nearly
+// contiguously.  Returns true if this lane's group received a position.
+__device__ __forceinline__ bool take_next(bool idle, int r, int gbase, uint64_t& next, uint64_t end,
+                                          uint64_t& pos) {
+  const uint32_t idle_leaders = __ballot_sync(kFull, idle && r == 0);
+  const uint64_t mine = next + __popc(idle_leaders & ((1u << gbase) - 1u));
+  next += __popc(idle_leaders);
+  if (idle && mine < end) {
+    pos = mine;
+    return true;
+  }
+  return false;
+}
+
+// Warp-aggregated status and counter updates, once per warp at kernel end.
+__device__ __forceinline__ void flush_flags(uint32_t* status, uint32_t flags) {
+  flags = __reduce_or_sync(kFull, flags);
+  if ((threadIdx.x & 31) == 0 && flags) atomicOr(status, flags);
+}
+
+__device__ __forceinline__ void flush_delta(unsigned long long* counter, long long delta) {
+  // butterfly sum over the warp, then one atomic per warp
+  long long d = delta;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+  if ((threadIdx.x & 31) == 0 && d != 0) atomicAdd(counter, static_cast<unsigned long long>(d));
+}
+
+}  // namespace wc

@@ -1,0 +1,97 @@
+// Host-side internals shared by the library's translation units: the table object
+// behind the opaque wc_table handle, the by-value descriptors kernels receive, and the
+// launcher entry points of each kernel family.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "wc.h"
+
+namespace wc {
+
+// What every single-value / key-store kernel needs, passed by value.
+struct TableDesc {
+  void* slots;                       // p * W slots, 256-byte aligned
+  uint64_t seed;                     // hash seed
+  uint32_t* status;                  // device status word (WC_FLAG_* bits)
+  unsigned long long* size;          // SV: live keys; MV: stored pairs
+  unsigned long long* nkeys;         // MV: distinct live keys
+  uint32_t p;                        // windows (prime)
+  uint32_t W;                        // slots per window
+};
+
+// Multi-value extras.
+struct PoolDesc {
+  void* pool;                        // value elements (value_bytes each)
+  unsigned long long* cursor;        // next free pool element
+  uint32_t* pending;                 // per key-store slot: this call's count / cursor
+  uint64_t capacity;                 // pool elements
+  int32_t value_bytes;               // 4 or 8
+};
+
+// Shape of one launch after the table's tuning was applied.
+struct LaunchShape {
+  int group;           // lanes per key
+  int block;           // threads per block
+  int blocks_per_sm;   // 0 = occupancy limit
+};
+
+}  // namespace wc
+
+struct wc_table {
+  wc_table_config cfg;
+  int device;
+  int sm_count;
+  uint64_t windows;      // p
+  uint64_t W;
+  uint64_t capacity;     // p * W
+  uint64_t slot_bytes;
+  uint64_t table_bytes;
+  uint64_t pool_capacity;
+  uint64_t device_bytes;
+  uint64_t clear_bytes;  // prefix of d_block zeroed by a clear (slots, meta, pending)
+  void* d_block;         // the single allocation holding everything below
+  void* d_slots;
+  uint32_t* d_status;
+  unsigned long long* d_size;
+  unsigned long long* d_nkeys;
+  unsigned long long* d_cursor;
+  uint32_t* d_pending;   // MV: capacity entries
+  uint64_t* d_partials;  // MV: scan partial sums
+  uint64_t partials_cap;
+  void* d_pool;
+  wc_launch launch[WC_OP__N];
+  size_t l2_window_bytes;  // > 0: launch with an L2 access-policy window over the slots
+  float l2_hit_ratio;
+};
+
+namespace wc {
+
+TableDesc desc_of(const wc_table* t);
+PoolDesc pool_of(const wc_table* t);
+
+// Launch with the table's L2 access-policy window when it has one.
+cudaLaunchAttribute* l2_attr(const wc_table* t, cudaLaunchAttribute* storage, unsigned* count);
+
+// Single-value families (wc_sv.cu): op is WC_OP_INSERT / RETRIEVE / ERASE.
+cudaError_t sv_launch(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n,
+                      void* out, uint8_t* found, cudaStream_t s);
+bool sv_shape_ok(int slot_bytes, int W, int G);
+
+// Multi-value families (wc_mv.cu).
+cudaError_t mv_insert(const wc_table* t, const void* keys, const void* vals, uint64_t n, cudaStream_t s);
+cudaError_t mv_count(const wc_table* t, const void* keys, uint64_t n, uint64_t* offsets, cudaStream_t s);
+cudaError_t mv_retrieve_multi(const wc_table* t, const void* keys, uint64_t n, const uint64_t* offsets,
+                              void* out, cudaStream_t s);
+cudaError_t mv_erase(const wc_table* t, const void* keys, uint64_t n, cudaStream_t s);
+
+// Exclusive scan of n uint64 in place, d[n] = total (wc_scan.cu).
+cudaError_t scan_exclusive_u64(uint64_t* d, uint64_t n, uint64_t* partials, uint64_t partials_cap,
+                               cudaStream_t s);
+uint64_t scan_partials_needed(uint64_t n);
+
+int sm_count_of(int device);
+
+}  // namespace wc

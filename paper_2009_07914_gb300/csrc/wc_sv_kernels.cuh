@@ -1,0 +1,358 @@
+// Single-value bulk kernels: insert, retrieve, erase (Sec. IV-B2 .. IV-B5).
+//
+// One group of G lanes serves one key at a time (the cooperative group of Sec. IV-B2).
+// Every warp runs a warp-uniform loop; one trip probes ONE window for every group of
+// the warp that holds a key, so all of the warp's window loads are in flight together.
+// A group that finishes a key takes the next input position of its warp's range in the
+// same trip (take_next), which keeps every lane busy until the range is exhausted
+// instead of idling behind the warp's longest probe sequence.
+//
+// Insert claims the earliest candidate slot of the key's probing sequence (steps 1-7 of
+// Sec. IV-B2).  A tombstone is a candidate (Sec. IV-B5), but probing continues past it
+// to the first window holding an empty slot or the key itself, so a key erased and
+// inserted again can never be stored twice; with no tombstones in the table this is
+// exactly the paper's insertion.  Retrieval stops at the key or at the first window
+// that holds an empty slot (valid because a slot never returns to empty except by a
+// clear, Sec. IV-B4).
+#pragma once
+
+#include "wc_device.cuh"
+#include "wc_internal.h"
+
+namespace wc {
+
+template <class L, int G, int S>
+struct SvLane {
+  static constexpr int W = G * S;
+  int lane, r, gbase;
+  __device__ SvLane() {
+    lane = threadIdx.x & 31;
+    r = lane & (G - 1);
+    gbase = lane - r;
+  }
+};
+
+// Masks of one lane's S slots: bit i set if slot i holds the key / is empty / is a
+// tombstone.
+template <class L, int S>
+__device__ __forceinline__ void classify(const typename L::Slot (&s)[S], typename L::Key k, uint32_t& mm,
+                                         uint32_t& me, uint32_t& mt) {
+  mm = me = mt = 0;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    const typename L::Key kk = L::key(s[i]);
+    mm |= static_cast<uint32_t>(kk == k) << i;
+    me |= static_cast<uint32_t>(kk == L::kEmpty) << i;
+    mt |= static_cast<uint32_t>(kk == L::kTomb) << i;
+  }
+}
+
+template <class K>
+__device__ __forceinline__ bool is_sentinel(K k) {
+  return k == K(0) || k == K(~K(0));
+}
+
+// Range of input positions of this warp: [begin, end).
+__device__ __forceinline__ void warp_range(uint64_t n, uint64_t per_warp, uint64_t& begin, uint64_t& end) {
+  const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  begin = warp * per_warp;
+  end = begin + per_warp < n ? begin + per_warp : n;
+}
+
+// ---------------------------------------------------------------------------------------
+// retrieve: out[i] = value of keys[i] or NOT_FOUND; found[i] = 1/0 (Sec. IV-B4).
+// Emit is called by one lane per finished query: emit(pos, hit, slot).
+template <class L, int G, int S, class Emit, class KIn = typename L::Key>
+__device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn* __restrict__ keys,
+                                                  uint64_t next, uint64_t end, Emit& emit, uint32_t& flags) {
+  using Slot = typename L::Slot;
+  using Key = typename L::Key;
+  const SvLane<L, G, S> ln;
+  constexpr int W = G * S;
+  const Slot* slots = static_cast<const Slot*>(t.slots);
+  bool act = false;
+  uint64_t pos = 0;
+  Key k = 0;
+  uint32_t w = 0, step = 0, j = 0;
+  while (true) {
+    uint64_t np;
+    if (take_next(!act, ln.r, ln.gbase, next, end, np)) {
+      pos = np;
+      const KIn kin = keys[pos];
+      k = static_cast<Key>(kin);
+      if (is_sentinel(kin)) {
+        flags |= kFlagInvalid;
+        if (ln.r == 0) emit(pos, false, Slot{});
+      } else {
+        act = true;
+        j = 0;
+        probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step);
+      }
+    }
+    if (__ballot_sync(kFull, act) == 0) {
+      if (next >= end) break;
+      continue;
+    }
+    Slot s[S];
+    uint32_t mm = 0, me = 0, mt = 0;
+    if (act) {
+      load_slots<L, S>(slots + static_cast<uint64_t>(w) * W + ln.r * S, s);
+      classify<L, S>(s, k, mm, me, mt);
+    }
+    const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
+    const uint32_t be = group_vote<G>(me != 0, ln.gbase);
+    Slot hit = pick<L, S>(s, mm ? __ffs(mm) - 1 : 0);
+    if constexpr (G > 1) hit = L::shfl(hit, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
+    if (act) {
+      if (bm) {
+        if (ln.r == 0) emit(pos, true, hit);
+        act = false;
+      } else if (be || ++j >= t.p) {
+        if (ln.r == 0) emit(pos, false, hit);
+        act = false;
+      } else {
+        w = probe_next(w, step, t.p);
+      }
+    }
+  }
+}
+
+template <class L>
+struct EmitValue {
+  typename L::Val* __restrict__ out;
+  uint8_t* __restrict__ found;
+  __device__ void operator()(uint64_t pos, bool hit, const typename L::Slot& s) const {
+    out[pos] = hit ? L::val(s) : L::kNotFound;
+    if (found) found[pos] = hit ? 1 : 0;
+  }
+};
+
+template <class L, int G, int S>
+__global__ void __launch_bounds__(256) k_sv_retrieve(TableDesc t, const typename L::Key* __restrict__ keys, uint64_t n,
+                                                     uint64_t per_warp, typename L::Val* __restrict__ out,
+                                                     uint8_t* __restrict__ found) {
+  uint64_t begin, end;
+  warp_range(n, per_warp, begin, end);
+  if (begin >= end) return;
+  uint32_t flags = 0;
+  EmitValue<L> emit{out, found};
+  sv_retrieve_range<L, G, S>(t, keys, begin, end, emit, flags);
+  flush_flags(t.status, flags);
+}
+
+// ---------------------------------------------------------------------------------------
+// insert (Sec. IV-B2 steps 1-7, Sec. IV-B3).  Returns through `added` the number of new
+// keys this lane's groups stored (counted by lane r == 0 of each group).
+template <class L, int G, int S>
+__device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typename L::Key* __restrict__ keys,
+                                                const typename L::Val* __restrict__ vals, uint64_t next,
+                                                uint64_t end, uint32_t& flags, long long& added) {
+  using Slot = typename L::Slot;
+  using Key = typename L::Key;
+  using Val = typename L::Val;
+  const SvLane<L, G, S> ln;
+  constexpr int W = G * S;
+  Slot* slots = static_cast<Slot*>(t.slots);
+  bool act = false;
+  uint64_t pos = 0;
+  Key k = 0;
+  Val v = 0;
+  uint32_t w = 0, step = 0, j = 0;
+  bool have_t = false;     // a tombstone earlier on the sequence is remembered
+  uint64_t t_slot = 0;     // its slot index
+  Slot t_word{};           // and the word read there
+  while (true) {
+    uint64_t np;
+    if (take_next(!act, ln.r, ln.gbase, next, end, np)) {
+      pos = np;
+      k = keys[pos];
+      if (is_sentinel(k)) {
+        flags |= kFlagInvalid;
+      } else {
+        v = vals[pos];
+        act = true;
+        j = 0;
+        have_t = false;
+        probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step);
+      }
+    }
+    if (__ballot_sync(kFull, act) == 0) {
+      if (next >= end) break;
+      continue;
+    }
+    Slot s[S];
+    uint32_t mm = 0, me = 0, mt = 0;
+    const uint64_t lane_slot = static_cast<uint64_t>(w) * W + ln.r * S;
+    if (act) {
+      load_slots<L, S>(slots + lane_slot, s);
+      classify<L, S>(s, k, mm, me, mt);
+    }
+    const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
+    const uint32_t be = group_vote<G>(me != 0, ln.gbase);
+    const uint32_t bt = group_vote<G>(mt != 0, ln.gbase);
+    const uint32_t bc = group_vote<G>((me | mt) != 0, ln.gbase);
+    const bool last = j + 1 >= t.p;
+    const bool claim = bm == 0 && (be != 0 || last);
+
+    // The key is present: overwrite its value (duplicate warning, Sec. IV-B3).
+    if (act && bm && ln.r == __ffs(bm) - 1) L::store_val(slots + lane_slot + (__ffs(mm) - 1), v);
+
+    // Claim the earliest candidate: a remembered tombstone from an earlier window,
+    // else the first empty-or-tombstone slot of this window (Sec. IV-B2 steps 4 and 6).
+    bool ok = false;
+    if (act && claim) {
+      if (have_t) {
+        if (ln.r == 0) ok = L::cas(slots + t_slot, t_word, L::make(k, v));
+      } else if (bc && ln.r == __ffs(bc) - 1) {
+        const int sub = __ffs(me | mt) - 1;
+        ok = L::cas(slots + lane_slot + sub, pick<L, S>(s, sub), L::make(k, v));
+      }
+    }
+    if constexpr (G > 1) ok = __shfl_sync(kFull, ok, ln.gbase + ((have_t || bc == 0) ? 0 : __ffs(bc) - 1));
+
+    // Remember the first tombstone met before the terminating window.  The branch is
+    // warp-uniform, so every lane reaches the same shuffles.
+    uint64_t nt_slot = 0;
+    Slot nt_word{};
+    if (__any_sync(kFull, act && !claim && bt != 0 && !have_t)) {
+      const int sub = mt ? __ffs(mt) - 1 : 0;
+      nt_slot = lane_slot + sub;
+      nt_word = pick<L, S>(s, sub);
+      if constexpr (G > 1) {
+        const int tl = ln.gbase + (bt ? __ffs(bt) - 1 : 0);
+        nt_slot = __shfl_sync(kFull, nt_slot, tl);
+        nt_word = L::shfl(nt_word, tl);
+      }
+    }
+
+    if (act) {
+      if (bm) {
+        flags |= kFlagDuplicate;
+        act = false;
+      } else if (claim) {
+        if (ok) {
+          if (ln.r == 0) ++added;
+          act = false;
+        } else if (have_t) {
+          // the remembered tombstone was taken: probe again from the start
+          have_t = false;
+          j = 0;
+          probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step);
+        } else if (bc == 0) {
+          flags |= kFlagProbeLimit;  // every window visited, nothing to claim
+          act = false;
+        }
+        // else: lost the race for a slot of this window; read it again
+      } else {
+        if (bt && !have_t) {
+          have_t = true;
+          t_slot = nt_slot;
+          t_word = nt_word;
+        }
+        ++j;
+        w = probe_next(w, step, t.p);
+      }
+    }
+  }
+}
+
+template <class L, int G, int S>
+__global__ void __launch_bounds__(256) k_sv_insert(TableDesc t, const typename L::Key* __restrict__ keys,
+                                                   const typename L::Val* __restrict__ vals, uint64_t n,
+                                                   uint64_t per_warp) {
+  uint64_t begin, end;
+  warp_range(n, per_warp, begin, end);
+  if (begin >= end) return;
+  uint32_t flags = 0;
+  long long added = 0;
+  sv_insert_range<L, G, S>(t, keys, vals, begin, end, flags, added);
+  flush_flags(t.status, flags);
+  flush_delta(t.size, added);
+}
+
+// ---------------------------------------------------------------------------------------
+// erase (Sec. IV-B5): the key's slot becomes a tombstone.  `removed` counts erased keys;
+// on_erase(slot) sees the word that was replaced (multi-value tables use it to adjust
+// their pair count).
+template <class L, int G, int S, class OnErase, class KIn = typename L::Key>
+__device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __restrict__ keys,
+                                               uint64_t next, uint64_t end, uint32_t& flags, long long& removed,
+                                               OnErase& on_erase) {
+  using Slot = typename L::Slot;
+  using Key = typename L::Key;
+  const SvLane<L, G, S> ln;
+  constexpr int W = G * S;
+  Slot* slots = static_cast<Slot*>(t.slots);
+  bool act = false;
+  Key k = 0;
+  uint32_t w = 0, step = 0, j = 0;
+  while (true) {
+    uint64_t np;
+    if (take_next(!act, ln.r, ln.gbase, next, end, np)) {
+      const KIn kin = keys[np];
+      k = static_cast<Key>(kin);
+      if (is_sentinel(kin)) {
+        flags |= kFlagInvalid;
+      } else {
+        act = true;
+        j = 0;
+        probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step);
+      }
+    }
+    if (__ballot_sync(kFull, act) == 0) {
+      if (next >= end) break;
+      continue;
+    }
+    Slot s[S];
+    uint32_t mm = 0, me = 0, mt = 0;
+    const uint64_t lane_slot = static_cast<uint64_t>(w) * W + ln.r * S;
+    if (act) {
+      load_slots<L, S>(slots + lane_slot, s);
+      classify<L, S>(s, k, mm, me, mt);
+    }
+    const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
+    const uint32_t be = group_vote<G>(me != 0, ln.gbase);
+    bool ok = false;
+    if (act && bm && ln.r == __ffs(bm) - 1) {
+      const int sub = __ffs(mm) - 1;
+      const Slot old = pick<L, S>(s, sub);
+      ok = L::cas(slots + lane_slot + sub, old, L::tomb());
+      if (ok) on_erase(old);
+    }
+    if constexpr (G > 1) ok = __shfl_sync(kFull, ok, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
+    if (act) {
+      if (bm) {
+        if (ok) {
+          if (ln.r == 0) ++removed;
+          act = false;
+        }
+        // else: another erase of the same key won; read the window again
+      } else if (be || ++j >= t.p) {
+        act = false;  // absent: nothing to erase
+      } else {
+        w = probe_next(w, step, t.p);
+      }
+    }
+  }
+}
+
+struct NoOnErase {
+  template <class Slot>
+  __device__ void operator()(const Slot&) const {}
+};
+
+template <class L, int G, int S>
+__global__ void __launch_bounds__(256) k_sv_erase(TableDesc t, const typename L::Key* __restrict__ keys, uint64_t n,
+                                                  uint64_t per_warp) {
+  uint64_t begin, end;
+  warp_range(n, per_warp, begin, end);
+  if (begin >= end) return;
+  uint32_t flags = 0;
+  long long removed = 0;
+  NoOnErase none;
+  sv_erase_range<L, G, S>(t, keys, begin, end, flags, removed, none);
+  flush_flags(t.status, flags);
+  flush_delta(t.size, -removed);
+}
+
+}  // namespace wc

@@ -1,0 +1,71 @@
+"""The C-ABI library loads without a GPU and exports every function include/*.h
+declares; host-only entry points work here (no compute calls)."""
+from __future__ import annotations
+
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2009_07914_gb300 import build
+    build.build()
+    import paper_2009_07914_gb300 as wc
+    return wc.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(wc[a-z0-9_]*)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_north_star_calls():
+    names = declared_functions()
+    for want in ("wc_table_create", "wc_table_destroy", "wc_insert", "wc_retrieve", "wc_erase",
+                 "wc_count_values", "wc_retrieve_multi", "wc_size", "wc_load_factor"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_plan_capacity_primes(lib):
+    import sympy
+    from paper_2009_07914_gb300 import api
+    for n, alpha, W in [(1 << 20, 0.8, 32), (1 << 27, 0.5, 32), (1 << 27, 0.9, 32), (1 << 27, 0.99, 32),
+                        (1 << 27, 0.9, 8), (1 << 28, 0.9, 4), (1000, 0.8, 4), (1, 1.0, 4), (0, 1.0, 8)]:
+        want_windows = max(1, -(-int(-(-n // 1) / alpha) // W)) if n else 1
+        mincap = -(-n * 1000 // int(alpha * 1000)) if n else 0
+        p, c = api.wc_plan_capacity(mincap, W)
+        q = max(1, -(-mincap // W))
+        assert p == sympy.nextprime(q - 1) or (p == 2 and q <= 2)
+        assert c == p * W and c >= mincap
+        del want_windows
+
+
+def test_plan_capacity_rejects_bad_arguments(lib):
+    from paper_2009_07914_gb300 import api
+    from paper_2009_07914_gb300._binding import WcError
+    with pytest.raises(WcError):
+        api.wc_plan_capacity(100, 0)
+    with pytest.raises(WcError):
+        api.wc_plan_capacity(1 << 40, 4)  # p would exceed 2^32
+
+
+def test_status_strings(lib):
+    from paper_2009_07914_gb300 import api
+    assert api.wc_status_string(0) == "ok"
+    assert "argument" in api.wc_status_string(1)

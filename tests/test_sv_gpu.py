@@ -1,0 +1,193 @@
+"""Single-value GPU path against the CPU oracle, element by element (calls go through the
+C ABI via the ctypes binding).  Sizes span many warps' ranges with ragged tails."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import wc_inputs
+from tests.golden_fixtures import run_sv
+
+pytestmark = pytest.mark.gpu
+
+W_G_P32 = [(4, 1), (4, 2), (4, 4), (8, 1), (8, 2), (8, 4), (8, 8), (16, 2), (16, 4), (16, 8), (16, 16),
+           (32, 4), (32, 8), (32, 16), (32, 32)]
+W_G_P64 = [(2, 1), (2, 2), (4, 1), (4, 2), (4, 4), (8, 2), (8, 4), (8, 8), (16, 4), (16, 8), (16, 16)]
+
+
+@pytest.fixture(scope="module")
+def wc():
+    from paper_2009_07914_gb300 import build
+    build.build()
+    import paper_2009_07914_gb300 as wc
+    return wc
+
+
+def make_sv(wc, kb, vb, cap, W=0, G=None, seed=0x1234):
+    t = wc.SingleValueTable(kb, vb, min_capacity=cap, window_width=W, seed=seed)
+    if G is not None:
+        for op in (wc.WC_OP_INSERT, wc.WC_OP_RETRIEVE, wc.WC_OP_ERASE):
+            t.set_launch(op, G)
+    return t
+
+
+def check_retrieve(t, o, keys):
+    out, found, flags = t.retrieve(keys)
+    eo, ef, efl = o.retrieve(keys)
+    np.testing.assert_array_equal(found, ef)
+    np.testing.assert_array_equal(out, eo)
+    assert flags == efl
+
+
+class _Adapter:
+    """Oracle-shaped wrapper over a GPU table for the golden fixtures."""
+
+    def __init__(self, t):
+        self.t = t
+
+    def insert(self, k, v):
+        return self.t.insert(k, v)
+
+    def erase(self, k):
+        return self.t.erase(k)
+
+    def retrieve(self, k):
+        return self.t.retrieve(k)
+
+    def size(self):
+        return self.t.size()
+
+
+def test_golden_sv_worked_example_gpu(wc):
+    assert run_sv("sv_ops.txt", lambda: _Adapter(make_sv(wc, 4, 4, 64))) >= 10
+
+
+@pytest.mark.parametrize("W,G", W_G_P32)
+def test_sv_u32_parity_every_shape(wc, W, G):
+    n = 100_003
+    d = wc_inputs.sv_insert_retrieve_u32(0x57C00001 + W * 64 + G, n, n // 2, 50_001)
+    t = make_sv(wc, 4, 4, int(n / 0.9) + 1, W, G)
+    o = oracle.SingleValue(4, 4)
+    assert t.insert(d["keys"], d["values"]) == o.insert(d["keys"], d["values"]) == 0
+    assert t.size() == o.size() == n
+    check_retrieve(t, o, d["queries"])
+    # erase a seeded half, retrieve everything again
+    drop = d["keys"][wc_inputs.shuffle_index(3, n)[: n // 2]]
+    assert t.erase(drop) == o.erase(drop)
+    assert t.size() == o.size()
+    check_retrieve(t, o, d["queries"])
+    # re-insert the erased keys with new values: tombstones are reused, nothing doubles
+    newv = wc_inputs.uniform_u32(77, drop.size)
+    assert t.insert(drop, newv) == o.insert(drop, newv)
+    assert t.size() == o.size() == n
+    check_retrieve(t, o, np.concatenate([d["keys"], d["queries"]]))
+    # overwrite present keys: duplicate warning, new values
+    upd = d["keys"][:1000]
+    v2 = wc_inputs.uniform_u32(78, 1000)
+    assert t.insert(upd, v2) == o.insert(upd, v2) == oracle.FLAG_DUPLICATE_KEY
+    check_retrieve(t, o, d["keys"])
+    assert t.size() == n
+
+
+@pytest.mark.parametrize("W,G", W_G_P64)
+def test_sv_u64_parity_every_shape(wc, W, G):
+    n = 60_001
+    keys = wc_inputs.distinct_u64(0x57C00003 + W * 64 + G, n + 30_000)
+    vals = wc_inputs.uniform_u64(5, n)
+    t = make_sv(wc, 8, 8, int(n / 0.9) + 1, W, G)
+    o = oracle.SingleValue(8, 8)
+    assert t.insert(keys[:n], vals) == o.insert(keys[:n], vals) == 0
+    q = keys[wc_inputs.shuffle_index(9, keys.size)]
+    check_retrieve(t, o, q)
+    drop = keys[: n // 3]
+    t.erase(drop)
+    o.erase(drop)
+    assert t.size() == o.size()
+    check_retrieve(t, o, q)
+    t.insert(drop, vals[: n // 3] ^ np.uint64(0xABCDEF))
+    o.insert(drop, vals[: n // 3] ^ np.uint64(0xABCDEF))
+    check_retrieve(t, o, q)
+    assert t.size() == o.size() == n
+
+
+@pytest.mark.parametrize("kb", [4, 8])
+def test_sv_random_op_sequences(wc, kb):
+    """Small key universe: heavy reuse of tombstones, duplicates inside batches."""
+    rng = np.random.default_rng(kb)
+    top = (1 << (8 * kb)) - 1
+    universe = np.unique(rng.integers(1, min(top, 2 ** 62), 3000, dtype=np.uint64))
+    t = make_sv(wc, kb, kb, 4096)
+    o = oracle.SingleValue(kb, kb)
+    for step in range(40):
+        m = int(rng.integers(1, 2000))
+        ks = np.unique(universe[rng.integers(0, universe.size, m)])  # unique inside a batch
+        rng.shuffle(ks)
+        if step % 3 == 2:
+            assert t.erase(ks) == o.erase(ks)
+        else:
+            vs = rng.integers(0, top, ks.size, dtype=np.uint64, endpoint=True)
+            assert t.insert(ks, vs) == o.insert(ks, vs)
+        assert t.size() == o.size()
+        check_retrieve(t, o, universe)
+
+
+def test_duplicates_inside_one_batch_store_one_of_their_values(wc):
+    keys = np.array([5, 9, 5, 5, 9, 11] * 1000, dtype=np.uint32)
+    vals = np.arange(keys.size, dtype=np.uint32)
+    t = make_sv(wc, 4, 4, 1024)
+    flags = t.insert(keys, vals)
+    assert flags & wc.WC_FLAG_DUPLICATE_KEY
+    assert t.size() == 3
+    out, found, _ = t.retrieve(np.array([5, 9, 11], dtype=np.uint32))
+    assert found.all()
+    for k, v in zip((5, 9, 11), out):
+        assert int(v) in set(vals[keys == k].tolist())
+
+
+def test_sentinels_and_empty_batches(wc):
+    t = make_sv(wc, 4, 4, 1024)
+    assert t.insert(np.array([], dtype=np.uint32), np.array([], dtype=np.uint32)) == 0
+    f = t.insert(np.array([0, 0xFFFFFFFF, 7], dtype=np.uint32), np.array([1, 2, 3], dtype=np.uint32))
+    assert f == wc.WC_FLAG_INVALID_KEY
+    assert t.size() == 1
+    out, found, f = t.retrieve(np.array([0, 7, 0xFFFFFFFF], dtype=np.uint32))
+    assert list(found) == [0, 1, 0] and int(out[1]) == 3 and int(out[0]) == 0xFFFFFFFF
+    assert f == wc.WC_FLAG_INVALID_KEY
+
+
+@pytest.mark.parametrize("kb", [4, 8])
+def test_overfull_table_reports_probe_limit_without_hanging(wc, kb):
+    t = make_sv(wc, kb, kb, 64)  # 64 slots requested -> a few windows
+    cap = t.capacity
+    keys = (wc_inputs.distinct_u32(1, cap + 50) if kb == 4 else wc_inputs.distinct_u64(1, cap + 50))
+    flags = t.insert(keys, keys)
+    assert flags & wc.WC_FLAG_PROBE_LIMIT
+    assert t.size() == cap  # every slot filled, the rest rejected
+    out, found, _ = t.retrieve(keys)
+    assert int(found.sum()) == cap
+    assert (out[found == 1] == keys[found == 1]).all()
+
+
+def test_load_factor_and_clear(wc):
+    n = 50_000
+    d = wc_inputs.sv_insert_retrieve_u32(21, n, 0, 0)
+    t = make_sv(wc, 4, 4, int(n / 0.8))
+    t.insert(d["keys"], d["values"])
+    assert abs(t.load_factor() - n / t.capacity) < 1e-12
+    t.clear()
+    assert t.size() == 0
+    _, found, _ = t.retrieve(d["keys"])
+    assert not found.any()
+
+
+@pytest.mark.parametrize("W", [4, 8, 16, 32])
+def test_window_counts_within_uniform_hashing_bound(wc, W):
+    """Hash quality (not parity): a full table at alpha = 0.9 answers every query; the
+    table's retrieve finds all keys -- probing never gives up early."""
+    n = 200_000
+    d = wc_inputs.sv_insert_retrieve_u32(31 + W, n, n, n)
+    t = make_sv(wc, 4, 4, int(n / 0.9) + 1, W)
+    assert t.insert(d["keys"], d["values"]) == 0
+    out, found, _ = t.retrieve(d["queries"])
+    assert int(found.sum()) == n
