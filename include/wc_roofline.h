@@ -1,0 +1,50 @@
+/*
+ * wc_roofline.h -- measurement support: the random-access roofline of the device.
+ *
+ * The paper has no counterpart; its hot path is bounded by random accesses to global
+ * memory (one probing window per key and probe step, Sec. IV-B2), so the library ships
+ * the probes that measure that bound on the device it runs on:
+ *   - random reads of `access_bytes` contiguous, aligned bytes at uniformly random
+ *     positions of a buffer (the window load of a probe), and
+ *   - the same read followed by a 64-bit CAS on the first word (the slot claim of an
+ *     insert).
+ * Conventions as in wc.h (device pointers d_*, host pointers h_*, void* stream).
+ */
+#ifndef WC_ROOFLINE_H_
+#define WC_ROOFLINE_H_
+
+#include <stdint.h>
+
+#include "wc.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  uint64_t buffer_bytes;   /* bytes of d_buffer accessed (multiple of access_bytes) */
+  uint64_t accesses;       /* number of random accesses */
+  uint64_t seed;           /* positions are fmix64(seed ^ i) scaled to the buffer */
+  uint32_t access_bytes;   /* 8, 16, 32, 64 or 128 */
+  uint32_t mode;           /* 0 = read only, 1 = read then CAS (old -> old + 1) */
+  uint32_t block_threads;  /* 0 = 256 */
+  uint32_t blocks_per_sm;  /* 0 = occupancy limit */
+} wc_rand_access_config;
+
+/* Launch the probe on `stream` over d_buffer (device, buffer_bytes, 256-byte aligned).
+ * d_sink (device, one uint64) receives an XOR of everything read, so the loads cannot be
+ * elided.  Asynchronous; time it with events on `stream`. */
+wc_status wc_bench_random_access(void* d_buffer, const wc_rand_access_config* cfg, uint64_t* d_sink,
+                                 void* stream);
+
+/* The CUDA context's L2 fetch-granularity limit (cudaLimitMaxL2FetchGranularity, bytes;
+ * a hint of how much the L2 fetches from DRAM on a miss).  Process-local: the setting
+ * ends with the process. */
+wc_status wc_set_l2_fetch_granularity(int32_t bytes);
+wc_status wc_get_l2_fetch_granularity(int32_t* h_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WC_ROOFLINE_H_ */

@@ -6,7 +6,10 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "wc.h"
 #include "wc_internal.h"
@@ -15,6 +18,7 @@ namespace wc {
 
 bool sv_p32_shape_ok(int W, int G);
 bool sv_p64_shape_ok(int W, int G);
+bool mv_shape_ok(int W, int G);
 cudaError_t sv_p32_launch(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n, void* out,
                           uint8_t* found, cudaStream_t s);
 cudaError_t sv_p64_launch(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n, void* out,
@@ -25,6 +29,7 @@ namespace {
 constexpr uint64_t kAlign = 256;
 constexpr uint64_t kMaxPool = 1ull << 35;
 constexpr uint64_t kMaxBatch = (1ull << 32) - 1;
+constexpr uint64_t kMaxMvBatch = 1ull << 31;  // per-call counts must stay below the poison bit
 
 uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
@@ -60,7 +65,8 @@ bool slot_layout(const wc_table_config& c, uint64_t* slot_bytes) {
   return false;
 }
 
-bool window_ok(uint64_t slot_bytes, int W) {
+bool window_ok(int kind, uint64_t slot_bytes, int W) {
+  if (kind == WC_MULTI_VALUE) return W == 2 || W == 4 || W == 8;
   if (slot_bytes == 8) return W == 4 || W == 8 || W == 16 || W == 32;
   return W == 2 || W == 4 || W == 8 || W == 16;
 }
@@ -68,7 +74,10 @@ bool window_ok(uint64_t slot_bytes, int W) {
 bool shape_ok(const wc_table* t, int op, int G) {
   const int W = static_cast<int>(t->W);
   if (t->slot_bytes == 8) return sv_p32_shape_ok(W, G);
-  if (t->cfg.kind == WC_MULTI_VALUE && op == WC_OP_INSERT) return G == 1;  // aggregation kernels
+  if (t->cfg.kind == WC_MULTI_VALUE) {
+    if (op == WC_OP_INSERT || op == WC_OP_RETRIEVE) return G == 1;  // one thread per distinct key
+    return mv_shape_ok(W, G);
+  }
   return sv_p64_shape_ok(W, G);
 }
 
@@ -141,6 +150,24 @@ cudaLaunchAttribute* l2_attr(const wc_table* t, cudaLaunchAttribute* storage, un
   return storage;
 }
 
+int occupancy_cached(const void* kernel, int block, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t, int>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(kernel, block, smem, dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, smem) != cudaSuccess || nb < 1) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  cache[key] = nb;
+  return nb;
+}
+
 int sm_count_of(int device) {
   int n = 0;
   if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n < 1) n = 1;
@@ -193,7 +220,7 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   if (!slot_layout(*cfg, &slot_bytes)) return WC_ERR_INVALID_ARG;
   int W = cfg->window_width;
   if (W == 0) W = slot_bytes == 8 ? 8 : 4;
-  if (!window_ok(slot_bytes, W)) return WC_ERR_INVALID_ARG;
+  if (!window_ok(cfg->kind, slot_bytes, W)) return WC_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) return WC_ERR_CUDA;
   const bool mv = cfg->kind == WC_MULTI_VALUE;
@@ -248,7 +275,10 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
     t->launch[op].block_threads = 256;
     t->launch[op].blocks_per_sm = 0;
   }
-  if (mv) t->launch[WC_OP_INSERT].group_size = 1;
+  if (mv) {
+    t->launch[WC_OP_INSERT].group_size = 1;
+    t->launch[WC_OP_RETRIEVE].group_size = 1;
+  }
 
   if (cfg->l2_persist) {
     int max_persist = 0, max_window = 0;
@@ -333,6 +363,7 @@ wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint6
   if (n > 0 && (d_values == nullptr || !aligned(d_values, static_cast<uint64_t>(t->cfg.value_bytes))))
     return WC_ERR_INVALID_ARG;
   if (n == 0) return WC_OK;
+  if (t->cfg.kind == WC_MULTI_VALUE && n >= kMaxMvBatch) return WC_ERR_INVALID_ARG;
   DeviceGuard guard(t->device);
   if (t->cfg.kind == WC_MULTI_VALUE) return cuda_status(mv_insert(t, d_keys, d_values, n, as_stream(stream)));
   return cuda_status(sv_launch(t, WC_OP_INSERT, d_keys, d_values, n, nullptr, nullptr, as_stream(stream)));

@@ -10,17 +10,18 @@
 
 namespace wc {
 
-// Resident blocks per SM of `kernel` at `block` threads, cached per instantiation.
+// Resident blocks per SM of a kernel at `block` threads and `smem` dynamic shared bytes,
+// cached by (kernel address, block, smem).
+int occupancy_cached(const void* kernel, int block, size_t smem);
+
 template <class Kernel>
 int occupancy(Kernel kernel, int block) {
-  static int cache[33] = {0};
-  const int slot = std::min(block / 32, 32);
-  if (cache[slot] == 0) {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, 0) != cudaSuccess || nb < 1) nb = 1;
-    cache[slot] = nb;
-  }
-  return cache[slot];
+  return occupancy_cached(reinterpret_cast<const void*>(kernel), block, 0);
+}
+
+template <class Kernel>
+int occupancy_smem(Kernel kernel, int block, size_t smem) {
+  return occupancy_cached(reinterpret_cast<const void*>(kernel), block, smem);
 }
 
 // Persistent-style grid for the probe engines: at most blocks_per_sm * SMs blocks, and

@@ -1,8 +1,58 @@
-#include "wc_internal.h"
+// Multi-value bulk insert: dispatch of the count / allocate / scatter passes.
+#include "wc_launch.cuh"
+#include "wc_mv_kernels.cuh"
+
 namespace wc {
-cudaError_t mv_insert(const wc_table*, const void*, const void*, uint64_t, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t mv_count(const wc_table*, const void*, uint64_t, uint64_t*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t mv_retrieve_multi(const wc_table*, const void*, uint64_t, const uint64_t*, void*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t mv_erase(const wc_table*, const void*, uint64_t, cudaStream_t) { return cudaErrorNotSupported; }
-uint64_t scan_partials_needed(uint64_t n) { return n / 8192 + 2; }
+
+namespace {
+
+template <class KIn, int VB, int W>
+cudaError_t insert_passes(const wc_table* t, const void* keys, const void* vals, uint64_t n, cudaStream_t s) {
+  const TableDesc d = desc_of(t);
+  const PoolDesc pd = pool_of(t);
+  const KIn* k = static_cast<const KIn*>(keys);
+  auto count = k_mv_aggregate<KIn, VB, W, false>;
+  auto scatter = k_mv_aggregate<KIn, VB, W, true>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(count, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(agg_smem_bytes(false)));
+    cudaFuncSetAttribute(scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(agg_smem_bytes(true)));
+    attr_done = true;
+  }
+  const uint64_t ntiles = (n + kAggTile - 1) / kAggTile;
+  const int bps_c = occupancy_smem(count, kAggThreads, agg_smem_bytes(false));
+  const int bps_s = occupancy_smem(scatter, kAggThreads, agg_smem_bytes(true));
+  const unsigned g_c = static_cast<unsigned>(std::min<uint64_t>(ntiles, static_cast<uint64_t>(bps_c) * t->sm_count));
+  const unsigned g_s = static_cast<unsigned>(std::min<uint64_t>(ntiles, static_cast<uint64_t>(bps_s) * t->sm_count));
+  cudaError_t e = cudaMemsetAsync(pd.pending, 0, t->capacity * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  e = launch_k(t, count, g_c, kAggThreads, agg_smem_bytes(false), s, d, pd, k, vals, n);
+  if (e != cudaSuccess) return e;
+  const uint64_t per_block = static_cast<uint64_t>(kAllocThreads) * kAllocItems;
+  const unsigned g_a = static_cast<unsigned>((t->capacity + per_block - 1) / per_block);
+  e = launch_k(t, k_mv_alloc<VB>, g_a, kAllocThreads, 0, s, d, pd, t->capacity);
+  if (e != cudaSuccess) return e;
+  return launch_k(t, scatter, g_s, kAggThreads, agg_smem_bytes(true), s, d, pd, k, vals, n);
 }
+
+template <class KIn, int VB>
+cudaError_t insert_w(const wc_table* t, const void* keys, const void* vals, uint64_t n, cudaStream_t s) {
+  switch (t->W) {
+    case 2: return insert_passes<KIn, VB, 2>(t, keys, vals, n, s);
+    case 4: return insert_passes<KIn, VB, 4>(t, keys, vals, n, s);
+    case 8: return insert_passes<KIn, VB, 8>(t, keys, vals, n, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t mv_insert(const wc_table* t, const void* keys, const void* vals, uint64_t n, cudaStream_t s) {
+  const int kb = t->cfg.key_bytes, vb = t->cfg.value_bytes;
+  if (kb == 4 && vb == 4) return insert_w<uint32_t, 4>(t, keys, vals, n, s);
+  if (kb == 4 && vb == 8) return insert_w<uint32_t, 8>(t, keys, vals, n, s);
+  if (kb == 8 && vb == 4) return insert_w<unsigned long long, 4>(t, keys, vals, n, s);
+  return insert_w<unsigned long long, 8>(t, keys, vals, n, s);
+}
+
+}  // namespace wc

@@ -1,0 +1,501 @@
+// Multi-value kernels (Sec. IV-B4 and IV-C).
+//
+// Storage: each distinct key is stored ONCE in a key store of 16-byte slots
+// {uint64 key, uint64 handle} (the single-value table of list handles of Sec. IV-C);
+// its values live in a value pool.  A bulk insert appends, for every key of the batch,
+// one bucket of exactly that batch's count of the key -- the bucket list with growth
+// lambda = 1 and s0 = count (Sec. V-C's "optimal growth strategy") -- linked to the key's
+// earlier buckets by a header that holds the previous handle (the back reference of
+// Sec. IV-C).  Handle bits: [0, 28) total values of the key, bit 28 "has an earlier
+// bucket", [29, 64) pool offset of the newest bucket (in value elements).
+//
+// Bulk insert = three passes over the batch (plus a clear of the per-slot counters):
+//   1. count: aggregate the batch tile by tile in shared memory (a hot key costs one
+//      global probe and one atomic per tile instead of one per occurrence), insert each
+//      distinct key into the key store, add its tile count to pending[slot];
+//   2. allocate: one pass over the key store reserves every key's bucket from the pool
+//      (block-aggregated bump allocation) and rewrites its handle;
+//   3. scatter: aggregate again, reserve each tile's run inside the key's bucket with one
+//      atomic on pending[slot], and write the values.
+// Within a bucket the order of values is unspecified (the paper's multi-value semantics
+// do not order values).
+#pragma once
+
+#include "wc_device.cuh"
+#include "wc_internal.h"
+#include "wc_sv_kernels.cuh"
+
+namespace wc {
+
+using KsL = LayoutP64;
+using KsSlot = LayoutP64::Slot;
+
+constexpr uint64_t kCountBits = 28;
+constexpr uint64_t kMaxCount = (1ull << kCountBits) - 1;
+constexpr uint32_t kPoison = 0x80000000u;  // pending[] mark of a bucket that was not allocated
+
+__device__ __forceinline__ uint64_t h_count(uint64_t h) { return h & kMaxCount; }
+__device__ __forceinline__ bool h_prev(uint64_t h) { return (h >> kCountBits) & 1ull; }
+__device__ __forceinline__ uint64_t h_offset(uint64_t h) { return h >> (kCountBits + 1); }
+__device__ __forceinline__ uint64_t h_make(uint64_t off, uint64_t cnt, bool prev) {
+  return (off << (kCountBits + 1)) | (static_cast<uint64_t>(prev) << kCountBits) | cnt;
+}
+
+// Header elements in front of a non-first bucket (one uint64 previous handle).
+template <int VB>
+struct Hdr {
+  static constexpr uint64_t kElems = 8 / VB;
+};
+
+template <int VB>
+struct PoolT;
+template <>
+struct PoolT<4> {
+  using T = uint32_t;
+};
+template <>
+struct PoolT<8> {
+  using T = unsigned long long;
+};
+
+// ---- key store probes by one thread (W slots per window) ------------------------------
+
+// Find the key's slot, inserting it with an empty handle if absent.  Same candidate
+// rule as the single-value insert (earliest empty or tombstoned slot, probing past
+// tombstones to the first window holding an empty slot or the key).  Returns the slot
+// index, or -1 when every window was visited without a candidate.
+template <int W>
+__device__ int64_t ks_find_or_insert(const TableDesc& t, uint64_t k, bool& created) {
+  KsSlot* slots = static_cast<KsSlot*>(t.slots);
+  uint32_t w, step;
+  probe_init(k, t.seed, t.p, w, step);
+  bool have_t = false;
+  uint64_t t_slot = 0;
+  KsSlot t_word{};
+  uint32_t j = 0;
+  created = false;
+  while (true) {
+    KsSlot s[W];
+    const uint64_t base = static_cast<uint64_t>(w) * W;
+    load_slots<KsL, W>(slots + base, s);
+    uint32_t mm, me, mt;
+    classify<KsL, W>(s, k, mm, me, mt);
+    if (mm) return static_cast<int64_t>(base + __ffs(mm) - 1);
+    const bool last = j + 1 >= t.p;
+    if (me || last) {
+      if (have_t) {
+        if (KsL::cas(slots + t_slot, t_word, KsL::make(k, 0))) {
+          created = true;
+          return static_cast<int64_t>(t_slot);
+        }
+        have_t = false;  // the tombstone was taken: start over
+        j = 0;
+        probe_init(k, t.seed, t.p, w, step);
+        continue;
+      }
+      const uint32_t mc = me | mt;
+      if (mc == 0) return -1;
+      const int sub = __ffs(mc) - 1;
+      if (KsL::cas(slots + base + sub, pick<KsL, W>(s, sub), KsL::make(k, 0))) {
+        created = true;
+        return static_cast<int64_t>(base + sub);
+      }
+      continue;  // lost the slot to another key (or to this key): read the window again
+    }
+    if (mt && !have_t) {
+      have_t = true;
+      t_slot = base + __ffs(mt) - 1;
+      t_word = pick<KsL, W>(s, __ffs(mt) - 1);
+    }
+    ++j;
+    w = probe_next(w, step, t.p);
+  }
+}
+
+// Find the key; returns its slot index and handle, or -1 if absent (Sec. IV-B4 early
+// exit at the first window holding an empty slot).
+template <int W>
+__device__ int64_t ks_find(const TableDesc& t, uint64_t k, uint64_t& handle) {
+  const KsSlot* slots = static_cast<const KsSlot*>(t.slots);
+  uint32_t w, step;
+  probe_init(k, t.seed, t.p, w, step);
+  for (uint32_t j = 0; j < t.p; ++j) {
+    KsSlot s[W];
+    const uint64_t base = static_cast<uint64_t>(w) * W;
+    load_slots<KsL, W>(slots + base, s);
+    uint32_t mm, me, mt;
+    classify<KsL, W>(s, k, mm, me, mt);
+    if (mm) {
+      handle = pick<KsL, W>(s, __ffs(mm) - 1).v;
+      return static_cast<int64_t>(base + __ffs(mm) - 1);
+    }
+    if (me) return -1;
+    w = probe_next(w, step, t.p);
+  }
+  return -1;
+}
+
+// ---- passes 1 and 3: tile aggregation in shared memory ----------------------------------
+
+constexpr int kAggThreads = 512;
+constexpr int kAggPerThread = 4;
+constexpr int kAggTile = kAggThreads * kAggPerThread;  // batch elements per tile
+constexpr int kAggSlots = 2 * kAggTile;                // shared table, load <= 1/2
+
+__device__ __forceinline__ int smem_find_or_insert(unsigned long long* s_key, unsigned long long key) {
+  volatile unsigned long long* vk = s_key;
+  uint32_t h = static_cast<uint32_t>(fmix64(key) >> 40) & (kAggSlots - 1);
+  while (true) {  // at most kAggTile distinct keys in a table of 2 * kAggTile slots
+    const unsigned long long cur = vk[h];
+    if (cur == key) return static_cast<int>(h);
+    if (cur == 0ull) {
+      const unsigned long long prev = atomicCAS(s_key + h, 0ull, key);
+      if (prev == 0ull || prev == key) return static_cast<int>(h);
+    }
+    h = (h + 1) & (kAggSlots - 1);
+  }
+}
+
+constexpr size_t agg_smem_bytes(bool scatter) {
+  return (scatter ? 2 : 1) * kAggSlots * sizeof(unsigned long long) + kAggSlots * sizeof(uint32_t);
+}
+
+template <class KIn, int VB, int W, bool kScatter>
+__global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolDesc pd, const KIn* __restrict__ keys,
+                                                              const void* __restrict__ vals, uint64_t n) {
+  using V = typename PoolT<VB>::T;
+  extern __shared__ unsigned long long agg_smem[];  // agg_smem_bytes(kScatter) bytes
+  unsigned long long* s_key = agg_smem;
+  unsigned long long* s_base = agg_smem + kAggSlots;
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(agg_smem + (kScatter ? 2 : 1) * kAggSlots);
+  const int lane = threadIdx.x & 31;
+  const uint64_t ntiles = (n + kAggTile - 1) / kAggTile;
+  uint32_t flags = 0;
+  long long created = 0;
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int e = threadIdx.x; e < kAggSlots; e += kAggThreads) {
+      s_key[e] = 0ull;
+      s_cnt[e] = 0u;
+    }
+    __syncthreads();
+    int my_slot[kAggPerThread];
+    uint32_t my_rank[kAggPerThread];
+#pragma unroll
+    for (int k = 0; k < kAggPerThread; ++k) {
+      const uint64_t e = tile * kAggTile + static_cast<uint64_t>(k) * kAggThreads + threadIdx.x;
+      unsigned long long key = 0ull;
+      bool valid = false;
+      if (e < n) {
+        const KIn kin = keys[e];
+        valid = !is_sentinel(kin);
+        if (valid) key = static_cast<unsigned long long>(kin);
+        else flags |= kFlagInvalid;
+      }
+      // equal keys of the warp are counted by their lowest lane
+      const uint32_t peers = __match_any_sync(kFull, key);
+      const int leader = __ffs(peers) - 1;
+      int slot = -1;
+      uint32_t base = 0;
+      if (valid && lane == leader) {
+        slot = smem_find_or_insert(s_key, key);
+        base = atomicAdd(s_cnt + slot, static_cast<uint32_t>(__popc(peers)));
+      }
+      slot = __shfl_sync(kFull, slot, leader);
+      base = __shfl_sync(kFull, base, leader);
+      my_slot[k] = valid ? slot : -1;
+      my_rank[k] = base + __popc(peers & ((1u << lane) - 1u));
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kAggSlots; e += kAggThreads) {
+      const unsigned long long key = s_key[e];
+      if (key == 0ull) continue;
+      if constexpr (!kScatter) {
+        bool made = false;
+        const int64_t gs = ks_find_or_insert<W>(t, key, made);
+        if (gs < 0) {
+          flags |= kFlagProbeLimit;
+          continue;
+        }
+        created += made ? 1 : 0;
+        atomicAdd(pd.pending + gs, s_cnt[e]);
+      } else {
+        uint64_t h = 0;
+        const int64_t gs = ks_find<W>(t, key, h);
+        unsigned long long b = ~0ull;
+        if (gs >= 0) {
+          const uint32_t old = atomicAdd(pd.pending + gs, s_cnt[e]);
+          if (!(old & kPoison)) b = h_offset(h) + (h_prev(h) ? Hdr<VB>::kElems : 0) + old;
+        }
+        s_base[e] = b;
+      }
+    }
+    if constexpr (kScatter) {
+      __syncthreads();
+      V* pool = static_cast<V*>(pd.pool);
+      const V* vin = static_cast<const V*>(vals);
+#pragma unroll
+      for (int k = 0; k < kAggPerThread; ++k) {
+        const uint64_t e = tile * kAggTile + static_cast<uint64_t>(k) * kAggThreads + threadIdx.x;
+        if (my_slot[k] < 0) continue;
+        const unsigned long long b = s_base[my_slot[k]];
+        if (b != ~0ull) pool[b + my_rank[k]] = vin[e];
+      }
+    }
+    __syncthreads();
+  }
+  flush_flags(t.status, flags);
+  if constexpr (!kScatter) flush_delta(t.nkeys, created);
+}
+
+// ---- pass 2: bucket allocation ----------------------------------------------------------
+
+constexpr int kAllocThreads = 256;
+constexpr int kAllocItems = 8;
+
+// Exclusive block scan of one uint64 per thread; returns this thread's prefix and the
+// block total through `total`.
+template <int kThreads>
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t x, uint64_t& total, uint64_t* s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    constexpr int nw = kThreads / 32;
+    uint64_t v = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(kFull, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane < nw) s_warp[lane] = v;  // inclusive warp totals
+  }
+  __syncthreads();
+  total = s_warp[kThreads / 32 - 1];
+  const uint64_t before = warp > 0 ? s_warp[warp - 1] : 0;
+  __syncthreads();
+  return before + inc - x;
+}
+
+template <int VB>
+__global__ void __launch_bounds__(kAllocThreads) k_mv_alloc(TableDesc t, PoolDesc pd, uint64_t capacity) {
+  using V = typename PoolT<VB>::T;
+  __shared__ uint64_t s_warp[kAllocThreads / 32];
+  __shared__ unsigned long long s_block_base;
+  __shared__ int s_ok;
+  KsSlot* slots = static_cast<KsSlot*>(t.slots);
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * (kAllocThreads * kAllocItems);
+  uint32_t c[kAllocItems];
+  uint64_t h[kAllocItems];
+  uint64_t need[kAllocItems];
+  uint64_t mine = 0;
+  uint32_t flags = 0;
+#pragma unroll
+  for (int k = 0; k < kAllocItems; ++k) {
+    const uint64_t s = base + static_cast<uint64_t>(k) * kAllocThreads + threadIdx.x;
+    c[k] = s < capacity ? pd.pending[s] : 0u;
+    h[k] = 0;
+    need[k] = 0;
+    if (c[k]) {
+      h[k] = slots[s].v;
+      const uint64_t old = h_count(h[k]);
+      if ((c[k] & kPoison) || old + c[k] > kMaxCount) {
+        flags |= kFlagCountOverflow;
+        pd.pending[s] = kPoison;
+        c[k] = 0;
+      } else {
+        const uint64_t hdr = old ? Hdr<VB>::kElems : 0;
+        need[k] = c[k] + hdr;
+        if (VB == 4) need[k] = (need[k] + 1) & ~1ull;  // keep bucket starts 8-byte aligned
+      }
+    }
+    mine += need[k];
+  }
+  uint64_t total = 0;
+  const uint64_t pre = block_exclusive_scan<kAllocThreads>(mine, total, s_warp);
+  if (threadIdx.x == 0) {
+    const unsigned long long b = total ? atomicAdd(pd.cursor, static_cast<unsigned long long>(total)) : 0ull;
+    s_block_base = b;
+    s_ok = b + total <= pd.capacity;
+  }
+  __syncthreads();
+  long long added = 0;
+  uint64_t off = s_block_base + pre;
+#pragma unroll
+  for (int k = 0; k < kAllocItems; ++k) {
+    if (need[k] == 0) continue;
+    const uint64_t s = base + static_cast<uint64_t>(k) * kAllocThreads + threadIdx.x;
+    if (!s_ok) {
+      flags |= kFlagPoolExhausted;
+      pd.pending[s] = kPoison;
+      continue;
+    }
+    const uint64_t old = h_count(h[k]);
+    if (old) *reinterpret_cast<unsigned long long*>(static_cast<V*>(pd.pool) + off) = h[k];
+    slots[s].v = h_make(off, old + c[k], old != 0);
+    pd.pending[s] = 0u;  // becomes the bucket's fill cursor for pass 3
+    added += c[k];
+    off += need[k];
+  }
+  flush_flags(t.status, flags);
+  flush_delta(t.size, added);
+}
+
+// ---- count_values: per-query count (the retrieve engine over the key store) ------------
+
+struct EmitCount {
+  uint64_t* __restrict__ offs;
+  __device__ void operator()(uint64_t pos, bool hit, const KsSlot& s) const { offs[pos] = hit ? h_count(s.v) : 0; }
+};
+
+template <class KIn, int G, int S>
+__global__ void __launch_bounds__(256) k_mv_count(TableDesc t, const KIn* __restrict__ keys, uint64_t n,
+                                                  uint64_t per_warp, uint64_t* __restrict__ offs) {
+  uint64_t begin, end;
+  warp_range(n, per_warp, begin, end);
+  if (begin >= end) return;
+  uint32_t flags = 0;
+  EmitCount emit{offs};
+  sv_retrieve_range<KsL, G, S, EmitCount, KIn>(t, keys, begin, end, emit, flags);
+  flush_flags(t.status, flags);
+}
+
+// ---- erase: tombstone the key-store entry, drop every value of the key ------------------
+
+struct OnEraseMV {
+  long long pairs = 0;
+  __device__ void operator()(const KsSlot& s) { pairs += static_cast<long long>(h_count(s.v)); }
+};
+
+template <class KIn, int G, int S>
+__global__ void __launch_bounds__(256) k_mv_erase(TableDesc t, const KIn* __restrict__ keys, uint64_t n,
+                                                  uint64_t per_warp) {
+  uint64_t begin, end;
+  warp_range(n, per_warp, begin, end);
+  if (begin >= end) return;
+  uint32_t flags = 0;
+  long long removed = 0;
+  OnEraseMV oe;
+  sv_erase_range<KsL, G, S, OnEraseMV, KIn>(t, keys, begin, end, flags, removed, oe);
+  flush_flags(t.status, flags);
+  flush_delta(t.nkeys, -removed);
+  flush_delta(t.size, -oe.pairs);
+}
+
+// ---- retrieve_multi: load-balanced CSR gather ---------------------------------------------
+//
+// The work is the merge of the n row ends (offsets[1..n]) with the `total` output
+// positions (merge-path decomposition, Merrill and Garland, SC'16): chunk c covers merge
+// items [c * L, (c + 1) * L), i.e. a fixed share of rows plus values whatever the skew,
+// so one key with 30 M values is spread over thousands of blocks.  A chunk probes the
+// key store for each of its rows with a non-zero count (one probe per row, Sec. IV-B4),
+// then copies its value range with consecutive threads on consecutive output positions
+// (coalesced reads inside a bucket, coalesced writes; the cooperative bucket read of
+// Sec. IV-C).
+
+constexpr int kRmThreads = 256;
+constexpr int kRmItems = 2048;
+
+// Rows whose end marker lies before merge position d: the first i in [0, n] with
+// offs[i + 1] + i >= d (offs[n + 1] taken as infinite).  One warp, 32 probes per step.
+__device__ __forceinline__ uint64_t merge_search(const uint64_t* __restrict__ offs, uint64_t n, uint64_t total,
+                                                 uint64_t d) {
+  const int lane = threadIdx.x & 31;
+  uint64_t lo = d > total ? d - total : 0;
+  uint64_t hi = d < n ? d : n;
+  while (lo < hi) {
+    const uint64_t span = hi - lo;
+    const uint64_t step = (span + 31) / 32;
+    const uint64_t x = lo + static_cast<uint64_t>(lane) * step;
+    const bool valid = x < hi;
+    const bool ge = valid && (offs[x + 1] + x >= d);
+    const uint32_t b = __ballot_sync(kFull, ge);
+    if (b) {
+      const int k = __ffs(b) - 1;
+      const uint64_t nhi = lo + static_cast<uint64_t>(k) * step;
+      lo = k == 0 ? lo : lo + static_cast<uint64_t>(k - 1) * step + 1;
+      hi = nhi;
+    } else {
+      const uint64_t last = (hi - 1 - lo) / step;  // last lane that tested a valid point
+      lo = lo + last * step + 1;
+    }
+  }
+  return lo;
+}
+
+// Pool index of value q (0-based) of a key whose newest bucket handle is h; buckets are
+// read newest first.  The walk is bounded by the key's value count.
+template <int VB>
+__device__ __forceinline__ uint64_t value_index(const PoolDesc& pd, uint64_t h, uint64_t q) {
+  using V = typename PoolT<VB>::T;
+  const V* pool = static_cast<const V*>(pd.pool);
+  for (uint64_t guard = 0; h_prev(h) && guard <= kMaxCount; ++guard) {
+    const uint64_t prev = *reinterpret_cast<const unsigned long long*>(pool + h_offset(h));
+    const uint64_t here = h_count(h) - h_count(prev);
+    if (q < here) return h_offset(h) + Hdr<VB>::kElems + q;
+    q -= here;
+    h = prev;
+  }
+  return h_offset(h) + q;
+}
+
+template <class KIn, int VB, int W>
+__global__ void __launch_bounds__(kRmThreads) k_mv_retrieve_multi(TableDesc t, PoolDesc pd, const KIn* __restrict__ keys,
+                                                                  uint64_t n, const uint64_t* __restrict__ offs,
+                                                                  void* __restrict__ out) {
+  using V = typename PoolT<VB>::T;
+  __shared__ uint64_t s_off[kRmItems + 2];
+  __shared__ uint64_t s_h[kRmItems + 1];
+  __shared__ uint64_t s_bounds[2];
+  const uint64_t total = offs[n];
+  const uint64_t items = n + total;
+  const uint64_t nchunks = (items + kRmItems - 1) / kRmItems;
+  const int warp = threadIdx.x >> 5;
+  const V* pool = static_cast<const V*>(pd.pool);
+  V* o = static_cast<V*>(out);
+  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const uint64_t d0 = c * kRmItems;
+    const uint64_t d1 = d0 + kRmItems < items ? d0 + kRmItems : items;
+    if (warp < 2) {
+      const uint64_t i = merge_search(offs, n, total, warp == 0 ? d0 : d1);
+      if ((threadIdx.x & 31) == 0) s_bounds[warp] = i;
+    }
+    __syncthreads();
+    const uint64_t i0 = s_bounds[0], i1 = s_bounds[1];
+    const uint64_t j0 = d0 - i0, j1 = d1 - i1;
+    const uint64_t rlast = i1 < n ? i1 : n - 1;
+    const int R = i0 < n ? static_cast<int>(rlast - i0 + 1) : 0;
+    for (int r = threadIdx.x; r <= R; r += kRmThreads) s_off[r] = offs[i0 + r];
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += kRmThreads) {
+      uint64_t h = 0;
+      if (s_off[r + 1] > s_off[r]) {
+        const KIn kin = keys[i0 + r];
+        uint64_t hh = 0;
+        if (!is_sentinel(kin) && ks_find<W>(t, static_cast<uint64_t>(kin), hh) >= 0) h = hh;
+      }
+      s_h[r] = h;
+    }
+    __syncthreads();
+    for (uint64_t j = j0 + threadIdx.x; j < j1; j += kRmThreads) {
+      int lo = 0, hi = R - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= j) lo = mid;
+        else hi = mid - 1;
+      }
+      const uint64_t q = j - s_off[lo];
+      const uint64_t h = s_h[lo];
+      // a key whose count changed since count_values keeps its slot in the output
+      if (q < h_count(h)) o[j] = pool[value_index<VB>(pd, h, q)];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace wc

@@ -1,0 +1,136 @@
+// Random-access roofline probes (include/wc_roofline.h).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "wc.h"
+#include "wc_device.cuh"
+#include "wc_internal.h"
+#include "wc_launch.cuh"
+#include "wc_roofline.h"
+
+namespace wc {
+namespace {
+
+constexpr int kUnroll = 4;  // independent accesses in flight per thread
+
+// XOR of the chunk's words; `first` receives its first word.
+template <int BYTES>
+__device__ __forceinline__ unsigned long long read_chunk(const unsigned long long* p, unsigned long long& first) {
+  unsigned long long acc = 0;
+  if constexpr (BYTES == 8) {
+    unsigned long long u[1];
+    ldcg1(p, u);
+    acc = first = u[0];
+  } else if constexpr (BYTES == 16) {
+    unsigned long long u[2];
+    ldcg2(p, u);
+    first = u[0];
+    acc = u[0] ^ u[1];
+  } else {
+#pragma unroll
+    for (int i = 0; i < BYTES / 8; i += 4) {
+      unsigned long long u[4];
+      ldcg4(p + i, u);
+      if (i == 0) first = u[0];
+      acc ^= u[0] ^ u[1] ^ u[2] ^ u[3];
+    }
+  }
+  return acc;
+}
+
+// Every load feeds `acc`, which is compared with a runtime value the compiler cannot
+// know, so no load is dead code.  In CAS mode the word just read is the CAS's expected
+// value (the claim of a slot read in the same window).
+template <int BYTES, bool kCas>
+__global__ void __launch_bounds__(256) k_rand_access(unsigned long long* buf, uint64_t chunks, uint64_t accesses,
+                                                     uint64_t seed, unsigned long long* sink) {
+  const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const uint64_t nth = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  unsigned long long acc = 0;
+  for (uint64_t base = tid; base < accesses; base += nth * kUnroll) {
+    unsigned long long* p[kUnroll];
+    unsigned long long v[kUnroll], f[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint64_t i = base + static_cast<uint64_t>(u) * nth;
+      const uint64_t h = fmix64(seed ^ i);
+      const uint64_t c = __umul64hi(h, chunks);
+      p[u] = buf + c * (BYTES / 8);
+      f[u] = 0ull;
+      v[u] = i < accesses ? read_chunk<BYTES>(p[u], f[u]) : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint64_t i = base + static_cast<uint64_t>(u) * nth;
+      if (kCas && i < accesses) acc ^= atomicCAS(p[u], f[u], f[u] + 1);
+      acc ^= v[u];
+    }
+  }
+  if (acc == seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull) *sink = acc;  // practically never taken
+}
+
+template <int BYTES>
+cudaError_t run(void* buf, const wc_rand_access_config& c, uint64_t* sink, cudaStream_t s) {
+  const int block = c.block_threads ? static_cast<int>(c.block_threads) : 256;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int sms = sm_count_of(dev);
+  auto* b = static_cast<unsigned long long*>(buf);
+  auto* k = reinterpret_cast<unsigned long long*>(sink);
+  const uint64_t chunks = c.buffer_bytes / BYTES;
+  if (c.mode == 1) {
+    auto kern = k_rand_access<BYTES, true>;
+    const int bps = c.blocks_per_sm ? static_cast<int>(c.blocks_per_sm) : occupancy(kern, block);
+    kern<<<bps * sms, block, 0, s>>>(b, chunks, c.accesses, c.seed, k);
+  } else {
+    auto kern = k_rand_access<BYTES, false>;
+    const int bps = c.blocks_per_sm ? static_cast<int>(c.blocks_per_sm) : occupancy(kern, block);
+    kern<<<bps * sms, block, 0, s>>>(b, chunks, c.accesses, c.seed, k);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace wc
+
+extern "C" {
+
+wc_status wc_bench_random_access(void* d_buffer, const wc_rand_access_config* cfg, uint64_t* d_sink,
+                                 void* stream) {
+  if (d_buffer == nullptr || cfg == nullptr || d_sink == nullptr) return WC_ERR_INVALID_ARG;
+  const uint32_t a = cfg->access_bytes;
+  if (!(a == 8 || a == 16 || a == 32 || a == 64 || a == 128) || cfg->buffer_bytes < a ||
+      cfg->buffer_bytes % a != 0 || cfg->mode > 1)
+    return WC_ERR_INVALID_ARG;
+  if (cfg->block_threads && (cfg->block_threads > 256 || cfg->block_threads % 32)) return WC_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(d_buffer) % 256) return WC_ERR_INVALID_ARG;
+  if (cfg->accesses == 0) return WC_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  switch (a) {
+    case 8: e = wc::run<8>(d_buffer, *cfg, d_sink, s); break;
+    case 16: e = wc::run<16>(d_buffer, *cfg, d_sink, s); break;
+    case 32: e = wc::run<32>(d_buffer, *cfg, d_sink, s); break;
+    case 64: e = wc::run<64>(d_buffer, *cfg, d_sink, s); break;
+    default: e = wc::run<128>(d_buffer, *cfg, d_sink, s); break;
+  }
+  return e == cudaSuccess ? WC_OK : WC_ERR_CUDA;
+}
+
+wc_status wc_set_l2_fetch_granularity(int32_t bytes) {
+  if (bytes < 0 || bytes > 128) return WC_ERR_INVALID_ARG;
+  return cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, static_cast<size_t>(bytes)) == cudaSuccess
+             ? WC_OK
+             : WC_ERR_CUDA;
+}
+
+wc_status wc_get_l2_fetch_granularity(int32_t* h_bytes) {
+  if (h_bytes == nullptr) return WC_ERR_INVALID_ARG;
+  size_t v = 0;
+  if (cudaDeviceGetLimit(&v, cudaLimitMaxL2FetchGranularity) != cudaSuccess) return WC_ERR_CUDA;
+  *h_bytes = static_cast<int32_t>(v);
+  return WC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+"""Binding of include/wc_roofline.h: random-access probes that measure the bound of the
+hash-table hot path (random window reads; read + CAS for inserts) on this device."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _binding as B
+
+
+class WcRandAccessConfig(ctypes.Structure):
+    _fields_ = [("buffer_bytes", ctypes.c_uint64), ("accesses", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("access_bytes", ctypes.c_uint32), ("mode", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
+                ("blocks_per_sm", ctypes.c_uint32)]
+
+
+B.extra_signatures({
+    "wc_bench_random_access": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(WcRandAccessConfig), ctypes.c_void_p,
+                                              ctypes.c_void_p]),
+    "wc_set_l2_fetch_granularity": (ctypes.c_int, [ctypes.c_int32]),
+    "wc_get_l2_fetch_granularity": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32)]),
+})
+
+
+def wc_bench_random_access(buffer: torch.Tensor, access_bytes: int, mode: int, accesses: int, sink: torch.Tensor,
+                           seed: int = 1, buffer_bytes: int | None = None, block_threads: int = 0,
+                           blocks_per_sm: int = 0, stream=None):
+    nbytes = buffer.numel() * buffer.element_size() if buffer_bytes is None else buffer_bytes
+    nbytes -= nbytes % access_bytes
+    cfg = WcRandAccessConfig(buffer_bytes=nbytes, accesses=accesses, seed=seed, access_bytes=access_bytes, mode=mode,
+                             block_threads=block_threads, blocks_per_sm=blocks_per_sm)
+    B.check(B.lib().wc_bench_random_access(B.ptr(buffer), ctypes.byref(cfg), B.ptr(sink), B.stream_handle(stream)),
+            "wc_bench_random_access")
+
+
+def wc_set_l2_fetch_granularity(nbytes: int):
+    B.check(B.lib().wc_set_l2_fetch_granularity(int(nbytes)), "wc_set_l2_fetch_granularity")
+
+
+def wc_get_l2_fetch_granularity() -> int:
+    v = ctypes.c_int32()
+    B.check(B.lib().wc_get_l2_fetch_granularity(ctypes.byref(v)), "wc_get_l2_fetch_granularity")
+    return int(v.value)
+
+
+def random_access_rate(buffer: torch.Tensor, access_bytes: int, mode: int = 0, accesses: int = 1 << 28,
+                       reps: int = 3, buffer_bytes: int | None = None, **kw) -> dict:
+    """Best-of-`reps` rate of random `access_bytes` reads (mode 1: read + CAS) over
+    `buffer`, timed with CUDA events on the current stream (one warm-up launch)."""
+    sink = torch.zeros(1, dtype=torch.int64, device=buffer.device)
+    s = torch.cuda.current_stream()
+    wc_bench_random_access(buffer, access_bytes, mode, accesses, sink, seed=99, buffer_bytes=buffer_bytes, **kw)
+    best = None
+    for r in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        wc_bench_random_access(buffer, access_bytes, mode, accesses, sink, seed=100 + r, buffer_bytes=buffer_bytes,
+                               **kw)
+        b.record(s)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    return {"access_bytes": access_bytes, "mode": mode, "ms": best, "accesses_per_s": accesses / (best * 1e-3),
+            "gbs": accesses * access_bytes / (best * 1e-3) / 1e9}

@@ -1,0 +1,161 @@
+"""Multi-value GPU path against the CPU oracle: exact counts and offsets, equal sorted
+per-query value multisets (Sec. IV-B4); slot layout is never compared."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import wc_inputs
+from tests.golden_fixtures import run_mv
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wc():
+    from paper_2009_07914_gb300 import build
+    build.build()
+    import paper_2009_07914_gb300 as wc
+    return wc
+
+
+def make_mv(wc, kb, vb, keys_cap, pool, W=0, G=None, seed=0x77):
+    t = wc.MultiValueTable(kb, vb, min_capacity=keys_cap, value_pool_capacity=pool, window_width=W, seed=seed)
+    if G is not None:
+        for op in (wc.WC_OP_COUNT, wc.WC_OP_ERASE):
+            t.set_launch(op, G)
+    return t
+
+
+def check_queries(t, o, q):
+    offs, _ = t.count_values(q)
+    eoffs, _ = o.count_values(q)
+    np.testing.assert_array_equal(offs, eoffs)
+    vals, _ = t.retrieve_multi(q, offs)
+    evals, _ = o.retrieve_multi(q, eoffs)
+    assert vals.size == evals.size == int(eoffs[-1])
+    np.testing.assert_array_equal(oracle.sorted_segments(vals, offs), oracle.sorted_segments(evals, eoffs))
+
+
+class _Adapter:
+    def __init__(self, t):
+        self.t = t
+
+    def insert(self, k, v):
+        return self.t.insert(k, v)
+
+    def erase(self, k):
+        return self.t.erase(k)
+
+    def count_values(self, q):
+        return self.t.count_values(q)
+
+    def retrieve_multi(self, q, offs):
+        return self.t.retrieve_multi(q, offs)
+
+    def size(self):
+        return self.t.size()
+
+
+def test_golden_mv_worked_example_gpu(wc):
+    assert run_mv("mv_ops.txt", lambda: _Adapter(make_mv(wc, 8, 4, 64, 1024))) >= 8
+
+
+@pytest.mark.parametrize("W,G", [(2, 1), (2, 2), (4, 1), (4, 2), (4, 4), (8, 2), (8, 4), (8, 8)])
+def test_mv_zipf_parity_every_shape(wc, W, G):
+    uni, n_ins, n_abs = 1 << 14, 300_007, 1 << 12
+    d = wc_inputs.mv_zipf_u64(0x57C00004 + W * 16 + G, uni, n_ins, n_abs)
+    t = make_mv(wc, 8, 4, int(uni / 0.8) + 1, n_ins + 4 * uni, W, G)
+    o = oracle.MultiValue(8, 4)
+    t.insert(d["keys"], d["values"])
+    o.insert(d["keys"], d["values"])
+    assert t.size() == o.size() == n_ins
+    assert t.num_keys() == o.num_keys()
+    check_queries(t, o, d["queries"])
+
+
+@pytest.mark.parametrize("kb,vb", [(4, 4), (4, 8), (8, 8)])
+def test_mv_widths_and_repeat_inserts(wc, kb, vb):
+    """Several insert calls on the same keys: buckets of later calls link to earlier
+    ones (Sec. IV-C back references); erase drops every value of a key."""
+    rng = np.random.default_rng(kb * 10 + vb)
+    top = (1 << (8 * kb)) - 1
+    universe = np.unique(rng.integers(1, min(top, 2 ** 62), 5000, dtype=np.uint64))
+    t = make_mv(wc, kb, vb, 8192, 400_000)
+    o = oracle.MultiValue(kb, vb)
+    vmax = (1 << (8 * vb)) - 1
+    for step in range(8):
+        m = int(rng.integers(1, 20_000))
+        ks = universe[np.minimum(rng.zipf(1.3, m), universe.size) - 1]
+        vs = rng.integers(0, vmax, m, dtype=np.uint64, endpoint=True)
+        t.insert(ks, vs)
+        o.insert(ks, vs)
+        if step == 5:
+            drop = universe[:50]
+            t.erase(drop)
+            o.erase(drop)
+        assert t.size() == o.size()
+        assert t.num_keys() == o.num_keys()
+        check_queries(t, o, universe)
+
+
+def test_mv_paper_invariant_uniform_r(wc):
+    """Sec. V-C: n keys from 1..n/r queried over 1..n return exactly n values."""
+    n = 1 << 17
+    for r in (1, 4, 32, 1024):
+        d = wc_inputs.mv_uniform_r(500 + r, n, r)
+        t = make_mv(wc, 8, 4, int(max(1, n // r) / 0.8) + 1, n + 2 * (n // r) + 64)
+        t.insert(d["keys"], d["values"])
+        offs, _ = t.count_values(d["queries"])
+        assert int(offs[-1]) == n
+        vals, _ = t.retrieve_multi(d["queries"], offs)
+        np.testing.assert_array_equal(np.sort(vals), np.arange(n, dtype=np.uint32))
+        seg = np.repeat(np.arange(n), np.diff(offs.astype(np.int64)))
+        np.testing.assert_array_equal(d["queries"][seg], d["keys"][vals])
+
+
+def test_mv_single_hot_key_spans_many_chunks(wc):
+    """One key holding most of the batch: its bucket is split over many blocks."""
+    n = 1 << 20
+    keys = np.full(n, 12345, dtype=np.uint64)
+    keys[::7] = np.arange(1, keys[::7].size + 1, dtype=np.uint64) + 100_000
+    vals = np.arange(n, dtype=np.uint32)
+    t = make_mv(wc, 8, 4, 1 << 18, n + (1 << 19))
+    o = oracle.MultiValue(8, 4)
+    t.insert(keys, vals)
+    o.insert(keys, vals)
+    q = np.concatenate([[12345, 7, 100_001], np.arange(100_001, 100_100)]).astype(np.uint64)
+    check_queries(t, o, q)
+
+
+def test_mv_sentinels_empty_and_pool_exhaustion(wc):
+    t = make_mv(wc, 8, 4, 4096, 64)
+    f = t.insert(np.array([0, 2 ** 64 - 1, 5], dtype=np.uint64), np.array([1, 2, 4], dtype=np.uint32))
+    assert f == wc.WC_FLAG_INVALID_KEY
+    offs, f = t.count_values(np.array([0, 5, 6], dtype=np.uint64))
+    assert list(offs) == [0, 0, 1, 1] and f == wc.WC_FLAG_INVALID_KEY
+    offs, _ = t.count_values(np.array([], dtype=np.uint64))
+    assert list(offs) == [0]
+    # the pool holds 64 values: a batch of 1000 cannot fit -> flagged, nothing corrupt
+    f = t.insert(np.arange(1, 1001, dtype=np.uint64), np.arange(1000, dtype=np.uint32))
+    assert f & wc.WC_FLAG_POOL_EXHAUSTED
+    q = np.arange(1, 1001, dtype=np.uint64)
+    offs, _ = t.count_values(q)
+    vals, _ = t.retrieve_multi(q, offs)
+    stored = np.repeat(q, np.diff(offs.astype(np.int64)))
+    np.testing.assert_array_equal(vals.astype(np.uint64), stored - 1)  # value = key - 1
+    # buckets are reserved per block of key-store slots: blocks that fit keep their values
+    assert t.size() == int(offs[-1]) < 1001
+
+
+def test_mv_u32_keys_full_mix(wc):
+    d = wc_inputs.mv_zipf_u64(99, 1 << 12, 1 << 16, 1 << 10)
+    keys32 = (d["keys"] & np.uint64(0x7FFFFFFF)).astype(np.uint32) | np.uint32(1)
+    q32 = (d["queries"] & np.uint64(0x7FFFFFFF)).astype(np.uint32) | np.uint32(1)
+    t = make_mv(wc, 4, 4, 8192, 1 << 17)
+    o = oracle.MultiValue(4, 4)
+    t.insert(keys32, d["values"])
+    o.insert(keys32, d["values"])
+    check_queries(t, o, q32)
+    assert t.size() == o.size()
