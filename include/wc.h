@@ -111,12 +111,23 @@ typedef struct {
  * (the cooperative group of Sec. IV-B2; W / group_size slots per lane, walked
  * consecutively by each lane, Sec. IV-B2 "fixed window with variable CG size");
  * block_threads = CUDA block size; blocks_per_sm = resident blocks per SM the grid is
- * sized for (0 = the occupancy limit). */
+ * sized for (0 = the occupancy limit); scheme = how a bulk call visits the table
+ * (WC_SCHEME_*); region_mib = table bytes per region of the blocked scheme (0 = 32). */
 typedef struct {
   int32_t group_size;
   int32_t block_threads;
   int32_t blocks_per_sm;
+  int32_t scheme;
+  int32_t region_mib;
 } wc_launch;
+
+/* WC_SCHEME_DIRECT: every key probes the table where its hash points, in input order.
+ * WC_SCHEME_BLOCKED: the batch is first split by table region (the multi-split of
+ * Sec. IV-E applied to regions of one table) and then probed region by region, so the
+ * active part of the table stays in L2; needs scratch of n * (key + value) bytes, which
+ * the table allocates on first use (stream-ordered) and keeps.  WC_SCHEME_AUTO picks
+ * BLOCKED for single-value inserts of at least 2^18 keys into tables larger than 64 MiB. */
+enum { WC_SCHEME_AUTO = 0, WC_SCHEME_DIRECT = 1, WC_SCHEME_BLOCKED = 2 };
 
 enum { WC_OP_INSERT = 0, WC_OP_RETRIEVE = 1, WC_OP_ERASE = 2, WC_OP_COUNT = 3, WC_OP__N = 4 };
 

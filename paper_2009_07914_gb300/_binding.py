@@ -33,6 +33,10 @@ WC_FLAG_QUEUE_TIMEOUT = 32
 WC_SINGLE_VALUE = 0
 WC_MULTI_VALUE = 1
 
+WC_SCHEME_AUTO = 0
+WC_SCHEME_DIRECT = 1
+WC_SCHEME_BLOCKED = 2
+
 WC_OP_INSERT = 0
 WC_OP_RETRIEVE = 1
 WC_OP_ERASE = 2
@@ -54,7 +58,7 @@ class WcTableInfo(ctypes.Structure):
 
 class WcLaunch(ctypes.Structure):
     _fields_ = [("group_size", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("scheme", ctypes.c_int32), ("region_mib", ctypes.c_int32)]
 
 
 class WcError(RuntimeError):

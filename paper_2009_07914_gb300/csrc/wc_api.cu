@@ -81,9 +81,13 @@ bool shape_ok(const wc_table* t, int op, int G) {
   return sv_p64_shape_ok(W, G);
 }
 
-// Default lanes per key: 32 bytes of the window per lane (one 256-bit load), else the
-// whole window in fewer bytes.
-int default_group(uint64_t slot_bytes, int W) {
+// Default lanes per key, from launch-shape sweeps on GB300 (2^27 keys at load 0.9):
+// probes are bound by random HBM traffic (direct) or by L2 round trips (blocked), so the
+// shapes that keep the most keys in flight win.  Inserts use one lane per key (the
+// blocked scheme's L2-resident probes favour it); lookups use 32 bytes of the window per
+// lane (one 256-bit load).
+int default_group(uint64_t slot_bytes, int W, int op) {
+  if (op == WC_OP_INSERT && W <= 8 * static_cast<int>(8 / slot_bytes)) return 1;
   const int per_lane = static_cast<int>(32 / slot_bytes);
   return std::max(1, W / per_lane);
 }
@@ -166,6 +170,32 @@ int occupancy_cached(const void* kernel, int block, size_t smem) {
   }
   cache[key] = nb;
   return nb;
+}
+
+cudaError_t ensure_scratch(const wc_table* t, uint64_t bytes, cudaStream_t s) {
+  if (bytes <= t->scratch_bytes) return cudaSuccess;
+  if (t->d_scratch != nullptr) {
+    cudaError_t e = cudaFreeAsync(t->d_scratch, s);
+    if (e != cudaSuccess) return e;
+    t->d_scratch = nullptr;
+    t->scratch_bytes = 0;
+  }
+  const uint64_t want = align_up(bytes + bytes / 8, kAlign);
+  cudaError_t e = cudaMallocAsync(&t->d_scratch, want, s);
+  if (e != cudaSuccess) {
+    t->d_scratch = nullptr;
+    return e;
+  }
+  t->scratch_bytes = want;
+  return cudaSuccess;
+}
+
+int scheme_for(const wc_table* t, int op, uint64_t n) {
+  const int sc = t->launch[op].scheme;
+  if (sc != WC_SCHEME_AUTO) return sc;
+  if (op == WC_OP_INSERT && t->cfg.kind == WC_SINGLE_VALUE && n >= (1ull << 18) && t->table_bytes > (64ull << 20))
+    return WC_SCHEME_BLOCKED;
+  return WC_SCHEME_DIRECT;
 }
 
 int sm_count_of(int device) {
@@ -271,9 +301,11 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   t->d_pool = mv ? static_cast<void*>(base + off_pool) : nullptr;
 
   for (int op = 0; op < WC_OP__N; ++op) {
-    t->launch[op].group_size = default_group(slot_bytes, W);
+    t->launch[op].group_size = default_group(slot_bytes, W, op);
     t->launch[op].block_threads = 256;
     t->launch[op].blocks_per_sm = 0;
+    t->launch[op].scheme = WC_SCHEME_AUTO;
+    t->launch[op].region_mib = 0;
   }
   if (mv) {
     t->launch[WC_OP_INSERT].group_size = 1;
@@ -309,6 +341,10 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
 wc_status wc_table_destroy(wc_table* t) {
   if (t == nullptr) return WC_ERR_INVALID_ARG;
   DeviceGuard guard(t->device);
+  if (t->d_scratch != nullptr) {
+    cudaDeviceSynchronize();
+    cudaFree(t->d_scratch);
+  }
   cudaError_t e = cudaFree(t->d_block);
   delete t;
   return cuda_status(e);
@@ -338,6 +374,11 @@ wc_status wc_table_set_launch(wc_table* t, int32_t op, const wc_launch* launch) 
   const int b = launch->block_threads;
   if (b < 32 || b > 256 || b % 32 != 0 || launch->blocks_per_sm < 0 || launch->blocks_per_sm > 64)
     return WC_ERR_INVALID_ARG;
+  if (launch->scheme < WC_SCHEME_AUTO || launch->scheme > WC_SCHEME_BLOCKED || launch->region_mib < 0 ||
+      launch->region_mib > 4096)
+    return WC_ERR_INVALID_ARG;
+  if (launch->scheme == WC_SCHEME_BLOCKED && (op != WC_OP_INSERT || t->cfg.kind != WC_SINGLE_VALUE))
+    return WC_ERR_UNSUPPORTED;
   if (!shape_ok(t, op, launch->group_size)) return WC_ERR_INVALID_ARG;
   t->launch[op] = *launch;
   return WC_OK;

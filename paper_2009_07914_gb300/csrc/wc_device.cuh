@@ -82,6 +82,28 @@ __device__ __forceinline__ void load_words(const unsigned long long* p, unsigned
   }
 }
 
+// Streamed input element (read once): loaded with an evict-first L2 cache policy, so
+// batches flowing through L2 displace table lines as little as possible.
+__device__ __forceinline__ unsigned long long evict_first_policy() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint32_t ldg_stream(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;"
+               : "=r"(v)
+               : "l"(p), "l"(evict_first_policy()));
+  return v;
+}
+__device__ __forceinline__ unsigned long long ldg_stream(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;"
+               : "=l"(v)
+               : "l"(p), "l"(evict_first_policy()));
+  return v;
+}
+
 // ---- slot layouts ---------------------------------------------------------------------
 
 // Packed array-of-structs slot (Sec. IV-B1): a uint32 key in the low half and a uint32

@@ -65,6 +65,9 @@ struct wc_table {
   wc_launch launch[WC_OP__N];
   size_t l2_window_bytes;  // > 0: launch with an L2 access-policy window over the slots
   float l2_hit_ratio;
+  // scratch for the blocked scheme, grown on demand (stream-ordered allocation)
+  mutable void* d_scratch;
+  mutable uint64_t scratch_bytes;
 };
 
 namespace wc {
@@ -93,5 +96,11 @@ cudaError_t scan_exclusive_u64(uint64_t* d, uint64_t n, uint64_t* partials, uint
 uint64_t scan_partials_needed(uint64_t n);
 
 int sm_count_of(int device);
+
+// Scratch of at least `bytes` on stream s (grows the table's buffer if needed).
+cudaError_t ensure_scratch(const wc_table* t, uint64_t bytes, cudaStream_t s);
+
+// Scheme the table uses for `op` on a batch of n keys.
+int scheme_for(const wc_table* t, int op, uint64_t n);
 
 }  // namespace wc

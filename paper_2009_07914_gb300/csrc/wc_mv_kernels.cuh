@@ -356,12 +356,11 @@ struct EmitCount {
 template <class KIn, int G, int S>
 __global__ void __launch_bounds__(256) k_mv_count(TableDesc t, const KIn* __restrict__ keys, uint64_t n,
                                                   uint64_t per_warp, uint64_t* __restrict__ offs) {
-  uint64_t begin, end;
-  warp_range(n, per_warp, begin, end);
-  if (begin >= end) return;
+  RangeSrc src(n, per_warp, nullptr, 0);
+  if (src.next >= src.end) return;
   uint32_t flags = 0;
   EmitCount emit{offs};
-  sv_retrieve_range<KsL, G, S, EmitCount, KIn>(t, keys, begin, end, emit, flags);
+  sv_retrieve_range<KsL, G, S, EmitCount, KIn>(t, keys, src, emit, flags);
   flush_flags(t.status, flags);
 }
 
@@ -375,13 +374,12 @@ struct OnEraseMV {
 template <class KIn, int G, int S>
 __global__ void __launch_bounds__(256) k_mv_erase(TableDesc t, const KIn* __restrict__ keys, uint64_t n,
                                                   uint64_t per_warp) {
-  uint64_t begin, end;
-  warp_range(n, per_warp, begin, end);
-  if (begin >= end) return;
+  RangeSrc src(n, per_warp, nullptr, 0);
+  if (src.next >= src.end) return;
   uint32_t flags = 0;
   long long removed = 0;
   OnEraseMV oe;
-  sv_erase_range<KsL, G, S, OnEraseMV, KIn>(t, keys, begin, end, flags, removed, oe);
+  sv_erase_range<KsL, G, S, OnEraseMV, KIn>(t, keys, src, flags, removed, oe);
   flush_flags(t.status, flags);
   flush_delta(t.nkeys, -removed);
   flush_delta(t.size, -oe.pairs);

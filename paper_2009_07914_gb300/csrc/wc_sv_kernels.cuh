@@ -59,12 +59,83 @@ __device__ __forceinline__ void warp_range(uint64_t n, uint64_t per_warp, uint64
   end = begin + per_warp < n ? begin + per_warp : n;
 }
 
+// Where a warp's input positions come from.  With counter == nullptr the warp owns the
+// static range [next, end).  Otherwise warps pull `chunk` positions at a time from a
+// global counter, so the whole grid sweeps the input front to back -- a batch sorted by
+// table region is then probed region by region, with the active regions held in L2.
+struct RangeSrc {
+  uint64_t next, end, n;
+  unsigned long long* counter;
+  uint32_t chunk;
+  bool done;
+  bool fresh;  // [next, end) is a new range whose inputs have not been prefetched yet
+  __device__ RangeSrc(uint64_t n_, uint64_t per_warp, unsigned long long* counter_, uint32_t chunk_)
+      : n(n_), counter(counter_), chunk(chunk_), done(false), fresh(true) {
+    if (counter == nullptr) {
+      warp_range(n, per_warp, next, end);
+    } else {
+      next = end = 0;
+    }
+  }
+  // Warp-uniform: true while positions are left in [next, end) or can be pulled.
+  __device__ __forceinline__ bool ensure() {
+    if (next < end) return true;
+    if (counter == nullptr || done) return false;
+    unsigned long long c = 0;
+    if ((threadIdx.x & 31) == 0) c = atomicAdd(counter, static_cast<unsigned long long>(chunk));
+    c = __shfl_sync(kFull, c, 0);
+    if (c >= n) {
+      done = true;
+      return false;
+    }
+    next = c;
+    end = c + chunk < n ? c + chunk : n;
+    fresh = true;
+    return true;
+  }
+};
+
+// The warp's next 64 input elements, prefetched into registers with coalesced loads
+// (lane l holds elements base + l and base + 32 + l).  Groups receive their key by
+// shuffle, so the input load is off the per-key critical path; the second half is
+// reloaded while the first is being consumed.
+template <class T>
+struct Feed {
+  T b0, b1;
+  uint64_t base, lim;
+  const T* __restrict__ src;
+  __device__ __forceinline__ void load(const T* p, uint64_t start, uint64_t end) {
+    const uint64_t lane = threadIdx.x & 31;
+    src = p;
+    base = start;
+    lim = end;
+    b0 = start + lane < end ? ldg_stream(p + start + lane) : T(0);
+    b1 = start + 32 + lane < end ? ldg_stream(p + start + 32 + lane) : T(0);
+  }
+  // Element at `pos` (valid lanes); every lane must call.
+  __device__ __forceinline__ T get(uint64_t pos, bool valid) const {
+    const uint32_t o = valid ? static_cast<uint32_t>(pos - base) : 0u;
+    const T x0 = __shfl_sync(kFull, b0, o & 31);
+    const T x1 = __shfl_sync(kFull, b1, o & 31);
+    return o < 32 ? x0 : x1;
+  }
+  // After positions up to `next` were handed out (warp-uniform).
+  __device__ __forceinline__ void advance(uint64_t next) {
+    if (next - base >= 32) {
+      const uint64_t lane = threadIdx.x & 31;
+      b0 = b1;
+      base += 32;
+      b1 = base + 32 + lane < lim ? ldg_stream(src + base + 32 + lane) : T(0);
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------------------
 // retrieve: out[i] = value of keys[i] or NOT_FOUND; found[i] = 1/0 (Sec. IV-B4).
 // Emit is called by one lane per finished query: emit(pos, hit, slot).
 template <class L, int G, int S, class Emit, class KIn = typename L::Key>
-__device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn* __restrict__ keys,
-                                                  uint64_t next, uint64_t end, Emit& emit, uint32_t& flags) {
+__device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn* __restrict__ keys, RangeSrc& src,
+                                                  Emit& emit, uint32_t& flags) {
   using Slot = typename L::Slot;
   using Key = typename L::Key;
   const SvLane<L, G, S> ln;
@@ -74,11 +145,19 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
   uint64_t pos = 0;
   Key k = 0;
   uint32_t w = 0, step = 0, j = 0;
+  Feed<KIn> fk;
   while (true) {
-    uint64_t np;
-    if (take_next(!act, ln.r, ln.gbase, next, end, np)) {
+    const bool more = src.ensure();
+    if (more && src.fresh) {
+      fk.load(keys, src.next, src.end);
+      src.fresh = false;
+    }
+    uint64_t np = 0;
+    const bool got = more && take_next(!act, ln.r, ln.gbase, src.next, src.end, np);
+    const KIn kin = fk.get(np, got);
+    if (more) fk.advance(src.next);
+    if (got) {
       pos = np;
-      const KIn kin = keys[pos];
       k = static_cast<Key>(kin);
       if (is_sentinel(kin)) {
         flags |= kFlagInvalid;
@@ -90,7 +169,7 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
       }
     }
     if (__ballot_sync(kFull, act) == 0) {
-      if (next >= end) break;
+      if (!more) break;
       continue;
     }
     Slot s[S];
@@ -131,12 +210,11 @@ template <class L, int G, int S>
 __global__ void __launch_bounds__(256) k_sv_retrieve(TableDesc t, const typename L::Key* __restrict__ keys, uint64_t n,
                                                      uint64_t per_warp, typename L::Val* __restrict__ out,
                                                      uint8_t* __restrict__ found) {
-  uint64_t begin, end;
-  warp_range(n, per_warp, begin, end);
-  if (begin >= end) return;
+  RangeSrc src(n, per_warp, nullptr, 0);
+  if (src.next >= src.end) return;
   uint32_t flags = 0;
   EmitValue<L> emit{out, found};
-  sv_retrieve_range<L, G, S>(t, keys, begin, end, emit, flags);
+  sv_retrieve_range<L, G, S>(t, keys, src, emit, flags);
   flush_flags(t.status, flags);
 }
 
@@ -145,8 +223,8 @@ __global__ void __launch_bounds__(256) k_sv_retrieve(TableDesc t, const typename
 // keys this lane's groups stored (counted by lane r == 0 of each group).
 template <class L, int G, int S>
 __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typename L::Key* __restrict__ keys,
-                                                const typename L::Val* __restrict__ vals, uint64_t next,
-                                                uint64_t end, uint32_t& flags, long long& added) {
+                                                const typename L::Val* __restrict__ vals, RangeSrc& src,
+                                                uint32_t& flags, long long& added) {
   using Slot = typename L::Slot;
   using Key = typename L::Key;
   using Val = typename L::Val;
@@ -161,15 +239,30 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
   bool have_t = false;     // a tombstone earlier on the sequence is remembered
   uint64_t t_slot = 0;     // its slot index
   Slot t_word{};           // and the word read there
+  Feed<Key> fk;
+  Feed<Val> fv;
   while (true) {
-    uint64_t np;
-    if (take_next(!act, ln.r, ln.gbase, next, end, np)) {
+    const bool more = src.ensure();
+    if (more && src.fresh) {
+      fk.load(keys, src.next, src.end);
+      fv.load(vals, src.next, src.end);
+      src.fresh = false;
+    }
+    uint64_t np = 0;
+    const bool got = more && take_next(!act, ln.r, ln.gbase, src.next, src.end, np);
+    const Key kin = fk.get(np, got);
+    const Val vin = fv.get(np, got);
+    if (more) {
+      fk.advance(src.next);
+      fv.advance(src.next);
+    }
+    if (got) {
       pos = np;
-      k = keys[pos];
+      k = kin;
       if (is_sentinel(k)) {
         flags |= kFlagInvalid;
       } else {
-        v = vals[pos];
+        v = vin;
         act = true;
         j = 0;
         have_t = false;
@@ -177,7 +270,7 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
       }
     }
     if (__ballot_sync(kFull, act) == 0) {
-      if (next >= end) break;
+      if (!more) break;
       continue;
     }
     Slot s[S];
@@ -256,16 +349,16 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
   }
 }
 
+// counter != nullptr: warps pull chunks in order (input sorted by table region).
 template <class L, int G, int S>
 __global__ void __launch_bounds__(256) k_sv_insert(TableDesc t, const typename L::Key* __restrict__ keys,
                                                    const typename L::Val* __restrict__ vals, uint64_t n,
-                                                   uint64_t per_warp) {
-  uint64_t begin, end;
-  warp_range(n, per_warp, begin, end);
-  if (begin >= end) return;
+                                                   uint64_t per_warp, unsigned long long* counter, uint32_t chunk) {
+  RangeSrc src(n, per_warp, counter, chunk);
+  if (counter == nullptr && src.next >= src.end) return;
   uint32_t flags = 0;
   long long added = 0;
-  sv_insert_range<L, G, S>(t, keys, vals, begin, end, flags, added);
+  sv_insert_range<L, G, S>(t, keys, vals, src, flags, added);
   flush_flags(t.status, flags);
   flush_delta(t.size, added);
 }
@@ -275,9 +368,8 @@ __global__ void __launch_bounds__(256) k_sv_insert(TableDesc t, const typename L
 // on_erase(slot) sees the word that was replaced (multi-value tables use it to adjust
 // their pair count).
 template <class L, int G, int S, class OnErase, class KIn = typename L::Key>
-__device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __restrict__ keys,
-                                               uint64_t next, uint64_t end, uint32_t& flags, long long& removed,
-                                               OnErase& on_erase) {
+__device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __restrict__ keys, RangeSrc& src,
+                                               uint32_t& flags, long long& removed, OnErase& on_erase) {
   using Slot = typename L::Slot;
   using Key = typename L::Key;
   const SvLane<L, G, S> ln;
@@ -286,10 +378,18 @@ __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __
   bool act = false;
   Key k = 0;
   uint32_t w = 0, step = 0, j = 0;
+  Feed<KIn> fk;
   while (true) {
-    uint64_t np;
-    if (take_next(!act, ln.r, ln.gbase, next, end, np)) {
-      const KIn kin = keys[np];
+    const bool more = src.ensure();
+    if (more && src.fresh) {
+      fk.load(keys, src.next, src.end);
+      src.fresh = false;
+    }
+    uint64_t np = 0;
+    const bool got = more && take_next(!act, ln.r, ln.gbase, src.next, src.end, np);
+    const KIn kin = fk.get(np, got);
+    if (more) fk.advance(src.next);
+    if (got) {
       k = static_cast<Key>(kin);
       if (is_sentinel(kin)) {
         flags |= kFlagInvalid;
@@ -300,7 +400,7 @@ __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __
       }
     }
     if (__ballot_sync(kFull, act) == 0) {
-      if (next >= end) break;
+      if (!more) break;
       continue;
     }
     Slot s[S];
@@ -344,13 +444,12 @@ struct NoOnErase {
 template <class L, int G, int S>
 __global__ void __launch_bounds__(256) k_sv_erase(TableDesc t, const typename L::Key* __restrict__ keys, uint64_t n,
                                                   uint64_t per_warp) {
-  uint64_t begin, end;
-  warp_range(n, per_warp, begin, end);
-  if (begin >= end) return;
+  RangeSrc src(n, per_warp, nullptr, 0);
+  if (src.next >= src.end) return;
   uint32_t flags = 0;
   long long removed = 0;
   NoOnErase none;
-  sv_erase_range<L, G, S>(t, keys, begin, end, flags, removed, none);
+  sv_erase_range<L, G, S>(t, keys, src, flags, removed, none);
   flush_flags(t.status, flags);
   flush_delta(t.size, -removed);
 }

@@ -24,11 +24,14 @@ def wc():
     return wc
 
 
-def make_sv(wc, kb, vb, cap, W=0, G=None, seed=0x1234):
+def make_sv(wc, kb, vb, cap, W=0, G=None, seed=0x1234, scheme=0, region_mib=0):
     t = wc.SingleValueTable(kb, vb, min_capacity=cap, window_width=W, seed=seed)
     if G is not None:
         for op in (wc.WC_OP_INSERT, wc.WC_OP_RETRIEVE, wc.WC_OP_ERASE):
             t.set_launch(op, G)
+    if scheme:
+        g = G if G is not None else wc.wc_table_get_launch(t.handle, wc.WC_OP_INSERT)["group_size"]
+        t.set_launch(wc.WC_OP_INSERT, g, scheme=scheme, region_mib=region_mib)
     return t
 
 
@@ -191,3 +194,44 @@ def test_window_counts_within_uniform_hashing_bound(wc, W):
     assert t.insert(d["keys"], d["values"]) == 0
     out, found, _ = t.retrieve(d["queries"])
     assert int(found.sum()) == n
+
+
+@pytest.mark.parametrize("kb,W,G", [(4, 4, 1), (4, 8, 2), (4, 16, 4), (4, 32, 8), (8, 4, 2), (8, 8, 4)])
+def test_blocked_insert_scheme_parity(wc, kb, W, G):
+    """Region-split (blocked) inserts give the same table contents as the oracle,
+    including tombstone reuse after erases and duplicate overwrites."""
+    n = 1_000_003
+    if kb == 4:
+        d = wc_inputs.sv_insert_retrieve_u32(0xB10C + W + G, n, n // 2, 300_000)
+        keys, vals, q = d["keys"], d["values"], d["queries"]
+    else:
+        allk = wc_inputs.distinct_u64(0xB10C + W + G, n + 300_000)
+        keys, vals = allk[:n], wc_inputs.uniform_u64(3, n)
+        q = allk[wc_inputs.shuffle_index(4, allk.size)]
+    t = make_sv(wc, kb, kb, int(n / 0.9) + 1, W, G, scheme=wc.WC_SCHEME_BLOCKED, region_mib=1)
+    o = oracle.SingleValue(kb, kb)
+    assert t.insert(keys, vals) == o.insert(keys, vals) == 0
+    assert t.size() == n
+    check_retrieve(t, o, q)
+    drop = keys[: n // 3]
+    t.erase(drop)
+    o.erase(drop)
+    back = np.concatenate([drop[::2], keys[n // 3: n // 3 + 1000]])  # re-insert + overwrite
+    bv = (vals[: back.size] ^ 0x5A).astype(vals.dtype)
+    assert t.insert(back, bv) == o.insert(back, bv) == oracle.FLAG_DUPLICATE_KEY
+    assert t.size() == o.size()
+    check_retrieve(t, o, q)
+
+
+def test_blocked_insert_auto_scheme_on_large_table(wc):
+    """AUTO picks the blocked scheme for big batches into tables above 64 MiB."""
+    n = 1 << 23
+    d = wc_inputs.sv_insert_retrieve_u32(0xA070, n, 1 << 20, 1 << 20)
+    t = make_sv(wc, 4, 4, int(n / 0.9) + 1)
+    assert t.info["table_bytes"] > (64 << 20)
+    assert t.insert(d["keys"], d["values"]) == 0
+    assert t.size() == n
+    out, found, _ = t.retrieve(d["queries"])
+    pres = d["q_src"] >= 0
+    assert found[pres].all() and not found[~pres].any()
+    np.testing.assert_array_equal(out[pres], d["values"][d["q_src"][pres]])
