@@ -1,0 +1,162 @@
+// Request-serving loop (include/wc_serve.h): admission by HBM budget, continuous batching
+// into the batched executor, or per-call launches as the baseline.  Host code only.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdint>
+#include <deque>
+#include <thread>
+#include <vector>
+
+#include "wc.h"
+#include "wc_exec.h"
+#include "wc_internal.h"
+#include "wc_serve.h"
+
+namespace {
+
+struct Launch {
+  uint64_t ticket = 0;       // batched mode
+  cudaEvent_t ev = nullptr;  // per-call mode
+  std::vector<uint32_t> reqs;
+};
+
+wc_status launch_one(const wc_work& w, void* stream) {
+  switch (w.op) {
+    case WC_OP_INSERT: return wc_insert(w.table, w.d_keys, w.d_values, w.n, stream);
+    case WC_OP_RETRIEVE: return wc_retrieve(w.table, w.d_keys, w.n, w.d_values_out, w.d_found_out, stream);
+    case WC_OP_ERASE: return wc_erase(w.table, w.d_keys, w.n, stream);
+    default: return WC_ERR_INVALID_ARG;
+  }
+}
+
+}  // namespace
+
+extern "C" wc_status wc_serve_run(wc_executor* ex, const wc_request* reqs, uint32_t nreq, const wc_serve_config* cfg,
+                                  void* stream, wc_request_timing* timing, wc_serve_stats* stats) {
+  if (cfg == nullptr || timing == nullptr || stats == nullptr || (nreq > 0 && reqs == nullptr))
+    return WC_ERR_INVALID_ARG;
+  const bool batched = cfg->mode == WC_SERVE_BATCHED;
+  if (!batched && cfg->mode != WC_SERVE_PER_CALL) return WC_ERR_INVALID_ARG;
+  if (batched && ex == nullptr) return WC_ERR_INVALID_ARG;
+  if (cfg->max_inflight == 0 || cfg->max_batch_items == 0) return WC_ERR_INVALID_ARG;
+  for (uint32_t i = 1; i < nreq; ++i)
+    if (reqs[i].arrival_ns < reqs[i - 1].arrival_ns) return WC_ERR_INVALID_ARG;
+
+  std::vector<cudaEvent_t> pool;
+  if (!batched) {
+    pool.resize(cfg->max_inflight);
+    for (auto& e : pool)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        for (auto& f : pool)
+          if (f) cudaEventDestroy(f);
+        return WC_ERR_CUDA;
+      }
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  auto now_ns = [&]() {
+    return static_cast<uint64_t>(
+        std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0).count());
+  };
+  uint32_t next_arrival = 0, completed = 0;
+  std::deque<uint32_t> waiting;  // arrived, not admitted
+  std::deque<uint32_t> ready;    // admitted, not launched
+  std::deque<Launch> inflight;   // launched, not seen finished (one stream: finish in order)
+  uint64_t admitted_bytes = 0, peak = 0, launches = 0, keys = 0;
+  uint32_t pool_next = 0;
+  std::vector<wc_work> batch;
+  batch.reserve(cfg->max_batch_items);
+  wc_status st = WC_OK;
+
+  while (completed < nreq && st == WC_OK) {
+    bool progress = false;
+    uint64_t now = now_ns();
+    while (next_arrival < nreq && reqs[next_arrival].arrival_ns <= now) waiting.push_back(next_arrival++);
+    // admission in arrival order within the HBM budget
+    while (!waiting.empty()) {
+      const uint32_t r = waiting.front();
+      const uint64_t b = reqs[r].io_bytes;
+      if (admitted_bytes + b > cfg->hbm_budget_bytes && admitted_bytes != 0) break;
+      admitted_bytes += b;
+      peak = std::max(peak, admitted_bytes);
+      timing[r].admitted_ns = now;
+      ready.push_back(r);
+      waiting.pop_front();
+      progress = true;
+    }
+    // completions
+    while (!inflight.empty()) {
+      Launch& f = inflight.front();
+      int32_t done = 0;
+      if (batched) {
+        st = wc_executor_query(ex, f.ticket, &done);
+        if (st != WC_OK) break;
+      } else {
+        const cudaError_t e = cudaEventQuery(f.ev);
+        if (e == cudaSuccess) {
+          done = 1;
+        } else if (e == cudaErrorNotReady) {
+          cudaGetLastError();
+        } else {
+          st = WC_ERR_CUDA;
+          break;
+        }
+      }
+      if (!done) break;
+      const uint64_t t = now_ns();
+      for (uint32_t r : f.reqs) {
+        timing[r].completed_ns = t;
+        admitted_bytes -= reqs[r].io_bytes;
+        ++completed;
+      }
+      inflight.pop_front();
+      progress = true;
+    }
+    // launches: while a slot is free, pack the admitted requests (continuous batching)
+    while (st == WC_OK && !ready.empty() && inflight.size() < cfg->max_inflight) {
+      Launch l;
+      const uint64_t t = now_ns();
+      if (batched) {
+        batch.clear();
+        uint64_t nk = 0;
+        while (!ready.empty() && batch.size() < cfg->max_batch_items) {
+          const uint32_t r = ready.front();
+          if (!batch.empty() && nk + reqs[r].work.n > cfg->max_batch_keys) break;
+          batch.push_back(reqs[r].work);
+          nk += reqs[r].work.n;
+          l.reqs.push_back(r);
+          ready.pop_front();
+        }
+        st = wc_executor_submit(ex, batch.data(), static_cast<uint32_t>(batch.size()), stream, &l.ticket);
+        keys += nk;
+      } else {
+        const uint32_t r = ready.front();
+        ready.pop_front();
+        l.reqs.push_back(r);
+        st = launch_one(reqs[r].work, stream);
+        l.ev = pool[pool_next++ % pool.size()];
+        if (st == WC_OK && cudaEventRecord(l.ev, static_cast<cudaStream_t>(stream)) != cudaSuccess) st = WC_ERR_CUDA;
+        keys += reqs[r].work.n;
+      }
+      for (uint32_t r : l.reqs) {
+        timing[r].launched_ns = t;
+        timing[r].batch = static_cast<uint32_t>(launches);
+      }
+      ++launches;
+      inflight.push_back(std::move(l));
+      progress = true;
+    }
+    if (!progress) std::this_thread::yield();
+  }
+  if (st == WC_OK && cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) st = WC_ERR_CUDA;
+  stats->wall_ns = now_ns();
+  uint64_t last = 0;
+  for (uint32_t i = 0; i < nreq; ++i) last = std::max(last, timing[i].completed_ns);
+  if (nreq) stats->wall_ns = last;
+  stats->launches = launches;
+  stats->keys = keys;
+  stats->peak_admitted_bytes = peak;
+  for (auto& e : pool) cudaEventDestroy(e);
+  return st;
+}

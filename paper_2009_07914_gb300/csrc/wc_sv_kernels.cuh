@@ -77,6 +77,9 @@ struct RangeSrc {
       next = end = 0;
     }
   }
+  // A fixed range [begin, end) (one tile of the batched executor).
+  __device__ RangeSrc(uint64_t begin, uint64_t end_)
+      : next(begin), end(end_), n(end_), counter(nullptr), chunk(0), done(false), fresh(true) {}
   // Warp-uniform: true while positions are left in [next, end) or can be pulled.
   __device__ __forceinline__ bool ensure() {
     if (next < end) return true;

@@ -1,0 +1,73 @@
+"""Serving loop: admission by HBM budget, continuous batching into the batched executor,
+per-call baseline.  Every request's result must be the same served in the mix (either
+mode) as run alone in arrival order (the CPU oracle applied one request at a time)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import wc_inputs
+from tests.test_exec_gpu import _oracle_apply, _oracles
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    from paper_2009_07914_gb300 import build
+    build.build()
+    import torch
+
+    from paper_2009_07914_gb300 import serve
+    return serve, torch
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_results_equal_alone_and_in_the_mix(env, mode):
+    serve, torch = env
+    tr = wc_inputs.serving_trace(77, n_tables=8, log2_cap=(12, 18), n_requests=120, log2_batch=(6, 14))
+    dt = serve.DeviceTrace(tr, window_width=8)
+    dt.reset()
+    arr = wc_inputs.poisson_arrivals(5, len(tr["requests"]), rate_per_s=20_000.0)
+    ex = serve.wc_executor_create(0, 8, max_items=64, tile_keys=1024) if mode == 0 else None
+    reqs = dt.requests(arr)
+    tim, st = serve.wc_serve_run(ex, reqs, mode, hbm_budget_bytes=1 << 30, max_batch_items=64, max_inflight=2)
+    assert st["keys"] == sum(r["keys"].size for r in tr["requests"])
+    assert (tim["completed_ns"] >= tim["launched_ns"]).all() and (tim["launched_ns"] >= tim["admitted_ns"]).all()
+    assert (tim["admitted_ns"] >= arr).all()
+    expect = _oracle_apply(_oracles(tr), tr)
+    for got, exp in zip(dt.retrieve_results(), expect):
+        if exp is not None:
+            np.testing.assert_array_equal(got[1], exp[1])
+            np.testing.assert_array_equal(got[0], exp[0])
+    ors = _oracles(tr)
+    _oracle_apply(ors, tr)
+    assert dt.sizes() == [o.size() for o in ors]
+    if mode == 0:
+        assert st["launches"] < len(reqs)  # requests were coalesced
+        serve.wc_executor_destroy(ex)
+    dt.close()
+
+
+def test_admission_respects_the_hbm_budget(env):
+    serve, torch = env
+    tr = wc_inputs.serving_trace(78, n_tables=4, log2_cap=(12, 16), n_requests=40, log2_batch=(8, 12))
+    dt = serve.DeviceTrace(tr, window_width=8)
+    dt.reset()
+    reqs = dt.requests(np.zeros(len(tr["requests"]), dtype=np.uint64))  # all arrive at once
+    biggest = max(r.io_bytes for r in reqs)
+    budget = 2 * biggest
+    ex = serve.wc_executor_create(0, 8, max_items=64, tile_keys=1024)
+    tim, st = serve.wc_serve_run(ex, reqs, 0, hbm_budget_bytes=budget, max_batch_items=64, max_inflight=2)
+    assert st["peak_admitted_bytes"] <= budget
+    assert st["launches"] >= 2
+    # admission is in arrival order
+    order = np.argsort(tim["admitted_ns"], kind="stable")
+    assert (np.diff(tim["admitted_ns"][order]) >= 0).all()
+    expect = _oracle_apply(_oracles(tr), tr)
+    for got, exp in zip(dt.retrieve_results(), expect):
+        if exp is not None:
+            np.testing.assert_array_equal(got[0], exp[0])
+    serve.wc_executor_destroy(ex)
+    dt.close()

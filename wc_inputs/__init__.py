@@ -254,3 +254,80 @@ def mv_uniform_r(seed: int, n: int, r: int):
     values = np.arange(n, dtype=np.uint64).astype(np.uint32)
     queries = np.arange(1, n + 1, dtype=np.uint64)
     return dict(keys=keys, values=values, queries=queries)
+
+
+def serving_trace(seed: int, n_tables: int = 64, log2_cap: tuple[float, float] = (16, 26),
+                  n_requests: int = 256, log2_batch: tuple[float, float] = (np.log2(1000), 24),
+                  mix: tuple[float, float, float] = (0.60, 0.35, 0.05), max_load: float = 0.9,
+                  prefill: tuple[float, float] = (0.0, 0.6), scale_keys: float = 1.0):
+    """The batched + served workload: tables with capacity 2^U(log2_cap), pre-filled to a
+    load ~U(prefill); requests with batch size 2^U(log2_batch) (times `scale_keys`), op
+    mix insert / retrieve / erase, inserts of fresh unique keys clamped to the room left
+    below `max_load`, retrieves half present / half absent, erases of present keys.
+    Arrival times are assigned by the caller (poisson_arrivals).
+
+    Returns dict(caps, prefill_keys[t], prefill_vals[t], requests=[dict(op, table, keys,
+    values)]) with ops 0 = insert, 1 = retrieve, 2 = erase."""
+    u = uniform_unit(seed, 4 * n_tables + 8 * n_requests)
+    caps = np.floor(2.0 ** (log2_cap[0] + (log2_cap[1] - log2_cap[0]) * u[:n_tables])).astype(np.int64)
+    pre = prefill[0] + (prefill[1] - prefill[0]) * u[n_tables:2 * n_tables]
+    universes, pf_keys, pf_vals, live, cursor = [], [], [], [], []
+    for t in range(n_tables):
+        m = int(caps[t])
+        uk = distinct_u32(seed * 1000003 + t, 2 * m + 64)  # [0, m): insertable, [m, 2m): never inserted
+        universes.append(uk)
+        k = int(pre[t] * m)
+        pf_keys.append(uk[:k].copy())
+        pf_vals.append(uniform_u32(seed * 7 + t, k))
+        live.append(list(range(k)))
+        cursor.append(k)
+    reqs = []
+    base = 2 * n_tables
+    for i in range(n_requests):
+        t = int(u[base + 8 * i] * n_tables) % n_tables
+        r = u[base + 8 * i + 1]
+        op = 0 if r < mix[0] else (1 if r < mix[0] + mix[1] else 2)
+        nb = int(2.0 ** (log2_batch[0] + (log2_batch[1] - log2_batch[0]) * u[base + 8 * i + 2]) * scale_keys)
+        nb = max(1, nb)
+        m = int(caps[t])
+        uk = universes[t]
+        rs = seed * 31 + i
+        if op == 0:
+            room = int(max_load * m) - len(live[t])
+            nb = min(nb, room, m - cursor[t])
+            if nb <= 0:
+                op, nb = 1, max(1, nb if nb > 0 else 1000)
+            else:
+                idx = np.arange(cursor[t], cursor[t] + nb)
+                cursor[t] += nb
+                live[t].extend(idx.tolist())
+                reqs.append(dict(op=0, table=t, keys=uk[idx], values=uniform_u32(rs, nb)))
+                continue
+        if op == 2:
+            if len(live[t]) == 0:
+                op = 1
+            else:
+                nb = min(nb, len(live[t]))
+                pick = shuffle_index(rs, len(live[t]))[:nb]
+                lv = np.asarray(live[t], dtype=np.int64)
+                gone = lv[pick]
+                keep = np.ones(lv.size, dtype=bool)
+                keep[pick] = False
+                live[t] = lv[keep].tolist()
+                reqs.append(dict(op=2, table=t, keys=uk[gone]))
+                continue
+        half = nb // 2
+        lv = np.asarray(live[t], dtype=np.int64)
+        pres = lv[shuffle_index(rs, lv.size)[: min(half, lv.size)]] if lv.size else np.zeros(0, dtype=np.int64)
+        absn = m + (np.arange(nb - pres.size) % m)
+        q = np.concatenate([uk[pres], uk[absn]])
+        q = q[shuffle_index(rs + 1, q.size)]
+        reqs.append(dict(op=1, table=t, keys=q))
+    return dict(caps=caps, prefill_keys=pf_keys, prefill_vals=pf_vals, requests=reqs)
+
+
+def poisson_arrivals(seed: int, n: int, rate_per_s: float) -> np.ndarray:
+    """Arrival times (ns) of a Poisson process: exponential gaps by inverse transform."""
+    u = uniform_unit(seed, n)
+    gaps = -np.log1p(-u) / rate_per_s
+    return (np.cumsum(gaps) * 1e9).astype(np.uint64)
