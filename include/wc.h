@@ -172,6 +172,23 @@ wc_status wc_table_get_launch(const wc_table* t, int32_t op, wc_launch* h_out);
 wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint64_t n,
                     void* stream);
 
+/* Insert without allocating: the same result as wc_insert on a single-value table (the
+ * paper has no counterpart -- this is a deployment variant of the region-split insert).
+ * For callers that cannot allocate device memory during the call (memory reserved up
+ * front, another allocator owning the device, code that must not grow a caching
+ * allocator): the batch is split by table region inside a static device buffer of
+ * WC_NOALLOC_SCRATCH_BYTES that the library holds in every context that loads it, until
+ * the process exits.  n may be at most WC_NOALLOC_SCRATCH_BYTES / (key_bytes +
+ * value_bytes) minus a few elements (2,097,088 pairs of 4+4 bytes; 1,048,544 of 8+8);
+ * larger n returns WC_ERR_INVALID_ARG -- split the batch.  The first call on a device
+ * looks up the buffer's device address with that device current; make that first call
+ * before capturing any stream.  All calls on a device share the buffer: calls whose GPU
+ * work may overlap (different streams with no ordering) race and must be ordered by the
+ * caller.  Multi-value tables return WC_ERR_UNSUPPORTED. */
+#define WC_NOALLOC_SCRATCH_BYTES (16ull << 20)
+wc_status wc_insert_noalloc(wc_table* t, const void* d_keys, const void* d_values, uint64_t n,
+                            void* stream);
+
 /* Single-value retrieve (Sec. IV-B4): d_values_out[i] = value of d_keys[i], or all ones
  * (NOT_FOUND) when absent; d_found_or_null[i] = 1/0 when the mask is given (a stored value
  * may itself be all ones).  Probing stops at the key or at the first window holding an

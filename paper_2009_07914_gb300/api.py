@@ -19,6 +19,7 @@ __all__ = [
     "wc_plan_capacity", "wc_table_create", "wc_table_destroy", "wc_table_clear", "wc_table_get_info",
     "wc_table_set_launch", "wc_table_get_launch", "wc_insert", "wc_retrieve", "wc_erase", "wc_count_values",
     "wc_retrieve_multi", "wc_size", "wc_num_keys", "wc_load_factor", "wc_get_status", "wc_status_string",
+    "wc_insert_noalloc", "WC_NOALLOC_SCRATCH_BYTES",
 ]
 
 
@@ -92,6 +93,21 @@ def wc_insert(t: int, keys, values, n: int | None = None, stream=None):
     n = _n_of(n, keys)
     _n_of(n, values)
     check(lib().wc_insert(t, ptr(keys), ptr(values), n, stream_handle(stream)), "wc_insert")
+
+
+B.extra_signatures({"wc_insert_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                          ctypes.c_uint64, ctypes.c_void_p])})
+
+WC_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def wc_insert_noalloc(t: int, keys, values, n: int | None = None, stream=None):
+    """wc_insert for callers that cannot allocate: splits the batch in the library's
+    fixed device buffer (at most WC_NOALLOC_SCRATCH_BYTES / (key + value bytes) pairs,
+    minus a few); calls on one device must not overlap on the GPU."""
+    n = _n_of(n, keys)
+    _n_of(n, values)
+    check(lib().wc_insert_noalloc(t, ptr(keys), ptr(values), n, stream_handle(stream)), "wc_insert_noalloc")
 
 
 def wc_retrieve(t: int, keys, values_out, found_out=None, n: int | None = None, stream=None):
