@@ -52,6 +52,14 @@ def parse():
     ap.add_argument("--group", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-probe", action="store_true", help="skip the random-access roofline probe")
+    ap.add_argument("--workload", default="sv32",
+                    choices=["sv32", "sv32_small", "sv64_zipf", "mv_zipf", "served"],
+                    help="sv32 (default): 2^27 uint32 pairs at load 0.9, insert + 50%% absent retrieve; "
+                         "sv32_small: 2^20 pairs at 0.8 with erase; sv64_zipf: 2^28 uint64 pairs, Zipf queries; "
+                         "mv_zipf: multi-value 2^28 Zipf inserts, count + CSR retrieve; "
+                         "served: 64 tables, Poisson requests, batched vs per-call")
+    ap.add_argument("--requests", type=int, default=512, help="served: number of requests")
     return ap.parse_args()
 
 
@@ -157,6 +165,47 @@ def cpu_baseline(log2n_sample: int, alpha: float):
             "sample": "2^%d inserts + 2^%d retrievals (half absent), std::unordered_map, one host thread"
                       % (log2n_sample, log2n_sample),
             "insert_gops": n / (t1 - t0) / 1e9, "retrieve_gops": n / (t2 - t1) / 1e9}
+
+
+
+def random_probe(dev, table_bytes: int):
+    """Live random-access roofline of this GPU over a buffer of the table's size: random
+    64 B and 32 B reads (a probing window) and 64 B read + CAS (an insert's claim)."""
+    import torch
+    from paper_2009_07914_gb300 import roofline as R
+    nbytes = max(1 << 26, (table_bytes + 255) // 256 * 256)
+    buf = torch.zeros(nbytes, dtype=torch.uint8, device=dev)
+    out = {"buffer_bytes": nbytes}
+    for ab, mode, key in ((64, 0, "rd64_gps"), (32, 0, "rd32_gps"), (64, 1, "rmw64_gps")):
+        r = R.random_access_rate(buf, ab, mode, accesses=1 << 26, reps=2)
+        out[key] = r["accesses_per_s"] / 1e9
+    del buf
+    torch.cuda.empty_cache()
+    return out
+
+
+def insert_launches(api, h, n: int) -> int:
+    """Kernels one wc_insert launches (3 for the region-split scheme, else 1)."""
+    lc = api.wc_table_get_launch(h, 0)
+    info = api.wc_table_get_info(h)
+    blocked = lc["scheme"] == 2 or (lc["scheme"] == 0 and info["kind"] == 0 and n >= (1 << 18)
+                                     and info["table_bytes"] > (64 << 20))
+    return 3 if blocked else 1
+
+
+def timed(s, f):
+    """Run f() between two events on stream s; returns ms."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    f()
+    b.record(s)
+    b.synchronize()
+    return a.elapsed_time(b)
+
+
+def emit(res):
+    print(json.dumps(res), flush=True)
 
 
 def run_reference(args, rank, world):
@@ -318,10 +367,213 @@ def run_wc(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "bytes_per_op": BYTES_PER_OP[dom], "traffic": traffic},
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (insert_launches(api, h, n) + 1) * args.steps,
+        "clocks": clk.summary(),
     }
+    if not args.no_probe:
+        pr = random_probe(dev, info["table_bytes"])
+        # retrieve reads ~1 window of W slots per present key and a few per absent key;
+        # report the query rate against the random-window read rate of the same buffer
+        res["random_roofline"] = dict(pr, retrieve_frac_of_rd64=res["retrieve_gops"] / pr["rd64_gps"],
+                                      insert_frac_of_rmw64=res["insert_gops"] / pr["rmw64_gps"])
     print(json.dumps(res), flush=True)
     api.wc_table_destroy(h)
+
+
+def _common(args, workload_name, metric, value, unit, ms_step, dtype, config, clk, launches, extra):
+    res = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+           "data": "synthetic", "config": dict(config, workload=workload_name), "gpu_launches": launches,
+           "clocks": clk.summary()}
+    res.update(extra)
+    emit(res)
+
+
+def run_sv32_small(args, dev):
+    """2^20 unique uint32 pairs at load 0.8 (a 10 MB table that fits in L2): insert, retrieve
+    2^20 present + 2^20 absent, erase a random half, retrieve all 2^21 again; with and
+    without the L2 access-policy window on the slot array."""
+    import torch
+    from paper_2009_07914_gb300 import api
+    from paper_2009_07914_gb300.table import to_device
+    n = 1 << 20
+    d = wc_inputs.sv_insert_retrieve_u32(0x57C00001, n, n, n)
+    keys, vals, qk = (to_device(d[k], 4, dev) for k in ("keys", "values", "queries"))
+    drop = to_device(d["keys"][wc_inputs.shuffle_index(0x57C00001, n)[: n // 2]], 4, dev)
+    out = torch.empty(2 * n, dtype=torch.int32, device=dev)
+    found = torch.empty(2 * n, dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream()
+    results = {}
+    for persist in (False, True):
+        h = api.wc_table_create(0, 4, 4, int(np.ceil(n / 0.8)), args.window, 0, 0x5EEDC0DE, dev.index, persist)
+
+        def step():
+            api.wc_table_clear(h, s)
+            api.wc_insert(h, keys, vals, n, s)
+            api.wc_retrieve(h, qk, out, found, 2 * n, s)
+            api.wc_erase(h, drop, n // 2, s)
+            api.wc_retrieve(h, qk, out, found, 2 * n, s)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        assert api.wc_size(h) == n - n // 2 and int(found.sum()) == n - n // 2
+        with ClockSampler(dev.index) as clk:
+            ms = timed(s, lambda: [step() for _ in range(args.steps)]) / args.steps
+        results[persist] = ms
+        info = api.wc_table_get_info(h)
+        api.wc_table_destroy(h)
+    ops = n + 2 * n + n // 2 + 2 * n
+    best = min(results.values())
+    _common(args, "sv_u32_n2^20_alpha0.80_erase", "G ops/s (insert + retrieve + erase + retrieve)", ops / best / 1e6,
+            "G ops/s", best, "u32", {"n": n, "capacity": info["capacity"], "table_bytes": info["table_bytes"],
+                                     "l2": "table fits in L2"}, clk, 4 * args.steps,
+            {"ms_per_step_no_l2_window": results[False], "ms_per_step_l2_window": results[True]})
+
+
+def run_sv64_zipf(args, dev):
+    """2^28 unique uint64 pairs at load 0.9 (4.8 GB of 16-byte slots, one 128-bit CAS per
+    claim); 2^28 queries drawn Zipf(1.1) over the inserted keys."""
+    import torch
+    from paper_2009_07914_gb300 import api
+    from paper_2009_07914_gb300.table import to_device
+    log2n = min(args.log2n, 28) if args.log2n != 27 else 28
+    n = 1 << log2n
+    d = wc_inputs.sv_u64_zipf(0x57C00003, n, n)
+    keys, vals, qk = (to_device(d[k], 8, dev) for k in ("keys", "values", "queries"))
+    out = torch.empty(n, dtype=torch.int64, device=dev)
+    found = torch.empty(n, dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream()
+    h = api.wc_table_create(0, 8, 8, int(np.ceil(n / 0.9)), args.window, 0, 0x5EEDC0DE, dev.index)
+    info = api.wc_table_get_info(h)
+    ev = []
+
+    def step(rec):
+        api.wc_table_clear(h, s)
+        t0 = timed(s, lambda: api.wc_insert(h, keys, vals, n, s))
+        t1 = timed(s, lambda: api.wc_retrieve(h, qk, out, found, n, s))
+        if rec:
+            ev.append((t0, t1))
+    for _ in range(args.warmup):
+        step(False)
+    assert api.wc_size(h) == n and int(found.sum()) == n
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.steps):
+            step(True)
+    ins = statistics.median(e[0] for e in ev)
+    ret = statistics.median(e[1] for e in ev)
+    peak, kind = peaks()
+    _common(args, "sv_u64_n2^%d_alpha0.90_zipf1.1" % log2n, "G ops/s (insert + Zipf retrieve)",
+            2 * n / ((ins + ret) * 1e-3) / 1e9, "G ops/s", ins + ret, "u64",
+            {"n": n, "capacity": info["capacity"], "table_bytes": info["table_bytes"],
+             "window_slots": info["window_width"], "l2": "no flush: table 4.8 GB"}, clk,
+            (insert_launches(api, h, n) + 1) * args.steps,
+            {"insert_gops": n / ins / 1e6, "retrieve_gops": n / ret / 1e6, "insert_ms": ins, "retrieve_ms": ret,
+             "roofline": {"bound": "hbm", "kernel": "k_sv_retrieve", "achieved": 48 * n / (ret * 1e-3) / 1e9,
+                          "peak": peak, "unit": "GB/s", "frac": 48 * n / (ret * 1e-3) / 1e9 / peak,
+                          "bytes_per_op": 48, "traffic": None}})
+    api.wc_table_destroy(h)
+
+
+def run_mv_zipf(args, dev):
+    """Multi-value: 2^28 inserts whose uint64 keys are drawn Zipf(1.1) over 2^24 distinct
+    keys (value = insert index, uint32); count_values then retrieve_multi for the whole
+    universe plus 2^22 absent keys, into CSR offsets."""
+    import torch
+    from paper_2009_07914_gb300 import api
+    from paper_2009_07914_gb300.table import to_device
+    uni, n, na = 1 << 24, 1 << 28, 1 << 22
+    d = wc_inputs.mv_zipf_u64(0x57C00004, uni, n, na)
+    keys = to_device(d["keys"], 8, dev)
+    vals = to_device(d["values"], 4, dev)
+    q = to_device(d["queries"], 8, dev)
+    nq = q.numel()
+    offs = torch.empty(nq + 1, dtype=torch.int64, device=dev)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    s = torch.cuda.current_stream()
+    h = api.wc_table_create(1, 8, 4, int(np.ceil(uni / 0.8)), args.window, n + (n >> 3), 0x5EEDC0DE, dev.index)
+    info = api.wc_table_get_info(h)
+    ev = []
+
+    def step(rec):
+        api.wc_table_clear(h, s)
+        t0 = timed(s, lambda: api.wc_insert(h, keys, vals, n, s))
+        t1 = timed(s, lambda: api.wc_count_values(h, q, offs, nq, want_total=False, stream=s))
+        t2 = timed(s, lambda: api.wc_retrieve_multi(h, q, offs, out, nq, s))
+        if rec:
+            ev.append((t0, t1, t2))
+    for _ in range(args.warmup):
+        step(False)
+    assert api.wc_size(h) == n and int(offs[-1].item()) == n and api.wc_get_status(h, True) == 0
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.steps):
+            step(True)
+    ins, cnt, ret = (statistics.median(e[i] for e in ev) for i in range(3))
+    total = ins + cnt + ret
+    _common(args, "mv_u64u32_n2^28_zipf1.1_over2^24", "G ops/s (inserts + queries + values retrieved)",
+            (n + nq + n) / (total * 1e-3) / 1e9, "G ops/s", total, "u64/u32",
+            {"n_inserts": n, "universe": uni, "queries": nq, "key_store_capacity": info["capacity"],
+             "pool": info["pool_capacity"], "l2": "no flush: 2 GB of inserts, 1 GB pool"}, clk,
+            5 * args.steps,
+            {"insert_gops": n / ins / 1e6, "count_gqps": nq / cnt / 1e6, "retrieve_multi_gvals": n / ret / 1e6,
+             "insert_ms": ins, "count_ms": cnt, "retrieve_multi_ms": ret, "distinct_keys": api.wc_num_keys(h)})
+    api.wc_table_destroy(h)
+
+
+def run_served(args, dev):
+    """64 uint32 tables (capacity 2^U(16,26), pre-filled to load U(0,0.6)); Poisson
+    requests with batch sizes 2^U(log2 1000, 24), 60/35/5 insert/retrieve/erase.  Each
+    mode serves the same trace from the same start: per-call launches and batched
+    (continuous batching into the persistent executor, up to 2^26 keys per launch), closed
+    loop and at 0.5/0.8/0.95 of the per-call saturation rate; p50/p99 latency per run.
+    One more closed-loop run caps batches at 2^22 keys and sends requests of 2^20 keys
+    or more as their own bulk call."""
+    import torch
+    from paper_2009_07914_gb300 import serve
+    tr = wc_inputs.serving_trace(0x57C00005, n_tables=64, n_requests=args.requests)
+    dt = serve.DeviceTrace(tr, device=dev.index, window_width=8)
+    ex = serve.wc_executor_create(dev.index, 8, max_items=1024, tile_keys=512)
+    nreq = len(tr["requests"])
+    keys_total = sum(r["keys"].size for r in tr["requests"])
+    budget = 64 << 30
+
+    def run(mode, arrivals, solo=0, max_keys=1 << 26):
+        dt.reset()
+        tim, st = serve.wc_serve_run(ex if mode == 0 else None, dt.requests(arrivals), mode, budget,
+                                     max_batch_keys=max_keys, max_batch_items=1024, max_inflight=2,
+                                     solo_min_keys=solo)
+        lat = (tim["completed_ns"] - arrivals).astype(np.float64) / 1e3
+        return {"throughput_gkeys": keys_total / st["wall_ns"], "p50_us": float(np.percentile(lat, 50)),
+                "p99_us": float(np.percentile(lat, 99)), "launches": st["launches"], "wall_ms": st["wall_ns"] / 1e6}
+    zero = np.zeros(nreq, dtype=np.uint64)
+    for _ in range(max(1, args.warmup)):
+        run(1, zero)
+        run(0, zero)
+    runs = {}
+    with ClockSampler(dev.index) as clk:
+        runs["per_call_closed"] = run(1, zero)
+        runs["batched_closed"] = run(0, zero)
+        runs["batched_small_batches_closed"] = run(0, zero, solo=1 << 20, max_keys=1 << 22)
+        sat = nreq / (runs["per_call_closed"]["wall_ms"] * 1e-3)
+        for f in (0.5, 0.8, 0.95):
+            arr = wc_inputs.poisson_arrivals(0x57C00005 + int(f * 100), nreq, f * sat)
+            runs["per_call_%.2f" % f] = run(1, arr)
+            runs["batched_%.2f" % f] = run(0, arr)
+    b, p = runs["batched_closed"], runs["per_call_closed"]
+    _common(args, "served_64tables_%dreq" % nreq, "G keys/s served (batched, closed loop)", b["throughput_gkeys"],
+            "G keys/s", b["wall_ms"], "u32", {"tables": 64, "requests": nreq, "keys": keys_total,
+                                              "per_call_saturation_req_per_s": sat}, clk,
+            b["launches"], {"runs": runs, "batched_over_per_call": b["throughput_gkeys"] / p["throughput_gkeys"]})
+    serve.wc_executor_destroy(ex)
+    dt.close()
+
+
+def run_workload(args, local_rank):
+    import torch
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    {"sv32_small": run_sv32_small, "sv64_zipf": run_sv64_zipf, "mv_zipf": run_mv_zipf,
+     "served": run_served}[args.workload](args, dev)
+
 
 
 def main():
@@ -331,6 +583,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload != "sv32":
+        if rank == 0:
+            run_workload(args, local_rank)
         return
     if world > 1:
         import torch

@@ -45,6 +45,11 @@ typedef struct {
   uint32_t max_inflight;      /* batches (or per-call launches) on the device at once */
   int32_t mode;               /* WC_SERVE_BATCHED or WC_SERVE_PER_CALL */
   int32_t reserved;
+  uint64_t solo_min_keys;     /* WC_SERVE_BATCHED: a request of at least this many keys runs
+                                 as its own bulk call (in order with the batches), since a
+                                 large batch gains nothing from packing and the per-call
+                                 path applies its own scheme (e.g. the region split);
+                                 0 = batch everything */
 } wc_serve_config;
 
 typedef struct {

@@ -84,7 +84,7 @@ struct ExecShape<4> {
 };
 template <>
 struct ExecShape<8> {
-  static constexpr int GI = 1, GR = 2;
+  static constexpr int GI = 2, GR = 2;
 };
 template <>
 struct ExecShape<16> {
@@ -92,7 +92,7 @@ struct ExecShape<16> {
 };
 
 template <int W>
-__global__ void __launch_bounds__(kExecThreads) k_exec(const ExecHeader* __restrict__ hdr,
+__global__ void __launch_bounds__(kExecThreads, 3) k_exec(const ExecHeader* __restrict__ hdr,
                                                        const unsigned long long* __restrict__ gtiles,
                                                        const ExecItem* __restrict__ items,
                                                        unsigned long long* __restrict__ next_tile,
@@ -172,9 +172,11 @@ struct wc_executor {
   cudaEvent_t ring[kTicketRing] = {};
   uint64_t next_ticket = 0;
   cudaStream_t last_stream = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t n_copy = nullptr, n_set = nullptr, n_kernel = nullptr;
+  // one graph per staging slot: [H2D copy of that slot's work list | reset of the tile and
+  // group counters | kernel], all with fixed arguments, so a submit never updates a graph
+  // that may still be running
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
   void* kernel = nullptr;
 };
 
@@ -193,8 +195,10 @@ struct Guard {
 };
 
 void free_executor(wc_executor* ex) {
-  if (ex->exec) cudaGraphExecDestroy(ex->exec);
-  if (ex->graph) cudaGraphDestroy(ex->graph);
+  for (int i = 0; i < 2; ++i) {
+    if (ex->exec[i]) cudaGraphExecDestroy(ex->exec[i]);
+    if (ex->graph[i]) cudaGraphDestroy(ex->graph[i]);
+  }
   for (auto& e : ex->ring)
     if (e) cudaEventDestroy(e);
   for (int i = 0; i < 2; ++i) {
@@ -243,39 +247,41 @@ wc_status wc_executor_create(wc_executor** out, const wc_executor_config* cfg) {
     free_executor(ex);
     return WC_ERR_OUT_OF_MEMORY;
   }
-  // graph: H2D copy of the work list -> reset of the tile/group counters -> kernel
-  ok = cudaGraphCreate(&ex->graph, 0) == cudaSuccess;
-  if (ok) {
-    ok = cudaGraphAddMemcpyNode1D(&ex->n_copy, ex->graph, nullptr, 0, ex->d_buf, ex->h_stage[0], ex->lay.items,
-                                  cudaMemcpyHostToDevice) == cudaSuccess;
-  }
-  if (ok) {
-    cudaMemsetParams mp = {};
-    mp.dst = ex->d_buf + ex->lay.next;
-    mp.value = 0;
-    mp.elementSize = 1;
-    mp.width = 8;
-    mp.height = 1;
-    ok = cudaGraphAddMemsetNode(&ex->n_set, ex->graph, &ex->n_copy, 1, &mp) == cudaSuccess;
-  }
-  if (ok) {
-    int bps = occupancy_cached(ex->kernel, kExecThreads, 0);
-    const auto* hdr = reinterpret_cast<const ExecHeader*>(ex->d_buf + ex->lay.hdr);
-    const auto* gt = reinterpret_cast<const unsigned long long*>(ex->d_buf + ex->lay.gtiles);
-    const auto* items = reinterpret_cast<const ExecItem*>(ex->d_buf + ex->lay.items);
-    auto* next = reinterpret_cast<unsigned long long*>(ex->d_buf + ex->lay.next);
-    auto* gdone = reinterpret_cast<unsigned long long*>(ex->d_buf + ex->lay.gdone);
-    auto* xst = reinterpret_cast<uint32_t*>(ex->d_buf + ex->lay.status);
-    uint64_t tmo = ex->cfg.timeout_ns;
-    uint32_t tkeys = ex->cfg.tile_keys;
-    void* args[] = {&hdr, &gt, &items, &next, &gdone, &xst, &tmo, &tkeys};
-    cudaKernelNodeParams kp = {};
-    kp.func = ex->kernel;
-    kp.gridDim = dim3(static_cast<unsigned>(bps * ex->sm_count));
-    kp.blockDim = dim3(kExecThreads);
-    kp.kernelParams = args;
-    ok = cudaGraphAddKernelNode(&ex->n_kernel, ex->graph, &ex->n_set, 1, &kp) == cudaSuccess &&
-         cudaGraphInstantiate(&ex->exec, ex->graph, 0) == cudaSuccess;
+  // graphs: H2D copy of the work list -> reset of the tile/group counters -> kernel
+  int bps = occupancy_cached(ex->kernel, kExecThreads, 0);
+  const auto* hdr = reinterpret_cast<const ExecHeader*>(ex->d_buf + ex->lay.hdr);
+  const auto* gt = reinterpret_cast<const unsigned long long*>(ex->d_buf + ex->lay.gtiles);
+  const auto* items = reinterpret_cast<const ExecItem*>(ex->d_buf + ex->lay.items);
+  auto* next = reinterpret_cast<unsigned long long*>(ex->d_buf + ex->lay.next);
+  auto* gdone = reinterpret_cast<unsigned long long*>(ex->d_buf + ex->lay.gdone);
+  auto* xst = reinterpret_cast<uint32_t*>(ex->d_buf + ex->lay.status);
+  uint64_t tmo = ex->cfg.timeout_ns;
+  uint32_t tkeys = ex->cfg.tile_keys;
+  void* args[] = {&hdr, &gt, &items, &next, &gdone, &xst, &tmo, &tkeys};
+  for (int g = 0; ok && g < 2; ++g) {
+    cudaGraphNode_t n_copy = nullptr, n_set = nullptr, n_kernel = nullptr;
+    ok = cudaGraphCreate(&ex->graph[g], 0) == cudaSuccess;
+    if (ok)
+      ok = cudaGraphAddMemcpyNode1D(&n_copy, ex->graph[g], nullptr, 0, ex->d_buf, ex->h_stage[g], ex->lay.next,
+                                    cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok) {
+      cudaMemsetParams mp = {};
+      mp.dst = ex->d_buf + ex->lay.next;
+      mp.value = 0;
+      mp.elementSize = 1;
+      mp.width = ex->lay.status - ex->lay.next;
+      mp.height = 1;
+      ok = cudaGraphAddMemsetNode(&n_set, ex->graph[g], &n_copy, 1, &mp) == cudaSuccess;
+    }
+    if (ok) {
+      cudaKernelNodeParams kp = {};
+      kp.func = ex->kernel;
+      kp.gridDim = dim3(static_cast<unsigned>(bps * ex->sm_count));
+      kp.blockDim = dim3(kExecThreads);
+      kp.kernelParams = args;
+      ok = cudaGraphAddKernelNode(&n_kernel, ex->graph[g], &n_set, 1, &kp) == cudaSuccess &&
+           cudaGraphInstantiate(&ex->exec[g], ex->graph[g], 0) == cudaSuccess;
+    }
   }
   if (!ok) {
     cudaGetLastError();
@@ -369,19 +375,7 @@ wc_status wc_executor_submit(wc_executor* ex, const wc_work* h_items, uint32_t c
   hdr->total_tiles = tiles;
   hdr->nitems = ni;
   hdr->ngroups = ng;
-  const size_t bytes = ex->lay.items + static_cast<size_t>(ni) * sizeof(ExecItem);
-  cudaError_t e = cudaGraphExecMemcpyNodeSetParams1D(ex->exec, ex->n_copy, ex->d_buf, st, bytes,
-                                                     cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) {
-    cudaMemsetParams mp = {};
-    mp.dst = ex->d_buf + ex->lay.next;
-    mp.value = 0;
-    mp.elementSize = 1;
-    mp.width = 8 + static_cast<size_t>(ng) * 8;
-    mp.height = 1;
-    e = cudaGraphExecMemsetNodeSetParams(ex->exec, ex->n_set, &mp);
-  }
-  if (e == cudaSuccess) e = cudaGraphLaunch(ex->exec, s);
+  cudaError_t e = cudaGraphLaunch(ex->exec[slot], s);
   if (e == cudaSuccess) e = cudaEventRecord(ex->stage_ev[slot], s);
   if (e == cudaSuccess) e = cudaEventRecord(ex->ring[ticket % kTicketRing], s);
   return e == cudaSuccess ? WC_OK : WC_ERR_CUDA;

@@ -45,7 +45,7 @@ extern "C" wc_status wc_serve_run(wc_executor* ex, const wc_request* reqs, uint3
     if (reqs[i].arrival_ns < reqs[i - 1].arrival_ns) return WC_ERR_INVALID_ARG;
 
   std::vector<cudaEvent_t> pool;
-  if (!batched) {
+  {
     pool.resize(cfg->max_inflight);
     for (auto& e : pool)
       if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
@@ -89,7 +89,7 @@ extern "C" wc_status wc_serve_run(wc_executor* ex, const wc_request* reqs, uint3
     while (!inflight.empty()) {
       Launch& f = inflight.front();
       int32_t done = 0;
-      if (batched) {
+      if (f.ev == nullptr) {
         st = wc_executor_query(ex, f.ticket, &done);
         if (st != WC_OK) break;
       } else {
@@ -117,12 +117,14 @@ extern "C" wc_status wc_serve_run(wc_executor* ex, const wc_request* reqs, uint3
     while (st == WC_OK && !ready.empty() && inflight.size() < cfg->max_inflight) {
       Launch l;
       const uint64_t t = now_ns();
-      if (batched) {
+      const bool solo = !batched || (cfg->solo_min_keys && reqs[ready.front()].work.n >= cfg->solo_min_keys);
+      if (!solo) {
         batch.clear();
         uint64_t nk = 0;
         while (!ready.empty() && batch.size() < cfg->max_batch_items) {
           const uint32_t r = ready.front();
           if (!batch.empty() && nk + reqs[r].work.n > cfg->max_batch_keys) break;
+          if (cfg->solo_min_keys && reqs[r].work.n >= cfg->solo_min_keys) break;  // keeps arrival order
           batch.push_back(reqs[r].work);
           nk += reqs[r].work.n;
           l.reqs.push_back(r);

@@ -30,7 +30,7 @@ class WcRequest(ctypes.Structure):
 class WcServeConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_batch_keys", ctypes.c_uint64),
                 ("max_batch_items", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32), ("mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("solo_min_keys", ctypes.c_uint64)]
 
 
 class WcRequestTiming(ctypes.Structure):
@@ -104,12 +104,14 @@ def wc_executor_get_status(ex: int, clear: bool = False) -> int:
 
 
 def wc_serve_run(ex: int | None, requests: list[WcRequest], mode: int, hbm_budget_bytes: int,
-                 max_batch_keys: int = 1 << 26, max_batch_items: int = 256, max_inflight: int = 2, stream=None):
+                 max_batch_keys: int = 1 << 26, max_batch_items: int = 256, max_inflight: int = 2, stream=None,
+                 solo_min_keys: int = 0):
     """Returns (timings as a dict of numpy arrays, stats dict)."""
     n = len(requests)
     arr = (WcRequest * max(1, n))(*requests)
     cfg = WcServeConfig(hbm_budget_bytes=hbm_budget_bytes, max_batch_keys=max_batch_keys,
-                        max_batch_items=max_batch_items, max_inflight=max_inflight, mode=mode, reserved=0)
+                        max_batch_items=max_batch_items, max_inflight=max_inflight, mode=mode, reserved=0,
+                        solo_min_keys=solo_min_keys)
     tim = (WcRequestTiming * max(1, n))()
     st = WcServeStats()
     B.check(B.lib().wc_serve_run(ex, arr, n, ctypes.byref(cfg), B.stream_handle(stream), tim, ctypes.byref(st)),

@@ -68,3 +68,29 @@ def test_sv_recipe_shapes():
     assert (d["q_src"] >= 0).sum() == 500
     assert np.array_equal(d["queries"][d["q_src"] >= 0], d["keys"][d["q_src"][d["q_src"] >= 0]])
     assert not np.isin(d["queries"][d["q_src"] < 0], d["keys"]).any()
+
+
+def test_c_stream_fills_equal_the_numpy_definitions():
+    w.build_helper()
+    assert w._helper() is not None
+    a = w.splitmix64(0xDEADBEEF, 17, 50_000)
+    b = w.splitmix64_np(0xDEADBEEF, 17, 50_000)
+    assert np.array_equal(a, b)
+    hi = w.uniform_u32(5, 50_000)
+    assert np.array_equal(hi, (w.splitmix64_np(5, 0, 50_000) >> np.uint64(32)).astype(np.uint32))
+    x = np.arange(50_002, dtype=np.uint64).astype(np.uint32) * np.uint32(0x9E3779B9) + np.uint32(12345)
+    ref = w.lowbias32(x)
+    keep = ref[(ref != 0) & (ref != np.uint32(0xFFFFFFFF))][:50_000]
+    assert np.array_equal(w.distinct_u32(12345, 50_000), keep)
+
+
+def test_serving_trace_shape():
+    tr = w.serving_trace(3, n_tables=4, log2_cap=(10, 12), n_requests=50, log2_batch=(4, 9))
+    assert len(tr["requests"]) == 50 and len(tr["caps"]) == 4
+    for r in tr["requests"]:
+        assert r["op"] in (0, 1, 2) and r["keys"].size >= 1
+        if r["op"] == 0:
+            assert r["values"].size == r["keys"].size
+    arr = w.poisson_arrivals(1, 1000, 1e6)
+    assert (np.diff(arr.astype(np.int64)) >= 0).all()
+    assert 0.5e-3 < arr[-1] / 1e9 < 2e-3  # ~1000 arrivals at 1e6/s take ~1 ms

@@ -23,8 +23,8 @@ def env():
     return serve, torch
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_results_equal_alone_and_in_the_mix(env, mode):
+@pytest.mark.parametrize("mode,solo", [(0, 0), (0, 2000), (1, 0)])
+def test_results_equal_alone_and_in_the_mix(env, mode, solo):
     serve, torch = env
     tr = wc_inputs.serving_trace(77, n_tables=8, log2_cap=(12, 18), n_requests=120, log2_batch=(6, 14))
     dt = serve.DeviceTrace(tr, window_width=8)
@@ -32,7 +32,8 @@ def test_results_equal_alone_and_in_the_mix(env, mode):
     arr = wc_inputs.poisson_arrivals(5, len(tr["requests"]), rate_per_s=20_000.0)
     ex = serve.wc_executor_create(0, 8, max_items=64, tile_keys=1024) if mode == 0 else None
     reqs = dt.requests(arr)
-    tim, st = serve.wc_serve_run(ex, reqs, mode, hbm_budget_bytes=1 << 30, max_batch_items=64, max_inflight=2)
+    tim, st = serve.wc_serve_run(ex, reqs, mode, hbm_budget_bytes=1 << 30, max_batch_items=64, max_inflight=2,
+                                 solo_min_keys=solo)
     assert st["keys"] == sum(r["keys"].size for r in tr["requests"])
     assert (tim["completed_ns"] >= tim["launched_ns"]).all() and (tim["launched_ns"] >= tim["admitted_ns"]).all()
     assert (tim["admitted_ns"] >= arr).all()

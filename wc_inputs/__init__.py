@@ -33,9 +33,51 @@ TOMBSTONE_KEY64 = 0xFFFFFFFFFFFFFFFF
 
 _CHUNK = 1 << 24  # elements per vector pass; bounds the temporaries
 
+# Optional C fills of the same streams (_gen.c); numpy below is the definition they are
+# tested against and the fallback when the helper is not built.
+import ctypes as _ct
+import os as _os
+import subprocess as _sp
+
+_HERE = _os.path.dirname(_os.path.abspath(__file__))
+_GEN_SRC = _os.path.join(_HERE, "_gen.c")
+_GEN_LIB = _os.path.join(_HERE, "libwcgen.so")
+_gen = None
+
+
+def build_helper() -> str:
+    """Compile _gen.c into libwcgen.so next to it (portable flags)."""
+    if not _os.path.exists(_GEN_LIB) or _os.path.getmtime(_GEN_LIB) < _os.path.getmtime(_GEN_SRC):
+        tmp = _GEN_LIB + ".tmp%d" % _os.getpid()
+        _sp.check_call(["gcc", "-O2", "-shared", "-fPIC", _GEN_SRC, "-o", tmp])
+        _os.replace(tmp, _GEN_LIB)
+    return _GEN_LIB
+
+
+def _helper():
+    global _gen
+    if _gen is None and _os.path.exists(_GEN_LIB):
+        lib = _ct.CDLL(_GEN_LIB)
+        u64, vp, u32 = _ct.c_uint64, _ct.c_void_p, _ct.c_uint32
+        lib.wcgen_splitmix64.argtypes = [u64, u64, u64, vp]
+        lib.wcgen_splitmix64_hi32.argtypes = [u64, u64, u64, vp]
+        lib.wcgen_lowbias32_weyl.argtypes = [u32, u64, u64, vp]
+        _gen = lib
+    return _gen
+
 
 def splitmix64(seed: int, start: int, count: int) -> np.ndarray:
     """Outputs start..start+count-1 of the SplitMix64 stream with the given seed."""
+    g = _helper()
+    if g is not None and count > 4096:
+        out = np.empty(count, dtype=np.uint64)
+        g.wcgen_splitmix64(seed & 0xFFFFFFFFFFFFFFFF, start, count, out.ctypes.data)
+        return out
+    return splitmix64_np(seed, start, count)
+
+
+def splitmix64_np(seed: int, start: int, count: int) -> np.ndarray:
+    """numpy definition of splitmix64 (the reference the C fill is checked against)."""
     out = np.empty(count, dtype=np.uint64)
     seed = U64(seed & 0xFFFFFFFFFFFFFFFF)
     c1 = U64(0xBF58476D1CE4E5B9)
@@ -71,8 +113,14 @@ def distinct_u32(seed: int, count: int) -> np.ndarray:
     """`count` pairwise-distinct uint32 keys, sentinels (0, 0xFFFFFFFF) excluded."""
     if count + 2 > (1 << 32):
         raise ValueError("at most 2^32 - 2 distinct uint32 keys exist")
-    out = np.empty(count + 2, dtype=np.uint32)
     base = np.uint32((seed ^ (seed >> 32)) & 0xFFFFFFFF)
+    g = _helper()
+    if g is not None and count > 4096:
+        out = np.empty(count + 2, dtype=np.uint32)
+        g.wcgen_lowbias32_weyl(int(base), 0, count + 2, out.ctypes.data)
+        keep = (out != 0) & (out != np.uint32(TOMBSTONE_KEY32))
+        return out[keep][:count].copy()
+    out = np.empty(count + 2, dtype=np.uint32)
     with np.errstate(over="ignore"):
         for lo in range(0, count + 2, _CHUNK):
             hi = min(count + 2, lo + _CHUNK)
@@ -93,6 +141,11 @@ def distinct_u64(seed: int, count: int) -> np.ndarray:
 
 def uniform_u32(seed: int, count: int) -> np.ndarray:
     """Uniform uint32 values (high halves of a SplitMix64 stream)."""
+    g = _helper()
+    if g is not None and count > 4096:
+        out = np.empty(count, dtype=np.uint32)
+        g.wcgen_splitmix64_hi32(seed & 0xFFFFFFFFFFFFFFFF, 0, count, out.ctypes.data)
+        return out
     return (splitmix64(seed, 0, count) >> U64(32)).astype(np.uint32)
 
 
@@ -271,57 +324,63 @@ def serving_trace(seed: int, n_tables: int = 64, log2_cap: tuple[float, float] =
     u = uniform_unit(seed, 4 * n_tables + 8 * n_requests)
     caps = np.floor(2.0 ** (log2_cap[0] + (log2_cap[1] - log2_cap[0]) * u[:n_tables])).astype(np.int64)
     pre = prefill[0] + (prefill[1] - prefill[0]) * u[n_tables:2 * n_tables]
-    universes, pf_keys, pf_vals, live, cursor = [], [], [], [], []
+    universes, pf_keys, pf_vals, state, cursor, nlive = [], [], [], [], [], []
     for t in range(n_tables):
         m = int(caps[t])
-        uk = distinct_u32(seed * 1000003 + t, 2 * m + 64)  # [0, m): insertable, [m, 2m): never inserted
+        # keys [0, m) may be inserted; keys [m, 2m) never are (the absent queries)
+        uk = distinct_u32(seed * 1000003 + t, 2 * m)
         universes.append(uk)
         k = int(pre[t] * m)
         pf_keys.append(uk[:k].copy())
         pf_vals.append(uniform_u32(seed * 7 + t, k))
-        live.append(list(range(k)))
+        st = np.zeros(m, dtype=np.int8)  # 0 never inserted, 1 live, 2 erased
+        st[:k] = 1
+        state.append(st)
         cursor.append(k)
+        nlive.append(k)
     reqs = []
     base = 2 * n_tables
     for i in range(n_requests):
         t = int(u[base + 8 * i] * n_tables) % n_tables
         r = u[base + 8 * i + 1]
         op = 0 if r < mix[0] else (1 if r < mix[0] + mix[1] else 2)
-        nb = int(2.0 ** (log2_batch[0] + (log2_batch[1] - log2_batch[0]) * u[base + 8 * i + 2]) * scale_keys)
-        nb = max(1, nb)
+        nb = max(1, int(2.0 ** (log2_batch[0] + (log2_batch[1] - log2_batch[0]) * u[base + 8 * i + 2]) * scale_keys))
         m = int(caps[t])
         uk = universes[t]
         rs = seed * 31 + i
         if op == 0:
-            room = int(max_load * m) - len(live[t])
-            nb = min(nb, room, m - cursor[t])
-            if nb <= 0:
-                op, nb = 1, max(1, nb if nb > 0 else 1000)
-            else:
+            room = min(int(max_load * m) - nlive[t], m - cursor[t])
+            if room > 0:
+                nb = min(nb, room)
                 idx = np.arange(cursor[t], cursor[t] + nb)
                 cursor[t] += nb
-                live[t].extend(idx.tolist())
+                state[t][idx] = 1
+                nlive[t] += nb
                 reqs.append(dict(op=0, table=t, keys=uk[idx], values=uniform_u32(rs, nb)))
                 continue
-        if op == 2:
-            if len(live[t]) == 0:
-                op = 1
-            else:
-                nb = min(nb, len(live[t]))
-                pick = shuffle_index(rs, len(live[t]))[:nb]
-                lv = np.asarray(live[t], dtype=np.int64)
-                gone = lv[pick]
-                keep = np.ones(lv.size, dtype=bool)
-                keep[pick] = False
-                live[t] = lv[keep].tolist()
+            op = 1  # table full: serve a retrieve instead
+        if op == 2 and nlive[t] > 0:
+            # a window of insertion positions from a random start; its live keys go
+            off = int(splitmix64(rs, 0, 1)[0] % np.uint64(cursor[t]))
+            cand = np.arange(off, min(cursor[t], off + 2 * nb))
+            gone = cand[state[t][cand] == 1][:nb]
+            if gone.size:
+                state[t][gone] = 2
+                nlive[t] -= gone.size
                 reqs.append(dict(op=2, table=t, keys=uk[gone]))
                 continue
-        half = nb // 2
-        lv = np.asarray(live[t], dtype=np.int64)
-        pres = lv[shuffle_index(rs, lv.size)[: min(half, lv.size)]] if lv.size else np.zeros(0, dtype=np.int64)
-        absn = m + (np.arange(nb - pres.size) % m)
-        q = np.concatenate([uk[pres], uk[absn]])
-        q = q[shuffle_index(rs + 1, q.size)]
+            op = 1
+        # retrieve: each query independently present or absent with probability 1/2;
+        # present keys are a window of insertion positions from a random start (the
+        # universe is in random order, so this is a random subset) -- erased ones among
+        # them are absent queries too; absent keys come from the never-inserted half
+        coin = uniform_unit(rs, nb) < 0.5
+        r2 = splitmix64(rs + 1, 0, 2)
+        cur = max(cursor[t], 1)
+        ip = (int(r2[0] % np.uint64(cur)) + np.arange(nb, dtype=np.int64)) % cur
+        ia = m + (int(r2[1] % np.uint64(m)) + np.arange(nb, dtype=np.int64)) % m
+        use_p = coin & (state[t][ip] == 1) if cursor[t] else np.zeros(nb, dtype=bool)
+        q = np.where(use_p, uk[ip], uk[ia])
         reqs.append(dict(op=1, table=t, keys=q))
     return dict(caps=caps, prefill_keys=pf_keys, prefill_vals=pf_vals, requests=reqs)
 
