@@ -87,7 +87,7 @@ bool shape_ok(const wc_table* t, int op, int G) {
 // blocked scheme's L2-resident probes favour it); lookups use 32 bytes of the window per
 // lane (one 256-bit load).
 int default_group(uint64_t slot_bytes, int W, int op) {
-  if (op == WC_OP_INSERT && W <= 8 * static_cast<int>(8 / slot_bytes)) return 1;
+  if (op == WC_OP_INSERT && static_cast<uint64_t>(W) * slot_bytes <= 64) return 1;
   const int per_lane = static_cast<int>(32 / slot_bytes);
   return std::max(1, W / per_lane);
 }

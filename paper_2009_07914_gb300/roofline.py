@@ -63,3 +63,39 @@ def random_access_rate(buffer: torch.Tensor, access_bytes: int, mode: int = 0, a
         best = ms if best is None else min(best, ms)
     return {"access_bytes": access_bytes, "mode": mode, "ms": best, "accesses_per_s": accesses / (best * 1e-3),
             "gbs": accesses * access_bytes / (best * 1e-3) / 1e9}
+
+
+def main():
+    """Sweep of the random-access roofline: rate vs access size, mode, buffer size and L2
+    fetch-granularity limit (one JSON line per point)."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--accesses", type=int, default=1 << 27)
+    ap.add_argument("--gran", default="32,64,128", help="L2 fetch-granularity limits to try")
+    ap.add_argument("--bytes", default="32,64,128")
+    ap.add_argument("--buffers-mib", default="8192,1024,64")
+    ap.add_argument("--capacity-curve", action="store_true",
+                    help="also sweep 64 B reads / read+CAS over buffers of 4 MiB .. 1 GiB")
+    a = ap.parse_args()
+    bufs = [int(x) for x in a.buffers_mib.split(",")]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    buf = torch.zeros(max(bufs + [1024]) << 20, dtype=torch.uint8, device=dev)
+    for g in (int(x) for x in a.gran.split(",")):
+        wc_set_l2_fetch_granularity(g)
+        for ab in (int(x) for x in a.bytes.split(",")):
+            for mode in (0, 1):
+                for mib in bufs:
+                    r = random_access_rate(buf, ab, mode, a.accesses, buffer_bytes=mib << 20)
+                    r.update(gran=g, buffer_mib=mib)
+                    print(json.dumps(r), flush=True)
+    if a.capacity_curve:
+        for mode in (0, 1):
+            for mib in (4, 8, 16, 24, 32, 48, 64, 80, 96, 128, 192, 256, 512, 1024):
+                r = random_access_rate(buf, 64, mode, a.accesses // 2, buffer_bytes=mib << 20)
+                r.update(curve=True, buffer_mib=mib)
+                print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+"""Autotuner: picks the probing window width W, the lanes per key (cooperative group
+size), the block size and the insert scheme for a key width and load factor by timing the
+library's own kernels on a seeded sample, and caches the choice.
+
+    python -m paper_2009_07914_gb300.tune --key-bytes 4 --log2n 27 --alpha 0.9
+
+prints one JSON line per measured candidate and a final line with the choice.  In code:
+
+    best = tune_table(handle, keys, values, queries)   # tunes one table's launch shapes
+    W = recommend_window(4, 4, n, alpha)               # window width for a new table
+
+The cache is a JSON file (WC_TUNE_CACHE, default tune_cache.json beside this module),
+keyed by GPU name, widths, W, load-factor decile and log2 of the batch size.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+
+import numpy as np
+import torch
+
+from . import api
+from ._binding import WC_OP_ERASE, WC_OP_INSERT, WC_OP_RETRIEVE, WC_SCHEME_BLOCKED, WC_SCHEME_DIRECT
+
+SHAPES = {  # slot bytes -> W -> valid lanes per key
+    8: {4: [1, 2, 4], 8: [1, 2, 4, 8], 16: [2, 4, 8, 16], 32: [4, 8, 16, 32]},
+    16: {2: [1, 2], 4: [1, 2, 4], 8: [2, 4, 8], 16: [4, 8, 16]},
+}
+BLOCKS = (256, 128)
+
+
+def _cache_path() -> str:
+    return os.environ.get("WC_TUNE_CACHE", os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                          "tune_cache.json"))
+
+
+def _load_cache() -> dict:
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _save_cache(c: dict):
+    tmp = _cache_path() + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(c, f, indent=1, sort_keys=True)
+    os.replace(tmp, _cache_path())
+
+
+def cache_key(kb: int, vb: int, W: int, alpha: float, n: int, op: str) -> str:
+    gpu = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    return "%s|k%d v%d|W%d|a%.1f|n2^%d|%s" % (gpu, kb, vb, W, round(alpha, 1), max(0, int(math.log2(max(n, 1)))),
+                                             op)
+
+
+def _time(f, reps: int = 3) -> float:
+    s = torch.cuda.current_stream()
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        f()
+        b.record(s)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def tune_table(h: int, keys: torch.Tensor, values: torch.Tensor, queries: torch.Tensor, reps: int = 3,
+               use_cache: bool = True, report=None) -> dict:
+    """Time every launch shape of insert and retrieve (and erase) on table `h` with the
+    given device sample, set the fastest with wc_table_set_launch and return them.
+    The table is cleared and left holding `keys`."""
+    info = api.wc_table_get_info(h)
+    if info["kind"] != 0:
+        raise ValueError("the tuner handles single-value tables")
+    W, sb = info["window_width"], info["slot_bytes"]
+    kb = vb = 4 if sb == 8 else 8
+    n = keys.numel()
+    alpha = n / info["capacity"]
+    cache = _load_cache() if use_cache else {}
+    best = {}
+    s = torch.cuda.current_stream()
+    out = torch.empty(queries.numel(), dtype=torch.int32 if vb == 4 else torch.int64, device=keys.device)
+    found = torch.empty(queries.numel(), dtype=torch.uint8, device=keys.device)
+    for opname, op in (("insert", WC_OP_INSERT), ("retrieve", WC_OP_RETRIEVE), ("erase", WC_OP_ERASE)):
+        key = cache_key(kb, vb, W, alpha, n, opname)
+        if key in cache:
+            c = cache[key]
+            api.wc_table_set_launch(h, op, c["group"], c["block"], 0, c["scheme"], 0)
+            best[opname] = dict(c, cached=True)
+            continue
+        schemes = [WC_SCHEME_DIRECT, WC_SCHEME_BLOCKED] if opname == "insert" else [WC_SCHEME_DIRECT]
+        results = []
+        for G in SHAPES[sb][W]:
+            for blk in BLOCKS:
+                for sc in schemes:
+                    api.wc_table_set_launch(h, op, G, blk, 0, sc, 0)
+                    if opname == "insert":
+                        def f():
+                            api.wc_table_clear(h, s)
+                            api.wc_insert(h, keys, values, n, s)
+                        ms = _time(f, reps)  # includes the clear: same for every candidate
+                    elif opname == "retrieve":
+                        ms = _time(lambda: api.wc_retrieve(h, queries, out, found, queries.numel(), s), reps)
+                    else:
+                        def f():
+                            api.wc_table_clear(h, s)
+                            api.wc_insert(h, keys, values, n, s)
+                            api.wc_erase(h, keys, n, s)
+                        ms = _time(f, reps)
+                    r = {"op": opname, "W": W, "group": G, "block": blk, "scheme": sc, "ms": ms,
+                         "gops": (queries.numel() if opname == "retrieve" else n) / ms / 1e6}
+                    results.append(r)
+                    if report:
+                        report(r)
+        # erase candidates include the insert; the differences are the erase's
+        b = min(results, key=lambda r: r["ms"])
+        api.wc_table_set_launch(h, op, b["group"], b["block"], 0, b["scheme"], 0)
+        best[opname] = {"group": b["group"], "block": b["block"], "scheme": b["scheme"], "ms": b["ms"]}
+        cache[key] = best[opname]
+        if opname == "insert":  # later ops need the table filled with the best insert
+            api.wc_table_clear(h, s)
+            api.wc_insert(h, keys, values, n, s)
+    if use_cache:
+        _save_cache(cache)
+    api.wc_table_clear(h, s)
+    api.wc_insert(h, keys, values, n, s)
+    torch.cuda.synchronize()
+    return best
+
+
+def sample(kb: int, n: int, seed: int = 0x7E57):
+    import wc_inputs
+    from .table import to_device
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if kb == 4:
+        d = wc_inputs.sv_insert_retrieve_u32(seed, n, n // 2, n // 2)
+        return (to_device(d["keys"], 4, dev), to_device(d["values"], 4, dev), to_device(d["queries"], 4, dev))
+    allk = wc_inputs.distinct_u64(seed, n + n // 2)
+    q = np.concatenate([allk[: n // 2], allk[n:]])
+    q = q[wc_inputs.shuffle_index(seed, q.size)]
+    return (to_device(allk[:n], 8, dev), to_device(wc_inputs.uniform_u64(seed, n), 8, dev), to_device(q, 8, dev))
+
+
+def recommend_window(kb: int, vb: int, n: int, alpha: float, reps: int = 3, report=None,
+                     use_cache: bool = True) -> dict:
+    """Best window width for a table of n keys at load alpha: tunes a table for each W
+    and picks the lowest insert + retrieve time.  Returns {"W": ..., "shapes": ...}."""
+    sb = 8 if kb == 4 else 16
+    keys, values, queries = sample(kb, n)
+    choices = []
+    for W in SHAPES[sb]:
+        h = api.wc_table_create(0, kb, vb, int(math.ceil(n / alpha)), W, 0, 0x5EED, torch.cuda.current_device())
+        try:
+            b = tune_table(h, keys, values, queries, reps=reps, report=report, use_cache=use_cache)
+        finally:
+            api.wc_table_destroy(h)
+        choices.append({"W": W, "shapes": b, "ms": b["insert"]["ms"] + b["retrieve"]["ms"]})
+    return min(choices, key=lambda c: c["ms"])
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--key-bytes", type=int, default=4, choices=[4, 8])
+    ap.add_argument("--log2n", type=int, default=27)
+    ap.add_argument("--alpha", type=float, default=0.9)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--no-cache", action="store_true")
+    a = ap.parse_args()
+    best = recommend_window(a.key_bytes, a.key_bytes, 1 << a.log2n, a.alpha, a.reps,
+                            report=lambda r: print(json.dumps(r), flush=True), use_cache=not a.no_cache)
+    print(json.dumps({"choice": best, "key_bytes": a.key_bytes, "n": 1 << a.log2n, "alpha": a.alpha}), flush=True)
+
+
+if __name__ == "__main__":
+    main()
