@@ -72,27 +72,32 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# Sources of the single-value probe kernels (a change to any of them invalidates the
+# committed traffic record of those kernels).
+SV_KERNEL_SOURCES = ("wc_device.cuh", "wc_sv_kernels.cuh", "wc_sv_dispatch.cuh", "wc_partition.cuh",
+                     "wc_launch.cuh", "wc_sv_p32.cu")
+
+
 def source_digest():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2009_07914_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
+    for name in SV_KERNEL_SOURCES:
         with open(os.path.join(d, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel: str, workload: str):
-    """dram bytes per launch of `kernel` from the committed ncu summary, if it was taken
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken
     on the current kernel sources; else None."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
-        with open(path) as f:
-            rows = json.load(f)
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.txt")) as f:
+            lines = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
     except Exception:
         return None
-    for r in rows:
-        if r.get("kernel") == kernel and r.get("workload") == workload and r.get("source") == source_digest():
-            return r.get("dram_bytes_per_launch")
+    for f in lines:
+        if len(f) >= 4 and f[0] == kernel and f[1] == workload and f[2] == source_digest():
+            return int(f[3])
     return None
 
 

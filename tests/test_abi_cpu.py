@@ -30,7 +30,7 @@ def declared_functions():
     return sorted(names)
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_bulk_table_calls():
     names = declared_functions()
     for want in ("wc_table_create", "wc_table_destroy", "wc_insert", "wc_retrieve", "wc_erase",
                  "wc_count_values", "wc_retrieve_multi", "wc_size", "wc_load_factor"):
