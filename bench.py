@@ -209,6 +209,18 @@ def timed(s, f):
     return a.elapsed_time(b)
 
 
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The slowest rank's time: every rank runs its own table (replicas), so the job's
+    time is the maximum (all_reduce MAX; no data-path collective exists)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def emit(res):
     print(json.dumps(res), flush=True)
 
@@ -304,10 +316,7 @@ def run_wc(args, rank, world, local_rank):
     clear_ms = [e[0].elapsed_time(e[1]) for e in evs]
     ins_ms = [e[1].elapsed_time(e[2]) for e in evs]
     ret_ms = [e[2].elapsed_time(e[3]) for e in evs]
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     ms_step = total_ms / args.steps
     value = world * 2 * n / (ms_step * 1e-3) / 1e9
 

@@ -294,8 +294,9 @@ def mv_zipf_u64(seed: int, universe: int, n_inserts: int, n_absent: int, s: floa
     keys = uni[ranks]
     values = np.arange(n_inserts, dtype=np.uint64).astype(np.uint32)
     qk = np.concatenate([uni, absent])
+    src = np.concatenate([np.arange(universe, dtype=np.int64), -np.ones(n_absent, dtype=np.int64)])
     perm = shuffle_index(seed ^ 0x0F0F0F0F0F0F0F0F, qk.size)
-    return dict(keys=keys, values=values, queries=qk[perm], ranks=ranks)
+    return dict(keys=keys, values=values, queries=qk[perm], ranks=ranks, q_src=src[perm])
 
 
 def mv_uniform_r(seed: int, n: int, r: int):
