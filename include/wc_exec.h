@@ -70,6 +70,13 @@ wc_status wc_executor_submit(wc_executor* ex, const wc_work* h_items, uint32_t c
 /* Non-blocking: *h_done = 1 once the batch `ticket` has finished on the device. */
 wc_status wc_executor_query(wc_executor* ex, uint64_t ticket, int32_t* h_done);
 
+/* Non-blocking, no CUDA call: *h_done = 1 once item `index` (its position in the
+ * wc_executor_submit array) of batch `ticket` has finished -- each item reports on its
+ * own through mapped host memory when its last tile is done, so small items of a large
+ * batch complete early.  Device-side results of a finished item are visible to work
+ * ordered after it on the executor's stream. */
+wc_status wc_executor_query_item(wc_executor* ex, uint64_t ticket, uint32_t index, int32_t* h_done);
+
 /* Block until batch `ticket` has finished. */
 wc_status wc_executor_wait(wc_executor* ex, uint64_t ticket);
 

@@ -40,17 +40,20 @@ struct ExecHeader {
   uint64_t total_tiles;
   uint32_t nitems;
   uint32_t ngroups;
+  uint64_t ticket;  // this batch's ticket (completion flags hold ticket + 1)
 };
 
 // Device layout: [header 256 B | group tile counts max*8 | items max*sizeof(ExecItem)]
-//                [next tile 8 | group done counters max*8] [status 4]
+//                [next tile 8 | group done counters max*8 | item done counters max*8]
+//                [status 4]
 struct Layout {
-  size_t hdr = 0, gtiles = 256, items = 0, next = 0, gdone = 0, status = 0, total = 0;
+  size_t hdr = 0, gtiles = 256, items = 0, next = 0, gdone = 0, idone = 0, status = 0, total = 0;
   explicit Layout(uint32_t max) {
     items = gtiles + static_cast<size_t>(max) * 8;
     next = (items + static_cast<size_t>(max) * sizeof(ExecItem) + 255) / 256 * 256;
     gdone = next + 8;
-    status = gdone + static_cast<size_t>(max) * 8;
+    idone = gdone + static_cast<size_t>(max) * 8;
+    status = idone + static_cast<size_t>(max) * 8;
     total = (status + 4 + 255) / 256 * 256;
   }
 };
@@ -96,7 +99,9 @@ __global__ void __launch_bounds__(kExecThreads, 3) k_exec(const ExecHeader* __re
                                                        const unsigned long long* __restrict__ gtiles,
                                                        const ExecItem* __restrict__ items,
                                                        unsigned long long* __restrict__ next_tile,
-                                                       unsigned long long* __restrict__ gdone, uint32_t* xstatus,
+                                                       unsigned long long* __restrict__ gdone,
+                                                       unsigned long long* __restrict__ idone,
+                                                       unsigned long long* item_flags, uint32_t* xstatus,
                                                        uint64_t timeout_ns, uint32_t tile_keys) {
   using L = LayoutP32;
   constexpr int GI = ExecShape<W>::GI, SI = W / GI;
@@ -153,7 +158,16 @@ __global__ void __launch_bounds__(kExecThreads, 3) k_exec(const ExecHeader* __re
     }
     __syncwarp();
     __threadfence();
-    if (lane == 0) atomicAdd(gdone + it.group, 1ull);
+    if (lane == 0) {
+      atomicAdd(gdone + it.group, 1ull);
+      // the warp that finishes an item's last tile reports it to the host (mapped memory)
+      const unsigned long long item_tiles = (it.n + tile_keys - 1) / tile_keys;
+      if (atomicAdd(idone + lo, 1ull) + 1 == item_tiles) {
+        __threadfence_system();
+        const unsigned long long flag = hdr->ticket + 1;
+        asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(item_flags + lo), "l"(flag) : "memory");
+      }
+    }
   }
 }
 
@@ -168,6 +182,9 @@ struct wc_executor {
   Layout lay{1};
   char* d_buf = nullptr;
   char* h_stage[2] = {nullptr, nullptr};
+  unsigned long long* h_flags[2] = {nullptr, nullptr};  // mapped: per item, ticket + 1 once done
+  uint64_t slot_ticket[2] = {~0ull, ~0ull};
+  std::vector<int32_t> item_map[2];  // caller's item index -> kernel item index (-1: n == 0)
   cudaEvent_t stage_ev[2] = {nullptr, nullptr};
   cudaEvent_t ring[kTicketRing] = {};
   uint64_t next_ticket = 0;
@@ -204,6 +221,7 @@ void free_executor(wc_executor* ex) {
   for (int i = 0; i < 2; ++i) {
     if (ex->stage_ev[i]) cudaEventDestroy(ex->stage_ev[i]);
     if (ex->h_stage[i]) cudaFreeHost(ex->h_stage[i]);
+    if (ex->h_flags[i]) cudaFreeHost(ex->h_flags[i]);
   }
   if (ex->d_buf) cudaFree(ex->d_buf);
   delete ex;
@@ -239,7 +257,10 @@ wc_status wc_executor_create(wc_executor** out, const wc_executor_config* cfg) {
             cudaMemset(ex->d_buf, 0, ex->lay.total) == cudaSuccess;
   for (int i = 0; ok && i < 2; ++i) {
     ok = cudaHostAlloc(&ex->h_stage[i], ex->lay.next, cudaHostAllocDefault) == cudaSuccess &&
+         cudaHostAlloc(reinterpret_cast<void**>(&ex->h_flags[i]), static_cast<size_t>(cfg->max_items) * 8,
+                       cudaHostAllocMapped) == cudaSuccess &&
          cudaEventCreateWithFlags(&ex->stage_ev[i], cudaEventDisableTiming) == cudaSuccess;
+    if (ok) std::memset(ex->h_flags[i], 0, static_cast<size_t>(cfg->max_items) * 8);
   }
   for (int i = 0; ok && i < kTicketRing; ++i) ok = cudaEventCreateWithFlags(&ex->ring[i], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
@@ -254,13 +275,16 @@ wc_status wc_executor_create(wc_executor** out, const wc_executor_config* cfg) {
   const auto* items = reinterpret_cast<const ExecItem*>(ex->d_buf + ex->lay.items);
   auto* next = reinterpret_cast<unsigned long long*>(ex->d_buf + ex->lay.next);
   auto* gdone = reinterpret_cast<unsigned long long*>(ex->d_buf + ex->lay.gdone);
+  auto* idone = reinterpret_cast<unsigned long long*>(ex->d_buf + ex->lay.idone);
   auto* xst = reinterpret_cast<uint32_t*>(ex->d_buf + ex->lay.status);
   uint64_t tmo = ex->cfg.timeout_ns;
   uint32_t tkeys = ex->cfg.tile_keys;
-  void* args[] = {&hdr, &gt, &items, &next, &gdone, &xst, &tmo, &tkeys};
   for (int g = 0; ok && g < 2; ++g) {
+    unsigned long long* dflags = nullptr;
+    ok = cudaHostGetDevicePointer(reinterpret_cast<void**>(&dflags), ex->h_flags[g], 0) == cudaSuccess;
+    void* args[] = {&hdr, &gt, &items, &next, &gdone, &idone, &dflags, &xst, &tmo, &tkeys};
     cudaGraphNode_t n_copy = nullptr, n_set = nullptr, n_kernel = nullptr;
-    ok = cudaGraphCreate(&ex->graph[g], 0) == cudaSuccess;
+    ok = ok && cudaGraphCreate(&ex->graph[g], 0) == cudaSuccess;
     if (ok)
       ok = cudaGraphAddMemcpyNode1D(&n_copy, ex->graph[g], nullptr, 0, ex->d_buf, ex->h_stage[g], ex->lay.next,
                                     cudaMemcpyHostToDevice) == cudaSuccess;
@@ -332,9 +356,11 @@ wc_status wc_executor_submit(wc_executor* ex, const wc_work* h_items, uint32_t c
   uint64_t tiles = 0;
   bool stalled = false;
   const uint64_t tk = ex->cfg.tile_keys;
+  ex->item_map[slot].assign(count, -1);
   for (uint32_t i = 0; i < count; ++i) {
     const wc_work& w = h_items[i];
     if (w.n == 0) continue;
+    ex->item_map[slot][i] = static_cast<int32_t>(ni);
     ExecItem& it = items[ni++];
     it.t = desc_of(w.table);
     it.keys = w.d_keys;
@@ -371,10 +397,12 @@ wc_status wc_executor_submit(wc_executor* ex, const wc_work* h_items, uint32_t c
   }
   *h_ticket = ticket;
   ex->last_stream = s;
+  ex->slot_ticket[slot] = ticket;
   if (ni == 0) return cudaEventRecord(ex->ring[ticket % kTicketRing], s) == cudaSuccess ? WC_OK : WC_ERR_CUDA;
   hdr->total_tiles = tiles;
   hdr->nitems = ni;
   hdr->ngroups = ng;
+  hdr->ticket = ticket;
   cudaError_t e = cudaGraphLaunch(ex->exec[slot], s);
   if (e == cudaSuccess) e = cudaEventRecord(ex->stage_ev[slot], s);
   if (e == cudaSuccess) e = cudaEventRecord(ex->ring[ticket % kTicketRing], s);
@@ -399,6 +427,24 @@ wc_status wc_executor_query(wc_executor* ex, uint64_t ticket, int32_t* h_done) {
     return WC_OK;
   }
   return WC_ERR_CUDA;
+}
+
+wc_status wc_executor_query_item(wc_executor* ex, uint64_t ticket, uint32_t index, int32_t* h_done) {
+  if (ex == nullptr || h_done == nullptr || ticket >= ex->next_ticket) return WC_ERR_INVALID_ARG;
+  const int slot = static_cast<int>(ticket & 1);
+  if (ex->slot_ticket[slot] != ticket) {
+    *h_done = 1;  // the slot was reused, which waits for this batch to finish
+    return WC_OK;
+  }
+  if (index >= ex->item_map[slot].size()) return WC_ERR_INVALID_ARG;
+  const int32_t k = ex->item_map[slot][index];
+  if (k < 0) {
+    *h_done = 1;
+    return WC_OK;
+  }
+  const volatile unsigned long long* f = ex->h_flags[slot];
+  *h_done = f[k] == ticket + 1 ? 1 : 0;
+  return WC_OK;
 }
 
 wc_status wc_executor_wait(wc_executor* ex, uint64_t ticket) {

@@ -17,9 +17,10 @@
 namespace {
 
 struct Launch {
-  uint64_t ticket = 0;       // batched mode
-  cudaEvent_t ev = nullptr;  // per-call mode
+  uint64_t ticket = 0;       // batched launch
+  cudaEvent_t ev = nullptr;  // per-call launch
   std::vector<uint32_t> reqs;
+  size_t left = 0;           // requests not finished yet
 };
 
 wc_status launch_one(const wc_work& w, void* stream) {
@@ -67,10 +68,20 @@ extern "C" wc_status wc_serve_run(wc_executor* ex, const wc_request* reqs, uint3
   uint32_t pool_next = 0;
   std::vector<wc_work> batch;
   batch.reserve(cfg->max_batch_items);
+  std::vector<uint8_t> finished(nreq, 0);
+  bool progress = false;
+  auto finish = [&](uint32_t r, uint64_t t) {
+    if (finished[r]) return;
+    finished[r] = 1;
+    timing[r].completed_ns = t;
+    admitted_bytes -= reqs[r].io_bytes;
+    ++completed;
+    progress = true;
+  };
   wc_status st = WC_OK;
 
   while (completed < nreq && st == WC_OK) {
-    bool progress = false;
+    progress = false;
     uint64_t now = now_ns();
     while (next_arrival < nreq && reqs[next_arrival].arrival_ns <= now) waiting.push_back(next_arrival++);
     // admission in arrival order within the HBM budget
@@ -85,33 +96,43 @@ extern "C" wc_status wc_serve_run(wc_executor* ex, const wc_request* reqs, uint3
       waiting.pop_front();
       progress = true;
     }
-    // completions
-    while (!inflight.empty()) {
-      Launch& f = inflight.front();
-      int32_t done = 0;
-      if (f.ev == nullptr) {
-        st = wc_executor_query(ex, f.ticket, &done);
-        if (st != WC_OK) break;
-      } else {
+    // completions: a per-call launch finishes as a whole; a batched request finishes when
+    // its own item does (reported by the executor through mapped memory)
+    for (auto it = inflight.begin(); it != inflight.end() && st == WC_OK;) {
+      Launch& f = *it;
+      const uint64_t t = now_ns();
+      if (f.ev != nullptr) {
         const cudaError_t e = cudaEventQuery(f.ev);
-        if (e == cudaSuccess) {
-          done = 1;
-        } else if (e == cudaErrorNotReady) {
+        if (e == cudaErrorNotReady) {
           cudaGetLastError();
-        } else {
+          ++it;
+          continue;
+        }
+        if (e != cudaSuccess) {
           st = WC_ERR_CUDA;
           break;
         }
+        for (uint32_t r : f.reqs) finish(r, t);
+        f.left = 0;
+      } else {
+        for (uint32_t j = 0; j < f.reqs.size(); ++j) {
+          const uint32_t r = f.reqs[j];
+          if (finished[r]) continue;
+          int32_t done = 0;
+          st = wc_executor_query_item(ex, f.ticket, j, &done);
+          if (st != WC_OK) break;
+          if (done) {
+            finish(r, t);
+            --f.left;
+          }
+        }
       }
-      if (!done) break;
-      const uint64_t t = now_ns();
-      for (uint32_t r : f.reqs) {
-        timing[r].completed_ns = t;
-        admitted_bytes -= reqs[r].io_bytes;
-        ++completed;
+      if (f.left == 0) {
+        it = inflight.erase(it);
+        progress = true;
+      } else {
+        ++it;
       }
-      inflight.pop_front();
-      progress = true;
     }
     // launches: while a slot is free, pack the admitted requests (continuous batching)
     while (st == WC_OK && !ready.empty() && inflight.size() < cfg->max_inflight) {
@@ -146,6 +167,7 @@ extern "C" wc_status wc_serve_run(wc_executor* ex, const wc_request* reqs, uint3
         timing[r].batch = static_cast<uint32_t>(launches);
       }
       ++launches;
+      l.left = l.reqs.size();
       inflight.push_back(std::move(l));
       progress = true;
     }

@@ -53,6 +53,7 @@ B.extra_signatures({
     "wc_executor_submit": (ctypes.c_int, [_vp, ctypes.POINTER(WcWork), _u32, _vp, ctypes.POINTER(_u64)]),
     "wc_executor_query": (ctypes.c_int, [_vp, _u64, ctypes.POINTER(_i32)]),
     "wc_executor_wait": (ctypes.c_int, [_vp, _u64]),
+    "wc_executor_query_item": (ctypes.c_int, [_vp, _u64, _u32, ctypes.POINTER(_i32)]),
     "wc_executor_get_status": (ctypes.c_int, [_vp, ctypes.POINTER(_u32), _i32]),
     "wc_serve_run": (ctypes.c_int, [_vp, ctypes.POINTER(WcRequest), _u32, ctypes.POINTER(WcServeConfig), _vp,
                                     ctypes.POINTER(WcRequestTiming), ctypes.POINTER(WcServeStats)]),
@@ -90,6 +91,12 @@ def wc_executor_submit(ex: int, items: list[WcWork], stream=None) -> int:
 def wc_executor_query(ex: int, ticket: int) -> bool:
     d = ctypes.c_int32()
     B.check(B.lib().wc_executor_query(ex, ticket, ctypes.byref(d)), "wc_executor_query")
+    return bool(d.value)
+
+
+def wc_executor_query_item(ex: int, ticket: int, index: int) -> bool:
+    d = ctypes.c_int32()
+    B.check(B.lib().wc_executor_query_item(ex, ticket, index, ctypes.byref(d)), "wc_executor_query_item")
     return bool(d.value)
 
 

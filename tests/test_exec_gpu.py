@@ -58,6 +58,8 @@ def test_executor_matches_oracle_in_submission_order(env, W):
     tickets = [serve.wc_executor_submit(ex, works[i:i + 17]) for i in range(0, len(works), 17)]
     serve.wc_executor_wait(ex, tickets[-1])
     assert all(serve.wc_executor_query(ex, t) for t in tickets)
+    last = works[(len(tickets) - 1) * 17:]
+    assert all(serve.wc_executor_query_item(ex, tickets[-1], j) for j in range(len(last)))
     assert serve.wc_executor_get_status(ex) == 0
     expect = _oracle_apply(_oracles(tr), tr)
     for got, exp in zip(dt.retrieve_results(), expect):
