@@ -1,6 +1,9 @@
 // Multi-value bulk insert: dispatch of the count / allocate / scatter passes.
+#include <algorithm>
+
 #include "wc_launch.cuh"
 #include "wc_mv_kernels.cuh"
+#include "wc_partition.cuh"
 
 namespace wc {
 
@@ -8,6 +11,7 @@ namespace {
 
 template <class KIn, int VB, int W>
 cudaError_t insert_passes(const wc_table* t, const void* keys, const void* vals, uint64_t n, cudaStream_t s) {
+  using V = typename PoolT<VB>::T;
   const TableDesc d = desc_of(t);
   const PoolDesc pd = pool_of(t);
   const KIn* k = static_cast<const KIn*>(keys);
@@ -19,20 +23,67 @@ cudaError_t insert_passes(const wc_table* t, const void* keys, const void* vals,
     cudaFuncSetAttribute(scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(agg_smem_bytes(true)));
     attr_done = true;
   }
+  // Large batches into a key store larger than L2 are first split by key-store region
+  // (the region split of the single-value insert): the passes then probe one L2-resident
+  // region of the key store at a time, and pass 3 writes one range of the pool at a time
+  // (pass 2 lays buckets out in key-store order).
+  unsigned long long* counters = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (n >= (1ull << 20) && t->table_bytes > (64ull << 20)) {
+    RegionMap m;
+    m.seed = t->cfg.seed;
+    m.p = static_cast<uint32_t>(t->windows);
+    uint64_t wpr = std::max<uint64_t>(1, (32ull << 20) / (t->W * t->slot_bytes));
+    if ((t->windows + wpr - 1) / wpr > static_cast<uint64_t>(kMaxRegions)) wpr = (t->windows + kMaxRegions - 1) / kMaxRegions;
+    m.wpr = static_cast<uint32_t>(wpr);
+    m.R = static_cast<uint32_t>((t->windows + wpr - 1) / wpr);
+    const uint64_t cur_off = 8192, cnt_off = cur_off + 8192, keys_off = cnt_off + 256;
+    const uint64_t vals_off = keys_off + (n * sizeof(KIn) + 255) / 256 * 256;
+    e = ensure_scratch(t, vals_off + n * sizeof(V), s);
+    if (e != cudaSuccess) return e;
+    char* sc = static_cast<char*>(t->d_scratch);
+    auto* hist = reinterpret_cast<unsigned int*>(sc);
+    auto* cursor = reinterpret_cast<unsigned long long*>(sc + cur_off);
+    counters = reinterpret_cast<unsigned long long*>(sc + cnt_off);
+    KIn* pk = reinterpret_cast<KIn*>(sc + keys_off);
+    V* pv = reinterpret_cast<V*>(sc + vals_off);
+    e = cudaMemsetAsync(sc, 0, keys_off, s);
+    if (e != cudaSuccess) return e;
+    auto hk = k_part_hist<KIn>;
+    auto sk = k_part_scatter<KIn, V>;
+    const size_t hsm = static_cast<size_t>(kHistWarps) * m.R * sizeof(unsigned int);
+    const size_t ssm = scatter_smem_bytes<KIn, V>();
+    static bool pattr = false;
+    if (!pattr) {
+      cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kHistWarps * kMaxRegions * 4));
+      cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(ssm));
+      pattr = true;
+    }
+    const uint64_t pt = (n + kPartTile - 1) / kPartTile;
+    const unsigned hg = static_cast<unsigned>(std::min<uint64_t>(
+        (n + kPartThreads - 1) / kPartThreads, static_cast<uint64_t>(occupancy_smem(hk, kPartThreads, hsm)) * t->sm_count));
+    const unsigned sg = static_cast<unsigned>(
+        std::min<uint64_t>(pt, static_cast<uint64_t>(occupancy_smem(sk, kPartThreads, ssm)) * t->sm_count));
+    hk<<<hg, kPartThreads, hsm, s>>>(k, n, m, hist);
+    sk<<<sg, kPartThreads, ssm, s>>>(k, static_cast<const V*>(vals), n, m, hist, cursor, pk, pv);
+    k = pk;
+    vals = pv;
+  }
   const uint64_t ntiles = (n + kAggTile - 1) / kAggTile;
   const int bps_c = occupancy_smem(count, kAggThreads, agg_smem_bytes(false));
   const int bps_s = occupancy_smem(scatter, kAggThreads, agg_smem_bytes(true));
   const unsigned g_c = static_cast<unsigned>(std::min<uint64_t>(ntiles, static_cast<uint64_t>(bps_c) * t->sm_count));
   const unsigned g_s = static_cast<unsigned>(std::min<uint64_t>(ntiles, static_cast<uint64_t>(bps_s) * t->sm_count));
-  cudaError_t e = cudaMemsetAsync(pd.pending, 0, t->capacity * sizeof(uint32_t), s);
+  e = cudaMemsetAsync(pd.pending, 0, t->capacity * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  e = launch_k(t, count, g_c, kAggThreads, agg_smem_bytes(false), s, d, pd, k, vals, n);
+  e = launch_k(t, count, g_c, kAggThreads, agg_smem_bytes(false), s, d, pd, k, vals, n, counters);
   if (e != cudaSuccess) return e;
   const uint64_t per_block = static_cast<uint64_t>(kAllocThreads) * kAllocItems;
   const unsigned g_a = static_cast<unsigned>((t->capacity + per_block - 1) / per_block);
   e = launch_k(t, k_mv_alloc<VB>, g_a, kAllocThreads, 0, s, d, pd, t->capacity);
   if (e != cudaSuccess) return e;
-  return launch_k(t, scatter, g_s, kAggThreads, agg_smem_bytes(true), s, d, pd, k, vals, n);
+  return launch_k(t, scatter, g_s, kAggThreads, agg_smem_bytes(true), s, d, pd, k, vals, n,
+                  counters ? counters + 1 : counters);
 }
 
 template <class KIn, int VB>

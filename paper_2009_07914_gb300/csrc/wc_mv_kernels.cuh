@@ -161,8 +161,12 @@ constexpr size_t agg_smem_bytes(bool scatter) {
 }
 
 template <class KIn, int VB, int W, bool kScatter>
+// tile_counter != nullptr: blocks take tiles in increasing order from it (the batch is
+// sorted by key-store region, so the active tiles touch one region of the key store and
+// one range of the value pool at a time); otherwise tiles are strided over the grid.
 __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolDesc pd, const KIn* __restrict__ keys,
-                                                              const void* __restrict__ vals, uint64_t n) {
+                                                              const void* __restrict__ vals, uint64_t n,
+                                                              unsigned long long* tile_counter) {
   using V = typename PoolT<VB>::T;
   extern __shared__ unsigned long long agg_smem[];  // agg_smem_bytes(kScatter) bytes
   unsigned long long* s_key = agg_smem;
@@ -172,7 +176,14 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
   const uint64_t ntiles = (n + kAggTile - 1) / kAggTile;
   uint32_t flags = 0;
   long long created = 0;
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  __shared__ unsigned long long s_tile;
+  uint64_t tile = blockIdx.x;
+  if (tile_counter != nullptr) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1ull);
+    __syncthreads();
+    tile = s_tile;
+  }
+  while (tile < ntiles) {
     for (int e = threadIdx.x; e < kAggSlots; e += kAggThreads) {
       s_key[e] = 0ull;
       s_cnt[e] = 0u;
@@ -242,6 +253,13 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
       }
     }
     __syncthreads();
+    if (tile_counter != nullptr) {
+      if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1ull);
+      __syncthreads();
+      tile = s_tile;
+    } else {
+      tile += gridDim.x;
+    }
   }
   flush_flags(t.status, flags);
   if constexpr (!kScatter) flush_delta(t.nkeys, created);

@@ -14,8 +14,8 @@
 
 namespace wc {
 
-constexpr int kPartThreads = 256;
-constexpr int kPartItems = 16;
+constexpr int kPartThreads = 512;
+constexpr int kPartItems = 8;
 constexpr int kPartTile = kPartThreads * kPartItems;
 constexpr int kMaxRegions = 1024;
 

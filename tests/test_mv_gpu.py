@@ -159,3 +159,20 @@ def test_mv_u32_keys_full_mix(wc):
     o.insert(keys32, d["values"])
     check_queries(t, o, q32)
     assert t.size() == o.size()
+
+
+def test_mv_region_split_insert_parity(wc):
+    """A key store above 64 MiB and a batch of >= 2^20 pairs take the region-split insert;
+    counts and value multisets still equal the oracle's, also on a repeat insert."""
+    uni, n = 1 << 22, 1 << 21
+    d = wc_inputs.mv_zipf_u64(0x5B117, uni, n, 1 << 16)
+    t = make_mv(wc, 8, 4, 5_000_000, 2 * n + 4 * uni)
+    assert t.info["table_bytes"] > (64 << 20)
+    o = oracle.MultiValue(8, 4)
+    for rep in range(2):
+        t.insert(d["keys"], d["values"])
+        o.insert(d["keys"], d["values"])
+        assert t.size() == o.size() == (rep + 1) * n
+        assert t.num_keys() == o.num_keys()
+    q = d["queries"][wc_inputs.shuffle_index(3, d["queries"].size)[:200_000]]
+    check_queries(t, o, q)
