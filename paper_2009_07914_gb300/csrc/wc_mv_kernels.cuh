@@ -60,58 +60,6 @@ struct PoolT<8> {
 
 // ---- key store probes by one thread (W slots per window) ------------------------------
 
-// Find the key's slot, inserting it with an empty handle if absent.  Same candidate
-// rule as the single-value insert (earliest empty or tombstoned slot, probing past
-// tombstones to the first window holding an empty slot or the key).  Returns the slot
-// index, or -1 when every window was visited without a candidate.
-template <int W>
-__device__ int64_t ks_find_or_insert(const TableDesc& t, uint64_t k, bool& created) {
-  KsSlot* slots = static_cast<KsSlot*>(t.slots);
-  uint32_t w, step;
-  probe_init(k, t.seed, t.p, w, step);
-  bool have_t = false;
-  uint64_t t_slot = 0;
-  KsSlot t_word{};
-  uint32_t j = 0;
-  created = false;
-  while (true) {
-    KsSlot s[W];
-    const uint64_t base = static_cast<uint64_t>(w) * W;
-    load_slots<KsL, W>(slots + base, s);
-    uint32_t mm, me, mt;
-    classify<KsL, W>(s, k, mm, me, mt);
-    if (mm) return static_cast<int64_t>(base + __ffs(mm) - 1);
-    const bool last = j + 1 >= t.p;
-    if (me || last) {
-      if (have_t) {
-        if (KsL::cas(slots + t_slot, t_word, KsL::make(k, 0))) {
-          created = true;
-          return static_cast<int64_t>(t_slot);
-        }
-        have_t = false;  // the tombstone was taken: start over
-        j = 0;
-        probe_init(k, t.seed, t.p, w, step);
-        continue;
-      }
-      const uint32_t mc = me | mt;
-      if (mc == 0) return -1;
-      const int sub = __ffs(mc) - 1;
-      if (KsL::cas(slots + base + sub, pick<KsL, W>(s, sub), KsL::make(k, 0))) {
-        created = true;
-        return static_cast<int64_t>(base + sub);
-      }
-      continue;  // lost the slot to another key (or to this key): read the window again
-    }
-    if (mt && !have_t) {
-      have_t = true;
-      t_slot = base + __ffs(mt) - 1;
-      t_word = pick<KsL, W>(s, __ffs(mt) - 1);
-    }
-    ++j;
-    w = probe_next(w, step, t.p);
-  }
-}
-
 // Find the key; returns its slot index and handle, or -1 if absent (Sec. IV-B4 early
 // exit at the first window holding an empty slot).
 template <int W>
@@ -157,7 +105,136 @@ __device__ __forceinline__ int smem_find_or_insert(unsigned long long* s_key, un
 }
 
 constexpr size_t agg_smem_bytes(bool scatter) {
-  return (scatter ? 2 : 1) * kAggSlots * sizeof(unsigned long long) + kAggSlots * sizeof(uint32_t);
+  return (scatter ? 2 : 1) * kAggSlots * sizeof(unsigned long long) + kAggSlots * sizeof(uint32_t) +
+         kAggSlots * sizeof(unsigned short);
+}
+
+// Exclusive block scan of one uint32 per thread; total gets the sum.
+template <int kThreads>
+__device__ __forceinline__ uint32_t block_exclusive_u32(uint32_t x, uint32_t& total, uint32_t* s_w) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_w[warp] = inc;
+  __syncthreads();
+  uint32_t before = 0;
+  total = 0;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) {
+    if (w < warp) before += s_w[w];
+    total += s_w[w];
+  }
+  __syncthreads();
+  return before + inc - x;
+}
+
+// The global phase of one tile: every distinct key of the tile (s_list[0..len)) is found
+// in -- or, in the counting pass, inserted into -- the key store with one lane per key.
+// The loop is warp-uniform: each trip loads one window for every lane holding a key,
+// so a warp's window loads are in flight together, and a lane that finishes takes the
+// next key of the list.  Counting pass: pending[slot] += the key's tile count.  Scatter
+// pass: reserve the key's run in its bucket (s_base[e] = first pool index, or all ones).
+template <int W, bool kScatter, int VB>
+__device__ __forceinline__ void ks_global_phase(const TableDesc& t, const PoolDesc& pd,
+                                                const unsigned long long* s_key, const uint32_t* s_cnt,
+                                                unsigned long long* s_base, const unsigned short* s_list,
+                                                uint32_t len, uint32_t* s_next, uint32_t& flags,
+                                                long long& created) {
+  KsSlot* slots = static_cast<KsSlot*>(t.slots);
+  const int lane = threadIdx.x & 31;
+  bool act = false, more = true;
+  uint32_t e = 0, w = 0, step = 0, j = 0;
+  unsigned long long k = 0;
+  bool have_t = false;
+  uint64_t t_slot = 0;
+  KsSlot t_word{};
+  while (true) {
+    const uint32_t idle = __ballot_sync(kFull, !act);
+    if (idle && more) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(s_next, static_cast<uint32_t>(__popc(idle)));
+      base = __shfl_sync(kFull, base, 0);
+      const uint32_t mine = base + __popc(idle & ((1u << lane) - 1u));
+      if (!act && mine < len) {
+        e = s_list[mine];
+        k = s_key[e];
+        act = true;
+        j = 0;
+        have_t = false;
+        probe_init(k, t.seed, t.p, w, step);
+      }
+      more = base + __popc(idle) < len;
+    }
+    if (__ballot_sync(kFull, act) == 0) {
+      if (!more) break;
+      continue;
+    }
+    if (act) {
+      KsSlot sl[W];
+      const uint64_t b = static_cast<uint64_t>(w) * W;
+      load_slots<KsL, W>(slots + b, sl);
+      uint32_t mm, me, mt;
+      classify<KsL, W>(sl, k, mm, me, mt);
+      int64_t slot = -1;
+      uint64_t handle = 0;
+      if (mm) {
+        slot = static_cast<int64_t>(b + __ffs(mm) - 1);
+        handle = pick<KsL, W>(sl, __ffs(mm) - 1).v;
+      } else if constexpr (!kScatter) {
+        const bool last = j + 1 >= t.p;
+        if (me || last) {
+          if (have_t) {
+            if (KsL::cas(slots + t_slot, t_word, KsL::make(k, 0))) {
+              slot = static_cast<int64_t>(t_slot);
+              ++created;
+            } else {
+              have_t = false;  // the tombstone was taken: probe again from the start
+              j = 0;
+              probe_init(k, t.seed, t.p, w, step);
+            }
+          } else if (me | mt) {
+            const int sub = __ffs(me | mt) - 1;
+            if (KsL::cas(slots + b + sub, pick<KsL, W>(sl, sub), KsL::make(k, 0))) {
+              slot = static_cast<int64_t>(b + sub);
+              ++created;
+            }
+            // else: the slot was taken; read the window again
+          } else {
+            flags |= kFlagProbeLimit;
+            act = false;
+          }
+        } else {
+          if (mt && !have_t) {
+            have_t = true;
+            t_slot = b + __ffs(mt) - 1;
+            t_word = pick<KsL, W>(sl, __ffs(mt) - 1);
+          }
+          ++j;
+          w = probe_next(w, step, t.p);
+        }
+      } else {
+        if (me || ++j >= t.p) {
+          s_base[e] = ~0ull;  // absent: the counting pass could not store it
+          act = false;
+        } else {
+          w = probe_next(w, step, t.p);
+        }
+      }
+      if (slot >= 0) {
+        if constexpr (!kScatter) {
+          atomicAdd(pd.pending + slot, s_cnt[e]);
+        } else {
+          const uint32_t old = atomicAdd(pd.pending + slot, s_cnt[e]);
+          s_base[e] = (old & kPoison) ? ~0ull : h_offset(handle) + (h_prev(handle) ? Hdr<VB>::kElems : 0) + old;
+        }
+        act = false;
+      }
+    }
+  }
 }
 
 template <class KIn, int VB, int W, bool kScatter>
@@ -172,6 +249,9 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
   unsigned long long* s_key = agg_smem;
   unsigned long long* s_base = agg_smem + kAggSlots;
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(agg_smem + (kScatter ? 2 : 1) * kAggSlots);
+  unsigned short* s_list = reinterpret_cast<unsigned short*>(s_cnt + kAggSlots);
+  __shared__ uint32_t s_wsum[kAggThreads / 32];
+  __shared__ uint32_t s_len, s_next;
   const int lane = threadIdx.x & 31;
   const uint64_t ntiles = (n + kAggTile - 1) / kAggTile;
   uint32_t flags = 0;
@@ -217,29 +297,25 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
       my_rank[k] = base + __popc(peers & ((1u << lane) - 1u));
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kAggSlots; e += kAggThreads) {
-      const unsigned long long key = s_key[e];
-      if (key == 0ull) continue;
-      if constexpr (!kScatter) {
-        bool made = false;
-        const int64_t gs = ks_find_or_insert<W>(t, key, made);
-        if (gs < 0) {
-          flags |= kFlagProbeLimit;
-          continue;
-        }
-        created += made ? 1 : 0;
-        atomicAdd(pd.pending + gs, s_cnt[e]);
-      } else {
-        uint64_t h = 0;
-        const int64_t gs = ks_find<W>(t, key, h);
-        unsigned long long b = ~0ull;
-        if (gs >= 0) {
-          const uint32_t old = atomicAdd(pd.pending + gs, s_cnt[e]);
-          if (!(old & kPoison)) b = h_offset(h) + (h_prev(h) ? Hdr<VB>::kElems : 0) + old;
-        }
-        s_base[e] = b;
+    // compact the tile's distinct keys into a list, then probe them warp-uniformly
+    {
+      constexpr int kPer = kAggSlots / kAggThreads;
+      const int e0 = threadIdx.x * kPer;
+      uint32_t c = 0;
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) c += s_key[e0 + i] != 0ull;
+      uint32_t total = 0;
+      uint32_t pos = block_exclusive_u32<kAggThreads>(c, total, s_wsum);
+#pragma unroll
+      for (int i = 0; i < kPer; ++i)
+        if (s_key[e0 + i] != 0ull) s_list[pos++] = static_cast<unsigned short>(e0 + i);
+      if (threadIdx.x == 0) {
+        s_len = total;
+        s_next = 0;
       }
+      __syncthreads();
     }
+    ks_global_phase<W, kScatter, VB>(t, pd, s_key, s_cnt, s_base, s_list, s_len, &s_next, flags, created);
     if constexpr (kScatter) {
       __syncthreads();
       V* pool = static_cast<V*>(pd.pool);
