@@ -495,7 +495,8 @@ def run_mv_zipf(args, dev):
     import torch
     from paper_2009_07914_gb300 import api
     from paper_2009_07914_gb300.table import to_device
-    uni, n, na = 1 << 24, 1 << 28, 1 << 22
+    log2n = 28 if args.log2n == 27 else args.log2n  # default: 2^28 inserts over 2^24 keys
+    uni, n, na = 1 << (log2n - 4), 1 << log2n, 1 << (log2n - 6)
     d = wc_inputs.mv_zipf_u64(0x57C00004, uni, n, na)
     keys = to_device(d["keys"], 8, dev)
     vals = to_device(d["values"], 4, dev)
@@ -523,7 +524,8 @@ def run_mv_zipf(args, dev):
             step(True)
     ins, cnt, ret = (statistics.median(e[i] for e in ev) for i in range(3))
     total = ins + cnt + ret
-    _common(args, "mv_u64u32_n2^28_zipf1.1_over2^24", "G ops/s (inserts + queries + values retrieved)",
+    _common(args, "mv_u64u32_n2^%d_zipf1.1_over2^%d" % (log2n, log2n - 4),
+            "G ops/s (inserts + queries + values retrieved)",
             (n + nq + n) / (total * 1e-3) / 1e9, "G ops/s", total, "u64/u32",
             {"n_inserts": n, "universe": uni, "queries": nq, "key_store_capacity": info["capacity"],
              "pool": info["pool_capacity"], "l2": "no flush: 2 GB of inserts, 1 GB pool"}, clk,
