@@ -54,12 +54,15 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access roofline probe")
     ap.add_argument("--workload", default="sv32",
-                    choices=["sv32", "sv32_small", "sv64_zipf", "mv_zipf", "served"],
+                    choices=["sv32", "sv32_small", "sv64_zipf", "mv_zipf", "mv_oa_uniform_r", "served"],
                     help="sv32 (default): 2^27 uint32 pairs at load 0.9, insert + 50%% absent retrieve; "
                          "sv32_small: 2^20 pairs at 0.8 with erase; sv64_zipf: 2^28 uint64 pairs, Zipf queries; "
                          "mv_zipf: multi-value 2^28 Zipf inserts, count + CSR retrieve; "
+                         "mv_oa_uniform_r: open-addressing multi-value, 2^28 uint32 pairs with keys uniform "
+                         "over 1..n/r at load 0.8, queries 1..n; "
                          "served: 64 tables, Poisson requests, batched vs per-call")
     ap.add_argument("--requests", type=int, default=512, help="served: number of requests")
+    ap.add_argument("--r", default="1,4,16,64", help="mv_oa_uniform_r: average copies per key, comma-separated")
     return ap.parse_args()
 
 
@@ -535,6 +538,66 @@ def run_mv_zipf(args, dev):
     api.wc_table_destroy(h)
 
 
+def run_mv_oa_uniform_r(args, dev):
+    """Open-addressing multi-value table (one slot per pair) on the Sec. V-C workload: n
+    uint32 keys drawn uniformly from 1..n/r (value = insert index) inserted at target
+    load 0.8, then count_values + retrieve_multi for all of 1..n, so exactly n values come
+    back.  One step = clear + insert + count + retrieve, for every r of --r."""
+    import torch
+    from paper_2009_07914_gb300 import api
+    from paper_2009_07914_gb300.table import to_device
+    log2n = 28 if args.log2n == 27 else args.log2n
+    n = 1 << log2n
+    rs = [int(x) for x in args.r.split(",")]
+    q = to_device(np.arange(1, n + 1, dtype=np.uint32), 4, dev)
+    vals = to_device(np.arange(n, dtype=np.uint32), 4, dev)
+    offs = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    s = torch.cuda.current_stream()
+    h = api.wc_table_create(2, 4, 4, int(np.ceil(n / 0.8)), args.window, 0, 0x5EEDC0DE, dev.index)
+    from paper_2009_07914_gb300 import WC_OP_COUNT, WC_OP_INSERT, WC_OP_RETRIEVE
+    if args.group:
+        for op in (WC_OP_INSERT, WC_OP_RETRIEVE, WC_OP_COUNT):
+            api.wc_table_set_launch(h, op, args.group, 256, 0, 0, 0)
+    info = api.wc_table_get_info(h)
+    keys = {}
+    for r in rs:
+        kk = wc_inputs.mv_uniform_r(0x57C00005 + r, n, r)["keys"].astype(np.uint32)
+        keys[r] = to_device(kk, 4, dev)
+    ev = {r: [] for r in rs}
+
+    def step(rec):
+        for r in rs:
+            api.wc_table_clear(h, s)
+            t0 = timed(s, lambda: api.wc_insert(h, keys[r], vals, n, s))
+            t1 = timed(s, lambda: api.wc_count_values(h, q, offs, n, want_total=False, stream=s))
+            t2 = timed(s, lambda: api.wc_retrieve_multi(h, q, offs, out, n, s))
+            if rec:
+                ev[r].append((t0, t1, t2))
+    for _ in range(args.warmup):
+        step(False)
+    assert api.wc_size(h) == n and int(offs[-1].item()) == n and api.wc_get_status(h, True) == 0
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.steps):
+            step(True)
+    per_r, total = {}, 0.0
+    for r in rs:
+        ins, cnt, ret = (statistics.median(e[i] for e in ev[r]) for i in range(3))
+        total += ins + cnt + ret
+        per_r[str(r)] = {"insert_gops": n / ins / 1e6, "retrieve_gqps": n / (cnt + ret) / 1e6,
+                         "count_gqps": n / cnt / 1e6, "insert_ms": ins, "count_ms": cnt, "retrieve_multi_ms": ret}
+    _common(args, "mv_oa_u32_n2^%d_uniform_r%s_alpha0.80" % (log2n, "-".join(map(str, rs))),
+            "G ops/s (inserts + queries, over every r)", 2 * n * len(rs) / (total * 1e-3) / 1e9, "G ops/s", total,
+            "u32", {"n": n, "r": rs, "capacity": info["capacity"], "table_bytes": info["table_bytes"],
+                    "window_slots": info["window_width"],
+                    "groups": {op: api.wc_table_get_launch(h, c)["group_size"] for op, c in
+                               (("insert", WC_OP_INSERT), ("count", WC_OP_COUNT),
+                                ("retrieve_multi", WC_OP_RETRIEVE))},
+                    "l2": "no flush: 2.7 GB table, 1 GB inputs"}, clk, 5 * len(rs) * args.steps,
+            {"per_r": per_r})
+    api.wc_table_destroy(h)
+
+
 def run_served(args, dev):
     """64 uint32 tables (capacity 2^U(16,26), pre-filled to load U(0,0.6)); Poisson
     requests with batch sizes 2^U(log2 1000, 24), 60/35/5 insert/retrieve/erase.  Each
@@ -588,7 +651,7 @@ def run_workload(args, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     {"sv32_small": run_sv32_small, "sv64_zipf": run_sv64_zipf, "mv_zipf": run_mv_zipf,
-     "served": run_served}[args.workload](args, dev)
+     "mv_oa_uniform_r": run_mv_oa_uniform_r, "served": run_served}[args.workload](args, dev)
 
 
 

@@ -58,26 +58,38 @@ enum {
   WC_FLAG_QUEUE_TIMEOUT = 32  /* the batched executor gave up waiting (bounded wait) */
 };
 
-enum { WC_SINGLE_VALUE = 0, WC_MULTI_VALUE = 1 };
+/* Table kinds.
+ *   WC_SINGLE_VALUE     one value per key (Sec. IV-B3).
+ *   WC_MULTI_VALUE      many values per key: keys stored once in a key store, values in
+ *                       per-key buckets of a value pool (Sec. IV-C, the bucket-list table).
+ *   WC_MULTI_VALUE_OA   many values per key, open addressing: every pair takes its own
+ *                       slot of the single-value slot layouts along the key's probing
+ *                       sequence (Sec. IV and Sec. V-C, the multi-value hash table).  Insert
+ *                       appends; count_values / retrieve_multi walk the sequence up to the
+ *                       first window holding an empty slot and count or copy every match;
+ *                       erase tombstones every copy.  wc_retrieve is not available. */
+enum { WC_SINGLE_VALUE = 0, WC_MULTI_VALUE = 1, WC_MULTI_VALUE_OA = 2 };
 
 /* Table configuration.
- *   kind                 WC_SINGLE_VALUE or WC_MULTI_VALUE.
- *   key_bytes/value_bytes  single-value: 4/4 (key and value packed in one 64-bit slot
- *                        word, claimed by one 64-bit CAS, Sec. IV-B1) or 8/8 (one 16-byte
- *                        slot claimed by one 128-bit CAS).  multi-value: key 4 or 8,
+ *   kind                 WC_SINGLE_VALUE, WC_MULTI_VALUE or WC_MULTI_VALUE_OA.
+ *   key_bytes/value_bytes  single-value and open-addressing multi-value: 4/4 (key and
+ *                        value packed in one 64-bit slot word, claimed by one 64-bit CAS,
+ *                        Sec. IV-B1) or 8/8 (one 16-byte slot claimed by one 128-bit CAS).
+ *                        bucket multi-value: key 4 or 8,
  *                        value 4 or 8 (keys are stored once in a 16-byte key-store slot
  *                        next to a handle to their values, Sec. IV-C).
  *   window_width         slots per probing window W (the inner linear-probing window of
  *                        the cooperative probing scheme, Sec. IV-B2).  Windows are
  *                        aligned to W slots.  0 = the library default for the widths.
- *                        Allowed: 4, 8, 16, 32 (8-byte slots); 2, 4, 8, 16 (16-byte slots).
+ *                        Allowed: 4, 8, 16, 32 (8-byte slots); 2, 4, 8, 16 (16-byte slots);
+ *                        2, 4, 8 (bucket multi-value key store).
  *   min_capacity         requested slots (key-store slots for multi-value).  The table
  *                        holds capacity = p * W slots with p the smallest prime
  *                        >= ceil(min_capacity / W), so the outer double-hashing sequence
  *                        over the p windows visits every window once (Sec. IV-B2).
  *                        p must stay below 2^32.
- *   value_pool_capacity  multi-value only: value elements in the pool (headers of
- *                        repeat-insert segments included); at most 2^35.
+ *   value_pool_capacity  bucket multi-value only: value elements in the pool (headers of
+ *                        repeat-insert segments included); at most 2^35.  Ignored otherwise.
  *   seed                 seeds the two hash functions of the outer probing scheme.
  *   device               CUDA device ordinal the table lives on.
  *   l2_persist           1 = launch this table's kernels with an L2 access-policy window
@@ -161,7 +173,10 @@ wc_status wc_table_get_launch(const wc_table* t, int32_t op, wc_launch* h_out);
 
 /* ---- bulk operations (Sec. IV-B3 .. IV-B5) ----------------------------------------- */
 
-/* Insert n pairs (d_keys[i], d_values[i]).  Single-value: a new key claims the earliest
+/* Insert n pairs (d_keys[i], d_values[i]).  Open-addressing multi-value: every pair
+ * claims the earliest free or tombstoned slot of its key's probing sequence, with no
+ * duplicate check (a table at capacity raises WC_FLAG_PROBE_LIMIT for the pairs that find
+ * no slot).  Single-value: a new key claims the earliest
  * free or tombstoned slot of its probing sequence with one CAS of the packed pair
  * (Sec. IV-B2 steps 1-7); a key already present gets its value overwritten and raises
  * WC_FLAG_DUPLICATE_KEY (Sec. IV-B3).  If the same key occurs several times in one
@@ -197,10 +212,12 @@ wc_status wc_retrieve(wc_table* t, const void* d_keys, uint64_t n, void* d_value
                       uint8_t* d_found_or_null, void* stream);
 
 /* Erase (Sec. IV-B5): the key's slot becomes a tombstone; absent keys are a no-op.
- * Multi-value: removes every value of the key (its pool space is not reused). */
+ * Multi-value: removes every value of the key (bucket table: its pool space is not
+ * reused; open-addressing table: every copy's slot becomes a tombstone). */
 wc_status wc_erase(wc_table* t, const void* d_keys, uint64_t n, void* stream);
 
-/* Multi-value counting pass (Sec. IV-B4): d_offsets[0..n] (n+1 uint64, caller-allocated)
+/* Multi-value counting pass (Sec. IV-B4, both multi-value kinds): d_offsets[0..n]
+ * (n+1 uint64, caller-allocated)
  * receives the exclusive prefix sum of the per-query value counts, so query i's values
  * go to [d_offsets[i], d_offsets[i+1]) and d_offsets[n] is the total.  If h_total_or_null
  * is given the call synchronises `stream` and stores the total there.  Sentinel
@@ -211,19 +228,24 @@ wc_status wc_count_values(wc_table* t, const void* d_keys, uint64_t n, uint64_t*
 /* Multi-value retrieve into CSR form (Sec. IV-B4): writes the values of query i to
  * d_values_out[d_offsets[i] .. d_offsets[i+1]), with d_offsets from wc_count_values on
  * the same keys and an unchanged table.  The order of values inside a segment is
- * unspecified.  d_values_out holds d_offsets[n] elements of value_bytes. */
+ * unspecified.  d_values_out holds d_offsets[n] elements of value_bytes and must not be
+ * NULL when n > 0. */
 wc_status wc_retrieve_multi(wc_table* t, const void* d_keys, uint64_t n,
                             const uint64_t* d_offsets, void* d_values_out, void* stream);
 
 /* ---- metrics (blocking) ---------------------------------------------------------- */
 
-/* Single-value: live keys.  Multi-value: stored key-value pairs.  Synchronises stream. */
+/* Single-value: live keys.  Multi-value (both kinds): stored key-value pairs.
+ * Synchronises stream. */
 wc_status wc_size(wc_table* t, uint64_t* h_out, void* stream);
 
-/* Multi-value: distinct live keys.  Single-value: same as wc_size. */
+/* Multi-value: distinct live keys (open-addressing kind: counted on the device by a pass
+ * over the slots, which finds each key's first copy along its probing sequence).
+ * Single-value: same as wc_size.  Synchronises stream. */
 wc_status wc_num_keys(wc_table* t, uint64_t* h_out, void* stream);
 
-/* Load factor alpha = live keys / capacity (key-store load for multi-value, Sec. II).
+/* Load factor alpha = live keys / capacity (key-store load for the bucket multi-value
+ * table, Sec. II; occupied slots = stored pairs / capacity for the open-addressing one).
  * Single-value tables have storage density rho = alpha (Sec. IV-C). */
 wc_status wc_load_factor(wc_table* t, double* h_out, void* stream);
 

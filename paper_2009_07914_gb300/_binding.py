@@ -32,6 +32,7 @@ WC_FLAG_QUEUE_TIMEOUT = 32
 
 WC_SINGLE_VALUE = 0
 WC_MULTI_VALUE = 1
+WC_MULTI_VALUE_OA = 2
 
 WC_SCHEME_AUTO = 0
 WC_SCHEME_DIRECT = 1

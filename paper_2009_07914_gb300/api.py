@@ -12,7 +12,7 @@ import ctypes
 import torch
 
 from . import _binding as B
-from ._binding import (WC_MULTI_VALUE, WC_SINGLE_VALUE, WcLaunch, WcTableConfig, WcTableInfo, check, lib, ptr,
+from ._binding import (WC_MULTI_VALUE, WC_MULTI_VALUE_OA, WC_SINGLE_VALUE, WcLaunch, WcTableConfig, WcTableInfo, check, lib, ptr,
                        stream_handle)
 
 __all__ = [
@@ -167,4 +167,4 @@ def wc_get_status(t: int, clear: bool = False, stream=None) -> int:
     return int(v.value)
 
 
-__all__ += ["WC_SINGLE_VALUE", "WC_MULTI_VALUE"]
+__all__ += ["WC_SINGLE_VALUE", "WC_MULTI_VALUE", "WC_MULTI_VALUE_OA"]

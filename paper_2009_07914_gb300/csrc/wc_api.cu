@@ -19,6 +19,14 @@ namespace wc {
 bool sv_p32_shape_ok(int W, int G);
 bool sv_p64_shape_ok(int W, int G);
 bool mv_shape_ok(int W, int G);
+bool oa_p32_shape_ok(int W, int G);
+bool oa_p64_shape_ok(int W, int G);
+cudaError_t oa_p32_launch(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n, uint64_t* offs,
+                          void* out, cudaStream_t s);
+cudaError_t oa_p64_launch(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n, uint64_t* offs,
+                          void* out, cudaStream_t s);
+cudaError_t oa_p32_num_keys(const wc_table* t, cudaStream_t s);
+cudaError_t oa_p64_num_keys(const wc_table* t, cudaStream_t s);
 cudaError_t sv_p32_launch(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n, void* out,
                           uint8_t* found, cudaStream_t s);
 cudaError_t sv_p64_launch(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n, void* out,
@@ -51,7 +59,7 @@ uint64_t next_prime(uint64_t x) {
 }
 
 bool slot_layout(const wc_table_config& c, uint64_t* slot_bytes) {
-  if (c.kind == WC_SINGLE_VALUE) {
+  if (c.kind == WC_SINGLE_VALUE || c.kind == WC_MULTI_VALUE_OA) {
     if (c.key_bytes == 4 && c.value_bytes == 4) { *slot_bytes = 8; return true; }
     if (c.key_bytes == 8 && c.value_bytes == 8) { *slot_bytes = 16; return true; }
     return false;
@@ -73,6 +81,7 @@ bool window_ok(int kind, uint64_t slot_bytes, int W) {
 
 bool shape_ok(const wc_table* t, int op, int G) {
   const int W = static_cast<int>(t->W);
+  if (t->cfg.kind == WC_MULTI_VALUE_OA) return t->slot_bytes == 8 ? oa_p32_shape_ok(W, G) : oa_p64_shape_ok(W, G);
   if (t->slot_bytes == 8) return sv_p32_shape_ok(W, G);
   if (t->cfg.kind == WC_MULTI_VALUE) {
     if (op == WC_OP_INSERT || op == WC_OP_RETRIEVE) return G == 1;  // one thread per distinct key
@@ -210,6 +219,12 @@ cudaError_t sv_launch(const wc_table* t, int op, const void* keys, const void* v
   return sv_p64_launch(t, op, keys, vals, n, out, found, s);
 }
 
+cudaError_t oa_launch(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n, uint64_t* offs,
+                      void* out, cudaStream_t s) {
+  if (t->slot_bytes == 8) return oa_p32_launch(t, op, keys, vals, n, offs, out, s);
+  return oa_p64_launch(t, op, keys, vals, n, offs, out, s);
+}
+
 }  // namespace wc
 
 using namespace wc;
@@ -254,6 +269,7 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) return WC_ERR_CUDA;
   const bool mv = cfg->kind == WC_MULTI_VALUE;
+  const bool oa = cfg->kind == WC_MULTI_VALUE_OA;
   if (mv && cfg->value_pool_capacity > kMaxPool) return WC_ERR_INVALID_ARG;
 
   uint64_t p = 0, cap = 0;
@@ -274,12 +290,12 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   DeviceGuard guard(t->device);
   t->sm_count = sm_count_of(t->device);
 
-  // One allocation: [slots | meta 256 B | pending (MV) | scan partials (MV) | pool (MV)]
+  // One allocation: [slots | meta 256 B | pending (MV) | scan partials (MV, OA) | pool (MV)]
   const uint64_t off_meta = align_up(t->table_bytes, kAlign);
   const uint64_t off_pending = off_meta + kAlign;
   const uint64_t pending_bytes = mv ? align_up(cap * 4, kAlign) : 0;
   const uint64_t off_partials = off_pending + pending_bytes;
-  t->partials_cap = mv ? scan_partials_needed(kMaxBatch + 1) : 0;
+  t->partials_cap = mv || oa ? scan_partials_needed(kMaxBatch + 1) : 0;
   const uint64_t partial_bytes = align_up(t->partials_cap * 8, kAlign);
   const uint64_t off_pool = off_partials + partial_bytes;
   const uint64_t pool_bytes = align_up(t->pool_capacity * static_cast<uint64_t>(cfg->value_bytes), kAlign);
@@ -297,7 +313,7 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   t->d_nkeys = reinterpret_cast<unsigned long long*>(base + off_meta + 16);
   t->d_cursor = reinterpret_cast<unsigned long long*>(base + off_meta + 24);
   t->d_pending = mv ? reinterpret_cast<uint32_t*>(base + off_pending) : nullptr;
-  t->d_partials = mv ? reinterpret_cast<uint64_t*>(base + off_partials) : nullptr;
+  t->d_partials = mv || oa ? reinterpret_cast<uint64_t*>(base + off_partials) : nullptr;
   t->d_pool = mv ? static_cast<void*>(base + off_pool) : nullptr;
 
   for (int op = 0; op < WC_OP__N; ++op) {
@@ -407,6 +423,8 @@ wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint6
   if (t->cfg.kind == WC_MULTI_VALUE && n >= kMaxMvBatch) return WC_ERR_INVALID_ARG;
   DeviceGuard guard(t->device);
   if (t->cfg.kind == WC_MULTI_VALUE) return cuda_status(mv_insert(t, d_keys, d_values, n, as_stream(stream)));
+  if (t->cfg.kind == WC_MULTI_VALUE_OA)
+    return cuda_status(oa_launch(t, WC_OP_INSERT, d_keys, d_values, n, nullptr, nullptr, as_stream(stream)));
   return cuda_status(sv_launch(t, WC_OP_INSERT, d_keys, d_values, n, nullptr, nullptr, as_stream(stream)));
 }
 
@@ -429,6 +447,8 @@ wc_status wc_erase(wc_table* t, const void* d_keys, uint64_t n, void* stream) {
   if (n == 0) return WC_OK;
   DeviceGuard guard(t->device);
   if (t->cfg.kind == WC_MULTI_VALUE) return cuda_status(mv_erase(t, d_keys, n, as_stream(stream)));
+  if (t->cfg.kind == WC_MULTI_VALUE_OA)
+    return cuda_status(oa_launch(t, WC_OP_ERASE, d_keys, nullptr, n, nullptr, nullptr, as_stream(stream)));
   return cuda_status(sv_launch(t, WC_OP_ERASE, d_keys, nullptr, n, nullptr, nullptr, as_stream(stream)));
 }
 
@@ -436,11 +456,17 @@ wc_status wc_count_values(wc_table* t, const void* d_keys, uint64_t n, uint64_t*
                           uint64_t* h_total_or_null, void* stream) {
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
-  if (t->cfg.kind != WC_MULTI_VALUE) return WC_ERR_UNSUPPORTED;
+  if (t->cfg.kind == WC_SINGLE_VALUE) return WC_ERR_UNSUPPORTED;
   if (d_offsets == nullptr || !aligned(d_offsets, 8)) return WC_ERR_INVALID_ARG;
   DeviceGuard guard(t->device);
   cudaStream_t s = as_stream(stream);
-  cudaError_t e = mv_count(t, d_keys, n, d_offsets, s);
+  cudaError_t e = cudaSuccess;
+  if (t->cfg.kind == WC_MULTI_VALUE) {
+    e = mv_count(t, d_keys, n, d_offsets, s);
+  } else {
+    if (n > 0) e = oa_launch(t, WC_OP_COUNT, d_keys, nullptr, n, d_offsets, nullptr, s);
+    if (e == cudaSuccess) e = scan_exclusive_u64(d_offsets, n, t->d_partials, t->partials_cap, s);
+  }
   if (e != cudaSuccess) return cuda_status(e);
   if (h_total_or_null != nullptr) {
     e = cudaMemcpyAsync(h_total_or_null, d_offsets + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
@@ -453,12 +479,15 @@ wc_status wc_retrieve_multi(wc_table* t, const void* d_keys, uint64_t n, const u
                             void* d_values_out, void* stream) {
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
-  if (t->cfg.kind != WC_MULTI_VALUE) return WC_ERR_UNSUPPORTED;
+  if (t->cfg.kind == WC_SINGLE_VALUE) return WC_ERR_UNSUPPORTED;
   if (d_offsets == nullptr || !aligned(d_offsets, 8)) return WC_ERR_INVALID_ARG;
-  if (d_values_out != nullptr && !aligned(d_values_out, static_cast<uint64_t>(t->cfg.value_bytes)))
+  if (n > 0 && (d_values_out == nullptr || !aligned(d_values_out, static_cast<uint64_t>(t->cfg.value_bytes))))
     return WC_ERR_INVALID_ARG;
   if (n == 0) return WC_OK;
   DeviceGuard guard(t->device);
+  if (t->cfg.kind == WC_MULTI_VALUE_OA)
+    return cuda_status(oa_launch(t, WC_OP_RETRIEVE, d_keys, nullptr, n, const_cast<uint64_t*>(d_offsets),
+                                 d_values_out, as_stream(stream)));
   return cuda_status(mv_retrieve_multi(t, d_keys, n, d_offsets, d_values_out, as_stream(stream)));
 }
 
@@ -477,14 +506,20 @@ wc_status wc_size(wc_table* t, uint64_t* h_out, void* stream) {
 }
 
 wc_status wc_num_keys(wc_table* t, uint64_t* h_out, void* stream) {
-  if (t == nullptr) return WC_ERR_INVALID_ARG;
+  if (t == nullptr || h_out == nullptr) return WC_ERR_INVALID_ARG;
+  if (t->cfg.kind == WC_MULTI_VALUE_OA) {
+    DeviceGuard guard(t->device);
+    cudaError_t e = t->slot_bytes == 8 ? oa_p32_num_keys(t, as_stream(stream)) : oa_p64_num_keys(t, as_stream(stream));
+    if (e != cudaSuccess) return cuda_status(e);
+    return read_counter(t, t->d_nkeys, sizeof(uint64_t), h_out, stream);
+  }
   return read_counter(t, t->cfg.kind == WC_MULTI_VALUE ? t->d_nkeys : t->d_size, sizeof(uint64_t), h_out, stream);
 }
 
 wc_status wc_load_factor(wc_table* t, double* h_out, void* stream) {
   if (t == nullptr || h_out == nullptr) return WC_ERR_INVALID_ARG;
   uint64_t live = 0;
-  wc_status st = wc_num_keys(t, &live, stream);
+  wc_status st = t->cfg.kind == WC_MULTI_VALUE_OA ? wc_size(t, &live, stream) : wc_num_keys(t, &live, stream);
   if (st != WC_OK) return st;
   *h_out = static_cast<double>(live) / static_cast<double>(t->capacity);
   return WC_OK;

@@ -7,7 +7,7 @@ import numpy as np
 import torch
 
 from . import api
-from ._binding import WC_MULTI_VALUE, WC_SINGLE_VALUE
+from ._binding import WC_MULTI_VALUE, WC_MULTI_VALUE_OA, WC_SINGLE_VALUE
 
 _INT = {4: torch.int32, 8: torch.int64}
 _NP_SIGNED = {4: np.int32, 8: np.int64}
@@ -120,3 +120,8 @@ class MultiValueTable(_Table):
         api.wc_retrieve_multi(self.handle, k, offs, out, stream=stream)
         flags = api.wc_get_status(self.handle, clear=True, stream=stream)
         return to_numpy(out, self.vb)[:total], flags
+
+
+class MultiValueOATable(MultiValueTable):
+    """Open-addressing multi-value table: one slot per stored pair (4+4 or 8+8 bytes)."""
+    kind = WC_MULTI_VALUE_OA
