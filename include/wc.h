@@ -137,8 +137,9 @@ typedef struct {
  * WC_SCHEME_BLOCKED: the batch is first split by table region (the multi-split of
  * Sec. IV-E applied to regions of one table) and then probed region by region, so the
  * active part of the table stays in L2; needs scratch of n * (key + value) bytes, which
- * the table allocates on first use (stream-ordered) and keeps.  WC_SCHEME_AUTO picks
- * BLOCKED for single-value inserts of at least 2^18 keys into tables larger than 64 MiB. */
+ * the table allocates on first use (stream-ordered) and keeps.  Inserts of single-value and
+ * open-addressing multi-value tables only.  WC_SCHEME_AUTO picks BLOCKED for those inserts
+ * when the batch holds at least 2^18 pairs and the table is larger than 64 MiB. */
 enum { WC_SCHEME_AUTO = 0, WC_SCHEME_DIRECT = 1, WC_SCHEME_BLOCKED = 2 };
 
 enum { WC_OP_INSERT = 0, WC_OP_RETRIEVE = 1, WC_OP_ERASE = 2, WC_OP_COUNT = 3, WC_OP__N = 4 };

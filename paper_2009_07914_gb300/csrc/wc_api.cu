@@ -202,7 +202,7 @@ cudaError_t ensure_scratch(const wc_table* t, uint64_t bytes, cudaStream_t s) {
 int scheme_for(const wc_table* t, int op, uint64_t n) {
   const int sc = t->launch[op].scheme;
   if (sc != WC_SCHEME_AUTO) return sc;
-  if (op == WC_OP_INSERT && t->cfg.kind == WC_SINGLE_VALUE && n >= (1ull << 18) && t->table_bytes > (64ull << 20))
+  if (op == WC_OP_INSERT && t->cfg.kind != WC_MULTI_VALUE && n >= (1ull << 18) && t->table_bytes > (64ull << 20))
     return WC_SCHEME_BLOCKED;
   return WC_SCHEME_DIRECT;
 }
@@ -393,7 +393,7 @@ wc_status wc_table_set_launch(wc_table* t, int32_t op, const wc_launch* launch) 
   if (launch->scheme < WC_SCHEME_AUTO || launch->scheme > WC_SCHEME_BLOCKED || launch->region_mib < 0 ||
       launch->region_mib > 4096)
     return WC_ERR_INVALID_ARG;
-  if (launch->scheme == WC_SCHEME_BLOCKED && (op != WC_OP_INSERT || t->cfg.kind != WC_SINGLE_VALUE))
+  if (launch->scheme == WC_SCHEME_BLOCKED && (op != WC_OP_INSERT || t->cfg.kind == WC_MULTI_VALUE))
     return WC_ERR_UNSUPPORTED;
   if (!shape_ok(t, op, launch->group_size)) return WC_ERR_INVALID_ARG;
   t->launch[op] = *launch;

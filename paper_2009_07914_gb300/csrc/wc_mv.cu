@@ -30,44 +30,12 @@ cudaError_t insert_passes(const wc_table* t, const void* keys, const void* vals,
   unsigned long long* counters = nullptr;
   cudaError_t e = cudaSuccess;
   if (n >= (1ull << 20) && t->table_bytes > (64ull << 20)) {
-    RegionMap m;
-    m.seed = t->cfg.seed;
-    m.p = static_cast<uint32_t>(t->windows);
-    uint64_t wpr = std::max<uint64_t>(1, (32ull << 20) / (t->W * t->slot_bytes));
-    if ((t->windows + wpr - 1) / wpr > static_cast<uint64_t>(kMaxRegions)) wpr = (t->windows + kMaxRegions - 1) / kMaxRegions;
-    m.wpr = static_cast<uint32_t>(wpr);
-    m.R = static_cast<uint32_t>((t->windows + wpr - 1) / wpr);
-    const uint64_t cur_off = 8192, cnt_off = cur_off + 8192, keys_off = cnt_off + 256;
-    const uint64_t vals_off = keys_off + (n * sizeof(KIn) + 255) / 256 * 256;
-    e = ensure_scratch(t, vals_off + n * sizeof(V), s);
+    RegionSplit<KIn, V> sp;
+    e = region_split(t, 32, k, static_cast<const V*>(vals), n, s, sp);
     if (e != cudaSuccess) return e;
-    char* sc = static_cast<char*>(t->d_scratch);
-    auto* hist = reinterpret_cast<unsigned int*>(sc);
-    auto* cursor = reinterpret_cast<unsigned long long*>(sc + cur_off);
-    counters = reinterpret_cast<unsigned long long*>(sc + cnt_off);
-    KIn* pk = reinterpret_cast<KIn*>(sc + keys_off);
-    V* pv = reinterpret_cast<V*>(sc + vals_off);
-    e = cudaMemsetAsync(sc, 0, keys_off, s);
-    if (e != cudaSuccess) return e;
-    auto hk = k_part_hist<KIn>;
-    auto sk = k_part_scatter<KIn, V>;
-    const size_t hsm = static_cast<size_t>(kHistWarps) * m.R * sizeof(unsigned int);
-    const size_t ssm = scatter_smem_bytes<KIn, V>();
-    static bool pattr = false;
-    if (!pattr) {
-      cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kHistWarps * kMaxRegions * 4));
-      cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(ssm));
-      pattr = true;
-    }
-    const uint64_t pt = (n + kPartTile - 1) / kPartTile;
-    const unsigned hg = static_cast<unsigned>(std::min<uint64_t>(
-        (n + kPartThreads - 1) / kPartThreads, static_cast<uint64_t>(occupancy_smem(hk, kPartThreads, hsm)) * t->sm_count));
-    const unsigned sg = static_cast<unsigned>(
-        std::min<uint64_t>(pt, static_cast<uint64_t>(occupancy_smem(sk, kPartThreads, ssm)) * t->sm_count));
-    hk<<<hg, kPartThreads, hsm, s>>>(k, n, m, hist);
-    sk<<<sg, kPartThreads, ssm, s>>>(k, static_cast<const V*>(vals), n, m, hist, cursor, pk, pv);
-    k = pk;
-    vals = pv;
+    k = sp.keys;
+    vals = sp.vals;
+    counters = sp.counters;
   }
   const uint64_t ntiles = (n + kAggTile - 1) / kAggTile;
   const int bps_c = occupancy_smem(count, kAggThreads, agg_smem_bytes(false));

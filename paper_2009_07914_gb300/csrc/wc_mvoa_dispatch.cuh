@@ -5,6 +5,7 @@
 
 #include "wc_launch.cuh"
 #include "wc_mvoa_kernels.cuh"
+#include "wc_partition.cuh"
 
 namespace wc {
 
@@ -21,7 +22,14 @@ cudaError_t oa_run(const wc_table* t, int op, const void* keys, const void* vals
     auto kern = k_oa_insert<L, G, S>;
     const int bps = lc.blocks_per_sm > 0 ? lc.blocks_per_sm : occupancy(kern, block);
     const EngineGrid g = engine_grid(n, G, block, bps, t->sm_count);
-    return launch_k(t, kern, g.blocks, block, 0, s, d, k, static_cast<const Val*>(vals), n, g.per_warp);
+    if (scheme_for(t, op, n) != WC_SCHEME_BLOCKED)
+      return launch_k(t, kern, g.blocks, block, 0, s, d, k, static_cast<const Val*>(vals), n, g.per_warp,
+                      static_cast<unsigned long long*>(nullptr), 0u);
+    RegionSplit<Key, Val> sp;
+    cudaError_t e = region_split(t, lc.region_mib, k, static_cast<const Val*>(vals), n, s, sp);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = static_cast<unsigned>(bps) * static_cast<unsigned>(t->sm_count);
+    return launch_k(t, kern, grid, block, 0, s, d, sp.keys, sp.vals, n, static_cast<uint64_t>(0), sp.counters, 512u);
   }
   if (op == WC_OP_COUNT || op == WC_OP_RETRIEVE) {
     auto kern = op == WC_OP_COUNT ? k_oa_walk<L, G, S, false> : k_oa_walk<L, G, S, true>;

@@ -42,15 +42,17 @@ __device__ __forceinline__ uint32_t group_exclusive(uint32_t x, int r) {
 }
 
 // ---- insert: append the pair -----------------------------------------------------------
+// counter == nullptr: each warp takes its static range; else warps pull `chunk` inputs at a
+// time in order (a batch split by table region is then inserted region by region).
 template <class L, int G, int S>
 __global__ void __launch_bounds__(256) k_oa_insert(TableDesc t, const typename L::Key* __restrict__ keys,
                                                    const typename L::Val* __restrict__ vals, uint64_t n,
-                                                   uint64_t per_warp) {
+                                                   uint64_t per_warp, unsigned long long* counter, uint32_t chunk) {
   using Slot = typename L::Slot;
   using Key = typename L::Key;
   using Val = typename L::Val;
-  RangeSrc src(n, per_warp, nullptr, 0);
-  if (src.next >= src.end) return;
+  RangeSrc src(n, per_warp, counter, chunk);
+  if (counter == nullptr && src.next >= src.end) return;
   const SvLane<L, G, S> ln;
   constexpr int W = G * S;
   Slot* slots = static_cast<Slot*>(t.slots);

@@ -9,8 +9,11 @@
 // sets of independent element operations).
 #pragma once
 
+#include <algorithm>
+
 #include "wc_device.cuh"
 #include "wc_internal.h"
+#include "wc_launch.cuh"
 
 namespace wc {
 
@@ -171,6 +174,67 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const K* __restri
 template <class K, class V>
 constexpr size_t scatter_smem_bytes() {
   return sizeof(ScatterSmem<K, V>);
+}
+
+// ---- host side -------------------------------------------------------------------------
+// A batch split by table region in the table's scratch buffer, plus kSplitCounters zeroed
+// chunk counters for the ordered sweeps of the kernels that consume it.
+constexpr int kSplitCounters = 32;
+
+template <class K, class V>
+struct RegionSplit {
+  const K* keys;
+  const V* vals;
+  unsigned long long* counters;
+};
+
+// Regions of about region_mib MiB of slots (at most kMaxRegions of them).  Scratch layout:
+// [hist 8 KiB | cursor 8 KiB | counters 256 B | keys | vals], grown on demand.
+template <class K, class V>
+cudaError_t region_split(const wc_table* t, int region_mib, const K* keys, const V* vals, uint64_t n, cudaStream_t s,
+                         RegionSplit<K, V>& out) {
+  static_assert(kMaxRegions * sizeof(unsigned long long) <= 8192, "cursor area");
+  RegionMap m;
+  m.seed = t->cfg.seed;
+  m.p = static_cast<uint32_t>(t->windows);
+  const uint64_t region_bytes = static_cast<uint64_t>(region_mib > 0 ? region_mib : 32) << 20;
+  uint64_t wpr = std::max<uint64_t>(1, region_bytes / (t->W * t->slot_bytes));
+  if ((t->windows + wpr - 1) / wpr > static_cast<uint64_t>(kMaxRegions)) wpr = (t->windows + kMaxRegions - 1) / kMaxRegions;
+  m.wpr = static_cast<uint32_t>(wpr);
+  m.R = static_cast<uint32_t>((t->windows + wpr - 1) / wpr);
+  const uint64_t cur_off = 8192, cnt_off = cur_off + 8192, keys_off = cnt_off + 256;
+  const uint64_t vals_off = keys_off + (n * sizeof(K) + 255) / 256 * 256;
+  cudaError_t e = ensure_scratch(t, vals_off + n * sizeof(V), s);
+  if (e != cudaSuccess) return e;
+  char* sc = static_cast<char*>(t->d_scratch);
+  auto* hist = reinterpret_cast<unsigned int*>(sc);
+  auto* cursor = reinterpret_cast<unsigned long long*>(sc + cur_off);
+  K* pk = reinterpret_cast<K*>(sc + keys_off);
+  V* pv = reinterpret_cast<V*>(sc + vals_off);
+  e = cudaMemsetAsync(sc, 0, keys_off, s);
+  if (e != cudaSuccess) return e;
+  auto hk = k_part_hist<K>;
+  auto sk = k_part_scatter<K, V>;
+  const size_t hsm = static_cast<size_t>(kHistWarps) * m.R * sizeof(unsigned int);
+  const size_t ssm = scatter_smem_bytes<K, V>();
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kHistWarps * kMaxRegions * 4));
+    cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(ssm));
+    attr = true;
+  }
+  const uint64_t ntiles = (n + kPartTile - 1) / kPartTile;
+  const unsigned hg = static_cast<unsigned>(std::min<uint64_t>(
+      (n + kPartThreads - 1) / kPartThreads, static_cast<uint64_t>(occupancy_smem(hk, kPartThreads, hsm)) * t->sm_count));
+  const unsigned sg = static_cast<unsigned>(
+      std::min<uint64_t>(ntiles, static_cast<uint64_t>(occupancy_smem(sk, kPartThreads, ssm)) * t->sm_count));
+  hk<<<hg, kPartThreads, hsm, s>>>(keys, n, m, hist);
+  sk<<<sg, kPartThreads, ssm, s>>>(keys, vals, n, m, hist, cursor, pk, pv);
+  e = cudaGetLastError();
+  out.keys = pk;
+  out.vals = pv;
+  out.counters = reinterpret_cast<unsigned long long*>(sc + cnt_off);
+  return e;
 }
 
 }  // namespace wc

@@ -180,3 +180,31 @@ def test_oa_sentinels_empty_overfull_and_unsupported(wc):
     assert t.size() == 0 and t.num_keys() == 0
     f = t.insert(ks[:60], ks[:60])
     assert f == 0 and t.size() == 60
+
+
+@pytest.mark.parametrize("kb", [4, 8])
+def test_oa_region_split_insert_parity(wc, kb):
+    """A table above 64 MiB and a batch of >= 2^18 pairs take the region-split insert
+    (automatically; a small table is forced onto it with 1 MiB regions); counts and
+    value multisets still equal the oracle's, also on a repeat insert."""
+    uni, n = 1 << 19, 1 << 21
+    d = _zipf_case(0x5B11A + kb, kb, uni, n, 1 << 14)
+    t = make_oa(wc, kb, 12_000_000 if kb == 4 else 6_000_000)
+    assert t.info["table_bytes"] > (64 << 20)
+    o = oracle.MultiValue(kb, kb)
+    for rep in range(2):
+        assert t.insert(d["keys"], d["values"]) == 0
+        o.insert(d["keys"], d["values"])
+        assert t.size() == o.size() == (rep + 1) * n
+    assert t.num_keys() == o.num_keys()
+    q = d["queries"][wc_inputs.shuffle_index(5, d["queries"].size)[:100_000]]
+    check_queries(t, o, q)
+    small = make_oa(wc, kb, 150_000)
+    small.set_launch(wc.WC_OP_INSERT, small.info["window_width"] // (4 if kb == 4 else 2) or 1,
+                     scheme=wc.WC_SCHEME_BLOCKED, region_mib=1)
+    o2 = oracle.MultiValue(kb, kb)
+    m = 100_000
+    assert small.insert(d["keys"][:m], d["values"][:m]) == 0
+    o2.insert(d["keys"][:m], d["values"][:m])
+    assert small.size() == m
+    check_queries(small, o2, q[:20_000])
