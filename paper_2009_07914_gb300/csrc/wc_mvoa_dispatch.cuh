@@ -35,12 +35,12 @@ cudaError_t oa_run(const wc_table* t, int op, const void* keys, const void* vals
     auto kern = op == WC_OP_COUNT ? k_oa_walk<L, G, S, false> : k_oa_walk<L, G, S, true>;
     const int bps = lc.blocks_per_sm > 0 ? lc.blocks_per_sm : occupancy(kern, block);
     const EngineGrid g = engine_grid(n, G, block, bps, t->sm_count);
-    return launch_k(t, kern, g.blocks, block, 0, s, d, k, n, g.per_warp, offs, static_cast<Val*>(out));
+    return launch_k(t, kern, g.blocks, block, 0, s, d, k, n, offs, static_cast<Val*>(out));
   }
   auto kern = k_oa_erase<L, G, S>;
   const int bps = lc.blocks_per_sm > 0 ? lc.blocks_per_sm : occupancy(kern, block);
   const EngineGrid g = engine_grid(n, G, block, bps, t->sm_count);
-  return launch_k(t, kern, g.blocks, block, 0, s, d, k, n, g.per_warp);
+  return launch_k(t, kern, g.blocks, block, 0, s, d, k, n);
 }
 
 // Distinct live keys into the table's nkeys word (zeroed first).

@@ -2,17 +2,18 @@
 // Sec. V-C): every (key, value) pair occupies its own slot of the same slot layouts as
 // the single-value table, along the key's probing sequence.
 //
-//   insert         claims the earliest empty-or-tombstoned slot of the sequence with one
-//                  CAS of the packed pair (Sec. IV-B2 steps 1-7, without the duplicate
-//                  check: the same key may occur many times);
+//   insert         claims an empty-or-tombstoned slot of the first window of the sequence
+//                  that has one, with one CAS of the packed pair (Sec. IV-B2 steps 1-7,
+//                  without the duplicate check: the same key may occur many times);
 //   count_values   walks the sequence up to the first window holding an empty slot and
 //                  counts the matches of each window with a group vote (the parallel
 //                  match counting of Sec. V-C), then an exclusive scan gives the offsets;
 //   retrieve_multi walks the same windows and writes each match to its query's segment
 //                  (lanes of a group write their matches at consecutive positions);
 //   erase          tombstones every copy of the key.
-// Copies of a key all sit before the first empty slot of its sequence (slots never go
-// back to empty except by a clear), so both walks see every copy.
+// Every window before a copy's window was full when the copy was claimed, and slots never
+// go back to empty except by a clear, so every copy sits at or before the first window of
+// its sequence holding an empty slot: the walks see every copy.
 #pragma once
 
 #include "wc_device.cuh"
@@ -41,9 +42,25 @@ __device__ __forceinline__ uint32_t group_exclusive(uint32_t x, int r) {
   return inc - x;
 }
 
+// Position of the (n+1)-th set bit of m (n < popc(m)).
+__device__ __forceinline__ int nth_set(uint32_t m, uint32_t n) {
+  for (uint32_t i = 0; i < n; ++i) m &= m - 1;
+  return __ffs(m) - 1;
+}
+
+// Inputs per chunk of the strided walks (two input prefetches of a warp).
+constexpr uint32_t kWalkChunk = 128;
+
 // ---- insert: append the pair -----------------------------------------------------------
 // counter == nullptr: each warp takes its static range; else warps pull `chunk` inputs at a
 // time in order (a batch split by table region is then inserted region by region).
+//
+// The walks below scan whole windows and stop after the first window holding an empty
+// slot, so a pair may take ANY free slot of the first window of its sequence that has one
+// (not only the lowest): every window before it is then full, which is all the walks need.
+// Each pair picks among the window's free slots by a hash of its input position, so the
+// copies of a hot key, which all probe the same windows, claim different slots at once
+// instead of all racing for the lowest one.
 template <class L, int G, int S>
 __global__ void __launch_bounds__(256) k_oa_insert(TableDesc t, const typename L::Key* __restrict__ keys,
                                                    const typename L::Val* __restrict__ vals, uint64_t n,
@@ -59,7 +76,7 @@ __global__ void __launch_bounds__(256) k_oa_insert(TableDesc t, const typename L
   bool act = false;
   Key k = 0;
   Val v = 0;
-  uint32_t w = 0, step = 0, j = 0, flags = 0;
+  uint32_t w = 0, step = 0, j = 0, flags = 0, salt = 0;
   long long added = 0;
   Feed<Key> fk;
   Feed<Val> fv;
@@ -86,6 +103,7 @@ __global__ void __launch_bounds__(256) k_oa_insert(TableDesc t, const typename L
         v = vin;
         act = true;
         j = 0;
+        salt = static_cast<uint32_t>(np) * 0x9E3779B1u;
         probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step);
       }
     }
@@ -100,13 +118,16 @@ __global__ void __launch_bounds__(256) k_oa_insert(TableDesc t, const typename L
       load_slots<L, S>(slots + lane_slot, s);
       classify<L, S>(s, k, mm, me, mt);
     }
-    const uint32_t bc = group_vote<G>((me | mt) != 0, ln.gbase);
+    const uint32_t fr = me | mt;
+    const uint32_t bc = group_vote<G>(fr != 0, ln.gbase);
+    // lane of the group that claims (group-uniform), then the slot inside that lane
+    const int cl = bc ? nth_set(bc, (salt >> 16) % __popc(bc)) : 0;
     bool ok = false;
-    if (act && bc && ln.r == __ffs(bc) - 1) {
-      const int sub = __ffs(me | mt) - 1;
+    if (act && bc && ln.r == cl) {
+      const int sub = nth_set(fr, (salt >> 8) % __popc(fr));
       ok = L::cas(slots + lane_slot + sub, pick<L, S>(s, sub), L::make(k, v));
     }
-    if constexpr (G > 1) ok = __shfl_sync(kFull, ok, ln.gbase + (bc ? __ffs(bc) - 1 : 0));
+    if constexpr (G > 1) ok = __shfl_sync(kFull, ok, ln.gbase + cl);
     if (act) {
       if (ok) {
         if (ln.r == 0) ++added;
@@ -118,8 +139,9 @@ __global__ void __launch_bounds__(256) k_oa_insert(TableDesc t, const typename L
         } else {
           w = probe_next(w, step, t.p);
         }
+      } else {
+        salt = salt * 0x2C9277B5u + 0xAC564B05u;  // lost the slot: read the window again, pick anew
       }
-      // else: lost the slot to another insert; read the window again
     }
   }
   flush_flags(t.status, flags);
@@ -128,14 +150,15 @@ __global__ void __launch_bounds__(256) k_oa_insert(TableDesc t, const typename L
 
 // ---- count_values / retrieve_multi: walk to the first window with an empty slot -------
 // kWrite = false: offs[pos] = number of copies of keys[pos].
-// kWrite = true: the copies go to out[offs[pos] ..) (at most offs[pos+1] - offs[pos]).
+// kWrite = true: the copies go to out[offs[pos] ..) (at most offs[pos+1] - offs[pos]);
+// a walk ends early once its segment is full.
 template <class L, int G, int S, bool kWrite>
 __global__ void __launch_bounds__(256) k_oa_walk(TableDesc t, const typename L::Key* __restrict__ keys, uint64_t n,
-                                                 uint64_t per_warp, uint64_t* __restrict__ offs,
+                                                 uint64_t* __restrict__ offs,
                                                  typename L::Val* __restrict__ out) {
   using Slot = typename L::Slot;
   using Key = typename L::Key;
-  RangeSrc src(n, per_warp, nullptr, 0);
+  RangeSrc src(StridedChunks{}, n, kWalkChunk);
   if (src.next >= src.end) return;
   const SvLane<L, G, S> ln;
   constexpr int W = G * S;
@@ -166,7 +189,7 @@ __global__ void __launch_bounds__(256) k_oa_walk(TableDesc t, const typename L::
       if (is_sentinel(k)) {
         flags |= kFlagInvalid;
         if (!kWrite && ln.r == 0) offs[pos] = 0;
-      } else {
+      } else if (!kWrite || cap != 0) {  // a query counted 0 has nothing to copy
         act = true;
         j = 0;
         probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step);
@@ -197,7 +220,7 @@ __global__ void __launch_bounds__(256) k_oa_walk(TableDesc t, const typename L::
     }
     if (act) {
       cnt += here;
-      if (be || ++j >= t.p) {
+      if (be || (kWrite && cnt >= cap) || ++j >= t.p) {
         if (!kWrite && ln.r == 0) offs[pos] = cnt;
         act = false;
       } else {
@@ -210,11 +233,10 @@ __global__ void __launch_bounds__(256) k_oa_walk(TableDesc t, const typename L::
 
 // ---- erase: every copy of the key becomes a tombstone -----------------------------------
 template <class L, int G, int S>
-__global__ void __launch_bounds__(256) k_oa_erase(TableDesc t, const typename L::Key* __restrict__ keys, uint64_t n,
-                                                  uint64_t per_warp) {
+__global__ void __launch_bounds__(256) k_oa_erase(TableDesc t, const typename L::Key* __restrict__ keys, uint64_t n) {
   using Slot = typename L::Slot;
   using Key = typename L::Key;
-  RangeSrc src(n, per_warp, nullptr, 0);
+  RangeSrc src(StridedChunks{}, n, kWalkChunk);
   if (src.next >= src.end) return;
   const SvLane<L, G, S> ln;
   constexpr int W = G * S;

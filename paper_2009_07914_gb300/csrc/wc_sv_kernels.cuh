@@ -63,12 +63,15 @@ __device__ __forceinline__ void warp_range(uint64_t n, uint64_t per_warp, uint64
 // static range [next, end).  Otherwise warps pull `chunk` positions at a time from a
 // global counter, so the whole grid sweeps the input front to back -- a batch sorted by
 // table region is then probed region by region, with the active regions held in L2.
+struct StridedChunks {};
+
 struct RangeSrc {
   uint64_t next, end, n;
   unsigned long long* counter;
   uint32_t chunk;
   bool done;
   bool fresh;  // [next, end) is a new range whose inputs have not been prefetched yet
+  uint64_t base = 0, stride = 0;  // strided mode: current chunk start, chunks of all warps
   __device__ RangeSrc(uint64_t n_, uint64_t per_warp, unsigned long long* counter_, uint32_t chunk_)
       : n(n_), counter(counter_), chunk(chunk_), done(false), fresh(true) {
     if (counter == nullptr) {
@@ -80,9 +83,28 @@ struct RangeSrc {
   // A fixed range [begin, end) (one tile of the batched executor).
   __device__ RangeSrc(uint64_t begin, uint64_t end_)
       : next(begin), end(end_), n(end_), counter(nullptr), chunk(0), done(false), fresh(true) {}
+  // Warp w takes chunks w, w + warps, w + 2 * warps, ... of `chunk_` positions: spreads
+  // inputs whose cost depends on their position (a sorted query range whose first part
+  // holds every present key) over all warps without a shared counter.
+  __device__ RangeSrc(StridedChunks, uint64_t n_, uint32_t chunk_)
+      : n(n_), counter(nullptr), chunk(chunk_), done(false), fresh(true) {
+    const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    stride = (static_cast<uint64_t>(gridDim.x) * blockDim.x >> 5) * chunk;
+    base = warp * chunk;
+    next = base < n ? base : n;
+    end = base + chunk < n ? base + chunk : n;
+  }
   // Warp-uniform: true while positions are left in [next, end) or can be pulled.
   __device__ __forceinline__ bool ensure() {
     if (next < end) return true;
+    if (stride != 0) {
+      base += stride;
+      if (base >= n) return false;
+      next = base;
+      end = base + chunk < n ? base + chunk : n;
+      fresh = true;
+      return true;
+    }
     if (counter == nullptr || done) return false;
     unsigned long long c = 0;
     if ((threadIdx.x & 31) == 0) c = atomicAdd(counter, static_cast<unsigned long long>(chunk));
