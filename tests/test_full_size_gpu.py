@@ -147,3 +147,47 @@ def test_mv_2e28_zipf_over_2e24(env):
     assert np.array_equal(goffs, eoffs.astype(np.int64))
     assert np.array_equal(oracle.sorted_segments(got, goffs), oracle.sorted_segments(ev, eoffs))
     api.wc_table_destroy(h)
+
+
+@pytest.mark.parametrize("r", [1, 64])
+def test_mv_oa_2e28_uniform_r(env, r):
+    """Open-addressing multi-value table at the benchmark size (2^28 uint32 pairs, keys
+    uniform over 1..n/r, load 0.8, default shapes with the region-split insert): exact
+    per-query counts against the generator's histogram, every insert index returned
+    once inside its own key's segment, and a sample of queries against the oracle."""
+    wc, api, torch, to_device, to_numpy = env
+    dev = torch.device("cuda", 0)
+    n = 1 << 28
+    d = wc_inputs.mv_uniform_r(0x57C00005 + r, n, r)
+    keys = d["keys"].astype(np.uint32)
+    h = api.wc_table_create(2, 4, 4, int(np.ceil(n / 0.8)), 0, 0, 0x5EEDC0DE, 0)
+    api.wc_insert(h, to_device(keys, 4, dev), to_device(d["values"], 4, dev))
+    assert api.wc_size(h) == n and api.wc_get_status(h, True) == 0
+    counts = np.bincount(keys, minlength=n + 1)
+    q = to_device(np.arange(1, n + 1, dtype=np.uint32), 4, dev)
+    offs = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    assert api.wc_count_values(h, q, offs) == n
+    offs_h = to_numpy(offs, 8).astype(np.int64)
+    assert np.array_equal(np.diff(offs_h), counts[1:])
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    api.wc_retrieve_multi(h, q, offs, out)
+    vals = to_numpy(out, 4)
+    assert np.array_equal(np.sort(vals), np.arange(n, dtype=np.uint32))
+    seg = np.repeat(np.arange(1, n + 1, dtype=np.uint32), counts[1:])
+    assert np.array_equal(seg, keys[vals])
+    del seg
+    if r == 1:
+        assert api.wc_num_keys(h) == int((counts > 0).sum())
+    # oracle on a sample of queries: the pairs of their keys only
+    qi = _sample(n, 4096, 6)
+    qk = (qi + 1).astype(np.uint32)
+    sel = np.isin(keys, qk)
+    orc = oracle.MultiValue(4, 4)
+    orc.insert(keys[sel], d["values"][sel])
+    eoffs, _ = orc.count_values(qk)
+    ev, _ = orc.retrieve_multi(qk, eoffs)
+    got = np.concatenate([vals[offs_h[i]:offs_h[i + 1]] for i in qi])
+    goffs = np.concatenate([[0], np.cumsum(np.diff(offs_h)[qi])])
+    assert np.array_equal(goffs, eoffs.astype(np.int64))
+    assert np.array_equal(oracle.sorted_segments(got, goffs), oracle.sorted_segments(ev, eoffs))
+    api.wc_table_destroy(h)
