@@ -254,8 +254,41 @@ wc_status wc_load_factor(wc_table* t, double* h_out, void* stream);
  * clear != 0 it is reset to 0 afterwards.  Synchronises stream. */
 wc_status wc_get_status(wc_table* t, uint32_t* h_flags, int32_t clear, void* stream);
 
+/* wc_get_status with clear, folded into a status code: WC_ERR_TIMEOUT if QUEUE_TIMEOUT
+ * was raised, WC_ERR_FULL if PROBE_LIMIT, POOL_EXHAUSTED or COUNT_OVERFLOW was (pairs
+ * were not stored), else WC_OK (DUPLICATE_KEY and INVALID_KEY are warnings).  The raw
+ * bits go to *h_flags_or_null.  Synchronises stream. */
+wc_status wc_check_status(wc_table* t, uint32_t* h_flags_or_null, void* stream);
+
 /* Static description of a status code. */
 const char* wc_status_string(wc_status s);
+
+/* ---- host copies: inspection, checkpoint and resume (no counterpart in the paper) -- */
+
+/* Copy the slot array (wc_table_info.table_bytes bytes, slot i at byte i * slot_bytes,
+ * layout as in wc_table_config) to host memory h_out of `bytes` >= table_bytes.
+ * Synchronises stream.  Used by the slot-dump invariant checks of the tests. */
+wc_status wc_table_dump_slots(const wc_table* t, void* h_out, uint64_t bytes, void* stream);
+
+/* Bytes of a whole-table snapshot: a header with the table's geometry, then its slots,
+ * counters, status word and (multi-value) pending array and value pool. */
+uint64_t wc_table_snapshot_bytes(const wc_table* t);
+
+/* Write a snapshot to host memory h_out (`bytes` >= wc_table_snapshot_bytes).  No
+ * operation on the table may be in flight on another stream.  Synchronises stream. */
+wc_status wc_table_snapshot(const wc_table* t, void* h_out, uint64_t bytes, void* stream);
+
+/* Replace the table's contents with a snapshot taken from a table of the same kind,
+ * widths, window width, window count, pool capacity and seed (WC_ERR_INVALID_ARG
+ * otherwise, table unchanged).  Synchronises stream. */
+wc_status wc_table_restore(wc_table* t, const void* h_in, uint64_t bytes, void* stream);
+
+/* ---- testing hook --------------------------------------------------------------- */
+
+/* The next `count` device allocations of the library (wc_table_create, the scratch of
+ * the region-split insert) fail as if the device were out of memory; 0 turns it off.
+ * Process-wide.  For tests of the out-of-memory paths. */
+wc_status wc_debug_fail_allocations(uint32_t count);
 
 #ifdef __cplusplus
 }

@@ -58,6 +58,8 @@ def _load():
         lib.oracle_num_keys.restype = u64
         lib.oracle_num_keys.argtypes = [vp]
         lib.oracle_reserve.argtypes = [vp, u64]
+        lib.oracle_check_slots.restype = ctypes.c_int
+        lib.oracle_check_slots.argtypes = [vp, u64, u32, u32, u64, ctypes.c_int, vp, vp, vp]
         _lib = lib
     return _lib
 
@@ -153,3 +155,19 @@ def sorted_segments(values: np.ndarray, offsets: np.ndarray) -> np.ndarray:
     seg = np.repeat(np.arange(n, dtype=np.int64), np.diff(offs))
     order = np.lexsort((out, seg))
     return out[order]
+
+
+def check_slots(dump: np.ndarray, p: int, W: int, slot_bytes: int, seed: int, unique_keys: bool) -> dict:
+    """Slot-dump invariant check of a table's slot array (host bytes, p * W slots):
+    live slots, duplicate keys (when keys must be unique) and live keys that sit behind
+    a window holding an empty slot on their own probing sequence (see oracle.cpp)."""
+    buf = np.ascontiguousarray(dump).view(np.uint8)
+    if buf.size < p * W * slot_bytes:
+        raise ValueError("dump holds %d bytes, need %d" % (buf.size, p * W * slot_bytes))
+    out = np.zeros(3, dtype=np.uint64)
+    rc = _load().oracle_check_slots(_ptr(buf), p, W, slot_bytes, seed & (2 ** 64 - 1), int(unique_keys),
+                                    _ptr(out[0:]), ctypes.c_void_p(out.ctypes.data + 8),
+                                    ctypes.c_void_p(out.ctypes.data + 16))
+    if rc != 0:
+        raise ValueError("bad table geometry")
+    return {"live": int(out[0]), "dups": int(out[1]), "unreachable": int(out[2])}

@@ -262,3 +262,76 @@ void oracle_reserve(void* p, uint64_t n) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Slot-dump invariant checker (layout, not values).  Given a host copy of a table's slot
+// array it checks the two properties that make the early exit of Sec. IV-B4 correct:
+//   * reachability: walking a live key's probing sequence window by window, the window
+//     holding it comes no later than the first window that holds an empty slot (a slot
+//     only moves empty -> key -> tombstone -> key, so nothing may sit behind an empty
+//     window of its own sequence);
+//   * uniqueness (single-value tables and key stores, Sec. IV: each key occurs once).
+// The probing sequence is the table's definition restated here: h = fmix64(key ^ seed)
+// (MurmurHash3's 64-bit finalizer), w_0 = floor(hi32(h) * p / 2^32),
+// step = 1 + floor(lo32(h) * (p - 1) / 2^32), w_{j+1} = (w_j + step) mod p; windows are
+// W consecutive slots.  Slot words: 8-byte slots hold key = low 32 bits (empty 0,
+// tombstone 0xffffffff); 16-byte slots hold key = first 64-bit word (empty 0, tombstone
+// all ones).
+namespace {
+
+uint64_t chk_fmix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+uint64_t chk_key(const unsigned char* slots, uint64_t i, uint32_t slot_bytes) {
+  if (slot_bytes == 8) {
+    uint64_t w;
+    std::memcpy(&w, slots + i * 8, 8);
+    return w & 0xffffffffull;
+  }
+  uint64_t k;
+  std::memcpy(&k, slots + i * 16, 8);
+  return k;
+}
+
+}  // namespace
+
+extern "C" int oracle_check_slots(const void* dump, uint64_t p, uint32_t W, uint32_t slot_bytes, uint64_t seed,
+                                  int unique_keys, uint64_t* out_live, uint64_t* out_dups,
+                                  uint64_t* out_unreachable) {
+  if (dump == nullptr || p < 2 || W == 0 || (slot_bytes != 8 && slot_bytes != 16)) return -1;
+  const unsigned char* s = static_cast<const unsigned char*>(dump);
+  const uint64_t cap = p * W;
+  const uint64_t tomb = slot_bytes == 8 ? 0xffffffffull : ~0ull;
+  std::vector<uint8_t> has_empty(p, 0);
+  for (uint64_t i = 0; i < cap; ++i)
+    if (chk_key(s, i, slot_bytes) == 0) has_empty[i / W] = 1;
+  std::unordered_map<uint64_t, uint64_t> seen;
+  uint64_t live = 0, dups = 0, unreachable = 0;
+  for (uint64_t i = 0; i < cap; ++i) {
+    const uint64_t k = chk_key(s, i, slot_bytes);
+    if (k == 0 || k == tomb) continue;
+    ++live;
+    if (unique_keys && seen[k]++ > 0) ++dups;
+    const uint64_t h = chk_fmix64(k ^ seed);
+    uint64_t w = ((h >> 32) * p) >> 32;
+    const uint64_t step = 1 + (((h & 0xffffffffull) * (p - 1)) >> 32);
+    const uint64_t home = i / W;
+    bool ok = false;
+    for (uint64_t j = 0; j < p; ++j) {
+      if (w == home) { ok = true; break; }
+      if (has_empty[w]) break;
+      w = (w + step) % p;
+    }
+    if (!ok) ++unreachable;
+  }
+  if (out_live) *out_live = live;
+  if (out_dups) *out_dups = dups;
+  if (out_unreachable) *out_unreachable = unreachable;
+  return 0;
+}

@@ -90,6 +90,12 @@ _SIGS = {
     "wc_num_keys": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), _vp]),
     "wc_load_factor": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), _vp]),
     "wc_get_status": (ctypes.c_int, [_vp, ctypes.POINTER(_u32), _i32, _vp]),
+    "wc_check_status": (ctypes.c_int, [_vp, ctypes.POINTER(_u32), _vp]),
+    "wc_table_dump_slots": (ctypes.c_int, [_vp, _vp, _u64, _vp]),
+    "wc_table_snapshot_bytes": (_u64, [_vp]),
+    "wc_table_snapshot": (ctypes.c_int, [_vp, _vp, _u64, _vp]),
+    "wc_table_restore": (ctypes.c_int, [_vp, _vp, _u64, _vp]),
+    "wc_debug_fail_allocations": (ctypes.c_int, [_u32]),
 }
 
 

@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 
+import numpy as np
 import torch
 
 from . import _binding as B
@@ -167,4 +168,43 @@ def wc_get_status(t: int, clear: bool = False, stream=None) -> int:
     return int(v.value)
 
 
+def wc_check_status(t: int, stream=None) -> tuple[int, int]:
+    """(wc_status code, raw flag bits); the word is cleared.  Does not raise for the
+    device conditions (WC_ERR_FULL / WC_ERR_TIMEOUT are returned as the code)."""
+    v = ctypes.c_uint32()
+    code = lib().wc_check_status(t, ctypes.byref(v), stream_handle(stream))
+    if code not in (B.WC_OK, B.WC_ERR_FULL, B.WC_ERR_TIMEOUT):
+        check(code, "wc_check_status")
+    return int(code), int(v.value)
+
+
+def wc_table_dump_slots(t: int, stream=None) -> np.ndarray:
+    """Host copy of the slot array as bytes (slot i at byte i * slot_bytes)."""
+    info = wc_table_get_info(t)
+    out = np.empty(info["table_bytes"], dtype=np.uint8)
+    check(lib().wc_table_dump_slots(t, out.ctypes.data, out.size, stream_handle(stream)), "wc_table_dump_slots")
+    return out
+
+
+def wc_table_snapshot_bytes(t: int) -> int:
+    return int(lib().wc_table_snapshot_bytes(t))
+
+
+def wc_table_snapshot(t: int, stream=None) -> np.ndarray:
+    out = np.empty(wc_table_snapshot_bytes(t), dtype=np.uint8)
+    check(lib().wc_table_snapshot(t, out.ctypes.data, out.size, stream_handle(stream)), "wc_table_snapshot")
+    return out
+
+
+def wc_table_restore(t: int, snapshot: np.ndarray, stream=None):
+    buf = np.ascontiguousarray(snapshot).view(np.uint8)
+    check(lib().wc_table_restore(t, buf.ctypes.data, buf.size, stream_handle(stream)), "wc_table_restore")
+
+
+def wc_debug_fail_allocations(count: int):
+    check(lib().wc_debug_fail_allocations(count), "wc_debug_fail_allocations")
+
+
+__all__ += ["wc_check_status", "wc_table_dump_slots", "wc_table_snapshot_bytes", "wc_table_snapshot",
+            "wc_table_restore", "wc_debug_fail_allocations"]
 __all__ += ["WC_SINGLE_VALUE", "WC_MULTI_VALUE", "WC_MULTI_VALUE_OA"]

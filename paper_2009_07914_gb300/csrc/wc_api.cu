@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -124,6 +125,16 @@ struct DeviceGuard {
 
 bool aligned(const void* p, uint64_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// Testing hook (wc_debug_fail_allocations): allocations still to fail on purpose.
+std::atomic<uint32_t> g_fail_allocs{0};
+
+bool injected_alloc_failure() {
+  uint32_t c = g_fail_allocs.load();
+  while (c > 0)
+    if (g_fail_allocs.compare_exchange_weak(c, c - 1)) return true;
+  return false;
+}
+
 }  // namespace
 
 TableDesc desc_of(const wc_table* t) {
@@ -190,6 +201,7 @@ cudaError_t ensure_scratch(const wc_table* t, uint64_t bytes, cudaStream_t s) {
     t->scratch_bytes = 0;
   }
   const uint64_t want = align_up(bytes + bytes / 8, kAlign);
+  if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMallocAsync(&t->d_scratch, want, s);
   if (e != cudaSuccess) {
     t->d_scratch = nullptr;
@@ -242,6 +254,11 @@ const char* wc_status_string(wc_status s) {
     case WC_ERR_UNSUPPORTED: return "operation not supported for this table kind";
   }
   return "unknown status";
+}
+
+wc_status wc_debug_fail_allocations(uint32_t count) {
+  g_fail_allocs.store(count);
+  return WC_OK;
 }
 
 wc_status wc_plan_capacity(uint64_t min_capacity, int32_t window_width, uint64_t* h_windows,
@@ -301,7 +318,7 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   const uint64_t pool_bytes = align_up(t->pool_capacity * static_cast<uint64_t>(cfg->value_bytes), kAlign);
   t->device_bytes = off_pool + pool_bytes;
 
-  if (cudaMalloc(&t->d_block, t->device_bytes) != cudaSuccess) {
+  if (injected_alloc_failure() || cudaMalloc(&t->d_block, t->device_bytes) != cudaSuccess) {
     cudaGetLastError();
     delete t;
     return WC_ERR_OUT_OF_MEMORY;

@@ -1,0 +1,125 @@
+"""Pins of the slot-dump invariant checker (oracle.check_slots) on the CPU.
+
+Valid dumps come from a brute-force insert written here with Python integers (walk the
+key's windows, take the first empty slot of the first window that has one); mistakes are
+then planted in those dumps -- an empty slot put back in front of a key, a key stored
+twice, the wrong hash seed -- and each must be reported.  A tombstone in the same place
+must not be (Sec. IV-B5: tombstones count as occupied for lookups)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+
+M64 = (1 << 64) - 1
+
+
+def fmix64(k: int) -> int:
+    k ^= k >> 33
+    k = (k * 0xFF51AFD7ED558CCD) & M64
+    k ^= k >> 33
+    k = (k * 0xC4CEB9FE1A85EC53) & M64
+    k ^= k >> 33
+    return k
+
+
+def windows(key: int, seed: int, p: int):
+    h = fmix64((key ^ seed) & M64)
+    w = ((h >> 32) * p) >> 32
+    step = 1 + (((h & 0xFFFFFFFF) * (p - 1)) >> 32)
+    for _ in range(p):
+        yield w
+        w = (w + step) % p
+
+
+class Table:
+    """Brute-force table: keys per slot, 0 = empty, `tomb` = tombstone."""
+
+    def __init__(self, p, W, slot_bytes, seed):
+        self.p, self.W, self.sb, self.seed = p, W, slot_bytes, seed
+        self.tomb = 0xFFFFFFFF if slot_bytes == 8 else M64
+        self.keys = [0] * (p * W)
+        self.where = {}
+
+    def insert(self, k):
+        for j, w in enumerate(windows(k, self.seed, self.p)):
+            for q in range(self.W):
+                if self.keys[w * self.W + q] == 0:
+                    self.keys[w * self.W + q] = k
+                    self.where[k] = (w * self.W + q, j)
+                    return True
+        return False
+
+    def dump(self) -> np.ndarray:
+        if self.sb == 8:
+            words = np.array(self.keys, dtype=np.uint64) | (np.uint64(7) << np.uint64(32))
+            words[np.array(self.keys, dtype=np.uint64) == 0] = 0
+            return words.view(np.uint8)
+        out = np.zeros((len(self.keys), 2), dtype=np.uint64)
+        out[:, 0] = np.array(self.keys, dtype=np.uint64)
+        out[:, 1] = 99
+        return out.view(np.uint8).reshape(-1)
+
+    def check(self, seed=None, unique=True):
+        return oracle.check_slots(self.dump(), self.p, self.W, self.sb, self.seed if seed is None else seed, unique)
+
+
+def filled(slot_bytes, p=101, W=8, n=600, seed=0xC0FFEE):
+    t = Table(p, W, slot_bytes, seed)
+    rng = np.random.default_rng(slot_bytes * 1000 + W)
+    top = 0xFFFFFFFE if slot_bytes == 8 else M64 - 1
+    for k in rng.integers(1, top, n, dtype=np.uint64, endpoint=False):
+        t.insert(int(k))
+    return t
+
+
+@pytest.mark.parametrize("sb", [8, 16])
+def test_valid_dump_passes(sb):
+    t = filled(sb)
+    r = t.check()
+    assert r == {"live": len(t.where), "dups": 0, "unreachable": 0}
+    assert oracle.check_slots(np.zeros(101 * 8 * sb, np.uint8), 101, 8, sb, 1, True) == {
+        "live": 0, "dups": 0, "unreachable": 0}
+
+
+@pytest.mark.parametrize("sb", [8, 16])
+def test_empty_slot_in_front_of_a_key_is_reported_but_a_tombstone_is_not(sb):
+    t = filled(sb)
+    # a key that sits in the second or a later window of its own sequence
+    k, (slot, j) = next((k, v) for k, v in t.where.items() if v[1] >= 1)
+    first = next(windows(k, t.seed, t.p))
+    victim = first * t.W  # a slot of an earlier window of k's sequence (it was full)
+    assert t.keys[victim] not in (0, t.tomb)
+    t.keys[victim] = t.tomb
+    r = t.check()
+    assert r["unreachable"] == 0 and r["live"] == len(t.where) - 1
+    t.keys[victim] = 0
+    r = t.check()
+    assert r["unreachable"] >= 1
+
+
+@pytest.mark.parametrize("sb", [8, 16])
+def test_duplicate_key_is_reported_only_when_keys_must_be_unique(sb):
+    t = filled(sb, n=300)
+    k = next(iter(t.where))
+    for w in windows(k, t.seed, t.p):
+        free = [w * t.W + q for q in range(t.W) if t.keys[w * t.W + q] == 0]
+        if free:
+            t.keys[free[-1]] = k
+            break
+    assert t.check() == {"live": len(t.where) + 1, "dups": 1, "unreachable": 0}
+    assert t.check(unique=False)["dups"] == 0
+
+
+def test_wrong_seed_breaks_reachability():
+    t = filled(8, n=700)
+    assert t.check()["unreachable"] == 0
+    assert t.check(seed=t.seed + 1)["unreachable"] > 0
+
+
+def test_geometry_is_validated():
+    with pytest.raises(ValueError):
+        oracle.check_slots(np.zeros(10, np.uint8), 11, 8, 8, 0, True)
+    with pytest.raises(ValueError):
+        oracle.check_slots(np.zeros(11 * 8 * 12, np.uint8), 11, 8, 12, 0, True)
