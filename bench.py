@@ -532,19 +532,22 @@ def run_mv_zipf(args, dev):
             (n + nq + n) / (total * 1e-3) / 1e9, "G ops/s", total, "u64/u32",
             {"n_inserts": n, "universe": uni, "queries": nq, "key_store_capacity": info["capacity"],
              "pool": info["pool_capacity"], "l2": "no flush: 2 GB of inserts, 1 GB pool"}, clk,
-            5 * args.steps,
+            10 * args.steps,  # hist, scatter, count, alloc, scatter; count, 3 scan kernels; gather
             {"insert_gops": n / ins / 1e6, "count_gqps": nq / cnt / 1e6, "retrieve_multi_gvals": n / ret / 1e6,
              "insert_ms": ins, "count_ms": cnt, "retrieve_multi_ms": ret, "distinct_keys": api.wc_num_keys(h)})
     api.wc_table_destroy(h)
 
 
 def run_mv_oa_uniform_r(args, dev):
-    """Open-addressing multi-value table (one slot per pair) on the Sec. V-C workload: n
-    uint32 keys drawn uniformly from 1..n/r (value = insert index) inserted at target
-    load 0.8, then count_values + retrieve_multi for all of 1..n, so exactly n values come
-    back.  One step = clear + insert + count + retrieve, for every r of --r."""
+    """The paper's multi-value workload (Sec. V-C): n uint32 keys drawn uniformly from
+    1..n/r (value = insert index), then count_values + retrieve_multi for all of 1..n, so
+    exactly n values come back.  For every r of --r, both multi-value layouts: the
+    open-addressing table (one slot per pair, load 0.8 over the pairs) and the key-once
+    bucket table (key store at load 0.8 over the n/r keys, exact-size buckets).  One step
+    = clear + insert + count + retrieve on one table; the value is the open-addressing
+    table's throughput over every r, the bucket table's is reported beside it."""
     import torch
-    from paper_2009_07914_gb300 import api
+    from paper_2009_07914_gb300 import WC_OP_COUNT, WC_OP_INSERT, WC_OP_RETRIEVE, api
     from paper_2009_07914_gb300.table import to_device
     log2n = 28 if args.log2n == 27 else args.log2n
     n = 1 << log2n
@@ -555,46 +558,48 @@ def run_mv_oa_uniform_r(args, dev):
     out = torch.empty(n, dtype=torch.int32, device=dev)
     s = torch.cuda.current_stream()
     h = api.wc_table_create(2, 4, 4, int(np.ceil(n / 0.8)), args.window, 0, 0x5EEDC0DE, dev.index)
-    from paper_2009_07914_gb300 import WC_OP_COUNT, WC_OP_INSERT, WC_OP_RETRIEVE
     if args.group:
         for op in (WC_OP_INSERT, WC_OP_RETRIEVE, WC_OP_COUNT):
             api.wc_table_set_launch(h, op, args.group, 256, 0, 0, 0)
     info = api.wc_table_get_info(h)
-    keys = {}
-    for r in rs:
-        kk = wc_inputs.mv_uniform_r(0x57C00005 + r, n, r)["keys"].astype(np.uint32)
-        keys[r] = to_device(kk, 4, dev)
-    ev = {r: [] for r in rs}
-
-    def step(rec):
-        for r in rs:
-            api.wc_table_clear(h, s)
-            t0 = timed(s, lambda: api.wc_insert(h, keys[r], vals, n, s))
-            t1 = timed(s, lambda: api.wc_count_values(h, q, offs, n, want_total=False, stream=s))
-            t2 = timed(s, lambda: api.wc_retrieve_multi(h, q, offs, out, n, s))
-            if rec:
-                ev[r].append((t0, t1, t2))
-    for _ in range(args.warmup):
-        step(False)
-    assert api.wc_size(h) == n and int(offs[-1].item()) == n and api.wc_get_status(h, True) == 0
+    res = {"oa": {}, "bucket": {}}
+    launches = 0
     with ClockSampler(dev.index) as clk:
-        for _ in range(args.steps):
-            step(True)
-    per_r, total = {}, 0.0
-    for r in rs:
-        ins, cnt, ret = (statistics.median(e[i] for e in ev[r]) for i in range(3))
-        total += ins + cnt + ret
-        per_r[str(r)] = {"insert_gops": n / ins / 1e6, "retrieve_gqps": n / (cnt + ret) / 1e6,
-                         "count_gqps": n / cnt / 1e6, "insert_ms": ins, "count_ms": cnt, "retrieve_multi_ms": ret}
+        for r in rs:
+            keys = to_device(wc_inputs.mv_uniform_r(0x57C00005 + r, n, r)["keys"].astype(np.uint32), 4, dev)
+            hb = api.wc_table_create(1, 4, 4, int(np.ceil(max(1, n // r) / 0.8)), 0, n + 2 * (n // r) + 1024,
+                                     0x5EEDC0DE, dev.index)
+            for name, t in (("oa", h), ("bucket", hb)):
+                ev = []
+                for i in range(args.warmup + args.steps):
+                    api.wc_table_clear(t, s)
+                    t0 = timed(s, lambda: api.wc_insert(t, keys, vals, n, s))
+                    t1 = timed(s, lambda: api.wc_count_values(t, q, offs, n, want_total=False, stream=s))
+                    t2 = timed(s, lambda: api.wc_retrieve_multi(t, q, offs, out, n, s))
+                    if i >= args.warmup:
+                        ev.append((t0, t1, t2))
+                    if i == 0:
+                        assert api.wc_size(t) == n and int(offs[-1].item()) == n and api.wc_get_status(t, True) == 0
+                ins, cnt, ret = (statistics.median(e[j] for e in ev) for j in range(3))
+                res[name][str(r)] = {"insert_gops": n / ins / 1e6, "retrieve_gqps": n / (cnt + ret) / 1e6,
+                                     "count_gqps": n / cnt / 1e6, "insert_ms": ins, "count_ms": cnt,
+                                     "retrieve_multi_ms": ret}
+                # OA: hist + scatter + insert, walk + 3 scan kernels, walk; bucket: hist +
+                # scatter + count + alloc + scatter, count + 3 scan kernels, gather
+                launches += (8 if name == "oa" else 10) * args.steps
+            api.wc_table_destroy(hb)
+            del keys
+    total = {m: sum(v["insert_ms"] + v["count_ms"] + v["retrieve_multi_ms"] for v in res[m].values()) for m in res}
     _common(args, "mv_oa_u32_n2^%d_uniform_r%s_alpha0.80" % (log2n, "-".join(map(str, rs))),
-            "G ops/s (inserts + queries, over every r)", 2 * n * len(rs) / (total * 1e-3) / 1e9, "G ops/s", total,
-            "u32", {"n": n, "r": rs, "capacity": info["capacity"], "table_bytes": info["table_bytes"],
-                    "window_slots": info["window_width"],
-                    "groups": {op: api.wc_table_get_launch(h, c)["group_size"] for op, c in
-                               (("insert", WC_OP_INSERT), ("count", WC_OP_COUNT),
-                                ("retrieve_multi", WC_OP_RETRIEVE))},
-                    "l2": "no flush: 2.7 GB table, 1 GB inputs"}, clk, 5 * len(rs) * args.steps,
-            {"per_r": per_r})
+            "G ops/s (inserts + queries, over every r)", 2 * n * len(rs) / (total["oa"] * 1e-3) / 1e9, "G ops/s",
+            total["oa"], "u32", {"n": n, "r": rs, "capacity": info["capacity"], "table_bytes": info["table_bytes"],
+                                 "window_slots": info["window_width"],
+                                 "groups": {op: api.wc_table_get_launch(h, c)["group_size"] for op, c in
+                                            (("insert", WC_OP_INSERT), ("count", WC_OP_COUNT),
+                                             ("retrieve_multi", WC_OP_RETRIEVE))},
+                                 "l2": "no flush: 2.7 GB table, 1 GB inputs"}, clk, launches,
+            {"per_r": res["oa"], "bucket_per_r": res["bucket"],
+             "bucket_value": 2 * n * len(rs) / (total["bucket"] * 1e-3) / 1e9})
     api.wc_table_destroy(h)
 
 
