@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access roofline probe")
+    ap.add_argument("--no-overflow-bits", action="store_true",
+                    help="sv32: table without per-window overflow bits (lookups walk to an empty slot)")
     ap.add_argument("--workload", default="sv32",
                     choices=["sv32", "sv32_small", "sv64_zipf", "mv_zipf", "mv_oa_uniform_r", "served"],
                     help="sv32 (default): 2^27 uint32 pairs at load 0.9, insert + 50%% absent retrieve; "
@@ -269,8 +271,9 @@ def run_wc(args, rank, world, local_rank):
     qk = to_device(d["queries"], 4, dev)
     out = torch.empty(n, dtype=torch.int32, device=dev)
     found = torch.empty(n, dtype=torch.uint8, device=dev)
+    opts = 0 if args.no_overflow_bits else wc.WC_OPT_OVERFLOW_BITS  # half the queries are absent
     h = api.wc_table_create(wc.WC_SINGLE_VALUE, 4, 4, int(np.ceil(n / args.alpha)), args.window, 0,
-                            0x5EEDC0DE + rank, local_rank)
+                            0x5EEDC0DE + rank, local_rank, options=opts)
     info = api.wc_table_get_info(h)
     if args.group:
         for op in (wc.WC_OP_INSERT, wc.WC_OP_RETRIEVE, wc.WC_OP_ERASE):
@@ -375,7 +378,7 @@ def run_wc(args, rank, world, local_rank):
         "config": {"workload": workload_name, "n": n, "queries": n, "present_fraction": 0.5,
                    "capacity": info["capacity"], "achieved_alpha": n / info["capacity"],
                    "window_slots": info["window_width"], "group_insert": g_ins, "group_retrieve": g_ret,
-                   "table_bytes": info["table_bytes"],
+                   "table_bytes": info["table_bytes"], "overflow_bits": bool(info["options"] & 1),
                    "l2": "no flush: inputs and table larger than L2 (table %.2f GB, keys %.2f GB)"
                          % (info["table_bytes"] / 1e9, n * 4 / 1e9),
                    "parallelism": "replicas (independent table per GPU)"},

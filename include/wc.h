@@ -94,6 +94,7 @@ enum { WC_SINGLE_VALUE = 0, WC_MULTI_VALUE = 1, WC_MULTI_VALUE_OA = 2 };
  *   device               CUDA device ordinal the table lives on.
  *   l2_persist           1 = launch this table's kernels with an L2 access-policy window
  *                        marking the slot array persisting (useful when it fits in L2).
+ *   options              WC_OPT_* bits (0 = none).
  */
 typedef struct {
   int32_t kind;
@@ -102,10 +103,23 @@ typedef struct {
   int32_t window_width;
   int32_t device;
   int32_t l2_persist;
+  int32_t options;
+  int32_t reserved;       /* 0 */
   uint64_t min_capacity;
   uint64_t value_pool_capacity;
   uint64_t seed;
 } wc_table_config;
+
+/* WC_OPT_OVERFLOW_BITS (single-value tables only; no counterpart in the paper): keep one
+ * overflow bit per window, set by an insert that walks past the window because it holds no
+ * empty slot.  Lookups and erases then stop at a window without the key, without an empty
+ * slot and with a clear bit -- a key stored further on would have set it -- instead of
+ * walking on to a window with an empty slot.  Shortens the walks of absent keys at high
+ * load (2^27 keys at load 0.9, half the queries absent: retrieve -8 %); costs present keys
+ * outside their first window one dependent read of the bit per window (skewed queries of
+ * present keys: slower), and inserts one atomic OR per window walked past.  The bits cost
+ * windows / 8 bytes. */
+enum { WC_OPT_OVERFLOW_BITS = 1 };
 
 /* Sizes of a created table (host copy; no device access). */
 typedef struct {
@@ -117,6 +131,8 @@ typedef struct {
   uint64_t device_bytes;    /* every device byte the table owns */
   int32_t window_width;     /* W */
   int32_t kind;
+  int32_t options;          /* WC_OPT_* bits the table was created with */
+  int32_t reserved;
 } wc_table_info;
 
 /* Launch shape of one operation class.  group_size = lanes that probe one key together
@@ -269,6 +285,11 @@ const char* wc_status_string(wc_status s);
  * layout as in wc_table_config) to host memory h_out of `bytes` >= table_bytes.
  * Synchronises stream.  Used by the slot-dump invariant checks of the tests. */
 wc_status wc_table_dump_slots(const wc_table* t, void* h_out, uint64_t bytes, void* stream);
+
+/* Copy a table's overflow bits (WC_OPT_OVERFLOW_BITS): ceil(windows / 32) uint32 words, bit
+ * w % 32 of word w / 32 = window w, to h_out (`words` >= that).  WC_ERR_UNSUPPORTED for a
+ * table without them.  Synchronises stream. */
+wc_status wc_table_dump_overflow_bits(const wc_table* t, uint32_t* h_out, uint64_t words, void* stream);
 
 /* Bytes of a whole-table snapshot: a header with the table's geometry, then its slots,
  * counters, status word and (multi-value) pending array and value pool. */

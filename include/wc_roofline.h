@@ -7,7 +7,9 @@
  *   - random reads of `access_bytes` contiguous, aligned bytes at uniformly random
  *     positions of a buffer (the window load of a probe), and
  *   - the same read followed by a 64-bit CAS on the first word (the slot claim of an
- *     insert).
+ *     insert), and
+ *   - random stores of `access_bytes` (the scatter of per-query results back to their
+ *     input positions).
  * Conventions as in wc.h (device pointers d_*, host pointers h_*, void* stream).
  */
 #ifndef WC_ROOFLINE_H_
@@ -25,15 +27,16 @@ typedef struct {
   uint64_t buffer_bytes;   /* bytes of d_buffer accessed (multiple of access_bytes) */
   uint64_t accesses;       /* number of random accesses */
   uint64_t seed;           /* positions are fmix64(seed ^ i) scaled to the buffer */
-  uint32_t access_bytes;   /* 8, 16, 32, 64 or 128 */
-  uint32_t mode;           /* 0 = read only, 1 = read then CAS (old -> old + 1) */
+  uint32_t access_bytes;   /* 8, 16, 32, 64 or 128 (mode 2 also 4) */
+  uint32_t mode;           /* 0 = read only, 1 = read then CAS (old -> old + 1), 2 = store */
   uint32_t block_threads;  /* 0 = 256 */
   uint32_t blocks_per_sm;  /* 0 = occupancy limit */
 } wc_rand_access_config;
 
 /* Launch the probe on `stream` over d_buffer (device, buffer_bytes, 256-byte aligned).
  * d_sink (device, one uint64) receives an XOR of everything read, so the loads cannot be
- * elided.  Asynchronous; time it with events on `stream`. */
+ * elided (unused by mode 2, still required).  Mode 2 overwrites the buffer.
+ * Asynchronous; time it with events on `stream`. */
 wc_status wc_bench_random_access(void* d_buffer, const wc_rand_access_config* cfg, uint64_t* d_sink,
                                  void* stream);
 

@@ -59,7 +59,7 @@ def _load():
         lib.oracle_num_keys.argtypes = [vp]
         lib.oracle_reserve.argtypes = [vp, u64]
         lib.oracle_check_slots.restype = ctypes.c_int
-        lib.oracle_check_slots.argtypes = [vp, u64, u32, u32, u64, ctypes.c_int, vp, vp, vp]
+        lib.oracle_check_slots.argtypes = [vp, u64, u32, u32, u64, ctypes.c_int, vp, vp, vp, vp]
         _lib = lib
     return _lib
 
@@ -157,15 +157,24 @@ def sorted_segments(values: np.ndarray, offsets: np.ndarray) -> np.ndarray:
     return out[order]
 
 
-def check_slots(dump: np.ndarray, p: int, W: int, slot_bytes: int, seed: int, unique_keys: bool) -> dict:
+def check_slots(dump: np.ndarray, p: int, W: int, slot_bytes: int, seed: int, unique_keys: bool,
+                overflow_bits: np.ndarray | None = None) -> dict:
     """Slot-dump invariant check of a table's slot array (host bytes, p * W slots):
     live slots, duplicate keys (when keys must be unique) and live keys that sit behind
-    a window holding an empty slot on their own probing sequence (see oracle.cpp)."""
+    a window holding an empty slot on their own probing sequence -- or, when the table's
+    overflow bits are given (uint32 words, bit w = window w), behind a window whose bit is
+    clear (see oracle.cpp)."""
     buf = np.ascontiguousarray(dump).view(np.uint8)
     if buf.size < p * W * slot_bytes:
         raise ValueError("dump holds %d bytes, need %d" % (buf.size, p * W * slot_bytes))
     out = np.zeros(3, dtype=np.uint64)
+    ovf = None
+    if overflow_bits is not None:
+        ovf = np.ascontiguousarray(overflow_bits).view(np.uint32)
+        if ovf.size < (p + 31) // 32:
+            raise ValueError("overflow bits hold %d words, need %d" % (ovf.size, (p + 31) // 32))
     rc = _load().oracle_check_slots(_ptr(buf), p, W, slot_bytes, seed & (2 ** 64 - 1), int(unique_keys),
+                                    None if ovf is None else _ptr(ovf),
                                     _ptr(out[0:]), ctypes.c_void_p(out.ctypes.data + 8),
                                     ctypes.c_void_p(out.ctypes.data + 16))
     if rc != 0:

@@ -270,7 +270,10 @@ void oracle_reserve(void* p, uint64_t n) {
 //     holding it comes no later than the first window that holds an empty slot (a slot
 //     only moves empty -> key -> tombstone -> key, so nothing may sit behind an empty
 //     window of its own sequence);
-//   * uniqueness (single-value tables and key stores, Sec. IV: each key occurs once).
+//   * uniqueness (single-value tables and key stores, Sec. IV: each key occurs once);
+//   * with the table's overflow bits (one per window, optional): every window a live key's
+//     sequence passes before the key's own window has its bit set, since lookups stop at a
+//     window without the key, without an empty slot and with a clear bit.
 // The probing sequence is the table's definition restated here: h = fmix64(key ^ seed)
 // (MurmurHash3's 64-bit finalizer), w_0 = floor(hi32(h) * p / 2^32),
 // step = 1 + floor(lo32(h) * (p - 1) / 2^32), w_{j+1} = (w_j + step) mod p; windows are
@@ -302,8 +305,8 @@ uint64_t chk_key(const unsigned char* slots, uint64_t i, uint32_t slot_bytes) {
 }  // namespace
 
 extern "C" int oracle_check_slots(const void* dump, uint64_t p, uint32_t W, uint32_t slot_bytes, uint64_t seed,
-                                  int unique_keys, uint64_t* out_live, uint64_t* out_dups,
-                                  uint64_t* out_unreachable) {
+                                  int unique_keys, const uint32_t* ovf_or_null, uint64_t* out_live,
+                                  uint64_t* out_dups, uint64_t* out_unreachable) {
   if (dump == nullptr || p < 2 || W == 0 || (slot_bytes != 8 && slot_bytes != 16)) return -1;
   const unsigned char* s = static_cast<const unsigned char*>(dump);
   const uint64_t cap = p * W;
@@ -326,6 +329,7 @@ extern "C" int oracle_check_slots(const void* dump, uint64_t p, uint32_t W, uint
     for (uint64_t j = 0; j < p; ++j) {
       if (w == home) { ok = true; break; }
       if (has_empty[w]) break;
+      if (ovf_or_null != nullptr && !((ovf_or_null[w >> 5] >> (w & 31)) & 1u)) break;
       w = (w + step) % p;
     }
     if (!ok) ++unreachable;

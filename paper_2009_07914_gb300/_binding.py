@@ -33,6 +33,7 @@ WC_FLAG_QUEUE_TIMEOUT = 32
 WC_SINGLE_VALUE = 0
 WC_MULTI_VALUE = 1
 WC_MULTI_VALUE_OA = 2
+WC_OPT_OVERFLOW_BITS = 1
 
 WC_SCHEME_AUTO = 0
 WC_SCHEME_DIRECT = 1
@@ -47,6 +48,7 @@ WC_OP_COUNT = 3
 class WcTableConfig(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("key_bytes", ctypes.c_int32), ("value_bytes", ctypes.c_int32),
                 ("window_width", ctypes.c_int32), ("device", ctypes.c_int32), ("l2_persist", ctypes.c_int32),
+                ("options", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("min_capacity", ctypes.c_uint64), ("value_pool_capacity", ctypes.c_uint64),
                 ("seed", ctypes.c_uint64)]
 
@@ -54,7 +56,8 @@ class WcTableConfig(ctypes.Structure):
 class WcTableInfo(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_uint64), ("windows", ctypes.c_uint64), ("slot_bytes", ctypes.c_uint64),
                 ("table_bytes", ctypes.c_uint64), ("pool_capacity", ctypes.c_uint64),
-                ("device_bytes", ctypes.c_uint64), ("window_width", ctypes.c_int32), ("kind", ctypes.c_int32)]
+                ("device_bytes", ctypes.c_uint64), ("window_width", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("options", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class WcLaunch(ctypes.Structure):
@@ -92,6 +95,7 @@ _SIGS = {
     "wc_get_status": (ctypes.c_int, [_vp, ctypes.POINTER(_u32), _i32, _vp]),
     "wc_check_status": (ctypes.c_int, [_vp, ctypes.POINTER(_u32), _vp]),
     "wc_table_dump_slots": (ctypes.c_int, [_vp, _vp, _u64, _vp]),
+    "wc_table_dump_overflow_bits": (ctypes.c_int, [_vp, _vp, _u64, _vp]),
     "wc_table_snapshot_bytes": (_u64, [_vp]),
     "wc_table_snapshot": (ctypes.c_int, [_vp, _vp, _u64, _vp]),
     "wc_table_restore": (ctypes.c_int, [_vp, _vp, _u64, _vp]),

@@ -13,8 +13,8 @@ import numpy as np
 import torch
 
 from . import _binding as B
-from ._binding import (WC_MULTI_VALUE, WC_MULTI_VALUE_OA, WC_SINGLE_VALUE, WcLaunch, WcTableConfig, WcTableInfo, check, lib, ptr,
-                       stream_handle)
+from ._binding import (WC_MULTI_VALUE, WC_MULTI_VALUE_OA, WC_OPT_OVERFLOW_BITS, WC_SINGLE_VALUE, WcLaunch,
+                       WcTableConfig, WcTableInfo, check, lib, ptr, stream_handle)
 
 __all__ = [
     "wc_plan_capacity", "wc_table_create", "wc_table_destroy", "wc_table_clear", "wc_table_get_info",
@@ -52,11 +52,12 @@ def wc_plan_capacity(min_capacity: int, window_width: int) -> tuple[int, int]:
 
 def wc_table_create(kind: int = WC_SINGLE_VALUE, key_bytes: int = 4, value_bytes: int = 4, min_capacity: int = 1024,
                     window_width: int = 0, value_pool_capacity: int = 0, seed: int = 0x5EED_C0DE,
-                    device: int | None = None, l2_persist: bool = False) -> int:
+                    device: int | None = None, l2_persist: bool = False, options: int = 0) -> int:
     if device is None:
         device = torch.cuda.current_device()
     cfg = WcTableConfig(kind=kind, key_bytes=key_bytes, value_bytes=value_bytes, window_width=window_width,
-                        device=device, l2_persist=1 if l2_persist else 0, min_capacity=int(min_capacity),
+                        device=device, l2_persist=1 if l2_persist else 0, options=int(options), reserved=0,
+                        min_capacity=int(min_capacity),
                         value_pool_capacity=int(value_pool_capacity), seed=int(seed) & (2 ** 64 - 1))
     h = ctypes.c_void_p()
     check(lib().wc_table_create(ctypes.byref(h), ctypes.byref(cfg)), "wc_table_create")
@@ -186,6 +187,15 @@ def wc_table_dump_slots(t: int, stream=None) -> np.ndarray:
     return out
 
 
+def wc_table_dump_overflow_bits(t: int, stream=None) -> np.ndarray:
+    """Host copy of a single-value table's overflow bits (uint32 words, bit w = window w)."""
+    info = wc_table_get_info(t)
+    out = np.empty((info["windows"] + 31) // 32, dtype=np.uint32)
+    check(lib().wc_table_dump_overflow_bits(t, out.ctypes.data, out.size, stream_handle(stream)),
+          "wc_table_dump_overflow_bits")
+    return out
+
+
 def wc_table_snapshot_bytes(t: int) -> int:
     return int(lib().wc_table_snapshot_bytes(t))
 
@@ -205,6 +215,7 @@ def wc_debug_fail_allocations(count: int):
     check(lib().wc_debug_fail_allocations(count), "wc_debug_fail_allocations")
 
 
-__all__ += ["wc_check_status", "wc_table_dump_slots", "wc_table_snapshot_bytes", "wc_table_snapshot",
+__all__ += ["wc_check_status", "wc_table_dump_slots", "wc_table_dump_overflow_bits", "wc_table_snapshot_bytes",
+            "wc_table_snapshot",
             "wc_table_restore", "wc_debug_fail_allocations"]
-__all__ += ["WC_SINGLE_VALUE", "WC_MULTI_VALUE", "WC_MULTI_VALUE_OA"]
+__all__ += ["WC_SINGLE_VALUE", "WC_MULTI_VALUE", "WC_MULTI_VALUE_OA", "WC_OPT_OVERFLOW_BITS"]

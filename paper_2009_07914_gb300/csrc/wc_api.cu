@@ -144,6 +144,7 @@ TableDesc desc_of(const wc_table* t) {
   d.status = t->d_status;
   d.size = t->d_size;
   d.nkeys = t->d_nkeys;
+  d.ovf = t->d_ovf;
   d.p = static_cast<uint32_t>(t->windows);
   d.W = static_cast<uint32_t>(t->W);
   return d;
@@ -287,6 +288,8 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) return WC_ERR_CUDA;
   const bool mv = cfg->kind == WC_MULTI_VALUE;
   const bool oa = cfg->kind == WC_MULTI_VALUE_OA;
+  if ((cfg->options & ~WC_OPT_OVERFLOW_BITS) != 0 || cfg->reserved != 0) return WC_ERR_INVALID_ARG;
+  if ((cfg->options & WC_OPT_OVERFLOW_BITS) && cfg->kind != WC_SINGLE_VALUE) return WC_ERR_INVALID_ARG;
   if (mv && cfg->value_pool_capacity > kMaxPool) return WC_ERR_INVALID_ARG;
 
   uint64_t p = 0, cap = 0;
@@ -307,9 +310,12 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   DeviceGuard guard(t->device);
   t->sm_count = sm_count_of(t->device);
 
-  // One allocation: [slots | meta 256 B | pending (MV) | scan partials (MV, OA) | pool (MV)]
+  // One allocation: [slots | meta 256 B | overflow bits (SV) | pending (MV) | scan partials (MV, OA) | pool (MV)]
+  const bool sv = cfg->kind == WC_SINGLE_VALUE && (cfg->options & WC_OPT_OVERFLOW_BITS);
   const uint64_t off_meta = align_up(t->table_bytes, kAlign);
-  const uint64_t off_pending = off_meta + kAlign;
+  const uint64_t off_ovf = off_meta + kAlign;
+  const uint64_t ovf_bytes = sv ? align_up((p + 31) / 32 * 4, kAlign) : 0;
+  const uint64_t off_pending = off_ovf + ovf_bytes;
   const uint64_t pending_bytes = mv ? align_up(cap * 4, kAlign) : 0;
   const uint64_t off_partials = off_pending + pending_bytes;
   t->partials_cap = mv || oa ? scan_partials_needed(kMaxBatch + 1) : 0;
@@ -329,6 +335,7 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   t->d_size = reinterpret_cast<unsigned long long*>(base + off_meta + 8);
   t->d_nkeys = reinterpret_cast<unsigned long long*>(base + off_meta + 16);
   t->d_cursor = reinterpret_cast<unsigned long long*>(base + off_meta + 24);
+  t->d_ovf = sv ? reinterpret_cast<uint32_t*>(base + off_ovf) : nullptr;
   t->d_pending = mv ? reinterpret_cast<uint32_t*>(base + off_pending) : nullptr;
   t->d_partials = mv || oa ? reinterpret_cast<uint64_t*>(base + off_partials) : nullptr;
   t->d_pool = mv ? static_cast<void*>(base + off_pool) : nullptr;
@@ -399,6 +406,8 @@ wc_status wc_table_get_info(const wc_table* t, wc_table_info* h_out) {
   h_out->device_bytes = t->device_bytes;
   h_out->window_width = static_cast<int32_t>(t->W);
   h_out->kind = t->cfg.kind;
+  h_out->options = t->cfg.options;
+  h_out->reserved = 0;
   return WC_OK;
 }
 
@@ -410,7 +419,8 @@ wc_status wc_table_set_launch(wc_table* t, int32_t op, const wc_launch* launch) 
   if (launch->scheme < WC_SCHEME_AUTO || launch->scheme > WC_SCHEME_BLOCKED || launch->region_mib < 0 ||
       launch->region_mib > 4096)
     return WC_ERR_INVALID_ARG;
-  if (launch->scheme == WC_SCHEME_BLOCKED && (op != WC_OP_INSERT || t->cfg.kind == WC_MULTI_VALUE))
+  if (launch->scheme == WC_SCHEME_BLOCKED &&
+      !((op == WC_OP_INSERT && t->cfg.kind != WC_MULTI_VALUE) || (op == WC_OP_RETRIEVE && t->cfg.kind == WC_SINGLE_VALUE)))
     return WC_ERR_UNSUPPORTED;
   if (!shape_ok(t, op, launch->group_size)) return WC_ERR_INVALID_ARG;
   t->launch[op] = *launch;

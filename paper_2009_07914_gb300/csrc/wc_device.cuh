@@ -104,6 +104,20 @@ __device__ __forceinline__ unsigned long long ldg_stream(const unsigned long lon
   return v;
 }
 
+// ---- overflow bits --------------------------------------------------------------------
+// One bit per window, set by an insert that walks past the window because it holds no
+// empty slot.  Every key stored beyond a window on its own sequence has passed that window,
+// so a lookup that meets a window without the key, without an empty slot and with a clear
+// bit may stop there: the key is absent.  The bits only ever get set (a clear resets them),
+// so they stay a superset of what lookups need after erases and re-inserts.
+__device__ __forceinline__ uint32_t ovf_word(const uint32_t* ovf, uint32_t w) {
+  uint32_t v;
+  asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(ovf + (w >> 5)));
+  return v;
+}
+__device__ __forceinline__ bool ovf_bit(uint32_t word, uint32_t w) { return (word >> (w & 31u)) & 1u; }
+__device__ __forceinline__ void ovf_mark(uint32_t* ovf, uint32_t w) { atomicOr(ovf + (w >> 5), 1u << (w & 31u)); }
+
 // ---- slot layouts ---------------------------------------------------------------------
 
 // Packed array-of-structs slot (Sec. IV-B1): a uint32 key in the low half and a uint32

@@ -75,6 +75,18 @@ wc_status wc_table_dump_slots(const wc_table* t, void* h_out, uint64_t bytes, vo
   return to_status(e);
 }
 
+wc_status wc_table_dump_overflow_bits(const wc_table* t, uint32_t* h_out, uint64_t words, void* stream) {
+  if (t == nullptr || h_out == nullptr) return WC_ERR_INVALID_ARG;
+  if (t->d_ovf == nullptr) return WC_ERR_UNSUPPORTED;
+  const uint64_t need = (t->windows + 31) / 32;
+  if (words < need) return WC_ERR_INVALID_ARG;
+  DevGuard g(t->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(h_out, t->d_ovf, need * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return to_status(e);
+}
+
 uint64_t wc_table_snapshot_bytes(const wc_table* t) {
   if (t == nullptr) return 0;
   const uint64_t pool_bytes = t->d_pool ? t->device_bytes - pool_offset(t) : 0;

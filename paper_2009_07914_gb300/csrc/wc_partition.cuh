@@ -27,15 +27,26 @@ struct RegionMap {
   uint32_t p;    // windows of the table
   uint32_t wpr;  // windows per region
   uint32_t R;    // regions
+  template <class K>
+  __device__ __forceinline__ uint32_t of(K key) const {
+    uint32_t w, step;
+    probe_init(static_cast<uint64_t>(key), seed, p, w, step);
+    const uint32_t r = w / wpr;
+    return r < R ? r : R - 1;
+  }
 };
 
-template <class K>
-__device__ __forceinline__ uint32_t region_of(const RegionMap& m, K key) {
-  uint32_t w, step;
-  probe_init(static_cast<uint64_t>(key), m.seed, m.p, w, step);
-  const uint32_t r = w / m.wpr;
-  return r < m.R ? r : m.R - 1;
-}
+// Region of an output position: `per` consecutive positions per region.  Bit 31 of the
+// word carries a flag (the found bit of a retrieve result) and is not part of the
+// position.
+struct IndexMap {
+  uint32_t per;
+  uint32_t R;
+  __device__ __forceinline__ uint32_t of(uint32_t x) const {
+    const uint32_t r = (x & 0x7fffffffu) / per;
+    return r < R ? r : R - 1;
+  }
+};
 
 // Per-region counts of the batch (hist[R], zeroed by the caller).  Each warp keeps its
 // own shared-memory histogram, so atomics only collide inside a warp.
@@ -50,7 +61,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_hist(const K* __restrict_
   unsigned int* mine = s_hw + (threadIdx.x >> 5) * m.R;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kPartThreads;
   for (uint64_t e = static_cast<uint64_t>(blockIdx.x) * kPartThreads + threadIdx.x; e < n; e += stride)
-    atomicAdd(mine + region_of(m, ldg_stream(keys + e)), 1u);
+    atomicAdd(mine + m.of(ldg_stream(keys + e)), 1u);
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < m.R; i += kPartThreads) {
     unsigned int c = 0;
@@ -116,9 +127,10 @@ struct ScatterSmem {
   unsigned int w32[kPartThreads / 32];
 };
 
-template <class K, class V>
+// kIota: the value of element i is its input position i (vals is not read).
+template <class K, class V, class M = RegionMap, bool kIota = false>
 __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const K* __restrict__ keys, const V* __restrict__ vals,
-                                                               uint64_t n, RegionMap m,
+                                                               uint64_t n, M m,
                                                                const unsigned int* __restrict__ hist,
                                                                unsigned long long* __restrict__ cursor,
                                                                K* __restrict__ okeys, V* __restrict__ ovals) {
@@ -143,8 +155,12 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const K* __restri
       rr[k] = 0xffffffffu;
       if (i < tn) {
         kk[k] = ldg_stream(keys + t0 + i);
-        vv[k] = ldg_stream(vals + t0 + i);
-        rr[k] = region_of(m, kk[k]);
+        if constexpr (kIota) {
+          vv[k] = static_cast<V>(t0 + i);
+        } else {
+          vv[k] = ldg_stream(vals + t0 + i);
+        }
+        rr[k] = m.of(kk[k]);
         rank[k] = atomicAdd(S.cnt + rr[k], 1u);
       }
     }
@@ -164,8 +180,10 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const K* __restri
     for (uint32_t i = threadIdx.x; i < tn; i += kPartThreads) {
       const uint32_t r = S.reg[i];
       const uint64_t o = S.pos[r] + (i - S.toff[r]);
-      okeys[o] = S.keys[i];
-      ovals[o] = S.vals[i];
+      if (o < n) {  // always true when hist holds this batch's counts
+        okeys[o] = S.keys[i];
+        ovals[o] = S.vals[i];
+      }
     }
     __syncthreads();
   }
@@ -178,22 +196,33 @@ constexpr size_t scatter_smem_bytes() {
 
 // ---- host side -------------------------------------------------------------------------
 // A batch split by table region in the table's scratch buffer, plus kSplitCounters zeroed
-// chunk counters for the ordered sweeps of the kernels that consume it.
+// chunk counters for the ordered sweeps of the kernels that consume it, and a zeroed
+// area for a second split (hist2 / cursor2) and `extra` bytes the caller asked for.
 constexpr int kSplitCounters = 32;
+constexpr uint64_t kSplitHist = 0, kSplitCursor = 8192, kSplitCnt = 16384, kSplitHist2 = 16640,
+                   kSplitCursor2 = 20736, kSplitHeader = 29184;
+static_assert(kMaxRegions * sizeof(unsigned int) <= kSplitCursor2 - kSplitHist2, "hist2 area");
+static_assert(kMaxRegions * sizeof(unsigned long long) <= kSplitHeader - kSplitCursor2, "cursor2 area");
 
 template <class K, class V>
 struct RegionSplit {
   const K* keys;
   const V* vals;
   unsigned long long* counters;
+  unsigned int* hist2;          // second split: per-region counts (zeroed)
+  unsigned long long* cursor2;  // second split: per-region cursors (zeroed)
+  char* extra;                  // `extra` bytes, 256-byte aligned (not zeroed)
 };
 
+inline uint64_t align256(uint64_t x) { return (x + 255) / 256 * 256; }
+
 // Regions of about region_mib MiB of slots (at most kMaxRegions of them).  Scratch layout:
-// [hist 8 KiB | cursor 8 KiB | counters 256 B | keys | vals], grown on demand.
-template <class K, class V>
+// [header kSplitHeader B | keys | vals | extra], grown on demand.  kIota: the values are
+// the input positions (uint32), `vals` is not read.
+template <class K, class V, bool kIota = false>
 cudaError_t region_split(const wc_table* t, int region_mib, const K* keys, const V* vals, uint64_t n, cudaStream_t s,
-                         RegionSplit<K, V>& out) {
-  static_assert(kMaxRegions * sizeof(unsigned long long) <= 8192, "cursor area");
+                         RegionSplit<K, V>& out, uint64_t extra = 0) {
+  static_assert(kMaxRegions * sizeof(unsigned long long) <= kSplitCnt - kSplitCursor, "cursor area");
   RegionMap m;
   m.seed = t->cfg.seed;
   m.p = static_cast<uint32_t>(t->windows);
@@ -202,19 +231,20 @@ cudaError_t region_split(const wc_table* t, int region_mib, const K* keys, const
   if ((t->windows + wpr - 1) / wpr > static_cast<uint64_t>(kMaxRegions)) wpr = (t->windows + kMaxRegions - 1) / kMaxRegions;
   m.wpr = static_cast<uint32_t>(wpr);
   m.R = static_cast<uint32_t>((t->windows + wpr - 1) / wpr);
-  const uint64_t cur_off = 8192, cnt_off = cur_off + 8192, keys_off = cnt_off + 256;
-  const uint64_t vals_off = keys_off + (n * sizeof(K) + 255) / 256 * 256;
-  cudaError_t e = ensure_scratch(t, vals_off + n * sizeof(V), s);
+  const uint64_t keys_off = kSplitHeader;
+  const uint64_t vals_off = keys_off + align256(n * sizeof(K));
+  const uint64_t extra_off = vals_off + align256(n * sizeof(V));
+  cudaError_t e = ensure_scratch(t, extra_off + extra, s);
   if (e != cudaSuccess) return e;
   char* sc = static_cast<char*>(t->d_scratch);
-  auto* hist = reinterpret_cast<unsigned int*>(sc);
-  auto* cursor = reinterpret_cast<unsigned long long*>(sc + cur_off);
+  auto* hist = reinterpret_cast<unsigned int*>(sc + kSplitHist);
+  auto* cursor = reinterpret_cast<unsigned long long*>(sc + kSplitCursor);
   K* pk = reinterpret_cast<K*>(sc + keys_off);
   V* pv = reinterpret_cast<V*>(sc + vals_off);
-  e = cudaMemsetAsync(sc, 0, keys_off, s);
+  e = cudaMemsetAsync(sc, 0, kSplitHeader, s);
   if (e != cudaSuccess) return e;
   auto hk = k_part_hist<K>;
-  auto sk = k_part_scatter<K, V>;
+  auto sk = k_part_scatter<K, V, RegionMap, kIota>;
   const size_t hsm = static_cast<size_t>(kHistWarps) * m.R * sizeof(unsigned int);
   const size_t ssm = scatter_smem_bytes<K, V>();
   static bool attr = false;
@@ -233,7 +263,10 @@ cudaError_t region_split(const wc_table* t, int region_mib, const K* keys, const
   e = cudaGetLastError();
   out.keys = pk;
   out.vals = pv;
-  out.counters = reinterpret_cast<unsigned long long*>(sc + cnt_off);
+  out.counters = reinterpret_cast<unsigned long long*>(sc + kSplitCnt);
+  out.hist2 = reinterpret_cast<unsigned int*>(sc + kSplitHist2);
+  out.cursor2 = reinterpret_cast<unsigned long long*>(sc + kSplitCursor2);
+  out.extra = sc + extra_off;
   return e;
 }
 

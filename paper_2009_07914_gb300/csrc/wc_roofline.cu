@@ -70,8 +70,41 @@ __global__ void __launch_bounds__(256) k_rand_access(unsigned long long* buf, ui
   if (acc == seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull) *sink = acc;  // practically never taken
 }
 
+// Random stores of BYTES (the scatter of results to their input positions): thread-
+// varying data, no read of the target.
+template <int BYTES>
+__global__ void __launch_bounds__(256) k_rand_write(unsigned long long* buf, uint64_t chunks, uint64_t accesses,
+                                                    uint64_t seed) {
+  const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const uint64_t nth = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = tid; i < accesses; i += nth) {
+    const uint64_t h = fmix64(seed ^ i);
+    const uint64_t c = __umul64hi(h, chunks);
+    char* p = reinterpret_cast<char*>(buf) + c * BYTES;
+    if constexpr (BYTES == 4) {
+      *reinterpret_cast<uint32_t*>(p) = static_cast<uint32_t>(h);
+    } else {
+#pragma unroll
+      for (int w = 0; w < BYTES / 8; ++w) reinterpret_cast<unsigned long long*>(p)[w] = h + w;
+    }
+  }
+}
+
+template <int BYTES>
+cudaError_t run_write(void* buf, const wc_rand_access_config& c, cudaStream_t s) {
+  const int block = c.block_threads ? static_cast<int>(c.block_threads) : 256;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto kern = k_rand_write<BYTES>;
+  const int bps = c.blocks_per_sm ? static_cast<int>(c.blocks_per_sm) : occupancy(kern, block);
+  kern<<<bps * sm_count_of(dev), block, 0, s>>>(static_cast<unsigned long long*>(buf), c.buffer_bytes / BYTES,
+                                                c.accesses, c.seed);
+  return cudaGetLastError();
+}
+
 template <int BYTES>
 cudaError_t run(void* buf, const wc_rand_access_config& c, uint64_t* sink, cudaStream_t s) {
+  if (c.mode == 2) return run_write<BYTES>(buf, c, s);
   const int block = c.block_threads ? static_cast<int>(c.block_threads) : 256;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -100,8 +133,8 @@ wc_status wc_bench_random_access(void* d_buffer, const wc_rand_access_config* cf
                                  void* stream) {
   if (d_buffer == nullptr || cfg == nullptr || d_sink == nullptr) return WC_ERR_INVALID_ARG;
   const uint32_t a = cfg->access_bytes;
-  if (!(a == 8 || a == 16 || a == 32 || a == 64 || a == 128) || cfg->buffer_bytes < a ||
-      cfg->buffer_bytes % a != 0 || cfg->mode > 1)
+  if (!(a == 8 || a == 16 || a == 32 || a == 64 || a == 128 || (a == 4 && cfg->mode == 2)) ||
+      cfg->buffer_bytes < a || cfg->buffer_bytes % a != 0 || cfg->mode > 2)
     return WC_ERR_INVALID_ARG;
   if (cfg->block_threads && (cfg->block_threads > 256 || cfg->block_threads % 32)) return WC_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(d_buffer) % 256) return WC_ERR_INVALID_ARG;
@@ -109,6 +142,7 @@ wc_status wc_bench_random_access(void* d_buffer, const wc_rand_access_config* cf
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   switch (a) {
+    case 4: e = wc::run_write<4>(d_buffer, *cfg, s); break;
     case 8: e = wc::run<8>(d_buffer, *cfg, d_sink, s); break;
     case 16: e = wc::run<16>(d_buffer, *cfg, d_sink, s); break;
     case 32: e = wc::run<32>(d_buffer, *cfg, d_sink, s); break;

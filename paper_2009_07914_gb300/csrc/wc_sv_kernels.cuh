@@ -205,13 +205,16 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
     }
     const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
     const uint32_t be = group_vote<G>(me != 0, ln.gbase);
+    // the overflow bit only matters for a window without the key and without an empty slot
+    uint32_t fw = 0xffffffffu;
+    if (t.ovf != nullptr && act && !bm && !be) fw = ovf_word(t.ovf, w);
     Slot hit = pick<L, S>(s, mm ? __ffs(mm) - 1 : 0);
     if constexpr (G > 1) hit = L::shfl(hit, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
     if (act) {
       if (bm) {
         if (ln.r == 0) emit(pos, true, hit);
         act = false;
-      } else if (be || ++j >= t.p) {
+      } else if (be || !ovf_bit(fw, w) || ++j >= t.p) {
         if (ln.r == 0) emit(pos, false, hit);
         act = false;
       } else {
@@ -241,6 +244,61 @@ __global__ void __launch_bounds__(256) k_sv_retrieve(TableDesc t, const typename
   EmitValue<L> emit{out, found};
   sv_retrieve_range<L, G, S>(t, keys, src, emit, flags);
   flush_flags(t.status, flags);
+}
+
+// Retrieve over a batch split by table region (the blocked scheme): warps pull chunks in
+// order, so the probes sweep the table region by region with the active regions in L2.
+// Results are written in the split order: rv[i] = value (or NOT_FOUND), rk[i] = the
+// query's input position qpos[i] with bit 31 set when found; a second split by position
+// and a placement pass put them back in input order.
+template <class L>
+struct EmitSwept {
+  const uint32_t* __restrict__ qpos;
+  uint32_t* __restrict__ rk;
+  typename L::Val* __restrict__ rv;
+  __device__ void operator()(uint64_t i, bool hit, const typename L::Slot& s) const {
+    rv[i] = hit ? L::val(s) : L::kNotFound;
+    rk[i] = qpos[i] | (hit ? 0x80000000u : 0u);
+  }
+};
+
+template <class L, int G, int S>
+__global__ void __launch_bounds__(256) k_sv_retrieve_swept(TableDesc t, const typename L::Key* __restrict__ keys,
+                                                           const uint32_t* __restrict__ qpos, uint64_t n,
+                                                           unsigned long long* counter, uint32_t chunk,
+                                                           uint32_t* __restrict__ rk,
+                                                           typename L::Val* __restrict__ rv) {
+  RangeSrc src(n, 0, counter, chunk);
+  uint32_t flags = 0;
+  EmitSwept<L> emit{qpos, rk, rv};
+  sv_retrieve_range<L, G, S>(t, keys, src, emit, flags);
+  flush_flags(t.status, flags);
+}
+
+// Placement of split-ordered results: out[pos] = value, found[pos] = bit 31 of rk.  The
+// input is grouped by position region and the grid walks it front to back, so the
+// scattered stores of a moment fall into one or two L2-sized output regions.
+template <class V>
+__global__ void __launch_bounds__(256) k_place_results(const uint32_t* __restrict__ rk, const V* __restrict__ rv,
+                                                       uint64_t n, V* __restrict__ out, uint8_t* __restrict__ found) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t k = ldg_stream(rk + i);
+    const V v = ldg_stream(rv + i);
+    const uint32_t pos = k & 0x7fffffffu;
+    out[pos] = v;
+    if (found) found[pos] = static_cast<uint8_t>(k >> 31);
+  }
+}
+
+// Exact per-region counts of the positions 0..n-1 (region r holds positions
+// [r * per, (r + 1) * per), the last one the rest).
+static __global__ void k_index_hist(unsigned int* __restrict__ hist, uint32_t R, uint32_t per, uint64_t n) {
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+    const uint64_t lo = static_cast<uint64_t>(r) * per;
+    const uint64_t hi = r + 1 == R ? n : lo + per;
+    hist[r] = static_cast<unsigned int>(hi > lo ? hi - lo : 0);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -367,6 +425,7 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
           t_slot = nt_slot;
           t_word = nt_word;
         }
+        if (t.ovf != nullptr && ln.r == 0) ovf_mark(t.ovf, w);  // walking past a window without an empty slot
         ++j;
         w = probe_next(w, step, t.p);
       }
@@ -437,6 +496,8 @@ __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __
     }
     const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
     const uint32_t be = group_vote<G>(me != 0, ln.gbase);
+    uint32_t fw = 0xffffffffu;
+    if (t.ovf != nullptr && act && !bm && !be) fw = ovf_word(t.ovf, w);
     bool ok = false;
     if (act && bm && ln.r == __ffs(bm) - 1) {
       const int sub = __ffs(mm) - 1;
@@ -452,7 +513,7 @@ __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __
           act = false;
         }
         // else: another erase of the same key won; read the window again
-      } else if (be || ++j >= t.p) {
+      } else if (be || !ovf_bit(fw, w) || ++j >= t.p) {
         act = false;  // absent: nothing to erase
       } else {
         w = probe_next(w, step, t.p);

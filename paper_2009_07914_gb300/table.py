@@ -32,11 +32,11 @@ class _Table:
     kind = -1
 
     def __init__(self, key_bytes=4, value_bytes=4, min_capacity=1024, window_width=0, value_pool_capacity=0,
-                 seed=0x5EED_C0DE, device=None, l2_persist=False):
+                 seed=0x5EED_C0DE, device=None, l2_persist=False, options=0):
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.kb, self.vb = key_bytes, value_bytes
         self.handle = api.wc_table_create(self.kind, key_bytes, value_bytes, min_capacity, window_width,
-                                          value_pool_capacity, seed, self.device.index, l2_persist)
+                                          value_pool_capacity, seed, self.device.index, l2_persist, options)
         self.info = api.wc_table_get_info(self.handle)
 
     def close(self):

@@ -69,3 +69,31 @@ def test_status_strings(lib):
     from paper_2009_07914_gb300 import api
     assert api.wc_status_string(0) == "ok"
     assert "argument" in api.wc_status_string(1)
+
+
+def test_binding_structs_match_the_c_layouts(tmp_path):
+    """Every ctypes mirror of a header struct has the C struct's size and field offsets
+    (a mismatch would pass garbage across the C ABI)."""
+    import subprocess
+    from paper_2009_07914_gb300 import _binding, roofline, serve
+    pairs = [(_binding.WcTableConfig, "wc_table_config"), (_binding.WcTableInfo, "wc_table_info"),
+             (_binding.WcLaunch, "wc_launch"), (roofline.WcRandAccessConfig, "wc_rand_access_config"),
+             (serve.WcWork, "wc_work"), (serve.WcExecutorConfig, "wc_executor_config"),
+             (serve.WcRequest, "wc_request"), (serve.WcServeConfig, "wc_serve_config"),
+             (serve.WcRequestTiming, "wc_request_timing"), (serve.WcServeStats, "wc_serve_stats")]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "wc.h"', '#include "wc_exec.h"',
+             '#include "wc_serve.h"', '#include "wc_roofline.h"', "int main(void) {"]
+    want = []
+    for cls, cname in pairs:
+        lines.append('printf("%%zu\\n", sizeof(%s));' % cname)
+        want.append(ctypes.sizeof(cls))
+        for f in cls._fields_:
+            lines.append('printf("%%zu\\n", offsetof(%s, %s));' % (cname, f[0]))
+            want.append(getattr(cls, f[0]).offset)
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got == want

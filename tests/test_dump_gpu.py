@@ -27,15 +27,21 @@ def checked(wc, t, unique):
     info = t.info
     dump = wc.api.wc_table_dump_slots(t.handle)
     assert dump.size == info["table_bytes"]
-    return oracle.check_slots(dump, info["windows"], info["window_width"], info["slot_bytes"], SEED, unique)
+    r = oracle.check_slots(dump, info["windows"], info["window_width"], info["slot_bytes"], SEED, unique)
+    if info["options"] & 1:  # overflow bits: lookups also stop at a window whose bit is clear
+        bits = wc.api.wc_table_dump_overflow_bits(t.handle)
+        rb = oracle.check_slots(dump, info["windows"], info["window_width"], info["slot_bytes"], SEED, unique, bits)
+        assert rb == r
+    return r
 
 
+@pytest.mark.parametrize("opt", [0, 1])
 @pytest.mark.parametrize("kb,W", [(4, 4), (4, 8), (4, 32), (8, 2), (8, 4), (8, 16)])
-def test_single_value_dump_invariants_after_inserts_erases_reinserts(wc, kb, W):
+def test_single_value_dump_invariants_after_inserts_erases_reinserts(wc, kb, W, opt):
     n = 60_000
     keys = wc_inputs.distinct_u32(11, n) if kb == 4 else wc_inputs.distinct_u64(11, n)
     vals = keys.copy()
-    t = wc.SingleValueTable(kb, kb, min_capacity=int(n / 0.9), window_width=W, seed=SEED)
+    t = wc.SingleValueTable(kb, kb, min_capacity=int(n / 0.9), window_width=W, seed=SEED, options=opt)
     t.insert(keys, vals)
     t.erase(keys[::3])
     t.insert(keys[::6], vals[::6])  # half of the erased keys come back, over tombstones
@@ -133,7 +139,7 @@ def test_injected_allocation_failures(wc):
     with pytest.raises(wc.WcError) as e:
         wc.SingleValueTable(4, 4, min_capacity=1000)
     assert e.value.code == 2  # WC_ERR_OUT_OF_MEMORY
-    t = wc.SingleValueTable(4, 4, min_capacity=40_000_000, seed=SEED)  # next create works
+    t = wc.SingleValueTable(4, 4, min_capacity=40_000_000, seed=SEED, options=1)  # next create works
     n = 1 << 20
     keys = wc_inputs.distinct_u32(41, n)
     # the region-split insert's scratch allocation fails: error, table untouched

@@ -41,6 +41,7 @@ class Table:
         self.tomb = 0xFFFFFFFF if slot_bytes == 8 else M64
         self.keys = [0] * (p * W)
         self.where = {}
+        self.ovf = np.zeros((p + 31) // 32, dtype=np.uint32)  # overflow bit per window
 
     def insert(self, k):
         for j, w in enumerate(windows(k, self.seed, self.p)):
@@ -49,6 +50,7 @@ class Table:
                     self.keys[w * self.W + q] = k
                     self.where[k] = (w * self.W + q, j)
                     return True
+            self.ovf[w >> 5] |= np.uint32(1 << (w & 31))  # walked past a window without an empty slot
         return False
 
     def dump(self) -> np.ndarray:
@@ -61,8 +63,9 @@ class Table:
         out[:, 1] = 99
         return out.view(np.uint8).reshape(-1)
 
-    def check(self, seed=None, unique=True):
-        return oracle.check_slots(self.dump(), self.p, self.W, self.sb, self.seed if seed is None else seed, unique)
+    def check(self, seed=None, unique=True, bits=False):
+        return oracle.check_slots(self.dump(), self.p, self.W, self.sb, self.seed if seed is None else seed, unique,
+                                  self.ovf if bits else None)
 
 
 def filled(slot_bytes, p=101, W=8, n=600, seed=0xC0FFEE):
@@ -123,3 +126,20 @@ def test_geometry_is_validated():
         oracle.check_slots(np.zeros(10, np.uint8), 11, 8, 8, 0, True)
     with pytest.raises(ValueError):
         oracle.check_slots(np.zeros(11 * 8 * 12, np.uint8), 11, 8, 12, 0, True)
+
+
+@pytest.mark.parametrize("sb", [8, 16])
+def test_overflow_bits(sb):
+    """With overflow bits, a key is reachable only if every window its sequence passes
+    before its own has the bit set; the brute-force insert sets exactly those bits."""
+    t = filled(sb, n=700)
+    assert t.check(bits=True) == t.check() == {"live": len(t.where), "dups": 0, "unreachable": 0}
+    k, (slot, j) = next((k, v) for k, v in t.where.items() if v[1] >= 1)
+    first = next(windows(k, t.seed, t.p))
+    t.ovf[first >> 5] &= np.uint32(~(1 << (first & 31)) & 0xFFFFFFFF)
+    assert t.check()["unreachable"] == 0  # without the bits nothing changed
+    assert t.check(bits=True)["unreachable"] >= 1
+    assert oracle.check_slots(np.zeros(101 * 8 * sb, np.uint8), 101, 8, sb, 1, True, np.zeros(4, np.uint32))[
+        "unreachable"] == 0
+    with pytest.raises(ValueError):  # too few words for the window count
+        oracle.check_slots(t.dump(), t.p, t.W, t.sb, t.seed, True, np.zeros(1, np.uint32))

@@ -24,8 +24,8 @@ def wc():
     return wc
 
 
-def make_sv(wc, kb, vb, cap, W=0, G=None, seed=0x1234, scheme=0, region_mib=0):
-    t = wc.SingleValueTable(kb, vb, min_capacity=cap, window_width=W, seed=seed)
+def make_sv(wc, kb, vb, cap, W=0, G=None, seed=0x1234, scheme=0, region_mib=0, options=0):
+    t = wc.SingleValueTable(kb, vb, min_capacity=cap, window_width=W, seed=seed, options=options)
     if G is not None:
         for op in (wc.WC_OP_INSERT, wc.WC_OP_RETRIEVE, wc.WC_OP_ERASE):
             t.set_launch(op, G)
@@ -114,13 +114,15 @@ def test_sv_u64_parity_every_shape(wc, W, G):
     assert t.size() == o.size() == n
 
 
+@pytest.mark.parametrize("opt", [0, 1])
 @pytest.mark.parametrize("kb", [4, 8])
-def test_sv_random_op_sequences(wc, kb):
-    """Small key universe: heavy reuse of tombstones, duplicates inside batches."""
+def test_sv_random_op_sequences(wc, kb, opt):
+    """Small key universe: heavy reuse of tombstones, duplicates inside batches (with and
+    without overflow bits)."""
     rng = np.random.default_rng(kb)
     top = (1 << (8 * kb)) - 1
     universe = np.unique(rng.integers(1, min(top, 2 ** 62), 3000, dtype=np.uint64))
-    t = make_sv(wc, kb, kb, 4096)
+    t = make_sv(wc, kb, kb, 4096, options=opt)
     o = oracle.SingleValue(kb, kb)
     for step in range(40):
         m = int(rng.integers(1, 2000))
@@ -235,3 +237,86 @@ def test_blocked_insert_auto_scheme_on_large_table(wc):
     pres = d["q_src"] >= 0
     assert found[pres].all() and not found[~pres].any()
     np.testing.assert_array_equal(out[pres], d["values"][d["q_src"][pres]])
+
+
+@pytest.mark.parametrize("kb,W,G", [(4, 4, 1), (4, 8, 2), (4, 16, 4), (4, 32, 8), (8, 2, 1), (8, 4, 2), (8, 8, 4)])
+def test_blocked_retrieve_scheme_parity(wc, kb, W, G):
+    """Region-split (blocked) retrieve: split by table region, probe in region order,
+    split the results by output position, place them -- same values and found mask as
+    the oracle, with absent keys, repeated queries, sentinels and a ragged tail; also
+    without a found mask and for batches of 1 and 0 queries."""
+    n = 700_001
+    if kb == 4:
+        d = wc_inputs.sv_insert_retrieve_u32(0xB10D + W + G, n, n // 2, 400_000)
+        keys, vals, q = d["keys"], d["values"], d["queries"]
+    else:
+        allk = wc_inputs.distinct_u64(0xB10D + W + G, n + 400_000)
+        keys, vals = allk[:n], wc_inputs.uniform_u64(5, n)
+        q = allk[wc_inputs.shuffle_index(6, allk.size)]
+    q = np.concatenate([q, q[:5000], np.array([0, 2 ** (8 * kb) - 1] * 3, dtype=q.dtype)])
+    t = make_sv(wc, kb, kb, int(n / 0.9) + 1, W, G)
+    t.set_launch(wc.WC_OP_RETRIEVE, G, scheme=wc.WC_SCHEME_BLOCKED, region_mib=1)
+    o = oracle.SingleValue(kb, kb)
+    t.insert(keys, vals)
+    o.insert(keys, vals)
+    check_retrieve(t, o, q)
+    t.erase(keys[::4])
+    o.erase(keys[::4])
+    check_retrieve(t, o, q)
+    # without the found mask
+    import torch
+    qd = t.keys_dev(q)
+    out = torch.empty(q.size, dtype=torch.int32 if kb == 4 else torch.int64, device=qd.device)
+    wc.wc_retrieve(t.handle, qd, out, None)
+    assert wc.wc_get_status(t.handle, True) == oracle.FLAG_INVALID_KEY  # the sentinel queries
+    eo, _, _ = o.retrieve(q)
+    np.testing.assert_array_equal(out.cpu().numpy().view(eo.dtype), eo)
+    for m in (1, 0):
+        check_retrieve(t, o, q[:m])
+
+
+@pytest.mark.parametrize("kb,W,G", [(4, 4, 1), (4, 8, 2), (4, 16, 4), (4, 32, 8), (8, 2, 1), (8, 4, 2), (8, 8, 4),
+                                    (8, 16, 8)])
+def test_overflow_bits_parity(wc, kb, W, G):
+    """WC_OPT_OVERFLOW_BITS: lookups and erases that stop at a window with a clear overflow
+    bit give the oracle's results at load 0.95, through erases (tombstones), re-inserts,
+    overwrites and the blocked insert and retrieve schemes; the bits exist only on request
+    and only for single-value tables."""
+    n = 400_003
+    if kb == 4:
+        d = wc_inputs.sv_insert_retrieve_u32(0x0F1 + W + G, n, n // 2, 300_000)
+        keys, vals, q = d["keys"], d["values"], d["queries"]
+    else:
+        allk = wc_inputs.distinct_u64(0x0F1 + W + G, n + 300_000)
+        keys, vals = allk[:n], wc_inputs.uniform_u64(7, n)
+        q = allk[wc_inputs.shuffle_index(8, allk.size)]
+    t = make_sv(wc, kb, kb, int(n / 0.95) + 1, W, G, options=wc.WC_OPT_OVERFLOW_BITS)
+    assert t.info["options"] == wc.WC_OPT_OVERFLOW_BITS
+    o = oracle.SingleValue(kb, kb)
+    assert t.insert(keys, vals) == o.insert(keys, vals) == 0
+    check_retrieve(t, o, q)
+    drop = keys[: n // 2]
+    assert t.erase(drop) == o.erase(drop)
+    assert t.erase(drop[:1000]) == o.erase(drop[:1000])  # absent now: stops early, no-op
+    assert t.size() == o.size()
+    check_retrieve(t, o, q)
+    back = np.concatenate([drop[::3], keys[n // 2: n // 2 + 5000]])
+    bv = (vals[: back.size] ^ 0x33).astype(vals.dtype)
+    assert t.insert(back, bv) == o.insert(back, bv)
+    check_retrieve(t, o, q)
+    for op in (wc.WC_OP_INSERT, wc.WC_OP_RETRIEVE):
+        t.set_launch(op, G, scheme=wc.WC_SCHEME_BLOCKED, region_mib=1)
+    more = q[~np.isin(q, keys)][:20_000]
+    assert t.insert(more, more) == o.insert(more, more)
+    check_retrieve(t, o, q)
+    assert t.size() == o.size()
+
+
+def test_overflow_bits_only_for_single_value_tables(wc):
+    with pytest.raises(wc.WcError):
+        wc.MultiValueTable(8, 4, min_capacity=1000, value_pool_capacity=1000, options=wc.WC_OPT_OVERFLOW_BITS)
+    with pytest.raises(wc.WcError):
+        wc.SingleValueTable(4, 4, min_capacity=1000, options=2)
+    t = wc.SingleValueTable(4, 4, min_capacity=1000)
+    with pytest.raises(wc.WcError):
+        wc.wc_table_dump_overflow_bits(t.handle)
