@@ -234,8 +234,16 @@ struct EmitValue {
   }
 };
 
+// Packed 8-byte slots with at most 32 bytes of the window per lane fit six 256-thread
+// blocks per SM (40 registers) without spilling; more warps in flight hide more of the
+// random-read latency.  Wider per-lane loads keep the compiler's choice.
+template <class L, int S>
+constexpr int retrieve_min_blocks() {
+  return (L::kWords == 1 && S <= 4) ? 6 : 1;
+}
+
 template <class L, int G, int S>
-__global__ void __launch_bounds__(256) k_sv_retrieve(TableDesc t, const typename L::Key* __restrict__ keys, uint64_t n,
+__global__ void __launch_bounds__(256, retrieve_min_blocks<L, S>()) k_sv_retrieve(TableDesc t, const typename L::Key* __restrict__ keys, uint64_t n,
                                                      uint64_t per_warp, typename L::Val* __restrict__ out,
                                                      uint8_t* __restrict__ found) {
   RangeSrc src(n, per_warp, nullptr, 0);
