@@ -65,6 +65,9 @@ def parse():
                          "served: 64 tables, Poisson requests, batched vs per-call")
     ap.add_argument("--requests", type=int, default=512, help="served: number of requests")
     ap.add_argument("--r", default="1,4,16,64", help="mv_oa_uniform_r: average copies per key, comma-separated")
+    ap.add_argument("--bucket-modes", default="exact",
+                    help="mv_oa_uniform_r: bucket-table legs, comma-separated: exact (one bucket of exactly each "
+                         "call's count), LAMBDA/S0 (growth strategy; S0 = r for s0 = the mean values per key)")
     return ap.parse_args()
 
 
@@ -565,14 +568,27 @@ def run_mv_oa_uniform_r(args, dev):
         for op in (WC_OP_INSERT, WC_OP_RETRIEVE, WC_OP_COUNT):
             api.wc_table_set_launch(h, op, args.group, 256, 0, 0, 0)
     info = api.wc_table_get_info(h)
-    res = {"oa": {}, "bucket": {}}
+    modes = [m.strip() for m in args.bucket_modes.split(",") if m.strip()]
+    res = {"oa": {}}
+    for m in modes:
+        res["bucket" if m == "exact" else "bucket_" + m] = {}
     launches = 0
     with ClockSampler(dev.index) as clk:
         for r in rs:
             keys = to_device(wc_inputs.mv_uniform_r(0x57C00005 + r, n, r)["keys"].astype(np.uint32), 4, dev)
-            hb = api.wc_table_create(1, 4, 4, int(np.ceil(max(1, n // r) / 0.8)), 0, n + 2 * (n // r) + 1024,
-                                     0x5EEDC0DE, dev.index)
-            for name, t in (("oa", h), ("bucket", hb)):
+            legs = [("oa", h)]
+            for m in modes:
+                if m == "exact":
+                    s0, lam = 0, 1.0
+                else:
+                    lam_s, s0_s = m.split("/")
+                    lam, s0 = float(lam_s), (r if s0_s == "r" else int(s0_s))
+                # pool: values + headers + padding of the largest layout (s0 = 1, lambda = 1: 4 per value)
+                pool = n + 2 * (n // r) + 1024 if s0 == 0 else 4 * n + 1024
+                legs.append(("bucket" if m == "exact" else "bucket_" + m,
+                             api.wc_table_create(1, 4, 4, int(np.ceil(max(1, n // r) / 0.8)), 0, pool, 0x5EEDC0DE,
+                                                 dev.index, bucket_first_size=s0, bucket_growth=lam)))
+            for name, t in legs:
                 ev = []
                 for i in range(args.warmup + args.steps):
                     api.wc_table_clear(t, s)
@@ -587,10 +603,13 @@ def run_mv_oa_uniform_r(args, dev):
                 res[name][str(r)] = {"insert_gops": n / ins / 1e6, "retrieve_gqps": n / (cnt + ret) / 1e6,
                                      "count_gqps": n / cnt / 1e6, "insert_ms": ins, "count_ms": cnt,
                                      "retrieve_multi_ms": ret}
+                if name != "oa":
+                    res[name][str(r)]["pool_elements_per_value"] = api.wc_value_pool_used(t) / n
                 # OA: hist + scatter + insert, walk + 3 scan kernels, walk; bucket: hist +
                 # scatter + count + alloc + scatter, count + 3 scan kernels, gather
                 launches += (8 if name == "oa" else 10) * args.steps
-            api.wc_table_destroy(hb)
+            for name, t in legs[1:]:
+                api.wc_table_destroy(t)
             del keys
     total = {m: sum(v["insert_ms"] + v["count_ms"] + v["retrieve_multi_ms"] for v in res[m].values()) for m in res}
     _common(args, "mv_oa_u32_n2^%d_uniform_r%s_alpha0.80" % (log2n, "-".join(map(str, rs))),
@@ -601,8 +620,9 @@ def run_mv_oa_uniform_r(args, dev):
                                             (("insert", WC_OP_INSERT), ("count", WC_OP_COUNT),
                                              ("retrieve_multi", WC_OP_RETRIEVE))},
                                  "l2": "no flush: 2.7 GB table, 1 GB inputs"}, clk, launches,
-            {"per_r": res["oa"], "bucket_per_r": res["bucket"],
-             "bucket_value": 2 * n * len(rs) / (total["bucket"] * 1e-3) / 1e9})
+            dict({"per_r": res["oa"]},
+                 **{k + "_per_r": v for k, v in res.items() if k != "oa"},
+                 **{k + "_value": 2 * n * len(rs) / (total[k] * 1e-3) / 1e9 for k in res if k != "oa"}))
     api.wc_table_destroy(h)
 
 

@@ -95,6 +95,16 @@ enum { WC_SINGLE_VALUE = 0, WC_MULTI_VALUE = 1, WC_MULTI_VALUE_OA = 2 };
  *   l2_persist           1 = launch this table's kernels with an L2 access-policy window
  *                        marking the slot array persisting (useful when it fits in L2).
  *   options              WC_OPT_* bits (0 = none).
+ *   bucket_first_size    bucket multi-value only: 0 (default) = every insert call appends
+ *                        one bucket of exactly its count per key (the bucket list with
+ *                        lambda = 1, s0 = count, Sec. V-C); s0 >= 1 = the growth strategy
+ *                        of Sec. IV-C: a key's buckets have sizes s0, s1 = ceil(lambda * s0),
+ *                        ..., s_i = ceil(lambda * s_{i-1}), each filled before the next is
+ *                        allocated, so calls append into the key's last bucket first.
+ *   bucket_growth        lambda >= 1 for the growth strategy (ignored when
+ *                        bucket_first_size = 0).  lambda > 1 must reach 2^28 values within
+ *                        1024 buckets (e.g. lambda = 1.1, s0 = 1 needs 161); lambda = 1 gives
+ *                        buckets of s0 values each.
  */
 typedef struct {
   int32_t kind;
@@ -108,6 +118,8 @@ typedef struct {
   uint64_t min_capacity;
   uint64_t value_pool_capacity;
   uint64_t seed;
+  uint64_t bucket_first_size;
+  double bucket_growth;
 } wc_table_config;
 
 /* WC_OPT_OVERFLOW_BITS (single-value tables only; no counterpart in the paper): keep one
@@ -260,6 +272,11 @@ wc_status wc_size(wc_table* t, uint64_t* h_out, void* stream);
  * over the slots, which finds each key's first copy along its probing sequence).
  * Single-value: same as wc_size.  Synchronises stream. */
 wc_status wc_num_keys(wc_table* t, uint64_t* h_out, void* stream);
+
+/* Bucket multi-value: value-pool elements allocated so far (bucket values, their headers
+ * and alignment padding; the storage-density denominator of Sec. IV-C).  Other kinds: 0.
+ * Synchronises stream. */
+wc_status wc_value_pool_used(wc_table* t, uint64_t* h_out, void* stream);
 
 /* Load factor alpha = live keys / capacity (key-store load for the bucket multi-value
  * table, Sec. II; occupied slots = stored pairs / capacity for the open-addressing one).

@@ -50,7 +50,7 @@ class WcTableConfig(ctypes.Structure):
                 ("window_width", ctypes.c_int32), ("device", ctypes.c_int32), ("l2_persist", ctypes.c_int32),
                 ("options", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("min_capacity", ctypes.c_uint64), ("value_pool_capacity", ctypes.c_uint64),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("bucket_first_size", ctypes.c_uint64), ("bucket_growth", ctypes.c_double)]
 
 
 class WcTableInfo(ctypes.Structure):
@@ -92,6 +92,7 @@ _SIGS = {
     "wc_size": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), _vp]),
     "wc_num_keys": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), _vp]),
     "wc_load_factor": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), _vp]),
+    "wc_value_pool_used": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), _vp]),
     "wc_get_status": (ctypes.c_int, [_vp, ctypes.POINTER(_u32), _i32, _vp]),
     "wc_check_status": (ctypes.c_int, [_vp, ctypes.POINTER(_u32), _vp]),
     "wc_table_dump_slots": (ctypes.c_int, [_vp, _vp, _u64, _vp]),

@@ -20,7 +20,7 @@ __all__ = [
     "wc_plan_capacity", "wc_table_create", "wc_table_destroy", "wc_table_clear", "wc_table_get_info",
     "wc_table_set_launch", "wc_table_get_launch", "wc_insert", "wc_retrieve", "wc_erase", "wc_count_values",
     "wc_retrieve_multi", "wc_size", "wc_num_keys", "wc_load_factor", "wc_get_status", "wc_status_string",
-    "wc_insert_noalloc", "WC_NOALLOC_SCRATCH_BYTES",
+    "wc_insert_noalloc", "WC_NOALLOC_SCRATCH_BYTES", "wc_value_pool_used",
 ]
 
 
@@ -52,13 +52,15 @@ def wc_plan_capacity(min_capacity: int, window_width: int) -> tuple[int, int]:
 
 def wc_table_create(kind: int = WC_SINGLE_VALUE, key_bytes: int = 4, value_bytes: int = 4, min_capacity: int = 1024,
                     window_width: int = 0, value_pool_capacity: int = 0, seed: int = 0x5EED_C0DE,
-                    device: int | None = None, l2_persist: bool = False, options: int = 0) -> int:
+                    device: int | None = None, l2_persist: bool = False, options: int = 0,
+                    bucket_first_size: int = 0, bucket_growth: float = 1.0) -> int:
     if device is None:
         device = torch.cuda.current_device()
     cfg = WcTableConfig(kind=kind, key_bytes=key_bytes, value_bytes=value_bytes, window_width=window_width,
                         device=device, l2_persist=1 if l2_persist else 0, options=int(options), reserved=0,
                         min_capacity=int(min_capacity),
-                        value_pool_capacity=int(value_pool_capacity), seed=int(seed) & (2 ** 64 - 1))
+                        value_pool_capacity=int(value_pool_capacity), seed=int(seed) & (2 ** 64 - 1),
+                        bucket_first_size=int(bucket_first_size), bucket_growth=float(bucket_growth))
     h = ctypes.c_void_p()
     check(lib().wc_table_create(ctypes.byref(h), ctypes.byref(cfg)), "wc_table_create")
     return int(h.value)
@@ -155,6 +157,10 @@ def wc_size(t: int, stream=None) -> int:
 
 def wc_num_keys(t: int, stream=None) -> int:
     return _read_u64(lib().wc_num_keys, t, stream, "wc_num_keys")
+
+
+def wc_value_pool_used(t: int, stream=None) -> int:
+    return _read_u64(lib().wc_value_pool_used, t, stream, "wc_value_pool_used")
 
 
 def wc_load_factor(t: int, stream=None) -> float:

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -11,6 +12,7 @@
 #include <mutex>
 #include <new>
 #include <tuple>
+#include <vector>
 
 #include "wc.h"
 #include "wc_internal.h"
@@ -39,6 +41,7 @@ constexpr uint64_t kAlign = 256;
 constexpr uint64_t kMaxPool = 1ull << 35;
 constexpr uint64_t kMaxBatch = (1ull << 32) - 1;
 constexpr uint64_t kMaxMvBatch = 1ull << 31;  // per-call counts must stay below the poison bit
+constexpr uint64_t kMaxCountHost = (1ull << 28) - 1;  // values per multi-value key
 
 uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
@@ -157,8 +160,36 @@ PoolDesc pool_of(const wc_table* t) {
   p.pending = t->d_pending;
   p.capacity = t->pool_capacity;
   p.value_bytes = t->cfg.value_bytes;
+  p.growth = t->growth;
+  p.nbuckets = t->nbuckets;
+  p.s0 = t->cfg.bucket_first_size;
+  p.foot0 = t->grow_foot0;
+  p.foot = t->grow_foot;
+  p.cum_size = t->d_growth;
+  p.cum_foot = t->d_growth ? t->d_growth + t->nbuckets : nullptr;
+  p.base = t->d_base;
   return p;
 }
+
+namespace {
+
+// Bucket sizes of the growth strategy (Sec. IV-C): s_0 = s0, s_i = ceil(lambda * s_{i-1}).
+// A product within a relative 1e-9 of an integer counts as that integer, so decimal
+// factors such as 1.1 (not exact in binary) give the sizes their decimal value gives.
+uint64_t next_bucket_size(double lambda, uint64_t s) {
+  const double x = lambda * static_cast<double>(s);
+  const double c = std::ceil(x - 1e-9 * x);
+  return std::max<uint64_t>(s, static_cast<uint64_t>(c));
+}
+
+// Pool elements of bucket i: values plus (for i > 0) the header holding the previous
+// handle, rounded to whole 8-byte words for 4-byte values.
+uint64_t bucket_foot(uint64_t i, uint64_t s, int value_bytes) {
+  const uint64_t e = s + (i ? 8u / static_cast<uint64_t>(value_bytes) : 0);
+  return value_bytes == 4 ? (e + 1) & ~1ull : e;
+}
+
+}  // namespace
 
 cudaLaunchAttribute* l2_attr(const wc_table* t, cudaLaunchAttribute* storage, unsigned* count) {
   if (t == nullptr || t->l2_window_bytes == 0) {
@@ -289,6 +320,32 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   const bool mv = cfg->kind == WC_MULTI_VALUE;
   const bool oa = cfg->kind == WC_MULTI_VALUE_OA;
   if ((cfg->options & ~WC_OPT_OVERFLOW_BITS) != 0 || cfg->reserved != 0) return WC_ERR_INVALID_ARG;
+  // bucket growth strategy (bucket multi-value tables)
+  int growth = kGrowExact;
+  std::vector<uint64_t> cum_size, cum_foot;
+  uint64_t foot0 = 0, foot = 0;
+  if (cfg->bucket_first_size != 0) {
+    const double lam = cfg->bucket_growth;
+    if (!mv || !(lam >= 1.0) || !(lam <= 1e6) || cfg->bucket_first_size > kMaxCountHost) return WC_ERR_INVALID_ARG;
+    const uint64_t s0 = cfg->bucket_first_size;
+    if (lam == 1.0) {
+      growth = kGrowConst;
+      foot0 = bucket_foot(0, s0, cfg->value_bytes);
+      foot = bucket_foot(1, s0, cfg->value_bytes);
+    } else {
+      growth = kGrowTable;
+      uint64_t s = s0, S = 0, F = 0;
+      for (uint64_t i = 0;; ++i) {
+        if (i >= kMaxGrowBuckets) return WC_ERR_INVALID_ARG;
+        S += s;
+        F += bucket_foot(i, s, cfg->value_bytes);
+        cum_size.push_back(S);
+        cum_foot.push_back(F);
+        if (S >= kMaxCountHost) break;
+        s = std::min<uint64_t>(next_bucket_size(lam, s), kMaxCountHost);
+      }
+    }
+  }
   if ((cfg->options & WC_OPT_OVERFLOW_BITS) && cfg->kind != WC_SINGLE_VALUE) return WC_ERR_INVALID_ARG;
   if (mv && cfg->value_pool_capacity > kMaxPool) return WC_ERR_INVALID_ARG;
 
@@ -317,12 +374,19 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   const uint64_t ovf_bytes = sv ? align_up((p + 31) / 32 * 4, kAlign) : 0;
   const uint64_t off_pending = off_ovf + ovf_bytes;
   const uint64_t pending_bytes = mv ? align_up(cap * 4, kAlign) : 0;
-  const uint64_t off_partials = off_pending + pending_bytes;
+  const uint64_t off_base = off_pending + pending_bytes;
+  const uint64_t base_bytes = growth != kGrowExact ? align_up(cap * 4, kAlign) : 0;
+  const uint64_t off_partials = off_base + base_bytes;
   t->partials_cap = mv || oa ? scan_partials_needed(kMaxBatch + 1) : 0;
   const uint64_t partial_bytes = align_up(t->partials_cap * 8, kAlign);
   const uint64_t off_pool = off_partials + partial_bytes;
   const uint64_t pool_bytes = align_up(t->pool_capacity * static_cast<uint64_t>(cfg->value_bytes), kAlign);
-  t->device_bytes = off_pool + pool_bytes;
+  const uint64_t off_growth = off_pool + pool_bytes;
+  t->device_bytes = off_growth + align_up(cum_size.size() * 16, kAlign);
+  t->growth = growth;
+  t->nbuckets = static_cast<uint32_t>(cum_size.size());
+  t->grow_foot0 = foot0;
+  t->grow_foot = foot;
 
   if (injected_alloc_failure() || cudaMalloc(&t->d_block, t->device_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -337,6 +401,8 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   t->d_cursor = reinterpret_cast<unsigned long long*>(base + off_meta + 24);
   t->d_ovf = sv ? reinterpret_cast<uint32_t*>(base + off_ovf) : nullptr;
   t->d_pending = mv ? reinterpret_cast<uint32_t*>(base + off_pending) : nullptr;
+  t->d_base = growth != kGrowExact ? reinterpret_cast<uint32_t*>(base + off_base) : nullptr;
+  t->d_growth = growth == kGrowTable ? reinterpret_cast<uint64_t*>(base + off_growth) : nullptr;
   t->d_partials = mv || oa ? reinterpret_cast<uint64_t*>(base + off_partials) : nullptr;
   t->d_pool = mv ? static_cast<void*>(base + off_pool) : nullptr;
 
@@ -369,7 +435,14 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   }
 
   t->clear_bytes = off_partials;
-  if (cudaMemset(t->d_block, 0, t->clear_bytes) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+  cudaError_t ge = cudaSuccess;
+  if (t->d_growth != nullptr) {
+    ge = cudaMemcpy(t->d_growth, cum_size.data(), cum_size.size() * 8, cudaMemcpyHostToDevice);
+    if (ge == cudaSuccess)
+      ge = cudaMemcpy(t->d_growth + t->nbuckets, cum_foot.data(), cum_foot.size() * 8, cudaMemcpyHostToDevice);
+  }
+  if (ge != cudaSuccess || cudaMemset(t->d_block, 0, t->clear_bytes) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
     cudaFree(t->d_block);
     delete t;
     return WC_ERR_CUDA;
@@ -541,6 +614,15 @@ wc_status wc_num_keys(wc_table* t, uint64_t* h_out, void* stream) {
     return read_counter(t, t->d_nkeys, sizeof(uint64_t), h_out, stream);
   }
   return read_counter(t, t->cfg.kind == WC_MULTI_VALUE ? t->d_nkeys : t->d_size, sizeof(uint64_t), h_out, stream);
+}
+
+wc_status wc_value_pool_used(wc_table* t, uint64_t* h_out, void* stream) {
+  if (t == nullptr || h_out == nullptr) return WC_ERR_INVALID_ARG;
+  if (t->cfg.kind != WC_MULTI_VALUE) {
+    *h_out = 0;
+    return WC_OK;
+  }
+  return read_counter(t, t->d_cursor, sizeof(uint64_t), h_out, stream);
 }
 
 wc_status wc_load_factor(wc_table* t, double* h_out, void* stream) {

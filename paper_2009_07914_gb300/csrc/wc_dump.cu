@@ -18,7 +18,7 @@ struct SnapHeader {
   uint64_t magic;
   int32_t kind, key_bytes, value_bytes, window_width;
   uint64_t windows, pool_capacity, seed, device_bytes, clear_bytes;
-  uint64_t reserved[2];
+  uint64_t bucket_first_size, bucket_growth_bits;
 };
 static_assert(sizeof(SnapHeader) == 80, "snapshot header layout");
 
@@ -53,6 +53,9 @@ SnapHeader header_of(const wc_table* t) {
   h.seed = t->cfg.seed;
   h.device_bytes = t->device_bytes;
   h.clear_bytes = t->clear_bytes;
+  h.bucket_first_size = t->cfg.bucket_first_size;
+  std::memcpy(&h.bucket_growth_bits, &t->cfg.bucket_growth, sizeof(double));
+  if (t->cfg.bucket_first_size == 0) h.bucket_growth_bits = 0;  // lambda unused
   return h;
 }
 
@@ -116,7 +119,8 @@ wc_status wc_table_restore(wc_table* t, const void* h_in, uint64_t bytes, void* 
   if (h.magic != kMagic || h.kind != want.kind || h.key_bytes != want.key_bytes ||
       h.value_bytes != want.value_bytes || h.window_width != want.window_width || h.windows != want.windows ||
       h.pool_capacity != want.pool_capacity || h.seed != want.seed || h.device_bytes != want.device_bytes ||
-      h.clear_bytes != want.clear_bytes || bytes < wc_table_snapshot_bytes(t))
+      h.clear_bytes != want.clear_bytes || h.bucket_first_size != want.bucket_first_size ||
+      h.bucket_growth_bits != want.bucket_growth_bits || bytes < wc_table_snapshot_bytes(t))
     return WC_ERR_INVALID_ARG;
   DevGuard g(t->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);

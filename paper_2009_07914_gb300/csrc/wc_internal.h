@@ -30,7 +30,18 @@ struct PoolDesc {
   uint32_t* pending;                 // per key-store slot: this call's count / cursor
   uint64_t capacity;                 // pool elements
   int32_t value_bytes;               // 4 or 8
+  // bucket growth strategy (kGrowExact: one exact bucket per call and key)
+  int32_t growth;                    // kGrowExact, kGrowConst (lambda = 1) or kGrowTable
+  uint32_t nbuckets;                 // kGrowTable: entries of cum_size / cum_foot
+  uint64_t s0;                       // first bucket size (kGrowConst: every bucket's)
+  uint64_t foot0, foot;              // kGrowConst: pool elements of bucket 0 / of later buckets
+  const uint64_t* cum_size;          // kGrowTable: values in buckets 0..i
+  const uint64_t* cum_foot;          // kGrowTable: pool elements of buckets 0..i
+  uint32_t* base;                    // growth: per key-store slot, the key's count before this call
 };
+
+enum { kGrowExact = 0, kGrowConst = 1, kGrowTable = 2 };
+constexpr uint32_t kMaxGrowBuckets = 1024;
 
 // Shape of one launch after the table's tuning was applied.
 struct LaunchShape {
@@ -61,6 +72,11 @@ struct wc_table {
   unsigned long long* d_cursor;
   uint32_t* d_ovf;       // SV: overflow bits, one per window
   uint32_t* d_pending;   // MV: capacity entries
+  uint32_t* d_base;      // MV with bucket growth: capacity entries
+  uint64_t* d_growth;    // MV with kGrowTable: cum_size[nbuckets] then cum_foot[nbuckets]
+  int32_t growth;
+  uint32_t nbuckets;
+  uint64_t grow_foot0, grow_foot;
   uint64_t* d_partials;  // MV: scan partial sums
   uint64_t partials_cap;
   void* d_pool;

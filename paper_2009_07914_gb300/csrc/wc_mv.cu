@@ -48,7 +48,8 @@ cudaError_t insert_passes(const wc_table* t, const void* keys, const void* vals,
   if (e != cudaSuccess) return e;
   const uint64_t per_block = static_cast<uint64_t>(kAllocThreads) * kAllocItems;
   const unsigned g_a = static_cast<unsigned>((t->capacity + per_block - 1) / per_block);
-  e = launch_k(t, k_mv_alloc<VB>, g_a, kAllocThreads, 0, s, d, pd, t->capacity);
+  e = launch_k(t, t->growth == kGrowExact ? k_mv_alloc<VB> : k_mv_alloc_growth<VB>, g_a, kAllocThreads, 0, s, d, pd,
+               t->capacity);
   if (e != cudaSuccess) return e;
   return launch_k(t, scatter, g_s, kAggThreads, agg_smem_bytes(true), s, d, pd, k, vals, n,
                   counters ? counters + 1 : counters);

@@ -58,6 +58,59 @@ struct PoolT<8> {
   using T = unsigned long long;
 };
 
+// ---- bucket growth strategy (Sec. IV-C) ----------------------------------------------------
+// With a growth strategy a key's buckets have fixed sizes s_0, s_1, ... (its bucket i holds
+// its values S_{i-1} .. S_i - 1, S_i = s_0 + ... + s_i); an insert call first fills the
+// key's last bucket, then allocates the buckets it still needs in one contiguous chunk.
+// Every bucket but the first leads with a header holding the handle of the previous
+// bucket {its start, S_{i-1}, i - 1 > 0}, the same back references as the exact layout,
+// so the count and retrieve kernels read both layouts alike.
+
+// Values in buckets 0..i (0 for i < 0).
+__device__ __forceinline__ uint64_t g_cum_size(const PoolDesc& pd, int64_t i) {
+  if (i < 0) return 0;
+  if (pd.growth == kGrowConst) return static_cast<uint64_t>(i + 1) * pd.s0;
+  return __ldg(pd.cum_size + i);
+}
+
+// Pool elements of buckets 0..i (0 for i < 0).
+__device__ __forceinline__ uint64_t g_cum_foot(const PoolDesc& pd, int64_t i) {
+  if (i < 0) return 0;
+  if (pd.growth == kGrowConst) return pd.foot0 + static_cast<uint64_t>(i) * pd.foot;
+  return __ldg(pd.cum_foot + i);
+}
+
+// Bucket holding the key's value number v (0-based, insertion order).
+__device__ __forceinline__ int64_t g_bucket_of(const PoolDesc& pd, uint64_t v) {
+  if (pd.growth == kGrowConst) return static_cast<int64_t>(v / pd.s0);
+  uint32_t lo = 0, hi = pd.nbuckets - 1;  // first i with S_i > v (S_{last} >= 2^28 > v)
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(pd.cum_size + mid) > v) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Pool index of value number v of a key whose handle after this call's allocation is H
+// and whose count before the call was c0 (v >= c0: a value of this call).
+template <int VB>
+__device__ __forceinline__ uint64_t g_value_index(const PoolDesc& pd, uint64_t H, uint64_t c0, uint64_t v) {
+  using V = typename PoolT<VB>::T;
+  const uint64_t c1 = h_count(H), o1 = h_offset(H);
+  const int64_t b1 = g_bucket_of(pd, c1 - 1), i = g_bucket_of(pd, v);
+  uint64_t start;
+  if (i == b1) {
+    start = o1;
+  } else if (g_cum_size(pd, i - 1) >= c0) {  // allocated by this call: in the chunk ending with b1
+    start = o1 - (g_cum_foot(pd, b1 - 1) - g_cum_foot(pd, i - 1));
+  } else {  // the key's earlier last bucket: bucket i + 1 (first of the chunk) links to it
+    const uint64_t next = o1 - (g_cum_foot(pd, b1 - 1) - g_cum_foot(pd, i));
+    start = h_offset(*reinterpret_cast<const unsigned long long*>(static_cast<const V*>(pd.pool) + next));
+  }
+  return start + (i > 0 ? Hdr<VB>::kElems : 0) + (v - g_cum_size(pd, i - 1));
+}
+
 // ---- key store probes by one thread (W slots per window) ------------------------------
 
 // Find the key; returns its slot index and handle, or -1 if absent (Sec. IV-B4 early
@@ -140,7 +193,7 @@ __device__ __forceinline__ uint32_t block_exclusive_u32(uint32_t x, uint32_t& to
 // pass: reserve the key's run in its bucket (s_base[e] = first pool index, or all ones).
 template <int W, bool kScatter, int VB>
 __device__ __forceinline__ void ks_global_phase(const TableDesc& t, const PoolDesc& pd,
-                                                const unsigned long long* s_key, const uint32_t* s_cnt,
+                                                unsigned long long* s_key, uint32_t* s_cnt,
                                                 unsigned long long* s_base, const unsigned short* s_list,
                                                 uint32_t len, uint32_t* s_next, uint32_t& flags,
                                                 long long& created) {
@@ -229,7 +282,15 @@ __device__ __forceinline__ void ks_global_phase(const TableDesc& t, const PoolDe
           atomicAdd(pd.pending + slot, s_cnt[e]);
         } else {
           const uint32_t old = atomicAdd(pd.pending + slot, s_cnt[e]);
-          s_base[e] = (old & kPoison) ? ~0ull : h_offset(handle) + (h_prev(handle) ? Hdr<VB>::kElems : 0) + old;
+          if (pd.growth == kGrowExact) {
+            s_base[e] = (old & kPoison) ? ~0ull : h_offset(handle) + (h_prev(handle) ? Hdr<VB>::kElems : 0) + old;
+          } else {
+            // growth: `old` is the value number of the run's first value; keep the handle
+            // and the key's count before the call for the per-value placement
+            s_base[e] = (old & kPoison) ? ~0ull : old;
+            s_key[e] = handle;
+            s_cnt[e] = pd.base[slot];
+          }
         }
         act = false;
       }
@@ -325,7 +386,11 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
         const uint64_t e = tile * kAggTile + static_cast<uint64_t>(k) * kAggThreads + threadIdx.x;
         if (my_slot[k] < 0) continue;
         const unsigned long long b = s_base[my_slot[k]];
-        if (b != ~0ull) pool[b + my_rank[k]] = vin[e];
+        if (b == ~0ull) continue;
+        if (pd.growth == kGrowExact)
+          pool[b + my_rank[k]] = vin[e];
+        else
+          pool[g_value_index<VB>(pd, s_key[my_slot[k]], s_cnt[my_slot[k]], b + my_rank[k])] = vin[e];
       }
     }
     __syncthreads();
@@ -433,6 +498,84 @@ __global__ void __launch_bounds__(kAllocThreads) k_mv_alloc(TableDesc t, PoolDes
     if (old) *reinterpret_cast<unsigned long long*>(static_cast<V*>(pd.pool) + off) = h[k];
     slots[s].v = h_make(off, old + c[k], old != 0);
     pd.pending[s] = 0u;  // becomes the bucket's fill cursor for pass 3
+    added += c[k];
+    off += need[k];
+  }
+  flush_flags(t.status, flags);
+  flush_delta(t.size, added);
+}
+
+// Pass 2 with a growth strategy: a key with c new values and c0 old ones needs its
+// buckets first..b1 (first = the bucket after its last one, b1 = the bucket of value
+// c0 + c - 1); they are allocated as one chunk, their headers written, the handle pointed
+// at bucket b1.  pending[s] and base[s] become c0: pass 3 counts value numbers from there.
+template <int VB>
+__global__ void __launch_bounds__(kAllocThreads) k_mv_alloc_growth(TableDesc t, PoolDesc pd, uint64_t capacity) {
+  using V = typename PoolT<VB>::T;
+  __shared__ uint64_t s_warp[kAllocThreads / 32];
+  __shared__ unsigned long long s_block_base;
+  __shared__ int s_ok;
+  KsSlot* slots = static_cast<KsSlot*>(t.slots);
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * (kAllocThreads * kAllocItems);
+  uint32_t c[kAllocItems];
+  uint64_t h[kAllocItems];
+  uint64_t need[kAllocItems];
+  uint64_t mine = 0;
+  uint32_t flags = 0;
+#pragma unroll
+  for (int k = 0; k < kAllocItems; ++k) {
+    const uint64_t s = base + static_cast<uint64_t>(k) * kAllocThreads + threadIdx.x;
+    c[k] = s < capacity ? pd.pending[s] : 0u;
+    h[k] = 0;
+    need[k] = 0;
+    if (c[k]) {
+      h[k] = slots[s].v;
+      const uint64_t old = h_count(h[k]);
+      if ((c[k] & kPoison) || old + c[k] > kMaxCount) {
+        flags |= kFlagCountOverflow;
+        pd.pending[s] = kPoison;
+        c[k] = 0;
+      } else {
+        const int64_t first = old ? g_bucket_of(pd, old - 1) + 1 : 0;
+        const int64_t b1 = g_bucket_of(pd, old + c[k] - 1);
+        need[k] = first <= b1 ? g_cum_foot(pd, b1) - g_cum_foot(pd, first - 1) : 0;
+      }
+    }
+    mine += need[k];
+  }
+  uint64_t total = 0;
+  const uint64_t pre = block_exclusive_scan<kAllocThreads>(mine, total, s_warp);
+  if (threadIdx.x == 0) {
+    const unsigned long long b = total ? atomicAdd(pd.cursor, static_cast<unsigned long long>(total)) : 0ull;
+    s_block_base = b;
+    s_ok = b + total <= pd.capacity;
+  }
+  __syncthreads();
+  long long added = 0;
+  uint64_t off = s_block_base + pre;
+  V* pool = static_cast<V*>(pd.pool);
+#pragma unroll
+  for (int k = 0; k < kAllocItems; ++k) {
+    if (c[k] == 0) continue;
+    const uint64_t s = base + static_cast<uint64_t>(k) * kAllocThreads + threadIdx.x;
+    if (need[k] != 0 && !s_ok) {
+      flags |= kFlagPoolExhausted;
+      pd.pending[s] = kPoison;
+      continue;
+    }
+    const uint64_t old = h_count(h[k]);
+    const int64_t first = old ? g_bucket_of(pd, old - 1) + 1 : 0;
+    const int64_t b1 = g_bucket_of(pd, old + c[k] - 1);
+    uint64_t tail = h_offset(h[k]);  // start of the key's last bucket so far
+    for (int64_t i = first; i <= b1; ++i) {
+      const uint64_t start = off + (g_cum_foot(pd, i - 1) - g_cum_foot(pd, first - 1));
+      if (i > 0)
+        *reinterpret_cast<unsigned long long*>(pool + start) = h_make(tail, g_cum_size(pd, i - 1), i - 1 > 0);
+      tail = start;
+    }
+    slots[s].v = h_make(tail, old + c[k], b1 > 0);
+    pd.pending[s] = static_cast<uint32_t>(old);  // value number of the call's first value
+    pd.base[s] = static_cast<uint32_t>(old);
     added += c[k];
     off += need[k];
   }
@@ -574,6 +717,30 @@ __global__ void __launch_bounds__(kRmThreads) k_mv_retrieve_multi(TableDesc t, P
       s_h[r] = h;
     }
     __syncthreads();
+    if (pd.growth != kGrowExact) {
+      // growth layouts: a key may have many buckets, so each row's part of the chunk is
+      // copied by one thread walking the row's buckets newest first, once
+      for (int r = threadIdx.x; r < R; r += kRmThreads) {
+        const uint64_t qa = (j0 > s_off[r] ? j0 : s_off[r]) - s_off[r];
+        const uint64_t qb = (j1 < s_off[r + 1] ? j1 : s_off[r + 1]) - s_off[r];
+        uint64_t h = s_h[r];
+        if (qa >= qb || qb > h_count(h)) continue;  // nothing here, or the count changed
+        uint64_t acc = 0;  // rank (newest first) of the current bucket's first value
+        for (uint64_t guard = 0; guard <= kMaxCount && acc < qb; ++guard) {
+          const bool prev = h_prev(h);
+          const uint64_t below = prev ? h_count(*reinterpret_cast<const unsigned long long*>(pool + h_offset(h))) : 0;
+          const uint64_t here = h_count(h) - below;
+          const uint64_t vstart = h_offset(h) + (prev ? Hdr<VB>::kElems : 0);
+          const uint64_t lo = qa > acc ? qa : acc, hi = qb < acc + here ? qb : acc + here;
+          for (uint64_t q = lo; q < hi; ++q) o[s_off[r] + q] = pool[vstart + (q - acc)];
+          acc += here;
+          if (!prev) break;
+          h = *reinterpret_cast<const unsigned long long*>(pool + h_offset(h));
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     for (uint64_t j = j0 + threadIdx.x; j < j1; j += kRmThreads) {
       int lo = 0, hi = R - 1;
       while (lo < hi) {

@@ -32,11 +32,12 @@ class _Table:
     kind = -1
 
     def __init__(self, key_bytes=4, value_bytes=4, min_capacity=1024, window_width=0, value_pool_capacity=0,
-                 seed=0x5EED_C0DE, device=None, l2_persist=False, options=0):
+                 seed=0x5EED_C0DE, device=None, l2_persist=False, options=0, bucket_first_size=0, bucket_growth=1.0):
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.kb, self.vb = key_bytes, value_bytes
         self.handle = api.wc_table_create(self.kind, key_bytes, value_bytes, min_capacity, window_width,
-                                          value_pool_capacity, seed, self.device.index, l2_persist, options)
+                                          value_pool_capacity, seed, self.device.index, l2_persist, options,
+                                          bucket_first_size, bucket_growth)
         self.info = api.wc_table_get_info(self.handle)
 
     def close(self):
@@ -104,6 +105,9 @@ class SingleValueTable(_Table):
 
 class MultiValueTable(_Table):
     kind = WC_MULTI_VALUE
+
+    def pool_used(self, stream=None) -> int:
+        return api.wc_value_pool_used(self.handle, stream)
 
     def count_values(self, keys, stream=None):
         k = self.keys_dev(keys)

@@ -176,3 +176,125 @@ def test_mv_region_split_insert_parity(wc):
         assert t.num_keys() == o.num_keys()
     q = d["queries"][wc_inputs.shuffle_index(3, d["queries"].size)[:200_000]]
     check_queries(t, o, q)
+
+
+# ---- bucket growth strategy (Sec. IV-C) ---------------------------------------------------
+
+def bucket_sizes(s0, lam, upto):
+    """s_0 = s0, s_i = ceil(lambda * s_{i-1}) (a product within 1e-9 of an integer counts as
+    that integer), until the sizes hold `upto` values."""
+    import math
+    sizes, total = [], 0
+    s = s0
+    while total < upto:
+        sizes.append(s)
+        total += s
+        x = lam * s
+        s = max(s, math.ceil(x - 1e-9 * x))
+    return sizes
+
+
+def pool_elements(count, s0, lam, vb):
+    """Pool elements a key with `count` values occupies: its buckets 0..b, each holding
+    its values plus (all but the first) an 8-byte back reference, in whole 8-byte words."""
+    if count == 0:
+        return 0
+    used = 0
+    for i, s in enumerate(bucket_sizes(s0, lam, count)):
+        e = s + (8 // vb if i else 0)
+        used += (e + 1) & ~1 if vb == 4 else e
+    return used
+
+
+def test_growth_paper_example_buckets_1_2_4(wc):
+    """Fig. 4 / Sec. IV-C: s0 = 1 and lambda = 2 give buckets of 1, 2 and 4 values for six
+    values; the seventh fills the last bucket, the eighth opens a bucket of 8."""
+    assert bucket_sizes(1, 2.0, 6) == [1, 2, 4]
+    t = wc.MultiValueTable(4, 4, min_capacity=64, value_pool_capacity=1024, bucket_first_size=1, bucket_growth=2.0)
+    o = oracle.MultiValue(4, 4)
+    for vals in ([1, 2], [3], [4, 5, 6]):  # three calls: appends go into the last bucket first
+        k = np.full(len(vals), 42, np.uint32)
+        t.insert(k, np.array(vals, np.uint32))
+        o.insert(k, np.array(vals, np.uint32))
+    check_queries(t, o, np.array([42, 7], np.uint32))
+    assert t.pool_used() == pool_elements(6, 1, 2.0, 4) == 2 + 4 + 6
+    t.insert(np.array([42], np.uint32), np.array([7], np.uint32))
+    assert t.pool_used() == pool_elements(7, 1, 2.0, 4) == 12
+    t.insert(np.array([42], np.uint32), np.array([8], np.uint32))
+    assert t.pool_used() == pool_elements(8, 1, 2.0, 4) == 12 + 10
+    o.insert(np.array([42, 42], np.uint32), np.array([7, 8], np.uint32))
+    check_queries(t, o, np.array([42], np.uint32))
+    assert run_mv("mv_ops.txt", lambda: _Adapter(wc.MultiValueTable(8, 4, min_capacity=64, value_pool_capacity=1024,
+                                                                    bucket_first_size=1, bucket_growth=2.0))) >= 8
+
+
+@pytest.mark.parametrize("kb,vb", [(4, 4), (8, 8)])
+@pytest.mark.parametrize("s0,lam", [(1, 1.1), (1, 2.0), (3, 1.5), (4, 1.0), (1, 1.0)])
+def test_growth_repeat_inserts_and_pool_accounting(wc, kb, vb, s0, lam):
+    """Growth strategy over repeated insert calls (each call first fills the key's last
+    bucket) with erases in between: counts and value multisets equal the oracle's, and the
+    pool holds exactly the buckets the growth formula gives each key's final count."""
+    rng = np.random.default_rng(int(s0 * 100 + lam * 10) + kb)
+    universe = np.unique(rng.integers(1, 2 ** 31 - 1, 4000, dtype=np.uint64))
+    if kb == 4:
+        universe = universe.astype(np.uint32)
+    t = wc.MultiValueTable(kb, vb, min_capacity=8192, value_pool_capacity=3_000_000, bucket_first_size=s0,
+                           bucket_growth=lam)
+    o = oracle.MultiValue(kb, vb)
+    counts, pool = {}, 0
+    vmax = (1 << (8 * vb)) - 1
+    for step in range(8):
+        m = int(rng.integers(1, 30_000))
+        ks = universe[np.minimum(rng.zipf(1.4, m), universe.size) - 1]
+        vs = rng.integers(0, vmax, m, dtype=np.uint64, endpoint=True)
+        if vb == 4:
+            vs = vs.astype(np.uint32)
+        assert t.insert(ks, vs) == 0
+        o.insert(ks, vs)
+        u, c = np.unique(ks, return_counts=True)
+        for k, n in zip(u.tolist(), c.tolist()):
+            counts[k] = counts.get(k, 0) + n
+        if step == 4:
+            drop = universe[:300]
+            t.erase(drop)
+            o.erase(drop)
+            for k in drop.tolist():
+                pool += pool_elements(counts.pop(k, 0), s0, lam, vb)  # erased buckets stay allocated
+        assert t.size() == o.size()
+        check_queries(t, o, universe)
+    expect = pool + sum(pool_elements(n, s0, lam, vb) for n in counts.values())
+    assert t.pool_used() == expect
+
+
+def test_growth_uniform_r_invariant_and_snapshot(wc):
+    """Sec. V-C invariant with the paper's default growth (lambda = 1.1, s0 = 1), then a
+    snapshot restored into a table of the same growth parameters (and refused by another)."""
+    n = 1 << 17
+    for r in (1, 16, 256):
+        d = wc_inputs.mv_uniform_r(900 + r, n, r)
+        t = wc.MultiValueTable(8, 4, min_capacity=int(max(1, n // r) / 0.8) + 1, value_pool_capacity=4 * n,
+                               bucket_first_size=1, bucket_growth=1.1)
+        t.insert(d["keys"][: n // 2], d["values"][: n // 2])
+        t.insert(d["keys"][n // 2:], d["values"][n // 2:])
+        offs, _ = t.count_values(d["queries"])
+        assert int(offs[-1]) == n
+        vals, _ = t.retrieve_multi(d["queries"], offs)
+        np.testing.assert_array_equal(np.sort(vals), np.arange(n, dtype=np.uint32))
+        seg = np.repeat(np.arange(n), np.diff(offs.astype(np.int64)))
+        np.testing.assert_array_equal(d["queries"][seg], d["keys"][vals])
+    snap = wc.api.wc_table_snapshot(t.handle)
+    kw = dict(min_capacity=int(max(1, n // 256) / 0.8) + 1, value_pool_capacity=4 * n, bucket_first_size=1)
+    u = wc.MultiValueTable(8, 4, bucket_growth=1.1, **kw)
+    wc.api.wc_table_restore(u.handle, snap)
+    offs2, _ = u.count_values(d["queries"])
+    np.testing.assert_array_equal(offs2, offs)
+    with pytest.raises(wc.WcError):
+        wc.api.wc_table_restore(wc.MultiValueTable(8, 4, bucket_growth=1.2, **kw).handle, snap)
+
+
+def test_growth_parameters_are_validated(wc):
+    for kw in (dict(bucket_first_size=1, bucket_growth=0.9), dict(bucket_first_size=1, bucket_growth=1.0001)):
+        with pytest.raises(wc.WcError):
+            wc.MultiValueTable(8, 4, min_capacity=64, value_pool_capacity=64, **kw)
+    with pytest.raises(wc.WcError):  # single-value tables have no buckets
+        wc.SingleValueTable(4, 4, min_capacity=64, bucket_first_size=1, bucket_growth=2.0)
