@@ -56,12 +56,14 @@ def parse():
     ap.add_argument("--no-overflow-bits", action="store_true",
                     help="sv32: table without per-window overflow bits (lookups walk to an empty slot)")
     ap.add_argument("--workload", default="sv32",
-                    choices=["sv32", "sv32_small", "sv64_zipf", "mv_zipf", "mv_oa_uniform_r", "served"],
+                    choices=["sv32", "sv32_small", "sv64_zipf", "mv_zipf", "mv_oa_uniform_r", "device_api", "served"],
                     help="sv32 (default): 2^27 uint32 pairs at load 0.9, insert + 50%% absent retrieve; "
                          "sv32_small: 2^20 pairs at 0.8 with erase; sv64_zipf: 2^28 uint64 pairs, Zipf queries; "
                          "mv_zipf: multi-value 2^28 Zipf inserts, count + CSR retrieve; "
                          "mv_oa_uniform_r: open-addressing multi-value, 2^28 uint32 pairs with keys uniform "
                          "over 1..n/r at load 0.8, queries 1..n; "
+                         "device_api: 2^27 keys produced inside one kernel and inserted / looked up per thread "
+                         "with the device API, against the bulk calls on the same keys; "
                          "served: 64 tables, Poisson requests, batched vs per-call")
     ap.add_argument("--requests", type=int, default=512, help="served: number of requests")
     ap.add_argument("--r", default="1,4,16,64", help="mv_oa_uniform_r: average copies per key, comma-separated")
@@ -626,6 +628,58 @@ def run_mv_oa_uniform_r(args, dev):
     api.wc_table_destroy(h)
 
 
+def run_device_api(args, dev):
+    """Device-side API (fused producer): one kernel whose threads produce the keys
+    k_i = (i * 2654435761 mod 2^32) xor seed (distinct) and insert (k_i, i), then one whose
+    threads look k_i up; against the bulk insert and retrieve of the same keys held in
+    device memory.  2^27 keys into a table at load 0.9 with overflow bits."""
+    import torch
+
+    import paper_2009_07914_gb300 as wc
+    from paper_2009_07914_gb300 import api
+    from paper_2009_07914_gb300.roofline import wc_bench_device_api
+    from paper_2009_07914_gb300.table import to_device
+    n = 1 << args.log2n
+    seed = 0x2468ACE1
+    idx = np.arange(n, dtype=np.uint64)
+    k = ((idx * np.uint64(2654435761)) & np.uint64(0xFFFFFFFF)).astype(np.uint32) ^ np.uint32(seed)
+    valid = (k != 0) & (k != 0xFFFFFFFF)
+    nv = int(valid.sum())
+    keys, vals = to_device(k, 4, dev), to_device(idx.astype(np.uint32), 4, dev)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    found = torch.empty(n, dtype=torch.uint8, device=dev)
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    want = int(idx[valid].astype(np.uint64).sum(dtype=np.uint64) & np.uint64(0x7FFFFFFFFFFFFFFF))
+    h = api.wc_table_create(0, 4, 4, int(np.ceil(n / args.alpha)), args.window, 0, 0x5EEDC0DE, dev.index,
+                            options=wc.WC_OPT_OVERFLOW_BITS)
+    s = torch.cuda.current_stream()
+    ev = []
+    with ClockSampler(dev.index) as clk:
+        for i in range(args.warmup + args.steps):
+            api.wc_table_clear(h, s)
+            sink.zero_()
+            t0 = timed(s, lambda: wc_bench_device_api(h, 0, n, seed, None, s))
+            t1 = timed(s, lambda: wc_bench_device_api(h, 1, n, seed, sink, s))
+            if i == 0:
+                assert api.wc_size(h) == nv and int(sink.item()) & 0x7FFFFFFFFFFFFFFF == want
+            api.wc_table_clear(h, s)
+            t2 = timed(s, lambda: api.wc_insert(h, keys, vals, n, s))
+            t3 = timed(s, lambda: api.wc_retrieve(h, keys, out, found, n, s))
+            if i == 0:
+                assert api.wc_size(h) == nv and int(found.sum()) == nv
+            if i >= args.warmup:
+                ev.append((t0, t1, t2, t3))
+    fi, fl, bi, br = (statistics.median(e[j] for e in ev) for j in range(4))
+    _common(args, "device_api_u32_n2^%d_alpha%.2f" % (args.log2n, args.alpha),
+            "G ops/s (device-API fused insert + lookup)", 2 * n / ((fi + fl) * 1e-3) / 1e9, "G ops/s", fi + fl, "u32",
+            {"n": n, "keys": "produced in the kernel: (i * 2654435761 mod 2^32) xor seed", "overflow_bits": True,
+             "l2": "no flush: table 1.19 GB"}, clk, 2 * args.steps,
+            {"fused_insert_gops": n / fi / 1e6, "fused_lookup_gops": n / fl / 1e6,
+             "bulk_insert_gops": n / bi / 1e6, "bulk_retrieve_gops": n / br / 1e6,
+             "fused_insert_ms": fi, "fused_lookup_ms": fl, "bulk_insert_ms": bi, "bulk_retrieve_ms": br})
+    api.wc_table_destroy(h)
+
+
 def run_served(args, dev):
     """64 uint32 tables (capacity 2^U(16,26), pre-filled to load U(0,0.6)); Poisson
     requests with batch sizes 2^U(log2 1000, 24), 60/35/5 insert/retrieve/erase.  Each
@@ -679,7 +733,8 @@ def run_workload(args, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     {"sv32_small": run_sv32_small, "sv64_zipf": run_sv64_zipf, "mv_zipf": run_mv_zipf,
-     "mv_oa_uniform_r": run_mv_oa_uniform_r, "served": run_served}[args.workload](args, dev)
+     "mv_oa_uniform_r": run_mv_oa_uniform_r, "device_api": run_device_api,
+     "served": run_served}[args.workload](args, dev)
 
 
 

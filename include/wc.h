@@ -296,6 +296,31 @@ wc_status wc_check_status(wc_table* t, uint32_t* h_flags_or_null, void* stream);
 /* Static description of a status code. */
 const char* wc_status_string(wc_status s);
 
+/* ---- device-side access (include/wc_device_api.cuh) ------------------------------- */
+
+/* Everything a user kernel needs to operate on a table with the device API of
+ * wc_device_api.cuh: device pointers and geometry, passed to kernels by value.  The
+ * pointers stay valid until wc_table_destroy. */
+typedef struct {
+  void* slots;                 /* capacity slots, layout of wc_table_config */
+  uint32_t* status;            /* the table's status word (WC_FLAG_* bits) */
+  unsigned long long* size;    /* stored pairs */
+  uint32_t* overflow_bits;     /* WC_OPT_OVERFLOW_BITS tables, else NULL */
+  uint64_t seed;
+  uint64_t capacity;           /* windows * window_width */
+  uint32_t windows;            /* p */
+  uint32_t window_width;       /* W */
+  int32_t kind;
+  int32_t key_bytes;
+  int32_t value_bytes;
+  int32_t slot_bytes;
+} wc_device_view;
+
+/* Fill *h_out for a single-value table (per-element insert / retrieve / erase, for_each,
+ * for_all) or an open-addressing multi-value table (for_all only).  Host only.
+ * WC_ERR_UNSUPPORTED for bucket multi-value tables. */
+wc_status wc_table_device_view(const wc_table* t, wc_device_view* h_out);
+
 /* ---- host copies: inspection, checkpoint and resume (no counterpart in the paper) -- */
 
 /* Copy the slot array (wc_table_info.table_bytes bytes, slot i at byte i * slot_bytes,

@@ -1,0 +1,394 @@
+/*
+ * wc_device_api.cuh -- device-side API: per-element operations on a single-value table from
+ * inside user kernels, and the higher-order bulk calls for_each / for_all (Sec. IV-A:
+ * the device-sided interface that fused pipelines call, Sec. IV-B4: for_each(keys,
+ * callback) and for_all(callback) with a device callback).  Header-only CUDA C++;
+ * include it from .cu files compiled for sm_103a (with --extended-lambda for device
+ * lambdas).  It holds the probing sequence the library's own kernels use, so a key
+ * inserted here is found by wc_retrieve and the other way round.
+ *
+ * A table is reached through a wc_device_view (wc.h: wc_table_device_view), a plain
+ * struct of device pointers and geometry, passed to kernels by value.  Rules as for the
+ * bulk calls: operations of one kind may run concurrently (from any number of threads and
+ * kernels); an insert or erase must not overlap a retrieve on the same table (Sec. IV-D).
+ *
+ * Per-element operations are executed by the calling thread alone: it walks the key's
+ * probing sequence window by window (W slots each) -- the paper's cooperative group of
+ * one thread.  Status conditions (DUPLICATE_KEY, INVALID_KEY, PROBE_LIMIT) are returned
+ * and also OR-ed into the table's status word; the pair count is updated with one atomic
+ * per converged group of threads.
+ */
+#ifndef WC_DEVICE_API_CUH_
+#define WC_DEVICE_API_CUH_
+
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wc.h"
+
+namespace wc_dev {
+
+// ---- probing sequence (Sec. IV-B2): outer double hashing over p windows ----------------
+
+// MurmurHash3's 64-bit finalizer "fmix64" (A. Appleby, public domain): an invertible
+// avalanche mix.  h1 and h2 of the outer double hashing are its two 32-bit halves.
+__host__ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+// First window w_0 = floor(h1 * p / 2^32) and step = 1 + floor(h2 * (p - 1) / 2^32) of a
+// key's sequence w_j = (w_0 + j * step) mod p; requires p >= 2.
+__device__ __forceinline__ void probe_init(uint64_t key, uint64_t seed, uint32_t p, uint32_t& w, uint32_t& step) {
+  const uint64_t h = fmix64(key ^ seed);
+  w = __umulhi(static_cast<uint32_t>(h >> 32), p);
+  step = 1u + __umulhi(static_cast<uint32_t>(h), p - 1u);
+}
+
+// (w + step) mod p for w, step < p < 2^32 (the u32 sum may wrap).
+__device__ __forceinline__ uint32_t probe_next(uint32_t w, uint32_t step, uint32_t p) {
+  uint32_t x = w + step;
+  if (x < w || x >= p) x -= p;
+  return x;
+}
+
+// ---- slot words of the two single-value layouts (wc.h: wc_table_config) ---------------
+// 4+4-byte pairs: one 64-bit word, key in the low half.  8+8-byte pairs: 16 bytes, key
+// first.  Key 0 = empty, all ones = tombstone.
+template <class K>
+struct Slots;
+
+template <>
+struct Slots<uint32_t> {
+  using V = uint32_t;
+  struct Word {
+    unsigned long long w;
+  };
+  static __device__ __forceinline__ Word load(const void* slots, uint64_t i) {
+    return Word{__ldcg(static_cast<const unsigned long long*>(slots) + i)};
+  }
+  static __device__ __forceinline__ uint32_t key(const Word& s) { return static_cast<uint32_t>(s.w); }
+  static __device__ __forceinline__ uint32_t val(const Word& s) { return static_cast<uint32_t>(s.w >> 32); }
+  static __device__ __forceinline__ bool cas(void* slots, uint64_t i, const Word& old, uint32_t k, uint32_t v) {
+    const unsigned long long nw = (static_cast<unsigned long long>(v) << 32) | k;
+    return atomicCAS(static_cast<unsigned long long*>(slots) + i, old.w, nw) == old.w;
+  }
+  static __device__ __forceinline__ bool cas_tomb(void* slots, uint64_t i, const Word& old) {
+    return atomicCAS(static_cast<unsigned long long*>(slots) + i, old.w, 0xffffffffull) == old.w;
+  }
+  static __device__ __forceinline__ void set_val(void* slots, uint64_t i, uint32_t v) {
+    atomicExch(reinterpret_cast<unsigned int*>(static_cast<unsigned long long*>(slots) + i) + 1, v);
+  }
+};
+
+template <>
+struct Slots<unsigned long long> {
+  using V = unsigned long long;
+  struct Word {
+    unsigned long long k, v;
+  };
+  static __device__ __forceinline__ Word load(const void* slots, uint64_t i) {
+    const ulonglong2 x = __ldcg(static_cast<const ulonglong2*>(slots) + i);
+    return Word{x.x, x.y};
+  }
+  static __device__ __forceinline__ unsigned long long key(const Word& s) { return s.k; }
+  static __device__ __forceinline__ unsigned long long val(const Word& s) { return s.v; }
+  // one 128-bit CAS of the whole pair (sm_90 and later)
+  static __device__ __forceinline__ bool cas128(void* slots, uint64_t i, const Word& old, unsigned long long k,
+                                                unsigned long long v) {
+    void* p = static_cast<char*>(slots) + i * 16;
+    unsigned long long ok, ov;
+    asm volatile(
+        "{\n\t.reg .b128 d, c, s;\n\t"
+        "mov.b128 c, {%2, %3};\n\t"
+        "mov.b128 s, {%4, %5};\n\t"
+        "atom.global.cas.b128 d, [%6], c, s;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t}"
+        : "=l"(ok), "=l"(ov)
+        : "l"(old.k), "l"(old.v), "l"(k), "l"(v), "l"(p)
+        : "memory");
+    return ok == old.k && ov == old.v;
+  }
+  static __device__ __forceinline__ bool cas(void* slots, uint64_t i, const Word& old, unsigned long long k,
+                                             unsigned long long v) {
+    return cas128(slots, i, old, k, v);
+  }
+  static __device__ __forceinline__ bool cas_tomb(void* slots, uint64_t i, const Word& old) {
+    return cas128(slots, i, old, ~0ull, 0ull);
+  }
+  static __device__ __forceinline__ void set_val(void* slots, uint64_t i, unsigned long long v) {
+    atomicExch(reinterpret_cast<unsigned long long*>(static_cast<char*>(slots) + i * 16) + 1, v);
+  }
+};
+
+template <class K>
+__device__ __forceinline__ bool is_sentinel(K k) {
+  return k == K(0) || k == K(~K(0));
+}
+
+// Pair-count update aggregated over the threads that arrive together.
+__device__ __forceinline__ void add_size(const wc_device_view& t, long long d) {
+  namespace cg = cooperative_groups;
+  cg::coalesced_group g = cg::coalesced_threads();
+  const long long sum = cg::reduce(g, d, cg::plus<long long>());
+  if (g.thread_rank() == 0 && sum != 0) atomicAdd(t.size, static_cast<unsigned long long>(sum));
+}
+
+__device__ __forceinline__ void raise(const wc_device_view& t, uint32_t f) {
+  if (f) atomicOr(t.status, f);
+}
+
+// ---- per-element operations (single-value tables) ---------------------------------------
+
+// The W slots of window w, loaded with 32-byte vector loads issued together (a window
+// holds a multiple of four 64-bit words for every supported width; windows are aligned).
+template <class K, int W>
+struct Window {
+  using S = Slots<K>;
+  static constexpr int kWords = W * static_cast<int>(sizeof(K) == 4 ? 1 : 2);
+  unsigned long long u[kWords];
+  __device__ __forceinline__ void load(const void* slots, uint32_t w) {
+    const unsigned long long* p = static_cast<const unsigned long long*>(slots) + static_cast<uint64_t>(w) * kWords;
+#pragma unroll
+    for (int i = 0; i < kWords; i += 4)
+      asm volatile("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];"
+                   : "=l"(u[i]), "=l"(u[i + 1]), "=l"(u[i + 2]), "=l"(u[i + 3])
+                   : "l"(p + i));
+  }
+  __device__ __forceinline__ typename S::Word slot(int q) const {
+    if constexpr (sizeof(K) == 4) {
+      return typename S::Word{u[q]};
+    } else {
+      return typename S::Word{u[2 * q], u[2 * q + 1]};
+    }
+  }
+};
+
+__device__ __forceinline__ bool overflow_clear(const wc_device_view& t, uint32_t w) {
+  return t.overflow_bits != nullptr && !((__ldcg(t.overflow_bits + (w >> 5)) >> (w & 31u)) & 1u);
+}
+
+template <class K, int W>
+__device__ uint32_t insert_w(const wc_device_view& t, K key, typename Slots<K>::V value) {
+  using S = Slots<K>;
+  using Word = typename S::Word;
+  uint32_t w0, step;
+  probe_init(static_cast<uint64_t>(key), t.seed, t.windows, w0, step);
+  uint32_t w = w0, j = 0;
+  bool have_t = false;  // first tombstone of the walk, claimed if the key turns out absent
+  uint64_t t_slot = 0;
+  Word t_word{};
+  // Every failed CAS means another insert consumed a free slot, so the retries end.
+  while (j < t.windows) {
+    Window<K, W> win;
+    win.load(t.slots, w);
+    const uint64_t base = static_cast<uint64_t>(w) * W;
+    bool empty = false;
+    int free_q = -1;  // first empty or tombstoned slot of the window
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const K k = S::key(win.slot(q));
+      if (k == key) {
+        S::set_val(t.slots, base + q, value);
+        raise(t, WC_FLAG_DUPLICATE_KEY);
+        return WC_FLAG_DUPLICATE_KEY;
+      }
+      const bool is_empty = k == K(0);
+      empty |= is_empty;
+      if ((is_empty || k == K(~K(0))) && free_q < 0) free_q = q;
+    }
+    if (empty || j + 1 == t.windows) {  // the key is absent: claim the earliest candidate
+      if (have_t) {
+        if (S::cas(t.slots, t_slot, t_word, key, value)) break;
+        have_t = false;  // the tombstone was taken: walk again from the start
+        w = w0;
+        j = 0;
+        continue;
+      }
+      if (free_q < 0) {  // last window and nothing free anywhere
+        raise(t, WC_FLAG_PROBE_LIMIT);
+        return WC_FLAG_PROBE_LIMIT;
+      }
+      Word fw = win.slot(0);
+#pragma unroll
+      for (int q = 1; q < W; ++q)
+        if (q == free_q) fw = win.slot(q);
+      if (S::cas(t.slots, base + free_q, fw, key, value)) break;
+      continue;  // lost the slot: read the window again
+    }
+    if (free_q >= 0 && !have_t) {  // a full window: its free slots are tombstones
+      have_t = true;
+      t_slot = base + free_q;
+      t_word = win.slot(0);
+#pragma unroll
+      for (int q = 1; q < W; ++q)
+        if (q == free_q) t_word = win.slot(q);
+    }
+    if (t.overflow_bits) atomicOr(t.overflow_bits + (w >> 5), 1u << (w & 31u));
+    w = probe_next(w, step, t.windows);
+    ++j;
+  }
+  add_size(t, 1);
+  return 0;
+}
+
+template <class K, int W>
+__device__ bool retrieve_w(const wc_device_view& t, K key, typename Slots<K>::V& value) {
+  using S = Slots<K>;
+  uint32_t w, step;
+  probe_init(static_cast<uint64_t>(key), t.seed, t.windows, w, step);
+  for (uint32_t j = 0; j < t.windows; ++j) {
+    Window<K, W> win;
+    win.load(t.slots, w);
+    bool empty = false, hit = false;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const typename S::Word s = win.slot(q);
+      if (S::key(s) == key) {
+        value = S::val(s);
+        hit = true;
+      }
+      empty |= S::key(s) == K(0);
+    }
+    if (hit) return true;
+    if (empty || overflow_clear(t, w)) return false;
+    w = probe_next(w, step, t.windows);
+  }
+  return false;
+}
+
+template <class K, int W>
+__device__ bool erase_w(const wc_device_view& t, K key) {
+  using S = Slots<K>;
+  uint32_t w, step;
+  probe_init(static_cast<uint64_t>(key), t.seed, t.windows, w, step);
+  for (uint32_t j = 0; j < t.windows; ++j) {
+    Window<K, W> win;
+    win.load(t.slots, w);
+    const uint64_t base = static_cast<uint64_t>(w) * W;
+    bool empty = false;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const typename S::Word s = win.slot(q);
+      if (S::key(s) == key) {
+        // only an erase of the same key can change this slot now: one CAS decides
+        const bool ok = S::cas_tomb(t.slots, base + q, s);
+        if (ok) add_size(t, -1);
+        return ok;
+      }
+      empty |= S::key(s) == K(0);
+    }
+    if (empty || overflow_clear(t, w)) return false;
+    w = probe_next(w, step, t.windows);
+  }
+  return false;
+}
+
+// insert_w / retrieve_w / erase_w take the table's window width W as a template argument
+// (it must equal view.window_width): a kernel that knows W keeps one window in registers
+// instead of the widest one.  insert / retrieve / erase below pick W at run time.
+
+// Window widths a table of key type K can have (wc.h: window_width).
+#define WC_DEV_DISPATCH(K, CALL)                                          \
+  if constexpr (sizeof(K) == 4) {                                         \
+    switch (t.window_width) {                                             \
+      case 4: return CALL(4);                                             \
+      case 8: return CALL(8);                                             \
+      case 16: return CALL(16);                                           \
+      default: return CALL(32);                                           \
+    }                                                                     \
+  } else {                                                                \
+    switch (t.window_width) {                                             \
+      case 2: return CALL(2);                                             \
+      case 4: return CALL(4);                                             \
+      case 8: return CALL(8);                                             \
+      default: return CALL(16);                                           \
+    }                                                                     \
+  }
+
+// Insert (Sec. IV-B2 steps 1-7, IV-B3): walk to the first window holding an empty slot or
+// the key; a present key gets its value replaced (WC_FLAG_DUPLICATE_KEY), else the
+// earliest free or tombstoned slot of the walk is claimed with one CAS.  Returns the
+// WC_FLAG_* bits of this insert (0 = stored as a new key).
+template <class K>
+__device__ uint32_t insert(const wc_device_view& t, K key, typename Slots<K>::V value) {
+  if (is_sentinel(key)) {
+    raise(t, WC_FLAG_INVALID_KEY);
+    return WC_FLAG_INVALID_KEY;
+  }
+#define WC_DEV_CALL(Wv) insert_w<K, Wv>(t, key, value)
+  WC_DEV_DISPATCH(K, WC_DEV_CALL)
+#undef WC_DEV_CALL
+}
+
+// Retrieve (Sec. IV-B4): the key's value, or false when absent (the walk stops at a window
+// holding an empty slot -- or, with overflow bits, a window whose bit is clear).
+template <class K>
+__device__ bool retrieve(const wc_device_view& t, K key, typename Slots<K>::V& value) {
+  if (is_sentinel(key)) return false;
+#define WC_DEV_CALL(Wv) retrieve_w<K, Wv>(t, key, value)
+  WC_DEV_DISPATCH(K, WC_DEV_CALL)
+#undef WC_DEV_CALL
+}
+
+// Erase (Sec. IV-B5): the key's slot becomes a tombstone; false when the key is absent.
+template <class K>
+__device__ bool erase(const wc_device_view& t, K key) {
+  if (is_sentinel(key)) return false;
+#define WC_DEV_CALL(Wv) erase_w<K, Wv>(t, key)
+  WC_DEV_DISPATCH(K, WC_DEV_CALL)
+#undef WC_DEV_CALL
+}
+
+#undef WC_DEV_DISPATCH
+
+// ---- higher-order bulk calls ----------------------------------------------------------
+
+template <class K, class F>
+__global__ void for_each_kernel(wc_device_view t, const K* __restrict__ keys, uint64_t n, F f) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    typename Slots<K>::V v;
+    if (retrieve<K>(t, keys[i], v)) f(keys[i], v, i);
+  }
+}
+
+template <class K, class F>
+__global__ void for_all_kernel(wc_device_view t, F f) {
+  using S = Slots<K>;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < t.capacity; i += stride) {
+    const typename S::Word s = S::load(t.slots, i);
+    if (!is_sentinel(S::key(s))) f(S::key(s), S::val(s), i);
+  }
+}
+
+// for_each(keys, callback): callback(key, value, i) for every keys[i] found, on `stream`
+// (asynchronous).  K = uint32_t for 4+4-byte tables, unsigned long long for 8+8.
+template <class K, class F>
+cudaError_t for_each(const wc_device_view& t, const K* d_keys, uint64_t n, F f, cudaStream_t stream = 0) {
+  if (n == 0) return cudaSuccess;
+  if (t.key_bytes != static_cast<int32_t>(sizeof(K))) return cudaErrorInvalidValue;
+  const uint64_t blocks = (n + 255) / 256;
+  for_each_kernel<K, F><<<static_cast<unsigned>(blocks < 65536 ? blocks : 65536), 256, 0, stream>>>(t, d_keys, n, f);
+  return cudaGetLastError();
+}
+
+// for_all(callback): callback(key, value, slot) for every stored pair (asynchronous).
+template <class K, class F>
+cudaError_t for_all(const wc_device_view& t, F f, cudaStream_t stream = 0) {
+  if (t.key_bytes != static_cast<int32_t>(sizeof(K))) return cudaErrorInvalidValue;
+  const uint64_t blocks = (t.capacity + 255) / 256;
+  for_all_kernel<K, F><<<static_cast<unsigned>(blocks < 65536 ? blocks : 65536), 256, 0, stream>>>(t, f);
+  return cudaGetLastError();
+}
+
+}  // namespace wc_dev
+
+#endif /* WC_DEVICE_API_CUH_ */

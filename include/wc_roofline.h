@@ -40,6 +40,14 @@ typedef struct {
 wc_status wc_bench_random_access(void* d_buffer, const wc_rand_access_config* cfg, uint64_t* d_sink,
                                  void* stream);
 
+/* Device-API probe (include/wc_device_api.cuh) on a single-value 4+4-byte table: one
+ * kernel whose threads produce the keys k_i = (i * 2654435761 mod 2^32) xor key_seed
+ * (i < n; distinct) and, per thread, mode 0 inserts (k_i, i), mode 1 looks k_i up and adds
+ * the found values into d_sink (one uint64) -- a fused producer with no key batch in
+ * memory.  Asynchronous on `stream`. */
+wc_status wc_bench_device_api(wc_table* t, int32_t mode, uint64_t n, uint32_t key_seed, uint64_t* d_sink,
+                              void* stream);
+
 /* The CUDA context's L2 fetch-granularity limit (cudaLimitMaxL2FetchGranularity, bytes;
  * a hint of how much the L2 fetches from DRAM on a miss).  Process-local: the setting
  * ends with the process. */

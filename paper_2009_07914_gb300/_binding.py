@@ -60,6 +60,13 @@ class WcTableInfo(ctypes.Structure):
                 ("options", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class WcDeviceView(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_void_p), ("status", ctypes.c_void_p), ("size", ctypes.c_void_p),
+                ("overflow_bits", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("capacity", ctypes.c_uint64),
+                ("windows", ctypes.c_uint32), ("window_width", ctypes.c_uint32), ("kind", ctypes.c_int32),
+                ("key_bytes", ctypes.c_int32), ("value_bytes", ctypes.c_int32), ("slot_bytes", ctypes.c_int32)]
+
+
 class WcLaunch(ctypes.Structure):
     _fields_ = [("group_size", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("scheme", ctypes.c_int32), ("region_mib", ctypes.c_int32)]
@@ -96,6 +103,7 @@ _SIGS = {
     "wc_get_status": (ctypes.c_int, [_vp, ctypes.POINTER(_u32), _i32, _vp]),
     "wc_check_status": (ctypes.c_int, [_vp, ctypes.POINTER(_u32), _vp]),
     "wc_table_dump_slots": (ctypes.c_int, [_vp, _vp, _u64, _vp]),
+    "wc_table_device_view": (ctypes.c_int, [_vp, ctypes.POINTER(WcDeviceView)]),
     "wc_table_dump_overflow_bits": (ctypes.c_int, [_vp, _vp, _u64, _vp]),
     "wc_table_snapshot_bytes": (_u64, [_vp]),
     "wc_table_snapshot": (ctypes.c_int, [_vp, _vp, _u64, _vp]),

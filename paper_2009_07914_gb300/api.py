@@ -193,6 +193,13 @@ def wc_table_dump_slots(t: int, stream=None) -> np.ndarray:
     return out
 
 
+def wc_table_device_view(t: int) -> B.WcDeviceView:
+    """The table's wc_device_view (device pointers and geometry for user kernels)."""
+    v = B.WcDeviceView()
+    check(lib().wc_table_device_view(t, ctypes.byref(v)), "wc_table_device_view")
+    return v
+
+
 def wc_table_dump_overflow_bits(t: int, stream=None) -> np.ndarray:
     """Host copy of a single-value table's overflow bits (uint32 words, bit w = window w)."""
     info = wc_table_get_info(t)
@@ -221,7 +228,8 @@ def wc_debug_fail_allocations(count: int):
     check(lib().wc_debug_fail_allocations(count), "wc_debug_fail_allocations")
 
 
-__all__ += ["wc_check_status", "wc_table_dump_slots", "wc_table_dump_overflow_bits", "wc_table_snapshot_bytes",
+__all__ += ["wc_check_status", "wc_table_dump_slots", "wc_table_device_view", "wc_table_dump_overflow_bits",
+            "wc_table_snapshot_bytes",
             "wc_table_snapshot",
             "wc_table_restore", "wc_debug_fail_allocations"]
 __all__ += ["WC_SINGLE_VALUE", "WC_MULTI_VALUE", "WC_MULTI_VALUE_OA", "WC_OPT_OVERFLOW_BITS"]

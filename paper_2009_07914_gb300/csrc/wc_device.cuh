@@ -12,6 +12,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "wc_device_api.cuh"
+
 namespace wc {
 
 constexpr uint32_t kFull = 0xffffffffu;
@@ -26,31 +28,12 @@ enum : uint32_t {
   kFlagQueueTimeout = 32u,
 };
 
-// MurmurHash3's 64-bit finalizer "fmix64" (A. Appleby, public domain): an invertible
-// avalanche mix.  h1 and h2 of the outer double hashing are its two 32-bit halves.
-__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
-  k ^= k >> 33;
-  k *= 0xff51afd7ed558ccdull;
-  k ^= k >> 33;
-  k *= 0xc4ceb9fe1a85ec53ull;
-  k ^= k >> 33;
-  return k;
-}
-
-// w_0 = floor(h1 * p / 2^32), step = 1 + floor(h2 * (p - 1) / 2^32); requires p >= 2.
-__device__ __forceinline__ void probe_init(uint64_t key, uint64_t seed, uint32_t p, uint32_t& w,
-                                           uint32_t& step) {
-  const uint64_t h = fmix64(key ^ seed);
-  w = __umulhi(static_cast<uint32_t>(h >> 32), p);
-  step = 1u + __umulhi(static_cast<uint32_t>(h), p - 1u);
-}
-
-// (w + step) mod p for w, step < p < 2^32 (the u32 sum may wrap).
-__device__ __forceinline__ uint32_t probe_next(uint32_t w, uint32_t step, uint32_t p) {
-  uint32_t x = w + step;
-  if (x < w || x >= p) x -= p;
-  return x;
-}
+// The probing sequence (fmix64 hash, first window and step, next window) is the one the
+// public device API defines, so keys inserted by user kernels and by the bulk kernels
+// follow the same sequences.
+using wc_dev::fmix64;
+using wc_dev::probe_init;
+using wc_dev::probe_next;
 
 // ---- vector loads that bypass L1 (L2 is the coherence point for CAS) ----------------
 

@@ -133,6 +133,24 @@ wc_status wc_table_restore(wc_table* t, const void* h_in, uint64_t bytes, void* 
   return to_status(e);
 }
 
+wc_status wc_table_device_view(const wc_table* t, wc_device_view* h_out) {
+  if (t == nullptr || h_out == nullptr) return WC_ERR_INVALID_ARG;
+  if (t->cfg.kind == WC_MULTI_VALUE) return WC_ERR_UNSUPPORTED;
+  h_out->slots = t->d_slots;
+  h_out->status = t->d_status;
+  h_out->size = t->d_size;
+  h_out->overflow_bits = t->d_ovf;
+  h_out->seed = t->cfg.seed;
+  h_out->capacity = t->capacity;
+  h_out->windows = static_cast<uint32_t>(t->windows);
+  h_out->window_width = static_cast<uint32_t>(t->W);
+  h_out->kind = t->cfg.kind;
+  h_out->key_bytes = t->cfg.key_bytes;
+  h_out->value_bytes = t->cfg.value_bytes;
+  h_out->slot_bytes = static_cast<int32_t>(t->slot_bytes);
+  return WC_OK;
+}
+
 wc_status wc_check_status(wc_table* t, uint32_t* h_flags_or_null, void* stream) {
   uint32_t f = 0;
   wc_status st = wc_get_status(t, &f, 1, stream);

@@ -8,6 +8,7 @@
 #include "wc_internal.h"
 #include "wc_launch.cuh"
 #include "wc_roofline.h"
+#include "wc_device_api.cuh"
 
 namespace wc {
 namespace {
@@ -124,10 +125,68 @@ cudaError_t run(void* buf, const wc_rand_access_config& c, uint64_t* sink, cudaS
   return cudaGetLastError();
 }
 
+template <int W>
+__global__ void __launch_bounds__(256) k_dev_insert(wc_device_view v, uint64_t n, uint32_t seed) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t k = static_cast<uint32_t>(i * 2654435761ull) ^ seed;
+    if (!wc_dev::is_sentinel(k)) wc_dev::insert_w<uint32_t, W>(v, k, static_cast<uint32_t>(i));
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) k_dev_lookup(wc_device_view v, uint64_t n, uint32_t seed,
+                                                    unsigned long long* sink) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  unsigned long long acc = 0;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t k = static_cast<uint32_t>(i * 2654435761ull) ^ seed;
+    uint32_t x;
+    if (!wc_dev::is_sentinel(k) && wc_dev::retrieve_w<uint32_t, W>(v, k, x)) acc += x;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(sink, acc);
+}
+
+template <int W>
+void dev_probe(const wc_device_view& v, int mode, uint64_t n, uint32_t seed, unsigned long long* sink, int sms,
+               cudaStream_t s) {
+  if (mode == 0) {
+    const int bps = occupancy(k_dev_insert<W>, 256);
+    k_dev_insert<W><<<bps * sms, 256, 0, s>>>(v, n, seed);
+  } else {
+    const int bps = occupancy(k_dev_lookup<W>, 256);
+    k_dev_lookup<W><<<bps * sms, 256, 0, s>>>(v, n, seed, sink);
+  }
+}
+
 }  // namespace
 }  // namespace wc
 
 extern "C" {
+
+wc_status wc_bench_device_api(wc_table* t, int32_t mode, uint64_t n, uint32_t key_seed, uint64_t* d_sink,
+                              void* stream) {
+  if (t == nullptr || (mode != 0 && mode != 1) || (mode == 1 && d_sink == nullptr)) return WC_ERR_INVALID_ARG;
+  wc_device_view v;
+  wc_status st = wc_table_device_view(t, &v);
+  if (st != WC_OK) return st;
+  if (v.kind != WC_SINGLE_VALUE || v.key_bytes != 4) return WC_ERR_UNSUPPORTED;
+  if (n == 0) return WC_OK;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != t->device) return WC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int sms = wc::sm_count_of(t->device);
+  auto* sink = reinterpret_cast<unsigned long long*>(d_sink);
+  switch (v.window_width) {
+    case 4: wc::dev_probe<4>(v, mode, n, key_seed, sink, sms, s); break;
+    case 8: wc::dev_probe<8>(v, mode, n, key_seed, sink, sms, s); break;
+    case 16: wc::dev_probe<16>(v, mode, n, key_seed, sink, sms, s); break;
+    default: wc::dev_probe<32>(v, mode, n, key_seed, sink, sms, s); break;
+  }
+  return cudaGetLastError() == cudaSuccess ? WC_OK : WC_ERR_CUDA;
+}
 
 wc_status wc_bench_random_access(void* d_buffer, const wc_rand_access_config* cfg, uint64_t* d_sink,
                                  void* stream) {

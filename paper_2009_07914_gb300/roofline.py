@@ -20,6 +20,8 @@ B.extra_signatures({
                                               ctypes.c_void_p]),
     "wc_set_l2_fetch_granularity": (ctypes.c_int, [ctypes.c_int32]),
     "wc_get_l2_fetch_granularity": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32)]),
+    "wc_bench_device_api": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
 })
 
 
@@ -42,6 +44,13 @@ def wc_get_l2_fetch_granularity() -> int:
     v = ctypes.c_int32()
     B.check(B.lib().wc_get_l2_fetch_granularity(ctypes.byref(v)), "wc_get_l2_fetch_granularity")
     return int(v.value)
+
+
+def wc_bench_device_api(table: int, mode: int, n: int, key_seed: int, sink: torch.Tensor | None = None,
+                        stream=None):
+    """Device-API probe (include/wc_roofline.h): mode 0 fused insert, mode 1 fused lookup."""
+    B.check(B.lib().wc_bench_device_api(table, mode, n, key_seed & 0xFFFFFFFF, None if sink is None else B.ptr(sink),
+                                        B.stream_handle(stream)), "wc_bench_device_api")
 
 
 def random_access_rate(buffer: torch.Tensor, access_bytes: int, mode: int = 0, accesses: int = 1 << 28,

@@ -1,0 +1,135 @@
+// A user's program of the device API (include/wc_device_api.cuh): its own kernels insert,
+// look up and erase single elements, and call for_each / for_all with device lambdas.
+// Test infrastructure: built by tests/test_device_api_gpu.py, called through ctypes.
+#include <cstdint>
+
+#include "wc_device_api.cuh"
+
+namespace {
+
+// Keys of the fused producer: an odd-multiplier bijection of the index, so distinct.
+__host__ __device__ uint32_t fused_key(uint64_t i, uint32_t seed) {
+  return static_cast<uint32_t>(i * 2654435761ull) ^ seed;
+}
+
+template <class K>
+__global__ void k_insert(wc_device_view v, const K* keys, const K* vals, uint64_t n, uint32_t* flags) {
+  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const uint32_t f = wc_dev::insert<K>(v, keys[i], vals[i]);
+    if (f) atomicOr(flags, f);
+  }
+}
+
+template <class K>
+__global__ void k_retrieve(wc_device_view v, const K* keys, uint64_t n, K* out, uint8_t* found) {
+  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) {
+    K x = K(~K(0));
+    found[i] = wc_dev::retrieve<K>(v, keys[i], x) ? 1 : 0;
+    out[i] = x;
+  }
+}
+
+template <class K>
+__global__ void k_erase(wc_device_view v, const K* keys, uint64_t n, unsigned long long* erased) {
+  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n && wc_dev::erase<K>(v, keys[i])) atomicAdd(erased, 1ull);
+}
+
+// A fused pipeline: each thread produces its key and inserts it, no batch in memory.
+__global__ void k_fused_insert(wc_device_view v, uint64_t n, uint32_t seed, uint32_t* flags) {
+  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const uint32_t f = wc_dev::insert<uint32_t>(v, fused_key(i, seed), static_cast<uint32_t>(i));
+    if (f) atomicOr(flags, f);
+  }
+}
+
+unsigned grid(uint64_t n) { return static_cast<unsigned>((n + 255) / 256); }
+
+}  // namespace
+
+extern "C" {
+
+int wcu_insert(const wc_device_view* v, const void* keys, const void* vals, uint64_t n, uint32_t* flags) {
+  if (n == 0) return 0;
+  if (v->key_bytes == 4)
+    k_insert<uint32_t><<<grid(n), 256>>>(*v, static_cast<const uint32_t*>(keys), static_cast<const uint32_t*>(vals), n,
+                                        flags);
+  else
+    k_insert<unsigned long long><<<grid(n), 256>>>(*v, static_cast<const unsigned long long*>(keys),
+                                                  static_cast<const unsigned long long*>(vals), n, flags);
+  return static_cast<int>(cudaDeviceSynchronize());
+}
+
+int wcu_retrieve(const wc_device_view* v, const void* keys, uint64_t n, void* out, uint8_t* found) {
+  if (n == 0) return 0;
+  if (v->key_bytes == 4)
+    k_retrieve<uint32_t><<<grid(n), 256>>>(*v, static_cast<const uint32_t*>(keys), n, static_cast<uint32_t*>(out),
+                                          found);
+  else
+    k_retrieve<unsigned long long><<<grid(n), 256>>>(*v, static_cast<const unsigned long long*>(keys), n,
+                                                    static_cast<unsigned long long*>(out), found);
+  return static_cast<int>(cudaDeviceSynchronize());
+}
+
+int wcu_erase(const wc_device_view* v, const void* keys, uint64_t n, unsigned long long* erased) {
+  if (n == 0) return 0;
+  if (v->key_bytes == 4)
+    k_erase<uint32_t><<<grid(n), 256>>>(*v, static_cast<const uint32_t*>(keys), n, erased);
+  else
+    k_erase<unsigned long long><<<grid(n), 256>>>(*v, static_cast<const unsigned long long*>(keys), n, erased);
+  return static_cast<int>(cudaDeviceSynchronize());
+}
+
+int wcu_fused_insert(const wc_device_view* v, uint64_t n, uint32_t seed, uint32_t* flags) {
+  if (n == 0) return 0;
+  k_fused_insert<<<grid(n), 256>>>(*v, n, seed, flags);
+  return static_cast<int>(cudaDeviceSynchronize());
+}
+
+// for_each: sum and count of the values found, and the found mask.
+int wcu_for_each(const wc_device_view* v, const void* keys, uint64_t n, unsigned long long* sums, uint8_t* found) {
+  cudaError_t e;
+  if (v->key_bytes == 4) {
+    e = wc_dev::for_each(*v, static_cast<const uint32_t*>(keys), n,
+                         [sums, found] __device__(uint32_t, uint32_t val, uint64_t i) {
+                           atomicAdd(sums, static_cast<unsigned long long>(val));
+                           atomicAdd(sums + 1, 1ull);
+                           found[i] = 1;
+                         });
+  } else {
+    e = wc_dev::for_each(*v, static_cast<const unsigned long long*>(keys), n,
+                         [sums, found] __device__(unsigned long long, unsigned long long val, uint64_t i) {
+                           atomicAdd(sums, val);
+                           atomicAdd(sums + 1, 1ull);
+                           found[i] = 1;
+                         });
+  }
+  if (e != cudaSuccess) return static_cast<int>(e);
+  return static_cast<int>(cudaDeviceSynchronize());
+}
+
+// for_all: number of stored pairs, sum of their keys and of their values.
+int wcu_for_all(const wc_device_view* v, unsigned long long* sums) {
+  cudaError_t e;
+  if (v->key_bytes == 4) {
+    e = wc_dev::for_all<uint32_t>(*v, [sums] __device__(uint32_t k, uint32_t val, uint64_t) {
+      atomicAdd(sums, 1ull);
+      atomicAdd(sums + 1, static_cast<unsigned long long>(k));
+      atomicAdd(sums + 2, static_cast<unsigned long long>(val));
+    });
+  } else {
+    e = wc_dev::for_all<unsigned long long>(*v, [sums] __device__(unsigned long long k, unsigned long long val,
+                                                                   uint64_t) {
+      atomicAdd(sums, 1ull);
+      atomicAdd(sums + 1, k);
+      atomicAdd(sums + 2, val);
+    });
+  }
+  if (e != cudaSuccess) return static_cast<int>(e);
+  return static_cast<int>(cudaDeviceSynchronize());
+}
+
+}  // extern "C"

@@ -77,7 +77,8 @@ def test_binding_structs_match_the_c_layouts(tmp_path):
     import subprocess
     from paper_2009_07914_gb300 import _binding, roofline, serve
     pairs = [(_binding.WcTableConfig, "wc_table_config"), (_binding.WcTableInfo, "wc_table_info"),
-             (_binding.WcLaunch, "wc_launch"), (roofline.WcRandAccessConfig, "wc_rand_access_config"),
+             (_binding.WcLaunch, "wc_launch"), (_binding.WcDeviceView, "wc_device_view"),
+             (roofline.WcRandAccessConfig, "wc_rand_access_config"),
              (serve.WcWork, "wc_work"), (serve.WcExecutorConfig, "wc_executor_config"),
              (serve.WcRequest, "wc_request"), (serve.WcServeConfig, "wc_serve_config"),
              (serve.WcRequestTiming, "wc_request_timing"), (serve.WcServeStats, "wc_serve_stats")]

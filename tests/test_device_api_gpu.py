@@ -1,0 +1,189 @@
+"""Device-side API (include/wc_device_api.cuh) from a user's program: per-element inserts,
+lookups and erases in user kernels, for_each / for_all with device lambdas, and a fused
+producer kernel.  Each direction is crossed with the bulk calls -- keys inserted by user
+kernels are found by wc_retrieve, keys inserted by wc_insert are found by user kernels --
+and every result is compared with the CPU oracle; the tables' slot dumps pass the
+invariant checker."""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import wc_inputs
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SEED = 0xD1CE
+
+
+@pytest.fixture(scope="module")
+def env(tmp_path_factory):
+    from paper_2009_07914_gb300 import build
+    build.build()
+    import torch
+
+    import paper_2009_07914_gb300 as wc
+    out = str(tmp_path_factory.mktemp("devapi") / "libwcuser.so")
+    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                           "--extended-lambda", "-shared", "-Xcompiler", "-fPIC", "-cudart", "shared",
+                           "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "device_api", "user_kernels.cu"), "-o", out])
+    lib = ctypes.CDLL(out)
+    vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
+    V = ctypes.POINTER(wc._binding.WcDeviceView)
+    lib.wcu_insert.argtypes = [V, vp, vp, u64, vp]
+    lib.wcu_retrieve.argtypes = [V, vp, u64, vp, vp]
+    lib.wcu_erase.argtypes = [V, vp, u64, vp]
+    lib.wcu_fused_insert.argtypes = [V, u64, u32, vp]
+    lib.wcu_for_each.argtypes = [V, vp, u64, vp, vp]
+    lib.wcu_for_all.argtypes = [V, vp]
+    return wc, torch, lib
+
+
+def dev(torch, a, width):
+    from paper_2009_07914_gb300.table import to_device
+    return to_device(a, width, torch.device("cuda", 0))
+
+
+def host(t, width):
+    from paper_2009_07914_gb300.table import to_numpy
+    return to_numpy(t, width)
+
+
+def check_dump(wc, t, opt):
+    info = t.info
+    bits = wc.api.wc_table_dump_overflow_bits(t.handle) if opt else None
+    r = oracle.check_slots(wc.api.wc_table_dump_slots(t.handle), info["windows"], info["window_width"],
+                           info["slot_bytes"], SEED, True, bits)
+    assert r["dups"] == 0 and r["unreachable"] == 0
+    return r
+
+
+@pytest.mark.parametrize("opt", [0, 1])
+@pytest.mark.parametrize("kb,W", [(4, 8), (4, 32), (8, 4), (8, 2)])
+def test_device_ops_interoperate_with_bulk_calls(env, kb, W, opt):
+    wc, torch, lib = env
+    n = 200_003
+    keys = wc_inputs.distinct_u32(71 + W, n) if kb == 4 else wc_inputs.distinct_u64(71 + W, n)
+    vals = (wc_inputs.uniform_u32(72, n) if kb == 4 else wc_inputs.uniform_u64(72, n)).astype(keys.dtype)
+    batch_k = np.concatenate([keys, keys[:5000], np.array([0, keys.dtype.type(~keys.dtype.type(0))], keys.dtype)])
+    batch_v = np.concatenate([vals, vals[:5000] ^ keys.dtype.type(0x5A), np.zeros(2, keys.dtype)])
+    absent = (wc_inputs.distinct_u32(7300 + W, n) | np.uint32(1 << 31)) if kb == 4 else wc_inputs.distinct_u64(7300 + W, n)
+    absent = absent[~np.isin(absent, keys)]
+    queries = np.concatenate([keys, absent[:100_000]])
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    # user-kernel inserts -> bulk retrieve
+    a = wc.SingleValueTable(kb, kb, min_capacity=int(n / 0.9), window_width=W, seed=SEED, options=opt)
+    va = wc.api.wc_table_device_view(a.handle)
+    assert lib.wcu_insert(ctypes.byref(va), dev(torch, batch_k, kb).data_ptr(), dev(torch, batch_v, kb).data_ptr(),
+                          batch_k.size, flags.data_ptr()) == 0
+    o = oracle.SingleValue(kb, kb)
+    of = o.insert(batch_k, batch_v)
+    assert int(flags.item()) == of == oracle.FLAG_DUPLICATE_KEY | oracle.FLAG_INVALID_KEY
+    assert a.status(clear=True) == of
+    assert a.size() == o.size() == n
+    out, found, _ = a.retrieve(queries)
+    eo, ef, _ = o.retrieve(queries)
+    np.testing.assert_array_equal(found, ef)
+    # a key inserted twice in one batch keeps one of its two values
+    dup = np.isin(queries, keys[:5000])
+    np.testing.assert_array_equal(out[~dup], eo[~dup])
+    ok = (out[dup] == eo[dup]) | (out[dup] == (eo[dup] ^ keys.dtype.type(0x5A)))
+    assert ok.all()
+    check_dump(wc, a, opt)
+
+    # bulk insert -> user-kernel retrieve, erase, for_each, for_all
+    b = wc.SingleValueTable(kb, kb, min_capacity=int(n / 0.9), window_width=W, seed=SEED, options=opt)
+    b.insert(keys, vals)
+    o2 = oracle.SingleValue(kb, kb)
+    o2.insert(keys, vals)
+    vb = wc.api.wc_table_device_view(b.handle)
+    qd = dev(torch, queries, kb)
+    outd = torch.empty_like(qd)
+    foundd = torch.empty(queries.size, dtype=torch.uint8, device="cuda")
+    assert lib.wcu_retrieve(ctypes.byref(vb), qd.data_ptr(), queries.size, outd.data_ptr(), foundd.data_ptr()) == 0
+    eo, ef, _ = o2.retrieve(queries)
+    np.testing.assert_array_equal(foundd.cpu().numpy(), ef)
+    np.testing.assert_array_equal(host(outd, kb)[ef == 1], eo[ef == 1])
+    drop = np.concatenate([keys[::4], absent[:1000]])
+    erased = torch.zeros(1, dtype=torch.int64, device="cuda")
+    assert lib.wcu_erase(ctypes.byref(vb), dev(torch, drop, kb).data_ptr(), drop.size, erased.data_ptr()) == 0
+    o2.erase(drop)
+    assert int(erased.item()) == keys[::4].size and b.size() == o2.size()
+    out, found, _ = b.retrieve(queries)
+    eo, ef, _ = o2.retrieve(queries)
+    np.testing.assert_array_equal(found, ef)
+    np.testing.assert_array_equal(out, eo)
+    check_dump(wc, b, opt)
+    sums = torch.zeros(2, dtype=torch.int64, device="cuda")
+    fmask = torch.zeros(queries.size, dtype=torch.uint8, device="cuda")
+    assert lib.wcu_for_each(ctypes.byref(vb), qd.data_ptr(), queries.size, sums.data_ptr(), fmask.data_ptr()) == 0
+    np.testing.assert_array_equal(fmask.cpu().numpy(), ef)
+    s = sums.cpu().numpy().view(np.uint64)
+    assert int(s[1]) == int(ef.sum())
+    assert int(s[0]) == int(eo[ef == 1].astype(np.uint64).sum(dtype=np.uint64))
+    alls = torch.zeros(3, dtype=torch.int64, device="cuda")
+    assert lib.wcu_for_all(ctypes.byref(vb), alls.data_ptr()) == 0
+    live = keys[~np.isin(keys, drop)]
+    lv = vals[~np.isin(keys, drop)]
+    a3 = alls.cpu().numpy().view(np.uint64)
+    assert int(a3[0]) == live.size
+    assert int(a3[1]) == int(live.astype(np.uint64).sum(dtype=np.uint64))
+    assert int(a3[2]) == int(lv.astype(np.uint64).sum(dtype=np.uint64))
+
+
+def test_fused_producer_kernel_and_full_table(env):
+    """A user kernel that produces its keys and inserts them directly (no batch in device
+    memory); the bulk retrieve finds every produced key with its index as value.  A table
+    too small for the stream reports PROBE_LIMIT without hanging."""
+    wc, torch, lib = env
+    n, seed = 1 << 20, 0x1234567
+    t = wc.SingleValueTable(4, 4, min_capacity=int(n / 0.85), seed=SEED, options=wc.WC_OPT_OVERFLOW_BITS)
+    v = wc.api.wc_table_device_view(t.handle)
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert lib.wcu_fused_insert(ctypes.byref(v), n, seed, flags.data_ptr()) == 0
+    idx = np.arange(n, dtype=np.uint64)
+    k = ((idx * np.uint64(2654435761)) & np.uint64(0xFFFFFFFF)).astype(np.uint32) ^ np.uint32(seed)
+    valid = (k != 0) & (k != 0xFFFFFFFF)
+    assert t.size() == int(valid.sum())
+    out, found, _ = t.retrieve(k[valid])
+    assert found.all()
+    np.testing.assert_array_equal(out, idx[valid].astype(np.uint32))
+    check_dump(wc, t, 1)
+    small = wc.SingleValueTable(4, 4, min_capacity=1000, seed=SEED)
+    vs = wc.api.wc_table_device_view(small.handle)
+    flags.zero_()
+    assert lib.wcu_fused_insert(ctypes.byref(vs), 5000, seed, flags.data_ptr()) == 0
+    assert int(flags.item()) & wc.WC_FLAG_PROBE_LIMIT
+    assert small.size() == small.capacity
+    mv = wc.MultiValueTable(8, 4, min_capacity=64, value_pool_capacity=64)
+    with pytest.raises(wc.WcError):  # bucket multi-value tables have no device view
+        wc.api.wc_table_device_view(mv.handle)
+
+
+def test_library_device_api_probe(env):
+    """wc_bench_device_api (the library's own fused producer over the device API) stores
+    exactly the produced pairs, and its lookup pass adds up their values."""
+    wc, torch, lib = env
+    from paper_2009_07914_gb300.roofline import wc_bench_device_api
+    n, seed = 300_001, 0xBEEF
+    t = wc.SingleValueTable(4, 4, min_capacity=int(n / 0.9), seed=SEED, options=wc.WC_OPT_OVERFLOW_BITS)
+    wc_bench_device_api(t.handle, 0, n, seed)
+    idx = np.arange(n, dtype=np.uint64)
+    k = ((idx * np.uint64(2654435761)) & np.uint64(0xFFFFFFFF)).astype(np.uint32) ^ np.uint32(seed)
+    valid = (k != 0) & (k != 0xFFFFFFFF)
+    assert t.size() == int(valid.sum())
+    out, found, _ = t.retrieve(k)
+    np.testing.assert_array_equal(found, valid.astype(np.uint8))
+    np.testing.assert_array_equal(out[valid], idx[valid].astype(np.uint32))
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    wc_bench_device_api(t.handle, 1, n, seed, sink)
+    assert int(sink.item()) == int(idx[valid].sum())
+    check_dump(wc, t, 1)

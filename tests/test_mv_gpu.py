@@ -288,8 +288,9 @@ def test_growth_uniform_r_invariant_and_snapshot(wc):
     wc.api.wc_table_restore(u.handle, snap)
     offs2, _ = u.count_values(d["queries"])
     np.testing.assert_array_equal(offs2, offs)
+    other = wc.MultiValueTable(8, 4, bucket_growth=1.2, **kw)  # held: a freed handle must not be passed
     with pytest.raises(wc.WcError):
-        wc.api.wc_table_restore(wc.MultiValueTable(8, 4, bucket_growth=1.2, **kw).handle, snap)
+        wc.api.wc_table_restore(other.handle, snap)
 
 
 def test_growth_parameters_are_validated(wc):
