@@ -67,8 +67,17 @@ enum {
  *                       sequence (Sec. IV and Sec. V-C, the multi-value hash table).  Insert
  *                       appends; count_values / retrieve_multi walk the sequence up to the
  *                       first window holding an empty slot and count or copy every match;
- *                       erase tombstones every copy.  wc_retrieve is not available. */
-enum { WC_SINGLE_VALUE = 0, WC_MULTI_VALUE = 1, WC_MULTI_VALUE_OA = 2 };
+ *                       erase tombstones every copy.  wc_retrieve is not available.
+ *   WC_HASH_SET         a set of keys (Sec. IV: HashSet), one 4- or 8-byte key per slot
+ *                       (value_bytes 0): insert, wc_contains, erase.
+ *   WC_COUNTING         occurrence counts per key (Sec. IV: CountingHashTable), the
+ *                       single-value slot layouts: an insert of a stored key adds its weight
+ *                       (wc_insert's values; NULL = 1 each) to the stored count, wrapping at
+ *                       the value width; wc_retrieve returns counts; erase removes keys.
+ *   WC_BLOOM_FILTER     set membership with false positives (Sec. IV: BloomFilter): a
+ *                       blocked filter of 256-bit blocks (see wc_bloom_config). */
+enum { WC_SINGLE_VALUE = 0, WC_MULTI_VALUE = 1, WC_MULTI_VALUE_OA = 2, WC_HASH_SET = 3, WC_COUNTING = 4,
+       WC_BLOOM_FILTER = 5 };
 
 /* Table configuration.
  *   kind                 WC_SINGLE_VALUE, WC_MULTI_VALUE or WC_MULTI_VALUE_OA.
@@ -233,7 +242,8 @@ wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint6
 wc_status wc_insert_noalloc(wc_table* t, const void* d_keys, const void* d_values, uint64_t n,
                             void* stream);
 
-/* Single-value retrieve (Sec. IV-B4): d_values_out[i] = value of d_keys[i], or all ones
+/* Single-value retrieve (Sec. IV-B4; counting tables: the counts): d_values_out[i] = value
+ * of d_keys[i], or all ones
  * (NOT_FOUND) when absent; d_found_or_null[i] = 1/0 when the mask is given (a stored value
  * may itself be all ones).  Probing stops at the key or at the first window holding an
  * empty slot.  Multi-value tables return WC_ERR_UNSUPPORTED. */

@@ -58,6 +58,17 @@ def _load():
         lib.oracle_num_keys.restype = u64
         lib.oracle_num_keys.argtypes = [vp]
         lib.oracle_reserve.argtypes = [vp, u64]
+        lib.oracle_counts_create.restype = vp
+        lib.oracle_counts_create.argtypes = [ctypes.c_int, ctypes.c_int]
+        lib.oracle_counts_destroy.argtypes = [vp]
+        lib.oracle_counts_add.restype = u32
+        lib.oracle_counts_add.argtypes = [vp, vp, vp, u64]
+        lib.oracle_counts_get.restype = u32
+        lib.oracle_counts_get.argtypes = [vp, vp, u64, vp, vp]
+        lib.oracle_counts_erase.restype = u32
+        lib.oracle_counts_erase.argtypes = [vp, vp, u64]
+        lib.oracle_counts_size.restype = u64
+        lib.oracle_counts_size.argtypes = [vp]
         lib.oracle_check_slots.restype = ctypes.c_int
         lib.oracle_check_slots.argtypes = [vp, u64, u32, u32, u64, ctypes.c_int, vp, vp, vp, vp]
         _lib = lib
@@ -143,6 +154,62 @@ class MultiValue(_Base):
         out = np.empty(int(offs[-1]), dtype=self.vdt)
         flags = int(self._lib.oracle_retrieve_multi(self._h, _ptr(k), k.size, _ptr(offs), _ptr(out)))
         return out, flags
+
+
+class Counting:
+    """Occurrence counts per key (Sec. IV, CountingHashTable): insert adds each key's
+    weight (1 when no weights) to its count, modulo 2^(8 * key_bytes)."""
+
+    is_set = False
+
+    def __init__(self, key_bytes: int = 4):
+        self._lib = _load()
+        self.kb = key_bytes
+        self.kdt = _dt(key_bytes)
+        self._h = self._lib.oracle_counts_create(key_bytes, int(self.is_set))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.oracle_counts_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _keys(self, keys):
+        return np.ascontiguousarray(np.asarray(keys).astype(self.kdt, copy=False))
+
+    def insert(self, keys, weights=None) -> int:
+        k = self._keys(keys)
+        w = None if weights is None else np.ascontiguousarray(np.asarray(weights).astype(self.kdt, copy=False))
+        return int(self._lib.oracle_counts_add(self._h, _ptr(k), None if w is None else _ptr(w), k.size))
+
+    def retrieve(self, keys):
+        k = self._keys(keys)
+        out = np.empty(k.size, dtype=self.kdt)
+        found = np.empty(k.size, dtype=np.uint8)
+        f = self._lib.oracle_counts_get(self._h, _ptr(k), k.size, _ptr(out), _ptr(found))
+        return out, found, int(f)
+
+    def erase(self, keys) -> int:
+        k = self._keys(keys)
+        return int(self._lib.oracle_counts_erase(self._h, _ptr(k), k.size))
+
+    def size(self) -> int:
+        return int(self._lib.oracle_counts_size(self._h))
+
+
+class HashSet(Counting):
+    """A set of keys (Sec. IV, HashSet): insert raises DUPLICATE_KEY for a key already in
+    the set; contains(keys) -> found mask."""
+
+    is_set = True
+
+    def contains(self, keys):
+        k = self._keys(keys)
+        found = np.empty(k.size, dtype=np.uint8)
+        f = self._lib.oracle_counts_get(self._h, _ptr(k), k.size, None, _ptr(found))
+        return found, int(f)
 
 
 def sorted_segments(values: np.ndarray, offsets: np.ndarray) -> np.ndarray:

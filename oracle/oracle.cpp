@@ -264,6 +264,91 @@ void oracle_reserve(void* p, uint64_t n) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------
+// Counting table (Sec. IV, "CountingHashTable": counts key occurrences) and hash set
+// (Sec. IV, "HashSet": a set of keys, each once), by their plain definitions.
+//   counting: add(k, w) -> C[k] += w (w = 1 when no weights), modulo 2^(8 * width);
+//             get(k) -> C[k] or NOT_FOUND; erase(k) removes k.
+//   set:      add(k) -> S += {k} (DUPLICATE_KEY when k was in S); contains(k); erase(k).
+// Keys and counts have the same width (4 or 8 bytes).
+namespace {
+
+struct Counts {
+  int kb;
+  bool set;
+  std::unordered_map<uint64_t, uint64_t> m;
+};
+
+uint64_t key_at(const void* keys, int kb, uint64_t i) {
+  return kb == 4 ? static_cast<const uint32_t*>(keys)[i] : static_cast<const uint64_t*>(keys)[i];
+}
+
+bool sentinel_w(uint64_t k, int kb) { return k == 0 || k == (kb == 4 ? 0xffffffffull : ~0ull); }
+
+}  // namespace
+
+extern "C" {
+
+void* oracle_counts_create(int key_bytes, int is_set) {
+  if (key_bytes != 4 && key_bytes != 8) return nullptr;
+  return new Counts{key_bytes, is_set != 0, {}};
+}
+
+void oracle_counts_destroy(void* p) { delete static_cast<Counts*>(p); }
+
+uint32_t oracle_counts_add(void* p, const void* keys, const void* weights, uint64_t n) {
+  auto* c = static_cast<Counts*>(p);
+  const uint64_t mask = c->kb == 4 ? 0xffffffffull : ~0ull;
+  uint32_t f = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint64_t k = key_at(keys, c->kb, i);
+    if (sentinel_w(k, c->kb)) { f |= F_INVALID; continue; }
+    auto it = c->m.find(k);
+    if (c->set) {
+      if (it != c->m.end()) f |= F_DUPLICATE;
+      else c->m.emplace(k, 0);
+      continue;
+    }
+    const uint64_t w = weights ? key_at(weights, c->kb, i) : 1;
+    if (it == c->m.end()) c->m.emplace(k, w & mask);
+    else it->second = (it->second + w) & mask;
+  }
+  return f;
+}
+
+uint32_t oracle_counts_get(void* p, const void* keys, uint64_t n, void* out, uint8_t* found) {
+  auto* c = static_cast<Counts*>(p);
+  uint32_t f = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint64_t k = key_at(keys, c->kb, i);
+    if (sentinel_w(k, c->kb)) f |= F_INVALID;
+    auto it = sentinel_w(k, c->kb) ? c->m.end() : c->m.find(k);
+    const bool hit = it != c->m.end();
+    const uint64_t v = hit ? it->second : ~0ull;
+    if (out) {
+      if (c->kb == 4) static_cast<uint32_t*>(out)[i] = static_cast<uint32_t>(v);
+      else static_cast<uint64_t*>(out)[i] = v;
+    }
+    if (found) found[i] = hit ? 1 : 0;
+  }
+  return f;
+}
+
+uint32_t oracle_counts_erase(void* p, const void* keys, uint64_t n) {
+  auto* c = static_cast<Counts*>(p);
+  uint32_t f = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint64_t k = key_at(keys, c->kb, i);
+    if (sentinel_w(k, c->kb)) { f |= F_INVALID; continue; }
+    c->m.erase(k);
+  }
+  return f;
+}
+
+uint64_t oracle_counts_size(void* p) { return static_cast<Counts*>(p)->m.size(); }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
 // Slot-dump invariant checker (layout, not values).  Given a host copy of a table's slot
 // array it checks the two properties that make the early exit of Sec. IV-B4 correct:
 //   * reachability: walking a live key's probing sequence window by window, the window

@@ -10,6 +10,6 @@ from ._binding import (WC_FLAG_COUNT_OVERFLOW, WC_FLAG_DUPLICATE_KEY, WC_FLAG_IN
                        WC_OP_INSERT, WC_OP_RETRIEVE, WC_SCHEME_AUTO, WC_SCHEME_BLOCKED, WC_SCHEME_DIRECT,
                        WC_SINGLE_VALUE, WC_MULTI_VALUE_OA, WC_OPT_OVERFLOW_BITS, WcError, lib)
 from .api import *  # noqa: F401,F403  (the C-ABI names)
-from .table import MultiValueOATable, MultiValueTable, SingleValueTable
+from .table import CountingTable, MultiValueOATable, MultiValueTable, SingleValueTable
 
-__all__ = ["api", "lib", "WcError", "SingleValueTable", "MultiValueTable", "MultiValueOATable"] + list(api.__all__)
+__all__ = ["api", "lib", "WcError", "SingleValueTable", "MultiValueTable", "MultiValueOATable", "CountingTable"] + list(api.__all__)

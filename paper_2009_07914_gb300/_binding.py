@@ -33,6 +33,9 @@ WC_FLAG_QUEUE_TIMEOUT = 32
 WC_SINGLE_VALUE = 0
 WC_MULTI_VALUE = 1
 WC_MULTI_VALUE_OA = 2
+WC_HASH_SET = 3
+WC_COUNTING = 4
+WC_BLOOM_FILTER = 5
 WC_OPT_OVERFLOW_BITS = 1
 
 WC_SCHEME_AUTO = 0

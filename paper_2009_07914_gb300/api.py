@@ -13,7 +13,8 @@ import numpy as np
 import torch
 
 from . import _binding as B
-from ._binding import (WC_MULTI_VALUE, WC_MULTI_VALUE_OA, WC_OPT_OVERFLOW_BITS, WC_SINGLE_VALUE, WcLaunch,
+from ._binding import (WC_BLOOM_FILTER, WC_COUNTING, WC_HASH_SET, WC_MULTI_VALUE, WC_MULTI_VALUE_OA,
+                       WC_OPT_OVERFLOW_BITS, WC_SINGLE_VALUE, WcLaunch,
                        WcTableConfig, WcTableInfo, check, lib, ptr, stream_handle)
 
 __all__ = [
@@ -94,8 +95,10 @@ def wc_table_get_launch(t: int, op: int) -> dict:
 
 
 def wc_insert(t: int, keys, values, n: int | None = None, stream=None):
+    """values may be None for counting tables (every key counts 1)."""
     n = _n_of(n, keys)
-    _n_of(n, values)
+    if values is not None:
+        _n_of(n, values)
     check(lib().wc_insert(t, ptr(keys), ptr(values), n, stream_handle(stream)), "wc_insert")
 
 
@@ -232,4 +235,5 @@ __all__ += ["wc_check_status", "wc_table_dump_slots", "wc_table_device_view", "w
             "wc_table_snapshot_bytes",
             "wc_table_snapshot",
             "wc_table_restore", "wc_debug_fail_allocations"]
-__all__ += ["WC_SINGLE_VALUE", "WC_MULTI_VALUE", "WC_MULTI_VALUE_OA", "WC_OPT_OVERFLOW_BITS"]
+__all__ += ["WC_SINGLE_VALUE", "WC_MULTI_VALUE", "WC_MULTI_VALUE_OA", "WC_HASH_SET", "WC_COUNTING",
+            "WC_BLOOM_FILTER", "WC_OPT_OVERFLOW_BITS"]

@@ -23,6 +23,8 @@ bool sv_p32_shape_ok(int W, int G);
 bool sv_p64_shape_ok(int W, int G);
 bool mv_shape_ok(int W, int G);
 bool oa_p32_shape_ok(int W, int G);
+bool count_shape_ok(int slot_bytes, int W, int G);
+cudaError_t count_insert(const wc_table* t, const void* keys, const void* weights, uint64_t n, cudaStream_t s);
 bool oa_p64_shape_ok(int W, int G);
 cudaError_t oa_p32_launch(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n, uint64_t* offs,
                           void* out, cudaStream_t s);
@@ -63,7 +65,7 @@ uint64_t next_prime(uint64_t x) {
 }
 
 bool slot_layout(const wc_table_config& c, uint64_t* slot_bytes) {
-  if (c.kind == WC_SINGLE_VALUE || c.kind == WC_MULTI_VALUE_OA) {
+  if (c.kind == WC_SINGLE_VALUE || c.kind == WC_MULTI_VALUE_OA || c.kind == WC_COUNTING) {
     if (c.key_bytes == 4 && c.value_bytes == 4) { *slot_bytes = 8; return true; }
     if (c.key_bytes == 8 && c.value_bytes == 8) { *slot_bytes = 16; return true; }
     return false;
@@ -86,6 +88,7 @@ bool window_ok(int kind, uint64_t slot_bytes, int W) {
 bool shape_ok(const wc_table* t, int op, int G) {
   const int W = static_cast<int>(t->W);
   if (t->cfg.kind == WC_MULTI_VALUE_OA) return t->slot_bytes == 8 ? oa_p32_shape_ok(W, G) : oa_p64_shape_ok(W, G);
+  if (t->cfg.kind == WC_COUNTING && op == WC_OP_INSERT) return count_shape_ok(static_cast<int>(t->slot_bytes), W, G);
   if (t->slot_bytes == 8) return sv_p32_shape_ok(W, G);
   if (t->cfg.kind == WC_MULTI_VALUE) {
     if (op == WC_OP_INSERT || op == WC_OP_RETRIEVE) return G == 1;  // one thread per distinct key
@@ -346,7 +349,8 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
       }
     }
   }
-  if ((cfg->options & WC_OPT_OVERFLOW_BITS) && cfg->kind != WC_SINGLE_VALUE) return WC_ERR_INVALID_ARG;
+  if ((cfg->options & WC_OPT_OVERFLOW_BITS) && cfg->kind != WC_SINGLE_VALUE && cfg->kind != WC_COUNTING)
+    return WC_ERR_INVALID_ARG;
   if (mv && cfg->value_pool_capacity > kMaxPool) return WC_ERR_INVALID_ARG;
 
   uint64_t p = 0, cap = 0;
@@ -368,7 +372,7 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   t->sm_count = sm_count_of(t->device);
 
   // One allocation: [slots | meta 256 B | overflow bits (SV) | pending (MV) | scan partials (MV, OA) | pool (MV)]
-  const bool sv = cfg->kind == WC_SINGLE_VALUE && (cfg->options & WC_OPT_OVERFLOW_BITS);
+  const bool sv = (cfg->kind == WC_SINGLE_VALUE || cfg->kind == WC_COUNTING) && (cfg->options & WC_OPT_OVERFLOW_BITS);
   const uint64_t off_meta = align_up(t->table_bytes, kAlign);
   const uint64_t off_ovf = off_meta + kAlign;
   const uint64_t ovf_bytes = sv ? align_up((p + 31) / 32 * 4, kAlign) : 0;
@@ -493,7 +497,8 @@ wc_status wc_table_set_launch(wc_table* t, int32_t op, const wc_launch* launch) 
       launch->region_mib > 4096)
     return WC_ERR_INVALID_ARG;
   if (launch->scheme == WC_SCHEME_BLOCKED &&
-      !((op == WC_OP_INSERT && t->cfg.kind != WC_MULTI_VALUE) || (op == WC_OP_RETRIEVE && t->cfg.kind == WC_SINGLE_VALUE)))
+      !((op == WC_OP_INSERT && t->cfg.kind != WC_MULTI_VALUE) ||
+        (op == WC_OP_RETRIEVE && (t->cfg.kind == WC_SINGLE_VALUE || t->cfg.kind == WC_COUNTING))))
     return WC_ERR_UNSUPPORTED;
   if (!shape_ok(t, op, launch->group_size)) return WC_ERR_INVALID_ARG;
   t->launch[op] = *launch;
@@ -517,9 +522,15 @@ static wc_status check_bulk(const wc_table* t, const void* keys, uint64_t n) {
 wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint64_t n, void* stream) {
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
-  if (n > 0 && (d_values == nullptr || !aligned(d_values, static_cast<uint64_t>(t->cfg.value_bytes))))
+  const bool weights_optional = t->cfg.kind == WC_COUNTING;
+  if (n > 0 && ((d_values == nullptr && !weights_optional) ||
+                (d_values != nullptr && !aligned(d_values, static_cast<uint64_t>(t->cfg.value_bytes)))))
     return WC_ERR_INVALID_ARG;
   if (n == 0) return WC_OK;
+  if (t->cfg.kind == WC_COUNTING) {
+    DeviceGuard guard(t->device);
+    return cuda_status(count_insert(t, d_keys, d_values, n, as_stream(stream)));
+  }
   if (t->cfg.kind == WC_MULTI_VALUE && n >= kMaxMvBatch) return WC_ERR_INVALID_ARG;
   DeviceGuard guard(t->device);
   if (t->cfg.kind == WC_MULTI_VALUE) return cuda_status(mv_insert(t, d_keys, d_values, n, as_stream(stream)));
@@ -532,7 +543,7 @@ wc_status wc_retrieve(wc_table* t, const void* d_keys, uint64_t n, void* d_value
                       void* stream) {
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
-  if (t->cfg.kind != WC_SINGLE_VALUE) return WC_ERR_UNSUPPORTED;
+  if (t->cfg.kind != WC_SINGLE_VALUE && t->cfg.kind != WC_COUNTING) return WC_ERR_UNSUPPORTED;
   if (n > 0 && (d_values_out == nullptr || !aligned(d_values_out, static_cast<uint64_t>(t->cfg.value_bytes))))
     return WC_ERR_INVALID_ARG;
   if (n == 0) return WC_OK;
@@ -556,7 +567,7 @@ wc_status wc_count_values(wc_table* t, const void* d_keys, uint64_t n, uint64_t*
                           uint64_t* h_total_or_null, void* stream) {
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
-  if (t->cfg.kind == WC_SINGLE_VALUE) return WC_ERR_UNSUPPORTED;
+  if (t->cfg.kind != WC_MULTI_VALUE && t->cfg.kind != WC_MULTI_VALUE_OA) return WC_ERR_UNSUPPORTED;
   if (d_offsets == nullptr || !aligned(d_offsets, 8)) return WC_ERR_INVALID_ARG;
   DeviceGuard guard(t->device);
   cudaStream_t s = as_stream(stream);
@@ -579,7 +590,7 @@ wc_status wc_retrieve_multi(wc_table* t, const void* d_keys, uint64_t n, const u
                             void* d_values_out, void* stream) {
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
-  if (t->cfg.kind == WC_SINGLE_VALUE) return WC_ERR_UNSUPPORTED;
+  if (t->cfg.kind != WC_MULTI_VALUE && t->cfg.kind != WC_MULTI_VALUE_OA) return WC_ERR_UNSUPPORTED;
   if (d_offsets == nullptr || !aligned(d_offsets, 8)) return WC_ERR_INVALID_ARG;
   if (n > 0 && (d_values_out == nullptr || !aligned(d_values_out, static_cast<uint64_t>(t->cfg.value_bytes))))
     return WC_ERR_INVALID_ARG;

@@ -112,6 +112,7 @@ struct LayoutP32 {
     unsigned long long w;
   };
   static constexpr int kWords = 1;
+  static constexpr bool kCount = false;  // duplicates overwrite the value (single-value table)
   static constexpr Key kEmpty = 0u;
   static constexpr Key kTomb = 0xffffffffu;
   static constexpr Val kNotFound = 0xffffffffu;
@@ -141,6 +142,7 @@ struct LayoutP64 {
     unsigned long long k, v;
   };
   static constexpr int kWords = 2;
+  static constexpr bool kCount = false;
   static constexpr Key kEmpty = 0ull;
   static constexpr Key kTomb = ~0ull;
   static constexpr Val kNotFound = ~0ull;
@@ -168,6 +170,18 @@ struct LayoutP64 {
   __device__ static Slot shfl(const Slot& s, int src) {
     return Slot{__shfl_sync(kFull, s.k, src), __shfl_sync(kFull, s.v, src)};
   }
+};
+
+// Counting tables (the paper's CountingHashTable: counts key occurrences): the same slot
+// words, but an insert of a stored key adds its weight to the stored count with one
+// atomic add on the value word instead of overwriting it.
+struct LayoutC32 : LayoutP32 {
+  static constexpr bool kCount = true;
+  __device__ static void store_val(Slot* p, Val v) { atomicAdd(reinterpret_cast<uint32_t*>(&p->w) + 1, v); }
+};
+struct LayoutC64 : LayoutP64 {
+  static constexpr bool kCount = true;
+  __device__ static void store_val(Slot* p, Val v) { atomicAdd(&p->v, v); }
 };
 
 // S consecutive slots of one lane.

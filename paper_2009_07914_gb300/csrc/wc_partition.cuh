@@ -127,8 +127,11 @@ struct ScatterSmem {
   unsigned int w32[kPartThreads / 32];
 };
 
-// kIota: the value of element i is its input position i (vals is not read).
-template <class K, class V, class M = RegionMap, bool kIota = false>
+// Where the values of a split come from: read from `vals`, element i's input position i,
+// or 1 (vals is not read in the last two).
+enum { kValsRead = 0, kValsIota = 1, kValsOne = 2 };
+
+template <class K, class V, class M = RegionMap, int kVals = kValsRead>
 __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const K* __restrict__ keys, const V* __restrict__ vals,
                                                                uint64_t n, M m,
                                                                const unsigned int* __restrict__ hist,
@@ -155,8 +158,10 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const K* __restri
       rr[k] = 0xffffffffu;
       if (i < tn) {
         kk[k] = ldg_stream(keys + t0 + i);
-        if constexpr (kIota) {
+        if constexpr (kVals == kValsIota) {
           vv[k] = static_cast<V>(t0 + i);
+        } else if constexpr (kVals == kValsOne) {
+          vv[k] = V(1);
         } else {
           vv[k] = ldg_stream(vals + t0 + i);
         }
@@ -217,9 +222,9 @@ struct RegionSplit {
 inline uint64_t align256(uint64_t x) { return (x + 255) / 256 * 256; }
 
 // Regions of about region_mib MiB of slots (at most kMaxRegions of them).  Scratch layout:
-// [header kSplitHeader B | keys | vals | extra], grown on demand.  kIota: the values are
-// the input positions (uint32), `vals` is not read.
-template <class K, class V, bool kIota = false>
+// [header kSplitHeader B | keys | vals | extra], grown on demand.  kVals: where the values
+// come from (kValsIota: the input positions as uint32; kValsOne: all 1).
+template <class K, class V, int kVals = kValsRead>
 cudaError_t region_split(const wc_table* t, int region_mib, const K* keys, const V* vals, uint64_t n, cudaStream_t s,
                          RegionSplit<K, V>& out, uint64_t extra = 0) {
   static_assert(kMaxRegions * sizeof(unsigned long long) <= kSplitCnt - kSplitCursor, "cursor area");
@@ -244,7 +249,7 @@ cudaError_t region_split(const wc_table* t, int region_mib, const K* keys, const
   e = cudaMemsetAsync(sc, 0, kSplitHeader, s);
   if (e != cudaSuccess) return e;
   auto hk = k_part_hist<K>;
-  auto sk = k_part_scatter<K, V, RegionMap, kIota>;
+  auto sk = k_part_scatter<K, V, RegionMap, kVals>;
   const size_t hsm = static_cast<size_t>(kHistWarps) * m.R * sizeof(unsigned int);
   const size_t ssm = scatter_smem_bytes<K, V>();
   static bool attr = false;

@@ -23,7 +23,7 @@ cudaError_t sv_retrieve_blocked(const wc_table* t, const wc_launch& lc, const ty
   const uint64_t rv_off = align256(n * sizeof(uint32_t));
   const uint64_t extra = rv_off + align256(n * sizeof(Val));
   RegionSplit<Key, uint32_t> sp;
-  cudaError_t e = region_split<Key, uint32_t, true>(t, lc.region_mib, k, nullptr, n, s, sp, extra);
+  cudaError_t e = region_split<Key, uint32_t, kValsIota>(t, lc.region_mib, k, nullptr, n, s, sp, extra);
   if (e != cudaSuccess) return e;
   auto* rk = reinterpret_cast<uint32_t*>(sp.extra);
   auto* rv = reinterpret_cast<Val*>(sp.extra + rv_off);
@@ -37,7 +37,7 @@ cudaError_t sv_retrieve_blocked(const wc_table* t, const wc_launch& lc, const ty
                sp.keys, sp.vals, n, sp.counters, 512u, rk, rv);
   if (e != cudaSuccess) return e;
   k_index_hist<<<(im.R + 255) / 256, 256, 0, s>>>(sp.hist2, im.R, im.per, n);
-  auto sk = k_part_scatter<uint32_t, Val, IndexMap, false>;
+  auto sk = k_part_scatter<uint32_t, Val, IndexMap, kValsRead>;
   const size_t ssm = scatter_smem_bytes<uint32_t, Val>();
   static bool attr = false;
   if (!attr) {
@@ -55,29 +55,40 @@ cudaError_t sv_retrieve_blocked(const wc_table* t, const wc_launch& lc, const ty
   return cudaGetLastError();
 }
 
+// Insert (direct, or the blocked scheme: split the batch by table region, then insert it
+// region by region).  vals == nullptr (counting tables): every key counts 1.
+template <class L, int G, int S>
+cudaError_t sv_insert_op(const wc_table* t, const void* keys, const void* vals, uint64_t n, cudaStream_t s) {
+  using Key = typename L::Key;
+  using Val = typename L::Val;
+  const wc_launch& lc = t->launch[WC_OP_INSERT];
+  const int block = lc.block_threads;
+  const TableDesc d = desc_of(t);
+  const Key* k = static_cast<const Key*>(keys);
+  auto kern = k_sv_insert<L, G, S>;
+  const int bps = lc.blocks_per_sm > 0 ? lc.blocks_per_sm : occupancy(kern, block);
+  const EngineGrid g = engine_grid(n, G, block, bps, t->sm_count);
+  if (scheme_for(t, WC_OP_INSERT, n) != WC_SCHEME_BLOCKED)
+    return launch_k(t, kern, g.blocks, block, 0, s, d, k, static_cast<const Val*>(vals), n, g.per_warp,
+                    static_cast<unsigned long long*>(nullptr), 0u);
+  RegionSplit<Key, Val> sp;
+  cudaError_t e = vals != nullptr ? region_split(t, lc.region_mib, k, static_cast<const Val*>(vals), n, s, sp)
+                                  : region_split<Key, Val, kValsOne>(t, lc.region_mib, k, nullptr, n, s, sp);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = static_cast<unsigned>(bps) * static_cast<unsigned>(t->sm_count);
+  return launch_k(t, kern, grid, block, 0, s, d, sp.keys, sp.vals, n, static_cast<uint64_t>(0), sp.counters, 512u);
+}
+
 template <class L, int G, int S>
 cudaError_t sv_run(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n, void* out,
                    uint8_t* found, cudaStream_t s) {
   using Key = typename L::Key;
   using Val = typename L::Val;
+  if (op == WC_OP_INSERT) return sv_insert_op<L, G, S>(t, keys, vals, n, s);
   const wc_launch& lc = t->launch[op];
   const int block = lc.block_threads;
   const TableDesc d = desc_of(t);
   const Key* k = static_cast<const Key*>(keys);
-  if (op == WC_OP_INSERT) {
-    auto kern = k_sv_insert<L, G, S>;
-    const int bps = lc.blocks_per_sm > 0 ? lc.blocks_per_sm : occupancy(kern, block);
-    const EngineGrid g = engine_grid(n, G, block, bps, t->sm_count);
-    if (scheme_for(t, op, n) != WC_SCHEME_BLOCKED)
-      return launch_k(t, kern, g.blocks, block, 0, s, d, k, static_cast<const Val*>(vals), n, g.per_warp,
-                      static_cast<unsigned long long*>(nullptr), 0u);
-    // blocked scheme: split the batch by table region, then insert it region by region
-    RegionSplit<Key, Val> sp;
-    cudaError_t e = region_split(t, lc.region_mib, k, static_cast<const Val*>(vals), n, s, sp);
-    if (e != cudaSuccess) return e;
-    const unsigned grid = static_cast<unsigned>(bps) * static_cast<unsigned>(t->sm_count);
-    return launch_k(t, kern, grid, block, 0, s, d, sp.keys, sp.vals, n, static_cast<uint64_t>(0), sp.counters, 512u);
-  }
   if (op == WC_OP_RETRIEVE) {
     if (scheme_for(t, op, n) == WC_SCHEME_BLOCKED && n < (1ull << 31))
       return sv_retrieve_blocked<L, G, S>(t, lc, k, n, static_cast<Val*>(out), found, s);

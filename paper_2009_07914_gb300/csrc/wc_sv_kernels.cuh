@@ -332,20 +332,21 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
   Slot t_word{};           // and the word read there
   Feed<Key> fk;
   Feed<Val> fv;
+  const bool unit = vals == nullptr;  // counting tables without weights: every occurrence counts 1
   while (true) {
     const bool more = src.ensure();
     if (more && src.fresh) {
       fk.load(keys, src.next, src.end);
-      fv.load(vals, src.next, src.end);
+      if (!unit) fv.load(vals, src.next, src.end);
       src.fresh = false;
     }
     uint64_t np = 0;
     const bool got = more && take_next(!act, ln.r, ln.gbase, src.next, src.end, np);
     const Key kin = fk.get(np, got);
-    const Val vin = fv.get(np, got);
+    const Val vin = unit ? Val(1) : fv.get(np, got);
     if (more) {
       fk.advance(src.next);
-      fv.advance(src.next);
+      if (!unit) fv.advance(src.next);
     }
     if (got) {
       pos = np;
@@ -411,7 +412,7 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
 
     if (act) {
       if (bm) {
-        flags |= kFlagDuplicate;
+        if constexpr (!L::kCount) flags |= kFlagDuplicate;
         act = false;
       } else if (claim) {
         if (ok) {

@@ -7,7 +7,7 @@ import numpy as np
 import torch
 
 from . import api
-from ._binding import WC_MULTI_VALUE, WC_MULTI_VALUE_OA, WC_SINGLE_VALUE
+from ._binding import WC_COUNTING, WC_MULTI_VALUE, WC_MULTI_VALUE_OA, WC_SINGLE_VALUE
 
 _INT = {4: torch.int32, 8: torch.int64}
 _NP_SIGNED = {4: np.int32, 8: np.int64}
@@ -129,3 +129,17 @@ class MultiValueTable(_Table):
 class MultiValueOATable(MultiValueTable):
     """Open-addressing multi-value table: one slot per stored pair (4+4 or 8+8 bytes)."""
     kind = WC_MULTI_VALUE_OA
+
+
+class CountingTable(SingleValueTable):
+    """Occurrence counts per key (key and count of the same width, 4 or 8 bytes)."""
+    kind = WC_COUNTING
+
+    def __init__(self, key_bytes=4, min_capacity=1024, **kw):
+        super().__init__(key_bytes, key_bytes, min_capacity=min_capacity, **kw)
+
+    def insert(self, keys, weights=None, stream=None):
+        k = self.keys_dev(keys)
+        w = None if weights is None else self.values_dev(weights)
+        api.wc_insert(self.handle, k, w, stream=stream)
+        return api.wc_get_status(self.handle, clear=True, stream=stream)

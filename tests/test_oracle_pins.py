@@ -209,3 +209,60 @@ def test_sentinels_are_rejected():
     o = oracle.SingleValue(8, 8)
     f = o.insert(np.array([0, 2 ** 64 - 1, 3], dtype=np.uint64), np.array([1, 2, 3], dtype=np.uint64))
     assert f == oracle.FLAG_INVALID_KEY and o.size() == 1
+
+
+# ---- counting table and hash set (Sec. IV: CountingHashTable, HashSet) ----------------------
+
+@pytest.mark.parametrize("kb", [4, 8])
+def test_counting_oracle_against_brute_force(kb):
+    """Counts equal np.unique's occurrence counts (unit weights), weighted sums wrap at the
+    key width, erase removes keys; sentinels are skipped and flagged."""
+    rng = np.random.default_rng(40 + kb)
+    top = (1 << (8 * kb)) - 1
+    universe = np.unique(rng.integers(1, min(top, 2 ** 62), 500, dtype=np.uint64))
+    o = oracle.Counting(kb)
+    ref = {}
+    mask = (1 << (8 * kb)) - 1
+    for step in range(6):
+        ks = universe[rng.integers(0, universe.size, 3000)]
+        if step % 2:
+            ws = rng.integers(0, top, ks.size, dtype=np.uint64, endpoint=True)
+            assert o.insert(ks, ws) == 0
+            for k, w in zip(ks.tolist(), ws.tolist()):
+                ref[k] = (ref.get(k, 0) + w) & mask
+        else:
+            assert o.insert(ks) == 0
+            u, c = np.unique(ks, return_counts=True)
+            for k, n in zip(u.tolist(), c.tolist()):
+                ref[k] = (ref.get(k, 0) + n) & mask
+        if step == 3:
+            drop = universe[:50]
+            o.erase(drop)
+            for k in drop.tolist():
+                ref.pop(k, None)
+        out, found, _ = o.retrieve(universe)
+        want = np.array([ref.get(k, mask) for k in universe.tolist()], dtype=np.uint64)
+        np.testing.assert_array_equal(found, np.array([k in ref for k in universe.tolist()], np.uint8))
+        np.testing.assert_array_equal(out.astype(np.uint64), want)
+        assert o.size() == len(ref)
+    assert o.insert(np.array([0, mask, 5], dtype=np.uint64)) == oracle.FLAG_INVALID_KEY
+
+
+@pytest.mark.parametrize("kb", [4, 8])
+def test_hash_set_oracle_against_python_set(kb):
+    rng = np.random.default_rng(50 + kb)
+    universe = np.unique(rng.integers(1, 2 ** 31, 800, dtype=np.uint64))
+    o = oracle.HashSet(kb)
+    ref = set()
+    for step in range(5):
+        ks = universe[rng.integers(0, universe.size, 400)]
+        f = o.insert(ks)
+        dup = any(k in ref for k in ks.tolist()) or len(set(ks.tolist())) < ks.size
+        assert f == (oracle.FLAG_DUPLICATE_KEY if dup else 0)
+        ref.update(ks.tolist())
+        if step == 2:
+            o.erase(universe[::3])
+            ref.difference_update(universe[::3].tolist())
+        found, _ = o.contains(universe)
+        np.testing.assert_array_equal(found, np.array([k in ref for k in universe.tolist()], np.uint8))
+        assert o.size() == len(ref)
