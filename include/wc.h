@@ -75,7 +75,13 @@ enum {
  *                       (wc_insert's values; NULL = 1 each) to the stored count, wrapping at
  *                       the value width; wc_retrieve returns counts; erase removes keys.
  *   WC_BLOOM_FILTER     set membership with false positives (Sec. IV: BloomFilter): a
- *                       blocked filter of 256-bit blocks (see wc_bloom_config). */
+ *                       blocked filter -- each key sets k bits inside one 256-bit block
+ *                       (one 32-byte sector) picked by its hash.  min_capacity = bits
+ *                       (rounded up to whole blocks), window_width = k (1..16, 0 = 8),
+ *                       value_bytes 0; insert and wc_contains only (no erase); wc_size
+ *                       counts inserted keys.  False-positive rate for n keys in m bits:
+ *                       about the average over blocks of (1 - exp(-k x / 256))^k, x the
+ *                       block's key count (Poisson with mean 256 n / m). */
 enum { WC_SINGLE_VALUE = 0, WC_MULTI_VALUE = 1, WC_MULTI_VALUE_OA = 2, WC_HASH_SET = 3, WC_COUNTING = 4,
        WC_BLOOM_FILTER = 5 };
 
@@ -249,6 +255,11 @@ wc_status wc_insert_noalloc(wc_table* t, const void* d_keys, const void* d_value
  * empty slot.  Multi-value tables return WC_ERR_UNSUPPORTED. */
 wc_status wc_retrieve(wc_table* t, const void* d_keys, uint64_t n, void* d_values_out,
                       uint8_t* d_found_or_null, void* stream);
+
+/* Membership (Sec. IV-B4 without values): d_found[i] = 1 if d_keys[i] is stored, else 0
+ * (Bloom filters: 1 if all the key's bits are set -- possibly a false positive, never a
+ * false negative).  Single-value, counting, hash-set and Bloom-filter tables. */
+wc_status wc_contains(wc_table* t, const void* d_keys, uint64_t n, uint8_t* d_found, void* stream);
 
 /* Erase (Sec. IV-B5): the key's slot becomes a tombstone; absent keys are a no-op.
  * Multi-value: removes every value of the key (bucket table: its pool space is not

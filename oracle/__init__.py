@@ -70,7 +70,14 @@ def _load():
         lib.oracle_counts_size.restype = u64
         lib.oracle_counts_size.argtypes = [vp]
         lib.oracle_check_slots.restype = ctypes.c_int
-        lib.oracle_check_slots.argtypes = [vp, u64, u32, u32, u64, ctypes.c_int, vp, vp, vp, vp]
+        lib.oracle_check_slots.argtypes = [vp, u64, u32, u32, u32, u64, ctypes.c_int, vp, vp, vp, vp]
+        lib.oracle_bloom_create.restype = vp
+        lib.oracle_bloom_create.argtypes = [ctypes.c_int, u64, ctypes.c_int, u64]
+        lib.oracle_bloom_destroy.argtypes = [vp]
+        lib.oracle_bloom_insert.restype = u32
+        lib.oracle_bloom_insert.argtypes = [vp, vp, u64]
+        lib.oracle_bloom_contains.restype = u32
+        lib.oracle_bloom_contains.argtypes = [vp, vp, u64, vp]
         _lib = lib
     return _lib
 
@@ -212,6 +219,36 @@ class HashSet(Counting):
         return found, int(f)
 
 
+class BloomFilter:
+    """Blocked Bloom filter by the library's documented definition (oracle.cpp): `blocks`
+    blocks of 256 bits, k bits per key."""
+
+    def __init__(self, key_bytes: int, blocks: int, k: int, seed: int):
+        self._lib = _load()
+        self.kdt = _dt(key_bytes)
+        self._h = self._lib.oracle_bloom_create(key_bytes, blocks, k, seed & (2 ** 64 - 1))
+        if not self._h:
+            raise ValueError("bad Bloom filter parameters")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.oracle_bloom_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def insert(self, keys) -> int:
+        k = np.ascontiguousarray(np.asarray(keys).astype(self.kdt, copy=False))
+        return int(self._lib.oracle_bloom_insert(self._h, _ptr(k), k.size))
+
+    def contains(self, keys):
+        k = np.ascontiguousarray(np.asarray(keys).astype(self.kdt, copy=False))
+        found = np.empty(k.size, dtype=np.uint8)
+        f = self._lib.oracle_bloom_contains(self._h, _ptr(k), k.size, _ptr(found))
+        return found, int(f)
+
+
 def sorted_segments(values: np.ndarray, offsets: np.ndarray) -> np.ndarray:
     """Sort every CSR segment in place-independent form (values compared as multisets)."""
     out = np.array(values, copy=True)
@@ -225,12 +262,13 @@ def sorted_segments(values: np.ndarray, offsets: np.ndarray) -> np.ndarray:
 
 
 def check_slots(dump: np.ndarray, p: int, W: int, slot_bytes: int, seed: int, unique_keys: bool,
-                overflow_bits: np.ndarray | None = None) -> dict:
+                overflow_bits: np.ndarray | None = None, key_bytes: int | None = None) -> dict:
     """Slot-dump invariant check of a table's slot array (host bytes, p * W slots):
     live slots, duplicate keys (when keys must be unique) and live keys that sit behind
     a window holding an empty slot on their own probing sequence -- or, when the table's
     overflow bits are given (uint32 words, bit w = window w), behind a window whose bit is
-    clear (see oracle.cpp)."""
+    clear (see oracle.cpp).  key_bytes defaults to 4 for 4- and 8-byte slots (packed 4+4-byte
+    pairs) and 8 for 16-byte slots."""
     buf = np.ascontiguousarray(dump).view(np.uint8)
     if buf.size < p * W * slot_bytes:
         raise ValueError("dump holds %d bytes, need %d" % (buf.size, p * W * slot_bytes))
@@ -240,7 +278,9 @@ def check_slots(dump: np.ndarray, p: int, W: int, slot_bytes: int, seed: int, un
         ovf = np.ascontiguousarray(overflow_bits).view(np.uint32)
         if ovf.size < (p + 31) // 32:
             raise ValueError("overflow bits hold %d words, need %d" % (ovf.size, (p + 31) // 32))
-    rc = _load().oracle_check_slots(_ptr(buf), p, W, slot_bytes, seed & (2 ** 64 - 1), int(unique_keys),
+    if key_bytes is None:
+        key_bytes = 8 if slot_bytes == 16 else 4
+    rc = _load().oracle_check_slots(_ptr(buf), p, W, slot_bytes, key_bytes, seed & (2 ** 64 - 1), int(unique_keys),
                                     None if ovf is None else _ptr(ovf),
                                     _ptr(out[0:]), ctypes.c_void_p(out.ctypes.data + 8),
                                     ctypes.c_void_p(out.ctypes.data + 16))

@@ -362,9 +362,9 @@ uint64_t oracle_counts_size(void* p) { return static_cast<Counts*>(p)->m.size();
 // The probing sequence is the table's definition restated here: h = fmix64(key ^ seed)
 // (MurmurHash3's 64-bit finalizer), w_0 = floor(hi32(h) * p / 2^32),
 // step = 1 + floor(lo32(h) * (p - 1) / 2^32), w_{j+1} = (w_j + step) mod p; windows are
-// W consecutive slots.  Slot words: 8-byte slots hold key = low 32 bits (empty 0,
-// tombstone 0xffffffff); 16-byte slots hold key = first 64-bit word (empty 0, tombstone
-// all ones).
+// W consecutive slots.  The key is the first key_bytes of a slot (little-endian): 4-byte
+// keys in 4- or 8-byte slots, 8-byte keys in 8- or 16-byte slots; empty = 0, tombstone =
+// all ones of the key width.
 namespace {
 
 uint64_t chk_fmix64(uint64_t k) {
@@ -376,33 +376,35 @@ uint64_t chk_fmix64(uint64_t k) {
   return k;
 }
 
-uint64_t chk_key(const unsigned char* slots, uint64_t i, uint32_t slot_bytes) {
-  if (slot_bytes == 8) {
-    uint64_t w;
-    std::memcpy(&w, slots + i * 8, 8);
-    return w & 0xffffffffull;
+uint64_t chk_key(const unsigned char* slots, uint64_t i, uint32_t slot_bytes, uint32_t key_bytes) {
+  if (key_bytes == 4) {
+    uint32_t k;
+    std::memcpy(&k, slots + i * slot_bytes, 4);
+    return k;
   }
   uint64_t k;
-  std::memcpy(&k, slots + i * 16, 8);
+  std::memcpy(&k, slots + i * slot_bytes, 8);
   return k;
 }
 
 }  // namespace
 
-extern "C" int oracle_check_slots(const void* dump, uint64_t p, uint32_t W, uint32_t slot_bytes, uint64_t seed,
-                                  int unique_keys, const uint32_t* ovf_or_null, uint64_t* out_live,
+extern "C" int oracle_check_slots(const void* dump, uint64_t p, uint32_t W, uint32_t slot_bytes, uint32_t key_bytes,
+                                  uint64_t seed, int unique_keys, const uint32_t* ovf_or_null, uint64_t* out_live,
                                   uint64_t* out_dups, uint64_t* out_unreachable) {
-  if (dump == nullptr || p < 2 || W == 0 || (slot_bytes != 8 && slot_bytes != 16)) return -1;
+  const bool shape_ok = (key_bytes == 4 && (slot_bytes == 4 || slot_bytes == 8)) ||
+                        (key_bytes == 8 && (slot_bytes == 8 || slot_bytes == 16));
+  if (dump == nullptr || p < 2 || W == 0 || !shape_ok) return -1;
   const unsigned char* s = static_cast<const unsigned char*>(dump);
   const uint64_t cap = p * W;
-  const uint64_t tomb = slot_bytes == 8 ? 0xffffffffull : ~0ull;
+  const uint64_t tomb = key_bytes == 4 ? 0xffffffffull : ~0ull;
   std::vector<uint8_t> has_empty(p, 0);
   for (uint64_t i = 0; i < cap; ++i)
-    if (chk_key(s, i, slot_bytes) == 0) has_empty[i / W] = 1;
+    if (chk_key(s, i, slot_bytes, key_bytes) == 0) has_empty[i / W] = 1;
   std::unordered_map<uint64_t, uint64_t> seen;
   uint64_t live = 0, dups = 0, unreachable = 0;
   for (uint64_t i = 0; i < cap; ++i) {
-    const uint64_t k = chk_key(s, i, slot_bytes);
+    const uint64_t k = chk_key(s, i, slot_bytes, key_bytes);
     if (k == 0 || k == tomb) continue;
     ++live;
     if (unique_keys && seen[k]++ > 0) ++dups;
@@ -424,3 +426,73 @@ extern "C" int oracle_check_slots(const void* dump, uint64_t p, uint32_t W, uint
   if (out_unreachable) *out_unreachable = unreachable;
   return 0;
 }
+
+// ---------------------------------------------------------------------------------------
+// Blocked Bloom filter (Sec. IV, "BloomFilter": set membership with false positives), by
+// the definition the library documents: h = fmix64(key ^ seed); the key's block is
+// floor(hi32(h) * blocks / 2^32) of `blocks` 256-bit blocks; its k bit positions are the
+// bytes of g1 = fmix64(h ^ 0x9e3779b97f4a7c15), g2 = fmix64(g1), ... (position i = byte
+// i % 8 of g_{i / 8 + 1}).  Insert sets the bits; a key is reported present when all of
+// its bits are set.
+namespace {
+
+struct Bloom {
+  int kb, k;
+  uint64_t blocks, seed;
+  std::vector<uint8_t> bits;  // blocks * 256 bits, one byte per bit
+};
+
+uint64_t bloom_fmix64(uint64_t x) { return chk_fmix64(x); }
+
+void bloom_bits(const Bloom& b, uint64_t key, uint64_t* block, uint32_t* pos) {
+  const uint64_t h = bloom_fmix64(key ^ b.seed);
+  *block = ((h >> 32) * b.blocks) >> 32;
+  uint64_t g = h ^ 0x9e3779b97f4a7c15ull;
+  for (int i = 0; i < b.k; ++i) {
+    if (i % 8 == 0) g = bloom_fmix64(g);
+    pos[i] = static_cast<uint32_t>((g >> (8 * (i % 8))) & 255u);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void* oracle_bloom_create(int key_bytes, uint64_t blocks, int k, uint64_t seed) {
+  if ((key_bytes != 4 && key_bytes != 8) || blocks == 0 || k < 1 || k > 16) return nullptr;
+  return new Bloom{key_bytes, k, blocks, seed, std::vector<uint8_t>(blocks * 256, 0)};
+}
+
+void oracle_bloom_destroy(void* p) { delete static_cast<Bloom*>(p); }
+
+uint32_t oracle_bloom_insert(void* p, const void* keys, uint64_t n) {
+  auto* b = static_cast<Bloom*>(p);
+  uint32_t f = 0;
+  uint32_t pos[16];
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint64_t key = key_at(keys, b->kb, i);
+    if (sentinel_w(key, b->kb)) { f |= F_INVALID; continue; }
+    uint64_t blk;
+    bloom_bits(*b, key, &blk, pos);
+    for (int j = 0; j < b->k; ++j) b->bits[blk * 256 + pos[j]] = 1;
+  }
+  return f;
+}
+
+uint32_t oracle_bloom_contains(void* p, const void* keys, uint64_t n, uint8_t* found) {
+  auto* b = static_cast<Bloom*>(p);
+  uint32_t f = 0;
+  uint32_t pos[16];
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint64_t key = key_at(keys, b->kb, i);
+    if (sentinel_w(key, b->kb)) { f |= F_INVALID; found[i] = 0; continue; }
+    uint64_t blk;
+    bloom_bits(*b, key, &blk, pos);
+    bool all = true;
+    for (int j = 0; j < b->k; ++j) all = all && b->bits[blk * 256 + pos[j]];
+    found[i] = all ? 1 : 0;
+  }
+  return f;
+}
+
+}  // extern "C"

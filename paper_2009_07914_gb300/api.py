@@ -21,7 +21,7 @@ __all__ = [
     "wc_plan_capacity", "wc_table_create", "wc_table_destroy", "wc_table_clear", "wc_table_get_info",
     "wc_table_set_launch", "wc_table_get_launch", "wc_insert", "wc_retrieve", "wc_erase", "wc_count_values",
     "wc_retrieve_multi", "wc_size", "wc_num_keys", "wc_load_factor", "wc_get_status", "wc_status_string",
-    "wc_insert_noalloc", "WC_NOALLOC_SCRATCH_BYTES", "wc_value_pool_used",
+    "wc_insert_noalloc", "WC_NOALLOC_SCRATCH_BYTES", "wc_value_pool_used", "wc_contains",
 ]
 
 
@@ -124,6 +124,12 @@ def wc_retrieve(t: int, keys, values_out, found_out=None, n: int | None = None, 
         _n_of(n, found_out, 1)
     check(lib().wc_retrieve(t, ptr(keys), n, ptr(values_out), ptr(found_out), stream_handle(stream)),
           "wc_retrieve")
+
+
+def wc_contains(t: int, keys, found_out, n: int | None = None, stream=None):
+    n = _n_of(n, keys)
+    _n_of(n, found_out)
+    check(lib().wc_contains(t, ptr(keys), n, ptr(found_out), stream_handle(stream)), "wc_contains")
 
 
 def wc_erase(t: int, keys, n: int | None = None, stream=None):

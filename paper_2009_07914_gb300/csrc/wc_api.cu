@@ -24,6 +24,9 @@ bool sv_p64_shape_ok(int W, int G);
 bool mv_shape_ok(int W, int G);
 bool oa_p32_shape_ok(int W, int G);
 bool count_shape_ok(int slot_bytes, int W, int G);
+bool set_shape_ok(int slot_bytes, int W, int G);
+cudaError_t set_launch(const wc_table* t, int op, const void* keys, uint64_t n, uint8_t* found, cudaStream_t s);
+cudaError_t bloom_launch(const wc_table* t, int op, const void* keys, uint64_t n, uint8_t* found, cudaStream_t s);
 cudaError_t count_insert(const wc_table* t, const void* keys, const void* weights, uint64_t n, cudaStream_t s);
 bool oa_p64_shape_ok(int W, int G);
 cudaError_t oa_p32_launch(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n, uint64_t* offs,
@@ -70,6 +73,20 @@ bool slot_layout(const wc_table_config& c, uint64_t* slot_bytes) {
     if (c.key_bytes == 8 && c.value_bytes == 8) { *slot_bytes = 16; return true; }
     return false;
   }
+  if (c.kind == WC_HASH_SET) {
+    if ((c.key_bytes == 4 || c.key_bytes == 8) && c.value_bytes == 0) {
+      *slot_bytes = static_cast<uint64_t>(c.key_bytes);
+      return true;
+    }
+    return false;
+  }
+  if (c.kind == WC_BLOOM_FILTER) {  // one 256-bit block per "slot"
+    if ((c.key_bytes == 4 || c.key_bytes == 8) && c.value_bytes == 0) {
+      *slot_bytes = 32;
+      return true;
+    }
+    return false;
+  }
   if (c.kind == WC_MULTI_VALUE) {
     if ((c.key_bytes == 4 || c.key_bytes == 8) && (c.value_bytes == 4 || c.value_bytes == 8)) {
       *slot_bytes = 16;
@@ -81,6 +98,7 @@ bool slot_layout(const wc_table_config& c, uint64_t* slot_bytes) {
 
 bool window_ok(int kind, uint64_t slot_bytes, int W) {
   if (kind == WC_MULTI_VALUE) return W == 2 || W == 4 || W == 8;
+  if (slot_bytes == 4) return W == 8 || W == 16 || W == 32;
   if (slot_bytes == 8) return W == 4 || W == 8 || W == 16 || W == 32;
   return W == 2 || W == 4 || W == 8 || W == 16;
 }
@@ -89,6 +107,7 @@ bool shape_ok(const wc_table* t, int op, int G) {
   const int W = static_cast<int>(t->W);
   if (t->cfg.kind == WC_MULTI_VALUE_OA) return t->slot_bytes == 8 ? oa_p32_shape_ok(W, G) : oa_p64_shape_ok(W, G);
   if (t->cfg.kind == WC_COUNTING && op == WC_OP_INSERT) return count_shape_ok(static_cast<int>(t->slot_bytes), W, G);
+  if (t->cfg.kind == WC_HASH_SET) return set_shape_ok(static_cast<int>(t->slot_bytes), W, G);
   if (t->slot_bytes == 8) return sv_p32_shape_ok(W, G);
   if (t->cfg.kind == WC_MULTI_VALUE) {
     if (op == WC_OP_INSERT || op == WC_OP_RETRIEVE) return G == 1;  // one thread per distinct key
@@ -315,9 +334,17 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   *out = nullptr;
   uint64_t slot_bytes = 0;
   if (!slot_layout(*cfg, &slot_bytes)) return WC_ERR_INVALID_ARG;
+  const bool bloom = cfg->kind == WC_BLOOM_FILTER;
   int W = cfg->window_width;
-  if (W == 0) W = slot_bytes == 8 ? 8 : 4;
-  if (!window_ok(cfg->kind, slot_bytes, W)) return WC_ERR_INVALID_ARG;
+  int bloom_k = 0;
+  if (bloom) {  // window_width carries k, the bits per key; a block is the unit of probing
+    bloom_k = W == 0 ? 8 : W;
+    if (bloom_k < 1 || bloom_k > 16) return WC_ERR_INVALID_ARG;
+    W = 1;
+  } else {
+    if (W == 0) W = slot_bytes == 4 ? 16 : (slot_bytes == 8 ? 8 : 4);  // 64-byte windows
+    if (!window_ok(cfg->kind, slot_bytes, W)) return WC_ERR_INVALID_ARG;
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) return WC_ERR_CUDA;
   const bool mv = cfg->kind == WC_MULTI_VALUE;
@@ -349,17 +376,19 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
       }
     }
   }
-  if ((cfg->options & WC_OPT_OVERFLOW_BITS) && cfg->kind != WC_SINGLE_VALUE && cfg->kind != WC_COUNTING)
+  if ((cfg->options & WC_OPT_OVERFLOW_BITS) && cfg->kind != WC_SINGLE_VALUE && cfg->kind != WC_COUNTING &&
+      cfg->kind != WC_HASH_SET)
     return WC_ERR_INVALID_ARG;
   if (mv && cfg->value_pool_capacity > kMaxPool) return WC_ERR_INVALID_ARG;
 
   uint64_t p = 0, cap = 0;
-  if (wc_plan_capacity(cfg->min_capacity, W, &p, &cap) != WC_OK) return WC_ERR_INVALID_ARG;
+  const uint64_t want = bloom ? (cfg->min_capacity + 255) / 256 : cfg->min_capacity;  // Bloom: bits -> blocks
+  if (wc_plan_capacity(want, W, &p, &cap) != WC_OK) return WC_ERR_INVALID_ARG;
 
   wc_table* t = new (std::nothrow) wc_table();
   if (t == nullptr) return WC_ERR_OUT_OF_MEMORY;
   t->cfg = *cfg;
-  t->cfg.window_width = W;
+  t->cfg.window_width = bloom ? bloom_k : W;
   t->device = cfg->device;
   t->windows = p;
   t->W = static_cast<uint64_t>(W);
@@ -372,7 +401,8 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   t->sm_count = sm_count_of(t->device);
 
   // One allocation: [slots | meta 256 B | overflow bits (SV) | pending (MV) | scan partials (MV, OA) | pool (MV)]
-  const bool sv = (cfg->kind == WC_SINGLE_VALUE || cfg->kind == WC_COUNTING) && (cfg->options & WC_OPT_OVERFLOW_BITS);
+  const bool sv = (cfg->kind == WC_SINGLE_VALUE || cfg->kind == WC_COUNTING || cfg->kind == WC_HASH_SET) &&
+                  (cfg->options & WC_OPT_OVERFLOW_BITS);
   const uint64_t off_meta = align_up(t->table_bytes, kAlign);
   const uint64_t off_ovf = off_meta + kAlign;
   const uint64_t ovf_bytes = sv ? align_up((p + 31) / 32 * 4, kAlign) : 0;
@@ -481,7 +511,7 @@ wc_status wc_table_get_info(const wc_table* t, wc_table_info* h_out) {
   h_out->table_bytes = t->table_bytes;
   h_out->pool_capacity = t->pool_capacity;
   h_out->device_bytes = t->device_bytes;
-  h_out->window_width = static_cast<int32_t>(t->W);
+  h_out->window_width = t->cfg.kind == WC_BLOOM_FILTER ? t->cfg.window_width : static_cast<int32_t>(t->W);
   h_out->kind = t->cfg.kind;
   h_out->options = t->cfg.options;
   h_out->reserved = 0;
@@ -490,6 +520,7 @@ wc_status wc_table_get_info(const wc_table* t, wc_table_info* h_out) {
 
 wc_status wc_table_set_launch(wc_table* t, int32_t op, const wc_launch* launch) {
   if (t == nullptr || launch == nullptr || op < 0 || op >= WC_OP__N) return WC_ERR_INVALID_ARG;
+  if (t->cfg.kind == WC_BLOOM_FILTER) return WC_ERR_UNSUPPORTED;  // one thread per key
   const int b = launch->block_threads;
   if (b < 32 || b > 256 || b % 32 != 0 || launch->blocks_per_sm < 0 || launch->blocks_per_sm > 64)
     return WC_ERR_INVALID_ARG;
@@ -522,7 +553,8 @@ static wc_status check_bulk(const wc_table* t, const void* keys, uint64_t n) {
 wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint64_t n, void* stream) {
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
-  const bool weights_optional = t->cfg.kind == WC_COUNTING;
+  const bool weights_optional =
+      t->cfg.kind == WC_COUNTING || t->cfg.kind == WC_HASH_SET || t->cfg.kind == WC_BLOOM_FILTER;
   if (n > 0 && ((d_values == nullptr && !weights_optional) ||
                 (d_values != nullptr && !aligned(d_values, static_cast<uint64_t>(t->cfg.value_bytes)))))
     return WC_ERR_INVALID_ARG;
@@ -530,6 +562,11 @@ wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint6
   if (t->cfg.kind == WC_COUNTING) {
     DeviceGuard guard(t->device);
     return cuda_status(count_insert(t, d_keys, d_values, n, as_stream(stream)));
+  }
+  if (t->cfg.kind == WC_HASH_SET || t->cfg.kind == WC_BLOOM_FILTER) {
+    DeviceGuard guard(t->device);
+    return cuda_status(t->cfg.kind == WC_HASH_SET ? set_launch(t, WC_OP_INSERT, d_keys, n, nullptr, as_stream(stream))
+                                                  : bloom_launch(t, WC_OP_INSERT, d_keys, n, nullptr, as_stream(stream)));
   }
   if (t->cfg.kind == WC_MULTI_VALUE && n >= kMaxMvBatch) return WC_ERR_INVALID_ARG;
   DeviceGuard guard(t->device);
@@ -555,12 +592,29 @@ wc_status wc_retrieve(wc_table* t, const void* d_keys, uint64_t n, void* d_value
 wc_status wc_erase(wc_table* t, const void* d_keys, uint64_t n, void* stream) {
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
+  if (t->cfg.kind == WC_BLOOM_FILTER) return WC_ERR_UNSUPPORTED;  // bits are shared between keys
   if (n == 0) return WC_OK;
   DeviceGuard guard(t->device);
   if (t->cfg.kind == WC_MULTI_VALUE) return cuda_status(mv_erase(t, d_keys, n, as_stream(stream)));
   if (t->cfg.kind == WC_MULTI_VALUE_OA)
     return cuda_status(oa_launch(t, WC_OP_ERASE, d_keys, nullptr, n, nullptr, nullptr, as_stream(stream)));
+  if (t->cfg.kind == WC_HASH_SET) return cuda_status(set_launch(t, WC_OP_ERASE, d_keys, n, nullptr, as_stream(stream)));
   return cuda_status(sv_launch(t, WC_OP_ERASE, d_keys, nullptr, n, nullptr, nullptr, as_stream(stream)));
+}
+
+wc_status wc_contains(wc_table* t, const void* d_keys, uint64_t n, uint8_t* d_found, void* stream) {
+  wc_status st = check_bulk(t, d_keys, n);
+  if (st != WC_OK) return st;
+  if (n > 0 && d_found == nullptr) return WC_ERR_INVALID_ARG;
+  const int kind = t->cfg.kind;
+  if (kind != WC_SINGLE_VALUE && kind != WC_COUNTING && kind != WC_HASH_SET && kind != WC_BLOOM_FILTER)
+    return WC_ERR_UNSUPPORTED;
+  if (n == 0) return WC_OK;
+  DeviceGuard guard(t->device);
+  cudaStream_t s = as_stream(stream);
+  if (kind == WC_HASH_SET) return cuda_status(set_launch(t, WC_OP_RETRIEVE, d_keys, n, d_found, s));
+  if (kind == WC_BLOOM_FILTER) return cuda_status(bloom_launch(t, WC_OP_RETRIEVE, d_keys, n, d_found, s));
+  return cuda_status(sv_launch(t, WC_OP_RETRIEVE, d_keys, nullptr, n, nullptr, d_found, s));
 }
 
 wc_status wc_count_values(wc_table* t, const void* d_keys, uint64_t n, uint64_t* d_offsets,

@@ -112,6 +112,7 @@ struct LayoutP32 {
     unsigned long long w;
   };
   static constexpr int kWords = 1;
+  static constexpr bool kHalf = false;   // slots of 4 bytes, two per loaded 64-bit word
   static constexpr bool kCount = false;  // duplicates overwrite the value (single-value table)
   static constexpr Key kEmpty = 0u;
   static constexpr Key kTomb = 0xffffffffu;
@@ -142,6 +143,7 @@ struct LayoutP64 {
     unsigned long long k, v;
   };
   static constexpr int kWords = 2;
+  static constexpr bool kHalf = false;
   static constexpr bool kCount = false;
   static constexpr Key kEmpty = 0ull;
   static constexpr Key kTomb = ~0ull;
@@ -184,13 +186,65 @@ struct LayoutC64 : LayoutP64 {
   __device__ static void store_val(Slot* p, Val v) { atomicAdd(&p->v, v); }
 };
 
+// Hash sets (the paper's HashSet): a slot holds only a key.  "Values" read back are 1 for
+// a stored key; inserting a stored key leaves it as it is (DUPLICATE_KEY is raised).
+struct LayoutK64 {
+  using Key = unsigned long long;
+  using Val = unsigned long long;
+  struct Slot {
+    unsigned long long k;
+  };
+  static constexpr int kWords = 1;
+  static constexpr bool kHalf = false;
+  static constexpr bool kCount = false;
+  static constexpr Key kEmpty = 0ull;
+  static constexpr Key kTomb = ~0ull;
+  static constexpr Val kNotFound = 0ull;
+  __device__ static Key key(const Slot& s) { return s.k; }
+  __device__ static Val val(const Slot&) { return 1ull; }
+  __device__ static Slot make(Key k, Val) { return Slot{k}; }
+  __device__ static Slot tomb() { return Slot{~0ull}; }
+  __device__ static Slot from_words(const unsigned long long* u) { return Slot{u[0]}; }
+  __device__ static bool cas(Slot* p, const Slot& e, const Slot& d) { return atomicCAS(&p->k, e.k, d.k) == e.k; }
+  __device__ static void store_val(Slot*, Val) {}
+  __device__ static Slot shfl(const Slot& s, int src) { return Slot{__shfl_sync(kFull, s.k, src)}; }
+};
+struct LayoutK32 {
+  using Key = uint32_t;
+  using Val = uint32_t;
+  struct Slot {
+    uint32_t k;
+  };
+  static constexpr int kWords = 1;       // per loaded word (two slots)
+  static constexpr bool kHalf = true;
+  static constexpr bool kCount = false;
+  static constexpr Key kEmpty = 0u;
+  static constexpr Key kTomb = 0xffffffffu;
+  static constexpr Val kNotFound = 0u;
+  __device__ static Key key(const Slot& s) { return s.k; }
+  __device__ static Val val(const Slot&) { return 1u; }
+  __device__ static Slot make(Key k, Val) { return Slot{k}; }
+  __device__ static Slot tomb() { return Slot{0xffffffffu}; }
+  __device__ static bool cas(Slot* p, const Slot& e, const Slot& d) { return atomicCAS(&p->k, e.k, d.k) == e.k; }
+  __device__ static void store_val(Slot*, Val) {}
+  __device__ static Slot shfl(const Slot& s, int src) { return Slot{__shfl_sync(kFull, s.k, src)}; }
+};
+
 // S consecutive slots of one lane.
 template <class L, int S>
 __device__ __forceinline__ void load_slots(const typename L::Slot* p, typename L::Slot (&s)[S]) {
-  unsigned long long u[S * L::kWords];
-  load_words<S * L::kWords>(reinterpret_cast<const unsigned long long*>(p), u);
+  if constexpr (L::kHalf) {  // 4-byte slots: S / 2 words, low half first (little-endian)
+    static_assert(S % 2 == 0, "4-byte slots are loaded in pairs");
+    unsigned long long u[S / 2];
+    load_words<S / 2>(reinterpret_cast<const unsigned long long*>(p), u);
 #pragma unroll
-  for (int i = 0; i < S; ++i) s[i] = L::from_words(u + i * L::kWords);
+    for (int i = 0; i < S; ++i) s[i].k = static_cast<uint32_t>(u[i / 2] >> (32 * (i & 1)));
+  } else {
+    unsigned long long u[S * L::kWords];
+    load_words<S * L::kWords>(reinterpret_cast<const unsigned long long*>(p), u);
+#pragma unroll
+    for (int i = 0; i < S; ++i) s[i] = L::from_words(u + i * L::kWords);
+  }
 }
 
 // s[i] selected without dynamic register indexing.

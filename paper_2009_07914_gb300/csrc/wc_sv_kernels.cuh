@@ -229,7 +229,7 @@ struct EmitValue {
   typename L::Val* __restrict__ out;
   uint8_t* __restrict__ found;
   __device__ void operator()(uint64_t pos, bool hit, const typename L::Slot& s) const {
-    out[pos] = hit ? L::val(s) : L::kNotFound;
+    if (out) out[pos] = hit ? L::val(s) : L::kNotFound;  // no output: membership only
     if (found) found[pos] = hit ? 1 : 0;
   }
 };
@@ -239,7 +239,7 @@ struct EmitValue {
 // random-read latency.  Wider per-lane loads keep the compiler's choice.
 template <class L, int S>
 constexpr int retrieve_min_blocks() {
-  return (L::kWords == 1 && S <= 4) ? 6 : 1;
+  return (L::kWords == 1 && sizeof(typename L::Key) == 4 && S <= 4) ? 6 : 1;
 }
 
 template <class L, int G, int S>

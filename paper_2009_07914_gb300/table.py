@@ -7,7 +7,7 @@ import numpy as np
 import torch
 
 from . import api
-from ._binding import WC_COUNTING, WC_MULTI_VALUE, WC_MULTI_VALUE_OA, WC_SINGLE_VALUE
+from ._binding import WC_BLOOM_FILTER, WC_COUNTING, WC_HASH_SET, WC_MULTI_VALUE, WC_MULTI_VALUE_OA, WC_SINGLE_VALUE
 
 _INT = {4: torch.int32, 8: torch.int64}
 _NP_SIGNED = {4: np.int32, 8: np.int64}
@@ -143,3 +143,32 @@ class CountingTable(SingleValueTable):
         w = None if weights is None else self.values_dev(weights)
         api.wc_insert(self.handle, k, w, stream=stream)
         return api.wc_get_status(self.handle, clear=True, stream=stream)
+
+
+class _Membership(_Table):
+    def insert(self, keys, stream=None):
+        api.wc_insert(self.handle, self.keys_dev(keys), None, stream=stream)
+        return api.wc_get_status(self.handle, clear=True, stream=stream)
+
+    def contains(self, keys, stream=None):
+        """Returns (found mask as numpy uint8, flags)."""
+        k = self.keys_dev(keys)
+        found = torch.empty(k.numel(), dtype=torch.uint8, device=self.device)
+        api.wc_contains(self.handle, k, found, stream=stream)
+        return found.cpu().numpy(), api.wc_get_status(self.handle, clear=True, stream=stream)
+
+
+class HashSetTable(_Membership):
+    """A set of 4- or 8-byte keys, one key per slot."""
+    kind = WC_HASH_SET
+
+    def __init__(self, key_bytes=4, min_capacity=1024, **kw):
+        super().__init__(key_bytes, 0, min_capacity=min_capacity, **kw)
+
+
+class BloomFilterTable(_Membership):
+    """Blocked Bloom filter of `bits` bits (whole 256-bit blocks), k bits per key."""
+    kind = WC_BLOOM_FILTER
+
+    def __init__(self, key_bytes=4, bits=1 << 20, k=8, seed=0x5EED_C0DE, device=None):
+        super().__init__(key_bytes, 0, min_capacity=bits, window_width=k, seed=seed, device=device)

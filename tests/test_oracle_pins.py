@@ -266,3 +266,27 @@ def test_hash_set_oracle_against_python_set(kb):
         found, _ = o.contains(universe)
         np.testing.assert_array_equal(found, np.array([k in ref for k in universe.tolist()], np.uint8))
         assert o.size() == len(ref)
+
+
+def test_bloom_oracle_no_false_negatives_and_formula_rate():
+    """The oracle's blocked Bloom filter: every inserted key is found, and the false
+    positive rate on absent keys matches the Poisson-averaged blocked-filter formula."""
+    import math
+    n, blocks, k = 20_000, 20_000 * 10 // 256, 7
+    o = oracle.BloomFilter(4, blocks, k, 123)
+    rng = np.random.default_rng(9)
+    keys = np.unique(rng.integers(1, 2 ** 31, n + 500, dtype=np.uint64))[:n].astype(np.uint32)
+    o.insert(keys)
+    found, _ = o.contains(keys)
+    assert found.all()
+    absent = (rng.integers(1, 2 ** 31, 200_000, dtype=np.uint64).astype(np.uint32) | np.uint32(1 << 31))
+    fp = o.contains(absent)[0].mean()
+    lam, p, total, x = 256.0 * n / (blocks * 256), None, 0.0, 0
+    p = math.exp(-lam)
+    while x < 200:
+        total += p * (1 - (1 - 1 / 256) ** (k * x)) ** k
+        x += 1
+        p *= lam / x
+    assert abs(fp - total) < 0.12 * total, (fp, total)
+    # plain (unblocked) Bloom filters do better: the blocked layout costs a little FP rate
+    assert total > (1 - math.exp(-k * n / (blocks * 256))) ** k
