@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--no-overflow-bits", action="store_true",
                     help="sv32: table without per-window overflow bits (lookups walk to an empty slot)")
     ap.add_argument("--workload", default="sv32",
-                    choices=["sv32", "sv32_small", "sv64_zipf", "mv_zipf", "mv_oa_uniform_r", "device_api", "served"],
+                    choices=["sv32", "sv32_small", "sv64_zipf", "mv_zipf", "mv_oa_uniform_r", "device_api", "membership",
+                             "served"],
                     help="sv32 (default): 2^27 uint32 pairs at load 0.9, insert + 50%% absent retrieve; "
                          "sv32_small: 2^20 pairs at 0.8 with erase; sv64_zipf: 2^28 uint64 pairs, Zipf queries; "
                          "mv_zipf: multi-value 2^28 Zipf inserts, count + CSR retrieve; "
@@ -64,6 +65,8 @@ def parse():
                          "over 1..n/r at load 0.8, queries 1..n; "
                          "device_api: 2^27 keys produced inside one kernel and inserted / looked up per thread "
                          "with the device API, against the bulk calls on the same keys; "
+                         "membership: 2^27 uint32 keys in a hash set (load 0.9), a Bloom filter (10 bits/key, k = 7) "
+                         "and a counting table (Zipf keys); "
                          "served: 64 tables, Poisson requests, batched vs per-call")
     ap.add_argument("--requests", type=int, default=512, help="served: number of requests")
     ap.add_argument("--r", default="1,4,16,64", help="mv_oa_uniform_r: average copies per key, comma-separated")
@@ -680,6 +683,66 @@ def run_device_api(args, dev):
     api.wc_table_destroy(h)
 
 
+def run_membership(args, dev):
+    """The other table types of Sec. IV on 2^27 uint32 keys: a hash set at load 0.9 (insert,
+    then membership of the keys plus as many absent ones), a blocked Bloom filter with 10
+    bits per key and k = 7 (insert, membership, measured false-positive rate), and a
+    counting table fed 2^27 Zipf(1.1) draws over 2^24 keys (insert, count lookups)."""
+    import torch
+
+    import paper_2009_07914_gb300 as wc
+    from paper_2009_07914_gb300 import api
+    from paper_2009_07914_gb300.table import to_device
+    n = 1 << args.log2n
+    d = wc_inputs.sv_insert_retrieve_u32(0x57C00006, n, n // 2, n // 2)
+    keys, q = to_device(d["keys"], 4, dev), to_device(d["queries"], 4, dev)
+    pres = torch.from_numpy((d["q_src"] >= 0).astype(np.uint8)).to(dev)
+    found = torch.empty(n, dtype=torch.uint8, device=dev)
+    z = wc_inputs.mv_zipf_u64(0x57C00007, 1 << 24, n, 1 << 20)
+    zk = to_device(((z["keys"] & np.uint64(0x7FFFFFFF)) | np.uint64(1)).astype(np.uint32), 4, dev)
+    zq = to_device(((z["queries"] & np.uint64(0x7FFFFFFF)) | np.uint64(1)).astype(np.uint32), 4, dev)
+    counts = torch.empty(zq.numel(), dtype=torch.int32, device=dev)
+    cfound = torch.empty(zq.numel(), dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream()
+    hs = api.wc_table_create(wc.WC_HASH_SET, 4, 0, int(np.ceil(n / 0.9)), 0, 0, 0x5EEDC0DE, dev.index,
+                             options=wc.WC_OPT_OVERFLOW_BITS)
+    bf = api.wc_table_create(wc.WC_BLOOM_FILTER, 4, 0, 10 * n, 7, 0, 0x5EEDC0DE, dev.index)
+    ct = api.wc_table_create(wc.WC_COUNTING, 4, 4, int(np.ceil((1 << 24) / 0.9)), 0, 0, 0x5EEDC0DE, dev.index)
+    ev = []
+    with ClockSampler(dev.index) as clk:
+        for i in range(args.warmup + args.steps):
+            r = []
+            for h, ins_keys, ins_n, qk, qn, out in ((hs, keys, n, q, n, None), (bf, keys, n, q, n, None),
+                                                    (ct, zk, n, zq, zq.numel(), counts)):
+                api.wc_table_clear(h, s)
+                r.append(timed(s, lambda: api.wc_insert(h, ins_keys, None, ins_n, s)))
+                if out is None:
+                    r.append(timed(s, lambda: api.wc_contains(h, qk, found, qn, s)))
+                else:
+                    r.append(timed(s, lambda: api.wc_retrieve(h, qk, out, cfound, qn, s)))
+                if i == 0 and h == hs:
+                    assert torch.equal(found, pres) and api.wc_size(hs) == n
+                if i == 0 and h == bf:
+                    fpos = int((found & (1 - pres)).sum().item()) / int((1 - pres).sum().item())
+                    assert bool((found >= pres).all())  # no false negatives
+            if i >= args.warmup:
+                ev.append(r)
+    med = [statistics.median(e[j] for e in ev) for j in range(6)]
+    nz = zq.numel()
+    total = sum(med)
+    _common(args, "membership_u32_n2^%d" % args.log2n, "G ops/s (set + Bloom + counting: inserts + lookups)",
+            (4 * n + n + nz) / (total * 1e-3) / 1e9, "G ops/s", total, "u32",
+            {"n": n, "set_alpha": 0.9, "bloom_bits_per_key": 10, "bloom_k": 7,
+             "counting": "2^27 Zipf(1.1) draws over 2^24 keys", "l2": "no flush: tables and inputs > L2"}, clk,
+            6 * args.steps,
+            {"set_insert_gops": n / med[0] / 1e6, "set_contains_gops": n / med[1] / 1e6,
+             "bloom_insert_gops": n / med[2] / 1e6, "bloom_contains_gops": n / med[3] / 1e6,
+             "bloom_false_positive_rate": fpos, "counting_insert_gops": n / med[4] / 1e6,
+             "counting_lookup_gops": nz / med[5] / 1e6})
+    for h in (hs, bf, ct):
+        api.wc_table_destroy(h)
+
+
 def run_served(args, dev):
     """64 uint32 tables (capacity 2^U(16,26), pre-filled to load U(0,0.6)); Poisson
     requests with batch sizes 2^U(log2 1000, 24), 60/35/5 insert/retrieve/erase.  Each
@@ -733,7 +796,7 @@ def run_workload(args, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     {"sv32_small": run_sv32_small, "sv64_zipf": run_sv64_zipf, "mv_zipf": run_mv_zipf,
-     "mv_oa_uniform_r": run_mv_oa_uniform_r, "device_api": run_device_api,
+     "mv_oa_uniform_r": run_mv_oa_uniform_r, "device_api": run_device_api, "membership": run_membership,
      "served": run_served}[args.workload](args, dev)
 
 

@@ -352,7 +352,9 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
       pos = np;
       k = kin;
       if (is_sentinel(k)) {
-        flags |= kFlagInvalid;
+        // counting inserts run on aggregated batches whose padding is key 0 (the
+        // aggregation pass already flagged the caller's sentinel keys)
+        if (!(L::kCount && k == Key(0))) flags |= kFlagInvalid;
       } else {
         v = vin;
         act = true;
