@@ -92,11 +92,15 @@ SV_KERNEL_SOURCES = ("wc_device.cuh", "wc_sv_kernels.cuh", "wc_sv_dispatch.cuh",
 
 
 def source_digest():
+    """Digest of the sources the single-value probe kernels are built from (the library's
+    own and the public device header that holds the probing sequence)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2009_07914_gb300", "csrc")
-    for name in SV_KERNEL_SOURCES:
-        with open(os.path.join(d, name), "rb") as f:
-            h.update(name.encode() + f.read())
+    paths = [os.path.join(d, name) for name in SV_KERNEL_SOURCES]
+    paths.append(os.path.join(ROOT, "include", "wc_device_api.cuh"))
+    for path in paths:
+        with open(path, "rb") as f:
+            h.update(os.path.basename(path).encode() + f.read())
     return h.hexdigest()[:16]
 
 
