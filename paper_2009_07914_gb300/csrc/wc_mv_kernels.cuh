@@ -679,7 +679,9 @@ __device__ __forceinline__ uint64_t value_index(const PoolDesc& pd, uint64_t h, 
   return h_offset(h) + q;
 }
 
-template <class KIn, int VB, int W>
+// kGrowth: the table uses a bucket growth strategy (rows are copied by walking their
+// bucket lists); otherwise every value is found from its row's handle.
+template <class KIn, int VB, int W, bool kGrowth>
 __global__ void __launch_bounds__(kRmThreads) k_mv_retrieve_multi(TableDesc t, PoolDesc pd, const KIn* __restrict__ keys,
                                                                   uint64_t n, const uint64_t* __restrict__ offs,
                                                                   void* __restrict__ out) {
@@ -717,7 +719,7 @@ __global__ void __launch_bounds__(kRmThreads) k_mv_retrieve_multi(TableDesc t, P
       s_h[r] = h;
     }
     __syncthreads();
-    if (pd.growth != kGrowExact) {
+    if constexpr (kGrowth) {
       // growth layouts: a key may have many buckets, so each row's part of the chunk is
       // copied by one thread walking the row's buckets newest first, once
       for (int r = threadIdx.x; r < R; r += kRmThreads) {
@@ -740,7 +742,7 @@ __global__ void __launch_bounds__(kRmThreads) k_mv_retrieve_multi(TableDesc t, P
       }
       __syncthreads();
       continue;
-    }
+    } else {
     for (uint64_t j = j0 + threadIdx.x; j < j1; j += kRmThreads) {
       int lo = 0, hi = R - 1;
       while (lo < hi) {
@@ -752,6 +754,7 @@ __global__ void __launch_bounds__(kRmThreads) k_mv_retrieve_multi(TableDesc t, P
       const uint64_t h = s_h[lo];
       // a key whose count changed since count_values keeps its slot in the output
       if (q < h_count(h)) o[j] = pool[value_index<VB>(pd, h, q)];
+    }
     }
     __syncthreads();
   }

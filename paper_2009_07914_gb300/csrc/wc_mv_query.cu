@@ -47,7 +47,7 @@ cudaError_t probe_dispatch(const wc_table* t, int op, const void* keys, uint64_t
 
 template <class KIn, int VB, int W>
 cudaError_t gather(const wc_table* t, const void* keys, uint64_t n, const uint64_t* offs, void* out, cudaStream_t s) {
-  auto kern = k_mv_retrieve_multi<KIn, VB, W>;
+  auto kern = t->growth == kGrowExact ? k_mv_retrieve_multi<KIn, VB, W, false> : k_mv_retrieve_multi<KIn, VB, W, true>;
   const int bps = occupancy(kern, kRmThreads);
   const unsigned grid = static_cast<unsigned>(bps * t->sm_count);
   return launch_k(t, kern, grid, kRmThreads, 0, s, desc_of(t), pool_of(t), static_cast<const KIn*>(keys), n, offs,
