@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access roofline probe")
+    ap.add_argument("--soa", action="store_true", help="sv32: struct-of-arrays table (keys and values in two arrays)")
     ap.add_argument("--no-overflow-bits", action="store_true",
                     help="sv32: table without per-window overflow bits (lookups walk to an empty slot)")
     ap.add_argument("--workload", default="sv32",
@@ -284,6 +285,8 @@ def run_wc(args, rank, world, local_rank):
     out = torch.empty(n, dtype=torch.int32, device=dev)
     found = torch.empty(n, dtype=torch.uint8, device=dev)
     opts = 0 if args.no_overflow_bits else wc.WC_OPT_OVERFLOW_BITS  # half the queries are absent
+    if args.soa:
+        opts |= wc.WC_OPT_SOA
     h = api.wc_table_create(wc.WC_SINGLE_VALUE, 4, 4, int(np.ceil(n / args.alpha)), args.window, 0,
                             0x5EEDC0DE + rank, local_rank, options=opts)
     info = api.wc_table_get_info(h)
@@ -391,6 +394,7 @@ def run_wc(args, rank, world, local_rank):
                    "capacity": info["capacity"], "achieved_alpha": n / info["capacity"],
                    "window_slots": info["window_width"], "group_insert": g_ins, "group_retrieve": g_ret,
                    "table_bytes": info["table_bytes"], "overflow_bits": bool(info["options"] & 1),
+                   "layout": "struct of arrays" if info["options"] & 2 else "packed 64-bit slots",
                    "l2": "no flush: inputs and table larger than L2 (table %.2f GB, keys %.2f GB)"
                          % (info["table_bytes"] / 1e9, n * 4 / 1e9),
                    "parallelism": "replicas (independent table per GPU)"},

@@ -148,6 +148,15 @@ typedef struct {
  * windows / 8 bytes. */
 enum { WC_OPT_OVERFLOW_BITS = 1 };
 
+/* WC_OPT_SOA (single-value tables): struct-of-arrays layout (Sec. IV-A) -- the keys in one
+ * array (4- or 8-byte slots, probed like a hash set's), the values in a second array of
+ * the same length.  An insert claims the key slot with one CAS and then writes the value
+ * with a plain store (complete when the call is; the paper's relaxed value writes); a hit
+ * reads the value at the key's index.  Windows are of W keys (4-byte keys: 8, 16, 32,
+ * default 16; 8-byte keys: 4, 8, 16, 32, default 8).  Not served by the batched executor,
+ * wc_insert_noalloc or the device API. */
+enum { WC_OPT_SOA = 2 };
+
 /* Sizes of a created table (host copy; no device access). */
 typedef struct {
   uint64_t capacity;        /* slots (key-store slots for multi-value) = windows * W */

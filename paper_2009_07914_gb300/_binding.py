@@ -37,6 +37,7 @@ WC_HASH_SET = 3
 WC_COUNTING = 4
 WC_BLOOM_FILTER = 5
 WC_OPT_OVERFLOW_BITS = 1
+WC_OPT_SOA = 2
 
 WC_SCHEME_AUTO = 0
 WC_SCHEME_DIRECT = 1

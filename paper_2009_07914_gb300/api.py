@@ -14,7 +14,7 @@ import torch
 
 from . import _binding as B
 from ._binding import (WC_BLOOM_FILTER, WC_COUNTING, WC_HASH_SET, WC_MULTI_VALUE, WC_MULTI_VALUE_OA,
-                       WC_OPT_OVERFLOW_BITS, WC_SINGLE_VALUE, WcLaunch,
+                       WC_OPT_OVERFLOW_BITS, WC_OPT_SOA, WC_SINGLE_VALUE, WcLaunch,
                        WcTableConfig, WcTableInfo, check, lib, ptr, stream_handle)
 
 __all__ = [
@@ -242,4 +242,4 @@ __all__ += ["wc_check_status", "wc_table_dump_slots", "wc_table_device_view", "w
             "wc_table_snapshot",
             "wc_table_restore", "wc_debug_fail_allocations"]
 __all__ += ["WC_SINGLE_VALUE", "WC_MULTI_VALUE", "WC_MULTI_VALUE_OA", "WC_HASH_SET", "WC_COUNTING",
-            "WC_BLOOM_FILTER", "WC_OPT_OVERFLOW_BITS"]
+            "WC_BLOOM_FILTER", "WC_OPT_OVERFLOW_BITS", "WC_OPT_SOA"]

@@ -24,6 +24,9 @@ bool sv_p64_shape_ok(int W, int G);
 bool mv_shape_ok(int W, int G);
 bool oa_p32_shape_ok(int W, int G);
 bool count_shape_ok(int slot_bytes, int W, int G);
+bool soa_shape_ok(int slot_bytes, int W, int G);
+cudaError_t soa_launch(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n, void* out,
+                       uint8_t* found, cudaStream_t s);
 bool set_shape_ok(int slot_bytes, int W, int G);
 cudaError_t set_launch(const wc_table* t, int op, const void* keys, uint64_t n, uint8_t* found, cudaStream_t s);
 cudaError_t bloom_launch(const wc_table* t, int op, const void* keys, uint64_t n, uint8_t* found, cudaStream_t s);
@@ -68,6 +71,13 @@ uint64_t next_prime(uint64_t x) {
 }
 
 bool slot_layout(const wc_table_config& c, uint64_t* slot_bytes) {
+  if (c.kind == WC_SINGLE_VALUE && (c.options & WC_OPT_SOA)) {  // key array; values in a second array
+    if ((c.key_bytes == 4 && c.value_bytes == 4) || (c.key_bytes == 8 && c.value_bytes == 8)) {
+      *slot_bytes = static_cast<uint64_t>(c.key_bytes);
+      return true;
+    }
+    return false;
+  }
   if (c.kind == WC_SINGLE_VALUE || c.kind == WC_MULTI_VALUE_OA || c.kind == WC_COUNTING) {
     if (c.key_bytes == 4 && c.value_bytes == 4) { *slot_bytes = 8; return true; }
     if (c.key_bytes == 8 && c.value_bytes == 8) { *slot_bytes = 16; return true; }
@@ -108,6 +118,7 @@ bool shape_ok(const wc_table* t, int op, int G) {
   if (t->cfg.kind == WC_MULTI_VALUE_OA) return t->slot_bytes == 8 ? oa_p32_shape_ok(W, G) : oa_p64_shape_ok(W, G);
   if (t->cfg.kind == WC_COUNTING && op == WC_OP_INSERT) return count_shape_ok(static_cast<int>(t->slot_bytes), W, G);
   if (t->cfg.kind == WC_HASH_SET) return set_shape_ok(static_cast<int>(t->slot_bytes), W, G);
+  if (t->d_vals != nullptr) return soa_shape_ok(static_cast<int>(t->slot_bytes), W, G);
   if (t->slot_bytes == 8) return sv_p32_shape_ok(W, G);
   if (t->cfg.kind == WC_MULTI_VALUE) {
     if (op == WC_OP_INSERT || op == WC_OP_RETRIEVE) return G == 1;  // one thread per distinct key
@@ -170,6 +181,7 @@ TableDesc desc_of(const wc_table* t) {
   d.size = t->d_size;
   d.nkeys = t->d_nkeys;
   d.ovf = t->d_ovf;
+  d.vals = t->d_vals;
   d.p = static_cast<uint32_t>(t->windows);
   d.W = static_cast<uint32_t>(t->W);
   return d;
@@ -281,6 +293,7 @@ int sm_count_of(int device) {
 
 cudaError_t sv_launch(const wc_table* t, int op, const void* keys, const void* vals, uint64_t n, void* out,
                       uint8_t* found, cudaStream_t s) {
+  if (t->d_vals != nullptr) return soa_launch(t, op, keys, vals, n, out, found, s);
   if (t->slot_bytes == 8) return sv_p32_launch(t, op, keys, vals, n, out, found, s);
   return sv_p64_launch(t, op, keys, vals, n, out, found, s);
 }
@@ -349,7 +362,9 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) return WC_ERR_CUDA;
   const bool mv = cfg->kind == WC_MULTI_VALUE;
   const bool oa = cfg->kind == WC_MULTI_VALUE_OA;
-  if ((cfg->options & ~WC_OPT_OVERFLOW_BITS) != 0 || cfg->reserved != 0) return WC_ERR_INVALID_ARG;
+  if ((cfg->options & ~(WC_OPT_OVERFLOW_BITS | WC_OPT_SOA)) != 0 || cfg->reserved != 0) return WC_ERR_INVALID_ARG;
+  if ((cfg->options & WC_OPT_SOA) && cfg->kind != WC_SINGLE_VALUE) return WC_ERR_INVALID_ARG;
+  const bool soa = (cfg->options & WC_OPT_SOA) != 0;
   // bucket growth strategy (bucket multi-value tables)
   int growth = kGrowExact;
   std::vector<uint64_t> cum_size, cum_foot;
@@ -395,6 +410,8 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   t->capacity = cap;
   t->slot_bytes = slot_bytes;
   t->table_bytes = cap * slot_bytes;
+  const uint64_t soa_vals_off = align_up(t->table_bytes, kAlign);  // SoA: the value array follows the keys
+  if (soa) t->table_bytes = soa_vals_off + cap * static_cast<uint64_t>(cfg->value_bytes);
   t->pool_capacity = mv ? cfg->value_pool_capacity : 0;
 
   DeviceGuard guard(t->device);
@@ -434,6 +451,7 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   t->d_nkeys = reinterpret_cast<unsigned long long*>(base + off_meta + 16);
   t->d_cursor = reinterpret_cast<unsigned long long*>(base + off_meta + 24);
   t->d_ovf = sv ? reinterpret_cast<uint32_t*>(base + off_ovf) : nullptr;
+  t->d_vals = soa ? static_cast<void*>(base + soa_vals_off) : nullptr;
   t->d_pending = mv ? reinterpret_cast<uint32_t*>(base + off_pending) : nullptr;
   t->d_base = growth != kGrowExact ? reinterpret_cast<uint32_t*>(base + off_base) : nullptr;
   t->d_growth = growth == kGrowTable ? reinterpret_cast<uint64_t*>(base + off_growth) : nullptr;

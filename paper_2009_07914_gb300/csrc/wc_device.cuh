@@ -114,6 +114,7 @@ struct LayoutP32 {
   static constexpr int kWords = 1;
   static constexpr bool kHalf = false;   // slots of 4 bytes, two per loaded 64-bit word
   static constexpr bool kCount = false;  // duplicates overwrite the value (single-value table)
+  static constexpr bool kSoA = false;    // values in the slot word (not in a separate array)
   static constexpr Key kEmpty = 0u;
   static constexpr Key kTomb = 0xffffffffu;
   static constexpr Val kNotFound = 0xffffffffu;
@@ -132,6 +133,7 @@ struct LayoutP32 {
   __device__ static Slot shfl(const Slot& s, int src) { return Slot{__shfl_sync(kFull, s.w, src)}; }
 };
 
+
 // 16-byte array-of-structs slot {uint64 key, uint64 value}, claimed with one 128-bit CAS
 // (atom.cas.b128, sm_90 and later).  The paper's GV100 had only 64-bit CAS and had to
 // swap the key first and store the value afterwards (Sec. II, hazard (1) of Sec. IV-D);
@@ -145,6 +147,7 @@ struct LayoutP64 {
   static constexpr int kWords = 2;
   static constexpr bool kHalf = false;
   static constexpr bool kCount = false;
+  static constexpr bool kSoA = false;
   static constexpr Key kEmpty = 0ull;
   static constexpr Key kTomb = ~0ull;
   static constexpr Val kNotFound = ~0ull;
@@ -197,6 +200,7 @@ struct LayoutK64 {
   static constexpr int kWords = 1;
   static constexpr bool kHalf = false;
   static constexpr bool kCount = false;
+  static constexpr bool kSoA = false;
   static constexpr Key kEmpty = 0ull;
   static constexpr Key kTomb = ~0ull;
   static constexpr Val kNotFound = 0ull;
@@ -218,6 +222,7 @@ struct LayoutK32 {
   static constexpr int kWords = 1;       // per loaded word (two slots)
   static constexpr bool kHalf = true;
   static constexpr bool kCount = false;
+  static constexpr bool kSoA = false;
   static constexpr Key kEmpty = 0u;
   static constexpr Key kTomb = 0xffffffffu;
   static constexpr Val kNotFound = 0u;
@@ -229,6 +234,40 @@ struct LayoutK32 {
   __device__ static void store_val(Slot*, Val) {}
   __device__ static Slot shfl(const Slot& s, int src) { return Slot{__shfl_sync(kFull, s.k, src)}; }
 };
+
+// Struct-of-arrays single-value tables (Sec. IV-A: keys and values in two arrays of the
+// same length): probing reads the key array only -- twice the keys per line for 4+4-byte
+// pairs -- and a hit reads the value at the same index.  An insert claims the key slot
+// with one CAS and then writes the value with a plain store; the value is complete when
+// the insert call is (Sec. IV-D orders calls), the relaxed value write the paper notes.
+struct LayoutS32 : LayoutK32 {
+  static constexpr bool kSoA = true;
+  static constexpr Val kNotFound = 0xffffffffu;
+};
+struct LayoutS64 : LayoutK64 {
+  static constexpr bool kSoA = true;
+  static constexpr Val kNotFound = ~0ull;
+};
+
+// Value of slot `idx` (whose word is s) and its update, for every layout: packed layouts
+// keep the value in the slot word; struct-of-arrays layouts in the value array.
+template <class L>
+__device__ __forceinline__ typename L::Val slot_value(const typename L::Slot& s, const void* vals, uint64_t idx) {
+  if constexpr (L::kSoA) {
+    return static_cast<const typename L::Val*>(vals)[idx];
+  } else {
+    return L::val(s);
+  }
+}
+
+template <class L>
+__device__ __forceinline__ void slot_store_value(void* slots, void* vals, uint64_t idx, typename L::Val v) {
+  if constexpr (L::kSoA) {
+    static_cast<typename L::Val*>(vals)[idx] = v;
+  } else {
+    L::store_val(static_cast<typename L::Slot*>(slots) + idx, v);
+  }
+}
 
 // S consecutive slots of one lane.
 template <class L, int S>

@@ -135,7 +135,8 @@ wc_status wc_table_restore(wc_table* t, const void* h_in, uint64_t bytes, void* 
 
 wc_status wc_table_device_view(const wc_table* t, wc_device_view* h_out) {
   if (t == nullptr || h_out == nullptr) return WC_ERR_INVALID_ARG;
-  if (t->cfg.kind != WC_SINGLE_VALUE && t->cfg.kind != WC_MULTI_VALUE_OA) return WC_ERR_UNSUPPORTED;
+  if ((t->cfg.kind != WC_SINGLE_VALUE && t->cfg.kind != WC_MULTI_VALUE_OA) || t->d_vals != nullptr)
+    return WC_ERR_UNSUPPORTED;
   h_out->slots = t->d_slots;
   h_out->status = t->d_status;
   h_out->size = t->d_size;

@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kExecThreads, 3) k_exec(const ExecHeader* __re
         sv_insert_range<L, GI, SI>(t, static_cast<const uint32_t*>(it.keys), static_cast<const uint32_t*>(it.vals),
                                    src, flags, delta);
       } else if (op == WC_OP_RETRIEVE) {
-        EmitValue<L> emit{static_cast<uint32_t*>(it.out), it.found};
+        EmitValue<L> emit{static_cast<uint32_t*>(it.out), it.found, nullptr};
         sv_retrieve_range<L, GR, SR>(t, static_cast<const uint32_t*>(it.keys), src, emit, flags);
       } else {
         NoOnErase none;
@@ -332,7 +332,7 @@ wc_status wc_executor_submit(wc_executor* ex, const wc_work* h_items, uint32_t c
     const wc_work& w = h_items[i];
     const wc_table* t = w.table;
     if (t == nullptr || w.op < WC_OP_INSERT || w.op > WC_OP_ERASE) return WC_ERR_INVALID_ARG;
-    if (t->cfg.kind != WC_SINGLE_VALUE || t->slot_bytes != 8 || static_cast<int>(t->W) != ex->cfg.window_width ||
+    if (t->cfg.kind != WC_SINGLE_VALUE || t->d_vals != nullptr || t->slot_bytes != 8 || static_cast<int>(t->W) != ex->cfg.window_width ||
         t->device != ex->cfg.device)
       return WC_ERR_UNSUPPORTED;
     if (w.n > 0 && (w.d_keys == nullptr || (w.op == WC_OP_INSERT && w.d_values == nullptr) ||

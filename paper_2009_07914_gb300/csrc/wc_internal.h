@@ -19,6 +19,7 @@ struct TableDesc {
   unsigned long long* size;          // SV: live keys; MV: stored pairs
   unsigned long long* nkeys;         // MV: distinct live keys
   uint32_t* ovf;                     // SV: one overflow bit per window (see wc_device.cuh); else null
+  void* vals;                        // SoA tables: the value array (slot i's value); else null
   uint32_t p;                        // windows (prime)
   uint32_t W;                        // slots per window
 };
@@ -71,6 +72,7 @@ struct wc_table {
   unsigned long long* d_nkeys;
   unsigned long long* d_cursor;
   uint32_t* d_ovf;       // SV: overflow bits, one per window
+  void* d_vals;          // SoA single-value tables: value array (capacity entries)
   uint32_t* d_pending;   // MV: capacity entries
   uint32_t* d_base;      // MV with bucket growth: capacity entries
   uint64_t* d_growth;    // MV with kGrowTable: cum_size[nbuckets] then cum_foot[nbuckets]

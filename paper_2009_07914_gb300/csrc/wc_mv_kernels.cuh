@@ -587,7 +587,9 @@ __global__ void __launch_bounds__(kAllocThreads) k_mv_alloc_growth(TableDesc t, 
 
 struct EmitCount {
   uint64_t* __restrict__ offs;
-  __device__ void operator()(uint64_t pos, bool hit, const KsSlot& s) const { offs[pos] = hit ? h_count(s.v) : 0; }
+  __device__ void operator()(uint64_t pos, bool hit, const KsSlot& s, uint64_t) const {
+    offs[pos] = hit ? h_count(s.v) : 0;
+  }
 };
 
 template <class KIn, int G, int S>

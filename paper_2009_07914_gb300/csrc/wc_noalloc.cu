@@ -122,7 +122,8 @@ cudaError_t dispatch(const wc_table* t, const void* keys, const void* vals, uint
 
 extern "C" wc_status wc_insert_noalloc(wc_table* t, const void* d_keys, const void* d_values, uint64_t n,
                                        void* stream) {
-  if (t == nullptr || t->cfg.kind != WC_SINGLE_VALUE) return t == nullptr ? WC_ERR_INVALID_ARG : WC_ERR_UNSUPPORTED;
+  if (t == nullptr || t->cfg.kind != WC_SINGLE_VALUE || t->d_vals != nullptr)
+    return t == nullptr ? WC_ERR_INVALID_ARG : WC_ERR_UNSUPPORTED;
   const uint64_t pair = static_cast<uint64_t>(t->cfg.key_bytes) + static_cast<uint64_t>(t->cfg.value_bytes);
   // keys and values each start on a 256-byte boundary inside the buffer
   if (n > (WC_NOALLOC_SCRATCH_BYTES - 512) / pair) return WC_ERR_INVALID_ARG;

@@ -157,7 +157,9 @@ struct Feed {
 
 // ---------------------------------------------------------------------------------------
 // retrieve: out[i] = value of keys[i] or NOT_FOUND; found[i] = 1/0 (Sec. IV-B4).
-// Emit is called by one lane per finished query: emit(pos, hit, slot).
+// Emit is called by one lane per finished query: emit(pos, hit, slot, index) -- index is
+// the matching slot's position in the table (struct-of-arrays layouts read the value
+// there; 0 for other layouts).
 template <class L, int G, int S, class Emit, class KIn = typename L::Key>
 __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn* __restrict__ keys, RangeSrc& src,
                                                   Emit& emit, uint32_t& flags) {
@@ -186,7 +188,7 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
       k = static_cast<Key>(kin);
       if (is_sentinel(kin)) {
         flags |= kFlagInvalid;
-        if (ln.r == 0) emit(pos, false, Slot{});
+        if (ln.r == 0) emit(pos, false, Slot{}, 0ull);
       } else {
         act = true;
         j = 0;
@@ -210,12 +212,17 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
     if (t.ovf != nullptr && act && !bm && !be) fw = ovf_word(t.ovf, w);
     Slot hit = pick<L, S>(s, mm ? __ffs(mm) - 1 : 0);
     if constexpr (G > 1) hit = L::shfl(hit, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
+    uint64_t hidx = 0;
+    if constexpr (L::kSoA) {
+      hidx = static_cast<uint64_t>(w) * W + ln.r * S + (mm ? __ffs(mm) - 1 : 0);
+      if constexpr (G > 1) hidx = __shfl_sync(kFull, hidx, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
+    }
     if (act) {
       if (bm) {
-        if (ln.r == 0) emit(pos, true, hit);
+        if (ln.r == 0) emit(pos, true, hit, hidx);
         act = false;
       } else if (be || !ovf_bit(fw, w) || ++j >= t.p) {
-        if (ln.r == 0) emit(pos, false, hit);
+        if (ln.r == 0) emit(pos, false, hit, hidx);
         act = false;
       } else {
         w = probe_next(w, step, t.p);
@@ -228,8 +235,9 @@ template <class L>
 struct EmitValue {
   typename L::Val* __restrict__ out;
   uint8_t* __restrict__ found;
-  __device__ void operator()(uint64_t pos, bool hit, const typename L::Slot& s) const {
-    if (out) out[pos] = hit ? L::val(s) : L::kNotFound;  // no output: membership only
+  const void* vals;  // struct-of-arrays value array (else unused)
+  __device__ void operator()(uint64_t pos, bool hit, const typename L::Slot& s, uint64_t idx) const {
+    if (out) out[pos] = hit ? slot_value<L>(s, vals, idx) : L::kNotFound;  // no output: membership only
     if (found) found[pos] = hit ? 1 : 0;
   }
 };
@@ -249,7 +257,7 @@ __global__ void __launch_bounds__(256, retrieve_min_blocks<L, S>()) k_sv_retriev
   RangeSrc src(n, per_warp, nullptr, 0);
   if (src.next >= src.end) return;
   uint32_t flags = 0;
-  EmitValue<L> emit{out, found};
+  EmitValue<L> emit{out, found, t.vals};
   sv_retrieve_range<L, G, S>(t, keys, src, emit, flags);
   flush_flags(t.status, flags);
 }
@@ -264,8 +272,9 @@ struct EmitSwept {
   const uint32_t* __restrict__ qpos;
   uint32_t* __restrict__ rk;
   typename L::Val* __restrict__ rv;
-  __device__ void operator()(uint64_t i, bool hit, const typename L::Slot& s) const {
-    rv[i] = hit ? L::val(s) : L::kNotFound;
+  const void* vals;
+  __device__ void operator()(uint64_t i, bool hit, const typename L::Slot& s, uint64_t idx) const {
+    rv[i] = hit ? slot_value<L>(s, vals, idx) : L::kNotFound;
     rk[i] = qpos[i] | (hit ? 0x80000000u : 0u);
   }
 };
@@ -278,7 +287,7 @@ __global__ void __launch_bounds__(256) k_sv_retrieve_swept(TableDesc t, const ty
                                                            typename L::Val* __restrict__ rv) {
   RangeSrc src(n, 0, counter, chunk);
   uint32_t flags = 0;
-  EmitSwept<L> emit{qpos, rk, rv};
+  EmitSwept<L> emit{qpos, rk, rv, t.vals};
   sv_retrieve_range<L, G, S>(t, keys, src, emit, flags);
   flush_flags(t.status, flags);
 }
@@ -382,17 +391,25 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
     const bool claim = bm == 0 && (be != 0 || last);
 
     // The key is present: overwrite its value (duplicate warning, Sec. IV-B3).
-    if (act && bm && ln.r == __ffs(bm) - 1) L::store_val(slots + lane_slot + (__ffs(mm) - 1), v);
+    if (act && bm && ln.r == __ffs(bm) - 1) slot_store_value<L>(slots, t.vals, lane_slot + (__ffs(mm) - 1), v);
 
     // Claim the earliest candidate: a remembered tombstone from an earlier window,
     // else the first empty-or-tombstone slot of this window (Sec. IV-B2 steps 4 and 6).
     bool ok = false;
     if (act && claim) {
       if (have_t) {
-        if (ln.r == 0) ok = L::cas(slots + t_slot, t_word, L::make(k, v));
+        if (ln.r == 0) {
+          ok = L::cas(slots + t_slot, t_word, L::make(k, v));
+          if constexpr (L::kSoA) {
+            if (ok) slot_store_value<L>(slots, t.vals, t_slot, v);
+          }
+        }
       } else if (bc && ln.r == __ffs(bc) - 1) {
         const int sub = __ffs(me | mt) - 1;
         ok = L::cas(slots + lane_slot + sub, pick<L, S>(s, sub), L::make(k, v));
+        if constexpr (L::kSoA) {
+          if (ok) slot_store_value<L>(slots, t.vals, lane_slot + sub, v);
+        }
       }
     }
     if constexpr (G > 1) ok = __shfl_sync(kFull, ok, ln.gbase + ((have_t || bc == 0) ? 0 : __ffs(bc) - 1));

@@ -316,7 +316,62 @@ def test_overflow_bits_only_for_single_value_tables(wc):
     with pytest.raises(wc.WcError):
         wc.MultiValueTable(8, 4, min_capacity=1000, value_pool_capacity=1000, options=wc.WC_OPT_OVERFLOW_BITS)
     with pytest.raises(wc.WcError):
-        wc.SingleValueTable(4, 4, min_capacity=1000, options=2)
+        wc.SingleValueTable(4, 4, min_capacity=1000, options=4)  # no such option
     t = wc.SingleValueTable(4, 4, min_capacity=1000)
     with pytest.raises(wc.WcError):
         wc.wc_table_dump_overflow_bits(t.handle)
+
+
+SOA_SHAPES = [(4, 8, 1), (4, 8, 2), (4, 16, 1), (4, 16, 2), (4, 16, 4), (4, 32, 4), (4, 32, 8),
+              (8, 4, 1), (8, 4, 2), (8, 8, 1), (8, 8, 2), (8, 16, 2), (8, 16, 4), (8, 32, 4), (8, 32, 8)]
+
+
+@pytest.mark.parametrize("kb,W,G", SOA_SHAPES)
+def test_soa_layout_parity_every_shape(wc, kb, W, G):
+    """WC_OPT_SOA (keys and values in two arrays, Sec. IV-A): inserts with overwrites,
+    lookups with absent keys and sentinels, erase and re-insert over tombstones, the
+    blocked insert and retrieve schemes and overflow bits -- the oracle's results, and the
+    key array passes the slot-dump invariant checker."""
+    n = 300_007
+    if kb == 4:
+        d = wc_inputs.sv_insert_retrieve_u32(0x50A + W + G, n, n // 2, 200_000)
+        keys, vals, q = d["keys"], d["values"], d["queries"]
+    else:
+        allk = wc_inputs.distinct_u64(0x50A + W + G, n + 200_000)
+        keys, vals = allk[:n], wc_inputs.uniform_u64(9, n)
+        q = allk[wc_inputs.shuffle_index(10, allk.size)]
+    q = np.concatenate([q, np.array([0, 2 ** (8 * kb) - 1], dtype=q.dtype)])
+    opts = wc.WC_OPT_SOA | (wc.WC_OPT_OVERFLOW_BITS if G % 2 == 0 else 0)
+    t = make_sv(wc, kb, kb, int(n / 0.9) + 1, W, G, options=opts, seed=0x50A)
+    assert t.info["slot_bytes"] == kb
+    o = oracle.SingleValue(kb, kb)
+    assert t.insert(keys, vals) == o.insert(keys, vals) == 0
+    check_retrieve(t, o, q)
+    over = (vals[:5000] ^ 0x77).astype(vals.dtype)
+    assert t.insert(keys[:5000], over) == o.insert(keys[:5000], over) == oracle.FLAG_DUPLICATE_KEY
+    t.erase(keys[5000::3])
+    o.erase(keys[5000::3])
+    check_retrieve(t, o, q)
+    for op in (wc.WC_OP_INSERT, wc.WC_OP_RETRIEVE):
+        t.set_launch(op, G, scheme=wc.WC_SCHEME_BLOCKED, region_mib=1)
+    back = keys[5000::6]
+    bv = (vals[5000::6] ^ 0x99).astype(vals.dtype)
+    assert t.insert(back, bv) == o.insert(back, bv) == 0
+    check_retrieve(t, o, q)
+    assert t.size() == o.size()
+    info = t.info
+    bits = wc.wc_table_dump_overflow_bits(t.handle) if opts & wc.WC_OPT_OVERFLOW_BITS else None
+    r = oracle.check_slots(wc.wc_table_dump_slots(t.handle), info["windows"], info["window_width"], kb, 0x50A, True,
+                           bits, key_bytes=kb)
+    assert r == {"live": o.size(), "dups": 0, "unreachable": 0}
+
+
+def test_soa_tables_are_refused_where_the_packed_layout_is_required(wc):
+    t = wc.SingleValueTable(4, 4, min_capacity=4096, options=wc.WC_OPT_SOA)
+    with pytest.raises(wc.WcError):
+        wc.wc_table_device_view(t.handle)
+    k = t.keys_dev(np.arange(1, 100, dtype=np.uint32))
+    with pytest.raises(wc.WcError):
+        wc.wc_insert_noalloc(t.handle, k, k)
+    with pytest.raises(wc.WcError):  # struct-of-arrays is a single-value layout
+        wc.CountingTable(4, min_capacity=1000, options=wc.WC_OPT_SOA)
