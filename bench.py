@@ -341,7 +341,7 @@ def run_wc(args, rank, world, local_rank):
     ms_step = total_ms / args.steps
     value = world * 2 * n / (ms_step * 1e-3) / 1e9
 
-    # end-to-end through the C ABI from pinned host buffers (H2D, insert, retrieve, D2H)
+    # end-to-end through the C ABI's host-buffer calls (H2D, insert, retrieve, D2H in the timed region)
     e2e = None
     if not args.no_e2e:
         hk = torch.from_numpy(d["keys"].view(np.int32)).pin_memory()
@@ -349,21 +349,16 @@ def run_wc(args, rank, world, local_rank):
         hq = torch.from_numpy(d["queries"].view(np.int32)).pin_memory()
         ho = torch.empty(n, dtype=torch.int32).pin_memory()
         hf = torch.empty(n, dtype=torch.uint8).pin_memory()
-        dk, dv, dq = torch.empty_like(keys), torch.empty_like(vals), torch.empty_like(qk)
 
         def e2e_step():
             api.wc_table_clear(h, s)
-            dk.copy_(hk, non_blocking=True)
-            dv.copy_(hv, non_blocking=True)
-            api.wc_insert(h, dk, dv, n, s)
-            dq.copy_(hq, non_blocking=True)
-            api.wc_retrieve(h, dq, out, found, n, s)
-            ho.copy_(out, non_blocking=True)
-            hf.copy_(found, non_blocking=True)
+            api.wc_insert_host(h, hk, hv, n, s)
+            api.wc_retrieve_host(h, hq, ho, hf, n, s)
         for _ in range(2):
             e2e_step()
         torch.cuda.synchronize()
         assert np.array_equal(hf.numpy(), found.cpu().numpy())
+        assert np.array_equal(ho.numpy()[hf.numpy() == 1], out.cpu().numpy()[hf.numpy() == 1])
         k = max(1, args.steps // 2)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(s)
@@ -373,7 +368,9 @@ def run_wc(args, rank, world, local_rank):
         torch.cuda.synchronize()
         e_ms = a.elapsed_time(b) / k
         e2e = {"value": world * 2 * n / (e_ms * 1e-3) / 1e9, "unit": "G ops/s",
-               "h2d_bytes_per_step": n * 4 * 3, "d2h_bytes_per_step": n * 5, "ms_per_step": e_ms}
+               "h2d_bytes_per_step": n * 4 * 3, "d2h_bytes_per_step": n * 5, "ms_per_step": e_ms,
+               "calls": "wc_insert_host + wc_retrieve_host from pinned buffers (chunked copies on the "
+                        "table's copy streams, overlapping the kernels)"}
 
     if rank != 0:
         return

@@ -4,8 +4,12 @@
  * GPUs", 2020).
  *
  * Conventions for every call below
- *   - Pointers named d_* are device pointers (global memory of the table's device).
- *     Pointers named h_* are host pointers.  The caller owns every key, value, output
+ *   - Pointers named d_* must be device-accessible: global memory of the table's device,
+ *     or host memory mapped into the device's address space (pinned with cudaHostAlloc /
+ *     cudaMallocHost), which the kernels then read and write over NVLink-C2C themselves;
+ *     any other pointer is refused with WC_ERR_INVALID_ARG before anything is launched.
+ *     Pointers named h_* are host pointers (the *_host calls stage them through the
+ *     device, which is faster than device access to host memory for scattered outputs).  The caller owns every key, value, output
  *     and offset buffer; the library owns a table's slot array, value pool and the few
  *     device words (status, counters) it allocates at create time.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
@@ -257,6 +261,14 @@ wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint6
 wc_status wc_insert_noalloc(wc_table* t, const void* d_keys, const void* d_values, uint64_t n,
                             void* stream);
 
+/* The same inserts from HOST buffers (pinned memory for full speed; pageable memory works,
+ * with copies synchronous to the host): the batch moves to the device in chunks of up to
+ * 2^25 pairs through two device staging buffers the table keeps (allocated on first use),
+ * each chunk's copy on the table's own copy stream overlapping the insert of the previous
+ * chunk on `stream`.  Asynchronous: the host buffers must stay valid and unchanged until
+ * `stream` has passed this call.  Values may be NULL where wc_insert allows it. */
+wc_status wc_insert_host(wc_table* t, const void* h_keys, const void* h_values, uint64_t n, void* stream);
+
 /* Single-value retrieve (Sec. IV-B4; counting tables: the counts): d_values_out[i] = value
  * of d_keys[i], or all ones
  * (NOT_FOUND) when absent; d_found_or_null[i] = 1/0 when the mask is given (a stored value
@@ -264,6 +276,13 @@ wc_status wc_insert_noalloc(wc_table* t, const void* d_keys, const void* d_value
  * empty slot.  Multi-value tables return WC_ERR_UNSUPPORTED. */
 wc_status wc_retrieve(wc_table* t, const void* d_keys, uint64_t n, void* d_values_out,
                       uint8_t* d_found_or_null, void* stream);
+
+/* wc_retrieve from and into HOST buffers: chunks of up to 2^23 queries are copied in on one
+ * copy stream, looked up on `stream` and the results copied out on another, so the copies
+ * of neighbouring chunks overlap the lookups.  `stream` completes after the last copy out.
+ * Single-value and counting tables.  Asynchronous as wc_insert_host. */
+wc_status wc_retrieve_host(wc_table* t, const void* h_keys, uint64_t n, void* h_values_out,
+                           uint8_t* h_found_or_null, void* stream);
 
 /* Membership (Sec. IV-B4 without values): d_found[i] = 1 if d_keys[i] is stored, else 0
  * (Bloom filters: 1 if all the key's bits are set -- possibly a false positive, never a

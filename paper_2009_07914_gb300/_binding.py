@@ -99,6 +99,8 @@ _SIGS = {
     "wc_retrieve": (ctypes.c_int, [_vp, _vp, _u64, _vp, _vp, _vp]),
     "wc_erase": (ctypes.c_int, [_vp, _vp, _u64, _vp]),
     "wc_contains": (ctypes.c_int, [_vp, _vp, _u64, _vp, _vp]),
+    "wc_insert_host": (ctypes.c_int, [_vp, _vp, _vp, _u64, _vp]),
+    "wc_retrieve_host": (ctypes.c_int, [_vp, _vp, _u64, _vp, _vp, _vp]),
     "wc_count_values": (ctypes.c_int, [_vp, _vp, _u64, _vp, ctypes.POINTER(_u64), _vp]),
     "wc_retrieve_multi": (ctypes.c_int, [_vp, _vp, _u64, _vp, _vp, _vp]),
     "wc_size": (ctypes.c_int, [_vp, ctypes.POINTER(_u64), _vp]),

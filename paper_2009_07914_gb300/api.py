@@ -21,7 +21,8 @@ __all__ = [
     "wc_plan_capacity", "wc_table_create", "wc_table_destroy", "wc_table_clear", "wc_table_get_info",
     "wc_table_set_launch", "wc_table_get_launch", "wc_insert", "wc_retrieve", "wc_erase", "wc_count_values",
     "wc_retrieve_multi", "wc_size", "wc_num_keys", "wc_load_factor", "wc_get_status", "wc_status_string",
-    "wc_insert_noalloc", "WC_NOALLOC_SCRATCH_BYTES", "wc_value_pool_used", "wc_contains",
+    "wc_insert_noalloc", "WC_NOALLOC_SCRATCH_BYTES", "wc_value_pool_used", "wc_contains", "wc_insert_host",
+    "wc_retrieve_host",
 ]
 
 
@@ -124,6 +125,38 @@ def wc_retrieve(t: int, keys, values_out, found_out=None, n: int | None = None, 
         _n_of(n, found_out, 1)
     check(lib().wc_retrieve(t, ptr(keys), n, ptr(values_out), ptr(found_out), stream_handle(stream)),
           "wc_retrieve")
+
+
+def _host_ptr(x) -> int | None:
+    """Address of a host buffer: a CPU tensor (pinned for full speed) or a numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, torch.Tensor):
+        if x.is_cuda:
+            raise ValueError("host buffers must be CPU tensors")
+        if x.numel() and not x.is_contiguous():
+            raise ValueError("buffers must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("buffers must be contiguous")
+        return x.ctypes.data
+    raise TypeError("expected a CPU tensor, a numpy array or an integer address, got %r" % type(x))
+
+
+def wc_insert_host(t: int, keys, values, n: int | None = None, stream=None):
+    """wc_insert from host buffers (pinned CPU tensors or numpy arrays)."""
+    n = len(keys) if n is None else int(n)
+    check(lib().wc_insert_host(t, _host_ptr(keys), _host_ptr(values), n, stream_handle(stream)), "wc_insert_host")
+
+
+def wc_retrieve_host(t: int, keys, values_out, found_out=None, n: int | None = None, stream=None):
+    """wc_retrieve from and into host buffers; the results are there once `stream` is."""
+    n = len(keys) if n is None else int(n)
+    check(lib().wc_retrieve_host(t, _host_ptr(keys), n, _host_ptr(values_out), _host_ptr(found_out),
+                                 stream_handle(stream)), "wc_retrieve_host")
 
 
 def wc_contains(t: int, keys, found_out, n: int | None = None, stream=None):

@@ -506,6 +506,7 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
 wc_status wc_table_destroy(wc_table* t) {
   if (t == nullptr) return WC_ERR_INVALID_ARG;
   DeviceGuard guard(t->device);
+  host_pipe_free(t);
   if (t->d_scratch != nullptr) {
     cudaDeviceSynchronize();
     cudaFree(t->d_scratch);
@@ -560,12 +561,34 @@ wc_status wc_table_get_launch(const wc_table* t, int32_t op, wc_launch* h_out) {
   return WC_OK;
 }
 
+// A buffer the table's kernels may read or write: device memory of the table's device
+// (or managed memory), or host memory mapped into the device's address space at the same
+// address (pinned with cudaHostAlloc / cudaMallocHost, or registered mapped) -- on GB300
+// the kernels then move it over NVLink-C2C themselves.  Anything else would fault on the
+// device and is refused here.
+static bool device_accessible(const wc_table* t, const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  if (a.type == cudaMemoryTypeDevice) return a.device == t->device;
+  if (a.type == cudaMemoryTypeHost) return a.devicePointer == p;
+  return false;  // unregistered host memory
+}
+
+static wc_status check_buffer(const wc_table* t, const void* p, uint64_t n, uint64_t align) {
+  if (n == 0) return WC_OK;
+  if (p == nullptr || !aligned(p, align) || !device_accessible(t, p)) return WC_ERR_INVALID_ARG;
+  return WC_OK;
+}
+
 static wc_status check_bulk(const wc_table* t, const void* keys, uint64_t n) {
   if (t == nullptr) return WC_ERR_INVALID_ARG;
   if (n > kMaxBatch) return WC_ERR_INVALID_ARG;
-  if (n > 0 && keys == nullptr) return WC_ERR_INVALID_ARG;
-  if (n > 0 && !aligned(keys, static_cast<uint64_t>(t->cfg.key_bytes))) return WC_ERR_INVALID_ARG;
-  return WC_OK;
+  return check_buffer(t, keys, n, static_cast<uint64_t>(t->cfg.key_bytes));
 }
 
 wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint64_t n, void* stream) {
@@ -573,9 +596,12 @@ wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint6
   if (st != WC_OK) return st;
   const bool weights_optional =
       t->cfg.kind == WC_COUNTING || t->cfg.kind == WC_HASH_SET || t->cfg.kind == WC_BLOOM_FILTER;
-  if (n > 0 && ((d_values == nullptr && !weights_optional) ||
-                (d_values != nullptr && !aligned(d_values, static_cast<uint64_t>(t->cfg.value_bytes)))))
-    return WC_ERR_INVALID_ARG;
+  if (n > 0 && d_values == nullptr && !weights_optional) return WC_ERR_INVALID_ARG;
+  if (d_values != nullptr && (t->cfg.kind == WC_HASH_SET || t->cfg.kind == WC_BLOOM_FILTER)) d_values = nullptr;
+  if (d_values != nullptr) {
+    st = check_buffer(t, d_values, n, static_cast<uint64_t>(t->cfg.value_bytes));
+    if (st != WC_OK) return st;
+  }
   if (n == 0) return WC_OK;
   if (t->cfg.kind == WC_COUNTING) {
     DeviceGuard guard(t->device);
@@ -599,8 +625,9 @@ wc_status wc_retrieve(wc_table* t, const void* d_keys, uint64_t n, void* d_value
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
   if (t->cfg.kind != WC_SINGLE_VALUE && t->cfg.kind != WC_COUNTING) return WC_ERR_UNSUPPORTED;
-  if (n > 0 && (d_values_out == nullptr || !aligned(d_values_out, static_cast<uint64_t>(t->cfg.value_bytes))))
-    return WC_ERR_INVALID_ARG;
+  st = check_buffer(t, d_values_out, n, static_cast<uint64_t>(t->cfg.value_bytes));
+  if (st == WC_OK && d_found_or_null != nullptr) st = check_buffer(t, d_found_or_null, n, 1);
+  if (st != WC_OK) return st;
   if (n == 0) return WC_OK;
   DeviceGuard guard(t->device);
   return cuda_status(
@@ -623,7 +650,8 @@ wc_status wc_erase(wc_table* t, const void* d_keys, uint64_t n, void* stream) {
 wc_status wc_contains(wc_table* t, const void* d_keys, uint64_t n, uint8_t* d_found, void* stream) {
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
-  if (n > 0 && d_found == nullptr) return WC_ERR_INVALID_ARG;
+  st = check_buffer(t, d_found, n, 1);
+  if (st != WC_OK) return st;
   const int kind = t->cfg.kind;
   if (kind != WC_SINGLE_VALUE && kind != WC_COUNTING && kind != WC_HASH_SET && kind != WC_BLOOM_FILTER)
     return WC_ERR_UNSUPPORTED;
@@ -640,7 +668,8 @@ wc_status wc_count_values(wc_table* t, const void* d_keys, uint64_t n, uint64_t*
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
   if (t->cfg.kind != WC_MULTI_VALUE && t->cfg.kind != WC_MULTI_VALUE_OA) return WC_ERR_UNSUPPORTED;
-  if (d_offsets == nullptr || !aligned(d_offsets, 8)) return WC_ERR_INVALID_ARG;
+  st = check_buffer(t, d_offsets, n + 1, 8);
+  if (st != WC_OK) return st;
   DeviceGuard guard(t->device);
   cudaStream_t s = as_stream(stream);
   cudaError_t e = cudaSuccess;
@@ -663,9 +692,9 @@ wc_status wc_retrieve_multi(wc_table* t, const void* d_keys, uint64_t n, const u
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
   if (t->cfg.kind != WC_MULTI_VALUE && t->cfg.kind != WC_MULTI_VALUE_OA) return WC_ERR_UNSUPPORTED;
-  if (d_offsets == nullptr || !aligned(d_offsets, 8)) return WC_ERR_INVALID_ARG;
-  if (n > 0 && (d_values_out == nullptr || !aligned(d_values_out, static_cast<uint64_t>(t->cfg.value_bytes))))
-    return WC_ERR_INVALID_ARG;
+  st = check_buffer(t, d_offsets, n + 1, 8);
+  if (st == WC_OK) st = check_buffer(t, d_values_out, n, static_cast<uint64_t>(t->cfg.value_bytes));
+  if (st != WC_OK) return st;
   if (n == 0) return WC_OK;
   DeviceGuard guard(t->device);
   if (t->cfg.kind == WC_MULTI_VALUE_OA)

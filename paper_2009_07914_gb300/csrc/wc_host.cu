@@ -1,0 +1,208 @@
+// Bulk calls on host buffers (include/wc.h: wc_insert_host, wc_retrieve_host): the batch
+// moves through double-buffered device staging in chunks, copies on the table's own copy
+// streams overlapping the kernels of the neighbouring chunks on the caller's stream.
+// Host code only.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <new>
+
+#include "wc.h"
+#include "wc_internal.h"
+
+namespace wc {
+
+// Per-table state of the host pipeline, created on first use.
+struct HostPipe {
+  int device = -1;
+  cudaStream_t in = nullptr, out = nullptr;  // copy streams (host -> device, device -> host)
+  cudaEvent_t ready[2] = {}, done[2] = {}, freed[2] = {}, tail = nullptr;
+  void* stage = nullptr;                     // two staging buffers of `half` bytes
+  uint64_t half = 0;
+};
+
+void host_pipe_free(wc_table* t) {
+  HostPipe* h = t->host;
+  if (h == nullptr) return;
+  if (h->in) cudaStreamSynchronize(h->in);
+  if (h->out) cudaStreamSynchronize(h->out);
+  for (int b = 0; b < 2; ++b) {
+    if (h->ready[b]) cudaEventDestroy(h->ready[b]);
+    if (h->done[b]) cudaEventDestroy(h->done[b]);
+    if (h->freed[b]) cudaEventDestroy(h->freed[b]);
+  }
+  if (h->tail) cudaEventDestroy(h->tail);
+  if (h->in) cudaStreamDestroy(h->in);
+  if (h->out) cudaStreamDestroy(h->out);
+  if (h->stage) cudaFree(h->stage);
+  delete h;
+  t->host = nullptr;
+}
+
+namespace {
+
+constexpr uint64_t kInsertChunk = 1ull << 25;    // pairs per insert chunk (few: inserts sweep the table)
+constexpr uint64_t kRetrieveChunk = 1ull << 23;  // queries per retrieve chunk
+
+cudaError_t pipe_of(wc_table* t, uint64_t half, HostPipe** out) {
+  HostPipe* h = t->host;
+  if (h == nullptr) {
+    h = new (std::nothrow) HostPipe();
+    if (h == nullptr) return cudaErrorMemoryAllocation;
+    t->host = h;
+    h->device = t->device;
+    cudaError_t e = cudaStreamCreateWithFlags(&h->in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->out, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = cudaEventCreateWithFlags(&h->ready[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->done[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->freed[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->tail, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      host_pipe_free(t);
+      return e;
+    }
+  }
+  if (h->half < half) {
+    if (h->stage) {
+      cudaStreamSynchronize(h->in);
+      cudaStreamSynchronize(h->out);
+      cudaDeviceSynchronize();  // kernels of earlier calls may still read the staging
+      cudaFree(h->stage);
+      h->stage = nullptr;
+      h->half = 0;
+    }
+    cudaError_t e = cudaMalloc(&h->stage, 2 * half);
+    if (e != cudaSuccess) {
+      h->stage = nullptr;
+      return e;
+    }
+    h->half = half;
+  }
+  *out = h;
+  return cudaSuccess;
+}
+
+uint64_t align256(uint64_t x) { return (x + 255) / 256 * 256; }
+
+bool is_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+struct Guard {
+  int prev = -1;
+  explicit Guard(int d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~Guard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+wc_status status_of(cudaError_t e) {
+  if (e == cudaSuccess) return WC_OK;
+  return e == cudaErrorMemoryAllocation ? WC_ERR_OUT_OF_MEMORY : WC_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace wc
+
+using namespace wc;
+
+extern "C" {
+
+wc_status wc_insert_host(wc_table* t, const void* h_keys, const void* h_values, uint64_t n, void* stream) {
+  if (t == nullptr) return WC_ERR_INVALID_ARG;
+  if (n == 0) return WC_OK;
+  const bool no_values = t->cfg.kind == WC_HASH_SET || t->cfg.kind == WC_BLOOM_FILTER ||
+                         (t->cfg.kind == WC_COUNTING && h_values == nullptr);
+  if (h_keys == nullptr || !is_host(h_keys) || (!no_values && (h_values == nullptr || !is_host(h_values))))
+    return WC_ERR_INVALID_ARG;
+  if (t->cfg.kind == WC_MULTI_VALUE && n >= (1ull << 31)) return WC_ERR_INVALID_ARG;
+  Guard g(t->device);
+  const uint64_t kb = static_cast<uint64_t>(t->cfg.key_bytes), vb = no_values ? 0 : t->cfg.value_bytes;
+  const uint64_t chunk = std::min<uint64_t>(n, kInsertChunk);
+  const uint64_t koff = 0, voff = align256(chunk * kb);
+  HostPipe* h = nullptr;
+  cudaError_t e = pipe_of(t, voff + align256(chunk * vb), &h);
+  if (e != cudaSuccess) return status_of(e);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint64_t nchunks = (n + chunk - 1) / chunk;
+  for (uint64_t c = 0; c < nchunks; ++c) {
+    const int b = static_cast<int>(c & 1);
+    const uint64_t base = c * chunk, cnt = std::min(chunk, n - base);
+    char* buf = static_cast<char*>(h->stage) + b * h->half;
+    // the buffer is free once the insert that last read it has run
+    if ((e = cudaStreamWaitEvent(h->in, h->freed[b], 0)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(buf + koff, static_cast<const char*>(h_keys) + base * kb, cnt * kb,
+                             cudaMemcpyHostToDevice, h->in)) != cudaSuccess)
+      break;
+    if (!no_values && (e = cudaMemcpyAsync(buf + voff, static_cast<const char*>(h_values) + base * vb, cnt * vb,
+                                           cudaMemcpyHostToDevice, h->in)) != cudaSuccess)
+      break;
+    if ((e = cudaEventRecord(h->ready[b], h->in)) != cudaSuccess) break;
+    if ((e = cudaStreamWaitEvent(s, h->ready[b], 0)) != cudaSuccess) break;
+    const wc_status st = wc_insert(t, buf + koff, no_values ? nullptr : buf + voff, cnt, stream);
+    if (st != WC_OK) return st;
+    if ((e = cudaEventRecord(h->freed[b], s)) != cudaSuccess) break;
+  }
+  return status_of(e);
+}
+
+wc_status wc_retrieve_host(wc_table* t, const void* h_keys, uint64_t n, void* h_values_out, uint8_t* h_found_or_null,
+                           void* stream) {
+  if (t == nullptr) return WC_ERR_INVALID_ARG;
+  if (t->cfg.kind != WC_SINGLE_VALUE && t->cfg.kind != WC_COUNTING) return WC_ERR_UNSUPPORTED;
+  if (n == 0) return WC_OK;
+  if (h_keys == nullptr || h_values_out == nullptr || !is_host(h_keys) || !is_host(h_values_out) ||
+      (h_found_or_null != nullptr && !is_host(h_found_or_null)))
+    return WC_ERR_INVALID_ARG;
+  Guard g(t->device);
+  const uint64_t kb = static_cast<uint64_t>(t->cfg.key_bytes), vb = static_cast<uint64_t>(t->cfg.value_bytes);
+  const uint64_t chunk = std::min<uint64_t>(n, kRetrieveChunk);
+  const uint64_t ooff = align256(chunk * kb), foff = ooff + align256(chunk * vb);
+  HostPipe* h = nullptr;
+  cudaError_t e = pipe_of(t, foff + align256(chunk), &h);
+  if (e != cudaSuccess) return status_of(e);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint64_t nchunks = (n + chunk - 1) / chunk;
+  for (uint64_t c = 0; c < nchunks; ++c) {
+    const int b = static_cast<int>(c & 1);
+    const uint64_t base = c * chunk, cnt = std::min(chunk, n - base);
+    char* buf = static_cast<char*>(h->stage) + b * h->half;
+    // the buffer is free once its previous results have been copied out
+    if ((e = cudaStreamWaitEvent(h->in, h->freed[b], 0)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(buf, static_cast<const char*>(h_keys) + base * kb, cnt * kb, cudaMemcpyHostToDevice,
+                             h->in)) != cudaSuccess)
+      break;
+    if ((e = cudaEventRecord(h->ready[b], h->in)) != cudaSuccess) break;
+    if ((e = cudaStreamWaitEvent(s, h->ready[b], 0)) != cudaSuccess) break;
+    const wc_status st = wc_retrieve(t, buf, cnt, buf + ooff,
+                                     h_found_or_null ? reinterpret_cast<uint8_t*>(buf + foff) : nullptr, stream);
+    if (st != WC_OK) return st;
+    if ((e = cudaEventRecord(h->done[b], s)) != cudaSuccess) break;
+    if ((e = cudaStreamWaitEvent(h->out, h->done[b], 0)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(static_cast<char*>(h_values_out) + base * vb, buf + ooff, cnt * vb,
+                             cudaMemcpyDeviceToHost, h->out)) != cudaSuccess)
+      break;
+    if (h_found_or_null &&
+        (e = cudaMemcpyAsync(h_found_or_null + base, buf + foff, cnt, cudaMemcpyDeviceToHost, h->out)) != cudaSuccess)
+      break;
+    if ((e = cudaEventRecord(h->freed[b], h->out)) != cudaSuccess) break;
+  }
+  // the caller's stream completes after the last copy out
+  if (e == cudaSuccess) e = cudaEventRecord(h->tail, h->out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->tail, 0);
+  return status_of(e);
+}
+
+}  // extern "C"

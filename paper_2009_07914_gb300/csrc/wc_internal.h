@@ -44,6 +44,8 @@ struct PoolDesc {
 enum { kGrowExact = 0, kGrowConst = 1, kGrowTable = 2 };
 constexpr uint32_t kMaxGrowBuckets = 1024;
 
+struct HostPipe;  // staging of wc_insert_host / wc_retrieve_host (wc_host.cu)
+
 // Shape of one launch after the table's tuning was applied.
 struct LaunchShape {
   int group;           // lanes per key
@@ -88,6 +90,7 @@ struct wc_table {
   // scratch for the blocked scheme, grown on demand (stream-ordered allocation)
   mutable void* d_scratch;
   mutable uint64_t scratch_bytes;
+  wc::HostPipe* host = nullptr;  // host-buffer pipeline, created on first use
 };
 
 namespace wc {
@@ -119,6 +122,9 @@ int sm_count_of(int device);
 
 // Scratch of at least `bytes` on stream s (grows the table's buffer if needed).
 cudaError_t ensure_scratch(const wc_table* t, uint64_t bytes, cudaStream_t s);
+
+// Release the table's host-buffer pipeline (streams, events, staging).
+void host_pipe_free(wc_table* t);
 
 // Scheme the table uses for `op` on a batch of n keys.
 int scheme_for(const wc_table* t, int op, uint64_t n);
