@@ -141,15 +141,17 @@ typedef struct {
   double bucket_growth;
 } wc_table_config;
 
-/* WC_OPT_OVERFLOW_BITS (single-value tables only; no counterpart in the paper): keep one
- * overflow bit per window, set by an insert that walks past the window because it holds no
- * empty slot.  Lookups and erases then stop at a window without the key, without an empty
- * slot and with a clear bit -- a key stored further on would have set it -- instead of
- * walking on to a window with an empty slot.  Shortens the walks of absent keys at high
- * load (2^27 keys at load 0.9, half the queries absent: retrieve -8 %); costs present keys
- * outside their first window one dependent read of the bit per window (skewed queries of
+/* WC_OPT_OVERFLOW_BITS (single-value, counting and hash-set tables; no counterpart in the
+ * paper): keep eight overflow bits per window (one byte).  Each key has a 3-bit tag g, the
+ * low three bits of h = fmix64(key ^ seed) (wc_device_api.cuh: probe_init); an insert that
+ * walks past a window because it holds no empty slot sets bit g of that window's byte.
+ * Lookups and erases then stop at a window without the key, without an empty slot and with
+ * bit g clear -- a key of tag g stored further on would have set it -- instead of walking
+ * on to a window with an empty slot.  Shortens the walks of absent keys at high load (W = 8,
+ * load 0.9: 2.9 windows per absent key without the bits, 1.2 with them); costs present keys
+ * outside their first window one dependent read of the byte per window (skewed queries of
  * present keys: slower), and inserts one atomic OR per window walked past.  The bits cost
- * windows / 8 bytes. */
+ * one byte per window. */
 enum { WC_OPT_OVERFLOW_BITS = 1 };
 
 /* WC_OPT_SOA (single-value tables): struct-of-arrays layout (Sec. IV-A) -- the keys in one
@@ -354,7 +356,7 @@ typedef struct {
   void* slots;                 /* capacity slots, layout of wc_table_config */
   uint32_t* status;            /* the table's status word (WC_FLAG_* bits) */
   unsigned long long* size;    /* stored pairs */
-  uint32_t* overflow_bits;     /* WC_OPT_OVERFLOW_BITS tables, else NULL */
+  uint32_t* overflow_bits;     /* WC_OPT_OVERFLOW_BITS tables (byte w = window w), else NULL */
   uint64_t seed;
   uint64_t capacity;           /* windows * window_width */
   uint32_t windows;            /* p */
@@ -377,8 +379,8 @@ wc_status wc_table_device_view(const wc_table* t, wc_device_view* h_out);
  * Synchronises stream.  Used by the slot-dump invariant checks of the tests. */
 wc_status wc_table_dump_slots(const wc_table* t, void* h_out, uint64_t bytes, void* stream);
 
-/* Copy a table's overflow bits (WC_OPT_OVERFLOW_BITS): ceil(windows / 32) uint32 words, bit
- * w % 32 of word w / 32 = window w, to h_out (`words` >= that).  WC_ERR_UNSUPPORTED for a
+/* Copy a table's overflow bits (WC_OPT_OVERFLOW_BITS): ceil(windows / 4) uint32 words, byte
+ * w % 4 (little-endian) of word w / 4 = window w's eight bits, to h_out (`words` >= that).  WC_ERR_UNSUPPORTED for a
  * table without them.  Synchronises stream. */
 wc_status wc_table_dump_overflow_bits(const wc_table* t, uint32_t* h_out, uint64_t words, void* stream);
 

@@ -51,6 +51,23 @@ __device__ __forceinline__ void probe_init(uint64_t key, uint64_t seed, uint32_t
   step = 1u + __umulhi(static_cast<uint32_t>(h), p - 1u);
 }
 
+// The same, plus the key's overflow tag (WC_OPT_OVERFLOW_BITS): the low three bits of the
+// hash.  w_0 comes from the high half and the step from the top bits of the low half, so
+// the tag is close to independent of both.
+__device__ __forceinline__ void probe_init(uint64_t key, uint64_t seed, uint32_t p, uint32_t& w, uint32_t& step,
+                                           uint32_t& tag) {
+  const uint64_t h = fmix64(key ^ seed);
+  w = __umulhi(static_cast<uint32_t>(h >> 32), p);
+  step = 1u + __umulhi(static_cast<uint32_t>(h), p - 1u);
+  tag = static_cast<uint32_t>(h) & 7u;
+}
+
+// Overflow bits (WC_OPT_OVERFLOW_BITS): eight per window, byte w of the array (four windows
+// per 32-bit word, little-endian) for window w.  An insert of a key with tag g that walks
+// past window w sets bit g of byte w; a lookup of such a key may stop at a window without
+// the key, without an empty slot and with bit g clear.  Position of that bit in its word:
+__device__ __forceinline__ uint32_t overflow_shift(uint32_t w, uint32_t tag) { return ((w & 3u) << 3) | tag; }
+
 // (w + step) mod p for w, step < p < 2^32 (the u32 sum may wrap).
 __device__ __forceinline__ uint32_t probe_next(uint32_t w, uint32_t step, uint32_t p) {
   uint32_t x = w + step;
@@ -170,16 +187,16 @@ struct Window {
   }
 };
 
-__device__ __forceinline__ bool overflow_clear(const wc_device_view& t, uint32_t w) {
-  return t.overflow_bits != nullptr && !((__ldcg(t.overflow_bits + (w >> 5)) >> (w & 31u)) & 1u);
+__device__ __forceinline__ bool overflow_clear(const wc_device_view& t, uint32_t w, uint32_t tag) {
+  return t.overflow_bits != nullptr && !((__ldcg(t.overflow_bits + (w >> 2)) >> overflow_shift(w, tag)) & 1u);
 }
 
 template <class K, int W>
 __device__ uint32_t insert_w(const wc_device_view& t, K key, typename Slots<K>::V value) {
   using S = Slots<K>;
   using Word = typename S::Word;
-  uint32_t w0, step;
-  probe_init(static_cast<uint64_t>(key), t.seed, t.windows, w0, step);
+  uint32_t w0, step, tag;
+  probe_init(static_cast<uint64_t>(key), t.seed, t.windows, w0, step, tag);
   uint32_t w = w0, j = 0;
   bool have_t = false;  // first tombstone of the walk, claimed if the key turns out absent
   uint64_t t_slot = 0;
@@ -230,7 +247,7 @@ __device__ uint32_t insert_w(const wc_device_view& t, K key, typename Slots<K>::
       for (int q = 1; q < W; ++q)
         if (q == free_q) t_word = win.slot(q);
     }
-    if (t.overflow_bits) atomicOr(t.overflow_bits + (w >> 5), 1u << (w & 31u));
+    if (t.overflow_bits) atomicOr(t.overflow_bits + (w >> 2), 1u << overflow_shift(w, tag));
     w = probe_next(w, step, t.windows);
     ++j;
   }
@@ -241,8 +258,8 @@ __device__ uint32_t insert_w(const wc_device_view& t, K key, typename Slots<K>::
 template <class K, int W>
 __device__ bool retrieve_w(const wc_device_view& t, K key, typename Slots<K>::V& value) {
   using S = Slots<K>;
-  uint32_t w, step;
-  probe_init(static_cast<uint64_t>(key), t.seed, t.windows, w, step);
+  uint32_t w, step, tag;
+  probe_init(static_cast<uint64_t>(key), t.seed, t.windows, w, step, tag);
   for (uint32_t j = 0; j < t.windows; ++j) {
     Window<K, W> win;
     win.load(t.slots, w);
@@ -257,7 +274,7 @@ __device__ bool retrieve_w(const wc_device_view& t, K key, typename Slots<K>::V&
       empty |= S::key(s) == K(0);
     }
     if (hit) return true;
-    if (empty || overflow_clear(t, w)) return false;
+    if (empty || overflow_clear(t, w, tag)) return false;
     w = probe_next(w, step, t.windows);
   }
   return false;
@@ -266,8 +283,8 @@ __device__ bool retrieve_w(const wc_device_view& t, K key, typename Slots<K>::V&
 template <class K, int W>
 __device__ bool erase_w(const wc_device_view& t, K key) {
   using S = Slots<K>;
-  uint32_t w, step;
-  probe_init(static_cast<uint64_t>(key), t.seed, t.windows, w, step);
+  uint32_t w, step, tag;
+  probe_init(static_cast<uint64_t>(key), t.seed, t.windows, w, step, tag);
   for (uint32_t j = 0; j < t.windows; ++j) {
     Window<K, W> win;
     win.load(t.slots, w);
@@ -284,7 +301,7 @@ __device__ bool erase_w(const wc_device_view& t, K key) {
       }
       empty |= S::key(s) == K(0);
     }
-    if (empty || overflow_clear(t, w)) return false;
+    if (empty || overflow_clear(t, w, tag)) return false;
     w = probe_next(w, step, t.windows);
   }
   return false;
@@ -328,7 +345,8 @@ __device__ uint32_t insert(const wc_device_view& t, K key, typename Slots<K>::V 
 }
 
 // Retrieve (Sec. IV-B4): the key's value, or false when absent (the walk stops at a window
-// holding an empty slot -- or, with overflow bits, a window whose bit is clear).
+// holding an empty slot -- or, with overflow bits, a window whose bit for the key's tag is
+// clear).
 template <class K>
 __device__ bool retrieve(const wc_device_view& t, K key, typename Slots<K>::V& value) {
   if (is_sentinel(key)) return false;

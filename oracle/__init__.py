@@ -71,6 +71,8 @@ def _load():
         lib.oracle_counts_size.argtypes = [vp]
         lib.oracle_check_slots.restype = ctypes.c_int
         lib.oracle_check_slots.argtypes = [vp, u64, u32, u32, u32, u64, ctypes.c_int, vp, vp, vp, vp]
+        lib.oracle_overflow_bits_of.restype = ctypes.c_int
+        lib.oracle_overflow_bits_of.argtypes = [vp, u64, u32, u32, u32, u64, vp]
         lib.oracle_bloom_create.restype = vp
         lib.oracle_bloom_create.argtypes = [ctypes.c_int, u64, ctypes.c_int, u64]
         lib.oracle_bloom_destroy.argtypes = [vp]
@@ -266,8 +268,9 @@ def check_slots(dump: np.ndarray, p: int, W: int, slot_bytes: int, seed: int, un
     """Slot-dump invariant check of a table's slot array (host bytes, p * W slots):
     live slots, duplicate keys (when keys must be unique) and live keys that sit behind
     a window holding an empty slot on their own probing sequence -- or, when the table's
-    overflow bits are given (uint32 words, bit w = window w), behind a window whose bit is
-    clear (see oracle.cpp).  key_bytes defaults to 4 for 4- and 8-byte slots (packed 4+4-byte
+    overflow bits are given (one byte per window, as bytes or as the little-endian uint32
+    words the library dumps), behind a window whose bit for the key's tag is clear (see
+    oracle.cpp).  key_bytes defaults to 4 for 4- and 8-byte slots (packed 4+4-byte
     pairs) and 8 for 16-byte slots."""
     buf = np.ascontiguousarray(dump).view(np.uint8)
     if buf.size < p * W * slot_bytes:
@@ -275,9 +278,9 @@ def check_slots(dump: np.ndarray, p: int, W: int, slot_bytes: int, seed: int, un
     out = np.zeros(3, dtype=np.uint64)
     ovf = None
     if overflow_bits is not None:
-        ovf = np.ascontiguousarray(overflow_bits).view(np.uint32)
-        if ovf.size < (p + 31) // 32:
-            raise ValueError("overflow bits hold %d words, need %d" % (ovf.size, (p + 31) // 32))
+        ovf = np.ascontiguousarray(overflow_bits).view(np.uint8)
+        if ovf.size < p:
+            raise ValueError("overflow bits hold %d bytes, need %d" % (ovf.size, p))
     if key_bytes is None:
         key_bytes = 8 if slot_bytes == 16 else 4
     rc = _load().oracle_check_slots(_ptr(buf), p, W, slot_bytes, key_bytes, seed & (2 ** 64 - 1), int(unique_keys),
@@ -287,3 +290,19 @@ def check_slots(dump: np.ndarray, p: int, W: int, slot_bytes: int, seed: int, un
     if rc != 0:
         raise ValueError("bad table geometry")
     return {"live": int(out[0]), "dups": int(out[1]), "unreachable": int(out[2])}
+
+
+def overflow_bits_of(dump: np.ndarray, p: int, W: int, slot_bytes: int, seed: int,
+                     key_bytes: int | None = None) -> np.ndarray:
+    """The overflow bits (one byte per window) that a table filled by inserts alone holds:
+    for every live key, the bit of its tag in each window its sequence passes before the
+    key's own window (see oracle.cpp)."""
+    buf = np.ascontiguousarray(dump).view(np.uint8)
+    if buf.size < p * W * slot_bytes:
+        raise ValueError("dump holds %d bytes, need %d" % (buf.size, p * W * slot_bytes))
+    if key_bytes is None:
+        key_bytes = 8 if slot_bytes == 16 else 4
+    out = np.zeros(p, dtype=np.uint8)
+    if _load().oracle_overflow_bits_of(_ptr(buf), p, W, slot_bytes, key_bytes, seed & (2 ** 64 - 1), _ptr(out)) != 0:
+        raise ValueError("bad table geometry")
+    return out

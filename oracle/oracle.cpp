@@ -356,9 +356,10 @@ uint64_t oracle_counts_size(void* p) { return static_cast<Counts*>(p)->m.size();
 //     only moves empty -> key -> tombstone -> key, so nothing may sit behind an empty
 //     window of its own sequence);
 //   * uniqueness (single-value tables and key stores, Sec. IV: each key occurs once);
-//   * with the table's overflow bits (one per window, optional): every window a live key's
-//     sequence passes before the key's own window has its bit set, since lookups stop at a
-//     window without the key, without an empty slot and with a clear bit.
+//   * with the table's overflow bits (optional; eight per window, one byte per window, bit
+//     g = the key's tag, the low three bits of h below): every window a live key's sequence
+//     passes before the key's own window has the bit of the key's tag set, since lookups
+//     stop at a window without the key, without an empty slot and with that bit clear.
 // The probing sequence is the table's definition restated here: h = fmix64(key ^ seed)
 // (MurmurHash3's 64-bit finalizer), w_0 = floor(hi32(h) * p / 2^32),
 // step = 1 + floor(lo32(h) * (p - 1) / 2^32), w_{j+1} = (w_j + step) mod p; windows are
@@ -390,7 +391,7 @@ uint64_t chk_key(const unsigned char* slots, uint64_t i, uint32_t slot_bytes, ui
 }  // namespace
 
 extern "C" int oracle_check_slots(const void* dump, uint64_t p, uint32_t W, uint32_t slot_bytes, uint32_t key_bytes,
-                                  uint64_t seed, int unique_keys, const uint32_t* ovf_or_null, uint64_t* out_live,
+                                  uint64_t seed, int unique_keys, const uint8_t* ovf_or_null, uint64_t* out_live,
                                   uint64_t* out_dups, uint64_t* out_unreachable) {
   const bool shape_ok = (key_bytes == 4 && (slot_bytes == 4 || slot_bytes == 8)) ||
                         (key_bytes == 8 && (slot_bytes == 8 || slot_bytes == 16));
@@ -411,12 +412,13 @@ extern "C" int oracle_check_slots(const void* dump, uint64_t p, uint32_t W, uint
     const uint64_t h = chk_fmix64(k ^ seed);
     uint64_t w = ((h >> 32) * p) >> 32;
     const uint64_t step = 1 + (((h & 0xffffffffull) * (p - 1)) >> 32);
+    const unsigned tag = static_cast<unsigned>(h & 7u);
     const uint64_t home = i / W;
     bool ok = false;
     for (uint64_t j = 0; j < p; ++j) {
       if (w == home) { ok = true; break; }
       if (has_empty[w]) break;
-      if (ovf_or_null != nullptr && !((ovf_or_null[w >> 5] >> (w & 31)) & 1u)) break;
+      if (ovf_or_null != nullptr && !((ovf_or_null[w] >> tag) & 1u)) break;
       w = (w + step) % p;
     }
     if (!ok) ++unreachable;
@@ -424,6 +426,38 @@ extern "C" int oracle_check_slots(const void* dump, uint64_t p, uint32_t W, uint
   if (out_live) *out_live = live;
   if (out_dups) *out_dups = dups;
   if (out_unreachable) *out_unreachable = unreachable;
+  return 0;
+}
+
+// The overflow bits a table filled by inserts alone must hold: an insert sets bit tag(k) of
+// every window it walks past, and walks past exactly the windows of its sequence before the
+// one it is stored in, so the bits are the union over live keys of those windows' tag bits.
+// out_bits: p bytes, one per window.  Keys that no walk reaches are skipped.
+extern "C" int oracle_overflow_bits_of(const void* dump, uint64_t p, uint32_t W, uint32_t slot_bytes,
+                                       uint32_t key_bytes, uint64_t seed, uint8_t* out_bits) {
+  const bool shape_ok = (key_bytes == 4 && (slot_bytes == 4 || slot_bytes == 8)) ||
+                        (key_bytes == 8 && (slot_bytes == 8 || slot_bytes == 16));
+  if (dump == nullptr || out_bits == nullptr || p < 2 || W == 0 || !shape_ok) return -1;
+  const unsigned char* s = static_cast<const unsigned char*>(dump);
+  const uint64_t tomb = key_bytes == 4 ? 0xffffffffull : ~0ull;
+  std::memset(out_bits, 0, p);
+  std::vector<uint64_t> passed;
+  for (uint64_t i = 0; i < p * W; ++i) {
+    const uint64_t k = chk_key(s, i, slot_bytes, key_bytes);
+    if (k == 0 || k == tomb) continue;
+    const uint64_t h = chk_fmix64(k ^ seed);
+    uint64_t w = ((h >> 32) * p) >> 32;
+    const uint64_t step = 1 + (((h & 0xffffffffull) * (p - 1)) >> 32);
+    passed.clear();
+    bool ok = false;
+    for (uint64_t j = 0; j < p; ++j) {
+      if (w == i / W) { ok = true; break; }
+      passed.push_back(w);
+      w = (w + step) % p;
+    }
+    if (ok)
+      for (uint64_t v : passed) out_bits[v] |= static_cast<uint8_t>(1u << (h & 7u));
+  }
   return 0;
 }
 

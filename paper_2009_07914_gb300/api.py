@@ -243,9 +243,10 @@ def wc_table_device_view(t: int) -> B.WcDeviceView:
 
 
 def wc_table_dump_overflow_bits(t: int, stream=None) -> np.ndarray:
-    """Host copy of a single-value table's overflow bits (uint32 words, bit w = window w)."""
+    """Host copy of a table's overflow bits: uint32 words holding one byte per window
+    (window w in byte w, little-endian), bit g of a byte = keys of tag g walked past."""
     info = wc_table_get_info(t)
-    out = np.empty((info["windows"] + 31) // 32, dtype=np.uint32)
+    out = np.empty((info["windows"] + 3) // 4, dtype=np.uint32)
     check(lib().wc_table_dump_overflow_bits(t, out.ctypes.data, out.size, stream_handle(stream)),
           "wc_table_dump_overflow_bits")
     return out

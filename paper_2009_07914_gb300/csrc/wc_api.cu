@@ -422,7 +422,7 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
                   (cfg->options & WC_OPT_OVERFLOW_BITS);
   const uint64_t off_meta = align_up(t->table_bytes, kAlign);
   const uint64_t off_ovf = off_meta + kAlign;
-  const uint64_t ovf_bytes = sv ? align_up((p + 31) / 32 * 4, kAlign) : 0;
+  const uint64_t ovf_bytes = sv ? align_up((p + 3) / 4 * 4, kAlign) : 0;  // one byte per window
   const uint64_t off_pending = off_ovf + ovf_bytes;
   const uint64_t pending_bytes = mv ? align_up(cap * 4, kAlign) : 0;
   const uint64_t off_base = off_pending + pending_bytes;

@@ -81,7 +81,7 @@ wc_status wc_table_dump_slots(const wc_table* t, void* h_out, uint64_t bytes, vo
 wc_status wc_table_dump_overflow_bits(const wc_table* t, uint32_t* h_out, uint64_t words, void* stream) {
   if (t == nullptr || h_out == nullptr) return WC_ERR_INVALID_ARG;
   if (t->d_ovf == nullptr) return WC_ERR_UNSUPPORTED;
-  const uint64_t need = (t->windows + 31) / 32;
+  const uint64_t need = (t->windows + 3) / 4;
   if (words < need) return WC_ERR_INVALID_ARG;
   DevGuard g(t->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -18,7 +18,7 @@ struct TableDesc {
   uint32_t* status;                  // device status word (WC_FLAG_* bits)
   unsigned long long* size;          // SV: live keys; MV: stored pairs
   unsigned long long* nkeys;         // MV: distinct live keys
-  uint32_t* ovf;                     // SV: one overflow bit per window (see wc_device.cuh); else null
+  uint32_t* ovf;                     // SV: eight overflow bits per window (see wc_device.cuh); else null
   void* vals;                        // SoA tables: the value array (slot i's value); else null
   uint32_t p;                        // windows (prime)
   uint32_t W;                        // slots per window
@@ -73,7 +73,7 @@ struct wc_table {
   unsigned long long* d_size;
   unsigned long long* d_nkeys;
   unsigned long long* d_cursor;
-  uint32_t* d_ovf;       // SV: overflow bits, one per window
+  uint32_t* d_ovf;       // SV: overflow bits, one byte per window
   void* d_vals;          // SoA single-value tables: value array (capacity entries)
   uint32_t* d_pending;   // MV: capacity entries
   uint32_t* d_base;      // MV with bucket growth: capacity entries

@@ -171,7 +171,7 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
   bool act = false;
   uint64_t pos = 0;
   Key k = 0;
-  uint32_t w = 0, step = 0, j = 0;
+  uint32_t w = 0, step = 0, j = 0, tag = 0;
   Feed<KIn> fk;
   while (true) {
     const bool more = src.ensure();
@@ -192,7 +192,7 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
       } else {
         act = true;
         j = 0;
-        probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step);
+        probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step, tag);
       }
     }
     if (__ballot_sync(kFull, act) == 0) {
@@ -221,7 +221,7 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
       if (bm) {
         if (ln.r == 0) emit(pos, true, hit, hidx);
         act = false;
-      } else if (be || !ovf_bit(fw, w) || ++j >= t.p) {
+      } else if (be || !ovf_bit(fw, w, tag) || ++j >= t.p) {
         if (ln.r == 0) emit(pos, false, hit, hidx);
         act = false;
       } else {
@@ -335,7 +335,7 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
   uint64_t pos = 0;
   Key k = 0;
   Val v = 0;
-  uint32_t w = 0, step = 0, j = 0;
+  uint32_t w = 0, step = 0, j = 0, tag = 0;
   bool have_t = false;     // a tombstone earlier on the sequence is remembered
   uint64_t t_slot = 0;     // its slot index
   Slot t_word{};           // and the word read there
@@ -369,7 +369,7 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
         act = true;
         j = 0;
         have_t = false;
-        probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step);
+        probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step, tag);
       }
     }
     if (__ballot_sync(kFull, act) == 0) {
@@ -441,7 +441,7 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
           // the remembered tombstone was taken: probe again from the start
           have_t = false;
           j = 0;
-          probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step);
+          probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step, tag);
         } else if (bc == 0) {
           flags |= kFlagProbeLimit;  // every window visited, nothing to claim
           act = false;
@@ -453,7 +453,7 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
           t_slot = nt_slot;
           t_word = nt_word;
         }
-        if (t.ovf != nullptr && ln.r == 0) ovf_mark(t.ovf, w);  // walking past a window without an empty slot
+        if (t.ovf != nullptr && ln.r == 0) ovf_mark(t.ovf, w, tag);  // walking past a window without an empty slot
         ++j;
         w = probe_next(w, step, t.p);
       }
@@ -489,7 +489,7 @@ __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __
   Slot* slots = static_cast<Slot*>(t.slots);
   bool act = false;
   Key k = 0;
-  uint32_t w = 0, step = 0, j = 0;
+  uint32_t w = 0, step = 0, j = 0, tag = 0;
   Feed<KIn> fk;
   while (true) {
     const bool more = src.ensure();
@@ -508,7 +508,7 @@ __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __
       } else {
         act = true;
         j = 0;
-        probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step);
+        probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step, tag);
       }
     }
     if (__ballot_sync(kFull, act) == 0) {
@@ -541,7 +541,7 @@ __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __
           act = false;
         }
         // else: another erase of the same key won; read the window again
-      } else if (be || !ovf_bit(fw, w) || ++j >= t.p) {
+      } else if (be || !ovf_bit(fw, w, tag) || ++j >= t.p) {
         act = false;  // absent: nothing to erase
       } else {
         w = probe_next(w, step, t.p);

@@ -71,6 +71,12 @@ def test_counting_region_split_unit_and_weighted(wc, kb):
     o = oracle.Counting(kb)
     t.insert(keys)
     o.insert(keys)
+    # region-split inserts set exactly the overflow bits the stored keys' walks imply
+    info = t.info
+    bits = wc.api.wc_table_dump_overflow_bits(t.handle).view(np.uint8)[:info["windows"]]
+    expect = oracle.overflow_bits_of(wc.api.wc_table_dump_slots(t.handle), info["windows"], info["window_width"],
+                                     info["slot_bytes"], 0x5EED_C0DE, key_bytes=kb)
+    np.testing.assert_array_equal(bits, expect)
     w = wc_inputs.uniform_u32(6, keys.size) if kb == 4 else wc_inputs.uniform_u64(6, keys.size)
     t.insert(keys, w)
     o.insert(keys, w)

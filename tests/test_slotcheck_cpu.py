@@ -24,6 +24,11 @@ def fmix64(k: int) -> int:
     return k
 
 
+def tag(key: int, seed: int) -> int:
+    """Overflow tag: the low three bits of the hash."""
+    return fmix64((key ^ seed) & M64) & 7
+
+
 def windows(key: int, seed: int, p: int):
     h = fmix64((key ^ seed) & M64)
     w = ((h >> 32) * p) >> 32
@@ -41,7 +46,7 @@ class Table:
         self.tomb = 0xFFFFFFFF if slot_bytes == 8 else M64
         self.keys = [0] * (p * W)
         self.where = {}
-        self.ovf = np.zeros((p + 31) // 32, dtype=np.uint32)  # overflow bit per window
+        self.ovf = np.zeros(p, dtype=np.uint8)  # eight overflow bits per window
 
     def insert(self, k):
         for j, w in enumerate(windows(k, self.seed, self.p)):
@@ -50,7 +55,7 @@ class Table:
                     self.keys[w * self.W + q] = k
                     self.where[k] = (w * self.W + q, j)
                     return True
-            self.ovf[w >> 5] |= np.uint32(1 << (w & 31))  # walked past a window without an empty slot
+            self.ovf[w] |= np.uint8(1 << tag(k, self.seed))  # walked past a window without an empty slot
         return False
 
     def dump(self) -> np.ndarray:
@@ -128,18 +133,38 @@ def test_geometry_is_validated():
         oracle.check_slots(np.zeros(11 * 8 * 12, np.uint8), 11, 8, 12, 0, True)
 
 
+def passed(t, k):
+    """Windows key k's sequence passes before its own window."""
+    slot, j = t.where[k]
+    return [w for _, w in zip(range(j), windows(k, t.seed, t.p))]
+
+
 @pytest.mark.parametrize("sb", [8, 16])
 def test_overflow_bits(sb):
     """With overflow bits, a key is reachable only if every window its sequence passes
-    before its own has the bit set; the brute-force insert sets exactly those bits."""
+    before its own has the bit of the key's tag set; the brute-force insert sets exactly
+    those bits.  Clearing one bit of a window makes unreachable exactly the keys of that
+    tag that passed the window -- keys of the other seven tags are unaffected."""
     t = filled(sb, n=700)
     assert t.check(bits=True) == t.check() == {"live": len(t.where), "dups": 0, "unreachable": 0}
     k, (slot, j) = next((k, v) for k, v in t.where.items() if v[1] >= 1)
     first = next(windows(k, t.seed, t.p))
-    t.ovf[first >> 5] &= np.uint32(~(1 << (first & 31)) & 0xFFFFFFFF)
-    assert t.check()["unreachable"] == 0  # without the bits nothing changed
-    assert t.check(bits=True)["unreachable"] >= 1
-    assert oracle.check_slots(np.zeros(101 * 8 * sb, np.uint8), 101, 8, sb, 1, True, np.zeros(4, np.uint32))[
+    g = tag(k, t.seed)
+    for other in range(8):
+        saved = t.ovf.copy()
+        t.ovf[first] &= np.uint8(~(1 << other) & 0xFF)
+        expect = sum(1 for q in t.where if tag(q, t.seed) == other and first in passed(t, q))
+        assert expect >= (1 if other == g else 0)
+        assert t.check()["unreachable"] == 0  # without the bits nothing changed
+        assert t.check(bits=True)["unreachable"] == expect
+        t.ovf = saved
+    # as little-endian uint32 words (the library's dump format) the result is the same
+    words = np.zeros((t.p + 3) // 4 * 4, np.uint8)
+    words[:t.p] = t.ovf
+    assert oracle.check_slots(t.dump(), t.p, t.W, t.sb, t.seed, True, words.view(np.uint32))["unreachable"] == 0
+    assert oracle.check_slots(np.zeros(101 * 8 * sb, np.uint8), 101, 8, sb, 1, True, np.zeros(101, np.uint8))[
         "unreachable"] == 0
-    with pytest.raises(ValueError):  # too few words for the window count
-        oracle.check_slots(t.dump(), t.p, t.W, t.sb, t.seed, True, np.zeros(1, np.uint32))
+    # the bits are exactly those the stored keys' walks imply
+    np.testing.assert_array_equal(oracle.overflow_bits_of(t.dump(), t.p, t.W, t.sb, t.seed), t.ovf)
+    with pytest.raises(ValueError):  # too few bytes for the window count
+        oracle.check_slots(t.dump(), t.p, t.W, t.sb, t.seed, True, np.zeros(25, np.uint32))

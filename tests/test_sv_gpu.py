@@ -275,6 +275,18 @@ def test_blocked_retrieve_scheme_parity(wc, kb, W, G):
         check_retrieve(t, o, q[:m])
 
 
+def assert_exact_overflow_bits(wc, t, seed, kb):
+    """After inserts alone, the table's overflow bits are exactly the tag bits of the
+    windows each stored key walked past (derived from the slot dump by the oracle)."""
+    info = t.info
+    p = info["windows"]
+    bits = wc.wc_table_dump_overflow_bits(t.handle).view(np.uint8)[:p]
+    expect = oracle.overflow_bits_of(wc.api.wc_table_dump_slots(t.handle), p, info["window_width"],
+                                     info["slot_bytes"], seed, key_bytes=kb)
+    np.testing.assert_array_equal(bits, expect)
+    assert np.count_nonzero(bits) > p // 10  # high load: many windows were walked past
+
+
 @pytest.mark.parametrize("kb,W,G", [(4, 4, 1), (4, 8, 2), (4, 16, 4), (4, 32, 8), (8, 2, 1), (8, 4, 2), (8, 8, 4),
                                     (8, 16, 8)])
 def test_overflow_bits_parity(wc, kb, W, G):
@@ -295,6 +307,7 @@ def test_overflow_bits_parity(wc, kb, W, G):
     o = oracle.SingleValue(kb, kb)
     assert t.insert(keys, vals) == o.insert(keys, vals) == 0
     check_retrieve(t, o, q)
+    assert_exact_overflow_bits(wc, t, 0x1234, kb)
     drop = keys[: n // 2]
     assert t.erase(drop) == o.erase(drop)
     assert t.erase(drop[:1000]) == o.erase(drop[:1000])  # absent now: stops early, no-op
