@@ -359,16 +359,18 @@ def run_wc(args, rank, world, local_rank):
         torch.cuda.synchronize()
         assert np.array_equal(hf.numpy(), found.cpu().numpy())
         assert np.array_equal(ho.numpy()[hf.numpy() == 1], out.cpu().numpy()[hf.numpy() == 1])
-        k = max(1, args.steps // 2)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(s)
-        for _ in range(k):
+        k = args.steps
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
+        marks[0].record(s)
+        for i in range(k):
             e2e_step()
-        b.record(s)
+            marks[i + 1].record(s)
         torch.cuda.synchronize()
-        e_ms = a.elapsed_time(b) / k
+        e_ms = marks[0].elapsed_time(marks[k]) / k
+        per = sorted(marks[i].elapsed_time(marks[i + 1]) for i in range(k))
         e2e = {"value": world * 2 * n / (e_ms * 1e-3) / 1e9, "unit": "G ops/s",
                "h2d_bytes_per_step": n * 4 * 3, "d2h_bytes_per_step": n * 5, "ms_per_step": e_ms,
+               "step_ms_min_median_max": [per[0], per[k // 2], per[-1]],
                "calls": "wc_insert_host + wc_retrieve_host from pinned buffers (chunked copies on the "
                         "table's copy streams, overlapping the kernels)"}
 

@@ -265,10 +265,11 @@ wc_status wc_insert_noalloc(wc_table* t, const void* d_keys, const void* d_value
 
 /* The same inserts from HOST buffers (pinned memory for full speed; pageable memory works,
  * with copies synchronous to the host): the batch moves to the device in chunks of up to
- * 2^25 pairs through two device staging buffers the table keeps (allocated on first use),
- * each chunk's copy on the table's own copy stream overlapping the insert of the previous
- * chunk on `stream`.  Asynchronous: the host buffers must stay valid and unchanged until
- * `stream` has passed this call.  Values may be NULL where wc_insert allows it. */
+ * 2^25 pairs (the first of up to 2^23) through three device staging buffers
+ * the table keeps (allocated on first use), each chunk's copy on the table's own copy
+ * stream overlapping the inserts of the chunks before it on `stream`.  Asynchronous: the
+ * host buffers must stay valid and unchanged until `stream` has passed this call.  Values
+ * may be NULL where wc_insert allows it. */
 wc_status wc_insert_host(wc_table* t, const void* h_keys, const void* h_values, uint64_t n, void* stream);
 
 /* Single-value retrieve (Sec. IV-B4; counting tables: the counts): d_values_out[i] = value

@@ -58,8 +58,9 @@ def test_host_calls_match_oracle(env, kb, pin):
 
 
 def test_multi_chunk_batches(env):
-    """2^25 + 4097 distinct pairs (two insert chunks, the second ragged) and 2^24 + 12345
-    queries (three retrieve chunks): every present key returns its own value."""
+    """2^25 + 4097 distinct pairs (two insert chunks: 2^23, then the ragged rest) and
+    2^25 + 12345 queries (five retrieve chunks, around the ring of three staging buffers):
+    every present key returns its own value."""
     wc, torch = env
     n = (1 << 25) + 4097
     keys = wc_inputs.distinct_u32(0x4060, n)
@@ -69,7 +70,7 @@ def test_multi_chunk_batches(env):
     wc.api.wc_insert_host(t.handle, hk, hv)
     torch.cuda.synchronize()
     assert t.size() == n and t.status(clear=True) == 0
-    m = (1 << 24) + 12345
+    m = (1 << 25) + 12345
     sel = wc_inputs.uniform_u64(0x4062, m) % np.uint64(n)
     q = keys[sel]
     q[::5] = 0xFFFFFFFF  # invalid key: not found
