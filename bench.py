@@ -661,7 +661,7 @@ def run_device_api(args, dev):
     sink = torch.zeros(1, dtype=torch.int64, device=dev)
     want = int(idx[valid].astype(np.uint64).sum(dtype=np.uint64) & np.uint64(0x7FFFFFFFFFFFFFFF))
     h = api.wc_table_create(0, 4, 4, int(np.ceil(n / args.alpha)), args.window, 0, 0x5EEDC0DE, dev.index,
-                            options=wc.WC_OPT_OVERFLOW_BITS)
+                            options=0 if args.no_overflow_bits else wc.WC_OPT_OVERFLOW_BITS)
     s = torch.cuda.current_stream()
     ev = []
     with ClockSampler(dev.index) as clk:
@@ -682,7 +682,8 @@ def run_device_api(args, dev):
     fi, fl, bi, br = (statistics.median(e[j] for e in ev) for j in range(4))
     _common(args, "device_api_u32_n2^%d_alpha%.2f" % (args.log2n, args.alpha),
             "G ops/s (device-API fused insert + lookup)", 2 * n / ((fi + fl) * 1e-3) / 1e9, "G ops/s", fi + fl, "u32",
-            {"n": n, "keys": "produced in the kernel: (i * 2654435761 mod 2^32) xor seed", "overflow_bits": True,
+            {"n": n, "keys": "produced in the kernel: (i * 2654435761 mod 2^32) xor seed",
+             "overflow_bits": not args.no_overflow_bits,
              "l2": "no flush: table 1.19 GB"}, clk, 2 * args.steps,
             {"fused_insert_gops": n / fi / 1e6, "fused_lookup_gops": n / fl / 1e6,
              "bulk_insert_gops": n / bi / 1e6, "bulk_retrieve_gops": n / br / 1e6,
