@@ -195,10 +195,17 @@ typedef struct {
  * WC_SCHEME_BLOCKED: the batch is first split by table region (the multi-split of
  * Sec. IV-E applied to regions of one table) and then probed region by region, so the
  * active part of the table stays in L2; needs scratch of n * (key + value) bytes, which
- * the table allocates on first use (stream-ordered) and keeps.  Inserts of single-value and
- * open-addressing multi-value tables only.  WC_SCHEME_AUTO picks BLOCKED for those inserts
- * when the batch holds at least 2^18 pairs and the table is larger than 64 MiB. */
-enum { WC_SCHEME_AUTO = 0, WC_SCHEME_DIRECT = 1, WC_SCHEME_BLOCKED = 2 };
+ * the table allocates on first use (stream-ordered) and keeps.  Inserts of single-value,
+ * counting, hash-set and open-addressing multi-value tables; retrieves of single-value and
+ * counting tables (the results are split back into input order).  WC_SCHEME_AUTO picks
+ * BLOCKED for those inserts when the batch holds at least 2^18 pairs and the table is
+ * larger than 64 MiB, DIRECT otherwise.
+ * WC_SCHEME_DEDUP (lookups of single-value, counting and hash-set tables: wc_retrieve,
+ * wc_contains): direct probing, but equal keys among each 32 consecutive queries of a
+ * warp are found with one warp vote (__match_any_sync) and probed once, the result written
+ * to each of their positions.  For skewed query streams, where the hot keys repeat inside
+ * a warp's queries; on distinct queries it only adds the vote. */
+enum { WC_SCHEME_AUTO = 0, WC_SCHEME_DIRECT = 1, WC_SCHEME_BLOCKED = 2, WC_SCHEME_DEDUP = 3 };
 
 enum { WC_OP_INSERT = 0, WC_OP_RETRIEVE = 1, WC_OP_ERASE = 2, WC_OP_COUNT = 3, WC_OP__N = 4 };
 

@@ -42,6 +42,7 @@ WC_OPT_SOA = 2
 WC_SCHEME_AUTO = 0
 WC_SCHEME_DIRECT = 1
 WC_SCHEME_BLOCKED = 2
+WC_SCHEME_DEDUP = 3
 
 WC_OP_INSERT = 0
 WC_OP_RETRIEVE = 1

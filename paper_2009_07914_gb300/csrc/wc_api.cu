@@ -543,12 +543,16 @@ wc_status wc_table_set_launch(wc_table* t, int32_t op, const wc_launch* launch) 
   const int b = launch->block_threads;
   if (b < 32 || b > 256 || b % 32 != 0 || launch->blocks_per_sm < 0 || launch->blocks_per_sm > 64)
     return WC_ERR_INVALID_ARG;
-  if (launch->scheme < WC_SCHEME_AUTO || launch->scheme > WC_SCHEME_BLOCKED || launch->region_mib < 0 ||
+  if (launch->scheme < WC_SCHEME_AUTO || launch->scheme > WC_SCHEME_DEDUP || launch->region_mib < 0 ||
       launch->region_mib > 4096)
     return WC_ERR_INVALID_ARG;
   if (launch->scheme == WC_SCHEME_BLOCKED &&
       !((op == WC_OP_INSERT && t->cfg.kind != WC_MULTI_VALUE) ||
         (op == WC_OP_RETRIEVE && (t->cfg.kind == WC_SINGLE_VALUE || t->cfg.kind == WC_COUNTING))))
+    return WC_ERR_UNSUPPORTED;
+  if (launch->scheme == WC_SCHEME_DEDUP &&
+      !(op == WC_OP_RETRIEVE && (t->cfg.kind == WC_SINGLE_VALUE || t->cfg.kind == WC_COUNTING ||
+                                 t->cfg.kind == WC_HASH_SET)))
     return WC_ERR_UNSUPPORTED;
   if (!shape_ok(t, op, launch->group_size)) return WC_ERR_INVALID_ARG;
   t->launch[op] = *launch;

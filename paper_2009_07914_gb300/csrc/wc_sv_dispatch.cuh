@@ -90,9 +90,10 @@ cudaError_t sv_run(const wc_table* t, int op, const void* keys, const void* vals
   const TableDesc d = desc_of(t);
   const Key* k = static_cast<const Key*>(keys);
   if (op == WC_OP_RETRIEVE) {
-    if (scheme_for(t, op, n) == WC_SCHEME_BLOCKED && n < (1ull << 31) && out != nullptr)
+    const int scheme = scheme_for(t, op, n);
+    if (scheme == WC_SCHEME_BLOCKED && n < (1ull << 31) && out != nullptr)
       return sv_retrieve_blocked<L, G, S>(t, lc, k, n, static_cast<Val*>(out), found, s);
-    auto kern = k_sv_retrieve<L, G, S>;
+    auto kern = scheme == WC_SCHEME_DEDUP ? k_sv_retrieve_dedup<L, G, S> : k_sv_retrieve<L, G, S>;
     const int bps = lc.blocks_per_sm > 0 ? lc.blocks_per_sm : occupancy(kern, block);
     const EngineGrid g = engine_grid(n, G, block, bps, t->sm_count);
     return launch_k(t, kern, g.blocks, block, 0, s, d, k, n, g.per_warp, static_cast<Val*>(out), found);

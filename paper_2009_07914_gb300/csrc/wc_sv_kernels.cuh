@@ -16,6 +16,8 @@
 // clear, Sec. IV-B4).
 #pragma once
 
+#include <type_traits>
+
 #include "wc_device.cuh"
 #include "wc_internal.h"
 
@@ -155,12 +157,48 @@ struct Feed {
   }
 };
 
+// Feed that also groups equal keys inside each 32-element block of the warp's input (the
+// warp-level aggregation of duplicate queries, __match_any_sync): next to its element,
+// lane l keeps the mask of the block's lanes holding the same key if l is the lowest of
+// them (the leader), 0 if a lower lane holds it (a follower), and 1 << l for a sentinel
+// (never grouped).  Only leaders probe; a leader writes the result of every follower.
+template <class T>
+struct DedupFeed : Feed<T> {
+  uint32_t m0, m1;
+  static __device__ __forceinline__ uint32_t group(T x) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t peers = __match_any_sync(kFull, x);
+    if (x == T(0) || x == T(~T(0))) return 1u << lane;
+    return static_cast<uint32_t>(__ffs(peers) - 1) == lane ? peers : 0u;
+  }
+  __device__ __forceinline__ void load(const T* p, uint64_t start, uint64_t end) {
+    Feed<T>::load(p, start, end);
+    m0 = group(this->b0);
+    m1 = group(this->b1);
+  }
+  // Group mask of the element at `pos` (valid lanes); every lane must call.
+  __device__ __forceinline__ uint32_t mask(uint64_t pos, bool valid) const {
+    const uint32_t o = valid ? static_cast<uint32_t>(pos - this->base) : 0u;
+    const uint32_t x0 = __shfl_sync(kFull, m0, o & 31);
+    const uint32_t x1 = __shfl_sync(kFull, m1, o & 31);
+    return o < 32 ? x0 : x1;
+  }
+  __device__ __forceinline__ void advance(uint64_t next) {
+    if (next - this->base >= 32) {
+      Feed<T>::advance(next);
+      m0 = m1;
+      m1 = group(this->b1);
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------------------
 // retrieve: out[i] = value of keys[i] or NOT_FOUND; found[i] = 1/0 (Sec. IV-B4).
 // Emit is called by one lane per finished query: emit(pos, hit, slot, index) -- index is
 // the matching slot's position in the table (struct-of-arrays layouts read the value
-// there; 0 for other layouts).
-template <class L, int G, int S, class Emit, class KIn = typename L::Key>
+// there; 0 for other layouts).  kDedup: equal queries of a 32-element block are probed
+// once, the result emitted for each of their positions (skewed query streams).
+template <class L, int G, int S, class Emit, class KIn = typename L::Key, bool kDedup = false>
 __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn* __restrict__ keys, RangeSrc& src,
                                                   Emit& emit, uint32_t& flags) {
   using Slot = typename L::Slot;
@@ -172,7 +210,8 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
   uint64_t pos = 0;
   Key k = 0;
   uint32_t w = 0, step = 0, j = 0, tag = 0;
-  Feed<KIn> fk;
+  uint32_t fm = 0;  // kDedup: group mask of the query being probed
+  std::conditional_t<kDedup, DedupFeed<KIn>, Feed<KIn>> fk;
   while (true) {
     const bool more = src.ensure();
     if (more && src.fresh) {
@@ -182,6 +221,10 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
     uint64_t np = 0;
     const bool got = more && take_next(!act, ln.r, ln.gbase, src.next, src.end, np);
     const KIn kin = fk.get(np, got);
+    if constexpr (kDedup) {
+      const uint32_t m = fk.mask(np, got);  // a shuffle: every lane calls
+      if (got) fm = m;
+    }
     if (more) fk.advance(src.next);
     if (got) {
       pos = np;
@@ -189,7 +232,7 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
       if (is_sentinel(kin)) {
         flags |= kFlagInvalid;
         if (ln.r == 0) emit(pos, false, Slot{}, 0ull);
-      } else {
+      } else if (!kDedup || fm != 0) {  // a follower is answered by its leader
         act = true;
         j = 0;
         probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step, tag);
@@ -217,7 +260,21 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
       hidx = static_cast<uint64_t>(w) * W + ln.r * S + (mm ? __ffs(mm) - 1 : 0);
       if constexpr (G > 1) hidx = __shfl_sync(kFull, hidx, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
     }
-    if (act) {
+    if constexpr (kDedup) {
+      if (act) {
+        const bool done = bm || be || !ovf_bit(fw, w, tag) || ++j >= t.p;
+        if (done && ln.r == 0) {
+          emit(pos, bm != 0, hit, hidx);
+          const uint64_t first = pos - static_cast<uint64_t>(__ffs(fm) - 1);  // the leader is the lowest lane
+          for (uint32_t f = fm & (fm - 1); f != 0; f &= f - 1) emit(first + (__ffs(f) - 1), bm != 0, hit, hidx);
+        }
+        if (done) {
+          act = false;
+        } else {
+          w = probe_next(w, step, t.p);
+        }
+      }
+    } else if (act) {
       if (bm) {
         if (ln.r == 0) emit(pos, true, hit, hidx);
         act = false;
@@ -259,6 +316,20 @@ __global__ void __launch_bounds__(256, retrieve_min_blocks<L, S>()) k_sv_retriev
   uint32_t flags = 0;
   EmitValue<L> emit{out, found, t.vals};
   sv_retrieve_range<L, G, S>(t, keys, src, emit, flags);
+  flush_flags(t.status, flags);
+}
+
+// The same with equal queries of each 32-element block probed once (WC_SCHEME_DEDUP).
+template <class L, int G, int S>
+__global__ void __launch_bounds__(256) k_sv_retrieve_dedup(TableDesc t, const typename L::Key* __restrict__ keys,
+                                                           uint64_t n, uint64_t per_warp,
+                                                           typename L::Val* __restrict__ out,
+                                                           uint8_t* __restrict__ found) {
+  RangeSrc src(n, per_warp, nullptr, 0);
+  if (src.next >= src.end) return;
+  uint32_t flags = 0;
+  EmitValue<L> emit{out, found, t.vals};
+  sv_retrieve_range<L, G, S, EmitValue<L>, typename L::Key, true>(t, keys, src, emit, flags);
   flush_flags(t.status, flags);
 }
 

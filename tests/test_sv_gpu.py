@@ -388,3 +388,91 @@ def test_soa_tables_are_refused_where_the_packed_layout_is_required(wc):
         wc.wc_insert_noalloc(t.handle, k, k)
     with pytest.raises(wc.WcError):  # struct-of-arrays is a single-value layout
         wc.CountingTable(4, min_capacity=1000, options=wc.WC_OPT_SOA)
+
+
+def dedup_queries(keys, absent, m, seed):
+    """m queries dense in repeats: a hot set of 48 keys (every 32-query block holds many
+    equal keys), uniform draws over all keys, absent keys, runs of one key, and sentinels."""
+    u = wc_inputs.uniform_u64(seed, m)
+    q = keys[(u % np.uint64(48)).astype(np.int64)].copy()
+    sel = (u >> np.uint64(8)) % np.uint64(4)
+    wide = keys[((u >> np.uint64(16)) % np.uint64(keys.size)).astype(np.int64)]
+    q[sel == 1] = wide[sel == 1]
+    q[sel == 2] = absent[((u >> np.uint64(24)) % np.uint64(absent.size)).astype(np.int64)][sel == 2]
+    q[100:160] = keys[7]  # a run across two blocks
+    top = keys.dtype.type(~keys.dtype.type(0))
+    q[5::97] = 0
+    q[11::101] = top
+    return q
+
+
+@pytest.mark.parametrize("kb,W,G", [(4, 8, 2), (4, 8, 1), (4, 16, 4), (4, 32, 8), (8, 4, 2), (8, 8, 4), (8, 2, 1)])
+@pytest.mark.parametrize("opt", [0, 1])
+def test_dedup_scheme_parity(wc, kb, W, G, opt):
+    """WC_SCHEME_DEDUP (one probe per group of equal queries in a warp's 32-query block,
+    the result written to every position of the group): values, found flags and status
+    equal the oracle's on query streams full of repeats, absent keys and sentinels, for
+    retrieve with and without the found mask and for wc_contains; batch sizes that end
+    inside a block."""
+    import torch
+    n = 200_003
+    keys = wc_inputs.distinct_u32(0xDD00 + W, n) if kb == 4 else wc_inputs.distinct_u64(0xDD00 + W, n)
+    vals = (wc_inputs.uniform_u32(0xDE01, n) if kb == 4 else wc_inputs.uniform_u64(0xDE01, n)).astype(keys.dtype)
+    other = wc_inputs.distinct_u32(0xDE02, 50_000) if kb == 4 else wc_inputs.distinct_u64(0xDE02, 50_000)
+    absent = other[~np.isin(other, keys)]
+    assert absent.size > 40_000
+    t = make_sv(wc, kb, kb, int(n / 0.9) + 1, W, G, options=opt)
+    t.set_launch(wc.WC_OP_RETRIEVE, G, scheme=wc.WC_SCHEME_DEDUP)
+    assert wc.wc_table_get_launch(t.handle, wc.WC_OP_RETRIEVE)["scheme"] == wc.WC_SCHEME_DEDUP
+    o = oracle.SingleValue(kb, kb)
+    assert t.insert(keys, vals) == o.insert(keys, vals) == 0
+    q = dedup_queries(keys, absent, 300_017, 0xDD3 + W)
+    eo, ef, eflags = o.retrieve(q)
+    out, found, flags = t.retrieve(q)
+    assert flags == eflags == oracle.FLAG_INVALID_KEY
+    np.testing.assert_array_equal(found, ef)
+    np.testing.assert_array_equal(out, eo)
+    qd = t.keys_dev(q)
+    vo = torch.empty_like(qd)
+    wc.wc_retrieve(t.handle, qd, vo, None)  # values only
+    np.testing.assert_array_equal(vo.cpu().numpy().view(eo.dtype), eo)
+    fm = torch.empty(q.size, dtype=torch.uint8, device="cuda")
+    wc.api.wc_contains(t.handle, qd, fm)  # membership only
+    np.testing.assert_array_equal(fm.cpu().numpy(), ef)
+    wc.wc_get_status(t.handle, True)
+    for m in (1, 31, 33, 65, 0):
+        eo, ef, _ = o.retrieve(q[:m])
+        out, found, _ = t.retrieve(q[:m])
+        np.testing.assert_array_equal(found, ef)
+        np.testing.assert_array_equal(out, eo)
+
+
+def test_dedup_scheme_counting_set_and_refusals(wc):
+    """The grouped lookup serves counting tables (counts) and hash sets (membership) too;
+    it is refused for inserts and erases and for tables without a single-slot lookup."""
+    d = wc_inputs.mv_zipf_u64(0xDD4, 1 << 12, 150_001, 1 << 10)
+    keys, q = d["keys"], d["queries"]
+    c = wc.CountingTable(8, min_capacity=1 << 13)
+    c.set_launch(wc.WC_OP_RETRIEVE, 2, scheme=wc.WC_SCHEME_DEDUP)
+    oc = oracle.Counting(8)
+    c.insert(keys)
+    oc.insert(keys)
+    qq = np.concatenate([keys[:100_000], q])
+    out, found, _ = c.retrieve(qq)
+    eo, ef, _ = oc.retrieve(qq)
+    np.testing.assert_array_equal(found, ef)
+    np.testing.assert_array_equal(out, eo)
+    st = wc.HashSetTable(8, min_capacity=1 << 13)
+    st.set_launch(wc.WC_OP_RETRIEVE, 2, scheme=wc.WC_SCHEME_DEDUP)
+    os_ = oracle.HashSet(8)
+    st.insert(keys)
+    os_.insert(keys)
+    found, _ = st.contains(qq)
+    ef, _ = os_.contains(qq)
+    np.testing.assert_array_equal(found, ef)
+    for op in (wc.WC_OP_INSERT, wc.WC_OP_ERASE):
+        with pytest.raises(wc.WcError):
+            c.set_launch(op, 2, scheme=wc.WC_SCHEME_DEDUP)
+    mv = wc.MultiValueOATable(4, 4, min_capacity=1 << 12)
+    with pytest.raises(wc.WcError):
+        mv.set_launch(wc.WC_OP_RETRIEVE, 2, scheme=wc.WC_SCHEME_DEDUP)
