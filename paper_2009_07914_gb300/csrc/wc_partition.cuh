@@ -113,9 +113,17 @@ __device__ __forceinline__ T block_scan_regions(const T* cnt, T* off, uint32_t R
 // region with shared-memory atomics, reserve one run per region in the output with one
 // global atomic on cursor[r] (zeroed by the caller), stage the tile in shared memory
 // grouped by region, then copy the runs out with consecutive threads on consecutive
-// addresses.
+// addresses.  For pairs of at most 8 bytes the next tile's input is copied into shared
+// memory with cp.async while the current tile is ranked and written out, so the input
+// stream never stops (wider pairs would halve the resident blocks and read directly).
+template <class K, class V>
+constexpr bool scatter_prefetch() {
+  return sizeof(K) + sizeof(V) <= 8;
+}
+
 template <class K, class V>
 struct ScatterSmem {
+  static constexpr int kIn = scatter_prefetch<K, V>() ? kPartTile : 1;
   K keys[kPartTile];
   V vals[kPartTile];
   unsigned short reg[kPartTile];
@@ -125,7 +133,22 @@ struct ScatterSmem {
   unsigned long long pos[kMaxRegions];
   unsigned long long w64[kPartThreads / 32];
   unsigned int w32[kPartThreads / 32];
+  K in_keys[kIn];  // the next tile's input (prefetching layouts only)
+  V in_vals[kIn];
 };
+
+// Asynchronous global -> shared copy of one 4- or 8-byte element (cp.async, L1 bypassed
+// for the streamed input with an evict-first L2 policy), and the wait for all of them.
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gmem_src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "element size");
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], %2, %3;"
+               :
+               : "r"(d), "l"(gmem_src), "n"(static_cast<int>(sizeof(T))), "l"(evict_first_policy())
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Where the values of a split come from: read from `vals`, element i's input position i,
 // or 1 (vals is not read in the last two).
@@ -139,13 +162,27 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const K* __restri
                                                                K* __restrict__ okeys, V* __restrict__ ovals) {
   extern __shared__ unsigned long long scatter_smem[];
   ScatterSmem<K, V>& S = *reinterpret_cast<ScatterSmem<K, V>*>(scatter_smem);
+  constexpr bool kPre = scatter_prefetch<K, V>();
+  const uint64_t ntiles = (n + kPartTile - 1) / kPartTile;
+  // copy tile `tl`'s input into S.in_keys / S.in_vals (prefetching layouts)
+  auto prefetch = [&](uint64_t tl) {
+    const uint64_t b = tl * kPartTile;
+    const uint32_t cnt = static_cast<uint32_t>(n - b < kPartTile ? n - b : kPartTile);
+    for (uint32_t i = threadIdx.x; i < cnt; i += kPartThreads) {
+      cp_async_elem(S.in_keys + i, keys + b + i);
+      if constexpr (kVals == kValsRead) cp_async_elem(S.in_vals + i, vals + b + i);
+    }
+  };
+  if constexpr (kPre) {
+    if (blockIdx.x < ntiles) prefetch(blockIdx.x);
+  }
   // region bases: exclusive prefix of the histogram (every block recomputes it)
   for (uint32_t i = threadIdx.x; i < m.R; i += kPartThreads) S.pos[i] = hist[i];
   __syncthreads();
   block_scan_regions<unsigned long long>(S.pos, S.base, m.R, S.w64);
-  const uint64_t ntiles = (n + kPartTile - 1) / kPartTile;
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     for (uint32_t i = threadIdx.x; i < m.R; i += kPartThreads) S.cnt[i] = 0;
+    if constexpr (kPre) cp_async_wait_all();  // this tile's input is in shared memory
     __syncthreads();
     const uint64_t t0 = tile * kPartTile;
     const uint32_t tn = static_cast<uint32_t>(n - t0 < kPartTile ? n - t0 : kPartTile);
@@ -157,11 +194,17 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const K* __restri
       const uint32_t i = k * kPartThreads + threadIdx.x;
       rr[k] = 0xffffffffu;
       if (i < tn) {
-        kk[k] = ldg_stream(keys + t0 + i);
+        if constexpr (kPre) {
+          kk[k] = S.in_keys[i];
+        } else {
+          kk[k] = ldg_stream(keys + t0 + i);
+        }
         if constexpr (kVals == kValsIota) {
           vv[k] = static_cast<V>(t0 + i);
         } else if constexpr (kVals == kValsOne) {
           vv[k] = V(1);
+        } else if constexpr (kPre) {
+          vv[k] = S.in_vals[i];
         } else {
           vv[k] = ldg_stream(vals + t0 + i);
         }
@@ -170,6 +213,10 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const K* __restri
       }
     }
     __syncthreads();
+    // the input buffer is free again: start copying the block's next tile
+    if constexpr (kPre) {
+      if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);
+    }
     block_scan_regions<unsigned int>(S.cnt, S.toff, m.R, S.w32);
     for (uint32_t r = threadIdx.x; r < m.R; r += kPartThreads)
       if (S.cnt[r]) S.pos[r] = S.base[r] + atomicAdd(cursor + r, static_cast<unsigned long long>(S.cnt[r]));
