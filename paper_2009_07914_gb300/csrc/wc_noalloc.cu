@@ -83,7 +83,7 @@ cudaError_t run(const wc_table* t, const void* keys, const void* vals, uint64_t 
   if (e != cudaSuccess) return e;
   const uint64_t ntiles = (n + kPartTile - 1) / kPartTile;
   const unsigned hg = static_cast<unsigned>(std::min<uint64_t>(
-      (n + kPartThreads - 1) / kPartThreads, static_cast<uint64_t>(occupancy_smem(hk, kPartThreads, hsm)) * t->sm_count));
+      (n + kPartTile - 1) / kPartTile, static_cast<uint64_t>(occupancy_smem(hk, kPartThreads, hsm)) * t->sm_count));
   const unsigned sg = static_cast<unsigned>(
       std::min<uint64_t>(ntiles, static_cast<uint64_t>(occupancy_smem(sk, kPartThreads, ssm)) * t->sm_count));
   hk<<<hg, kPartThreads, hsm, s>>>(static_cast<const Key*>(keys), n, m, hist);

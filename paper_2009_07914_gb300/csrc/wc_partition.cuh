@@ -59,9 +59,20 @@ __global__ void __launch_bounds__(kPartThreads) k_part_hist(const K* __restrict_
   for (uint32_t i = threadIdx.x; i < kHistWarps * m.R; i += kPartThreads) s_hw[i] = 0;
   __syncthreads();
   unsigned int* mine = s_hw + (threadIdx.x >> 5) * m.R;
-  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kPartThreads;
-  for (uint64_t e = static_cast<uint64_t>(blockIdx.x) * kPartThreads + threadIdx.x; e < n; e += stride)
-    atomicAdd(mine + m.of(ldg_stream(keys + e)), 1u);
+  // kPartItems independent loads in flight per thread (block b takes elements
+  // [b * kPartTile, (b + 1) * kPartTile) of every grid-wide stride, one per thread per item)
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kPartTile;
+  for (uint64_t e0 = static_cast<uint64_t>(blockIdx.x) * kPartTile + threadIdx.x; e0 < n; e0 += stride) {
+    K x[kPartItems];
+#pragma unroll
+    for (int u = 0; u < kPartItems; ++u) {
+      const uint64_t e = e0 + static_cast<uint64_t>(u) * kPartThreads;
+      x[u] = e < n ? ldg_stream(keys + e) : K(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kPartItems; ++u)
+      if (e0 + static_cast<uint64_t>(u) * kPartThreads < n) atomicAdd(mine + m.of(x[u]), 1u);
+  }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < m.R; i += kPartThreads) {
     unsigned int c = 0;
@@ -307,7 +318,7 @@ cudaError_t region_split(const wc_table* t, int region_mib, const K* keys, const
   }
   const uint64_t ntiles = (n + kPartTile - 1) / kPartTile;
   const unsigned hg = static_cast<unsigned>(std::min<uint64_t>(
-      (n + kPartThreads - 1) / kPartThreads, static_cast<uint64_t>(occupancy_smem(hk, kPartThreads, hsm)) * t->sm_count));
+      (n + kPartTile - 1) / kPartTile, static_cast<uint64_t>(occupancy_smem(hk, kPartThreads, hsm)) * t->sm_count));
   const unsigned sg = static_cast<unsigned>(
       std::min<uint64_t>(ntiles, static_cast<uint64_t>(occupancy_smem(sk, kPartThreads, ssm)) * t->sm_count));
   hk<<<hg, kPartThreads, hsm, s>>>(keys, n, m, hist);
