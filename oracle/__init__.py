@@ -72,6 +72,8 @@ def _load():
         lib.oracle_check_slots.restype = ctypes.c_int
         lib.oracle_check_slots.argtypes = [vp, u64, u32, u32, u32, u64, ctypes.c_int, vp, vp, vp, vp]
         lib.oracle_overflow_bits_of.restype = ctypes.c_int
+        lib.oracle_walk_stats.restype = ctypes.c_int
+        lib.oracle_walk_stats.argtypes = [vp, u64, u32, u32, u32, u64, vp, vp, u64, vp]
         lib.oracle_overflow_bits_of.argtypes = [vp, u64, u32, u32, u32, u64, vp]
         lib.oracle_bloom_create.restype = vp
         lib.oracle_bloom_create.argtypes = [ctypes.c_int, u64, ctypes.c_int, u64]
@@ -306,3 +308,31 @@ def overflow_bits_of(dump: np.ndarray, p: int, W: int, slot_bytes: int, seed: in
     if _load().oracle_overflow_bits_of(_ptr(buf), p, W, slot_bytes, key_bytes, seed & (2 ** 64 - 1), _ptr(out)) != 0:
         raise ValueError("bad table geometry")
     return out
+
+
+def walk_stats(dump: np.ndarray, p: int, W: int, slot_bytes: int, seed: int, absent: np.ndarray | None = None,
+               overflow_bits: np.ndarray | None = None, key_bytes: int | None = None) -> dict:
+    """Mean windows a lookup visits on a slot dump: `hit` over the live keys (up to the
+    window holding the key), `miss` over the `absent` keys (up to the first window with an
+    empty slot, or with overflow bits given, also a window whose bit for the key's tag is
+    clear); see oracle.cpp."""
+    buf = np.ascontiguousarray(dump).view(np.uint8)
+    if buf.size < p * W * slot_bytes:
+        raise ValueError("dump holds %d bytes, need %d" % (buf.size, p * W * slot_bytes))
+    if key_bytes is None:
+        key_bytes = 8 if slot_bytes == 16 else 4
+    ab = np.zeros(0, dtype=np.uint32 if key_bytes == 4 else np.uint64) if absent is None else \
+        np.ascontiguousarray(absent, dtype=np.uint32 if key_bytes == 4 else np.uint64)
+    ovf = None
+    if overflow_bits is not None:
+        ovf = np.ascontiguousarray(overflow_bits).view(np.uint8)
+        if ovf.size < p:
+            raise ValueError("overflow bits hold %d bytes, need %d" % (ovf.size, p))
+    out = np.zeros(4, dtype=np.uint64)
+    rc = _load().oracle_walk_stats(_ptr(buf), p, W, slot_bytes, key_bytes, seed & (2 ** 64 - 1),
+                                   None if ovf is None else _ptr(ovf), _ptr(ab) if ab.size else None, ab.size,
+                                   _ptr(out))
+    if rc != 0:
+        raise ValueError("bad table geometry")
+    h, nh, m, nm = (int(x) for x in out)
+    return {"hit": h / nh if nh else 0.0, "hits": nh, "miss": m / nm if nm else 0.0, "misses": nm}

@@ -461,6 +461,70 @@ extern "C" int oracle_overflow_bits_of(const void* dump, uint64_t p, uint32_t W,
   return 0;
 }
 
+// Walk lengths on a slot dump (hash-quality statistics): for every live key, the number
+// of windows its probing sequence visits up to and including the one that holds it; for
+// every key of `absent` (keys not in the table), the number of windows a lookup visits
+// before it may stop -- up to and including the first window holding an empty slot, or,
+// with the overflow bits given, the first window that holds an empty slot or has the bit
+// of the key's tag clear.  out[0..3] = sum over live keys, live keys counted, sum over
+// absent keys, absent keys counted (keys whose walk never ends are left out of the sums).
+extern "C" int oracle_walk_stats(const void* dump, uint64_t p, uint32_t W, uint32_t slot_bytes, uint32_t key_bytes,
+                                 uint64_t seed, const uint8_t* ovf_or_null, const void* absent, uint64_t n_absent,
+                                 uint64_t* out) {
+  const bool shape_ok = (key_bytes == 4 && (slot_bytes == 4 || slot_bytes == 8)) ||
+                        (key_bytes == 8 && (slot_bytes == 8 || slot_bytes == 16));
+  if (dump == nullptr || out == nullptr || p < 2 || W == 0 || !shape_ok || (n_absent > 0 && absent == nullptr))
+    return -1;
+  const unsigned char* s = static_cast<const unsigned char*>(dump);
+  const uint64_t tomb = key_bytes == 4 ? 0xffffffffull : ~0ull;
+  std::vector<uint8_t> has_empty(p, 0);
+  for (uint64_t i = 0; i < p * W; ++i)
+    if (chk_key(s, i, slot_bytes, key_bytes) == 0) has_empty[i / W] = 1;
+  uint64_t hit_sum = 0, hits = 0, miss_sum = 0, misses = 0;
+  for (uint64_t i = 0; i < p * W; ++i) {
+    const uint64_t k = chk_key(s, i, slot_bytes, key_bytes);
+    if (k == 0 || k == tomb) continue;
+    const uint64_t h = chk_fmix64(k ^ seed);
+    uint64_t w = ((h >> 32) * p) >> 32;
+    const uint64_t step = 1 + (((h & 0xffffffffull) * (p - 1)) >> 32);
+    for (uint64_t j = 0; j < p; ++j) {
+      if (w == i / W) {
+        hit_sum += j + 1;
+        ++hits;
+        break;
+      }
+      w = (w + step) % p;
+    }
+  }
+  for (uint64_t a = 0; a < n_absent; ++a) {
+    uint64_t k;
+    if (key_bytes == 4) {
+      uint32_t k32;
+      std::memcpy(&k32, static_cast<const unsigned char*>(absent) + a * 4, 4);
+      k = k32;
+    } else {
+      std::memcpy(&k, static_cast<const unsigned char*>(absent) + a * 8, 8);
+    }
+    const uint64_t h = chk_fmix64(k ^ seed);
+    uint64_t w = ((h >> 32) * p) >> 32;
+    const uint64_t step = 1 + (((h & 0xffffffffull) * (p - 1)) >> 32);
+    const unsigned tag = static_cast<unsigned>(h & 7u);
+    for (uint64_t j = 0; j < p; ++j) {
+      if (has_empty[w] || (ovf_or_null != nullptr && !((ovf_or_null[w] >> tag) & 1u))) {
+        miss_sum += j + 1;
+        ++misses;
+        break;
+      }
+      w = (w + step) % p;
+    }
+  }
+  out[0] = hit_sum;
+  out[1] = hits;
+  out[2] = miss_sum;
+  out[3] = misses;
+  return 0;
+}
+
 // ---------------------------------------------------------------------------------------
 // Blocked Bloom filter (Sec. IV, "BloomFilter": set membership with false positives), by
 // the definition the library documents: h = fmix64(key ^ seed); the key's block is

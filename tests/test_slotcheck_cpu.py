@@ -168,3 +168,34 @@ def test_overflow_bits(sb):
     np.testing.assert_array_equal(oracle.overflow_bits_of(t.dump(), t.p, t.W, t.sb, t.seed), t.ovf)
     with pytest.raises(ValueError):  # too few bytes for the window count
         oracle.check_slots(t.dump(), t.p, t.W, t.sb, t.seed, True, np.zeros(25, np.uint32))
+
+
+@pytest.mark.parametrize("sb", [8, 16])
+def test_walk_stats_equal_brute_force(sb):
+    """oracle.walk_stats: the mean windows of live keys equals the brute-force insert's own
+    record (key stored in the j-th window of its walk: j + 1 windows), and the mean windows
+    of absent keys equals a walk written here (to the first window with an empty slot, or
+    with overflow bits to the first window that also has the key's tag bit clear)."""
+    t = filled(sb, n=700)
+    rng = np.random.default_rng(sb)
+    top = 0xFFFFFFFE if sb == 8 else M64 - 1
+    absent = [int(k) for k in rng.integers(1, top, 300, dtype=np.uint64) if int(k) not in t.where]
+    dtype = np.uint32 if sb == 8 else np.uint64
+
+    def miss_len(k, bits):
+        g = tag(k, t.seed)
+        for j, w in enumerate(windows(k, t.seed, t.p)):
+            if 0 in t.keys[w * t.W:(w + 1) * t.W] or (bits and not (int(t.ovf[w]) >> g) & 1):
+                return j + 1
+        return None
+
+    for bits in (False, True):
+        r = oracle.walk_stats(t.dump(), t.p, t.W, t.sb, t.seed, np.array(absent, dtype=dtype),
+                              t.ovf if bits else None)
+        assert r["hits"] == len(t.where)
+        assert r["hit"] == pytest.approx(np.mean([j + 1 for _, j in t.where.values()]), abs=1e-12)
+        lens = [miss_len(k, bits) for k in absent]
+        assert r["misses"] == len(absent)
+        assert r["miss"] == pytest.approx(np.mean(lens), abs=1e-12)
+    # at this load some walks are longer than one window, and the bits shorten misses
+    assert oracle.walk_stats(t.dump(), t.p, t.W, t.sb, t.seed, np.array(absent, dtype=dtype))["miss"] > 1.0
