@@ -19,6 +19,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -187,8 +188,22 @@ def cpu_baseline(log2n_sample: int, alpha: float):
     return {"value": 2 * n / (t2 - t0) / 1e9, "unit": "G ops/s", "cores": 1, "kind": "oracle",
             "sample": "2^%d inserts + 2^%d retrievals (half absent), std::unordered_map, one host thread"
                       % (log2n_sample, log2n_sample),
-            "insert_gops": n / (t1 - t0) / 1e9, "retrieve_gops": n / (t2 - t1) / 1e9}
+            "insert_gops": n / (t1 - t0) / 1e9, "retrieve_gops": n / (t2 - t1) / 1e9,
+            "host": host_cpu()}
 
+
+def host_cpu() -> dict:
+    """CPU model and core count of this host (lscpu), for the CPU baseline's record."""
+    model = None
+    try:
+        outp = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in outp.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model or platform.processor() or platform.machine(), "cores": os.cpu_count()}
 
 
 def random_probe(dev, table_bytes: int):
@@ -261,7 +276,8 @@ def run_reference(args, rank, world):
         "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": "sv_u32_n2^%d_alpha%.2f" % (args.log2n, args.alpha), "sample_log2n": log2s},
-        "cpu_baseline": {"value": v, "unit": "G ops/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "G ops/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
         "e2e": {"value": v, "unit": "G ops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "insert_gops": statistics.mean(x["insert_gops"] for x in vals),
         "retrieve_gops": statistics.mean(x["retrieve_gops"] for x in vals),
