@@ -127,3 +127,27 @@ def test_host_calls_refuse_device_pointers(env):
         wc.api.wc_insert_host(t.handle, dk, dk)
     wc.api.wc_insert_host(t.handle, np.arange(1, 11, dtype=np.uint32), np.arange(10, dtype=np.uint32), 0)
     assert t.size() == 0
+
+
+@pytest.mark.parametrize("kb", [4, 8])
+def test_host_calls_struct_of_arrays_and_overflow_bits(env, kb):
+    """The host calls serve every single-value layout: struct-of-arrays slots and tables
+    with overflow bits give the oracle's results."""
+    wc, torch = env
+    n = 250_001
+    keys = wc_inputs.distinct_u32(0x4070 + kb, n) if kb == 4 else wc_inputs.distinct_u64(0x4070 + kb, n)
+    vals = (wc_inputs.uniform_u32(0x4071, n) if kb == 4 else wc_inputs.uniform_u64(0x4071, n)).astype(keys.dtype)
+    other = wc_inputs.distinct_u32(0x4072, 100_000) if kb == 4 else wc_inputs.distinct_u64(0x4072, 100_000)
+    q = np.concatenate([keys[::2], other[~np.isin(other, keys)]])
+    o = oracle.SingleValue(kb, kb)
+    o.insert(keys, vals)
+    eo, ef, _ = o.retrieve(q)
+    for opt in (wc.WC_OPT_SOA, wc.WC_OPT_OVERFLOW_BITS, wc.WC_OPT_SOA | wc.WC_OPT_OVERFLOW_BITS):
+        t = wc.SingleValueTable(kb, kb, min_capacity=int(n / 0.9), options=opt)
+        wc.api.wc_insert_host(t.handle, pinned(torch, keys), pinned(torch, vals))
+        ho, hf = np.empty_like(q), np.empty(q.size, np.uint8)
+        wc.api.wc_retrieve_host(t.handle, q, ho, hf)
+        torch.cuda.synchronize()
+        assert t.size() == n
+        np.testing.assert_array_equal(hf, ef)
+        np.testing.assert_array_equal(ho[ef == 1], eo[ef == 1])
