@@ -270,13 +270,18 @@ wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint6
 wc_status wc_insert_noalloc(wc_table* t, const void* d_keys, const void* d_values, uint64_t n,
                             void* stream);
 
-/* The same inserts from HOST buffers (pinned memory for full speed; pageable memory works,
- * with copies synchronous to the host): the batch moves to the device in chunks of up to
- * 2^25 pairs (the first of up to 2^23) through three device staging buffers
- * the table keeps (allocated on first use), each chunk's copy on the table's own copy
- * stream overlapping the inserts of the chunks before it on `stream`.  Asynchronous: the
- * host buffers must stay valid and unchanged until `stream` has passed this call.  Values
- * may be NULL where wc_insert allows it. */
+/* wc_insert (Sec. IV-B2, IV-B3) from HOST buffers: h_keys[i], h_values[i] as d_keys and
+ * d_values, in host memory (pinned for full speed; pageable memory works, with copies
+ * synchronous to the host).  The batch moves to the device in chunks of up to 2^25 pairs
+ * (the first of up to 2^23) through three device staging buffers the table keeps
+ * (allocated on first use, freed by wc_table_destroy), each chunk's copy on the table's own
+ * copy stream overlapping the inserts of the chunks before it on `stream`.  Asynchronous:
+ * the host buffers stay owned by the caller and must stay valid and unchanged until
+ * `stream` has passed this call.  Values may be NULL where wc_insert allows it.  Errors:
+ * WC_ERR_INVALID_ARG for a NULL table or buffer or a buffer the runtime reports as device
+ * or managed memory, WC_ERR_OUT_OF_MEMORY when the staging buffers cannot be allocated,
+ * WC_ERR_CUDA for a failed copy; otherwise as wc_insert, chunk by chunk (chunks before a
+ * failing one stay inserted). */
 wc_status wc_insert_host(wc_table* t, const void* h_keys, const void* h_values, uint64_t n, void* stream);
 
 /* Single-value retrieve (Sec. IV-B4; counting tables: the counts): d_values_out[i] = value
@@ -287,10 +292,13 @@ wc_status wc_insert_host(wc_table* t, const void* h_keys, const void* h_values, 
 wc_status wc_retrieve(wc_table* t, const void* d_keys, uint64_t n, void* d_values_out,
                       uint8_t* d_found_or_null, void* stream);
 
-/* wc_retrieve from and into HOST buffers: chunks of up to 2^23 queries are copied in on one
- * copy stream, looked up on `stream` and the results copied out on another, so the copies
- * of neighbouring chunks overlap the lookups.  `stream` completes after the last copy out.
- * Single-value and counting tables.  Asynchronous as wc_insert_host. */
+/* wc_retrieve (Sec. IV-B4) from and into HOST buffers: h_keys[i] in, h_values_out[i] and
+ * (if given) h_found_or_null[i] out, layouts as wc_retrieve's, all owned by the caller.
+ * Chunks of up to 2^23 queries are copied in on one copy stream, looked up on `stream` and
+ * the results copied out on another, so the copies of neighbouring chunks overlap the
+ * lookups; `stream` completes after the last copy out, and the outputs may be read only
+ * then.  Single-value and counting tables (others: WC_ERR_UNSUPPORTED).  Asynchronous and
+ * with the errors of wc_insert_host. */
 wc_status wc_retrieve_host(wc_table* t, const void* h_keys, uint64_t n, void* h_values_out,
                            uint8_t* h_found_or_null, void* stream);
 
