@@ -20,6 +20,7 @@ import hashlib
 import json
 import os
 import platform
+import re
 import statistics
 import subprocess
 import sys
@@ -93,16 +94,25 @@ SV_KERNEL_SOURCES = ("wc_device.cuh", "wc_sv_kernels.cuh", "wc_sv_dispatch.cuh",
                      "wc_launch.cuh", "wc_sv_p32.cu")
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments and blank lines (string literals with comment
+    markers do not occur in these files)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def source_digest():
-    """Digest of the sources the single-value probe kernels are built from (the library's
-    own and the public device header that holds the probing sequence)."""
+    """Digest of the code the single-value probe kernels are built from (the library's own
+    sources and the public device header that holds the probing sequence), comments left
+    out, so that edits of comments keep a recorded profile valid."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2009_07914_gb300", "csrc")
     paths = [os.path.join(d, name) for name in SV_KERNEL_SOURCES]
     paths.append(os.path.join(ROOT, "include", "wc_device_api.cuh"))
     for path in paths:
-        with open(path, "rb") as f:
-            h.update(os.path.basename(path).encode() + f.read())
+        with open(path, encoding="utf-8") as f:
+            h.update(os.path.basename(path).encode() + _code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

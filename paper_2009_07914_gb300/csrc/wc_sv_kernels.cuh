@@ -13,7 +13,8 @@
 // inserted again can never be stored twice; with no tombstones in the table this is
 // exactly the paper's insertion.  Retrieval stops at the key or at the first window
 // that holds an empty slot (valid because a slot never returns to empty except by a
-// clear, Sec. IV-B4).
+// clear, Sec. IV-B4) -- or, in tables with overflow bits, at a window without an empty
+// slot whose bit for the key's tag is clear (no key of that tag walked past it).
 #pragma once
 
 #include <type_traits>
