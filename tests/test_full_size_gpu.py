@@ -29,15 +29,29 @@ def _sample(n, k, seed):
     return wc_inputs.shuffle_index(seed, n)[:k]
 
 
-def test_sv_u32_2e27_load_0p9(env):
+@pytest.mark.parametrize("opts", [0, 1])
+def test_sv_u32_2e27_load_0p9(env, opts):
+    """The bench's default workload and table (opts = 1: with overflow bits, as bench.py
+    times it); with the bits, the whole slot dump passes the reachability check and the
+    dumped bits equal the ones the oracle derives from it."""
     wc, api, torch, to_device, to_numpy = env
     dev = torch.device("cuda", 0)
     n = 1 << 27
     d = wc_inputs.sv_insert_retrieve_u32(0x57C00002, n, n // 2, n // 2)
     keys, vals, q = (to_device(d[k], 4, dev) for k in ("keys", "values", "queries"))
-    h = api.wc_table_create(0, 4, 4, int(np.ceil(n / 0.9)), 0, 0, 0x5EEDC0DE, 0)
+    h = api.wc_table_create(0, 4, 4, int(np.ceil(n / 0.9)), 0, 0, 0x5EEDC0DE, 0, options=opts)
     api.wc_insert(h, keys, vals)
     assert api.wc_size(h) == n and api.wc_get_status(h, True) == 0
+    if opts:
+        info = api.wc_table_get_info(h)
+        dump = api.wc_table_dump_slots(h)
+        bits = api.wc_table_dump_overflow_bits(h)
+        r = oracle.check_slots(dump, info["windows"], info["window_width"], info["slot_bytes"], 0x5EEDC0DE, False,
+                               bits)
+        assert r == {"live": n, "dups": 0, "unreachable": 0}
+        expect = oracle.overflow_bits_of(dump, info["windows"], info["window_width"], info["slot_bytes"], 0x5EEDC0DE)
+        assert np.array_equal(bits.view(np.uint8)[:info["windows"]], expect)
+        del dump
     out = torch.empty(n, dtype=torch.int32, device=dev)
     found = torch.empty(n, dtype=torch.uint8, device=dev)
     api.wc_retrieve(h, q, out, found)
