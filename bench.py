@@ -431,7 +431,12 @@ def run_wc(args, rank, world, local_rank):
         "clear_ms": statistics.median(clear_ms), "insert_ms": ins, "retrieve_ms": ret,
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
-                     "bytes_per_op": BYTES_PER_OP[dom], "traffic": traffic},
+                     "bytes_per_op": BYTES_PER_OP[dom], "traffic": traffic,
+                     # the DRAM bytes the kernel actually moves (recorded ncu traffic) over its
+                     # measured duration: how close the random walk runs to the copy bandwidth
+                     "dram_gbs": None if traffic is None else traffic / (dom_ms * 1e-3) / 1e9,
+                     "dram_frac": None if traffic is None else traffic / (dom_ms * 1e-3) / 1e9 / peak,
+                     "dram_sectors_per_op": None if traffic is None else traffic / 32 / n},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (insert_launches(api, h, n) + 1) * args.steps,
         "clocks": clk.summary(),
     }
