@@ -73,6 +73,8 @@ def _load():
         lib.oracle_check_slots.argtypes = [vp, u64, u32, u32, u32, u64, ctypes.c_int, vp, vp, vp, vp]
         lib.oracle_overflow_bits_of.restype = ctypes.c_int
         lib.oracle_walk_stats.restype = ctypes.c_int
+        lib.oracle_build_packed_table.restype = ctypes.c_int64
+        lib.oracle_build_packed_table.argtypes = [vp, vp, u64, u64, u32, u64, vp, vp]
         lib.oracle_walk_stats.argtypes = [vp, u64, u32, u32, u32, u64, vp, vp, u64, vp]
         lib.oracle_overflow_bits_of.argtypes = [vp, u64, u32, u32, u32, u64, vp]
         lib.oracle_bloom_create.restype = vp
@@ -336,3 +338,19 @@ def walk_stats(dump: np.ndarray, p: int, W: int, slot_bytes: int, seed: int, abs
         raise ValueError("bad table geometry")
     h, nh, m, nm = (int(x) for x in out)
     return {"hit": h / nh if nh else 0.0, "hits": nh, "miss": m / nm if nm else 0.0, "misses": nm}
+
+
+def build_packed_table(keys: np.ndarray, values: np.ndarray | None, p: int, W: int, seed: int):
+    """(slot dump as bytes, overflow bits as p bytes) of a packed 4+4-byte table built by
+    inserting the distinct uint32 `keys` one at a time (see oracle.cpp)."""
+    k = np.ascontiguousarray(keys, dtype=np.uint32)
+    v = None if values is None else np.ascontiguousarray(values, dtype=np.uint32)
+    slots = np.zeros(p * W, dtype=np.uint64)
+    bits = np.zeros(p, dtype=np.uint8)
+    failed = _load().oracle_build_packed_table(_ptr(k), None if v is None else _ptr(v), k.size, p, W,
+                                               seed & (2 ** 64 - 1), _ptr(slots), _ptr(bits))
+    if failed < 0:
+        raise ValueError("bad table geometry")
+    if failed:
+        raise ValueError("%d keys found no slot" % failed)
+    return slots.view(np.uint8), bits

@@ -525,6 +525,44 @@ extern "C" int oracle_walk_stats(const void* dump, uint64_t p, uint32_t W, uint3
   return 0;
 }
 
+// A single-value table of packed 4+4-byte slots built by the paper's insertion applied to
+// one key at a time (Sec. IV-B2: walk the key's windows, store the pair in the lowest empty
+// slot of the first window that has one), with the overflow bits such an insert sets (bit
+// tag(k) of every window it walks past).  Distinct keys, no erases.  out_slots: p * W
+// packed words (key | value << 32); out_bits: p bytes.  Returns the number of keys that
+// found no slot (0 below a full table).  Sequential order is one of the orders a parallel
+// insert may produce; walk statistics of such tables predict those of the GPU's.
+extern "C" int64_t oracle_build_packed_table(const uint32_t* keys, const uint32_t* vals, uint64_t n, uint64_t p,
+                                             uint32_t W, uint64_t seed, uint64_t* out_slots, uint8_t* out_bits) {
+  if (keys == nullptr || out_slots == nullptr || out_bits == nullptr || p < 2 || W == 0) return -1;
+  std::memset(out_slots, 0, p * W * sizeof(uint64_t));
+  std::memset(out_bits, 0, p);
+  int64_t failed = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint64_t k = keys[i];
+    const uint64_t h = chk_fmix64(k ^ seed);
+    uint64_t w = ((h >> 32) * p) >> 32;
+    const uint64_t step = 1 + (((h & 0xffffffffull) * (p - 1)) >> 32);
+    bool stored = false;
+    for (uint64_t j = 0; j < p && !stored; ++j) {
+      for (uint32_t q = 0; q < W; ++q) {
+        uint64_t& slot = out_slots[w * W + q];
+        if (static_cast<uint32_t>(slot) == 0) {
+          slot = k | (static_cast<uint64_t>(vals ? vals[i] : 0) << 32);
+          stored = true;
+          break;
+        }
+      }
+      if (!stored) {
+        out_bits[w] |= static_cast<uint8_t>(1u << (h & 7u));
+        w = (w + step) % p;
+      }
+    }
+    if (!stored) ++failed;
+  }
+  return failed;
+}
+
 // ---------------------------------------------------------------------------------------
 // Blocked Bloom filter (Sec. IV, "BloomFilter": set membership with false positives), by
 // the definition the library documents: h = fmix64(key ^ seed); the key's block is

@@ -199,3 +199,40 @@ def test_walk_stats_equal_brute_force(sb):
         assert r["miss"] == pytest.approx(np.mean(lens), abs=1e-12)
     # at this load some walks are longer than one window, and the bits shorten misses
     assert oracle.walk_stats(t.dump(), t.p, t.W, t.sb, t.seed, np.array(absent, dtype=dtype))["miss"] > 1.0
+
+
+def test_sequential_table_builder_equals_brute_force():
+    """oracle.build_packed_table builds, key by key, the same slots and overflow bits as
+    the brute-force insert written here in Python integers."""
+    t = Table(101, 8, 8, 0xC0FFEE)
+    rng = np.random.default_rng(5)
+    keys = []
+    for k in rng.integers(1, 0xFFFFFFFE, 760, dtype=np.uint64):
+        if int(k) not in t.where and t.insert(int(k)):
+            keys.append(int(k))
+    dump, bits = oracle.build_packed_table(np.array(keys, dtype=np.uint32), np.full(len(keys), 7, np.uint32),
+                                           101, 8, 0xC0FFEE)
+    np.testing.assert_array_equal(dump, t.dump())
+    np.testing.assert_array_equal(bits, t.ovf)
+
+
+def test_walk_lengths_at_load_0p9():
+    """Walk lengths of a table built key by key at load 0.9 (W = 8, 2^18 windows): present
+    keys visit 1.22 windows; absent keys 2.87 without overflow bits, 2.07 with one bit per
+    window (any key walked past) and 1.20 with eight bits selected by the key's tag."""
+    import wc_inputs
+    p, W = 262_139, 8  # prime
+    n = int(0.9 * p * W)
+    keys = wc_inputs.distinct_u32(0x51A, n + 200_000)
+    absent, keys = keys[n:], keys[:n]
+    dump, tags = oracle.build_packed_table(keys, None, p, W, 0x5EED)
+    one_bit = np.where(tags != 0, 0xFF, 0).astype(np.uint8)
+    plain = oracle.walk_stats(dump, p, W, 8, 0x5EED, absent)
+    one = oracle.walk_stats(dump, p, W, 8, 0x5EED, absent, one_bit)
+    tagged = oracle.walk_stats(dump, p, W, 8, 0x5EED, absent, tags)
+    assert plain["hits"] == n and plain["misses"] == absent.size
+    assert plain["hit"] == pytest.approx(1.22, abs=0.02)
+    assert plain["miss"] == pytest.approx(2.87, abs=0.1)
+    assert one["miss"] == pytest.approx(2.07, abs=0.1)
+    assert tagged["miss"] == pytest.approx(1.20, abs=0.05)
+    assert one["hit"] == tagged["hit"] == plain["hit"]
