@@ -98,3 +98,16 @@ def test_binding_structs_match_the_c_layouts(tmp_path):
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     assert got == want
+
+
+def test_binding_constants_match_the_header():
+    """Every WC_* enumerator of include/wc.h has the same value in the Python binding."""
+    from paper_2009_07914_gb300 import _binding as B
+    text = open(os.path.join(ROOT, "include", "wc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    found = dict((m.group(1), int(m.group(2))) for m in re.finditer(r"\b(WC_[A-Z0-9_]+)\s*=\s*(\d+)", text))
+    assert len(found) >= 25
+    for name, value in found.items():
+        if name == "WC_OP__N":
+            continue
+        assert getattr(B, name) == value, name
