@@ -111,3 +111,20 @@ def test_binding_constants_match_the_header():
         if name == "WC_OP__N":
             continue
         assert getattr(B, name) == value, name
+
+
+def test_device_api_header_compiles_for_sm103a(tmp_path):
+    """The public device API (include/wc_device_api.cuh) compiles into a user's program for
+    sm_103a: the example kernels of tests/device_api are built here without a GPU."""
+    import shutil
+    import subprocess
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    out = str(tmp_path / "user_kernels.o")
+    r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "--extended-lambda",
+                        "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-c",
+                        os.path.join(ROOT, "tests", "device_api", "user_kernels.cu"), "-o", out],
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    assert os.path.getsize(out) > 0
