@@ -140,25 +140,6 @@ int default_group(uint64_t slot_bytes, int W, int op) {
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
-wc_status cuda_status(cudaError_t e) {
-  if (e == cudaSuccess) return WC_OK;
-  if (e == cudaErrorMemoryAllocation) return WC_ERR_OUT_OF_MEMORY;
-  return WC_ERR_CUDA;
-}
-
-// Bulk ops run on the table's device; restore the caller's device afterwards.
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
 bool aligned(const void* p, uint64_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 // Testing hook (wc_debug_fail_allocations): allocations still to fail on purpose.

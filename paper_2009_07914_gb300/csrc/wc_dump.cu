@@ -22,24 +22,6 @@ struct SnapHeader {
 };
 static_assert(sizeof(SnapHeader) == 80, "snapshot header layout");
 
-struct DevGuard {
-  int prev = -1;
-  explicit DevGuard(int d) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != d) cudaSetDevice(d);
-  }
-  ~DevGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
-wc_status to_status(cudaError_t e) {
-  if (e == cudaSuccess) return WC_OK;
-  if (e == cudaErrorMemoryAllocation) return WC_ERR_OUT_OF_MEMORY;
-  return WC_ERR_CUDA;
-}
-
 SnapHeader header_of(const wc_table* t) {
   SnapHeader h;
   std::memset(&h, 0, sizeof(h));
@@ -71,11 +53,11 @@ extern "C" {
 
 wc_status wc_table_dump_slots(const wc_table* t, void* h_out, uint64_t bytes, void* stream) {
   if (t == nullptr || h_out == nullptr || bytes < t->table_bytes) return WC_ERR_INVALID_ARG;
-  DevGuard g(t->device);
+  wc::DeviceGuard g(t->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(h_out, t->d_slots, t->table_bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return to_status(e);
+  return wc::cuda_status(e);
 }
 
 wc_status wc_table_dump_overflow_bits(const wc_table* t, uint32_t* h_out, uint64_t words, void* stream) {
@@ -83,11 +65,11 @@ wc_status wc_table_dump_overflow_bits(const wc_table* t, uint32_t* h_out, uint64
   if (t->d_ovf == nullptr) return WC_ERR_UNSUPPORTED;
   const uint64_t need = (t->windows + 3) / 4;
   if (words < need) return WC_ERR_INVALID_ARG;
-  DevGuard g(t->device);
+  wc::DeviceGuard g(t->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(h_out, t->d_ovf, need * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return to_status(e);
+  return wc::cuda_status(e);
 }
 
 uint64_t wc_table_snapshot_bytes(const wc_table* t) {
@@ -98,7 +80,7 @@ uint64_t wc_table_snapshot_bytes(const wc_table* t) {
 
 wc_status wc_table_snapshot(const wc_table* t, void* h_out, uint64_t bytes, void* stream) {
   if (t == nullptr || h_out == nullptr || bytes < wc_table_snapshot_bytes(t)) return WC_ERR_INVALID_ARG;
-  DevGuard g(t->device);
+  wc::DeviceGuard g(t->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const SnapHeader h = header_of(t);
   std::memcpy(h_out, &h, sizeof(h));
@@ -108,7 +90,7 @@ wc_status wc_table_snapshot(const wc_table* t, void* h_out, uint64_t bytes, void
     e = cudaMemcpyAsync(dst + t->clear_bytes, t->d_pool, t->device_bytes - pool_offset(t), cudaMemcpyDeviceToHost,
                         s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return to_status(e);
+  return wc::cuda_status(e);
 }
 
 wc_status wc_table_restore(wc_table* t, const void* h_in, uint64_t bytes, void* stream) {
@@ -122,7 +104,7 @@ wc_status wc_table_restore(wc_table* t, const void* h_in, uint64_t bytes, void* 
       h.clear_bytes != want.clear_bytes || h.bucket_first_size != want.bucket_first_size ||
       h.bucket_growth_bits != want.bucket_growth_bits || bytes < wc_table_snapshot_bytes(t))
     return WC_ERR_INVALID_ARG;
-  DevGuard g(t->device);
+  wc::DeviceGuard g(t->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const char* src = static_cast<const char*>(h_in) + sizeof(h);
   cudaError_t e = cudaMemcpyAsync(t->d_block, src, t->clear_bytes, cudaMemcpyHostToDevice, s);
@@ -130,7 +112,7 @@ wc_status wc_table_restore(wc_table* t, const void* h_in, uint64_t bytes, void* 
     e = cudaMemcpyAsync(t->d_pool, src + t->clear_bytes, t->device_bytes - pool_offset(t), cudaMemcpyHostToDevice,
                         s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return to_status(e);
+  return wc::cuda_status(e);
 }
 
 wc_status wc_table_device_view(const wc_table* t, wc_device_view* h_out) {

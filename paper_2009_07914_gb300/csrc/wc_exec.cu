@@ -199,18 +199,6 @@ struct wc_executor {
 
 namespace {
 
-struct Guard {
-  int prev = -1;
-  explicit Guard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~Guard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
 void free_executor(wc_executor* ex) {
   for (int i = 0; i < 2; ++i) {
     if (ex->exec[i]) cudaGraphExecDestroy(ex->exec[i]);
@@ -249,7 +237,7 @@ wc_status wc_executor_create(wc_executor** out, const wc_executor_config* cfg) {
   ex->cfg = *cfg;
   ex->cfg.tile_keys = tk;
   if (ex->cfg.timeout_ns == 0) ex->cfg.timeout_ns = 2000000000ull;
-  Guard guard(cfg->device);
+  DeviceGuard guard(cfg->device);
   ex->sm_count = sm_count_of(cfg->device);
   ex->lay = Layout(cfg->max_items);
   ex->kernel = W == 4 ? kernel_for<4>() : W == 8 ? kernel_for<8>() : kernel_for<16>();
@@ -318,7 +306,7 @@ wc_status wc_executor_create(wc_executor** out, const wc_executor_config* cfg) {
 
 wc_status wc_executor_destroy(wc_executor* ex) {
   if (ex == nullptr) return WC_ERR_INVALID_ARG;
-  Guard guard(ex->cfg.device);
+  DeviceGuard guard(ex->cfg.device);
   cudaDeviceSynchronize();
   free_executor(ex);
   return WC_OK;
@@ -340,7 +328,7 @@ wc_status wc_executor_submit(wc_executor* ex, const wc_work* h_items, uint32_t c
       return WC_ERR_INVALID_ARG;
     if (w.n >= (1ull << 40)) return WC_ERR_INVALID_ARG;
   }
-  Guard guard(ex->cfg.device);
+  DeviceGuard guard(ex->cfg.device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const uint64_t ticket = ex->next_ticket++;
   const int slot = static_cast<int>(ticket & 1);
@@ -415,7 +403,7 @@ wc_status wc_executor_query(wc_executor* ex, uint64_t ticket, int32_t* h_done) {
     *h_done = 1;  // older than the ring: finished before a later launch on the same stream
     return WC_OK;
   }
-  Guard guard(ex->cfg.device);
+  DeviceGuard guard(ex->cfg.device);
   const cudaError_t e = cudaEventQuery(ex->ring[ticket % kTicketRing]);
   if (e == cudaSuccess) {
     *h_done = 1;
@@ -450,13 +438,13 @@ wc_status wc_executor_query_item(wc_executor* ex, uint64_t ticket, uint32_t inde
 wc_status wc_executor_wait(wc_executor* ex, uint64_t ticket) {
   if (ex == nullptr || ticket >= ex->next_ticket) return WC_ERR_INVALID_ARG;
   if (ticket + kTicketRing < ex->next_ticket) return WC_OK;
-  Guard guard(ex->cfg.device);
+  DeviceGuard guard(ex->cfg.device);
   return cudaEventSynchronize(ex->ring[ticket % kTicketRing]) == cudaSuccess ? WC_OK : WC_ERR_CUDA;
 }
 
 wc_status wc_executor_get_status(wc_executor* ex, uint32_t* h_flags, int32_t clear) {
   if (ex == nullptr || h_flags == nullptr) return WC_ERR_INVALID_ARG;
-  Guard guard(ex->cfg.device);
+  DeviceGuard guard(ex->cfg.device);
   cudaStream_t s = ex->last_stream;
   uint32_t* d = reinterpret_cast<uint32_t*>(ex->d_buf + ex->lay.status);
   cudaError_t e = cudaMemcpyAsync(h_flags, d, 4, cudaMemcpyDeviceToHost, s);

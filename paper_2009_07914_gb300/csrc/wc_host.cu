@@ -109,23 +109,6 @@ bool is_host(const void* p) {
   return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
 }
 
-struct Guard {
-  int prev = -1;
-  explicit Guard(int d) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != d) cudaSetDevice(d);
-  }
-  ~Guard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
-wc_status status_of(cudaError_t e) {
-  if (e == cudaSuccess) return WC_OK;
-  return e == cudaErrorMemoryAllocation ? WC_ERR_OUT_OF_MEMORY : WC_ERR_CUDA;
-}
-
 }  // namespace
 }  // namespace wc
 
@@ -141,13 +124,13 @@ wc_status wc_insert_host(wc_table* t, const void* h_keys, const void* h_values, 
   if (h_keys == nullptr || !is_host(h_keys) || (!no_values && (h_values == nullptr || !is_host(h_values))))
     return WC_ERR_INVALID_ARG;
   if (t->cfg.kind == WC_MULTI_VALUE && n >= (1ull << 31)) return WC_ERR_INVALID_ARG;
-  Guard g(t->device);
+  DeviceGuard g(t->device);
   const uint64_t kb = static_cast<uint64_t>(t->cfg.key_bytes), vb = no_values ? 0 : t->cfg.value_bytes;
   const uint64_t chunk = std::min<uint64_t>(n, kInsertChunk);
   const uint64_t koff = 0, voff = align256(chunk * kb);
   HostPipe* h = nullptr;
   cudaError_t e = pipe_of(t, voff + align256(chunk * vb), &h);
-  if (e != cudaSuccess) return status_of(e);
+  if (e != cudaSuccess) return cuda_status(e);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint64_t base = 0;
   for (uint64_t c = 0; base < n; ++c) {
@@ -169,7 +152,7 @@ wc_status wc_insert_host(wc_table* t, const void* h_keys, const void* h_values, 
     if ((e = cudaEventRecord(h->freed[b], s)) != cudaSuccess) break;
     base += cnt;
   }
-  return status_of(e);
+  return cuda_status(e);
 }
 
 wc_status wc_retrieve_host(wc_table* t, const void* h_keys, uint64_t n, void* h_values_out, uint8_t* h_found_or_null,
@@ -180,13 +163,13 @@ wc_status wc_retrieve_host(wc_table* t, const void* h_keys, uint64_t n, void* h_
   if (h_keys == nullptr || h_values_out == nullptr || !is_host(h_keys) || !is_host(h_values_out) ||
       (h_found_or_null != nullptr && !is_host(h_found_or_null)))
     return WC_ERR_INVALID_ARG;
-  Guard g(t->device);
+  DeviceGuard g(t->device);
   const uint64_t kb = static_cast<uint64_t>(t->cfg.key_bytes), vb = static_cast<uint64_t>(t->cfg.value_bytes);
   const uint64_t chunk = std::min<uint64_t>(n, kRetrieveChunk);
   const uint64_t ooff = align256(chunk * kb), foff = ooff + align256(chunk * vb);
   HostPipe* h = nullptr;
   cudaError_t e = pipe_of(t, foff + align256(chunk), &h);
-  if (e != cudaSuccess) return status_of(e);
+  if (e != cudaSuccess) return cuda_status(e);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const uint64_t nchunks = (n + chunk - 1) / chunk;
   for (uint64_t c = 0; c < nchunks; ++c) {
@@ -216,7 +199,7 @@ wc_status wc_retrieve_host(wc_table* t, const void* h_keys, uint64_t n, void* h_
   // the caller's stream completes after the last copy out
   if (e == cudaSuccess) e = cudaEventRecord(h->tail, h->out);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->tail, 0);
-  return status_of(e);
+  return cuda_status(e);
 }
 
 }  // extern "C"

@@ -11,6 +11,28 @@
 
 namespace wc {
 
+// Host calls run on the table's device and give the caller's device back afterwards.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
+// wc_status of a CUDA runtime result (allocation failures: WC_ERR_OUT_OF_MEMORY).
+inline wc_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return WC_OK;
+  if (e == cudaErrorMemoryAllocation) return WC_ERR_OUT_OF_MEMORY;
+  return WC_ERR_CUDA;
+}
+
 // What every single-value / key-store kernel needs, passed by value.
 struct TableDesc {
   void* slots;                       // p * W slots, 256-byte aligned
