@@ -498,6 +498,7 @@ wc_status wc_table_destroy(wc_table* t) {
 }
 
 wc_status wc_table_clear(wc_table* t, void* stream) {
+  TraceRange trace("wc_table_clear");
   if (t == nullptr) return WC_ERR_INVALID_ARG;
   DeviceGuard guard(t->device);
   return cuda_status(cudaMemsetAsync(t->d_block, 0, t->clear_bytes, as_stream(stream)));
@@ -577,6 +578,7 @@ static wc_status check_bulk(const wc_table* t, const void* keys, uint64_t n) {
 }
 
 wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint64_t n, void* stream) {
+  TraceRange trace("wc_insert");
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
   const bool weights_optional =
@@ -607,6 +609,7 @@ wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint6
 
 wc_status wc_retrieve(wc_table* t, const void* d_keys, uint64_t n, void* d_values_out, uint8_t* d_found_or_null,
                       void* stream) {
+  TraceRange trace("wc_retrieve");
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
   if (t->cfg.kind != WC_SINGLE_VALUE && t->cfg.kind != WC_COUNTING) return WC_ERR_UNSUPPORTED;
@@ -620,6 +623,7 @@ wc_status wc_retrieve(wc_table* t, const void* d_keys, uint64_t n, void* d_value
 }
 
 wc_status wc_erase(wc_table* t, const void* d_keys, uint64_t n, void* stream) {
+  TraceRange trace("wc_erase");
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
   if (t->cfg.kind == WC_BLOOM_FILTER) return WC_ERR_UNSUPPORTED;  // bits are shared between keys
@@ -633,6 +637,7 @@ wc_status wc_erase(wc_table* t, const void* d_keys, uint64_t n, void* stream) {
 }
 
 wc_status wc_contains(wc_table* t, const void* d_keys, uint64_t n, uint8_t* d_found, void* stream) {
+  TraceRange trace("wc_contains");
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
   st = check_buffer(t, d_found, n, 1);
@@ -650,6 +655,7 @@ wc_status wc_contains(wc_table* t, const void* d_keys, uint64_t n, uint8_t* d_fo
 
 wc_status wc_count_values(wc_table* t, const void* d_keys, uint64_t n, uint64_t* d_offsets,
                           uint64_t* h_total_or_null, void* stream) {
+  TraceRange trace("wc_count_values");
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
   if (t->cfg.kind != WC_MULTI_VALUE && t->cfg.kind != WC_MULTI_VALUE_OA) return WC_ERR_UNSUPPORTED;
@@ -674,6 +680,7 @@ wc_status wc_count_values(wc_table* t, const void* d_keys, uint64_t n, uint64_t*
 
 wc_status wc_retrieve_multi(wc_table* t, const void* d_keys, uint64_t n, const uint64_t* d_offsets,
                             void* d_values_out, void* stream) {
+  TraceRange trace("wc_retrieve_multi");
   wc_status st = check_bulk(t, d_keys, n);
   if (st != WC_OK) return st;
   if (t->cfg.kind != WC_MULTI_VALUE && t->cfg.kind != WC_MULTI_VALUE_OA) return WC_ERR_UNSUPPORTED;

@@ -117,6 +117,7 @@ using namespace wc;
 extern "C" {
 
 wc_status wc_insert_host(wc_table* t, const void* h_keys, const void* h_values, uint64_t n, void* stream) {
+  TraceRange trace("wc_insert_host");
   if (t == nullptr) return WC_ERR_INVALID_ARG;
   if (n == 0) return WC_OK;
   const bool no_values = t->cfg.kind == WC_HASH_SET || t->cfg.kind == WC_BLOOM_FILTER ||
@@ -157,6 +158,7 @@ wc_status wc_insert_host(wc_table* t, const void* h_keys, const void* h_values, 
 
 wc_status wc_retrieve_host(wc_table* t, const void* h_keys, uint64_t n, void* h_values_out, uint8_t* h_found_or_null,
                            void* stream) {
+  TraceRange trace("wc_retrieve_host");
   if (t == nullptr) return WC_ERR_INVALID_ARG;
   if (t->cfg.kind != WC_SINGLE_VALUE && t->cfg.kind != WC_COUNTING) return WC_ERR_UNSUPPORTED;
   if (n == 0) return WC_OK;

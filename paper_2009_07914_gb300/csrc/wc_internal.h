@@ -9,7 +9,18 @@
 
 #include "wc.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace wc {
+
+// Named range on the NVTX timeline around a host call of the C ABI (a no-op unless a
+// profiler is attached), so profiles show which call launched which kernels.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Host calls run on the table's device and give the caller's device back afterwards.
 struct DeviceGuard {
