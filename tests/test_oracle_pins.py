@@ -290,3 +290,48 @@ def test_bloom_oracle_no_false_negatives_and_formula_rate():
     assert abs(fp - total) < 0.12 * total, (fp, total)
     # plain (unblocked) Bloom filters do better: the blocked layout costs a little FP rate
     assert total > (1 - math.exp(-k * n / (blocks * 256))) ** k
+
+
+def _fmix64_py(x: int) -> int:
+    m = (1 << 64) - 1
+    x ^= x >> 33
+    x = (x * 0xFF51AFD7ED558CCD) & m
+    x ^= x >> 33
+    x = (x * 0xC4CEB9FE1A85EC53) & m
+    x ^= x >> 33
+    return x
+
+
+@pytest.mark.parametrize("kb,k", [(4, 1), (4, 7), (8, 8), (8, 9), (4, 16)])
+def test_bloom_oracle_equals_the_documented_bit_rule(kb, k):
+    """Exact pin of the oracle's Bloom filter: a Python restatement of the documented rule
+    (block = hi32(h) * blocks >> 32 with h = fmix64(key ^ seed); bit i = byte i % 8 of
+    g_{i/8+1}, g_1 = fmix64(h ^ 0x9e3779b97f4a7c15), g_{j+1} = fmix64(g_j)) on a filter small
+    enough that most answers are false positives, so any change of the rule shows."""
+    blocks, seed = 37, 0xB10C
+    rng = np.random.default_rng(k * 10 + kb)
+    top = 2 ** 31 if kb == 4 else 2 ** 62
+    dt = np.uint32 if kb == 4 else np.uint64
+    keys = rng.integers(1, top, 2000, dtype=np.uint64).astype(dt)
+    queries = np.concatenate([rng.integers(1, top, 3000, dtype=np.uint64).astype(dt), keys[:200]])
+
+    def bits_of(key):
+        h = _fmix64_py(int(key) ^ seed)
+        block = ((h >> 32) * blocks) >> 32
+        g, pos = h ^ 0x9E3779B97F4A7C15, []
+        for i in range(k):
+            if i % 8 == 0:
+                g = _fmix64_py(g)
+            pos.append((g >> (8 * (i % 8))) & 255)
+        return block, pos
+
+    set_bits = set()
+    for key in keys:
+        b, pos = bits_of(key)
+        set_bits.update((b, p) for p in pos)
+    expect = np.array([all((b, p) in set_bits for p in pos) for b, pos in map(bits_of, queries)], np.uint8)
+    o = oracle.BloomFilter(kb, blocks, k, seed)
+    o.insert(keys)
+    found, _ = o.contains(queries)
+    np.testing.assert_array_equal(found, expect)
+    assert expect[3000:].all() and 0 < expect[:3000].mean() < 1  # inserted keys found; both answers occur
