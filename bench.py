@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access roofline probe")
+    ap.add_argument("--alphas", default="0.5,0.8,0.9,0.95,0.99",
+                    help="sv32: target loads of the density sweep reported beside the headline ('' = none)")
     ap.add_argument("--soa", action="store_true", help="sv32: struct-of-arrays table (keys and values in two arrays)")
     ap.add_argument("--no-overflow-bits", action="store_true",
                     help="sv32: table without per-window overflow bits (lookups walk to an empty slot)")
@@ -182,23 +184,35 @@ def workload(log2n: int, alpha: float):
     return n, d
 
 
-def cpu_baseline(log2n_sample: int, alpha: float):
-    """The oracle (single-threaded std::unordered_map, reserve(n)) on a bounded sample of
-    the same workload: insert n pairs then retrieve n queries (half absent)."""
-    import oracle
-    n = 1 << log2n_sample
-    d = wc_inputs.sv_insert_retrieve_u32(SEED, n, n // 2, n // 2)
-    o = oracle.SingleValue(4, 4)
+def _time_oracle(o, d, n, alpha):
+    """Insert then retrieve one sample into oracle object o; returns (insert_s, retrieve_s)."""
     o.reserve(int(n / alpha))
     t0 = time.perf_counter()
     o.insert(d["keys"], d["values"])
     t1 = time.perf_counter()
     o.retrieve(d["queries"])
     t2 = time.perf_counter()
-    return {"value": 2 * n / (t2 - t0) / 1e9, "unit": "G ops/s", "cores": 1, "kind": "oracle",
-            "sample": "2^%d inserts + 2^%d retrievals (half absent), std::unordered_map, one host thread"
-                      % (log2n_sample, log2n_sample),
-            "insert_gops": n / (t1 - t0) / 1e9, "retrieve_gops": n / (t2 - t1) / 1e9,
+    return t1 - t0, t2 - t1
+
+
+def cpu_baseline(log2n_sample: int, alpha: float):
+    """The oracle on the host cores, on bounded samples of the same workload (insert n
+    pairs, then retrieve n queries, half absent), in its two forms: one thread over one
+    std::unordered_map (reserve(n)), and sharded over every host core (one plain
+    std::unordered_map per shard, key k in shard hash(k) mod T).  `value` is the sharded
+    form; the single-thread one is reported beside it."""
+    import oracle
+    n = 1 << log2n_sample
+    d = wc_inputs.sv_insert_retrieve_u32(SEED, n, n // 2, n // 2)
+    ti1, tr1 = _time_oracle(oracle.SingleValue(4, 4), d, n, alpha)
+    cores = os.cpu_count() or 1
+    tis, trs = _time_oracle(oracle.ShardedSingleValue(4, 4, threads=cores), d, n, alpha)
+    return {"value": 2 * n / (tis + trs) / 1e9, "unit": "G ops/s", "cores": cores, "kind": "oracle",
+            "sample": "2^%d inserts + 2^%d retrievals (half absent), sharded std::unordered_map, one thread per "
+                      "host core" % (log2n_sample, log2n_sample),
+            "insert_gops": n / tis / 1e9, "retrieve_gops": n / trs / 1e9,
+            "single_thread": {"value": 2 * n / (ti1 + tr1) / 1e9, "cores": 1, "insert_gops": n / ti1 / 1e9,
+                              "retrieve_gops": n / tr1 / 1e9},
             "host": host_cpu()}
 
 
@@ -269,28 +283,39 @@ def emit(res):
 
 
 def run_reference(args, rank, world):
+    """The oracle timed on the host cores (the reference arm): every step inserts a
+    2^23-pair sample of the default workload into a fresh sharded oracle (one plain
+    std::unordered_map per host core) and retrieves 2^23 queries (half absent)."""
     if rank != 0:
         return
+    import oracle
     steps, warm = args.steps, args.warmup
-    log2s = 21
-    vals = []
+    log2s = 23
+    n = 1 << log2s
+    d = wc_inputs.sv_insert_retrieve_u32(SEED, n, n // 2, n // 2)
+    cores = os.cpu_count() or 1
+    ins, ret = [], []
     for i in range(warm + steps):
-        r = cpu_baseline(log2s, args.alpha)
+        ti, tr = _time_oracle(oracle.ShardedSingleValue(4, 4, threads=cores), d, n, args.alpha)
         if i >= warm:
-            vals.append(r)
-    v = statistics.mean(x["value"] for x in vals)
-    sample = vals[0]["sample"]
-    ms = 2 * (1 << log2s) / (v * 1e9) * 1e3
+            ins.append(ti)
+            ret.append(tr)
+    t_step = statistics.mean(a + b for a, b in zip(ins, ret))
+    v = 2 * n / t_step / 1e9
+    ti1, tr1 = _time_oracle(oracle.SingleValue(4, 4), d, n, args.alpha)
+    sample = ("2^%d inserts + 2^%d retrievals (half absent) per step, sharded std::unordered_map, one thread per "
+              "host core" % (log2s, log2s))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "G ops/s", "n_gpus": args.gpus,
-        "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "steps": steps, "warmup": warm, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": "sv_u32_n2^%d_alpha%.2f" % (args.log2n, args.alpha), "sample_log2n": log2s},
-        "cpu_baseline": {"value": v, "unit": "G ops/s", "cores": 1, "kind": "oracle", "sample": sample,
+        "cpu_baseline": {"value": v, "unit": "G ops/s", "cores": cores, "kind": "oracle", "sample": sample,
+                         "single_thread": {"value": 2 * n / (ti1 + tr1) / 1e9, "cores": 1},
                          "host": host_cpu()},
         "e2e": {"value": v, "unit": "G ops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "insert_gops": statistics.mean(x["insert_gops"] for x in vals),
-        "retrieve_gops": statistics.mean(x["retrieve_gops"] for x in vals),
+        "insert_gops": n / statistics.mean(ins) / 1e9,
+        "retrieve_gops": n / statistics.mean(ret) / 1e9,
     }), flush=True)
 
 
@@ -440,6 +465,8 @@ def run_wc(args, rank, world, local_rank):
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (insert_launches(api, h, n) + 1) * args.steps,
         "clocks": clk.summary(),
     }
+    if args.alphas:
+        res["load_sweep"] = load_sweep(args, api, wc, h, keys, vals, qk, out, found, n, s, peak, rank, local_rank)
     if not args.no_probe:
         pr = random_probe(dev, info["table_bytes"])
         # retrieve reads ~1 window of W slots per present key and a few per absent key;
@@ -448,6 +475,42 @@ def run_wc(args, rank, world, local_rank):
                                       insert_frac_of_rmw64=res["insert_gops"] / pr["rmw64_gps"])
     print(json.dumps(res), flush=True)
     api.wc_table_destroy(h)
+
+
+def load_sweep(args, api, wc, h_main, keys, vals, qk, out, found, n, s, peak, rank, local_rank):
+    """The paper's density sweep (Sec. V-A) on the default workload: for every target load
+    of --alphas, a table of the bench's kind (same options and shapes as the headline
+    table) is filled with the 2^27 pairs and queried with the 2^27 half-absent queries;
+    insert and retrieve are timed separately with CUDA events (median of the steps), and
+    every table is checked (size, no status flag, found count) before it is timed."""
+    import torch
+    info_main = api.wc_table_get_info(h_main)
+    rows = []
+    steps = max(3, min(args.steps, 10))
+    for a in (float(x) for x in args.alphas.split(",") if x.strip()):
+        h = api.wc_table_create(wc.WC_SINGLE_VALUE, 4, 4, int(np.ceil(n / a)), args.window, 0, 0x5EEDC0DE + rank,
+                                local_rank, options=info_main["options"])
+        info = api.wc_table_get_info(h)
+        ins, ret = [], []
+        for i in range(2 + steps):
+            api.wc_table_clear(h, s)
+            ti = timed(s, lambda: api.wc_insert(h, keys, vals, n, s))
+            tr = timed(s, lambda: api.wc_retrieve(h, qk, out, found, n, s))
+            if i == 0:
+                assert api.wc_size(h) == n and api.wc_get_status(h, clear=True) == 0, a
+                assert int(found.sum().item()) == n // 2, a
+            if i >= 2:
+                ins.append(ti)
+                ret.append(tr)
+        im, rm = statistics.median(ins), statistics.median(ret)
+        rows.append({"target_alpha": a, "achieved_alpha": n / info["capacity"], "capacity": info["capacity"],
+                     "insert_gops": n / (im * 1e-3) / 1e9, "retrieve_gops": n / (rm * 1e-3) / 1e9,
+                     "insert_ms": im, "retrieve_ms": rm,
+                     "insert_frac": BYTES_PER_OP["insert"] * n / (im * 1e-3) / 1e9 / peak,
+                     "retrieve_frac": BYTES_PER_OP["retrieve"] * n / (rm * 1e-3) / 1e9 / peak})
+        api.wc_table_destroy(h)
+    torch.cuda.synchronize()
+    return rows
 
 
 def _common(args, workload_name, metric, value, unit, ms_step, dtype, config, clk, launches, extra):

@@ -261,11 +261,16 @@ wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint6
  * WC_NOALLOC_SCRATCH_BYTES that the library holds in every context that loads it, until
  * the process exits.  n may be at most WC_NOALLOC_SCRATCH_BYTES / (key_bytes +
  * value_bytes) minus a few elements (2,097,088 pairs of 4+4 bytes; 1,048,544 of 8+8);
- * larger n returns WC_ERR_INVALID_ARG -- split the batch.  The first call on a device
- * looks up the buffer's device address with that device current; make that first call
- * before capturing any stream.  All calls on a device share the buffer: calls whose GPU
- * work may overlap (different streams with no ordering) race and must be ordered by the
- * caller.  Multi-value tables return WC_ERR_UNSUPPORTED. */
+ * larger n returns WC_ERR_INVALID_ARG -- split the batch.  Keys and values must be memory
+ * the table's device can reach, as for wc_insert (pageable host memory or another GPU's
+ * memory: WC_ERR_INVALID_ARG).  The first call on a device (and the first after that
+ * device's context was reset) looks up the buffer's device address with that device
+ * current; under lazy module loading that lookup is also what places the buffer on the
+ * device, so it can fail with WC_ERR_OUT_OF_MEMORY when the device is full: make that first
+ * call early, and before capturing any stream.  All calls on a device share the buffer,
+ * which keeps what the last call left in it: calls whose GPU work may overlap (different
+ * streams with no ordering) race and must be ordered by the caller.  Multi-value and
+ * struct-of-arrays tables return WC_ERR_UNSUPPORTED. */
 #define WC_NOALLOC_SCRATCH_BYTES (16ull << 20)
 wc_status wc_insert_noalloc(wc_table* t, const void* d_keys, const void* d_values, uint64_t n,
                             void* stream);
@@ -288,7 +293,9 @@ wc_status wc_insert_host(wc_table* t, const void* h_keys, const void* h_values, 
  * of d_keys[i], or all ones
  * (NOT_FOUND) when absent; d_found_or_null[i] = 1/0 when the mask is given (a stored value
  * may itself be all ones).  Probing stops at the key or at the first window holding an
- * empty slot.  Multi-value tables return WC_ERR_UNSUPPORTED. */
+ * empty slot; in tables with WC_OPT_OVERFLOW_BITS also at the first window without the
+ * key whose overflow bit for the key's tag is clear (no key of that tag was ever placed
+ * beyond it).  Multi-value tables return WC_ERR_UNSUPPORTED. */
 wc_status wc_retrieve(wc_table* t, const void* d_keys, uint64_t n, void* d_values_out,
                       uint8_t* d_found_or_null, void* stream);
 

@@ -29,7 +29,7 @@ def build(force: bool = False) -> str:
     """Compile oracle.cpp into liboracle.so next to it (portable flags: x86 and Arm)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", tmp])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-pthread", "-shared", "-fPIC", _SRC, "-o", tmp])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -77,6 +77,18 @@ def _load():
         lib.oracle_build_packed_table.argtypes = [vp, vp, u64, u64, u32, u64, vp, vp]
         lib.oracle_walk_stats.argtypes = [vp, u64, u32, u32, u32, u64, vp, vp, u64, vp]
         lib.oracle_overflow_bits_of.argtypes = [vp, u64, u32, u32, u32, u64, vp]
+        lib.oracle_sharded_create.restype = vp
+        lib.oracle_sharded_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.oracle_sharded_destroy.argtypes = [vp]
+        lib.oracle_sharded_insert.restype = u32
+        lib.oracle_sharded_insert.argtypes = [vp, vp, vp, u64]
+        lib.oracle_sharded_retrieve.restype = u32
+        lib.oracle_sharded_retrieve.argtypes = [vp, vp, u64, vp, vp]
+        lib.oracle_sharded_erase.restype = u32
+        lib.oracle_sharded_erase.argtypes = [vp, vp, u64]
+        lib.oracle_sharded_size.restype = u64
+        lib.oracle_sharded_size.argtypes = [vp]
+        lib.oracle_sharded_reserve.argtypes = [vp, u64]
         lib.oracle_bloom_create.restype = vp
         lib.oracle_bloom_create.argtypes = [ctypes.c_int, u64, ctypes.c_int, u64]
         lib.oracle_bloom_destroy.argtypes = [vp]
@@ -148,6 +160,51 @@ class SingleValue(_Base):
         found = np.empty(k.size, dtype=np.uint8)
         flags = int(self._lib.oracle_retrieve(self._h, _ptr(k), k.size, _ptr(out), _ptr(found)))
         return out, found, flags
+
+
+class ShardedSingleValue:
+    """The single-value definition on `threads` host cores: one plain std::unordered_map
+    per shard, key k in shard std::hash(k) mod threads, each batch applied by one thread
+    per shard walking it in input order.  Every result equals SingleValue's."""
+
+    def __init__(self, key_bytes: int = 4, value_bytes: int = 4, threads: int | None = None):
+        self._lib = _load()
+        self.threads = int(threads or os.cpu_count() or 1)
+        self.kdt, self.vdt = _dt(key_bytes), _dt(value_bytes)
+        self._h = self._lib.oracle_sharded_create(key_bytes, value_bytes, self.threads)
+        if not self._h:
+            raise ValueError("unsupported key/value widths")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.oracle_sharded_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def insert(self, keys, values) -> int:
+        k = np.ascontiguousarray(keys, dtype=self.kdt)
+        v = np.ascontiguousarray(values, dtype=self.vdt)
+        assert k.size == v.size
+        return int(self._lib.oracle_sharded_insert(self._h, _ptr(k), _ptr(v), k.size))
+
+    def retrieve(self, keys):
+        k = np.ascontiguousarray(keys, dtype=self.kdt)
+        out = np.empty(k.size, dtype=self.vdt)
+        found = np.empty(k.size, dtype=np.uint8)
+        flags = int(self._lib.oracle_sharded_retrieve(self._h, _ptr(k), k.size, _ptr(out), _ptr(found)))
+        return out, found, flags
+
+    def erase(self, keys) -> int:
+        k = np.ascontiguousarray(keys, dtype=self.kdt)
+        return int(self._lib.oracle_sharded_erase(self._h, _ptr(k), k.size))
+
+    def size(self) -> int:
+        return int(self._lib.oracle_sharded_size(self._h))
+
+    def reserve(self, n: int):
+        self._lib.oracle_sharded_reserve(self._h, int(n))
 
 
 class MultiValue(_Base):

@@ -25,6 +25,8 @@
 // Flag bits match the meaning (not the code) of the library's device status word.
 #include <cstdint>
 #include <cstring>
+#include <functional>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -38,6 +40,8 @@ bool is_sentinel(K k) { return k == K(0) || k == K(~K(0)); }
 
 template <class K, class V>
 struct SV {
+  using Key = K;
+  using Val = V;
   std::unordered_map<K, V> m;
 
   uint32_t insert(const K* keys, const V* vals, uint64_t n) {
@@ -259,6 +263,138 @@ void oracle_reserve(void* p, uint64_t n) {
   auto* h = static_cast<Handle*>(p);
   if (h->kind == 0) dispatch<SV>(h, [&](auto* t) { t->m.reserve(n); return 0; });
   else dispatch<MV>(h, [&](auto* t) { t->m.reserve(n); return 0; });
+}
+
+}  // extern "C"
+
+// ---- sharded single-value table (the multi-core form of the same definition) ----------
+// T single-value maps; key k belongs to shard std::hash<K>()(k) mod T.  Thread t walks
+// every batch in input order and applies the elements of its own shard to its own map,
+// so every key sees its operations in batch order, in one map: the results are those of
+// the single map above (every flag, value and found bit), only computed on T cores.
+namespace {
+
+template <class K, class V>
+struct Sharded {
+  std::vector<SV<K, V>> shards;
+  explicit Sharded(int t) : shards(static_cast<size_t>(t)) {}
+  int T() const { return static_cast<int>(shards.size()); }
+  bool mine(K k, int t) const { return std::hash<K>()(k) % static_cast<size_t>(T()) == static_cast<size_t>(t); }
+
+  template <class F>
+  uint32_t each(F f) {
+    std::vector<uint32_t> flags(shards.size(), 0u);
+    std::vector<std::thread> th;
+    for (int t = 0; t < T(); ++t) th.emplace_back([&, t] { flags[t] = f(t); });
+    for (auto& x : th) x.join();
+    uint32_t all = 0;
+    for (uint32_t x : flags) all |= x;
+    return all;
+  }
+  uint32_t insert(const K* keys, const V* vals, uint64_t n) {
+    return each([&](int t) {
+      uint32_t f = 0;
+      for (uint64_t i = 0; i < n; ++i) {
+        if (is_sentinel(keys[i])) { f |= F_INVALID; continue; }
+        if (mine(keys[i], t)) f |= shards[t].insert(keys + i, vals + i, 1);
+      }
+      return f;
+    });
+  }
+  uint32_t retrieve(const K* keys, uint64_t n, V* out, uint8_t* found) {
+    return each([&](int t) {
+      uint32_t f = 0;
+      for (uint64_t i = 0; i < n; ++i) {
+        if (is_sentinel(keys[i])) {
+          if (t == 0) f |= shards[0].retrieve(keys + i, 1, out + i, found ? found + i : nullptr);
+          continue;
+        }
+        if (mine(keys[i], t)) f |= shards[t].retrieve(keys + i, 1, out + i, found ? found + i : nullptr);
+      }
+      return f;
+    });
+  }
+  uint32_t erase(const K* keys, uint64_t n) {
+    return each([&](int t) {
+      uint32_t f = 0;
+      for (uint64_t i = 0; i < n; ++i) {
+        if (is_sentinel(keys[i])) { f |= F_INVALID; continue; }
+        if (mine(keys[i], t)) f |= shards[t].erase(keys + i, 1);
+      }
+      return f;
+    });
+  }
+  uint64_t size() const {
+    uint64_t s = 0;
+    for (const auto& x : shards) s += x.m.size();
+    return s;
+  }
+  void reserve(uint64_t n) {
+    for (auto& x : shards) x.m.reserve(n / shards.size() + 1);
+  }
+};
+
+template <class F>
+auto sharded_dispatch(Handle* h, F&& f) {
+  if (h->kb == 4 && h->vb == 4) return f(static_cast<Sharded<uint32_t, uint32_t>*>(h->impl));
+  if (h->kb == 8 && h->vb == 8) return f(static_cast<Sharded<uint64_t, uint64_t>*>(h->impl));
+  if (h->kb == 8 && h->vb == 4) return f(static_cast<Sharded<uint64_t, uint32_t>*>(h->impl));
+  return f(static_cast<Sharded<uint32_t, uint64_t>*>(h->impl));
+}
+
+}  // namespace
+
+extern "C" {
+
+void* oracle_sharded_create(int key_bytes, int value_bytes, int threads) {
+  if (!valid_widths(key_bytes, value_bytes) || threads < 1) return nullptr;
+  auto* h = new Handle{2, key_bytes, value_bytes, nullptr};
+  if (key_bytes == 4 && value_bytes == 4) h->impl = new Sharded<uint32_t, uint32_t>(threads);
+  else if (key_bytes == 8 && value_bytes == 8) h->impl = new Sharded<uint64_t, uint64_t>(threads);
+  else if (key_bytes == 8) h->impl = new Sharded<uint64_t, uint32_t>(threads);
+  else h->impl = new Sharded<uint32_t, uint64_t>(threads);
+  return h;
+}
+
+void oracle_sharded_destroy(void* p) {
+  auto* h = static_cast<Handle*>(p);
+  if (!h) return;
+  sharded_dispatch(h, [](auto* t) { delete t; return 0; });
+  delete h;
+}
+
+uint32_t oracle_sharded_insert(void* p, const void* keys, const void* vals, uint64_t n) {
+  return sharded_dispatch(static_cast<Handle*>(p), [&](auto* t) {
+    using M = std::remove_pointer_t<decltype(t)>;
+    using K = typename decltype(M::shards)::value_type::Key;
+    using V = typename decltype(M::shards)::value_type::Val;
+    return t->insert(static_cast<const K*>(keys), static_cast<const V*>(vals), n);
+  });
+}
+
+uint32_t oracle_sharded_retrieve(void* p, const void* keys, uint64_t n, void* out, uint8_t* found) {
+  return sharded_dispatch(static_cast<Handle*>(p), [&](auto* t) {
+    using M = std::remove_pointer_t<decltype(t)>;
+    using K = typename decltype(M::shards)::value_type::Key;
+    using V = typename decltype(M::shards)::value_type::Val;
+    return t->retrieve(static_cast<const K*>(keys), n, static_cast<V*>(out), found);
+  });
+}
+
+uint32_t oracle_sharded_erase(void* p, const void* keys, uint64_t n) {
+  return sharded_dispatch(static_cast<Handle*>(p), [&](auto* t) {
+    using M = std::remove_pointer_t<decltype(t)>;
+    using K = typename decltype(M::shards)::value_type::Key;
+    return t->erase(static_cast<const K*>(keys), n);
+  });
+}
+
+uint64_t oracle_sharded_size(void* p) {
+  return sharded_dispatch(static_cast<Handle*>(p), [](auto* t) { return t->size(); });
+}
+
+void oracle_sharded_reserve(void* p, uint64_t n) {
+  sharded_dispatch(static_cast<Handle*>(p), [&](auto* t) { t->reserve(n); return 0; });
 }
 
 }  // extern "C"

@@ -323,6 +323,38 @@ wc_status wc_plan_capacity(uint64_t min_capacity, int32_t window_width, uint64_t
   return WC_OK;
 }
 
+// The persisting-L2 carve-out (cudaLimitPersistingL2CacheSize) is a limit of the device's
+// context, shared by every table with l2_persist.  The first such table on a device
+// records the limit it found; when the last one is destroyed, the persisting lines are
+// turned back into normal ones and the limit is put back, so later work in the process
+// gets the whole L2 again.
+namespace {
+std::mutex g_l2_mu;
+struct L2Hold {
+  int tables = 0;
+  size_t before = 0;
+};
+L2Hold g_l2_hold[64];
+}  // namespace
+
+static void l2_carveout_hold(wc_table* t, size_t limit_now) {
+  if (t->device < 0 || t->device >= 64) return;
+  std::lock_guard<std::mutex> lock(g_l2_mu);
+  if (g_l2_hold[t->device].tables++ == 0) g_l2_hold[t->device].before = limit_now;
+  t->l2_held = true;
+}
+
+static void l2_carveout_release(wc_table* t) {
+  if (!t->l2_held) return;
+  std::lock_guard<std::mutex> lock(g_l2_mu);
+  t->l2_held = false;
+  if (--g_l2_hold[t->device].tables > 0) return;
+  cudaDeviceSynchronize();  // no kernel of this table still reads with the window
+  cudaCtxResetPersistingL2Cache();
+  cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, g_l2_hold[t->device].before);
+  cudaGetLastError();
+}
+
 wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   if (out == nullptr || cfg == nullptr) return WC_ERR_INVALID_ARG;
   *out = nullptr;
@@ -459,6 +491,7 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
       const size_t persist = std::min<size_t>(t->table_bytes, static_cast<size_t>(max_persist));
       size_t cur = 0;
       cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+      l2_carveout_hold(t, cur);
       if (cur < persist) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, persist);
       cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
       t->l2_window_bytes = std::min<size_t>(t->table_bytes, static_cast<size_t>(max_window));
@@ -488,6 +521,7 @@ wc_status wc_table_destroy(wc_table* t) {
   if (t == nullptr) return WC_ERR_INVALID_ARG;
   DeviceGuard guard(t->device);
   host_pipe_free(t);
+  l2_carveout_release(t);
   if (t->d_scratch != nullptr) {
     cudaDeviceSynchronize();
     cudaFree(t->d_scratch);
@@ -547,23 +581,7 @@ wc_status wc_table_get_launch(const wc_table* t, int32_t op, wc_launch* h_out) {
   return WC_OK;
 }
 
-// A buffer the table's kernels may read or write: device memory of the table's device
-// (or managed memory), or host memory mapped into the device's address space at the same
-// address (pinned with cudaHostAlloc / cudaMallocHost, or registered mapped) -- on GB300
-// the kernels then move it over NVLink-C2C themselves.  Anything else would fault on the
-// device and is refused here.
-static bool device_accessible(const wc_table* t, const void* p) {
-  if (p == nullptr) return false;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  if (a.type == cudaMemoryTypeManaged) return true;
-  if (a.type == cudaMemoryTypeDevice) return a.device == t->device;
-  if (a.type == cudaMemoryTypeHost) return a.devicePointer == p;
-  return false;  // unregistered host memory
-}
+static bool device_accessible(const wc_table* t, const void* p) { return wc::device_accessible(t->device, p); }
 
 static wc_status check_buffer(const wc_table* t, const void* p, uint64_t n, uint64_t align) {
   if (n == 0) return WC_OK;

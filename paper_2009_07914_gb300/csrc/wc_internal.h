@@ -44,6 +44,24 @@ inline wc_status cuda_status(cudaError_t e) {
   return WC_ERR_CUDA;
 }
 
+// A buffer the kernels of a table on `device` may read or write: device memory of that
+// device (or managed memory), or host memory mapped into the device's address space at
+// the same address (pinned with cudaHostAlloc / cudaMallocHost, or registered mapped) --
+// on GB300 the kernels then move it over NVLink-C2C themselves.  Anything else would
+// fault on the device and is refused by the host calls.
+inline bool device_accessible(int device, const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  if (a.type == cudaMemoryTypeDevice) return a.device == device;
+  if (a.type == cudaMemoryTypeHost) return a.devicePointer == p;
+  return false;  // unregistered host memory
+}
+
 // What every single-value / key-store kernel needs, passed by value.
 struct TableDesc {
   void* slots;                       // p * W slots, 256-byte aligned
@@ -120,6 +138,7 @@ struct wc_table {
   wc_launch launch[WC_OP__N];
   size_t l2_window_bytes;  // > 0: launch with an L2 access-policy window over the slots
   float l2_hit_ratio;
+  bool l2_held = false;    // counted in its device's persisting-L2 carve-out (released on destroy)
   // scratch for the blocked scheme, grown on demand (stream-ordered allocation)
   mutable void* d_scratch;
   mutable uint64_t scratch_bytes;

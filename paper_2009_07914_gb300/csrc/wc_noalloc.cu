@@ -13,6 +13,7 @@
 // it; the counters a call needs zeroed are cleared by that call.  Two calls whose work
 // overlaps on the GPU (different streams, no ordering between them) race on the buffer
 // and give wrong results: order them (same stream, or events).
+#include <cuda.h>  // driver API types; the two driver calls are reached through the runtime
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,21 +36,57 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Device address of g_noalloc_scratch on each device (host code cannot use the symbol
-// itself as an address).  Filled once per device, with that device current.
+// Identity of the CUDA context current on this thread (cuCtxGetId: unique for the life of
+// the process), through the runtime's driver entry-point query, so that the library needs
+// no link against the driver library.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+cudaError_t current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (get_current == nullptr || get_id == nullptr) {
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = cudaDriverEntryPointSymbolNotFound;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess) return e;
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return cudaErrorNotSupported;
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return cudaErrorDeviceUninitialized;
+  if (get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  return cudaSuccess;
+}
+
+// Device address of g_noalloc_scratch in the current context of each device (host code
+// cannot use the symbol itself as an address: in host code it names a host-side shadow).
+// Looked up once per device, with that device current, and looked up again if the device's
+// context changed since (after cudaDeviceReset the old address is gone).
 std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
+struct Cached {
+  unsigned long long ctx;
+  void* addr;
+};
+Cached g_addr[kMaxDevices] = {};
 
 cudaError_t scratch_address(int device, void** out) {
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  unsigned long long ctx = 0;
+  cudaError_t e = current_context_id(&ctx);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (g_addr[device] == nullptr) {
+  if (g_addr[device].addr == nullptr || g_addr[device].ctx != ctx) {
     void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // loads this file's module on first use
     if (e != cudaSuccess) return e;
-    g_addr[device] = p;
+    g_addr[device] = Cached{ctx, p};
   }
-  *out = g_addr[device];
+  *out = g_addr[device].addr;
   return cudaSuccess;
 }
 
@@ -87,8 +124,12 @@ cudaError_t run(const wc_table* t, const void* keys, const void* vals, uint64_t 
   const unsigned sg = static_cast<unsigned>(
       std::min<uint64_t>(ntiles, static_cast<uint64_t>(occupancy_smem(sk, kPartThreads, ssm)) * t->sm_count));
   hk<<<hg, kPartThreads, hsm, s>>>(static_cast<const Key*>(keys), n, m, hist);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   sk<<<sg, kPartThreads, ssm, s>>>(static_cast<const Key*>(keys), static_cast<const Val*>(vals), n, m, hist, cursor,
                                    pk, pv);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;  // no insert over a split that was never written
   const int block = lc.block_threads;
   const int bps = lc.blocks_per_sm > 0 ? lc.blocks_per_sm : occupancy(ik, block);
   return launch_k(t, ik, static_cast<unsigned>(bps) * static_cast<unsigned>(t->sm_count), block, 0, s, desc_of(t),
@@ -122,6 +163,7 @@ cudaError_t dispatch(const wc_table* t, const void* keys, const void* vals, uint
 
 extern "C" wc_status wc_insert_noalloc(wc_table* t, const void* d_keys, const void* d_values, uint64_t n,
                                        void* stream) {
+  wc::TraceRange trace("wc_insert_noalloc");
   if (t == nullptr || t->cfg.kind != WC_SINGLE_VALUE || t->d_vals != nullptr)
     return t == nullptr ? WC_ERR_INVALID_ARG : WC_ERR_UNSUPPORTED;
   const uint64_t pair = static_cast<uint64_t>(t->cfg.key_bytes) + static_cast<uint64_t>(t->cfg.value_bytes);
@@ -132,13 +174,18 @@ extern "C" wc_status wc_insert_noalloc(wc_table* t, const void* d_keys, const vo
   if (reinterpret_cast<uintptr_t>(d_keys) % static_cast<uint64_t>(t->cfg.key_bytes) ||
       reinterpret_cast<uintptr_t>(d_values) % static_cast<uint64_t>(t->cfg.value_bytes))
     return WC_ERR_INVALID_ARG;
+  // buffers the kernels cannot reach (pageable host memory, another GPU's memory) would
+  // fault on the device: refused here, as wc_insert refuses them
+  if (!wc::device_accessible(t->device, d_keys) || !wc::device_accessible(t->device, d_values))
+    return WC_ERR_INVALID_ARG;
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) return WC_ERR_CUDA;
-  if (prev != t->device && cudaSetDevice(t->device) != cudaSuccess) return WC_ERR_CUDA;
+  // made current even when it already is: that also makes its primary context current
+  if (cudaSetDevice(t->device) != cudaSuccess) return WC_ERR_CUDA;
   void* sc = nullptr;
   cudaError_t e = wc::scratch_address(t->device, &sc);
   if (e == cudaSuccess)
     e = wc::dispatch(t, d_keys, d_values, n, static_cast<char*>(sc), static_cast<cudaStream_t>(stream));
   if (prev != t->device) cudaSetDevice(prev);
-  return e == cudaSuccess ? WC_OK : WC_ERR_CUDA;
+  return wc::cuda_status(e);  // an out-of-memory error keeps its own code
 }

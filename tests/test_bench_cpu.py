@@ -33,7 +33,9 @@ def test_reference_arm_prints_the_contract_line():
     assert d["higher_is_better"] is True and d["vs_baseline"] is None
     assert d["config"]["workload"] == "sv_u32_n2^27_alpha0.90"
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    # the sharded oracle on every host core, with the single-thread form beside it
+    assert cb["kind"] == "oracle" and cb["cores"] == os.cpu_count() and cb["value"] == d["value"] and cb["sample"]
+    assert cb["single_thread"]["cores"] == 1 and cb["single_thread"]["value"] > 0
     assert cb["host"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 

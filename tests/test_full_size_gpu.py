@@ -29,21 +29,39 @@ def _sample(n, k, seed):
     return wc_inputs.shuffle_index(seed, n)[:k]
 
 
-@pytest.mark.parametrize("opts", [0, 1])
-def test_sv_u32_2e27_load_0p9(env, opts):
-    """The bench's default workload and table (opts = 1: with overflow bits, as bench.py
-    times it); with the bits, the whole slot dump passes the reachability check and the
-    dumped bits equal the ones the oracle derives from it."""
-    wc, api, torch, to_device, to_numpy = env
-    dev = torch.device("cuda", 0)
+@pytest.fixture(scope="module")
+def sv27():
+    """The 2^27-pair workload of the single-value load sweep, generated once per module."""
     n = 1 << 27
-    d = wc_inputs.sv_insert_retrieve_u32(0x57C00002, n, n // 2, n // 2)
+    return n, wc_inputs.sv_insert_retrieve_u32(0x57C00002, n, n // 2, n // 2)
+
+
+# (target load, table options): the bench's table (overflow bits) at every load of the
+# paper's density sweep (Sec. V-A), and the plain table at the headline load.
+SWEEP = [(0.9, 0), (0.9, 1), (0.5, 1), (0.8, 1), (0.95, 1), (0.99, 1)]
+
+
+@pytest.mark.parametrize("alpha,opts", SWEEP, ids=["a%.2f-o%d" % x for x in SWEEP])
+def test_sv_u32_2e27_load_sweep(env, sv27, alpha, opts):
+    """2^27 unique uint32 pairs inserted at target load alpha, then 2^26 present + 2^26
+    absent queries, in the bench's launch configuration (opts = 1: overflow bits, as
+    bench.py times it).  Checked: no status flag (in particular no PROBE_LIMIT) and the
+    exact size; found mask and values of every query against the generator's bookkeeping;
+    a sample against the oracle; with the bits, the whole slot dump passes the
+    reachability check and the dumped bits equal the ones the oracle derives from it;
+    then an erase of 2^20 keys."""
+    wc, api, torch, to_device, to_numpy = env
+    n, d = sv27
+    dev = torch.device("cuda", 0)
     keys, vals, q = (to_device(d[k], 4, dev) for k in ("keys", "values", "queries"))
-    h = api.wc_table_create(0, 4, 4, int(np.ceil(n / 0.9)), 0, 0, 0x5EEDC0DE, 0, options=opts)
+    h = api.wc_table_create(0, 4, 4, int(np.ceil(n / alpha)), 0, 0, 0x5EEDC0DE, 0, options=opts)
+    info = api.wc_table_get_info(h)
+    assert n / info["capacity"] <= alpha and n / info["capacity"] > alpha - 0.001
     api.wc_insert(h, keys, vals)
-    assert api.wc_size(h) == n and api.wc_get_status(h, True) == 0
+    del keys, vals
+    assert api.wc_get_status(h, True) == 0, "status flags after the insert"
+    assert api.wc_size(h) == n
     if opts:
-        info = api.wc_table_get_info(h)
         dump = api.wc_table_dump_slots(h)
         bits = api.wc_table_dump_overflow_bits(h)
         r = oracle.check_slots(dump, info["windows"], info["window_width"], info["slot_bytes"], 0x5EEDC0DE, False,
@@ -51,10 +69,11 @@ def test_sv_u32_2e27_load_0p9(env, opts):
         assert r == {"live": n, "dups": 0, "unreachable": 0}
         expect = oracle.overflow_bits_of(dump, info["windows"], info["window_width"], info["slot_bytes"], 0x5EEDC0DE)
         assert np.array_equal(bits.view(np.uint8)[:info["windows"]], expect)
-        del dump
+        del dump, bits, expect
     out = torch.empty(n, dtype=torch.int32, device=dev)
     found = torch.empty(n, dtype=torch.uint8, device=dev)
     api.wc_retrieve(h, q, out, found)
+    assert api.wc_get_status(h, True) == 0
     f = found.cpu().numpy()
     o = to_numpy(out, 4)
     pres = d["q_src"] >= 0
@@ -74,6 +93,13 @@ def test_sv_u32_2e27_load_0p9(env, opts):
     assert api.wc_size(h) == n - (1 << 20)
     api.wc_retrieve(h, to_device(drop, 4, dev), out, found, n=drop.size)
     assert not found[: drop.size].any().item()
+    api.wc_retrieve(h, q, out, found)
+    keep = np.ones(n, dtype=bool)
+    keep[_sample(n, 1 << 20, 2)] = False  # positions of the erased keys in d["keys"]
+    still = pres.copy()
+    still[pres] = keep[d["q_src"][pres]]
+    assert np.array_equal(found.cpu().numpy(), still.astype(np.uint8))
+    assert api.wc_get_status(h, True) == 0
     api.wc_table_destroy(h)
 
 

@@ -8,7 +8,8 @@
   exclusive prefix sum with offsets[n] = total);
 * the paper's multi-value benchmark invariant (Sec. V-C): keys from 1..n/r queried over
   1..n return exactly n values;
-* hand-derived worked examples under tests/golden/ (each line cites its section).
+* hand-derived worked examples under tests/golden/ (each line cites its section);
+* the sharded multi-core form of the single-value oracle against the same brute force.
 """
 from __future__ import annotations
 
@@ -107,6 +108,38 @@ def test_sv_oracle_matches_brute_force(kb, vb, seed):
         if op == 0:
             vs = rng.integers(0, vmax, m, dtype=np.uint64, endpoint=True).astype(vdt)
             # the oracle applies a batch in call order; so does the brute force
+            assert o.insert(ks, vs) == b.insert([int(x) for x in ks], [int(x) for x in vs])
+        elif op == 1:
+            assert o.erase(ks) == b.erase([int(x) for x in ks])
+        else:
+            out, found, f = o.retrieve(ks)
+            bo, bf, bfl = b.retrieve([int(x) for x in ks], vmax)
+            assert [int(x) for x in out] == bo
+            assert [int(x) for x in found] == bf
+            assert f == bfl
+        assert o.size() == len(b.pairs)
+
+
+@pytest.mark.parametrize("kb,vb", [(4, 4), (8, 8)])
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_sharded_sv_oracle_matches_brute_force(kb, vb, threads):
+    """The sharded (multi-core) single-value oracle against the same linear-scan brute
+    force, on batches that repeat keys inside one batch (so a shard's input order
+    matters) and mix erase and sentinels."""
+    kmax = (1 << (8 * kb)) - 1
+    vmax = (1 << (8 * vb)) - 1
+    kdt = np.uint32 if kb == 4 else np.uint64
+    vdt = np.uint32 if vb == 4 else np.uint64
+    rng = np.random.default_rng(100 + threads)
+    o = oracle.ShardedSingleValue(kb, vb, threads=threads)
+    b = BruteSV(kmax)
+    universe = np.array([0, kmax] + list(rng.integers(1, kmax, 60, dtype=np.uint64)), dtype=np.uint64)
+    for step in range(80):
+        op = rng.integers(0, 3)
+        m = int(rng.integers(0, 40))
+        ks = universe[rng.integers(0, universe.size, m)].astype(kdt)
+        if op == 0:
+            vs = rng.integers(0, vmax, m, dtype=np.uint64, endpoint=True).astype(vdt)
             assert o.insert(ks, vs) == b.insert([int(x) for x in ks], [int(x) for x in vs])
         elif op == 1:
             assert o.erase(ks) == b.erase([int(x) for x in ks])

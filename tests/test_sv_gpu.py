@@ -476,3 +476,31 @@ def test_dedup_scheme_counting_set_and_refusals(wc):
     mv = wc.MultiValueOATable(4, 4, min_capacity=1 << 12)
     with pytest.raises(wc.WcError):
         mv.set_launch(wc.WC_OP_RETRIEVE, 2, scheme=wc.WC_SCHEME_DEDUP)
+
+
+def test_l2_persist_carveout_is_given_back(wc):
+    """Tables created with l2_persist raise the context's persisting-L2 carve-out; the
+    limit found before the first of them comes back when the last one is destroyed."""
+    import ctypes
+    rt = ctypes.CDLL("libcudart.so.13")  # the runtime instance libwc.so is linked against
+    limit_persisting_l2 = 0x06  # cudaLimitPersistingL2CacheSize
+
+    def limit():
+        v = ctypes.c_size_t(0)
+        assert rt.cudaDeviceGetLimit(ctypes.byref(v), limit_persisting_l2) == 0
+        return v.value
+
+    before = limit()
+    a = wc.SingleValueTable(4, 4, min_capacity=1 << 20, l2_persist=True)
+    b = wc.SingleValueTable(4, 4, min_capacity=1 << 19, l2_persist=True)
+    raised = limit()
+    assert raised > before
+    o = oracle.SingleValue(4, 4)
+    keys = wc_inputs.distinct_u32(0xC0FE, 1 << 18)
+    vals = wc_inputs.uniform_u32(0xC0FF, 1 << 18)
+    assert a.insert(keys, vals) == o.insert(keys, vals) == 0
+    check_retrieve(a, o, keys)
+    a.close()
+    assert limit() == raised  # b still holds it
+    b.close()
+    assert limit() == before
