@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--log2n", type=int, default=27)
     ap.add_argument("--alpha", type=float, default=0.9)
     ap.add_argument("--window", type=int, default=0)
-    ap.add_argument("--group", type=int, default=0)
+    ap.add_argument("--group", default="0",
+                    help="lanes per key: G for every operation, or G_insert,G_retrieve[,G_erase] (0 = default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access roofline probe")
@@ -231,19 +232,28 @@ def host_cpu() -> dict:
 
 
 def random_probe(dev, table_bytes: int):
-    """Live random-access roofline of this GPU over a buffer of the table's size: random
-    64 B and 32 B reads (a probing window) and 64 B read + CAS (an insert's claim)."""
+    """Live random-access ceiling of this GPU over a buffer of the table's size: the best
+    rate over probe shapes (accesses in flight per thread x lanes per access) of random
+    64 B reads (a probing window), 32 B reads, and 64 B read + CAS (an insert's claim)."""
     import torch
     from paper_2009_07914_gb300 import roofline as R
     nbytes = max(1 << 26, (table_bytes + 255) // 256 * 256)
     buf = torch.zeros(nbytes, dtype=torch.uint8, device=dev)
     out = {"buffer_bytes": nbytes}
     for ab, mode, key in ((64, 0, "rd64_gps"), (32, 0, "rd32_gps"), (64, 1, "rmw64_gps")):
-        r = R.random_access_rate(buf, ab, mode, accesses=1 << 26, reps=2)
+        r = R.best_rate(buf, ab, mode, accesses=1 << 26)
         out[key] = r["accesses_per_s"] / 1e9
+        out[key.replace("_gps", "_shape")] = {"in_flight": r["in_flight"], "lanes": r["lanes"]}
     del buf
     torch.cuda.empty_cache()
     return out
+
+
+def random_bound(stream_bytes: float, window_rate_gps: float, bw_gbs: float) -> float:
+    """The method's bound in G ops/s when every op streams `stream_bytes` through HBM and
+    makes one random window access at the measured ceiling `window_rate_gps`:
+    1 / (stream_B / BW + 1 / R_window)."""
+    return 1.0 / (stream_bytes / bw_gbs + 1.0 / window_rate_gps)
 
 
 def insert_launches(api, h, n: int) -> int:
@@ -341,9 +351,7 @@ def run_wc(args, rank, world, local_rank):
     h = api.wc_table_create(wc.WC_SINGLE_VALUE, 4, 4, int(np.ceil(n / args.alpha)), args.window, 0,
                             0x5EEDC0DE + rank, local_rank, options=opts)
     info = api.wc_table_get_info(h)
-    if args.group:
-        for op in (wc.WC_OP_INSERT, wc.WC_OP_RETRIEVE, wc.WC_OP_ERASE):
-            api.wc_table_set_launch(h, op, args.group)
+    apply_groups(api, wc, h, args.group)
     g_ins = api.wc_table_get_launch(h, wc.WC_OP_INSERT)["group_size"]
     g_ret = api.wc_table_get_launch(h, wc.WC_OP_RETRIEVE)["group_size"]
     s = torch.cuda.current_stream()
@@ -471,10 +479,28 @@ def run_wc(args, rank, world, local_rank):
         pr = random_probe(dev, info["table_bytes"])
         # retrieve reads ~1 window of W slots per present key and a few per absent key;
         # report the query rate against the random-window read rate of the same buffer
-        res["random_roofline"] = dict(pr, retrieve_frac_of_rd64=res["retrieve_gops"] / pr["rd64_gps"],
-                                      insert_frac_of_rmw64=res["insert_gops"] / pr["rmw64_gps"])
+        ret_bound = random_bound(9, pr["rd64_gps"], peak)
+        ins_bound = random_bound(8, pr["rmw64_gps"], peak)
+        res["random_roofline"] = dict(pr, retrieve_bound_gops=ret_bound, insert_bound_gops=ins_bound,
+                                      retrieve_frac_of_rd64=res["retrieve_gops"] / pr["rd64_gps"],
+                                      insert_frac_of_rmw64=res["insert_gops"] / pr["rmw64_gps"],
+                                      retrieve_frac_of_bound=res["retrieve_gops"] / ret_bound,
+                                      insert_frac_of_bound=res["insert_gops"] / ins_bound,
+                                      formula="1 / (stream_B / BW + 1 / R_window): retrieve 9 B streamed + one 64 B "
+                                              "random read, insert 8 B + one 64 B random read + CAS")
     print(json.dumps(res), flush=True)
     api.wc_table_destroy(h)
+
+
+def apply_groups(api, wc, h, spec: str):
+    """--group: one lane count for every operation, or one per operation (insert,
+    retrieve[, erase]); 0 keeps the table's default."""
+    gs = [int(x) for x in str(spec).split(",") if x.strip()]
+    if len(gs) == 1:
+        gs = gs * 3
+    for op, g in zip((wc.WC_OP_INSERT, wc.WC_OP_RETRIEVE, wc.WC_OP_ERASE), gs):
+        if g:
+            api.wc_table_set_launch(h, op, g)
 
 
 def load_sweep(args, api, wc, h_main, keys, vals, qk, out, found, n, s, peak, rank, local_rank):
@@ -490,6 +516,7 @@ def load_sweep(args, api, wc, h_main, keys, vals, qk, out, found, n, s, peak, ra
     for a in (float(x) for x in args.alphas.split(",") if x.strip()):
         h = api.wc_table_create(wc.WC_SINGLE_VALUE, 4, 4, int(np.ceil(n / a)), args.window, 0, 0x5EEDC0DE + rank,
                                 local_rank, options=info_main["options"])
+        apply_groups(api, wc, h, args.group)
         info = api.wc_table_get_info(h)
         ins, ret = [], []
         for i in range(2 + steps):
@@ -686,9 +713,9 @@ def run_mv_oa_uniform_r(args, dev):
     out = torch.empty(n, dtype=torch.int32, device=dev)
     s = torch.cuda.current_stream()
     h = api.wc_table_create(2, 4, 4, int(np.ceil(n / 0.8)), args.window, 0, 0x5EEDC0DE, dev.index)
-    if args.group:
+    if int(args.group.split(",")[0]):
         for op in (WC_OP_INSERT, WC_OP_RETRIEVE, WC_OP_COUNT):
-            api.wc_table_set_launch(h, op, args.group, 256, 0, 0, 0)
+            api.wc_table_set_launch(h, op, int(args.group.split(",")[0]), 256, 0, 0, 0)
     info = api.wc_table_get_info(h)
     modes = [m.strip() for m in args.bucket_modes.split(",") if m.strip()]
     res = {"oa": {}}

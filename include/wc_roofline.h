@@ -5,7 +5,8 @@
  * memory (one probing window per key and probe step, Sec. IV-B2), so the library ships
  * the probes that measure that bound on the device it runs on:
  *   - random reads of `access_bytes` contiguous, aligned bytes at uniformly random
- *     positions of a buffer (the window load of a probe), and
+ *     positions of a buffer (the window load of a probe), by one thread or by a group of
+ *     adjacent threads (a probing group), with a chosen number in flight per thread, and
  *   - the same read followed by a 64-bit CAS on the first word (the slot claim of an
  *     insert), and
  *   - random stores of `access_bytes` (the scatter of per-query results back to their
@@ -31,6 +32,9 @@ typedef struct {
   uint32_t mode;           /* 0 = read only, 1 = read then CAS (old -> old + 1), 2 = store */
   uint32_t block_threads;  /* 0 = 256 */
   uint32_t blocks_per_sm;  /* 0 = occupancy limit */
+  uint32_t in_flight;      /* reads: independent accesses in flight per thread, 1/2/4/8/16 (0 = 4) */
+  uint32_t lanes;          /* reads: adjacent threads sharing one access, each reading
+                              access_bytes / lanes >= 8 bytes of it, 1/2/4 (0 = 1) */
 } wc_rand_access_config;
 
 /* Launch the probe on `stream` over d_buffer (device, buffer_bytes, 256-byte aligned).

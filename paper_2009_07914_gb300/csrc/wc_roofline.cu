@@ -13,8 +13,6 @@
 namespace wc {
 namespace {
 
-constexpr int kUnroll = 4;  // independent accesses in flight per thread
-
 // XOR of the chunk's words; `first` receives its first word.
 template <int BYTES>
 __device__ __forceinline__ unsigned long long read_chunk(const unsigned long long* p, unsigned long long& first) {
@@ -40,31 +38,38 @@ __device__ __forceinline__ unsigned long long read_chunk(const unsigned long lon
   return acc;
 }
 
-// Every load feeds `acc`, which is compared with a runtime value the compiler cannot
-// know, so no load is dead code.  In CAS mode the word just read is the CAS's expected
-// value (the claim of a slot read in the same window).
-template <int BYTES, bool kCas>
+// One access = BYTES contiguous bytes at a random BYTES-aligned position, read by a group
+// of LANES adjacent threads (lane r reads bytes [r, r + 1) * BYTES / LANES: the window load
+// of a probing group); every thread keeps U accesses in flight.  Every load feeds `acc`,
+// which is compared with a runtime value the compiler cannot know, so no load is dead
+// code.  In CAS mode lane 0 then CASes the first word of the access with the value it read
+// (the claim of a slot read in the same window).
+template <int BYTES, int LANES, int U, bool kCas>
 __global__ void __launch_bounds__(256) k_rand_access(unsigned long long* buf, uint64_t chunks, uint64_t accesses,
                                                      uint64_t seed, unsigned long long* sink) {
+  constexpr int PER = BYTES / LANES;
+  static_assert(PER >= 8 && BYTES % LANES == 0, "each lane reads whole 8-byte words");
   const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const uint64_t nth = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  const uint64_t grp = tid / LANES;
+  const int r = static_cast<int>(threadIdx.x % LANES);
+  const uint64_t ngrp = static_cast<uint64_t>(gridDim.x) * blockDim.x / LANES;
   unsigned long long acc = 0;
-  for (uint64_t base = tid; base < accesses; base += nth * kUnroll) {
-    unsigned long long* p[kUnroll];
-    unsigned long long v[kUnroll], f[kUnroll];
+  for (uint64_t base = grp; base < accesses; base += ngrp * U) {
+    unsigned long long* p[U];
+    unsigned long long v[U], f[U];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const uint64_t i = base + static_cast<uint64_t>(u) * nth;
+    for (int u = 0; u < U; ++u) {
+      const uint64_t i = base + static_cast<uint64_t>(u) * ngrp;
       const uint64_t h = fmix64(seed ^ i);
       const uint64_t c = __umul64hi(h, chunks);
-      p[u] = buf + c * (BYTES / 8);
+      p[u] = buf + c * (BYTES / 8) + r * (PER / 8);
       f[u] = 0ull;
-      v[u] = i < accesses ? read_chunk<BYTES>(p[u], f[u]) : 0ull;
+      v[u] = i < accesses ? read_chunk<PER>(p[u], f[u]) : 0ull;
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const uint64_t i = base + static_cast<uint64_t>(u) * nth;
-      if (kCas && i < accesses) acc ^= atomicCAS(p[u], f[u], f[u] + 1);
+    for (int u = 0; u < U; ++u) {
+      const uint64_t i = base + static_cast<uint64_t>(u) * ngrp;
+      if (kCas && r == 0 && i < accesses) acc ^= atomicCAS(p[u], f[u], f[u] + 1);
       acc ^= v[u];
     }
   }
@@ -103,26 +108,48 @@ cudaError_t run_write(void* buf, const wc_rand_access_config& c, cudaStream_t s)
   return cudaGetLastError();
 }
 
+template <int BYTES, int LANES, int U>
+cudaError_t launch_read(unsigned long long* b, const wc_rand_access_config& c, unsigned long long* k, int sms,
+                        cudaStream_t s) {
+  const int block = c.block_threads ? static_cast<int>(c.block_threads) : 256;
+  const uint64_t chunks = c.buffer_bytes / BYTES;
+  auto kern = c.mode == 1 ? k_rand_access<BYTES, LANES, U, true> : k_rand_access<BYTES, LANES, U, false>;
+  const int bps = c.blocks_per_sm ? static_cast<int>(c.blocks_per_sm) : occupancy(kern, block);
+  kern<<<bps * sms, block, 0, s>>>(b, chunks, c.accesses, c.seed, k);
+  return cudaGetLastError();
+}
+
+template <int BYTES, int LANES>
+cudaError_t run_lanes(unsigned long long* b, const wc_rand_access_config& c, unsigned long long* k, int sms,
+                      cudaStream_t s) {
+  if constexpr (BYTES / LANES < 8) {
+    return cudaErrorInvalidValue;
+  } else {
+    switch (c.in_flight ? c.in_flight : 4u) {
+      case 1: return launch_read<BYTES, LANES, 1>(b, c, k, sms, s);
+      case 2: return launch_read<BYTES, LANES, 2>(b, c, k, sms, s);
+      case 4: return launch_read<BYTES, LANES, 4>(b, c, k, sms, s);
+      case 8: return launch_read<BYTES, LANES, 8>(b, c, k, sms, s);
+      case 16: return launch_read<BYTES, LANES, 16>(b, c, k, sms, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+}
+
 template <int BYTES>
 cudaError_t run(void* buf, const wc_rand_access_config& c, uint64_t* sink, cudaStream_t s) {
   if (c.mode == 2) return run_write<BYTES>(buf, c, s);
-  const int block = c.block_threads ? static_cast<int>(c.block_threads) : 256;
   int dev = 0;
   cudaGetDevice(&dev);
   const int sms = sm_count_of(dev);
   auto* b = static_cast<unsigned long long*>(buf);
   auto* k = reinterpret_cast<unsigned long long*>(sink);
-  const uint64_t chunks = c.buffer_bytes / BYTES;
-  if (c.mode == 1) {
-    auto kern = k_rand_access<BYTES, true>;
-    const int bps = c.blocks_per_sm ? static_cast<int>(c.blocks_per_sm) : occupancy(kern, block);
-    kern<<<bps * sms, block, 0, s>>>(b, chunks, c.accesses, c.seed, k);
-  } else {
-    auto kern = k_rand_access<BYTES, false>;
-    const int bps = c.blocks_per_sm ? static_cast<int>(c.blocks_per_sm) : occupancy(kern, block);
-    kern<<<bps * sms, block, 0, s>>>(b, chunks, c.accesses, c.seed, k);
+  switch (c.lanes ? c.lanes : 1u) {
+    case 1: return run_lanes<BYTES, 1>(b, c, k, sms, s);
+    case 2: return run_lanes<BYTES, 2>(b, c, k, sms, s);
+    case 4: return run_lanes<BYTES, 4>(b, c, k, sms, s);
+    default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 template <int W>
@@ -197,6 +224,10 @@ wc_status wc_bench_random_access(void* d_buffer, const wc_rand_access_config* cf
     return WC_ERR_INVALID_ARG;
   if (cfg->block_threads && (cfg->block_threads > 256 || cfg->block_threads % 32)) return WC_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(d_buffer) % 256) return WC_ERR_INVALID_ARG;
+  const uint32_t lanes = cfg->lanes ? cfg->lanes : 1u, inflight = cfg->in_flight ? cfg->in_flight : 4u;
+  if (cfg->mode != 2 && ((lanes != 1 && lanes != 2 && lanes != 4) || a / lanes < 8 ||
+                         (inflight != 1 && inflight != 2 && inflight != 4 && inflight != 8 && inflight != 16)))
+    return WC_ERR_INVALID_ARG;
   if (cfg->accesses == 0) return WC_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
@@ -208,7 +239,7 @@ wc_status wc_bench_random_access(void* d_buffer, const wc_rand_access_config* cf
     case 64: e = wc::run<64>(d_buffer, *cfg, d_sink, s); break;
     default: e = wc::run<128>(d_buffer, *cfg, d_sink, s); break;
   }
-  return e == cudaSuccess ? WC_OK : WC_ERR_CUDA;
+  return e == cudaSuccess ? WC_OK : (e == cudaErrorInvalidValue ? WC_ERR_INVALID_ARG : WC_ERR_CUDA);
 }
 
 wc_status wc_set_l2_fetch_granularity(int32_t bytes) {

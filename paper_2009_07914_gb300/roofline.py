@@ -12,7 +12,7 @@ from . import _binding as B
 class WcRandAccessConfig(ctypes.Structure):
     _fields_ = [("buffer_bytes", ctypes.c_uint64), ("accesses", ctypes.c_uint64), ("seed", ctypes.c_uint64),
                 ("access_bytes", ctypes.c_uint32), ("mode", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
-                ("blocks_per_sm", ctypes.c_uint32)]
+                ("blocks_per_sm", ctypes.c_uint32), ("in_flight", ctypes.c_uint32), ("lanes", ctypes.c_uint32)]
 
 
 B.extra_signatures({
@@ -27,11 +27,12 @@ B.extra_signatures({
 
 def wc_bench_random_access(buffer: torch.Tensor, access_bytes: int, mode: int, accesses: int, sink: torch.Tensor,
                            seed: int = 1, buffer_bytes: int | None = None, block_threads: int = 0,
-                           blocks_per_sm: int = 0, stream=None):
+                           blocks_per_sm: int = 0, in_flight: int = 0, lanes: int = 0, stream=None):
     nbytes = buffer.numel() * buffer.element_size() if buffer_bytes is None else buffer_bytes
     nbytes -= nbytes % access_bytes
     cfg = WcRandAccessConfig(buffer_bytes=nbytes, accesses=accesses, seed=seed, access_bytes=access_bytes, mode=mode,
-                             block_threads=block_threads, blocks_per_sm=blocks_per_sm)
+                             block_threads=block_threads, blocks_per_sm=blocks_per_sm, in_flight=in_flight,
+                             lanes=lanes)
     B.check(B.lib().wc_bench_random_access(B.ptr(buffer), ctypes.byref(cfg), B.ptr(sink), B.stream_handle(stream)),
             "wc_bench_random_access")
 
@@ -74,6 +75,24 @@ def random_access_rate(buffer: torch.Tensor, access_bytes: int, mode: int = 0, a
             "gbs": accesses * access_bytes / (best * 1e-3) / 1e9}
 
 
+def best_rate(buffer: torch.Tensor, access_bytes: int, mode: int, accesses: int, buffer_bytes: int | None = None,
+              in_flight=(4, 8, 16), lanes=(1, 2), reps: int = 2) -> dict:
+    """The highest rate of random `access_bytes` accesses (mode 0 read, 1 read + CAS) over
+    every shape of in_flight x lanes: the memory system's ceiling for this access, not
+    the limit of one probe shape."""
+    best = None
+    for u in in_flight:
+        for g in lanes:
+            if access_bytes // g < 8:
+                continue
+            r = random_access_rate(buffer, access_bytes, mode, accesses, reps=reps, buffer_bytes=buffer_bytes,
+                                   in_flight=u, lanes=g)
+            r.update(in_flight=u, lanes=g)
+            if best is None or r["accesses_per_s"] > best["accesses_per_s"]:
+                best = r
+    return best
+
+
 def main():
     """Sweep of the random-access roofline: rate vs access size, mode, buffer size and L2
     fetch-granularity limit (one JSON line per point)."""
@@ -86,10 +105,29 @@ def main():
     ap.add_argument("--buffers-mib", default="8192,1024,64")
     ap.add_argument("--capacity-curve", action="store_true",
                     help="also sweep 64 B reads / read+CAS over buffers of 4 MiB .. 1 GiB")
+    ap.add_argument("--mlp-sweep", action="store_true",
+                    help="only: rate vs accesses in flight per thread (1..16) and lanes per access (1, 2, 4) for "
+                         "--bytes reads and read+CAS over --buffers-mib, at the default fetch granularity")
+    ap.add_argument("--in-flight", default="1,2,4,8,16", help="--mlp-sweep: accesses in flight per thread")
+    ap.add_argument("--lanes", default="1,2,4", help="--mlp-sweep: lanes per access")
+    ap.add_argument("--modes", default="0,1", help="--mlp-sweep: 0 read, 1 read + CAS")
     a = ap.parse_args()
     bufs = [int(x) for x in a.buffers_mib.split(",")]
     dev = torch.device("cuda", torch.cuda.current_device())
     buf = torch.zeros(max(bufs + [1024]) << 20, dtype=torch.uint8, device=dev)
+    if a.mlp_sweep:
+        for ab in (int(x) for x in a.bytes.split(",")):
+            for mode in (int(x) for x in a.modes.split(",")):
+                for mib in bufs:
+                    for u in (int(x) for x in a.in_flight.split(",")):
+                        for g in (int(x) for x in a.lanes.split(",")):
+                            if ab // g < 8:
+                                continue
+                            r = random_access_rate(buf, ab, mode, a.accesses, reps=2, buffer_bytes=mib << 20,
+                                                   in_flight=u, lanes=g)
+                            r.update(buffer_mib=mib, in_flight=u, lanes=g)
+                            print(json.dumps(r), flush=True)
+        return
     for g in (int(x) for x in a.gran.split(",")):
         wc_set_l2_fetch_granularity(g)
         for ab in (int(x) for x in a.bytes.split(",")):

@@ -72,3 +72,49 @@ def test_admission_respects_the_hbm_budget(env):
             np.testing.assert_array_equal(got[0], exp[0])
     serve.wc_executor_destroy(ex)
     dt.close()
+
+
+def _sharded_oracles(trace):
+    os_ = []
+    for k, v in zip(trace["prefill_keys"], trace["prefill_vals"]):
+        o = oracle.ShardedSingleValue(4, 4)
+        o.insert(k, v)
+        os_.append(o)
+    return os_
+
+
+@pytest.mark.slow
+def test_served_workload_at_its_own_scale(env):
+    """The batched + served workload at its own scale: 64 tables of capacity 2^U(16, 26)
+    pre-filled to load U(0, 0.6), 160 requests of 2^U(log2 1000, 24) keys (insert /
+    retrieve / erase 60 / 35 / 5, inserts clamped to load 0.9).  Served three times from
+    the same start -- batched with Poisson arrivals, batched closed loop, per call with
+    Poisson arrivals -- every retrieve result (values and found masks) and every table
+    size equals the oracle's with the requests applied one at a time in arrival order."""
+    serve, torch = env
+    tr = wc_inputs.serving_trace(0x57C00005, n_tables=64, n_requests=160)
+    nreq = len(tr["requests"])
+    assert max(r["keys"].size for r in tr["requests"]) > (1 << 22)
+    ors = _sharded_oracles(tr)
+    expect = _oracle_apply(ors, tr)
+    sizes = [o.size() for o in ors]
+    del ors
+    dt = serve.DeviceTrace(tr, window_width=8)
+    ex = serve.wc_executor_create(0, 8, max_items=1024, tile_keys=512)
+    poisson = wc_inputs.poisson_arrivals(0x5E5, nreq, rate_per_s=10_000.0)
+    for mode, arr in ((0, poisson), (0, np.zeros(nreq, dtype=np.uint64)), (1, poisson)):
+        dt.reset()
+        tim, st = serve.wc_serve_run(ex if mode == 0 else None, dt.requests(arr), mode, hbm_budget_bytes=4 << 30,
+                                     max_batch_keys=1 << 26, max_batch_items=1024, max_inflight=2)
+        assert st["keys"] == sum(r["keys"].size for r in tr["requests"])
+        assert (tim["completed_ns"] >= tim["launched_ns"]).all() and (tim["admitted_ns"] >= arr).all()
+        for i, (got, exp) in enumerate(zip(dt.retrieve_results(), expect)):
+            if exp is not None:
+                np.testing.assert_array_equal(got[1], exp[1], err_msg="found mask of request %d" % i)
+                np.testing.assert_array_equal(got[0], exp[0], err_msg="values of request %d" % i)
+        assert dt.sizes() == sizes
+        if mode == 0:
+            assert serve.wc_executor_get_status(ex, clear=True) == 0
+            assert st["launches"] < nreq  # requests were coalesced
+    serve.wc_executor_destroy(ex)
+    dt.close()

@@ -490,7 +490,11 @@ def test_l2_persist_carveout_is_given_back(wc):
         assert rt.cudaDeviceGetLimit(ctypes.byref(v), limit_persisting_l2) == 0
         return v.value
 
+    # start from no carve-out (a limit of this process's context only), so that the
+    # tables have something to raise
+    assert rt.cudaDeviceSetLimit(limit_persisting_l2, ctypes.c_size_t(0)) == 0
     before = limit()
+    assert before == 0
     a = wc.SingleValueTable(4, 4, min_capacity=1 << 20, l2_persist=True)
     b = wc.SingleValueTable(4, 4, min_capacity=1 << 19, l2_persist=True)
     raised = limit()

@@ -124,11 +124,12 @@ def test_noalloc_insert_refuses_what_it_cannot_take(env):
     assert e.value.code == 1  # WC_ERR_INVALID_ARG
     host = torch.arange(1, 1025, dtype=torch.int32)  # pageable CPU memory
     dev_vals = torch.ones(1024, dtype=torch.int32, device="cuda")
+    # raw addresses, so that the C ABI itself (not the Python binding) sees the host buffer
     with pytest.raises(wc.WcError) as e:
-        api.wc_insert_noalloc(t.handle, host, dev_vals)
+        api.wc_insert_noalloc(t.handle, host.data_ptr(), dev_vals, n=1024)
     assert e.value.code == 1
     with pytest.raises(wc.WcError) as e:
-        api.wc_insert_noalloc(t.handle, dev_vals, host)
+        api.wc_insert_noalloc(t.handle, dev_vals, host.data_ptr(), n=1024)
     assert e.value.code == 1
     assert t.size() == 0 and t.status() == 0
     t.close()
