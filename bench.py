@@ -75,6 +75,8 @@ def parse():
                          "and a counting table (Zipf keys); "
                          "served: 64 tables, Poisson requests, batched vs per-call")
     ap.add_argument("--requests", type=int, default=512, help="served: number of requests")
+    ap.add_argument("--mv-block", type=int, default=0,
+                    help="mv_zipf: block size of the bucket table's insert passes (256 or 512; 0 = default)")
     ap.add_argument("--r", default="1,4,16,64", help="mv_oa_uniform_r: average copies per key, comma-separated")
     ap.add_argument("--bucket-modes", default="exact",
                     help="mv_oa_uniform_r: bucket-table legs, comma-separated: exact (one bucket of exactly each "
@@ -664,6 +666,10 @@ def run_mv_zipf(args, dev):
     out = torch.empty(n, dtype=torch.int32, device=dev)
     s = torch.cuda.current_stream()
     h = api.wc_table_create(1, 8, 4, int(np.ceil(uni / 0.8)), args.window, n + (n >> 3), 0x5EEDC0DE, dev.index)
+    if args.mv_block:
+        lc = api.wc_table_get_launch(h, 0)
+        api.wc_table_set_launch(h, 0, lc["group_size"], args.mv_block, lc["blocks_per_sm"], lc["scheme"],
+                                lc["region_mib"])
     info = api.wc_table_get_info(h)
     ev = []
 
@@ -686,6 +692,7 @@ def run_mv_zipf(args, dev):
             "G ops/s (inserts + queries + values retrieved)",
             (n + nq + n) / (total * 1e-3) / 1e9, "G ops/s", total, "u64/u32",
             {"n_inserts": n, "universe": uni, "queries": nq, "key_store_capacity": info["capacity"],
+             "insert_block": api.wc_table_get_launch(h, 0)["block_threads"],
              "pool": info["pool_capacity"], "l2": "no flush: 2 GB of inserts, 1 GB pool"}, clk,
             10 * args.steps,  # hist, scatter, count, alloc, scatter; count, 3 scan kernels; gather
             {"insert_gops": n / ins / 1e6, "count_gqps": nq / cnt / 1e6, "retrieve_multi_gvals": n / ret / 1e6,

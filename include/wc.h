@@ -180,7 +180,9 @@ typedef struct {
 /* Launch shape of one operation class.  group_size = lanes that probe one key together
  * (the cooperative group of Sec. IV-B2; W / group_size slots per lane, walked
  * consecutively by each lane, Sec. IV-B2 "fixed window with variable CG size");
- * block_threads = CUDA block size; blocks_per_sm = resident blocks per SM the grid is
+ * block_threads = CUDA block size, 32..256 in steps of 32 (the bucket multi-value table's
+ * insert: 256 or 512, the block of its aggregation passes, default 512, with tiles of four
+ * keys per thread); blocks_per_sm = resident blocks per SM the grid is
  * sized for (0 = the occupancy limit); scheme = how a bulk call visits the table
  * (WC_SCHEME_*); region_mib = table bytes per region of the blocked scheme (0 = 32). */
 typedef struct {

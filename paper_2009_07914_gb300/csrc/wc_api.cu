@@ -479,6 +479,7 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
     t->launch[op].region_mib = 0;
   }
   if (mv) {
+    t->launch[WC_OP_INSERT].block_threads = 512;
     t->launch[WC_OP_INSERT].group_size = 1;
     t->launch[WC_OP_RETRIEVE].group_size = 1;
   }
@@ -557,8 +558,10 @@ wc_status wc_table_set_launch(wc_table* t, int32_t op, const wc_launch* launch) 
   if (t == nullptr || launch == nullptr || op < 0 || op >= WC_OP__N) return WC_ERR_INVALID_ARG;
   if (t->cfg.kind == WC_BLOOM_FILTER) return WC_ERR_UNSUPPORTED;  // one thread per key
   const int b = launch->block_threads;
-  if (b < 32 || b > 256 || b % 32 != 0 || launch->blocks_per_sm < 0 || launch->blocks_per_sm > 64)
-    return WC_ERR_INVALID_ARG;
+  // the bucket table's insert runs its aggregation passes in blocks of 256 or 512 threads
+  const bool mv_insert = t->cfg.kind == WC_MULTI_VALUE && op == WC_OP_INSERT;
+  if (mv_insert ? (b != 256 && b != 512) : (b < 32 || b > 256 || b % 32 != 0)) return WC_ERR_INVALID_ARG;
+  if (launch->blocks_per_sm < 0 || launch->blocks_per_sm > 64) return WC_ERR_INVALID_ARG;
   if (launch->scheme < WC_SCHEME_AUTO || launch->scheme > WC_SCHEME_DEDUP || launch->region_mib < 0 ||
       launch->region_mib > 4096)
     return WC_ERR_INVALID_ARG;

@@ -9,18 +9,19 @@ namespace wc {
 
 namespace {
 
-template <class KIn, int VB, int W>
+template <class KIn, int VB, int W, int kThreads>
 cudaError_t insert_passes(const wc_table* t, const void* keys, const void* vals, uint64_t n, cudaStream_t s) {
   using V = typename PoolT<VB>::T;
+  using A = Agg<kThreads>;
   const TableDesc d = desc_of(t);
   const PoolDesc pd = pool_of(t);
   const KIn* k = static_cast<const KIn*>(keys);
-  auto count = k_mv_aggregate<KIn, VB, W, false>;
-  auto scatter = k_mv_aggregate<KIn, VB, W, true>;
+  auto count = k_mv_aggregate<KIn, VB, W, false, kThreads>;
+  auto scatter = k_mv_aggregate<KIn, VB, W, true, kThreads>;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(count, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(agg_smem_bytes(false)));
-    cudaFuncSetAttribute(scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(agg_smem_bytes(true)));
+    cudaFuncSetAttribute(count, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(A::smem_bytes(false)));
+    cudaFuncSetAttribute(scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(A::smem_bytes(true)));
     attr_done = true;
   }
   // Large batches into a key store larger than L2 are first split by key-store region
@@ -37,30 +38,37 @@ cudaError_t insert_passes(const wc_table* t, const void* keys, const void* vals,
     vals = sp.vals;
     counters = sp.counters;
   }
-  const uint64_t ntiles = (n + kAggTile - 1) / kAggTile;
-  const int bps_c = occupancy_smem(count, kAggThreads, agg_smem_bytes(false));
-  const int bps_s = occupancy_smem(scatter, kAggThreads, agg_smem_bytes(true));
+  const uint64_t ntiles = (n + A::kTile - 1) / A::kTile;
+  const int bps_c = occupancy_smem(count, kThreads, A::smem_bytes(false));
+  const int bps_s = occupancy_smem(scatter, kThreads, A::smem_bytes(true));
   const unsigned g_c = static_cast<unsigned>(std::min<uint64_t>(ntiles, static_cast<uint64_t>(bps_c) * t->sm_count));
   const unsigned g_s = static_cast<unsigned>(std::min<uint64_t>(ntiles, static_cast<uint64_t>(bps_s) * t->sm_count));
   e = cudaMemsetAsync(pd.pending, 0, t->capacity * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  e = launch_k(t, count, g_c, kAggThreads, agg_smem_bytes(false), s, d, pd, k, vals, n, counters);
+  e = launch_k(t, count, g_c, kThreads, A::smem_bytes(false), s, d, pd, k, vals, n, counters);
   if (e != cudaSuccess) return e;
   const uint64_t per_block = static_cast<uint64_t>(kAllocThreads) * kAllocItems;
   const unsigned g_a = static_cast<unsigned>((t->capacity + per_block - 1) / per_block);
   e = launch_k(t, t->growth == kGrowExact ? k_mv_alloc<VB> : k_mv_alloc_growth<VB>, g_a, kAllocThreads, 0, s, d, pd,
                t->capacity);
   if (e != cudaSuccess) return e;
-  return launch_k(t, scatter, g_s, kAggThreads, agg_smem_bytes(true), s, d, pd, k, vals, n,
+  return launch_k(t, scatter, g_s, kThreads, A::smem_bytes(true), s, d, pd, k, vals, n,
                   counters ? counters + 1 : counters);
+}
+
+// The aggregation passes run blocks of the insert launch's block_threads (256 or 512).
+template <class KIn, int VB, int W>
+cudaError_t insert_block(const wc_table* t, const void* keys, const void* vals, uint64_t n, cudaStream_t s) {
+  if (t->launch[WC_OP_INSERT].block_threads == 256) return insert_passes<KIn, VB, W, 256>(t, keys, vals, n, s);
+  return insert_passes<KIn, VB, W, 512>(t, keys, vals, n, s);
 }
 
 template <class KIn, int VB>
 cudaError_t insert_w(const wc_table* t, const void* keys, const void* vals, uint64_t n, cudaStream_t s) {
   switch (t->W) {
-    case 2: return insert_passes<KIn, VB, 2>(t, keys, vals, n, s);
-    case 4: return insert_passes<KIn, VB, 4>(t, keys, vals, n, s);
-    case 8: return insert_passes<KIn, VB, 8>(t, keys, vals, n, s);
+    case 2: return insert_block<KIn, VB, 2>(t, keys, vals, n, s);
+    case 4: return insert_block<KIn, VB, 4>(t, keys, vals, n, s);
+    case 8: return insert_block<KIn, VB, 8>(t, keys, vals, n, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -138,28 +138,33 @@ __device__ int64_t ks_find(const TableDesc& t, uint64_t k, uint64_t& handle) {
 
 // ---- passes 1 and 3: tile aggregation in shared memory ----------------------------------
 
-constexpr int kAggThreads = 512;
+// A block of kThreads threads aggregates tiles of kThreads * kAggPerThread batch elements
+// in a shared table of twice as many slots (load <= 1/2).  Smaller blocks hold smaller
+// tables, so more of them fit on an SM and more tiles' probe phases overlap.
 constexpr int kAggPerThread = 4;
-constexpr int kAggTile = kAggThreads * kAggPerThread;  // batch elements per tile
-constexpr int kAggSlots = 2 * kAggTile;                // shared table, load <= 1/2
+template <int kThreads>
+struct Agg {
+  static constexpr int kTile = kThreads * kAggPerThread;  // batch elements per tile
+  static constexpr int kSlots = 2 * kTile;
+  static constexpr size_t smem_bytes(bool scatter) {
+    return (scatter ? 2 : 1) * kSlots * sizeof(unsigned long long) + kSlots * sizeof(uint32_t) +
+           kSlots * sizeof(unsigned short);
+  }
+};
 
+template <int kSlots>
 __device__ __forceinline__ int smem_find_or_insert(unsigned long long* s_key, unsigned long long key) {
   volatile unsigned long long* vk = s_key;
-  uint32_t h = static_cast<uint32_t>(fmix64(key) >> 40) & (kAggSlots - 1);
-  while (true) {  // at most kAggTile distinct keys in a table of 2 * kAggTile slots
+  uint32_t h = static_cast<uint32_t>(fmix64(key) >> 40) & (kSlots - 1);
+  while (true) {  // at most kSlots / 2 distinct keys in a table of kSlots slots
     const unsigned long long cur = vk[h];
     if (cur == key) return static_cast<int>(h);
     if (cur == 0ull) {
       const unsigned long long prev = atomicCAS(s_key + h, 0ull, key);
       if (prev == 0ull || prev == key) return static_cast<int>(h);
     }
-    h = (h + 1) & (kAggSlots - 1);
+    h = (h + 1) & (kSlots - 1);
   }
-}
-
-constexpr size_t agg_smem_bytes(bool scatter) {
-  return (scatter ? 2 : 1) * kAggSlots * sizeof(unsigned long long) + kAggSlots * sizeof(uint32_t) +
-         kAggSlots * sizeof(unsigned short);
 }
 
 // Exclusive block scan of one uint32 per thread; total gets the sum.
@@ -298,7 +303,7 @@ __device__ __forceinline__ void ks_global_phase(const TableDesc& t, const PoolDe
   }
 }
 
-template <class KIn, int VB, int W, bool kScatter>
+template <class KIn, int VB, int W, bool kScatter, int kAggThreads>
 // tile_counter != nullptr: blocks take tiles in increasing order from it (the batch is
 // sorted by key-store region, so the active tiles touch one region of the key store and
 // one range of the value pool at a time); otherwise tiles are strided over the grid.
@@ -306,7 +311,9 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
                                                               const void* __restrict__ vals, uint64_t n,
                                                               unsigned long long* tile_counter) {
   using V = typename PoolT<VB>::T;
-  extern __shared__ unsigned long long agg_smem[];  // agg_smem_bytes(kScatter) bytes
+  constexpr int kAggTile = Agg<kAggThreads>::kTile;
+  constexpr int kAggSlots = Agg<kAggThreads>::kSlots;
+  extern __shared__ unsigned long long agg_smem[];  // Agg<kAggThreads>::smem_bytes(kScatter) bytes
   unsigned long long* s_key = agg_smem;
   unsigned long long* s_base = agg_smem + kAggSlots;
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(agg_smem + (kScatter ? 2 : 1) * kAggSlots);
@@ -349,7 +356,7 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
       int slot = -1;
       uint32_t base = 0;
       if (valid && lane == leader) {
-        slot = smem_find_or_insert(s_key, key);
+        slot = smem_find_or_insert<kAggSlots>(s_key, key);
         base = atomicAdd(s_cnt + slot, static_cast<uint32_t>(__popc(peers)));
       }
       slot = __shfl_sync(kFull, slot, leader);

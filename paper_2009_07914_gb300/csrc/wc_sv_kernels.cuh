@@ -245,15 +245,18 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
     }
     Slot s[S];
     uint32_t mm = 0, me = 0, mt = 0;
+    // The overflow bit only matters for a window without the key and without an empty
+    // slot, but its word is read in the same trip as the window: read after the window
+    // was classified, it would add a second dependent round trip to every trip that walks
+    // on.  The word is kept in L2 (evict-last), so the extra read costs no DRAM line.
+    uint32_t fw = 0xffffffffu;
     if (act) {
       load_slots<L, S>(slots + static_cast<uint64_t>(w) * W + ln.r * S, s);
+      if (t.ovf != nullptr) fw = ovf_word(t.ovf, w);
       classify<L, S>(s, k, mm, me, mt);
     }
     const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
     const uint32_t be = group_vote<G>(me != 0, ln.gbase);
-    // the overflow bit only matters for a window without the key and without an empty slot
-    uint32_t fw = 0xffffffffu;
-    if (t.ovf != nullptr && act && !bm && !be) fw = ovf_word(t.ovf, w);
     Slot hit = pick<L, S>(s, mm ? __ffs(mm) - 1 : 0);
     if constexpr (G > 1) hit = L::shfl(hit, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
     uint64_t hidx = 0;
