@@ -181,16 +181,21 @@ typedef struct {
  * (the cooperative group of Sec. IV-B2; W / group_size slots per lane, walked
  * consecutively by each lane, Sec. IV-B2 "fixed window with variable CG size");
  * block_threads = CUDA block size, 32..256 in steps of 32 (the bucket multi-value table's
- * insert: 256 or 512, the block of its aggregation passes, default 512, with tiles of four
+ * insert: 256 or 512, the block of its aggregation passes, default 256, with tiles of four
  * keys per thread); blocks_per_sm = resident blocks per SM the grid is
  * sized for (0 = the occupancy limit); scheme = how a bulk call visits the table
- * (WC_SCHEME_*); region_mib = table bytes per region of the blocked scheme (0 = 32). */
+ * (WC_SCHEME_*); region_mib = table bytes per region of the blocked scheme (0 = 32);
+ * keys_in_flight = keys each group probes at once (1 or 2; 0 = 1): with 2, every trip of
+ * a group loads the windows of two keys, so twice as many random window reads are in
+ * flight per warp (single-value retrieves of up to 32 bytes of window per lane; elsewhere
+ * it is taken as 1). */
 typedef struct {
   int32_t group_size;
   int32_t block_threads;
   int32_t blocks_per_sm;
   int32_t scheme;
   int32_t region_mib;
+  int32_t keys_in_flight;
 } wc_launch;
 
 /* WC_SCHEME_DIRECT: every key probes the table where its hash points, in input order.

@@ -3,13 +3,16 @@
  *
  * The paper has no counterpart (it benchmarks bulk calls one at a time, Sec. V); this
  * loop serves a stream of insert / retrieve / erase requests as they arrive:
- *   - admission: a request is admitted when the HBM held by admitted, unfinished
- *     requests (their `io_bytes`) plus its own stays within the budget; requests are
- *     admitted in arrival order (a request that does not fit waits, and so do the ones
- *     behind it);
+ *   - admission: a request is admitted when the HBM of the served tables (every device
+ *     byte they own, counted once per table for the whole run) plus that held by admitted,
+ *     unfinished requests (their `io_bytes`) plus its own stays within the budget;
+ *     requests are admitted in arrival order (a request that does not fit waits, and so do
+ *     the ones behind it);
  *   - continuous batching (WC_SERVE_BATCHED): admitted requests are packed into the next
  *     batched launch (wc_exec.h) while up to `max_inflight` earlier batches are still on
- *     the device, so requests arriving during a launch join the next one;
+ *     the device, so requests arriving during a launch join the next one; a request that
+ *     finds the device idle and no other request waiting runs at once as its own bulk
+ *     call (nothing to pack it with);
  *   - WC_SERVE_PER_CALL: every admitted request is launched at once as its own bulk call
  *     (the plain per-call API of wc.h) -- the baseline the batched mode is compared with.
  * Results are the same in both modes and equal to running the requests one by one in
@@ -64,13 +67,15 @@ typedef struct {
   uint64_t wall_ns;       /* start of the run to the last completion */
   uint64_t launches;      /* batched launches or per-call launches */
   uint64_t keys;          /* keys processed */
-  uint64_t peak_admitted_bytes;
+  uint64_t peak_admitted_bytes;  /* most HBM held at once: resident_bytes + admitted io_bytes */
+  uint64_t resident_bytes;       /* device bytes of the served tables (counted against the budget) */
 } wc_serve_stats;
 
 /* Serve `nreq` requests (sorted by arrival_ns).  `ex` is required for WC_SERVE_BATCHED
  * and ignored otherwise.  h_timing receives one record per request; h_stats the totals.
- * All device work goes to `stream`.  A request larger than the budget on its own is
- * admitted alone when nothing else is in flight. */
+ * All device work goes to `stream`.  A request larger than what the tables leave of the
+ * budget is admitted alone when nothing else is in flight; tables that alone exceed the
+ * budget return WC_ERR_OUT_OF_MEMORY before anything runs. */
 wc_status wc_serve_run(wc_executor* ex, const wc_request* h_requests, uint32_t nreq, const wc_serve_config* cfg,
                        void* stream, wc_request_timing* h_timing, wc_serve_stats* h_stats);
 

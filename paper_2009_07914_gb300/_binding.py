@@ -74,7 +74,8 @@ class WcDeviceView(ctypes.Structure):
 
 class WcLaunch(ctypes.Structure):
     _fields_ = [("group_size", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("scheme", ctypes.c_int32), ("region_mib", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("scheme", ctypes.c_int32), ("region_mib", ctypes.c_int32),
+                ("keys_in_flight", ctypes.c_int32)]
 
 
 class WcError(RuntimeError):

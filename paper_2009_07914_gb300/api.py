@@ -83,9 +83,9 @@ def wc_table_get_info(t: int) -> dict:
 
 
 def wc_table_set_launch(t: int, op: int, group_size: int, block_threads: int = 256, blocks_per_sm: int = 0,
-                        scheme: int = 0, region_mib: int = 0):
+                        scheme: int = 0, region_mib: int = 0, keys_in_flight: int = 0):
     lc = WcLaunch(group_size=group_size, block_threads=block_threads, blocks_per_sm=blocks_per_sm, scheme=scheme,
-                  region_mib=region_mib)
+                  region_mib=region_mib, keys_in_flight=keys_in_flight)
     check(lib().wc_table_set_launch(t, op, ctypes.byref(lc)), "wc_table_set_launch")
 
 

@@ -477,9 +477,10 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
     t->launch[op].blocks_per_sm = 0;
     t->launch[op].scheme = WC_SCHEME_AUTO;
     t->launch[op].region_mib = 0;
+    t->launch[op].keys_in_flight = 1;
   }
   if (mv) {
-    t->launch[WC_OP_INSERT].block_threads = 512;
+    t->launch[WC_OP_INSERT].block_threads = 256;
     t->launch[WC_OP_INSERT].group_size = 1;
     t->launch[WC_OP_RETRIEVE].group_size = 1;
   }
@@ -562,6 +563,7 @@ wc_status wc_table_set_launch(wc_table* t, int32_t op, const wc_launch* launch) 
   const bool mv_insert = t->cfg.kind == WC_MULTI_VALUE && op == WC_OP_INSERT;
   if (mv_insert ? (b != 256 && b != 512) : (b < 32 || b > 256 || b % 32 != 0)) return WC_ERR_INVALID_ARG;
   if (launch->blocks_per_sm < 0 || launch->blocks_per_sm > 64) return WC_ERR_INVALID_ARG;
+  if (launch->keys_in_flight < 0 || launch->keys_in_flight > 2) return WC_ERR_INVALID_ARG;
   if (launch->scheme < WC_SCHEME_AUTO || launch->scheme > WC_SCHEME_DEDUP || launch->region_mib < 0 ||
       launch->region_mib > 4096)
     return WC_ERR_INVALID_ARG;

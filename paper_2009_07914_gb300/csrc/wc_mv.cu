@@ -56,11 +56,13 @@ cudaError_t insert_passes(const wc_table* t, const void* keys, const void* vals,
                   counters ? counters + 1 : counters);
 }
 
-// The aggregation passes run blocks of the insert launch's block_threads (256 or 512).
+// The aggregation passes run blocks of the insert launch's block_threads (256 or 512;
+// 2^28 Zipf inserts over 2^24 keys: 16.5 G/s with 256, 15.4 with 512 -- smaller shared
+// tables fit more blocks per SM, whose probe phases overlap).
 template <class KIn, int VB, int W>
 cudaError_t insert_block(const wc_table* t, const void* keys, const void* vals, uint64_t n, cudaStream_t s) {
-  if (t->launch[WC_OP_INSERT].block_threads == 256) return insert_passes<KIn, VB, W, 256>(t, keys, vals, n, s);
-  return insert_passes<KIn, VB, W, 512>(t, keys, vals, n, s);
+  if (t->launch[WC_OP_INSERT].block_threads == 512) return insert_passes<KIn, VB, W, 512>(t, keys, vals, n, s);
+  return insert_passes<KIn, VB, W, 256>(t, keys, vals, n, s);
 }
 
 template <class KIn, int VB>

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <deque>
 #include <thread>
+#include <unordered_set>
 #include <vector>
 
 #include "wc.h"
@@ -44,6 +45,18 @@ extern "C" wc_status wc_serve_run(wc_executor* ex, const wc_request* reqs, uint3
   if (cfg->max_inflight == 0 || cfg->max_batch_items == 0) return WC_ERR_INVALID_ARG;
   for (uint32_t i = 1; i < nreq; ++i)
     if (reqs[i].arrival_ns < reqs[i - 1].arrival_ns) return WC_ERR_INVALID_ARG;
+  // HBM the served tables hold for the whole run (slots, metadata, scratch they own): the
+  // budget covers them first, and the admitted requests' buffers share what is left
+  uint64_t resident = 0;
+  {
+    std::unordered_set<const wc_table*> seen;
+    for (uint32_t i = 0; i < nreq; ++i) {
+      const wc_table* t = reqs[i].work.table;
+      if (t == nullptr) return WC_ERR_INVALID_ARG;
+      if (seen.insert(t).second) resident += t->device_bytes + t->scratch_bytes;
+    }
+  }
+  if (resident > cfg->hbm_budget_bytes) return WC_ERR_OUT_OF_MEMORY;
 
   std::vector<cudaEvent_t> pool;
   {
@@ -88,9 +101,9 @@ extern "C" wc_status wc_serve_run(wc_executor* ex, const wc_request* reqs, uint3
     while (!waiting.empty()) {
       const uint32_t r = waiting.front();
       const uint64_t b = reqs[r].io_bytes;
-      if (admitted_bytes + b > cfg->hbm_budget_bytes && admitted_bytes != 0) break;
+      if (resident + admitted_bytes + b > cfg->hbm_budget_bytes && admitted_bytes != 0) break;
       admitted_bytes += b;
-      peak = std::max(peak, admitted_bytes);
+      peak = std::max(peak, resident + admitted_bytes);
       timing[r].admitted_ns = now;
       ready.push_back(r);
       waiting.pop_front();
@@ -138,7 +151,12 @@ extern "C" wc_status wc_serve_run(wc_executor* ex, const wc_request* reqs, uint3
     while (st == WC_OK && !ready.empty() && inflight.size() < cfg->max_inflight) {
       Launch l;
       const uint64_t t = now_ns();
-      const bool solo = !batched || (cfg->solo_min_keys && reqs[ready.front()].work.n >= cfg->solo_min_keys);
+      // A request that finds the device idle and nothing else admitted runs at once as
+      // its own bulk call: there is nothing to pack it with, and the plain launch has the
+      // shortest path to the device.  Batches form while earlier work is on the device.
+      const bool idle_single = inflight.empty() && ready.size() == 1 && waiting.empty();
+      const bool solo = !batched || idle_single ||
+                        (cfg->solo_min_keys && reqs[ready.front()].work.n >= cfg->solo_min_keys);
       if (!solo) {
         batch.clear();
         uint64_t nk = 0;
@@ -181,6 +199,7 @@ extern "C" wc_status wc_serve_run(wc_executor* ex, const wc_request* reqs, uint3
   stats->launches = launches;
   stats->keys = keys;
   stats->peak_admitted_bytes = peak;
+  stats->resident_bytes = resident;
   for (auto& e : pool) cudaEventDestroy(e);
   return st;
 }

@@ -94,6 +94,9 @@ cudaError_t sv_run(const wc_table* t, int op, const void* keys, const void* vals
     if (scheme == WC_SCHEME_BLOCKED && n < (1ull << 31) && out != nullptr)
       return sv_retrieve_blocked<L, G, S>(t, lc, k, n, static_cast<Val*>(out), found, s);
     auto kern = scheme == WC_SCHEME_DEDUP ? k_sv_retrieve_dedup<L, G, S> : k_sv_retrieve<L, G, S>;
+    // two keys per group: windows of at most 32 bytes per lane (register budget)
+    if constexpr (S * L::kWords * 8 <= 32 || (L::kHalf && S * 4 <= 32))
+      if (scheme != WC_SCHEME_DEDUP && lc.keys_in_flight == 2) kern = k_sv_retrieve2<L, G, S>;
     const int bps = lc.blocks_per_sm > 0 ? lc.blocks_per_sm : occupancy(kern, block);
     const EngineGrid g = engine_grid(n, G, block, bps, t->sm_count);
     return launch_k(t, kern, g.blocks, block, 0, s, d, k, n, g.per_warp, static_cast<Val*>(out), found);

@@ -245,18 +245,18 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
     }
     Slot s[S];
     uint32_t mm = 0, me = 0, mt = 0;
-    // The overflow bit only matters for a window without the key and without an empty
-    // slot, but its word is read in the same trip as the window: read after the window
-    // was classified, it would add a second dependent round trip to every trip that walks
-    // on.  The word is kept in L2 (evict-last), so the extra read costs no DRAM line.
-    uint32_t fw = 0xffffffffu;
     if (act) {
       load_slots<L, S>(slots + static_cast<uint64_t>(w) * W + ln.r * S, s);
-      if (t.ovf != nullptr) fw = ovf_word(t.ovf, w);
       classify<L, S>(s, k, mm, me, mt);
     }
     const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
     const uint32_t be = group_vote<G>(me != 0, ln.gbase);
+    // The overflow bit only matters for a window without the key and without an empty
+    // slot, so its word is read only then.  Reading it in the same trip as the window
+    // (to save the dependent round trip) measured slower: the lookup is bound by the L2's
+    // request rate, and every trip would then make two requests.
+    uint32_t fw = 0xffffffffu;
+    if (t.ovf != nullptr && act && !bm && !be) fw = ovf_word(t.ovf, w);
     Slot hit = pick<L, S>(s, mm ? __ffs(mm) - 1 : 0);
     if constexpr (G > 1) hit = L::shfl(hit, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
     uint64_t hidx = 0;
@@ -292,6 +292,96 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
   }
 }
 
+// The same lookup with K keys per group in flight: every trip, each group loads the
+// windows of up to K keys at once (all of a warp's loads are issued before any is used), so
+// a warp keeps K times as many random window reads in flight.  A lookup is bound by how
+// many reads are in flight against the memory latency, not by the instructions of a trip.
+// Each of a group's K keys is an independent probe with the retrieve's own stop rules.
+template <class L, int G, int S, int K, class Emit, class KIn = typename L::Key>
+__device__ __forceinline__ void sv_retrieve_range_k(const TableDesc& t, const KIn* __restrict__ keys, RangeSrc& src,
+                                                    Emit& emit, uint32_t& flags) {
+  using Slot = typename L::Slot;
+  using Key = typename L::Key;
+  const SvLane<L, G, S> ln;
+  constexpr int W = G * S;
+  const Slot* slots = static_cast<const Slot*>(t.slots);
+  bool act[K];
+  uint64_t pos[K];
+  Key k[K];
+  uint32_t w[K], step[K], j[K], tag[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    act[q] = false;
+    pos[q] = 0;
+    k[q] = 0;
+    w[q] = step[q] = j[q] = tag[q] = 0;
+  }
+  Feed<KIn> fk;
+  while (true) {
+    const bool more = src.ensure();
+    if (more && src.fresh) {
+      fk.load(keys, src.next, src.end);
+      src.fresh = false;
+    }
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      uint64_t np = 0;
+      const bool got = more && take_next(!act[q], ln.r, ln.gbase, src.next, src.end, np);
+      const KIn kin = fk.get(np, got);
+      if (more) fk.advance(src.next);
+      if (got) {
+        pos[q] = np;
+        k[q] = static_cast<Key>(kin);
+        if (is_sentinel(kin)) {
+          flags |= kFlagInvalid;
+          if (ln.r == 0) emit(pos[q], false, Slot{}, 0ull);
+        } else {
+          act[q] = true;
+          j[q] = 0;
+          probe_init(static_cast<uint64_t>(k[q]), t.seed, t.p, w[q], step[q], tag[q]);
+        }
+      }
+      any |= act[q];
+    }
+    if (__ballot_sync(kFull, any) == 0) {
+      if (!more) break;
+      continue;
+    }
+    Slot s[K][S];
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+      if (act[q]) load_slots<L, S>(slots + static_cast<uint64_t>(w[q]) * W + ln.r * S, s[q]);
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      uint32_t mm = 0, me = 0, mt = 0;
+      if (act[q]) classify<L, S>(s[q], k[q], mm, me, mt);
+      const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
+      const uint32_t be = group_vote<G>(me != 0, ln.gbase);
+      uint32_t fw = 0xffffffffu;
+      if (t.ovf != nullptr && act[q] && !bm && !be) fw = ovf_word(t.ovf, w[q]);
+      Slot hit = pick<L, S>(s[q], mm ? __ffs(mm) - 1 : 0);
+      if constexpr (G > 1) hit = L::shfl(hit, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
+      uint64_t hidx = 0;
+      if constexpr (L::kSoA) {
+        hidx = static_cast<uint64_t>(w[q]) * W + ln.r * S + (mm ? __ffs(mm) - 1 : 0);
+        if constexpr (G > 1) hidx = __shfl_sync(kFull, hidx, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
+      }
+      if (act[q]) {
+        if (bm) {
+          if (ln.r == 0) emit(pos[q], true, hit, hidx);
+          act[q] = false;
+        } else if (be || !ovf_bit(fw, w[q], tag[q]) || ++j[q] >= t.p) {
+          if (ln.r == 0) emit(pos[q], false, hit, hidx);
+          act[q] = false;
+        } else {
+          w[q] = probe_next(w[q], step[q], t.p);
+        }
+      }
+    }
+  }
+}
+
 template <class L>
 struct EmitValue {
   typename L::Val* __restrict__ out;
@@ -320,6 +410,19 @@ __global__ void __launch_bounds__(256, retrieve_min_blocks<L, S>()) k_sv_retriev
   uint32_t flags = 0;
   EmitValue<L> emit{out, found, t.vals};
   sv_retrieve_range<L, G, S>(t, keys, src, emit, flags);
+  flush_flags(t.status, flags);
+}
+
+// The same with two keys per group in flight (launch keys_in_flight = 2).
+template <class L, int G, int S>
+__global__ void __launch_bounds__(256) k_sv_retrieve2(TableDesc t, const typename L::Key* __restrict__ keys, uint64_t n,
+                                                      uint64_t per_warp, typename L::Val* __restrict__ out,
+                                                      uint8_t* __restrict__ found) {
+  RangeSrc src(n, per_warp, nullptr, 0);
+  if (src.next >= src.end) return;
+  uint32_t flags = 0;
+  EmitValue<L> emit{out, found, t.vals};
+  sv_retrieve_range_k<L, G, S, 2>(t, keys, src, emit, flags);
   flush_flags(t.status, flags);
 }
 

@@ -40,7 +40,7 @@ class WcRequestTiming(ctypes.Structure):
 
 class WcServeStats(ctypes.Structure):
     _fields_ = [("wall_ns", ctypes.c_uint64), ("launches", ctypes.c_uint64), ("keys", ctypes.c_uint64),
-                ("peak_admitted_bytes", ctypes.c_uint64)]
+                ("peak_admitted_bytes", ctypes.c_uint64), ("resident_bytes", ctypes.c_uint64)]
 
 
 WC_SERVE_BATCHED = 0

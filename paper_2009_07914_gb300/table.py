@@ -86,8 +86,10 @@ class _Table:
     def status(self, clear=False, stream=None) -> int:
         return api.wc_get_status(self.handle, clear, stream)
 
-    def set_launch(self, op, group_size, block_threads=256, blocks_per_sm=0, scheme=0, region_mib=0):
-        api.wc_table_set_launch(self.handle, op, group_size, block_threads, blocks_per_sm, scheme, region_mib)
+    def set_launch(self, op, group_size, block_threads=256, blocks_per_sm=0, scheme=0, region_mib=0,
+                   keys_in_flight=0):
+        api.wc_table_set_launch(self.handle, op, group_size, block_threads, blocks_per_sm, scheme, region_mib,
+                                keys_in_flight)
 
 
 class SingleValueTable(_Table):

@@ -46,7 +46,17 @@ def test_results_equal_alone_and_in_the_mix(env, mode, solo):
     _oracle_apply(ors, tr)
     assert dt.sizes() == [o.size() for o in ors]
     if mode == 0:
+        # all requests at once: the device is never idle with one request waiting, so the
+        # executor coalesces them; the results stay those of the oracle
+        dt.reset()
+        reqs = dt.requests(np.zeros(len(tr["requests"]), dtype=np.uint64))
+        tim, st = serve.wc_serve_run(ex, reqs, mode, hbm_budget_bytes=1 << 30, max_batch_items=64, max_inflight=2,
+                                     solo_min_keys=solo)
         assert st["launches"] < len(reqs)  # requests were coalesced
+        for got, exp in zip(dt.retrieve_results(), expect):
+            if exp is not None:
+                np.testing.assert_array_equal(got[1], exp[1])
+                np.testing.assert_array_equal(got[0], exp[0])
         serve.wc_executor_destroy(ex)
     dt.close()
 
@@ -58,10 +68,16 @@ def test_admission_respects_the_hbm_budget(env):
     dt.reset()
     reqs = dt.requests(np.zeros(len(tr["requests"]), dtype=np.uint64))  # all arrive at once
     biggest = max(r.io_bytes for r in reqs)
-    budget = 2 * biggest
+    from paper_2009_07914_gb300 import api
+    resident = sum(api.wc_table_get_info(h)["device_bytes"] for h in dt.tables)
+    budget = resident + 2 * biggest
     ex = serve.wc_executor_create(0, 8, max_items=64, tile_keys=1024)
+    # the tables alone do not fit in a budget of their own size minus one byte
+    with pytest.raises(Exception):
+        serve.wc_serve_run(ex, reqs, 0, hbm_budget_bytes=resident - 1, max_batch_items=64, max_inflight=2)
     tim, st = serve.wc_serve_run(ex, reqs, 0, hbm_budget_bytes=budget, max_batch_items=64, max_inflight=2)
-    assert st["peak_admitted_bytes"] <= budget
+    assert st["resident_bytes"] == resident
+    assert resident < st["peak_admitted_bytes"] <= budget
     assert st["launches"] >= 2
     # admission is in arrival order
     order = np.argsort(tim["admitted_ns"], kind="stable")

@@ -508,3 +508,37 @@ def test_l2_persist_carveout_is_given_back(wc):
     assert limit() == raised  # b still holds it
     b.close()
     assert limit() == before
+
+
+# shapes where lookups keep two keys per group in flight (up to 32 bytes of window per lane)
+KIF2_P32 = [(W, G) for W, G in W_G_P32 if W // G <= 4]
+KIF2_P64 = [(W, G) for W, G in W_G_P64 if W // G <= 2]
+
+
+@pytest.mark.parametrize("opt", [0, 1], ids=["plain", "overflow_bits"])
+@pytest.mark.parametrize("kb,W,G", [(4,) + x for x in KIF2_P32] + [(8,) + x for x in KIF2_P64])
+def test_retrieve_two_keys_per_group_in_flight(wc, kb, W, G, opt):
+    """Lookups with keys_in_flight = 2 against the oracle, element by element: present and
+    absent keys, sentinels, after erases (tombstones walked past) and re-inserts; a batch
+    with a ragged tail that does not fill the warps' ranges evenly."""
+    n = 70_001
+    if kb == 4:
+        keys = wc_inputs.distinct_u32(0x2F17 + W * 64 + G, n + 35_000)
+        vals = wc_inputs.uniform_u32(6, n)
+    else:
+        keys = wc_inputs.distinct_u64(0x2F17 + W * 64 + G, n + 35_000)
+        vals = wc_inputs.uniform_u64(6, n)
+    t = make_sv(wc, kb, kb, int(n / 0.92) + 1, W, G, options=opt)
+    t.set_launch(wc.WC_OP_RETRIEVE, G, keys_in_flight=2)
+    assert wc.wc_table_get_launch(t.handle, wc.WC_OP_RETRIEVE)["keys_in_flight"] == 2
+    o = oracle.SingleValue(kb, kb)
+    assert t.insert(keys[:n], vals) == o.insert(keys[:n], vals) == 0
+    q = keys[wc_inputs.shuffle_index(11, keys.size)]
+    q = np.concatenate([q, np.array([0, 0, (1 << (8 * kb)) - 1], dtype=q.dtype), q[:17]])
+    check_retrieve(t, o, q)
+    drop = keys[: n // 3]
+    assert t.erase(drop) == o.erase(drop)
+    check_retrieve(t, o, q)
+    assert t.insert(drop[::2], vals[: n // 3: 2]) == o.insert(drop[::2], vals[: n // 3: 2])
+    check_retrieve(t, o, q)
+    assert t.size() == o.size()
