@@ -926,10 +926,13 @@ def run_served(args, dev):
     from paper_2009_07914_gb300 import serve
     tr = wc_inputs.serving_trace(0x57C00005, n_tables=64, n_requests=args.requests)
     dt = serve.DeviceTrace(tr, device=dev.index, window_width=8)
-    ex = serve.wc_executor_create(dev.index, 8, max_items=1024, tile_keys=512)
+    ex = serve.wc_executor_create(dev.index, 8, max_items=1024, tile_keys=4096)
     nreq = len(tr["requests"])
     keys_total = sum(r["keys"].size for r in tr["requests"])
-    budget = 64 << 30
+    from paper_2009_07914_gb300 import api
+    resident = sum(api.wc_table_get_info(h)["device_bytes"] for h in dt.tables)
+    # the tables plus 512 MiB of request buffers: admission binds whenever requests queue
+    budget = resident + (512 << 20)
 
     def run(mode, arrivals, solo=0, max_keys=1 << 26):
         dt.reset()
@@ -938,7 +941,8 @@ def run_served(args, dev):
                                      solo_min_keys=solo)
         lat = (tim["completed_ns"] - arrivals).astype(np.float64) / 1e3
         return {"throughput_gkeys": keys_total / st["wall_ns"], "p50_us": float(np.percentile(lat, 50)),
-                "p99_us": float(np.percentile(lat, 99)), "launches": st["launches"], "wall_ms": st["wall_ns"] / 1e6}
+                "p99_us": float(np.percentile(lat, 99)), "launches": st["launches"], "wall_ms": st["wall_ns"] / 1e6,
+                "peak_admitted_bytes": st["peak_admitted_bytes"]}
     zero = np.zeros(nreq, dtype=np.uint64)
     for _ in range(max(1, args.warmup)):
         run(1, zero)
@@ -956,7 +960,8 @@ def run_served(args, dev):
     b, p = runs["batched_closed"], runs["per_call_closed"]
     _common(args, "served_64tables_%dreq" % nreq, "G keys/s served (batched, closed loop)", b["throughput_gkeys"],
             "G keys/s", b["wall_ms"], "u32", {"tables": 64, "requests": nreq, "keys": keys_total,
-                                              "per_call_saturation_req_per_s": sat}, clk,
+                                              "per_call_saturation_req_per_s": sat, "hbm_budget_bytes": budget,
+                                              "resident_table_bytes": resident}, clk,
             b["launches"], {"runs": runs, "batched_over_per_call": b["throughput_gkeys"] / p["throughput_gkeys"]})
     serve.wc_executor_destroy(ex)
     dt.close()

@@ -48,7 +48,9 @@ typedef struct {
   int32_t device;
   int32_t window_width;   /* window width of every table the executor serves (4, 8, 16) */
   uint32_t max_items;     /* work items per batch */
-  uint32_t tile_keys;     /* keys per tile (power of two, 256..65536; 0 = 4096) */
+  uint32_t tile_keys;     /* most keys per tile (power of two, 64..65536; 0 = 4096): each
+                             item is cut into tiles of a multiple of 64 keys, small enough to
+                             spread it over every warp of the kernel, up to this size */
   uint64_t timeout_ns;    /* bound of every device-side wait (0 = 2 s) */
   int32_t test_stall;     /* testing: 1 = the first write item of every batch is never
                              reported complete, so items depending on it time out */

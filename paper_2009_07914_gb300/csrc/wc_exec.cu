@@ -19,6 +19,7 @@ namespace wc {
 namespace {
 
 constexpr uint32_t kMaxExecItems = 4096;
+constexpr uint32_t kMinTileKeys = 64;
 constexpr int kExecThreads = 256;
 constexpr int kTicketRing = 256;
 
@@ -33,7 +34,7 @@ struct ExecItem {
   uint32_t op;
   int32_t dep;          // group this item waits for (-1: none)
   uint32_t group;       // group this item counts its finished tiles into
-  uint32_t pad;
+  uint32_t tile_keys;   // keys per tile of this item
 };
 
 struct ExecHeader {
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(kExecThreads, 3) k_exec(const ExecHeader* __re
                                                        unsigned long long* __restrict__ gdone,
                                                        unsigned long long* __restrict__ idone,
                                                        unsigned long long* item_flags, uint32_t* xstatus,
-                                                       uint64_t timeout_ns, uint32_t tile_keys) {
+                                                       uint64_t timeout_ns) {
   using L = LayoutP32;
   constexpr int GI = ExecShape<W>::GI, SI = W / GI;
   constexpr int GR = ExecShape<W>::GR, SR = W / GR;
@@ -133,8 +134,8 @@ __global__ void __launch_bounds__(kExecThreads, 3) k_exec(const ExecHeader* __re
       __threadfence();
     }
     if (ok) {
-      const uint64_t begin = (tile - it.tile_begin) * tile_keys;
-      const uint64_t end = begin + tile_keys < it.n ? begin + tile_keys : it.n;
+      const uint64_t begin = (tile - it.tile_begin) * it.tile_keys;
+      const uint64_t end = begin + it.tile_keys < it.n ? begin + it.tile_keys : it.n;
       RangeSrc src(begin, end);
       uint32_t flags = 0;
       long long delta = 0;
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(kExecThreads, 3) k_exec(const ExecHeader* __re
     if (lane == 0) {
       atomicAdd(gdone + it.group, 1ull);
       // the warp that finishes an item's last tile reports it to the host (mapped memory)
-      const unsigned long long item_tiles = (it.n + tile_keys - 1) / tile_keys;
+      const unsigned long long item_tiles = (it.n + it.tile_keys - 1) / it.tile_keys;
       if (atomicAdd(idone + lo, 1ull) + 1 == item_tiles) {
         __threadfence_system();
         const unsigned long long flag = hdr->ticket + 1;
@@ -195,6 +196,7 @@ struct wc_executor {
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   void* kernel = nullptr;
+  unsigned grid_blocks = 1;  // blocks of the persistent kernel
 };
 
 namespace {
@@ -231,7 +233,7 @@ wc_status wc_executor_create(wc_executor** out, const wc_executor_config* cfg) {
   if (W != 4 && W != 8 && W != 16) return WC_ERR_INVALID_ARG;
   if (cfg->max_items == 0 || cfg->max_items > kMaxExecItems) return WC_ERR_INVALID_ARG;
   const uint32_t tk = cfg->tile_keys ? cfg->tile_keys : 4096;
-  if (tk < 256 || tk > 65536 || (tk & (tk - 1))) return WC_ERR_INVALID_ARG;
+  if (tk < kMinTileKeys || tk > 65536 || (tk & (tk - 1))) return WC_ERR_INVALID_ARG;
   wc_executor* ex = new (std::nothrow) wc_executor();
   if (ex == nullptr) return WC_ERR_OUT_OF_MEMORY;
   ex->cfg = *cfg;
@@ -266,11 +268,10 @@ wc_status wc_executor_create(wc_executor** out, const wc_executor_config* cfg) {
   auto* idone = reinterpret_cast<unsigned long long*>(ex->d_buf + ex->lay.idone);
   auto* xst = reinterpret_cast<uint32_t*>(ex->d_buf + ex->lay.status);
   uint64_t tmo = ex->cfg.timeout_ns;
-  uint32_t tkeys = ex->cfg.tile_keys;
   for (int g = 0; ok && g < 2; ++g) {
     unsigned long long* dflags = nullptr;
     ok = cudaHostGetDevicePointer(reinterpret_cast<void**>(&dflags), ex->h_flags[g], 0) == cudaSuccess;
-    void* args[] = {&hdr, &gt, &items, &next, &gdone, &idone, &dflags, &xst, &tmo, &tkeys};
+    void* args[] = {&hdr, &gt, &items, &next, &gdone, &idone, &dflags, &xst, &tmo};
     cudaGraphNode_t n_copy = nullptr, n_set = nullptr, n_kernel = nullptr;
     ok = ok && cudaGraphCreate(&ex->graph[g], 0) == cudaSuccess;
     if (ok)
@@ -288,7 +289,8 @@ wc_status wc_executor_create(wc_executor** out, const wc_executor_config* cfg) {
     if (ok) {
       cudaKernelNodeParams kp = {};
       kp.func = ex->kernel;
-      kp.gridDim = dim3(static_cast<unsigned>(bps * ex->sm_count));
+      ex->grid_blocks = static_cast<unsigned>(bps * ex->sm_count);
+      kp.gridDim = dim3(ex->grid_blocks);
       kp.blockDim = dim3(kExecThreads);
       kp.kernelParams = args;
       ok = cudaGraphAddKernelNode(&n_kernel, ex->graph[g], &n_set, 1, &kp) == cudaSuccess &&
@@ -343,7 +345,12 @@ wc_status wc_executor_submit(wc_executor* ex, const wc_work* h_items, uint32_t c
   uint32_t ni = 0, ng = 0;
   uint64_t tiles = 0;
   bool stalled = false;
-  const uint64_t tk = ex->cfg.tile_keys;
+  // Every item is cut into tiles small enough to spread it over all of the kernel's warps
+  // (from kMinTileKeys up to the configured tile size): the warps take tiles in order, so
+  // an item's keys are then probed by the whole GPU at once and a small request finishes
+  // about as soon as it would as a call of its own.
+  const uint64_t warps = static_cast<uint64_t>(ex->grid_blocks) * (kExecThreads / 32);
+  const uint64_t tk_max = ex->cfg.tile_keys;
   ex->item_map[slot].assign(count, -1);
   for (uint32_t i = 0; i < count; ++i) {
     const wc_work& w = h_items[i];
@@ -358,7 +365,9 @@ wc_status wc_executor_submit(wc_executor* ex, const wc_work* h_items, uint32_t c
     it.n = w.n;
     it.tile_begin = tiles;
     it.op = static_cast<uint32_t>(w.op);
-    it.pad = 0;
+    uint64_t tk = (w.n + warps - 1) / warps;
+    tk = std::min<uint64_t>(tk_max, std::max<uint64_t>(kMinTileKeys, (tk + kMinTileKeys - 1) / kMinTileKeys * kMinTileKeys));
+    it.tile_keys = static_cast<uint32_t>(tk);
     const uint64_t nt = (w.n + tk - 1) / tk;
     tiles += nt;
     auto f = cur.find(w.table);

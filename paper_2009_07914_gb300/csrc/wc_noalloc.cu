@@ -90,7 +90,7 @@ cudaError_t scratch_address(int device, void** out) {
   return cudaSuccess;
 }
 
-template <class L, int G, int S>
+template <class L, int G, int S, int H = 1>
 cudaError_t run(const wc_table* t, const void* keys, const void* vals, uint64_t n, char* sc, cudaStream_t s) {
   using Key = typename L::Key;
   using Val = typename L::Val;
@@ -112,7 +112,7 @@ cudaError_t run(const wc_table* t, const void* keys, const void* vals, uint64_t 
   if (e != cudaSuccess) return e;
   auto hk = k_part_hist<Key>;
   auto sk = k_part_scatter<Key, Val>;
-  auto ik = k_sv_insert<L, G, S>;
+  auto ik = k_sv_insert<L, G, S, H>;
   const size_t hsm = static_cast<size_t>(kHistWarps) * m.R * sizeof(unsigned int);
   const size_t ssm = scatter_smem_bytes<Key, Val>();
   e = cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kHistWarps * kMaxRegions * 4));
@@ -138,6 +138,8 @@ cudaError_t run(const wc_table* t, const void* keys, const void* vals, uint64_t 
 
 #define WC_NA_CASE(L, Wv, Gv) \
   if (W == (Wv) && G == (Gv)) return run<L, (Gv), (Wv) / (Gv)>(t, keys, vals, n, sc, s);
+#define WC_NA_CASE_H(L, Wv, Gv, Hv) \
+  if (W == (Wv) && G == (Gv)) return run<L, (Gv), (Wv) / (Gv) / (Hv), (Hv)>(t, keys, vals, n, sc, s);
 
 cudaError_t dispatch(const wc_table* t, const void* keys, const void* vals, uint64_t n, char* sc, cudaStream_t s) {
   const int W = static_cast<int>(t->W);
@@ -145,6 +147,7 @@ cudaError_t dispatch(const wc_table* t, const void* keys, const void* vals, uint
   if (t->slot_bytes == 8) {
     WC_NA_CASE(LayoutP32, 4, 1) WC_NA_CASE(LayoutP32, 4, 2) WC_NA_CASE(LayoutP32, 4, 4)
     WC_NA_CASE(LayoutP32, 8, 1) WC_NA_CASE(LayoutP32, 8, 2) WC_NA_CASE(LayoutP32, 8, 4) WC_NA_CASE(LayoutP32, 8, 8)
+    WC_NA_CASE_H(LayoutP32, 16, 1, 2)
     WC_NA_CASE(LayoutP32, 16, 2) WC_NA_CASE(LayoutP32, 16, 4) WC_NA_CASE(LayoutP32, 16, 8)
     WC_NA_CASE(LayoutP32, 16, 16)
     WC_NA_CASE(LayoutP32, 32, 4) WC_NA_CASE(LayoutP32, 32, 8) WC_NA_CASE(LayoutP32, 32, 16)

@@ -199,18 +199,19 @@ struct DedupFeed : Feed<T> {
 // the matching slot's position in the table (struct-of-arrays layouts read the value
 // there; 0 for other layouts).  kDedup: equal queries of a 32-element block are probed
 // once, the result emitted for each of their positions (skewed query streams).
-template <class L, int G, int S, class Emit, class KIn = typename L::Key, bool kDedup = false>
+template <class L, int G, int S, class Emit, class KIn = typename L::Key, bool kDedup = false, int H = 1>
 __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn* __restrict__ keys, RangeSrc& src,
                                                   Emit& emit, uint32_t& flags) {
   using Slot = typename L::Slot;
   using Key = typename L::Key;
   const SvLane<L, G, S> ln;
-  constexpr int W = G * S;
+  constexpr int SW = G * S;  // slots of one step; a window is walked in H steps
+  constexpr int W = SW * H;
   const Slot* slots = static_cast<const Slot*>(t.slots);
   bool act = false;
   uint64_t pos = 0;
   Key k = 0;
-  uint32_t w = 0, step = 0, j = 0, tag = 0;
+  uint32_t w = 0, step = 0, j = 0, tag = 0, h = 0;
   uint32_t fm = 0;  // kDedup: group mask of the query being probed
   std::conditional_t<kDedup, DedupFeed<KIn>, Feed<KIn>> fk;
   while (true) {
@@ -236,6 +237,7 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
       } else if (!kDedup || fm != 0) {  // a follower is answered by its leader
         act = true;
         j = 0;
+        h = 0;
         probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step, tag);
       }
     }
@@ -246,7 +248,7 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
     Slot s[S];
     uint32_t mm = 0, me = 0, mt = 0;
     if (act) {
-      load_slots<L, S>(slots + static_cast<uint64_t>(w) * W + ln.r * S, s);
+      load_slots<L, S>(slots + static_cast<uint64_t>(w) * W + h * SW + ln.r * S, s);
       classify<L, S>(s, k, mm, me, mt);
     }
     const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
@@ -256,17 +258,20 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
     // (to save the dependent round trip) measured slower: the lookup is bound by the L2's
     // request rate, and every trip would then make two requests.
     uint32_t fw = 0xffffffffu;
-    if (t.ovf != nullptr && act && !bm && !be) fw = ovf_word(t.ovf, w);
+    if (t.ovf != nullptr && act && !bm && !be && h + 1 == H) fw = ovf_word(t.ovf, w);
     Slot hit = pick<L, S>(s, mm ? __ffs(mm) - 1 : 0);
     if constexpr (G > 1) hit = L::shfl(hit, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
     uint64_t hidx = 0;
     if constexpr (L::kSoA) {
-      hidx = static_cast<uint64_t>(w) * W + ln.r * S + (mm ? __ffs(mm) - 1 : 0);
+      hidx = static_cast<uint64_t>(w) * W + h * SW + ln.r * S + (mm ? __ffs(mm) - 1 : 0);
       if constexpr (G > 1) hidx = __shfl_sync(kFull, hidx, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
     }
     if constexpr (kDedup) {
       if (act) {
-        const bool done = bm || be || !ovf_bit(fw, w, tag) || ++j >= t.p;
+        // an empty slot ends the walk wherever it is; the rest of a window follows its
+        // first part; a whole window without either ends it through its overflow bit
+        const bool next_part = !bm && !be && h + 1 < H;
+        const bool done = !next_part && (bm || be || !ovf_bit(fw, w, tag) || ++j >= t.p);
         if (done && ln.r == 0) {
           emit(pos, bm != 0, hit, hidx);
           const uint64_t first = pos - static_cast<uint64_t>(__ffs(fm) - 1);  // the leader is the lowest lane
@@ -274,7 +279,10 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
         }
         if (done) {
           act = false;
+        } else if (next_part) {
+          ++h;
         } else {
+          h = 0;
           w = probe_next(w, step, t.p);
         }
       }
@@ -282,10 +290,16 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
       if (bm) {
         if (ln.r == 0) emit(pos, true, hit, hidx);
         act = false;
-      } else if (be || !ovf_bit(fw, w, tag) || ++j >= t.p) {
+      } else if (be) {
+        if (ln.r == 0) emit(pos, false, hit, hidx);
+        act = false;
+      } else if (h + 1 < H) {
+        ++h;  // the rest of this window
+      } else if (!ovf_bit(fw, w, tag) || ++j >= t.p) {
         if (ln.r == 0) emit(pos, false, hit, hidx);
         act = false;
       } else {
+        h = 0;
         w = probe_next(w, step, t.p);
       }
     }
@@ -297,24 +311,25 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
 // a warp keeps K times as many random window reads in flight.  A lookup is bound by how
 // many reads are in flight against the memory latency, not by the instructions of a trip.
 // Each of a group's K keys is an independent probe with the retrieve's own stop rules.
-template <class L, int G, int S, int K, class Emit, class KIn = typename L::Key>
+template <class L, int G, int S, int K, class Emit, class KIn = typename L::Key, int H = 1>
 __device__ __forceinline__ void sv_retrieve_range_k(const TableDesc& t, const KIn* __restrict__ keys, RangeSrc& src,
                                                     Emit& emit, uint32_t& flags) {
   using Slot = typename L::Slot;
   using Key = typename L::Key;
   const SvLane<L, G, S> ln;
-  constexpr int W = G * S;
+  constexpr int SW = G * S;  // slots of one step; a window is walked in H steps
+  constexpr int W = SW * H;
   const Slot* slots = static_cast<const Slot*>(t.slots);
   bool act[K];
   uint64_t pos[K];
   Key k[K];
-  uint32_t w[K], step[K], j[K], tag[K];
+  uint32_t w[K], step[K], j[K], tag[K], h[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) {
     act[q] = false;
     pos[q] = 0;
     k[q] = 0;
-    w[q] = step[q] = j[q] = tag[q] = 0;
+    w[q] = step[q] = j[q] = tag[q] = h[q] = 0;
   }
   Feed<KIn> fk;
   while (true) {
@@ -339,6 +354,7 @@ __device__ __forceinline__ void sv_retrieve_range_k(const TableDesc& t, const KI
         } else {
           act[q] = true;
           j[q] = 0;
+          h[q] = 0;
           probe_init(static_cast<uint64_t>(k[q]), t.seed, t.p, w[q], step[q], tag[q]);
         }
       }
@@ -351,7 +367,7 @@ __device__ __forceinline__ void sv_retrieve_range_k(const TableDesc& t, const KI
     Slot s[K][S];
 #pragma unroll
     for (int q = 0; q < K; ++q)
-      if (act[q]) load_slots<L, S>(slots + static_cast<uint64_t>(w[q]) * W + ln.r * S, s[q]);
+      if (act[q]) load_slots<L, S>(slots + static_cast<uint64_t>(w[q]) * W + h[q] * SW + ln.r * S, s[q]);
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       uint32_t mm = 0, me = 0, mt = 0;
@@ -359,22 +375,28 @@ __device__ __forceinline__ void sv_retrieve_range_k(const TableDesc& t, const KI
       const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
       const uint32_t be = group_vote<G>(me != 0, ln.gbase);
       uint32_t fw = 0xffffffffu;
-      if (t.ovf != nullptr && act[q] && !bm && !be) fw = ovf_word(t.ovf, w[q]);
+      if (t.ovf != nullptr && act[q] && !bm && !be && h[q] + 1 == H) fw = ovf_word(t.ovf, w[q]);
       Slot hit = pick<L, S>(s[q], mm ? __ffs(mm) - 1 : 0);
       if constexpr (G > 1) hit = L::shfl(hit, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
       uint64_t hidx = 0;
       if constexpr (L::kSoA) {
-        hidx = static_cast<uint64_t>(w[q]) * W + ln.r * S + (mm ? __ffs(mm) - 1 : 0);
+        hidx = static_cast<uint64_t>(w[q]) * W + h[q] * SW + ln.r * S + (mm ? __ffs(mm) - 1 : 0);
         if constexpr (G > 1) hidx = __shfl_sync(kFull, hidx, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
       }
       if (act[q]) {
         if (bm) {
           if (ln.r == 0) emit(pos[q], true, hit, hidx);
           act[q] = false;
-        } else if (be || !ovf_bit(fw, w[q], tag[q]) || ++j[q] >= t.p) {
+        } else if (be) {
+          if (ln.r == 0) emit(pos[q], false, hit, hidx);
+          act[q] = false;
+        } else if (h[q] + 1 < H) {
+          ++h[q];  // the rest of this window
+        } else if (!ovf_bit(fw, w[q], tag[q]) || ++j[q] >= t.p) {
           if (ln.r == 0) emit(pos[q], false, hit, hidx);
           act[q] = false;
         } else {
+          h[q] = 0;
           w[q] = probe_next(w[q], step[q], t.p);
         }
       }
@@ -401,7 +423,7 @@ constexpr int retrieve_min_blocks() {
   return (L::kWords == 1 && sizeof(typename L::Key) == 4 && S <= 4) ? 6 : 1;
 }
 
-template <class L, int G, int S>
+template <class L, int G, int S, int H = 1>
 __global__ void __launch_bounds__(256, retrieve_min_blocks<L, S>()) k_sv_retrieve(TableDesc t, const typename L::Key* __restrict__ keys, uint64_t n,
                                                      uint64_t per_warp, typename L::Val* __restrict__ out,
                                                      uint8_t* __restrict__ found) {
@@ -409,12 +431,12 @@ __global__ void __launch_bounds__(256, retrieve_min_blocks<L, S>()) k_sv_retriev
   if (src.next >= src.end) return;
   uint32_t flags = 0;
   EmitValue<L> emit{out, found, t.vals};
-  sv_retrieve_range<L, G, S>(t, keys, src, emit, flags);
+  sv_retrieve_range<L, G, S, EmitValue<L>, typename L::Key, false, H>(t, keys, src, emit, flags);
   flush_flags(t.status, flags);
 }
 
 // The same with two keys per group in flight (launch keys_in_flight = 2).
-template <class L, int G, int S>
+template <class L, int G, int S, int H = 1>
 __global__ void __launch_bounds__(256) k_sv_retrieve2(TableDesc t, const typename L::Key* __restrict__ keys, uint64_t n,
                                                       uint64_t per_warp, typename L::Val* __restrict__ out,
                                                       uint8_t* __restrict__ found) {
@@ -422,12 +444,12 @@ __global__ void __launch_bounds__(256) k_sv_retrieve2(TableDesc t, const typenam
   if (src.next >= src.end) return;
   uint32_t flags = 0;
   EmitValue<L> emit{out, found, t.vals};
-  sv_retrieve_range_k<L, G, S, 2>(t, keys, src, emit, flags);
+  sv_retrieve_range_k<L, G, S, 2, EmitValue<L>, typename L::Key, H>(t, keys, src, emit, flags);
   flush_flags(t.status, flags);
 }
 
 // The same with equal queries of each 32-element block probed once (WC_SCHEME_DEDUP).
-template <class L, int G, int S>
+template <class L, int G, int S, int H = 1>
 __global__ void __launch_bounds__(256) k_sv_retrieve_dedup(TableDesc t, const typename L::Key* __restrict__ keys,
                                                            uint64_t n, uint64_t per_warp,
                                                            typename L::Val* __restrict__ out,
@@ -436,7 +458,7 @@ __global__ void __launch_bounds__(256) k_sv_retrieve_dedup(TableDesc t, const ty
   if (src.next >= src.end) return;
   uint32_t flags = 0;
   EmitValue<L> emit{out, found, t.vals};
-  sv_retrieve_range<L, G, S, EmitValue<L>, typename L::Key, true>(t, keys, src, emit, flags);
+  sv_retrieve_range<L, G, S, EmitValue<L>, typename L::Key, true, H>(t, keys, src, emit, flags);
   flush_flags(t.status, flags);
 }
 
@@ -457,7 +479,7 @@ struct EmitSwept {
   }
 };
 
-template <class L, int G, int S>
+template <class L, int G, int S, int H = 1>
 __global__ void __launch_bounds__(256) k_sv_retrieve_swept(TableDesc t, const typename L::Key* __restrict__ keys,
                                                            const uint32_t* __restrict__ qpos, uint64_t n,
                                                            unsigned long long* counter, uint32_t chunk,
@@ -466,7 +488,7 @@ __global__ void __launch_bounds__(256) k_sv_retrieve_swept(TableDesc t, const ty
   RangeSrc src(n, 0, counter, chunk);
   uint32_t flags = 0;
   EmitSwept<L> emit{qpos, rk, rv, t.vals};
-  sv_retrieve_range<L, G, S>(t, keys, src, emit, flags);
+  sv_retrieve_range<L, G, S, EmitSwept<L>, typename L::Key, false, H>(t, keys, src, emit, flags);
   flush_flags(t.status, flags);
 }
 
@@ -499,7 +521,14 @@ static __global__ void k_index_hist(unsigned int* __restrict__ hist, uint32_t R,
 // ---------------------------------------------------------------------------------------
 // insert (Sec. IV-B2 steps 1-7, Sec. IV-B3).  Returns through `added` the number of new
 // keys this lane's groups stored (counted by lane r == 0 of each group).
-template <class L, int G, int S>
+//
+// A window of W = G * S * H slots is walked in H steps of G * S slots (the paper's fixed
+// window walked by a smaller group, Sec. IV-B2): a step that finds the key or an empty
+// slot ends the walk, so the rest of the window is read only when the part before it is
+// full.  That is the same order the whole-window read gives: an insert claims the earliest
+// candidate of its sequence, so no live key ever sits behind an empty slot of its own
+// sequence, whatever the window's width.
+template <class L, int G, int S, int H = 1>
 __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typename L::Key* __restrict__ keys,
                                                 const typename L::Val* __restrict__ vals, RangeSrc& src,
                                                 uint32_t& flags, long long& added) {
@@ -507,13 +536,14 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
   using Key = typename L::Key;
   using Val = typename L::Val;
   const SvLane<L, G, S> ln;
-  constexpr int W = G * S;
+  constexpr int SW = G * S;  // slots of one step
+  constexpr int W = SW * H;
   Slot* slots = static_cast<Slot*>(t.slots);
   bool act = false;
   uint64_t pos = 0;
   Key k = 0;
   Val v = 0;
-  uint32_t w = 0, step = 0, j = 0, tag = 0;
+  uint32_t w = 0, step = 0, j = 0, tag = 0, h = 0;
   bool have_t = false;     // a tombstone earlier on the sequence is remembered
   uint64_t t_slot = 0;     // its slot index
   Slot t_word{};           // and the word read there
@@ -546,6 +576,7 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
         v = vin;
         act = true;
         j = 0;
+        h = 0;
         have_t = false;
         probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step, tag);
       }
@@ -556,7 +587,7 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
     }
     Slot s[S];
     uint32_t mm = 0, me = 0, mt = 0;
-    const uint64_t lane_slot = static_cast<uint64_t>(w) * W + ln.r * S;
+    const uint64_t lane_slot = static_cast<uint64_t>(w) * W + h * SW + ln.r * S;
     if (act) {
       load_slots<L, S>(slots + lane_slot, s);
       classify<L, S>(s, k, mm, me, mt);
@@ -565,7 +596,7 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
     const uint32_t be = group_vote<G>(me != 0, ln.gbase);
     const uint32_t bt = group_vote<G>(mt != 0, ln.gbase);
     const uint32_t bc = group_vote<G>((me | mt) != 0, ln.gbase);
-    const bool last = j + 1 >= t.p;
+    const bool last = j + 1 >= t.p && h + 1 == H;
     const bool claim = bm == 0 && (be != 0 || last);
 
     // The key is present: overwrite its value (duplicate warning, Sec. IV-B3).
@@ -619,6 +650,7 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
           // the remembered tombstone was taken: probe again from the start
           have_t = false;
           j = 0;
+          h = 0;
           probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step, tag);
         } else if (bc == 0) {
           flags |= kFlagProbeLimit;  // every window visited, nothing to claim
@@ -631,16 +663,21 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
           t_slot = nt_slot;
           t_word = nt_word;
         }
-        if (t.ovf != nullptr && ln.r == 0) ovf_mark(t.ovf, w, tag);  // walking past a window without an empty slot
-        ++j;
-        w = probe_next(w, step, t.p);
+        if (h + 1 < H) {
+          ++h;  // the rest of this window, in the next trip
+        } else {
+          if (t.ovf != nullptr && ln.r == 0) ovf_mark(t.ovf, w, tag);  // walking past a window without an empty slot
+          h = 0;
+          ++j;
+          w = probe_next(w, step, t.p);
+        }
       }
     }
   }
 }
 
 // counter != nullptr: warps pull chunks in order (input sorted by table region).
-template <class L, int G, int S>
+template <class L, int G, int S, int H = 1>
 __global__ void __launch_bounds__(256) k_sv_insert(TableDesc t, const typename L::Key* __restrict__ keys,
                                                    const typename L::Val* __restrict__ vals, uint64_t n,
                                                    uint64_t per_warp, unsigned long long* counter, uint32_t chunk) {
@@ -648,7 +685,7 @@ __global__ void __launch_bounds__(256) k_sv_insert(TableDesc t, const typename L
   if (counter == nullptr && src.next >= src.end) return;
   uint32_t flags = 0;
   long long added = 0;
-  sv_insert_range<L, G, S>(t, keys, vals, src, flags, added);
+  sv_insert_range<L, G, S, H>(t, keys, vals, src, flags, added);
   flush_flags(t.status, flags);
   flush_delta(t.size, added);
 }
@@ -657,17 +694,18 @@ __global__ void __launch_bounds__(256) k_sv_insert(TableDesc t, const typename L
 // erase (Sec. IV-B5): the key's slot becomes a tombstone.  `removed` counts erased keys;
 // on_erase(slot) sees the word that was replaced (multi-value tables use it to adjust
 // their pair count).
-template <class L, int G, int S, class OnErase, class KIn = typename L::Key>
+template <class L, int G, int S, class OnErase, class KIn = typename L::Key, int H = 1>
 __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __restrict__ keys, RangeSrc& src,
                                                uint32_t& flags, long long& removed, OnErase& on_erase) {
   using Slot = typename L::Slot;
   using Key = typename L::Key;
   const SvLane<L, G, S> ln;
-  constexpr int W = G * S;
+  constexpr int SW = G * S;  // slots of one step; a window is walked in H steps
+  constexpr int W = SW * H;
   Slot* slots = static_cast<Slot*>(t.slots);
   bool act = false;
   Key k = 0;
-  uint32_t w = 0, step = 0, j = 0, tag = 0;
+  uint32_t w = 0, step = 0, j = 0, tag = 0, h = 0;
   Feed<KIn> fk;
   while (true) {
     const bool more = src.ensure();
@@ -686,6 +724,7 @@ __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __
       } else {
         act = true;
         j = 0;
+        h = 0;
         probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step, tag);
       }
     }
@@ -695,7 +734,7 @@ __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __
     }
     Slot s[S];
     uint32_t mm = 0, me = 0, mt = 0;
-    const uint64_t lane_slot = static_cast<uint64_t>(w) * W + ln.r * S;
+    const uint64_t lane_slot = static_cast<uint64_t>(w) * W + h * SW + ln.r * S;
     if (act) {
       load_slots<L, S>(slots + lane_slot, s);
       classify<L, S>(s, k, mm, me, mt);
@@ -703,7 +742,7 @@ __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __
     const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
     const uint32_t be = group_vote<G>(me != 0, ln.gbase);
     uint32_t fw = 0xffffffffu;
-    if (t.ovf != nullptr && act && !bm && !be) fw = ovf_word(t.ovf, w);
+    if (t.ovf != nullptr && act && !bm && !be && h + 1 == H) fw = ovf_word(t.ovf, w);
     bool ok = false;
     if (act && bm && ln.r == __ffs(bm) - 1) {
       const int sub = __ffs(mm) - 1;
@@ -719,9 +758,14 @@ __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __
           act = false;
         }
         // else: another erase of the same key won; read the window again
-      } else if (be || !ovf_bit(fw, w, tag) || ++j >= t.p) {
+      } else if (be) {
         act = false;  // absent: nothing to erase
+      } else if (h + 1 < H) {
+        ++h;  // the rest of this window
+      } else if (!ovf_bit(fw, w, tag) || ++j >= t.p) {
+        act = false;
       } else {
+        h = 0;
         w = probe_next(w, step, t.p);
       }
     }
@@ -733,7 +777,7 @@ struct NoOnErase {
   __device__ void operator()(const Slot&) const {}
 };
 
-template <class L, int G, int S>
+template <class L, int G, int S, int H = 1>
 __global__ void __launch_bounds__(256) k_sv_erase(TableDesc t, const typename L::Key* __restrict__ keys, uint64_t n,
                                                   uint64_t per_warp) {
   RangeSrc src(n, per_warp, nullptr, 0);
@@ -741,7 +785,7 @@ __global__ void __launch_bounds__(256) k_sv_erase(TableDesc t, const typename L:
   uint32_t flags = 0;
   long long removed = 0;
   NoOnErase none;
-  sv_erase_range<L, G, S>(t, keys, src, flags, removed, none);
+  sv_erase_range<L, G, S, NoOnErase, typename L::Key, H>(t, keys, src, flags, removed, none);
   flush_flags(t.status, flags);
   flush_delta(t.size, -removed);
 }

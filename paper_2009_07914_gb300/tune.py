@@ -26,7 +26,7 @@ from . import api
 from ._binding import WC_OP_ERASE, WC_OP_INSERT, WC_OP_RETRIEVE, WC_SCHEME_BLOCKED, WC_SCHEME_DIRECT
 
 SHAPES = {  # slot bytes -> W -> valid lanes per key
-    8: {4: [1, 2, 4], 8: [1, 2, 4, 8], 16: [2, 4, 8, 16], 32: [4, 8, 16, 32]},
+    8: {4: [1, 2, 4], 8: [1, 2, 4, 8], 16: [1, 2, 4, 8, 16], 32: [4, 8, 16, 32]},
     16: {2: [1, 2], 4: [1, 2, 4], 8: [2, 4, 8], 16: [4, 8, 16]},
 }
 BLOCKS = (256, 128)

@@ -116,12 +116,17 @@ def test_served_workload_at_its_own_scale(env):
     sizes = [o.size() for o in ors]
     del ors
     dt = serve.DeviceTrace(tr, window_width=8)
-    ex = serve.wc_executor_create(0, 8, max_items=1024, tile_keys=512)
+    ex = serve.wc_executor_create(0, 8, max_items=1024, tile_keys=4096)
     poisson = wc_inputs.poisson_arrivals(0x5E5, nreq, rate_per_s=10_000.0)
+    from paper_2009_07914_gb300 import api
+    resident = sum(api.wc_table_get_info(h)["device_bytes"] for h in dt.tables)
     for mode, arr in ((0, poisson), (0, np.zeros(nreq, dtype=np.uint64)), (1, poisson)):
         dt.reset()
-        tim, st = serve.wc_serve_run(ex if mode == 0 else None, dt.requests(arr), mode, hbm_budget_bytes=4 << 30,
-                                     max_batch_keys=1 << 26, max_batch_items=1024, max_inflight=2)
+        # the tables' own bytes plus 1 GiB for the requests' buffers: binds when they queue
+        tim, st = serve.wc_serve_run(ex if mode == 0 else None, dt.requests(arr), mode,
+                                     hbm_budget_bytes=resident + (1 << 30), max_batch_keys=1 << 26,
+                                     max_batch_items=1024, max_inflight=2)
+        assert st["peak_admitted_bytes"] <= resident + (1 << 30)
         assert st["keys"] == sum(r["keys"].size for r in tr["requests"])
         assert (tim["completed_ns"] >= tim["launched_ns"]).all() and (tim["admitted_ns"] >= arr).all()
         for i, (got, exp) in enumerate(zip(dt.retrieve_results(), expect)):
