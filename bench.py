@@ -930,7 +930,7 @@ def run_served(args, dev):
     nreq = len(tr["requests"])
     keys_total = sum(r["keys"].size for r in tr["requests"])
     from paper_2009_07914_gb300 import api
-    resident = sum(api.wc_table_get_info(h)["device_bytes"] for h in dt.tables)
+    resident = sum(i["device_bytes"] + i["work_bytes"] for i in map(api.wc_table_get_info, dt.tables))
     # the tables plus 512 MiB of request buffers: admission binds whenever requests queue
     budget = resident + (512 << 20)
 

@@ -175,6 +175,9 @@ typedef struct {
   int32_t kind;
   int32_t options;          /* WC_OPT_* bits the table was created with */
   int32_t reserved;
+  uint64_t work_bytes;      /* device scratch and staging the table holds at the moment
+                               (grown on demand by region-split calls and host-buffer calls,
+                               kept until wc_table_destroy); not in device_bytes */
 } wc_table_info;
 
 /* Launch shape of one operation class.  group_size = lanes that probe one key together
@@ -395,11 +398,25 @@ typedef struct {
   int32_t key_bytes;
   int32_t value_bytes;
   int32_t slot_bytes;
+  /* bucket multi-value tables with a growth strategy (per-element appends); else zero */
+  void* pool;                          /* value pool, value_bytes per element */
+  unsigned long long* pool_cursor;     /* next free pool element */
+  unsigned long long* num_keys;        /* distinct live keys */
+  const uint64_t* bucket_cum_size;     /* lambda > 1: values in buckets 0..i, i < bucket_count */
+  const uint64_t* bucket_cum_foot;     /* lambda > 1: pool elements of buckets 0..i */
+  uint64_t pool_capacity;              /* pool elements */
+  uint64_t bucket_size;                /* lambda = 1: values per bucket (s0) */
+  uint64_t bucket_foot0, bucket_foot;  /* lambda = 1: pool elements of bucket 0 / of a later one */
+  uint32_t bucket_count;               /* lambda > 1: entries of the two tables */
+  int32_t growth;                      /* 1: lambda = 1, 2: lambda > 1 (the tables) */
+  uint64_t wait_ns;                    /* bound of an append's wait for a blocked list (0: 1 s) */
 } wc_device_view;
 
 /* Fill *h_out for a single-value table (per-element insert / retrieve / erase, for_each,
- * for_all) or an open-addressing multi-value table (for_all only).  Host only.
- * WC_ERR_UNSUPPORTED for bucket multi-value tables. */
+ * for_all), an open-addressing multi-value table (for_all only) or a bucket multi-value
+ * table created with a growth strategy (bucket_first_size > 0; per-element appends, whose
+ * pool must hold fewer than 2^34 elements).  Host only.  WC_ERR_UNSUPPORTED for other
+ * bucket multi-value tables (their buckets are sized per bulk call). */
 wc_status wc_table_device_view(const wc_table* t, wc_device_view* h_out);
 
 /* ---- host copies: inspection, checkpoint and resume (no counterpart in the paper) -- */

@@ -12,6 +12,9 @@
  * bulk calls: operations of one kind may run concurrently (from any number of threads and
  * kernels); an insert or erase must not overlap a retrieve on the same table (Sec. IV-D).
  *
+ * Bucket multi-value tables with a growth strategy take per-element appends (append
+ * below; Sec. IV-C), which the bulk count / retrieve calls see.
+ *
  * Per-element operations are executed by the calling thread alone: it walks the key's
  * probing sequence window by window (W slots each) -- the paper's cooperative group of
  * one thread.  Status conditions (DUPLICATE_KEY, INVALID_KEY, PROBE_LIMIT) are returned
@@ -365,6 +368,250 @@ __device__ bool erase(const wc_device_view& t, K key) {
 }
 
 #undef WC_DEV_DISPATCH
+
+// ---- per-element appends to a bucket multi-value table (Sec. IV-C) ----------------------
+//
+// A bucket multi-value table keeps each key once, in a key store of 16-byte slots
+// {uint64 key, uint64 list handle}, and the key's values in buckets of a value pool.  With
+// a growth strategy the key's buckets have the sizes s_0, s_i = ceil(lambda * s_(i-1)),
+// fixed when the table is created, and every bucket after the first starts with an 8-byte
+// header holding the handle of the bucket before it (the back reference the bulk count and
+// retrieve kernels follow).  The handle packs: bits [0, 28) the key's values, bit 28 "the
+// newest bucket has a predecessor", bits [29, 63) the pool offset of the newest bucket, and
+// bit 63 "blocked": a thread is making the key's next bucket (zero whenever no append runs,
+// so the bulk calls read the same handles).
+//
+// An append takes the next value number of its key with one CAS on the handle while the
+// newest bucket has room.  The value that finds it full (or the key without a bucket) CASes
+// the handle to blocked, takes the next bucket of the growth sequence from the pool,
+// writes the back reference and its value, and publishes the new handle with a release
+// store.  Appends that find the handle blocked back off exponentially; a wait is bounded
+// by view.wait_ns (%globaltimer), after which the append gives up with
+// WC_FLAG_QUEUE_TIMEOUT.  Appends may run concurrently with each other from any threads
+// and kernels; like every insert they must not overlap a lookup of the table (Sec. IV-D).
+
+namespace bl {
+
+constexpr uint64_t kCountBits = 28;
+constexpr uint64_t kMaxCount = (1ull << kCountBits) - 1;
+constexpr uint64_t kBlocked = 1ull << 63;
+
+__device__ __forceinline__ uint64_t count(uint64_t h) { return h & kMaxCount; }
+__device__ __forceinline__ uint64_t offset(uint64_t h) { return (h & ~kBlocked) >> (kCountBits + 1); }
+__device__ __forceinline__ uint64_t make(uint64_t off, uint64_t cnt, bool prev) {
+  return (off << (kCountBits + 1)) | (static_cast<uint64_t>(prev) << kCountBits) | cnt;
+}
+
+// Values held by buckets 0..i, and their pool elements (headers and padding included).
+__device__ __forceinline__ uint64_t cum_size(const wc_device_view& t, int64_t i) {
+  if (i < 0) return 0;
+  return t.growth == 1 ? static_cast<uint64_t>(i + 1) * t.bucket_size : t.bucket_cum_size[i];
+}
+__device__ __forceinline__ uint64_t cum_foot(const wc_device_view& t, int64_t i) {
+  if (i < 0) return 0;
+  return t.growth == 1 ? t.bucket_foot0 + static_cast<uint64_t>(i) * t.bucket_foot : t.bucket_cum_foot[i];
+}
+// The bucket holding value number v.
+__device__ __forceinline__ int64_t bucket_of(const wc_device_view& t, uint64_t v) {
+  if (t.growth == 1) return static_cast<int64_t>(v / t.bucket_size);
+  uint32_t lo = 0, hi = t.bucket_count - 1;  // first i with cum_size(i) > v
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (t.bucket_cum_size[mid] > v) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t x;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(x));
+  return x;
+}
+
+__device__ __forceinline__ uint64_t load_relaxed(const unsigned long long* p) {
+  uint64_t x;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(x) : "l"(p) : "memory");
+  return x;
+}
+
+__device__ __forceinline__ void store_release(unsigned long long* p, uint64_t x) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(x) : "memory");
+}
+
+// The key's slot in the key store (windows of W 16-byte slots, the probing sequence of
+// the bulk calls), inserted with handle 0 (no bucket) when absent: the earliest empty or
+// tombstoned slot of the walk, claimed with one 128-bit CAS.  -1 with the flag set when
+// the key store is full.
+template <int W>
+__device__ int64_t key_slot(const wc_device_view& t, unsigned long long key, uint32_t& flags) {
+  using S = Slots<unsigned long long>;
+  using Word = typename S::Word;
+  uint32_t w0, step;
+  probe_init(key, t.seed, t.windows, w0, step);
+  uint32_t w = w0, j = 0;
+  bool have_t = false;
+  uint64_t t_slot = 0;
+  Word t_word{};
+  while (j < t.windows) {
+    Window<unsigned long long, W> win;
+    win.load(t.slots, w);
+    const uint64_t base = static_cast<uint64_t>(w) * W;
+    bool empty = false;
+    int free_q = -1;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const unsigned long long k = S::key(win.slot(q));
+      if (k == key) return static_cast<int64_t>(base + q);
+      const bool is_empty = k == 0ull;
+      empty |= is_empty;
+      if ((is_empty || k == ~0ull) && free_q < 0) free_q = q;
+    }
+    if (empty || j + 1 == t.windows) {
+      if (have_t) {
+        if (S::cas(t.slots, t_slot, t_word, key, 0ull)) {
+          atomicAdd(t.num_keys, 1ull);
+          return static_cast<int64_t>(t_slot);
+        }
+        have_t = false;  // the tombstone was taken: walk again from the start
+        w = w0;
+        j = 0;
+        continue;
+      }
+      if (free_q < 0) {
+        flags |= WC_FLAG_PROBE_LIMIT;
+        return -1;
+      }
+      Word fw = win.slot(0);
+#pragma unroll
+      for (int q = 1; q < W; ++q)
+        if (q == free_q) fw = win.slot(q);
+      if (S::cas(t.slots, base + free_q, fw, key, 0ull)) {
+        atomicAdd(t.num_keys, 1ull);
+        return static_cast<int64_t>(base + free_q);
+      }
+      continue;  // the slot was taken (maybe by this key): read the window again
+    }
+    if (free_q >= 0 && !have_t) {
+      have_t = true;
+      t_slot = base + free_q;
+      t_word = win.slot(0);
+#pragma unroll
+      for (int q = 1; q < W; ++q)
+        if (q == free_q) t_word = win.slot(q);
+    }
+    w = probe_next(w, step, t.windows);
+    ++j;
+  }
+  flags |= WC_FLAG_PROBE_LIMIT;
+  return -1;
+}
+
+template <class V>
+__device__ __forceinline__ void put(const wc_device_view& t, uint64_t index, V value) {
+  static_cast<V*>(t.pool)[index] = value;
+}
+
+// Append value number c (the caller holds it) at its place in the key's bucket b whose
+// pool start is `start`.
+template <class V>
+__device__ __forceinline__ void put_value(const wc_device_view& t, uint64_t start, int64_t b, uint64_t c, V value) {
+  constexpr uint64_t hdr = 8 / sizeof(V);  // header elements of a non-first bucket
+  put<V>(t, start + (b > 0 ? hdr : 0) + (c - cum_size(t, b - 1)), value);
+}
+
+template <int W, class V>
+__device__ uint32_t append_w(const wc_device_view& t, unsigned long long key, V value) {
+  uint32_t flags = 0;
+  const int64_t slot = key_slot<W>(t, key, flags);
+  if (slot < 0) {
+    atomicOr(t.status, flags);
+    return flags;
+  }
+  unsigned long long* handle = reinterpret_cast<unsigned long long*>(static_cast<char*>(t.slots) + slot * 16 + 8);
+  const uint64_t limit = t.wait_ns ? t.wait_ns : 1000000000ull;
+  uint64_t t0 = 0;
+  uint32_t pause = 32;
+  for (uint32_t it = 0;; ++it) {
+    const uint64_t h = load_relaxed(handle);
+    const uint64_t c = count(h);
+    const bool blocked = (h & kBlocked) != 0;
+    if (!blocked && c >= kMaxCount) {
+      flags |= WC_FLAG_COUNT_OVERFLOW;
+      break;
+    }
+    const int64_t newest = c == 0 ? -1 : bucket_of(t, c - 1);
+    if (!blocked && newest >= 0 && c < cum_size(t, newest)) {
+      // room in the newest bucket: take value number c
+      if (atomicCAS(handle, h, h + 1) == h) {
+        put_value<V>(t, offset(h), newest, c, value);
+        atomicAdd(t.size, 1ull);
+        return 0;
+      }
+    } else if (!blocked) {
+      // the newest bucket is full (or there is none): make bucket newest + 1
+      if (atomicCAS(handle, h, h | kBlocked) == h) {
+        const int64_t b = newest + 1;
+        const uint64_t foot = cum_foot(t, b) - cum_foot(t, b - 1);
+        const uint64_t off = atomicAdd(t.pool_cursor, foot);
+        if (off + foot > t.pool_capacity) {
+          store_release(handle, h);  // unblock, unchanged
+          flags |= WC_FLAG_POOL_EXHAUSTED;
+          break;
+        }
+        if (b > 0) {
+          // back reference: the handle of the bucket before, as the bulk layout has it
+          *reinterpret_cast<unsigned long long*>(static_cast<char*>(t.pool) + off * sizeof(V)) = h;
+        }
+        put_value<V>(t, off, b, c, value);
+        store_release(handle, make(off, c + 1, b > 0));
+        atomicAdd(t.size, 1ull);
+        return 0;
+      }
+    } else {
+      // another thread is making the next bucket: back off, at most `limit` in all
+      if (t0 == 0) {
+        t0 = now_ns();
+      } else if (now_ns() - t0 > limit) {
+        flags |= WC_FLAG_QUEUE_TIMEOUT;
+        break;
+      }
+      __nanosleep(pause);
+      pause = pause < 4096 ? pause * 2 : pause;
+    }
+    // a lost CAS means another append went ahead; the same time bound covers the retries
+    if ((it & 63) == 63) {
+      if (t0 == 0) t0 = now_ns();
+      else if (now_ns() - t0 > limit) {
+        flags |= WC_FLAG_QUEUE_TIMEOUT;
+        break;
+      }
+    }
+  }
+  atomicOr(t.status, flags);
+  return flags;
+}
+
+}  // namespace bl
+
+// Append (key, value) to a bucket multi-value table with a growth strategy (wc_device_view
+// from wc_table_device_view): K is the table's key type (uint32_t or unsigned long long),
+// V its value type.  Returns 0, or the WC_FLAG_* bits of a failed append (INVALID_KEY,
+// PROBE_LIMIT, POOL_EXHAUSTED, COUNT_OVERFLOW, QUEUE_TIMEOUT), also OR-ed into the table's
+// status word.  The bulk count_values / retrieve_multi calls see the appended values.
+template <class K, class V>
+__device__ uint32_t append(const wc_device_view& t, K key, V value) {
+  if (is_sentinel(key)) {
+    atomicOr(t.status, static_cast<uint32_t>(WC_FLAG_INVALID_KEY));
+    return WC_FLAG_INVALID_KEY;
+  }
+  const unsigned long long k = static_cast<unsigned long long>(key);  // keys are stored as 8 bytes
+  switch (t.window_width) {
+    case 2: return bl::append_w<2, V>(t, k, value);
+    case 4: return bl::append_w<4, V>(t, k, value);
+    default: return bl::append_w<8, V>(t, k, value);
+  }
+}
 
 // ---- higher-order bulk calls ----------------------------------------------------------
 

@@ -62,14 +62,19 @@ class WcTableInfo(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_uint64), ("windows", ctypes.c_uint64), ("slot_bytes", ctypes.c_uint64),
                 ("table_bytes", ctypes.c_uint64), ("pool_capacity", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("window_width", ctypes.c_int32), ("kind", ctypes.c_int32),
-                ("options", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("options", ctypes.c_int32), ("reserved", ctypes.c_int32), ("work_bytes", ctypes.c_uint64)]
 
 
 class WcDeviceView(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_void_p), ("status", ctypes.c_void_p), ("size", ctypes.c_void_p),
                 ("overflow_bits", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("capacity", ctypes.c_uint64),
                 ("windows", ctypes.c_uint32), ("window_width", ctypes.c_uint32), ("kind", ctypes.c_int32),
-                ("key_bytes", ctypes.c_int32), ("value_bytes", ctypes.c_int32), ("slot_bytes", ctypes.c_int32)]
+                ("key_bytes", ctypes.c_int32), ("value_bytes", ctypes.c_int32), ("slot_bytes", ctypes.c_int32),
+                ("pool", ctypes.c_void_p), ("pool_cursor", ctypes.c_void_p), ("num_keys", ctypes.c_void_p),
+                ("bucket_cum_size", ctypes.c_void_p), ("bucket_cum_foot", ctypes.c_void_p),
+                ("pool_capacity", ctypes.c_uint64), ("bucket_size", ctypes.c_uint64),
+                ("bucket_foot0", ctypes.c_uint64), ("bucket_foot", ctypes.c_uint64),
+                ("bucket_count", ctypes.c_uint32), ("growth", ctypes.c_int32), ("wait_ns", ctypes.c_uint64)]
 
 
 class WcLaunch(ctypes.Structure):

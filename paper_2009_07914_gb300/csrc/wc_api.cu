@@ -552,6 +552,7 @@ wc_status wc_table_get_info(const wc_table* t, wc_table_info* h_out) {
   h_out->kind = t->cfg.kind;
   h_out->options = t->cfg.options;
   h_out->reserved = 0;
+  h_out->work_bytes = t->scratch_bytes + host_pipe_bytes(t);
   return WC_OK;
 }
 

@@ -117,8 +117,13 @@ wc_status wc_table_restore(wc_table* t, const void* h_in, uint64_t bytes, void* 
 
 wc_status wc_table_device_view(const wc_table* t, wc_device_view* h_out) {
   if (t == nullptr || h_out == nullptr) return WC_ERR_INVALID_ARG;
-  if ((t->cfg.kind != WC_SINGLE_VALUE && t->cfg.kind != WC_MULTI_VALUE_OA) || t->d_vals != nullptr)
+  const bool bl = t->cfg.kind == WC_MULTI_VALUE;
+  if ((t->cfg.kind != WC_SINGLE_VALUE && t->cfg.kind != WC_MULTI_VALUE_OA && !bl) || t->d_vals != nullptr)
     return WC_ERR_UNSUPPORTED;
+  // per-element appends need buckets of known sizes (a growth strategy) and pool offsets
+  // below bit 63 of the list handle, which marks a list whose next bucket is being made
+  if (bl && (t->growth == wc::kGrowExact || t->pool_capacity >= (1ull << 34))) return WC_ERR_UNSUPPORTED;
+  *h_out = wc_device_view{};
   h_out->slots = t->d_slots;
   h_out->status = t->d_status;
   h_out->size = t->d_size;
@@ -131,6 +136,19 @@ wc_status wc_table_device_view(const wc_table* t, wc_device_view* h_out) {
   h_out->key_bytes = t->cfg.key_bytes;
   h_out->value_bytes = t->cfg.value_bytes;
   h_out->slot_bytes = static_cast<int32_t>(t->slot_bytes);
+  if (bl) {
+    h_out->pool = t->d_pool;
+    h_out->pool_cursor = t->d_cursor;
+    h_out->num_keys = t->d_nkeys;
+    h_out->pool_capacity = t->pool_capacity;
+    h_out->growth = t->growth;
+    h_out->bucket_size = t->cfg.bucket_first_size;
+    h_out->bucket_foot0 = t->grow_foot0;
+    h_out->bucket_foot = t->grow_foot;
+    h_out->bucket_count = t->nbuckets;
+    h_out->bucket_cum_size = t->d_growth;
+    h_out->bucket_cum_foot = t->d_growth ? t->d_growth + t->nbuckets : nullptr;
+  }
   return WC_OK;
 }
 

@@ -24,6 +24,10 @@ struct HostPipe {
   uint64_t each = 0;
 };
 
+uint64_t host_pipe_bytes(const wc_table* t) {
+  return t->host != nullptr && t->host->stage != nullptr ? kStages * t->host->each : 0;
+}
+
 void host_pipe_free(wc_table* t) {
   HostPipe* h = t->host;
   if (h == nullptr) return;

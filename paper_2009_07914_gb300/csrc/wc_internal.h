@@ -178,6 +178,9 @@ cudaError_t ensure_scratch(const wc_table* t, uint64_t bytes, cudaStream_t s);
 // Release the table's host-buffer pipeline (streams, events, staging).
 void host_pipe_free(wc_table* t);
 
+// Device bytes of the table's host-buffer staging (0 before the first host-buffer call).
+uint64_t host_pipe_bytes(const wc_table* t);
+
 // Scheme the table uses for `op` on a batch of n keys.
 int scheme_for(const wc_table* t, int op, uint64_t n);
 

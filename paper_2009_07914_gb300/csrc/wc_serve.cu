@@ -53,7 +53,7 @@ extern "C" wc_status wc_serve_run(wc_executor* ex, const wc_request* reqs, uint3
     for (uint32_t i = 0; i < nreq; ++i) {
       const wc_table* t = reqs[i].work.table;
       if (t == nullptr) return WC_ERR_INVALID_ARG;
-      if (seen.insert(t).second) resident += t->device_bytes + t->scratch_bytes;
+      if (seen.insert(t).second) resident += t->device_bytes + t->scratch_bytes + wc::host_pipe_bytes(t);
     }
   }
   if (resident > cfg->hbm_budget_bytes) return WC_ERR_OUT_OF_MEMORY;

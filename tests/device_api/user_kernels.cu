@@ -46,6 +46,16 @@ __global__ void k_fused_insert(wc_device_view v, uint64_t n, uint32_t seed, uint
   }
 }
 
+// Per-element appends to a bucket multi-value table, all in one launch (concurrent).
+template <class K, class V>
+__global__ void k_mv_append(wc_device_view v, const K* keys, const V* vals, uint64_t n, uint32_t* flags) {
+  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const uint32_t f = wc_dev::append<K, V>(v, keys[i], vals[i]);
+    if (f) atomicOr(flags, f);
+  }
+}
+
 unsigned grid(uint64_t n) { return static_cast<unsigned>((n + 255) / 256); }
 
 }  // namespace
@@ -81,6 +91,29 @@ int wcu_erase(const wc_device_view* v, const void* keys, uint64_t n, unsigned lo
   else
     k_erase<unsigned long long><<<grid(n), 256>>>(*v, static_cast<const unsigned long long*>(keys), n, erased);
   return static_cast<int>(cudaDeviceSynchronize());
+}
+
+int wcu_mv_append(const wc_device_view* v, const void* keys, const void* vals, uint64_t n, uint32_t* flags) {
+  if (n == 0) return 0;
+  if (v->key_bytes == 4 && v->value_bytes == 4)
+    k_mv_append<uint32_t, uint32_t><<<grid(n), 256>>>(*v, static_cast<const uint32_t*>(keys),
+                                                      static_cast<const uint32_t*>(vals), n, flags);
+  else if (v->key_bytes == 8 && v->value_bytes == 4)
+    k_mv_append<unsigned long long, uint32_t><<<grid(n), 256>>>(*v, static_cast<const unsigned long long*>(keys),
+                                                                static_cast<const uint32_t*>(vals), n, flags);
+  else if (v->key_bytes == 8)
+    k_mv_append<unsigned long long, unsigned long long><<<grid(n), 256>>>(
+        *v, static_cast<const unsigned long long*>(keys), static_cast<const unsigned long long*>(vals), n, flags);
+  else
+    k_mv_append<uint32_t, unsigned long long><<<grid(n), 256>>>(*v, static_cast<const uint32_t*>(keys),
+                                                                static_cast<const unsigned long long*>(vals), n, flags);
+  return static_cast<int>(cudaDeviceSynchronize());
+}
+
+// Write one 8-byte word of device memory from the host (the tests' way to leave a list
+// handle blocked, as if its owner had stopped).
+int wcu_poke_u64(void* dptr, uint64_t value) {
+  return static_cast<int>(cudaMemcpy(dptr, &value, 8, cudaMemcpyHostToDevice));
 }
 
 int wcu_fused_insert(const wc_device_view* v, uint64_t n, uint32_t seed, uint32_t* flags) {

@@ -43,6 +43,8 @@ def env(tmp_path_factory):
     lib.wcu_fused_insert.argtypes = [V, u64, u32, vp]
     lib.wcu_for_each.argtypes = [V, vp, u64, vp, vp]
     lib.wcu_for_all.argtypes = [V, vp]
+    lib.wcu_mv_append.argtypes = [V, vp, vp, u64, vp]
+    lib.wcu_poke_u64.argtypes = [vp, u64]
     return wc, torch, lib
 
 
@@ -187,3 +189,121 @@ def test_library_device_api_probe(env):
     wc_bench_device_api(t.handle, 1, n, seed, sink)
     assert int(sink.item()) == int(idx[valid].sum())
     check_dump(wc, t, 1)
+
+
+
+# ---- per-element appends to a bucket multi-value table (Sec. IV-C) -----------------------
+
+def _mv_view(wc, t, wait_ns=0):
+    v = wc._binding.WcDeviceView()
+    wc._binding.check(wc._binding.lib().wc_table_device_view(t.handle, ctypes.byref(v)), "wc_table_device_view")
+    v.wait_ns = wait_ns
+    return v
+
+
+def _mv_check(t, o, queries):
+    offs, _ = t.count_values(queries)
+    eoffs, _ = o.count_values(queries)
+    np.testing.assert_array_equal(offs, eoffs)
+    vals, _ = t.retrieve_multi(queries, offs)
+    evals, _ = o.retrieve_multi(queries, eoffs)
+    np.testing.assert_array_equal(oracle.sorted_segments(vals, offs), oracle.sorted_segments(evals, eoffs))
+
+
+@pytest.mark.parametrize("kb,vb", [(4, 4), (8, 4), (8, 8)])
+@pytest.mark.parametrize("s0,lam", [(1, 1.1), (4, 1.0), (1, 2.0)])
+def test_device_appends_build_the_bucket_lists(env, kb, vb, s0, lam):
+    """Concurrent per-element appends of hot keys (2^18 values over 1000 keys, every key's
+    copies spread over the launch) against the multiset oracle, then a bulk insert into
+    the same lists and appends again: counts, offsets and sorted values per key equal the
+    oracle's; the size counts every value, the key count every distinct key."""
+    wc, torch, lib = env
+    n, nk = 1 << 18, 1000
+    kdt = np.uint32 if kb == 4 else np.uint64
+    vdt = np.uint32 if vb == 4 else np.uint64
+    uni = (wc_inputs.distinct_u32(0xB1 + kb, nk) if kb == 4 else wc_inputs.distinct_u64(0xB1 + kb, nk)).astype(kdt)
+    absent = uni[: nk // 4] ^ kdt(0x5A5A5A5A)
+    absent = absent[~np.isin(absent, uni) & (absent != 0)]
+    rng = np.random.default_rng(kb * 8 + vb)
+    t = wc.MultiValueTable(kb, vb, min_capacity=2 * nk, value_pool_capacity=8 * n, bucket_first_size=s0,
+                           bucket_growth=lam)
+    o = oracle.MultiValue(kb, vb)
+    v = _mv_view(wc, t)
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for rnd in range(2):
+        keys = uni[rng.integers(0, nk, n)]
+        vals = rng.integers(0, 1 << (8 * vb - 1), n, dtype=np.uint64).astype(vdt)
+        dk, dv = dev(torch, keys, kb), dev(torch, vals, vb)
+        assert lib.wcu_mv_append(ctypes.byref(v), dk.data_ptr(), dv.data_ptr(), n, flags.data_ptr()) == 0
+        o.insert(keys, vals)
+        assert int(flags.item()) == 0 and t.status(clear=True) == 0
+        assert t.size() == o.size() and t.num_keys() == nk
+        _mv_check(t, o, np.concatenate([uni, absent]))
+        if rnd == 0:  # a bulk insert fills the lists' last buckets and adds more
+            bk = uni[rng.integers(0, nk, 5000)]
+            bv = rng.integers(0, 1 << (8 * vb - 1), 5000, dtype=np.uint64).astype(vdt)
+            t.insert(bk, bv)
+            o.insert(bk, bv)
+            _mv_check(t, o, uni)
+
+
+def test_device_appends_stop_at_a_full_pool(env):
+    """A pool too small for the appends: POOL_EXHAUSTED is raised and what was stored is
+    consistent -- every key's values are a sub-multiset of its appended ones, and the
+    counts add up to the size."""
+    wc, torch, lib = env
+    n, nk = 50_000, 300
+    uni = wc_inputs.distinct_u32(0xC4, nk)
+    rng = np.random.default_rng(9)
+    keys = uni[rng.integers(0, nk, n)]
+    vals = np.arange(n, dtype=np.uint32)
+    t = wc.MultiValueTable(4, 4, min_capacity=2 * nk, value_pool_capacity=n // 2, bucket_first_size=2,
+                           bucket_growth=1.5)
+    v = _mv_view(wc, t)
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dk, dv = dev(torch, keys, 4), dev(torch, vals, 4)
+    assert lib.wcu_mv_append(ctypes.byref(v), dk.data_ptr(), dv.data_ptr(), n, flags.data_ptr()) == 0
+    assert int(flags.item()) & wc.WC_FLAG_POOL_EXHAUSTED
+    assert t.status(clear=True) & wc.WC_FLAG_POOL_EXHAUSTED
+    offs, _ = t.count_values(uni)
+    got, _ = t.retrieve_multi(uni, offs)
+    assert int(offs[-1]) == t.size() < n
+    for i in range(nk):
+        seg = got[offs[i]:offs[i + 1]]
+        mine = vals[keys == uni[i]]
+        assert np.isin(seg, mine).all() and np.unique(seg).size == seg.size
+
+
+def test_device_append_wait_is_bounded(env):
+    """A list handle left blocked (its blocked bit set from the host, as if the thread
+    making its next bucket had stopped): an append to that key waits at most wait_ns, then
+    returns QUEUE_TIMEOUT and sets it in the status word -- the kernel ends; appends of other
+    keys are unaffected.  Clearing the bit lets appends of the key go on."""
+    wc, torch, lib = env
+    t = wc.MultiValueTable(8, 4, min_capacity=64, value_pool_capacity=1024, bucket_first_size=1, bucket_growth=1.0)
+    v = _mv_view(wc, t, wait_ns=2_000_000)
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    k = np.array([0x1234567, 0x7654321], dtype=np.uint64)
+    one = np.array([7, 8], dtype=np.uint32)
+    assert lib.wcu_mv_append(ctypes.byref(v), dev(torch, k, 8).data_ptr(), dev(torch, one, 4).data_ptr(), 2,
+                             flags.data_ptr()) == 0
+    assert int(flags.item()) == 0
+    dump = wc.api.wc_table_dump_slots(t.handle).view(np.uint64).reshape(-1, 2)
+    idx = int(np.nonzero(dump[:, 0] == k[0])[0][0])
+    handle = int(dump[idx, 1])
+    addr = v.slots + idx * 16 + 8
+    assert lib.wcu_poke_u64(addr, handle | (1 << 63)) == 0
+    k2 = np.array([k[0], k[1]], dtype=np.uint64)
+    assert lib.wcu_mv_append(ctypes.byref(v), dev(torch, k2, 8).data_ptr(), dev(torch, one, 4).data_ptr(), 2,
+                             flags.data_ptr()) == 0
+    assert int(flags.item()) == wc.WC_FLAG_QUEUE_TIMEOUT
+    assert t.status(clear=True) == wc.WC_FLAG_QUEUE_TIMEOUT
+    assert lib.wcu_poke_u64(addr, handle) == 0
+    flags.zero_()
+    assert lib.wcu_mv_append(ctypes.byref(v), dev(torch, k[:1], 8).data_ptr(), dev(torch, one[1:], 4).data_ptr(), 1,
+                             flags.data_ptr()) == 0
+    assert int(flags.item()) == 0
+    offs, _ = t.count_values(k)
+    got, _ = t.retrieve_multi(k, offs)
+    assert list(np.diff(offs)) == [2, 2]
+    assert sorted(got[:2].tolist()) == [7, 8] and sorted(got[2:].tolist()) == [8, 8]

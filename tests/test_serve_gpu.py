@@ -69,7 +69,7 @@ def test_admission_respects_the_hbm_budget(env):
     reqs = dt.requests(np.zeros(len(tr["requests"]), dtype=np.uint64))  # all arrive at once
     biggest = max(r.io_bytes for r in reqs)
     from paper_2009_07914_gb300 import api
-    resident = sum(api.wc_table_get_info(h)["device_bytes"] for h in dt.tables)
+    resident = sum(i["device_bytes"] + i["work_bytes"] for i in map(api.wc_table_get_info, dt.tables))
     budget = resident + 2 * biggest
     ex = serve.wc_executor_create(0, 8, max_items=64, tile_keys=1024)
     # the tables alone do not fit in a budget of their own size minus one byte
@@ -119,7 +119,7 @@ def test_served_workload_at_its_own_scale(env):
     ex = serve.wc_executor_create(0, 8, max_items=1024, tile_keys=4096)
     poisson = wc_inputs.poisson_arrivals(0x5E5, nreq, rate_per_s=10_000.0)
     from paper_2009_07914_gb300 import api
-    resident = sum(api.wc_table_get_info(h)["device_bytes"] for h in dt.tables)
+    resident = sum(i["device_bytes"] + i["work_bytes"] for i in map(api.wc_table_get_info, dt.tables))
     for mode, arr in ((0, poisson), (0, np.zeros(nreq, dtype=np.uint64)), (1, poisson)):
         dt.reset()
         # the tables' own bytes plus 1 GiB for the requests' buffers: binds when they queue
