@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access roofline probe")
-    ap.add_argument("--kif", type=int, default=0, help="sv32: keys in flight per group of the lookups (1, 2; 0 = default)")
+    ap.add_argument("--kif", default="0",
+                    help="sv32: keys in flight per group (1, 2; 0 = default): K for the lookups, or K_insert,K_lookup")
     ap.add_argument("--alphas", default="0.5,0.8,0.9,0.95,0.99",
                     help="sv32: target loads of the density sweep reported beside the headline ('' = none)")
     ap.add_argument("--soa", action="store_true", help="sv32: struct-of-arrays table (keys and values in two arrays)")
@@ -470,6 +471,7 @@ def run_wc(args, rank, world, local_rank):
         "config": {"workload": workload_name, "n": n, "queries": n, "present_fraction": 0.5,
                    "capacity": info["capacity"], "achieved_alpha": n / info["capacity"],
                    "window_slots": info["window_width"], "group_insert": g_ins, "group_retrieve": g_ret,
+                   "insert_keys_in_flight": api.wc_table_get_launch(h, wc.WC_OP_INSERT)["keys_in_flight"],
                    "retrieve_keys_in_flight": api.wc_table_get_launch(h, wc.WC_OP_RETRIEVE)["keys_in_flight"],
                    "table_bytes": info["table_bytes"], "overflow_bits": bool(info["options"] & 1),
                    "layout": "struct of arrays" if info["options"] & 2 else "packed 64-bit slots",
@@ -508,20 +510,23 @@ def run_wc(args, rank, world, local_rank):
     api.wc_table_destroy(h)
 
 
-def apply_groups(api, wc, h, spec: str, kif: int = 0):
+def apply_groups(api, wc, h, spec: str, kif: str = "0"):
     """--group: one lane count for every operation, or one per operation (insert,
-    retrieve[, erase]); 0 keeps the table's default.  kif: keys in flight per group of
-    the lookups (0 keeps the default)."""
+    retrieve[, erase]); 0 keeps the table's default.  kif: keys in flight per group, for
+    the lookups alone ("2") or for insert and lookups ("2,2"); 0 keeps the default."""
     gs = [int(x) for x in str(spec).split(",") if x.strip()]
     if len(gs) == 1:
         gs = gs * 3
     for op, g in zip((wc.WC_OP_INSERT, wc.WC_OP_RETRIEVE, wc.WC_OP_ERASE), gs):
         if g:
             api.wc_table_set_launch(h, op, g)
-    if kif:
-        lc = api.wc_table_get_launch(h, wc.WC_OP_RETRIEVE)
-        api.wc_table_set_launch(h, wc.WC_OP_RETRIEVE, lc["group_size"], lc["block_threads"], lc["blocks_per_sm"],
-                                lc["scheme"], lc["region_mib"], kif)
+    ks = [int(x) for x in str(kif).split(",") if x.strip()]
+    ops = (wc.WC_OP_RETRIEVE,) if len(ks) == 1 else (wc.WC_OP_INSERT, wc.WC_OP_RETRIEVE)
+    for op, k in zip(ops, ks):
+        if k:
+            lc = api.wc_table_get_launch(h, op)
+            api.wc_table_set_launch(h, op, lc["group_size"], lc["block_threads"], lc["blocks_per_sm"], lc["scheme"],
+                                    lc["region_mib"], k)
 
 
 def load_sweep(args, api, wc, h_main, keys, vals, qk, out, found, n, s, peak, rank, local_rank):
@@ -930,6 +935,7 @@ def run_served(args, dev):
     nreq = len(tr["requests"])
     keys_total = sum(r["keys"].size for r in tr["requests"])
     from paper_2009_07914_gb300 import api
+    dt.reset()  # the pre-fill grows the tables' scratch to its size for the run
     resident = sum(i["device_bytes"] + i["work_bytes"] for i in map(api.wc_table_get_info, dt.tables))
     # the tables plus 512 MiB of request buffers: admission binds whenever requests queue
     budget = resident + (512 << 20)
