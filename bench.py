@@ -487,7 +487,10 @@ def run_wc(args, rank, world, local_rank):
                      # measured duration: how close the random walk runs to the copy bandwidth
                      "dram_gbs": None if traffic is None else traffic / (dom_ms * 1e-3) / 1e9,
                      "dram_frac": None if traffic is None else traffic / (dom_ms * 1e-3) / 1e9 / peak,
-                     "dram_sectors_per_op": None if traffic is None else traffic / 32 / n},
+                     "dram_sectors_per_op": None if traffic is None else traffic / 32 / n,
+                     # a random miss fills a whole 128-byte L2 line (measured with the library's
+                     # random-access probe): the traffic in lines per operation
+                     "dram_lines_per_op": None if traffic is None else traffic / 128 / n},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (insert_launches(api, h, n) + 1) * args.steps,
         "clocks": clk.summary(),
     }
@@ -931,7 +934,9 @@ def run_served(args, dev):
     from paper_2009_07914_gb300 import serve
     tr = wc_inputs.serving_trace(0x57C00005, n_tables=64, n_requests=args.requests)
     dt = serve.DeviceTrace(tr, device=dev.index, window_width=8)
-    ex = serve.wc_executor_create(dev.index, 8, max_items=1024, tile_keys=4096)
+    from paper_2009_07914_gb300 import tune
+    groups = tune.executor_groups(8, use_cache=False)  # lanes per key of the executor, timed on this GPU
+    ex = serve.wc_executor_create(dev.index, 8, max_items=1024, tile_keys=4096, **groups)
     nreq = len(tr["requests"])
     keys_total = sum(r["keys"].size for r in tr["requests"])
     from paper_2009_07914_gb300 import api
@@ -957,16 +962,21 @@ def run_served(args, dev):
     with ClockSampler(dev.index) as clk:
         runs["per_call_closed"] = run(1, zero)
         runs["batched_closed"] = run(0, zero)
+        # requests of 2^20 keys or more go as their own bulk calls (the per-call path splits
+        # large inserts by table region), the rest are packed into executor batches
+        runs["batched_solo_closed"] = run(0, zero, solo=1 << 20)
         runs["batched_small_batches_closed"] = run(0, zero, solo=1 << 20, max_keys=1 << 22)
         sat = nreq / (runs["per_call_closed"]["wall_ms"] * 1e-3)
         for f in (0.5, 0.8, 0.95):
             arr = wc_inputs.poisson_arrivals(0x57C00005 + int(f * 100), nreq, f * sat)
             runs["per_call_%.2f" % f] = run(1, arr)
             runs["batched_%.2f" % f] = run(0, arr)
+            runs["batched_solo_%.2f" % f] = run(0, arr, solo=1 << 20)
     b, p = runs["batched_closed"], runs["per_call_closed"]
     _common(args, "served_64tables_%dreq" % nreq, "G keys/s served (batched, closed loop)", b["throughput_gkeys"],
             "G keys/s", b["wall_ms"], "u32", {"tables": 64, "requests": nreq, "keys": keys_total,
                                               "per_call_saturation_req_per_s": sat, "hbm_budget_bytes": budget,
+                                              "executor_groups": groups,
                                               "resident_table_bytes": resident}, clk,
             b["launches"], {"runs": runs, "batched_over_per_call": b["throughput_gkeys"] / p["throughput_gkeys"]})
     serve.wc_executor_destroy(ex)

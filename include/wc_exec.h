@@ -55,6 +55,10 @@ typedef struct {
   int32_t test_stall;     /* testing: 1 = the first write item of every batch is never
                              reported complete, so items depending on it time out */
   int32_t reserved;
+  int32_t group_insert;   /* lanes per key of inserts (0 = 2 for W 8 and 16, 1 for W 4);
+                             W 4: 1 or 2, W 8: 1, 2 or 4, W 16: 2 or 4 -- e.g. the autotuner's
+                             direct-insert choice for the tables' key width and load */
+  int32_t group_retrieve; /* lanes per key of lookups and erases (0 = 2, 4 for W 16); same sets */
 } wc_executor_config;
 
 /* Create an executor: device work-list buffers, two pinned host staging buffers, the

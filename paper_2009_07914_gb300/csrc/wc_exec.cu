@@ -79,23 +79,9 @@ __device__ bool wait_group(const unsigned long long* gtiles, const unsigned long
   }
 }
 
-// Lanes per key per operation for each window width (packed 64-bit slots).
-template <int W>
-struct ExecShape;
-template <>
-struct ExecShape<4> {
-  static constexpr int GI = 1, GR = 1;
-};
-template <>
-struct ExecShape<8> {
-  static constexpr int GI = 2, GR = 2;
-};
-template <>
-struct ExecShape<16> {
-  static constexpr int GI = 2, GR = 4;
-};
-
-template <int W>
+// Lanes per key per operation (packed 64-bit slots): GI for inserts, GR for lookups and
+// erases; the kernel is instantiated for every valid pair of each window width.
+template <int W, int GI, int GR>
 __global__ void __launch_bounds__(kExecThreads, 3) k_exec(const ExecHeader* __restrict__ hdr,
                                                        const unsigned long long* __restrict__ gtiles,
                                                        const ExecItem* __restrict__ items,
@@ -105,8 +91,7 @@ __global__ void __launch_bounds__(kExecThreads, 3) k_exec(const ExecHeader* __re
                                                        unsigned long long* item_flags, uint32_t* xstatus,
                                                        uint64_t timeout_ns) {
   using L = LayoutP32;
-  constexpr int GI = ExecShape<W>::GI, SI = W / GI;
-  constexpr int GR = ExecShape<W>::GR, SR = W / GR;
+  constexpr int SI = W / GI, SR = W / GR;
   __shared__ uint64_t s_tb[kMaxExecItems];
   const uint32_t nitems = hdr->nitems;
   const uint64_t total = hdr->total_tiles;
@@ -217,9 +202,16 @@ void free_executor(wc_executor* ex) {
   delete ex;
 }
 
-template <int W>
-void* kernel_for() {
-  return reinterpret_cast<void*>(k_exec<W>);
+// The kernel of (W, GI, GR), or nullptr for a pair outside the instantiated sets.
+void* kernel_for(int W, int GI, int GR) {
+#define WC_EXEC_K(Wv, I, R) \
+  if (W == (Wv) && GI == (I) && GR == (R)) return reinterpret_cast<void*>(k_exec<Wv, I, R>);
+  WC_EXEC_K(4, 1, 1) WC_EXEC_K(4, 1, 2) WC_EXEC_K(4, 2, 1) WC_EXEC_K(4, 2, 2)
+  WC_EXEC_K(8, 1, 1) WC_EXEC_K(8, 1, 2) WC_EXEC_K(8, 1, 4) WC_EXEC_K(8, 2, 1) WC_EXEC_K(8, 2, 2)
+  WC_EXEC_K(8, 2, 4) WC_EXEC_K(8, 4, 1) WC_EXEC_K(8, 4, 2) WC_EXEC_K(8, 4, 4)
+  WC_EXEC_K(16, 2, 2) WC_EXEC_K(16, 2, 4) WC_EXEC_K(16, 4, 2) WC_EXEC_K(16, 4, 4)
+#undef WC_EXEC_K
+  return nullptr;
 }
 
 }  // namespace
@@ -242,7 +234,13 @@ wc_status wc_executor_create(wc_executor** out, const wc_executor_config* cfg) {
   DeviceGuard guard(cfg->device);
   ex->sm_count = sm_count_of(cfg->device);
   ex->lay = Layout(cfg->max_items);
-  ex->kernel = W == 4 ? kernel_for<4>() : W == 8 ? kernel_for<8>() : kernel_for<16>();
+  const int gi = cfg->group_insert ? cfg->group_insert : (W == 4 ? 1 : 2);
+  const int gr = cfg->group_retrieve ? cfg->group_retrieve : (W == 16 ? 4 : 2);
+  ex->kernel = kernel_for(W, gi, gr);
+  if (ex->kernel == nullptr) {
+    delete ex;
+    return WC_ERR_INVALID_ARG;
+  }
   bool ok = cudaMalloc(&ex->d_buf, ex->lay.total) == cudaSuccess &&
             cudaMemset(ex->d_buf, 0, ex->lay.total) == cudaSuccess;
   for (int i = 0; ok && i < 2; ++i) {

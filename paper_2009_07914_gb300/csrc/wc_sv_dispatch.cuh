@@ -66,9 +66,6 @@ cudaError_t sv_insert_op(const wc_table* t, const void* keys, const void* vals, 
   const TableDesc d = desc_of(t);
   const Key* k = static_cast<const Key*>(keys);
   auto kern = k_sv_insert<L, G, S, H>;
-  // two keys per group: windows of at most 32 bytes per lane (register budget)
-  if constexpr (H == 1 && (S * L::kWords * 8 <= 32 || (L::kHalf && S * 4 <= 32)))
-    if (lc.keys_in_flight == 2) kern = k_sv_insert<L, G, S, H, 2>;
   const int bps = lc.blocks_per_sm > 0 ? lc.blocks_per_sm : occupancy(kern, block);
   const EngineGrid g = engine_grid(n, G, block, bps, t->sm_count);
   if (scheme_for(t, WC_OP_INSERT, n) != WC_SCHEME_BLOCKED)

@@ -50,6 +50,34 @@ __device__ __forceinline__ void classify(const typename L::Slot (&s)[S], typenam
   }
 }
 
+// Steps of a window walk (a window of H steps of SW slots): offset of step h in the
+// window, whether h is its last step, whether steps follow.  With H == 1 they are the
+// constants 0 / true / false, so a whole-window walk carries no step bookkeeping.
+template <int H>
+struct Steps {
+  static __device__ __forceinline__ uint32_t offset(uint32_t h, int SW) {
+    if constexpr (H == 1) {
+      return 0;
+    } else {
+      return h * static_cast<uint32_t>(SW);
+    }
+  }
+  static __device__ __forceinline__ bool last(uint32_t h) {
+    if constexpr (H == 1) {
+      return true;
+    } else {
+      return Steps<H>::last(h);
+    }
+  }
+  static __device__ __forceinline__ bool more(uint32_t h) {
+    if constexpr (H == 1) {
+      return false;
+    } else {
+      return Steps<H>::more(h);
+    }
+  }
+};
+
 template <class K>
 __device__ __forceinline__ bool is_sentinel(K k) {
   return k == K(0) || k == K(~K(0));
@@ -248,7 +276,7 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
     Slot s[S];
     uint32_t mm = 0, me = 0, mt = 0;
     if (act) {
-      load_slots<L, S>(slots + static_cast<uint64_t>(w) * W + h * SW + ln.r * S, s);
+      load_slots<L, S>(slots + static_cast<uint64_t>(w) * W + Steps<H>::offset(h, SW) + ln.r * S, s);
       classify<L, S>(s, k, mm, me, mt);
     }
     const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
@@ -258,19 +286,19 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
     // (to save the dependent round trip) measured slower: the lookup is bound by the L2's
     // request rate, and every trip would then make two requests.
     uint32_t fw = 0xffffffffu;
-    if (t.ovf != nullptr && act && !bm && !be && h + 1 == H) fw = ovf_word(t.ovf, w);
+    if (t.ovf != nullptr && act && !bm && !be && Steps<H>::last(h)) fw = ovf_word(t.ovf, w);
     Slot hit = pick<L, S>(s, mm ? __ffs(mm) - 1 : 0);
     if constexpr (G > 1) hit = L::shfl(hit, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
     uint64_t hidx = 0;
     if constexpr (L::kSoA) {
-      hidx = static_cast<uint64_t>(w) * W + h * SW + ln.r * S + (mm ? __ffs(mm) - 1 : 0);
+      hidx = static_cast<uint64_t>(w) * W + Steps<H>::offset(h, SW) + ln.r * S + (mm ? __ffs(mm) - 1 : 0);
       if constexpr (G > 1) hidx = __shfl_sync(kFull, hidx, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
     }
     if constexpr (kDedup) {
       if (act) {
         // an empty slot ends the walk wherever it is; the rest of a window follows its
         // first part; a whole window without either ends it through its overflow bit
-        const bool next_part = !bm && !be && h + 1 < H;
+        const bool next_part = !bm && !be && Steps<H>::more(h);
         const bool done = !next_part && (bm || be || !ovf_bit(fw, w, tag) || ++j >= t.p);
         if (done && ln.r == 0) {
           emit(pos, bm != 0, hit, hidx);
@@ -293,7 +321,7 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
       } else if (be) {
         if (ln.r == 0) emit(pos, false, hit, hidx);
         act = false;
-      } else if (h + 1 < H) {
+      } else if (Steps<H>::more(h)) {
         ++h;  // the rest of this window
       } else if (!ovf_bit(fw, w, tag) || ++j >= t.p) {
         if (ln.r == 0) emit(pos, false, hit, hidx);
@@ -367,7 +395,7 @@ __device__ __forceinline__ void sv_retrieve_range_k(const TableDesc& t, const KI
     Slot s[K][S];
 #pragma unroll
     for (int q = 0; q < K; ++q)
-      if (act[q]) load_slots<L, S>(slots + static_cast<uint64_t>(w[q]) * W + h[q] * SW + ln.r * S, s[q]);
+      if (act[q]) load_slots<L, S>(slots + static_cast<uint64_t>(w[q]) * W + Steps<H>::offset(h[q], SW) + ln.r * S, s[q]);
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       uint32_t mm = 0, me = 0, mt = 0;
@@ -375,12 +403,12 @@ __device__ __forceinline__ void sv_retrieve_range_k(const TableDesc& t, const KI
       const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
       const uint32_t be = group_vote<G>(me != 0, ln.gbase);
       uint32_t fw = 0xffffffffu;
-      if (t.ovf != nullptr && act[q] && !bm && !be && h[q] + 1 == H) fw = ovf_word(t.ovf, w[q]);
+      if (t.ovf != nullptr && act[q] && !bm && !be && Steps<H>::last(h[q])) fw = ovf_word(t.ovf, w[q]);
       Slot hit = pick<L, S>(s[q], mm ? __ffs(mm) - 1 : 0);
       if constexpr (G > 1) hit = L::shfl(hit, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
       uint64_t hidx = 0;
       if constexpr (L::kSoA) {
-        hidx = static_cast<uint64_t>(w[q]) * W + h[q] * SW + ln.r * S + (mm ? __ffs(mm) - 1 : 0);
+        hidx = static_cast<uint64_t>(w[q]) * W + Steps<H>::offset(h[q], SW) + ln.r * S + (mm ? __ffs(mm) - 1 : 0);
         if constexpr (G > 1) hidx = __shfl_sync(kFull, hidx, ln.gbase + (bm ? __ffs(bm) - 1 : 0));
       }
       if (act[q]) {
@@ -390,7 +418,7 @@ __device__ __forceinline__ void sv_retrieve_range_k(const TableDesc& t, const KI
         } else if (be) {
           if (ln.r == 0) emit(pos[q], false, hit, hidx);
           act[q] = false;
-        } else if (h[q] + 1 < H) {
+        } else if (Steps<H>::more(h[q])) {
           ++h[q];  // the rest of this window
         } else if (!ovf_bit(fw, w[q], tag[q]) || ++j[q] >= t.p) {
           if (ln.r == 0) emit(pos[q], false, hit, hidx);
@@ -528,117 +556,7 @@ static __global__ void k_index_hist(unsigned int* __restrict__ hist, uint32_t R,
 // full.  That is the same order the whole-window read gives: an insert claims the earliest
 // candidate of its sequence, so no live key ever sits behind an empty slot of its own
 // sequence, whatever the window's width.
-//
-// A group may carry K keys at once: every trip loads the next window of each of its keys
-// before any is examined, so K windows per group are in flight (with G lanes reading a
-// window in one load instruction each, one L2 request per window).
-
-// One key's insert walk.
-template <class L>
-struct InsertProbe {
-  typename L::Key k = 0;
-  typename L::Val v = 0;
-  uint32_t w = 0, step = 0, j = 0, tag = 0, h = 0;
-  bool act = false;
-  bool have_t = false;          // a tombstone earlier on the sequence is remembered
-  uint64_t t_slot = 0;          // its slot index
-  typename L::Slot t_word{};    // and the word read there
-};
-
-// Examine the step of q's walk loaded into s (lane_slot = this lane's first slot of it) and
-// claim, update or walk on.  Warp-collective: every lane calls it, active or not.
-template <class L, int G, int S, int H>
-__device__ __forceinline__ void insert_step(const TableDesc& t, const SvLane<L, G, S>& ln, InsertProbe<L>& q,
-                                            const typename L::Slot (&s)[S], uint64_t lane_slot, uint32_t& flags,
-                                            long long& added) {
-  using Slot = typename L::Slot;
-  Slot* slots = static_cast<Slot*>(t.slots);
-  uint32_t mm = 0, me = 0, mt = 0;
-  if (q.act) classify<L, S>(s, q.k, mm, me, mt);
-  const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
-  const uint32_t be = group_vote<G>(me != 0, ln.gbase);
-  const uint32_t bt = group_vote<G>(mt != 0, ln.gbase);
-  const uint32_t bc = group_vote<G>((me | mt) != 0, ln.gbase);
-  const bool last = q.j + 1 >= t.p && q.h + 1 == H;
-  const bool claim = bm == 0 && (be != 0 || last);
-
-  // The key is present: overwrite its value (duplicate warning, Sec. IV-B3).
-  if (q.act && bm && ln.r == __ffs(bm) - 1) slot_store_value<L>(slots, t.vals, lane_slot + (__ffs(mm) - 1), q.v);
-
-  // Claim the earliest candidate: a remembered tombstone from an earlier window,
-  // else the first empty-or-tombstone slot of this window (Sec. IV-B2 steps 4 and 6).
-  bool ok = false;
-  if (q.act && claim) {
-    if (q.have_t) {
-      if (ln.r == 0) {
-        ok = L::cas(slots + q.t_slot, q.t_word, L::make(q.k, q.v));
-        if constexpr (L::kSoA) {
-          if (ok) slot_store_value<L>(slots, t.vals, q.t_slot, q.v);
-        }
-      }
-    } else if (bc && ln.r == __ffs(bc) - 1) {
-      const int sub = __ffs(me | mt) - 1;
-      ok = L::cas(slots + lane_slot + sub, pick<L, S>(s, sub), L::make(q.k, q.v));
-      if constexpr (L::kSoA) {
-        if (ok) slot_store_value<L>(slots, t.vals, lane_slot + sub, q.v);
-      }
-    }
-  }
-  if constexpr (G > 1) ok = __shfl_sync(kFull, ok, ln.gbase + ((q.have_t || bc == 0) ? 0 : __ffs(bc) - 1));
-
-  // Remember the first tombstone met before the terminating window.  The branch is
-  // warp-uniform, so every lane reaches the same shuffles.
-  uint64_t nt_slot = 0;
-  Slot nt_word{};
-  if (__any_sync(kFull, q.act && !claim && bt != 0 && !q.have_t)) {
-    const int sub = mt ? __ffs(mt) - 1 : 0;
-    nt_slot = lane_slot + sub;
-    nt_word = pick<L, S>(s, sub);
-    if constexpr (G > 1) {
-      const int tl = ln.gbase + (bt ? __ffs(bt) - 1 : 0);
-      nt_slot = __shfl_sync(kFull, nt_slot, tl);
-      nt_word = L::shfl(nt_word, tl);
-    }
-  }
-
-  if (q.act) {
-    if (bm) {
-      if constexpr (!L::kCount) flags |= kFlagDuplicate;
-      q.act = false;
-    } else if (claim) {
-      if (ok) {
-        if (ln.r == 0) ++added;
-        q.act = false;
-      } else if (q.have_t) {
-        // the remembered tombstone was taken: probe again from the start
-        q.have_t = false;
-        q.j = 0;
-        q.h = 0;
-        probe_init(static_cast<uint64_t>(q.k), t.seed, t.p, q.w, q.step, q.tag);
-      } else if (bc == 0) {
-        flags |= kFlagProbeLimit;  // every window visited, nothing to claim
-        q.act = false;
-      }
-      // else: lost the race for a slot of this window; read it again
-    } else {
-      if (bt && !q.have_t) {
-        q.have_t = true;
-        q.t_slot = nt_slot;
-        q.t_word = nt_word;
-      }
-      if (q.h + 1 < H) {
-        ++q.h;  // the rest of this window, in the next trip
-      } else {
-        if (t.ovf != nullptr && ln.r == 0) ovf_mark(t.ovf, q.w, q.tag);  // walking past a window without an empty slot
-        q.h = 0;
-        ++q.j;
-        q.w = probe_next(q.w, q.step, t.p);
-      }
-    }
-  }
-}
-
-template <class L, int G, int S, int H = 1, int K = 1>
+template <class L, int G, int S, int H = 1>
 __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typename L::Key* __restrict__ keys,
                                                 const typename L::Val* __restrict__ vals, RangeSrc& src,
                                                 uint32_t& flags, long long& added) {
@@ -648,8 +566,15 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
   const SvLane<L, G, S> ln;
   constexpr int SW = G * S;  // slots of one step
   constexpr int W = SW * H;
-  const Slot* slots = static_cast<const Slot*>(t.slots);
-  InsertProbe<L> q[K];
+  Slot* slots = static_cast<Slot*>(t.slots);
+  bool act = false;
+  uint64_t pos = 0;
+  Key k = 0;
+  Val v = 0;
+  uint32_t w = 0, step = 0, j = 0, tag = 0, h = 0;
+  bool have_t = false;     // a tombstone earlier on the sequence is remembered
+  uint64_t t_slot = 0;     // its slot index
+  Slot t_word{};           // and the word read there
   Feed<Key> fk;
   Feed<Val> fv;
   const bool unit = vals == nullptr;  // counting tables without weights: every occurrence counts 1
@@ -660,67 +585,135 @@ __device__ __forceinline__ void sv_insert_range(const TableDesc& t, const typena
       if (!unit) fv.load(vals, src.next, src.end);
       src.fresh = false;
     }
-    bool any = false;
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-      uint64_t np = 0;
-      const bool got = more && take_next(!q[i].act, ln.r, ln.gbase, src.next, src.end, np);
-      const Key kin = fk.get(np, got);
-      const Val vin = unit ? Val(1) : fv.get(np, got);
-      if (more) {
-        fk.advance(src.next);
-        if (!unit) fv.advance(src.next);
-      }
-      if (got) {
-        q[i].k = kin;
-        if (is_sentinel(kin)) {
-          // counting inserts run on aggregated batches whose padding is key 0 (the
-          // aggregation pass already flagged the caller's sentinel keys)
-          if (!(L::kCount && kin == Key(0))) flags |= kFlagInvalid;
-        } else {
-          q[i].v = vin;
-          q[i].act = true;
-          q[i].j = 0;
-          q[i].h = 0;
-          q[i].have_t = false;
-          probe_init(static_cast<uint64_t>(kin), t.seed, t.p, q[i].w, q[i].step, q[i].tag);
-        }
-      }
-      any |= q[i].act;
+    uint64_t np = 0;
+    const bool got = more && take_next(!act, ln.r, ln.gbase, src.next, src.end, np);
+    const Key kin = fk.get(np, got);
+    const Val vin = unit ? Val(1) : fv.get(np, got);
+    if (more) {
+      fk.advance(src.next);
+      if (!unit) fv.advance(src.next);
     }
-    if (__ballot_sync(kFull, any) == 0) {
+    if (got) {
+      pos = np;
+      k = kin;
+      if (is_sentinel(k)) {
+        // counting inserts run on aggregated batches whose padding is key 0 (the
+        // aggregation pass already flagged the caller's sentinel keys)
+        if (!(L::kCount && k == Key(0))) flags |= kFlagInvalid;
+      } else {
+        v = vin;
+        act = true;
+        j = 0;
+        h = 0;
+        have_t = false;
+        probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step, tag);
+      }
+    }
+    if (__ballot_sync(kFull, act) == 0) {
       if (!more) break;
       continue;
     }
-    Slot s[K][S];
-    uint64_t lane_slot[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-      lane_slot[i] = static_cast<uint64_t>(q[i].w) * W + q[i].h * SW + ln.r * S;
-      if (q[i].act) load_slots<L, S>(slots + lane_slot[i], s[i]);
+    Slot s[S];
+    uint32_t mm = 0, me = 0, mt = 0;
+    const uint64_t lane_slot = static_cast<uint64_t>(w) * W + Steps<H>::offset(h, SW) + ln.r * S;
+    if (act) {
+      load_slots<L, S>(slots + lane_slot, s);
+      classify<L, S>(s, k, mm, me, mt);
     }
-#pragma unroll
-    for (int i = 0; i < K; ++i) insert_step<L, G, S, H>(t, ln, q[i], s[i], lane_slot[i], flags, added);
+    const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
+    const uint32_t be = group_vote<G>(me != 0, ln.gbase);
+    const uint32_t bt = group_vote<G>(mt != 0, ln.gbase);
+    const uint32_t bc = group_vote<G>((me | mt) != 0, ln.gbase);
+    const bool last = j + 1 >= t.p && Steps<H>::last(h);
+    const bool claim = bm == 0 && (be != 0 || last);
+
+    // The key is present: overwrite its value (duplicate warning, Sec. IV-B3).
+    if (act && bm && ln.r == __ffs(bm) - 1) slot_store_value<L>(slots, t.vals, lane_slot + (__ffs(mm) - 1), v);
+
+    // Claim the earliest candidate: a remembered tombstone from an earlier window,
+    // else the first empty-or-tombstone slot of this window (Sec. IV-B2 steps 4 and 6).
+    bool ok = false;
+    if (act && claim) {
+      if (have_t) {
+        if (ln.r == 0) {
+          ok = L::cas(slots + t_slot, t_word, L::make(k, v));
+          if constexpr (L::kSoA) {
+            if (ok) slot_store_value<L>(slots, t.vals, t_slot, v);
+          }
+        }
+      } else if (bc && ln.r == __ffs(bc) - 1) {
+        const int sub = __ffs(me | mt) - 1;
+        ok = L::cas(slots + lane_slot + sub, pick<L, S>(s, sub), L::make(k, v));
+        if constexpr (L::kSoA) {
+          if (ok) slot_store_value<L>(slots, t.vals, lane_slot + sub, v);
+        }
+      }
+    }
+    if constexpr (G > 1) ok = __shfl_sync(kFull, ok, ln.gbase + ((have_t || bc == 0) ? 0 : __ffs(bc) - 1));
+
+    // Remember the first tombstone met before the terminating window.  The branch is
+    // warp-uniform, so every lane reaches the same shuffles.
+    uint64_t nt_slot = 0;
+    Slot nt_word{};
+    if (__any_sync(kFull, act && !claim && bt != 0 && !have_t)) {
+      const int sub = mt ? __ffs(mt) - 1 : 0;
+      nt_slot = lane_slot + sub;
+      nt_word = pick<L, S>(s, sub);
+      if constexpr (G > 1) {
+        const int tl = ln.gbase + (bt ? __ffs(bt) - 1 : 0);
+        nt_slot = __shfl_sync(kFull, nt_slot, tl);
+        nt_word = L::shfl(nt_word, tl);
+      }
+    }
+
+    if (act) {
+      if (bm) {
+        if constexpr (!L::kCount) flags |= kFlagDuplicate;
+        act = false;
+      } else if (claim) {
+        if (ok) {
+          if (ln.r == 0) ++added;
+          act = false;
+        } else if (have_t) {
+          // the remembered tombstone was taken: probe again from the start
+          have_t = false;
+          j = 0;
+          h = 0;
+          probe_init(static_cast<uint64_t>(k), t.seed, t.p, w, step, tag);
+        } else if (bc == 0) {
+          flags |= kFlagProbeLimit;  // every window visited, nothing to claim
+          act = false;
+        }
+        // else: lost the race for a slot of this window; read it again
+      } else {
+        if (bt && !have_t) {
+          have_t = true;
+          t_slot = nt_slot;
+          t_word = nt_word;
+        }
+        if (Steps<H>::more(h)) {
+          ++h;  // the rest of this window, in the next trip
+        } else {
+          if (t.ovf != nullptr && ln.r == 0) ovf_mark(t.ovf, w, tag);  // walking past a window without an empty slot
+          h = 0;
+          ++j;
+          w = probe_next(w, step, t.p);
+        }
+      }
+    }
   }
 }
 
 // counter != nullptr: warps pull chunks in order (input sorted by table region).
-// Packed 8-byte slots: four 256-thread blocks per SM (64 registers) for one key per group,
-// three for two; other layouts keep the compiler's choice.
-template <class L, int S, int K>
-constexpr int insert_min_blocks() {
-  return (L::kWords == 1 && sizeof(typename L::Key) == 4 && !L::kHalf) ? (K == 1 ? 4 : 3) : 1;
-}
-
-template <class L, int G, int S, int H = 1, int K = 1>
-__global__ void __launch_bounds__(256, (insert_min_blocks<L, S, K>())) k_sv_insert(TableDesc t, const typename L::Key* __restrict__ keys,
+template <class L, int G, int S, int H = 1>
+__global__ void __launch_bounds__(256) k_sv_insert(TableDesc t, const typename L::Key* __restrict__ keys,
                                                    const typename L::Val* __restrict__ vals, uint64_t n,
                                                    uint64_t per_warp, unsigned long long* counter, uint32_t chunk) {
   RangeSrc src(n, per_warp, counter, chunk);
   if (counter == nullptr && src.next >= src.end) return;
   uint32_t flags = 0;
   long long added = 0;
-  sv_insert_range<L, G, S, H, K>(t, keys, vals, src, flags, added);
+  sv_insert_range<L, G, S, H>(t, keys, vals, src, flags, added);
   flush_flags(t.status, flags);
   flush_delta(t.size, added);
 }
@@ -769,7 +762,7 @@ __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __
     }
     Slot s[S];
     uint32_t mm = 0, me = 0, mt = 0;
-    const uint64_t lane_slot = static_cast<uint64_t>(w) * W + h * SW + ln.r * S;
+    const uint64_t lane_slot = static_cast<uint64_t>(w) * W + Steps<H>::offset(h, SW) + ln.r * S;
     if (act) {
       load_slots<L, S>(slots + lane_slot, s);
       classify<L, S>(s, k, mm, me, mt);
@@ -777,7 +770,7 @@ __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __
     const uint32_t bm = group_vote<G>(mm != 0, ln.gbase);
     const uint32_t be = group_vote<G>(me != 0, ln.gbase);
     uint32_t fw = 0xffffffffu;
-    if (t.ovf != nullptr && act && !bm && !be && h + 1 == H) fw = ovf_word(t.ovf, w);
+    if (t.ovf != nullptr && act && !bm && !be && Steps<H>::last(h)) fw = ovf_word(t.ovf, w);
     bool ok = false;
     if (act && bm && ln.r == __ffs(bm) - 1) {
       const int sub = __ffs(mm) - 1;
@@ -795,7 +788,7 @@ __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __
         // else: another erase of the same key won; read the window again
       } else if (be) {
         act = false;  // absent: nothing to erase
-      } else if (h + 1 < H) {
+      } else if (Steps<H>::more(h)) {
         ++h;  // the rest of this window
       } else if (!ovf_bit(fw, w, tag) || ++j >= t.p) {
         act = false;

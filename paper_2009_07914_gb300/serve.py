@@ -20,7 +20,7 @@ class WcWork(ctypes.Structure):
 class WcExecutorConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("window_width", ctypes.c_int32), ("max_items", ctypes.c_uint32),
                 ("tile_keys", ctypes.c_uint32), ("timeout_ns", ctypes.c_uint64), ("test_stall", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("group_insert", ctypes.c_int32), ("group_retrieve", ctypes.c_int32)]
 
 
 class WcRequest(ctypes.Structure):
@@ -68,9 +68,13 @@ def work(op: int, table: int, keys, values=None, values_out=None, found_out=None
 
 
 def wc_executor_create(device: int, window_width: int, max_items: int = 1024, tile_keys: int = 4096,
-                       timeout_ns: int = 0, test_stall: bool = False) -> int:
+                       timeout_ns: int = 0, test_stall: bool = False, group_insert: int = 0,
+                       group_retrieve: int = 0) -> int:
+    """group_insert / group_retrieve: lanes per key (0 = the defaults), e.g. the choice of
+    tune.executor_groups for the served tables."""
     cfg = WcExecutorConfig(device=device, window_width=window_width, max_items=max_items, tile_keys=tile_keys,
-                           timeout_ns=timeout_ns, test_stall=1 if test_stall else 0, reserved=0)
+                           timeout_ns=timeout_ns, test_stall=1 if test_stall else 0, reserved=0,
+                           group_insert=group_insert, group_retrieve=group_retrieve)
     h = ctypes.c_void_p()
     B.check(B.lib().wc_executor_create(ctypes.byref(h), ctypes.byref(cfg)), "wc_executor_create")
     return int(h.value)

@@ -8,6 +8,7 @@ prints one JSON line per measured candidate and a final line with the choice.  I
 
     best = tune_table(handle, keys, values, queries)   # tunes one table's launch shapes
     W = recommend_window(4, 4, n, alpha)               # window width for a new table
+    g = executor_groups(8)                             # lanes per key for the batched executor
 
 The cache is a JSON file (WC_TUNE_CACHE, default tune_cache.json beside this module),
 keyed by GPU name, widths, W, load-factor decile and log2 of the batch size.
@@ -163,6 +164,57 @@ def recommend_window(kb: int, vb: int, n: int, alpha: float, reps: int = 3, repo
             api.wc_table_destroy(h)
         choices.append({"W": W, "shapes": b, "ms": b["insert"]["ms"] + b["retrieve"]["ms"]})
     return min(choices, key=lambda c: c["ms"])
+
+
+# Lanes per key the batched executor is built for (wc_exec.h): window width -> (insert, lookup).
+EXEC_SHAPES = {4: ([1, 2], [1, 2]), 8: ([1, 2, 4], [1, 2, 4]), 16: ([2, 4], [2, 4])}
+
+
+def executor_groups(W: int, n: int = 1 << 22, alpha: float = 0.75, reps: int = 3, use_cache: bool = True,
+                    report=None) -> dict:
+    """Lanes per key for the batched executor's inserts and lookups (wc_executor_config
+    group_insert / group_retrieve) on 4+4-byte tables of window width W: the executor
+    cuts work into tiles and never region-splits, so the candidates are timed with the
+    direct scheme on a seeded sample of n keys at load alpha.  Cached like tune_table."""
+    keys, values, queries = sample(4, n)
+    cache = _load_cache() if use_cache else {}
+    gi_set, gr_set = EXEC_SHAPES[W]
+    h = api.wc_table_create(0, 4, 4, int(math.ceil(n / alpha)), W, 0, 0x5EED, torch.cuda.current_device())
+    s = torch.cuda.current_stream()
+    out = torch.empty(queries.numel(), dtype=torch.int32, device=keys.device)
+    found = torch.empty(queries.numel(), dtype=torch.uint8, device=keys.device)
+    best = {}
+    try:
+        for opname, op, gset in (("exec_insert", WC_OP_INSERT, gi_set), ("exec_retrieve", WC_OP_RETRIEVE, gr_set)):
+            key = cache_key(4, 4, W, alpha, n, opname)
+            if key in cache:
+                best[opname] = cache[key]
+                continue
+            res = []
+            for G in gset:
+                api.wc_table_set_launch(h, op, G, 256, 0, WC_SCHEME_DIRECT, 0)
+                if op == WC_OP_INSERT:
+                    def f():
+                        api.wc_table_clear(h, s)
+                        api.wc_insert(h, keys, values, n, s)
+                    ms = _time(f, reps)
+                else:
+                    ms = _time(lambda: api.wc_retrieve(h, queries, out, found, queries.numel(), s), reps)
+                res.append({"op": opname, "W": W, "group": G, "ms": ms})
+                if report:
+                    report(res[-1])
+            best[opname] = min(res, key=lambda r: r["ms"])
+            cache[key] = best[opname]
+            if op == WC_OP_INSERT:  # lookups need the table filled
+                api.wc_table_set_launch(h, op, best[opname]["group"], 256, 0, WC_SCHEME_DIRECT, 0)
+                api.wc_table_clear(h, s)
+                api.wc_insert(h, keys, values, n, s)
+    finally:
+        torch.cuda.synchronize()
+        api.wc_table_destroy(h)
+    if use_cache:
+        _save_cache(cache)
+    return {"group_insert": best["exec_insert"]["group"], "group_retrieve": best["exec_retrieve"]["group"]}
 
 
 def main():

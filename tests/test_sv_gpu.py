@@ -542,44 +542,3 @@ def test_retrieve_two_keys_per_group_in_flight(wc, kb, W, G, opt):
     assert t.insert(drop[::2], vals[: n // 3: 2]) == o.insert(drop[::2], vals[: n // 3: 2])
     check_retrieve(t, o, q)
     assert t.size() == o.size()
-
-
-@pytest.mark.parametrize("scheme", [1, 2], ids=["direct", "region_split"])
-@pytest.mark.parametrize("opt", [0, 1], ids=["plain", "overflow_bits"])
-@pytest.mark.parametrize("kb,W,G", [(4, 8, 2), (4, 16, 4), (4, 4, 1), (8, 4, 2), (8, 8, 4)])
-def test_insert_two_keys_per_group_in_flight(wc, kb, W, G, opt, scheme):
-    """Inserts with keys_in_flight = 2 against the oracle: new keys, duplicates inside and
-    across batches, erase and re-insert (tombstones reused), at load 0.95; the slot dump
-    has no duplicate and no unreachable key, and with overflow bits the dumped bits are the
-    ones the oracle derives after the insert-only phase."""
-    n = 90_001
-    if kb == 4:
-        keys = wc_inputs.distinct_u32(0x3A + W * 64 + G, n)
-        vals = wc_inputs.uniform_u32(7, n)
-    else:
-        keys = wc_inputs.distinct_u64(0x3A + W * 64 + G, n)
-        vals = wc_inputs.uniform_u64(7, n)
-    t = make_sv(wc, kb, kb, int(n / 0.95) + 1, W, G, options=opt)
-    t.set_launch(wc.WC_OP_INSERT, G, scheme=scheme, keys_in_flight=2)
-    o = oracle.SingleValue(kb, kb)
-    assert t.insert(keys, vals) == o.insert(keys, vals) == 0
-    info = t.info
-    dump = wc.api.wc_table_dump_slots(t.handle)
-    bits = wc.api.wc_table_dump_overflow_bits(t.handle) if opt else None
-    r = oracle.check_slots(dump, info["windows"], info["window_width"], info["slot_bytes"], 0x1234, True, bits)
-    assert r == {"live": n, "dups": 0, "unreachable": 0}
-    if opt:
-        expect = oracle.overflow_bits_of(dump, info["windows"], info["window_width"], info["slot_bytes"], 0x1234)
-        assert np.array_equal(bits.view(np.uint8)[:info["windows"]], expect)
-    q = keys[wc_inputs.shuffle_index(4, n)]
-    check_retrieve(t, o, q)
-    drop = keys[: n // 3]
-    assert t.erase(drop) == o.erase(drop)
-    again = np.concatenate([drop[::2], keys[n // 2: n // 2 + 500]])  # re-inserts and duplicates
-    v2 = vals[: again.size] ^ vals.dtype.type(0x55)
-    assert t.insert(again, v2) == o.insert(again, v2)
-    assert t.size() == o.size()
-    check_retrieve(t, o, q)
-    r = oracle.check_slots(wc.api.wc_table_dump_slots(t.handle), info["windows"], info["window_width"],
-                           info["slot_bytes"], 0x1234, True, wc.api.wc_table_dump_overflow_bits(t.handle) if opt else None)
-    assert r["dups"] == 0 and r["unreachable"] == 0 and r["live"] == o.size()
