@@ -77,6 +77,9 @@ def parse():
                          "and a counting table (Zipf keys); "
                          "served: 64 tables, Poisson requests, batched vs per-call")
     ap.add_argument("--requests", type=int, default=512, help="served: number of requests")
+    ap.add_argument("--append-modes", default="1.1/1,1/r",
+                    help="mv_oa_uniform_r: per-element device-API append legs into bucket tables, comma-separated "
+                         "LAMBDA/S0 growth strategies ('' = none)")
     ap.add_argument("--mv-block", type=int, default=0,
                     help="mv_zipf: block size of the bucket table's insert passes (256 or 512; 0 = default)")
     ap.add_argument("--r", default="1,4,16,64", help="mv_oa_uniform_r: average copies per key, comma-separated")
@@ -752,9 +755,16 @@ def run_mv_oa_uniform_r(args, dev):
             api.wc_table_set_launch(h, op, int(args.group.split(",")[0]), 256, 0, 0, 0)
     info = api.wc_table_get_info(h)
     modes = [m.strip() for m in args.bucket_modes.split(",") if m.strip()]
+    amodes = [m.strip() for m in args.append_modes.split(",") if m.strip()]
     res = {"oa": {}}
     for m in modes:
         res["bucket" if m == "exact" else "bucket_" + m] = {}
+    for m in amodes:
+        res["append_" + m] = {}
+
+    def growth_of(m, r):
+        lam_s, s0_s = m.split("/")
+        return float(lam_s), (r if s0_s == "r" else int(s0_s))
     launches = 0
     with ClockSampler(dev.index) as clk:
         for r in rs:
@@ -764,18 +774,25 @@ def run_mv_oa_uniform_r(args, dev):
                 if m == "exact":
                     s0, lam = 0, 1.0
                 else:
-                    lam_s, s0_s = m.split("/")
-                    lam, s0 = float(lam_s), (r if s0_s == "r" else int(s0_s))
+                    lam, s0 = growth_of(m, r)
                 # pool: values + headers + padding of the largest layout (s0 = 1, lambda = 1: 4 per value)
                 pool = n + 2 * (n // r) + 1024 if s0 == 0 else 4 * n + 1024
                 legs.append(("bucket" if m == "exact" else "bucket_" + m,
                              api.wc_table_create(1, 4, 4, int(np.ceil(max(1, n // r) / 0.8)), 0, pool, 0x5EEDC0DE,
                                                  dev.index, bucket_first_size=s0, bucket_growth=lam)))
+            for m in amodes:  # the same tables, filled by per-element device-API appends
+                lam, s0 = growth_of(m, r)
+                legs.append(("append_" + m,
+                             api.wc_table_create(1, 4, 4, int(np.ceil(max(1, n // r) / 0.8)), 0, 4 * n + 1024,
+                                                 0x5EEDC0DE, dev.index, bucket_first_size=s0, bucket_growth=lam)))
+            from paper_2009_07914_gb300.roofline import wc_bench_mv_append
             for name, t in legs:
                 ev = []
+                ins = (lambda: wc_bench_mv_append(t, keys, vals, n, s)) if name.startswith("append_") else \
+                    (lambda: api.wc_insert(t, keys, vals, n, s))
                 for i in range(args.warmup + args.steps):
                     api.wc_table_clear(t, s)
-                    t0 = timed(s, lambda: api.wc_insert(t, keys, vals, n, s))
+                    t0 = timed(s, ins)
                     t1 = timed(s, lambda: api.wc_count_values(t, q, offs, n, want_total=False, stream=s))
                     t2 = timed(s, lambda: api.wc_retrieve_multi(t, q, offs, out, n, s))
                     if i >= args.warmup:
@@ -790,7 +807,8 @@ def run_mv_oa_uniform_r(args, dev):
                     res[name][str(r)]["pool_elements_per_value"] = api.wc_value_pool_used(t) / n
                 # OA: hist + scatter + insert, walk + 3 scan kernels, walk; bucket: hist +
                 # scatter + count + alloc + scatter, count + 3 scan kernels, gather
-                launches += (8 if name == "oa" else 10) * args.steps
+                # append legs: one append kernel, count + 3 scan kernels, gather
+                launches += (8 if name == "oa" else 6 if name.startswith("append_") else 10) * args.steps
             for name, t in legs[1:]:
                 api.wc_table_destroy(t)
             del keys

@@ -52,6 +52,13 @@ wc_status wc_bench_random_access(void* d_buffer, const wc_rand_access_config* cf
 wc_status wc_bench_device_api(wc_table* t, int32_t mode, uint64_t n, uint32_t key_seed, uint64_t* d_sink,
                               void* stream);
 
+/* Device-API probe of the bucket list (include/wc_device_api.cuh, wc_dev::append): one
+ * thread per pair appends (d_keys[i], d_values[i]) -- device arrays of the table's key and
+ * value widths -- to a bucket multi-value table created with a growth strategy, every pair
+ * an independent concurrent append (Sec. IV-C).  Status conditions go to the table's
+ * status word.  Asynchronous on `stream`; WC_ERR_UNSUPPORTED for other tables. */
+wc_status wc_bench_mv_append(wc_table* t, const void* d_keys, const void* d_values, uint64_t n, void* stream);
+
 /* The CUDA context's L2 fetch-granularity limit (cudaLimitMaxL2FetchGranularity, bytes;
  * a hint of how much the L2 fetches from DRAM on a miss).  Process-local: the setting
  * ends with the process. */

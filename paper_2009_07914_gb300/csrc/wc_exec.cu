@@ -180,6 +180,7 @@ struct wc_executor {
   // that may still be running
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaGraphNode_t copy_node[2] = {nullptr, nullptr};  // the work-list copy of each graph
   void* kernel = nullptr;
   unsigned grid_blocks = 1;  // blocks of the persistent kernel
 };
@@ -275,6 +276,7 @@ wc_status wc_executor_create(wc_executor** out, const wc_executor_config* cfg) {
     if (ok)
       ok = cudaGraphAddMemcpyNode1D(&n_copy, ex->graph[g], nullptr, 0, ex->d_buf, ex->h_stage[g], ex->lay.next,
                                     cudaMemcpyHostToDevice) == cudaSuccess;
+    ex->copy_node[g] = n_copy;
     if (ok) {
       cudaMemsetParams mp = {};
       mp.dst = ex->d_buf + ex->lay.next;
@@ -398,7 +400,12 @@ wc_status wc_executor_submit(wc_executor* ex, const wc_work* h_items, uint32_t c
   hdr->nitems = ni;
   hdr->ngroups = ng;
   hdr->ticket = ticket;
-  cudaError_t e = cudaGraphLaunch(ex->exec[slot], s);
+  // copy only the part of the work list this batch uses (header, group counts, its items):
+  // a small batch then costs a few KB of copy instead of the whole list's capacity
+  const size_t used = ex->lay.items + static_cast<size_t>(ni) * sizeof(ExecItem);
+  cudaError_t e = cudaGraphExecMemcpyNodeSetParams1D(ex->exec[slot], ex->copy_node[slot], ex->d_buf,
+                                                     ex->h_stage[slot], used, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ex->exec[slot], s);
   if (e == cudaSuccess) e = cudaEventRecord(ex->stage_ev[slot], s);
   if (e == cudaSuccess) e = cudaEventRecord(ex->ring[ticket % kTicketRing], s);
   return e == cudaSuccess ? WC_OK : WC_ERR_CUDA;

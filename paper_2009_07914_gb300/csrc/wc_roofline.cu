@@ -187,10 +187,48 @@ void dev_probe(const wc_device_view& v, int mode, uint64_t n, uint32_t seed, uns
   }
 }
 
+// One thread per pair appends (keys[i], values[i]) to a bucket multi-value table with the
+// device API's per-element append (the concurrent bucket-list insert).
+template <class K, class V>
+__global__ void __launch_bounds__(256) k_dev_append(wc_device_view v, const K* __restrict__ keys,
+                                                    const V* __restrict__ vals, uint64_t n) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+    wc_dev::append<K, V>(v, keys[i], vals[i]);
+}
+
 }  // namespace
 }  // namespace wc
 
 extern "C" {
+
+wc_status wc_bench_mv_append(wc_table* t, const void* d_keys, const void* d_values, uint64_t n, void* stream) {
+  if (t == nullptr || (n > 0 && (d_keys == nullptr || d_values == nullptr))) return WC_ERR_INVALID_ARG;
+  wc_device_view v;
+  const wc_status st = wc_table_device_view(t, &v);
+  if (st != WC_OK) return st;
+  if (v.kind != WC_MULTI_VALUE) return WC_ERR_UNSUPPORTED;
+  if (n == 0) return WC_OK;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != t->device) return WC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const unsigned blocks = static_cast<unsigned>(wc::occupancy(wc::k_dev_append<uint32_t, uint32_t>, 256) *
+                                                wc::sm_count_of(t->device));
+  if (v.key_bytes == 4 && v.value_bytes == 4)
+    wc::k_dev_append<uint32_t, uint32_t><<<blocks, 256, 0, s>>>(v, static_cast<const uint32_t*>(d_keys),
+                                                               static_cast<const uint32_t*>(d_values), n);
+  else if (v.key_bytes == 8 && v.value_bytes == 4)
+    wc::k_dev_append<unsigned long long, uint32_t><<<blocks, 256, 0, s>>>(
+        v, static_cast<const unsigned long long*>(d_keys), static_cast<const uint32_t*>(d_values), n);
+  else if (v.key_bytes == 8)
+    wc::k_dev_append<unsigned long long, unsigned long long><<<blocks, 256, 0, s>>>(
+        v, static_cast<const unsigned long long*>(d_keys), static_cast<const unsigned long long*>(d_values), n);
+  else
+    wc::k_dev_append<uint32_t, unsigned long long><<<blocks, 256, 0, s>>>(
+        v, static_cast<const uint32_t*>(d_keys), static_cast<const unsigned long long*>(d_values), n);
+  return cudaGetLastError() == cudaSuccess ? WC_OK : WC_ERR_CUDA;
+}
 
 wc_status wc_bench_device_api(wc_table* t, int32_t mode, uint64_t n, uint32_t key_seed, uint64_t* d_sink,
                               void* stream) {

@@ -66,14 +66,14 @@ struct Steps {
     if constexpr (H == 1) {
       return true;
     } else {
-      return Steps<H>::last(h);
+      return h + 1 == static_cast<uint32_t>(H);
     }
   }
   static __device__ __forceinline__ bool more(uint32_t h) {
     if constexpr (H == 1) {
       return false;
     } else {
-      return Steps<H>::more(h);
+      return h + 1 < static_cast<uint32_t>(H);
     }
   }
 };

@@ -22,7 +22,16 @@ B.extra_signatures({
     "wc_get_l2_fetch_granularity": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32)]),
     "wc_bench_device_api": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32,
                                            ctypes.c_void_p, ctypes.c_void_p]),
+    "wc_bench_mv_append": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                          ctypes.c_void_p]),
 })
+
+
+def wc_bench_mv_append(table: int, keys: torch.Tensor, values: torch.Tensor, n: int | None = None, stream=None):
+    """Device-API probe: one thread per pair appends to a bucket multi-value table."""
+    n = keys.numel() if n is None else n
+    B.check(B.lib().wc_bench_mv_append(table, B.ptr(keys), B.ptr(values), n, B.stream_handle(stream)),
+            "wc_bench_mv_append")
 
 
 def wc_bench_random_access(buffer: torch.Tensor, access_bytes: int, mode: int, accesses: int, sink: torch.Tensor,
