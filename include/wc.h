@@ -413,10 +413,12 @@ typedef struct {
 } wc_device_view;
 
 /* Fill *h_out for a single-value table (per-element insert / retrieve / erase, for_each,
- * for_all), an open-addressing multi-value table (for_all only) or a bucket multi-value
- * table created with a growth strategy (bucket_first_size > 0; per-element appends, whose
- * pool must hold fewer than 2^34 elements).  Host only.  WC_ERR_UNSUPPORTED for other
- * bucket multi-value tables (their buckets are sized per bulk call). */
+ * for_all), a hash set (set_insert / set_contains / set_erase), a counting table
+ * (count_add / count_get), an open-addressing multi-value table (for_all only) or a bucket
+ * multi-value table created with a growth strategy (bucket_first_size > 0; per-element
+ * appends, whose pool must hold fewer than 2^34 elements).  Host only.
+ * WC_ERR_UNSUPPORTED for struct-of-arrays tables, Bloom filters and other bucket
+ * multi-value tables (their buckets are sized per bulk call). */
 wc_status wc_table_device_view(const wc_table* t, wc_device_view* h_out);
 
 /* ---- host copies: inspection, checkpoint and resume (no counterpart in the paper) -- */

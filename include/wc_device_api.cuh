@@ -13,7 +13,9 @@
  * kernels); an insert or erase must not overlap a retrieve on the same table (Sec. IV-D).
  *
  * Bucket multi-value tables with a growth strategy take per-element appends (append
- * below; Sec. IV-C), which the bulk count / retrieve calls see.
+ * below; Sec. IV-C), which the bulk count / retrieve calls see; hash sets take set_insert /
+ * set_contains / set_erase and counting tables count_add / count_get (Sec. IV's HashSet
+ * and CountingHashTable), on the slots the bulk calls use.
  *
  * Per-element operations are executed by the calling thread alone: it walks the key's
  * probing sequence window by window (W slots each) -- the paper's cooperative group of
@@ -105,6 +107,9 @@ struct Slots<uint32_t> {
   static __device__ __forceinline__ void set_val(void* slots, uint64_t i, uint32_t v) {
     atomicExch(reinterpret_cast<unsigned int*>(static_cast<unsigned long long*>(slots) + i) + 1, v);
   }
+  static __device__ __forceinline__ void add_val(void* slots, uint64_t i, uint32_t v) {
+    atomicAdd(reinterpret_cast<unsigned int*>(static_cast<unsigned long long*>(slots) + i) + 1, v);
+  }
 };
 
 template <>
@@ -144,6 +149,9 @@ struct Slots<unsigned long long> {
   }
   static __device__ __forceinline__ void set_val(void* slots, uint64_t i, unsigned long long v) {
     atomicExch(reinterpret_cast<unsigned long long*>(static_cast<char*>(slots) + i * 16) + 1, v);
+  }
+  static __device__ __forceinline__ void add_val(void* slots, uint64_t i, unsigned long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(static_cast<char*>(slots) + i * 16) + 1, v);
   }
 };
 
@@ -194,7 +202,9 @@ __device__ __forceinline__ bool overflow_clear(const wc_device_view& t, uint32_t
   return t.overflow_bits != nullptr && !((__ldcg(t.overflow_bits + (w >> 2)) >> overflow_shift(w, tag)) & 1u);
 }
 
-template <class K, int W>
+// kAdd: a counting table -- a stored key gets the value added to its count (no warning),
+// an absent one is stored with the value as its count.
+template <class K, int W, bool kAdd = false>
 __device__ uint32_t insert_w(const wc_device_view& t, K key, typename Slots<K>::V value) {
   using S = Slots<K>;
   using Word = typename S::Word;
@@ -215,9 +225,14 @@ __device__ uint32_t insert_w(const wc_device_view& t, K key, typename Slots<K>::
     for (int q = 0; q < W; ++q) {
       const K k = S::key(win.slot(q));
       if (k == key) {
-        S::set_val(t.slots, base + q, value);
-        raise(t, WC_FLAG_DUPLICATE_KEY);
-        return WC_FLAG_DUPLICATE_KEY;
+        if constexpr (kAdd) {
+          S::add_val(t.slots, base + q, value);
+          return 0;
+        } else {
+          S::set_val(t.slots, base + q, value);
+          raise(t, WC_FLAG_DUPLICATE_KEY);
+          return WC_FLAG_DUPLICATE_KEY;
+        }
       }
       const bool is_empty = k == K(0);
       empty |= is_empty;
@@ -367,7 +382,194 @@ __device__ bool erase(const wc_device_view& t, K key) {
 #undef WC_DEV_CALL
 }
 
+// Counting tables (Sec. IV, CountingHashTable; wc_table_device_view of a WC_COUNTING
+// table): count_add adds `weight` to the key's count, storing the key with that count when
+// absent (counts wrap at the key width); count_get reads it (false when absent).  Returns
+// 0, or WC_FLAG_INVALID_KEY / WC_FLAG_PROBE_LIMIT.
+template <class K>
+__device__ uint32_t count_add(const wc_device_view& t, K key, typename Slots<K>::V weight) {
+  if (is_sentinel(key)) {
+    raise(t, WC_FLAG_INVALID_KEY);
+    return WC_FLAG_INVALID_KEY;
+  }
+#define WC_DEV_CALL(Wv) insert_w<K, Wv, true>(t, key, weight)
+  WC_DEV_DISPATCH(K, WC_DEV_CALL)
+#undef WC_DEV_CALL
+}
+
+template <class K>
+__device__ bool count_get(const wc_device_view& t, K key, typename Slots<K>::V& count) {
+  return retrieve<K>(t, key, count);
+}
+
 #undef WC_DEV_DISPATCH
+
+// ---- hash sets (Sec. IV, HashSet): key-only slots ----------------------------------------
+
+// The W keys of window w (4- or 8-byte slots), loaded with 32-byte vector loads issued
+// together (a set's window holds a multiple of 32 bytes; windows are aligned).
+template <class K, int W>
+struct KeyWindow {
+  static constexpr int kWords = W * static_cast<int>(sizeof(K)) / 8;
+  static_assert(kWords % 4 == 0, "windows of whole 32-byte sectors");
+  unsigned long long u[kWords];
+  __device__ __forceinline__ void load(const void* slots, uint32_t w) {
+    const unsigned long long* p = static_cast<const unsigned long long*>(slots) + static_cast<uint64_t>(w) * kWords;
+#pragma unroll
+    for (int i = 0; i < kWords; i += 4)
+      asm volatile("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];"
+                   : "=l"(u[i]), "=l"(u[i + 1]), "=l"(u[i + 2]), "=l"(u[i + 3])
+                   : "l"(p + i));
+  }
+  __device__ __forceinline__ K key(int q) const {
+    if constexpr (sizeof(K) == 4) {
+      return static_cast<uint32_t>(u[q >> 1] >> (32 * (q & 1)));
+    } else {
+      return u[q];
+    }
+  }
+};
+
+// Key-only CAS (a 4- or 8-byte slot).
+template <class K>
+__device__ __forceinline__ bool key_cas(void* slots, uint64_t i, K old, K key) {
+  if constexpr (sizeof(K) == 4) {
+    return atomicCAS(static_cast<unsigned int*>(slots) + i, old, key) == old;
+  } else {
+    return atomicCAS(static_cast<unsigned long long*>(slots) + i, old, key) == old;
+  }
+}
+
+template <class K, int W>
+__device__ uint32_t set_insert_w(const wc_device_view& t, K key) {
+  uint32_t w0, step, tag;
+  probe_init(static_cast<uint64_t>(key), t.seed, t.windows, w0, step, tag);
+  uint32_t w = w0, j = 0;
+  bool have_t = false;  // first tombstone of the walk, claimed if the key turns out absent
+  uint64_t t_slot = 0;
+  while (j < t.windows) {
+    KeyWindow<K, W> win;
+    win.load(t.slots, w);
+    const uint64_t base = static_cast<uint64_t>(w) * W;
+    bool empty = false;
+    int free_q = -1;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const K k = win.key(q);
+      if (k == key) {
+        raise(t, WC_FLAG_DUPLICATE_KEY);
+        return WC_FLAG_DUPLICATE_KEY;
+      }
+      const bool is_empty = k == K(0);
+      empty |= is_empty;
+      if ((is_empty || k == K(~K(0))) && free_q < 0) free_q = q;
+    }
+    if (empty || j + 1 == t.windows) {  // absent: claim the earliest candidate
+      if (have_t) {
+        if (key_cas<K>(t.slots, t_slot, K(~K(0)), key)) break;
+        have_t = false;  // the tombstone was taken: walk again from the start
+        w = w0;
+        j = 0;
+        continue;
+      }
+      if (free_q < 0) {
+        raise(t, WC_FLAG_PROBE_LIMIT);
+        return WC_FLAG_PROBE_LIMIT;
+      }
+      K fk = win.key(0);
+#pragma unroll
+      for (int q = 1; q < W; ++q)
+        if (q == free_q) fk = win.key(q);
+      if (key_cas<K>(t.slots, base + free_q, fk, key)) break;
+      continue;  // lost the slot: read the window again
+    }
+    if (free_q >= 0 && !have_t) {  // a full window: its free slots are tombstones
+      have_t = true;
+      t_slot = base + free_q;
+    }
+    if (t.overflow_bits) atomicOr(t.overflow_bits + (w >> 2), 1u << overflow_shift(w, tag));
+    w = probe_next(w, step, t.windows);
+    ++j;
+  }
+  add_size(t, 1);
+  return 0;
+}
+
+template <class K, int W>
+__device__ bool set_find_w(const wc_device_view& t, K key, bool erase) {
+  uint32_t w, step, tag;
+  probe_init(static_cast<uint64_t>(key), t.seed, t.windows, w, step, tag);
+  for (uint32_t j = 0; j < t.windows; ++j) {
+    KeyWindow<K, W> win;
+    win.load(t.slots, w);
+    bool empty = false;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const K k = win.key(q);
+      if (k == key) {
+        if (!erase) return true;
+        // only an erase of the same key can change this slot now: one CAS decides
+        const bool ok = key_cas<K>(t.slots, static_cast<uint64_t>(w) * W + q, key, K(~K(0)));
+        if (ok) add_size(t, -1);
+        return ok;
+      }
+      empty |= k == K(0);
+    }
+    if (empty || overflow_clear(t, w, tag)) return false;
+    w = probe_next(w, step, t.windows);
+  }
+  return false;
+}
+
+#define WC_SET_DISPATCH(K, CALL)                                          \
+  if constexpr (sizeof(K) == 4) {                                         \
+    switch (t.window_width) {                                             \
+      case 8: return CALL(8);                                             \
+      case 16: return CALL(16);                                           \
+      default: return CALL(32);                                           \
+    }                                                                     \
+  } else {                                                                \
+    switch (t.window_width) {                                             \
+      case 4: return CALL(4);                                             \
+      case 8: return CALL(8);                                             \
+      case 16: return CALL(16);                                           \
+      default: return CALL(32);                                           \
+    }                                                                     \
+  }
+
+// Set insert (wc_table_device_view of a WC_HASH_SET table): stores an absent key in the
+// earliest free or tombstoned slot of its walk; a stored key raises WC_FLAG_DUPLICATE_KEY and
+// changes nothing.  Returns the WC_FLAG_* bits (0 = stored).
+template <class K>
+__device__ uint32_t set_insert(const wc_device_view& t, K key) {
+  if (is_sentinel(key)) {
+    raise(t, WC_FLAG_INVALID_KEY);
+    return WC_FLAG_INVALID_KEY;
+  }
+#define WC_DEV_CALL(Wv) set_insert_w<K, Wv>(t, key)
+  WC_SET_DISPATCH(K, WC_DEV_CALL)
+#undef WC_DEV_CALL
+}
+
+// Set membership (the lookup's stop rules of Sec. IV-B4).
+template <class K>
+__device__ bool set_contains(const wc_device_view& t, K key) {
+  if (is_sentinel(key)) return false;
+#define WC_DEV_CALL(Wv) set_find_w<K, Wv>(t, key, false)
+  WC_SET_DISPATCH(K, WC_DEV_CALL)
+#undef WC_DEV_CALL
+}
+
+// Set erase (Sec. IV-B5): the key's slot becomes a tombstone; false when absent.
+template <class K>
+__device__ bool set_erase(const wc_device_view& t, K key) {
+  if (is_sentinel(key)) return false;
+#define WC_DEV_CALL(Wv) set_find_w<K, Wv>(t, key, true)
+  WC_SET_DISPATCH(K, WC_DEV_CALL)
+#undef WC_DEV_CALL
+}
+
+#undef WC_SET_DISPATCH
 
 // ---- per-element appends to a bucket multi-value table (Sec. IV-C) ----------------------
 //

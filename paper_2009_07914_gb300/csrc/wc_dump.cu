@@ -118,7 +118,9 @@ wc_status wc_table_restore(wc_table* t, const void* h_in, uint64_t bytes, void* 
 wc_status wc_table_device_view(const wc_table* t, wc_device_view* h_out) {
   if (t == nullptr || h_out == nullptr) return WC_ERR_INVALID_ARG;
   const bool bl = t->cfg.kind == WC_MULTI_VALUE;
-  if ((t->cfg.kind != WC_SINGLE_VALUE && t->cfg.kind != WC_MULTI_VALUE_OA && !bl) || t->d_vals != nullptr)
+  if ((t->cfg.kind != WC_SINGLE_VALUE && t->cfg.kind != WC_MULTI_VALUE_OA && t->cfg.kind != WC_HASH_SET &&
+       t->cfg.kind != WC_COUNTING && !bl) ||
+      t->d_vals != nullptr)
     return WC_ERR_UNSUPPORTED;
   // per-element appends need buckets of known sizes (a growth strategy) and pool offsets
   // below bit 63 of the list handle, which marks a list whose next bucket is being made

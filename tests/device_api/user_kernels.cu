@@ -56,6 +56,42 @@ __global__ void k_mv_append(wc_device_view v, const K* keys, const V* vals, uint
   }
 }
 
+// Hash sets: op 0 insert (out[i] = 1 if stored now), 1 contains, 2 erase (out[i] = 1 if erased).
+template <class K>
+__global__ void k_set_op(wc_device_view v, int op, const K* keys, uint64_t n, uint8_t* out, uint32_t* flags) {
+  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (op == 0) {
+    const uint32_t f = wc_dev::set_insert<K>(v, keys[i]);
+    if (f) atomicOr(flags, f);
+    out[i] = f == 0 ? 1 : 0;
+  } else if (op == 1) {
+    out[i] = wc_dev::set_contains<K>(v, keys[i]) ? 1 : 0;
+  } else {
+    out[i] = wc_dev::set_erase<K>(v, keys[i]) ? 1 : 0;
+  }
+}
+
+// Counting tables: add weights[i] (1 when weights is null) to keys[i]'s count; read counts.
+template <class K>
+__global__ void k_count_add(wc_device_view v, const K* keys, const K* weights, uint64_t n, uint32_t* flags) {
+  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const uint32_t f = wc_dev::count_add<K>(v, keys[i], weights ? weights[i] : K(1));
+    if (f) atomicOr(flags, f);
+  }
+}
+
+template <class K>
+__global__ void k_count_get(wc_device_view v, const K* keys, uint64_t n, K* out, uint8_t* found) {
+  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) {
+    K c = 0;
+    found[i] = wc_dev::count_get<K>(v, keys[i], c) ? 1 : 0;
+    out[i] = c;
+  }
+}
+
 unsigned grid(uint64_t n) { return static_cast<unsigned>((n + 255) / 256); }
 
 }  // namespace
@@ -107,6 +143,38 @@ int wcu_mv_append(const wc_device_view* v, const void* keys, const void* vals, u
   else
     k_mv_append<uint32_t, unsigned long long><<<grid(n), 256>>>(*v, static_cast<const uint32_t*>(keys),
                                                                 static_cast<const unsigned long long*>(vals), n, flags);
+  return static_cast<int>(cudaDeviceSynchronize());
+}
+
+int wcu_set_op(const wc_device_view* v, int op, const void* keys, uint64_t n, uint8_t* out, uint32_t* flags) {
+  if (n == 0) return 0;
+  if (v->key_bytes == 4)
+    k_set_op<uint32_t><<<grid(n), 256>>>(*v, op, static_cast<const uint32_t*>(keys), n, out, flags);
+  else
+    k_set_op<unsigned long long><<<grid(n), 256>>>(*v, op, static_cast<const unsigned long long*>(keys), n, out,
+                                                  flags);
+  return static_cast<int>(cudaDeviceSynchronize());
+}
+
+int wcu_count_add(const wc_device_view* v, const void* keys, const void* weights, uint64_t n, uint32_t* flags) {
+  if (n == 0) return 0;
+  if (v->key_bytes == 4)
+    k_count_add<uint32_t><<<grid(n), 256>>>(*v, static_cast<const uint32_t*>(keys),
+                                           static_cast<const uint32_t*>(weights), n, flags);
+  else
+    k_count_add<unsigned long long><<<grid(n), 256>>>(*v, static_cast<const unsigned long long*>(keys),
+                                                     static_cast<const unsigned long long*>(weights), n, flags);
+  return static_cast<int>(cudaDeviceSynchronize());
+}
+
+int wcu_count_get(const wc_device_view* v, const void* keys, uint64_t n, void* out, uint8_t* found) {
+  if (n == 0) return 0;
+  if (v->key_bytes == 4)
+    k_count_get<uint32_t><<<grid(n), 256>>>(*v, static_cast<const uint32_t*>(keys), n, static_cast<uint32_t*>(out),
+                                           found);
+  else
+    k_count_get<unsigned long long><<<grid(n), 256>>>(*v, static_cast<const unsigned long long*>(keys), n,
+                                                     static_cast<unsigned long long*>(out), found);
   return static_cast<int>(cudaDeviceSynchronize());
 }
 

@@ -44,6 +44,9 @@ def env(tmp_path_factory):
     lib.wcu_for_each.argtypes = [V, vp, u64, vp, vp]
     lib.wcu_for_all.argtypes = [V, vp]
     lib.wcu_mv_append.argtypes = [V, vp, vp, u64, vp]
+    lib.wcu_set_op.argtypes = [V, ctypes.c_int, vp, u64, vp, vp]
+    lib.wcu_count_add.argtypes = [V, vp, vp, u64, vp]
+    lib.wcu_count_get.argtypes = [V, vp, u64, vp, vp]
     lib.wcu_poke_u64.argtypes = [vp, u64]
     return wc, torch, lib
 
@@ -307,3 +310,99 @@ def test_device_append_wait_is_bounded(env):
     got, _ = t.retrieve_multi(k, offs)
     assert list(np.diff(offs)) == [2, 2]
     assert sorted(got[:2].tolist()) == [7, 8] and sorted(got[2:].tolist()) == [8, 8]
+
+
+
+# ---- hash sets and counting tables from user kernels (Sec. IV: HashSet, CountingHashTable) --
+
+def _view(wc, t):
+    v = wc._binding.WcDeviceView()
+    wc._binding.check(wc._binding.lib().wc_table_device_view(t.handle, ctypes.byref(v)), "wc_table_device_view")
+    return v
+
+
+@pytest.mark.parametrize("opt", [0, 1], ids=["plain", "overflow_bits"])
+@pytest.mark.parametrize("kb,W", [(4, 8), (4, 32), (8, 4), (8, 16)])
+def test_device_set_ops_match_the_oracle(env, kb, W, opt):
+    """Set inserts from a user kernel (duplicates inside the batch and of stored keys),
+    membership and erase by user kernels and by the bulk calls, crossed: every answer
+    equals the oracle's set; the slot dump has no duplicate and no unreachable key."""
+    wc, torch, lib = env
+    n = 60_000
+    allk = wc_inputs.distinct_u32(0x5E7 + W, 2 * n) if kb == 4 else wc_inputs.distinct_u64(0x5E7 + W, 2 * n)
+    keys = np.concatenate([allk[:n], allk[: n // 10]])  # the tail repeats stored keys
+    rng = np.random.default_rng(W)
+    rng.shuffle(keys)
+    t = wc.HashSetTable(kb, min_capacity=int(n / 0.85), window_width=W, seed=SEED, options=opt)
+    v = _view(wc, t)
+    o = oracle.HashSet(kb)
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = torch.empty(keys.size, dtype=torch.uint8, device="cuda")
+    assert lib.wcu_set_op(ctypes.byref(v), 0, dev(torch, keys, kb).data_ptr(), keys.size, out.data_ptr(),
+                          flags.data_ptr()) == 0
+    assert int(flags.item()) == o.insert(keys) == wc.WC_FLAG_DUPLICATE_KEY
+    assert int(out.sum().item()) == n and t.size() == o.size() == n
+    q = allk[wc_inputs.shuffle_index(3, allk.size)]
+    qo = torch.empty(q.size, dtype=torch.uint8, device="cuda")
+    assert lib.wcu_set_op(ctypes.byref(v), 1, dev(torch, q, kb).data_ptr(), q.size, qo.data_ptr(),
+                          flags.data_ptr()) == 0
+    ef, _ = o.contains(q)
+    np.testing.assert_array_equal(qo.cpu().numpy(), ef)
+    np.testing.assert_array_equal(t.contains(q), ef)  # the bulk call sees the user kernel's keys
+    drop = allk[: n // 3]
+    eo = torch.empty(drop.size, dtype=torch.uint8, device="cuda")
+    assert lib.wcu_set_op(ctypes.byref(v), 2, dev(torch, drop, kb).data_ptr(), drop.size, eo.data_ptr(),
+                          flags.data_ptr()) == 0
+    assert int(eo.sum().item()) == drop.size
+    o.erase(drop)
+    t.insert(allk[n: n + 1000])  # bulk inserts, seen by the user kernel's lookups
+    o.insert(allk[n: n + 1000])
+    assert lib.wcu_set_op(ctypes.byref(v), 1, dev(torch, q, kb).data_ptr(), q.size, qo.data_ptr(),
+                          flags.data_ptr()) == 0
+    ef, _ = o.contains(q)
+    np.testing.assert_array_equal(qo.cpu().numpy(), ef)
+    assert t.size() == o.size()
+    info = t.info
+    r = oracle.check_slots(wc.api.wc_table_dump_slots(t.handle), info["windows"], info["window_width"],
+                           info["slot_bytes"], SEED, True,
+                           wc.api.wc_table_dump_overflow_bits(t.handle) if opt else None, key_bytes=kb)
+    assert r["dups"] == 0 and r["unreachable"] == 0 and r["live"] == o.size()
+
+
+@pytest.mark.parametrize("kb,W", [(4, 8), (4, 16), (8, 4), (8, 8)])
+def test_device_count_add_matches_the_oracle(env, kb, W):
+    """Counting-table adds from a user kernel: 2^18 skewed occurrences with weights (and a
+    second launch without), crossed with bulk inserts and lookups; every count equals the
+    oracle's sum of weights per key (wrapping at the key width)."""
+    wc, torch, lib = env
+    n, nk = 1 << 18, 3000
+    kdt = np.uint32 if kb == 4 else np.uint64
+    uni = (wc_inputs.distinct_u32(0xC0 + W, 2 * nk) if kb == 4 else wc_inputs.distinct_u64(0xC0 + W, 2 * nk))
+    rng = np.random.default_rng(kb * 16 + W)
+    ranks = np.minimum(rng.zipf(1.3, n) - 1, nk - 1)
+    keys = uni[ranks].astype(kdt)
+    wts = rng.integers(0, 1000, n, dtype=np.uint64).astype(kdt)
+    t = wc.CountingTable(kb, min_capacity=int(nk / 0.8), window_width=W, seed=SEED)
+    v = _view(wc, t)
+    o = oracle.Counting(kb)
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert lib.wcu_count_add(ctypes.byref(v), dev(torch, keys, kb).data_ptr(), dev(torch, wts, kb).data_ptr(), n,
+                             flags.data_ptr()) == 0
+    o.insert(keys, wts)
+    assert lib.wcu_count_add(ctypes.byref(v), dev(torch, keys[: n // 2], kb).data_ptr(), None, n // 2,
+                             flags.data_ptr()) == 0
+    o.insert(keys[: n // 2])
+    t.insert(keys[: 5000])  # bulk occurrences of the same keys
+    o.insert(keys[: 5000])
+    assert int(flags.item()) == 0 and t.size() == o.size()
+    q = uni  # half of them never occur
+    out = torch.empty(q.size, dtype=torch.int32 if kb == 4 else torch.int64, device="cuda")
+    found = torch.empty(q.size, dtype=torch.uint8, device="cuda")
+    assert lib.wcu_count_get(ctypes.byref(v), dev(torch, q, kb).data_ptr(), q.size, out.data_ptr(),
+                             found.data_ptr()) == 0
+    eo, ef, _ = o.retrieve(q)
+    np.testing.assert_array_equal(found.cpu().numpy(), ef)
+    np.testing.assert_array_equal(host(out, kb)[ef == 1], eo[ef == 1])
+    bo, bf, _ = t.retrieve(q)  # the bulk lookup reads the same counts
+    np.testing.assert_array_equal(bf, ef)
+    np.testing.assert_array_equal(bo[ef == 1], eo[ef == 1])
