@@ -10,9 +10,9 @@
  *     the ones behind it);
  *   - continuous batching (WC_SERVE_BATCHED): admitted requests are packed into the next
  *     batched launch (wc_exec.h) while up to `max_inflight` earlier batches are still on
- *     the device, so requests arriving during a launch join the next one; a request that
- *     finds the device idle and no other request waiting runs at once as its own bulk
- *     call (nothing to pack it with);
+ *     the device, so requests arriving during a launch join the next one; a lone request
+ *     (no other admitted or waiting) runs at once as its own bulk call (nothing to pack it
+ *     with);
  *   - WC_SERVE_PER_CALL: every admitted request is launched at once as its own bulk call
  *     (the plain per-call API of wc.h) -- the baseline the batched mode is compared with.
  * Results are the same in both modes and equal to running the requests one by one in

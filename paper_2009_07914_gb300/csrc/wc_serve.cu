@@ -151,11 +151,12 @@ extern "C" wc_status wc_serve_run(wc_executor* ex, const wc_request* reqs, uint3
     while (st == WC_OK && !ready.empty() && inflight.size() < cfg->max_inflight) {
       Launch l;
       const uint64_t t = now_ns();
-      // A request that finds the device idle and nothing else admitted runs at once as
-      // its own bulk call: there is nothing to pack it with, and the plain launch has the
-      // shortest path to the device.  Batches form while earlier work is on the device.
-      const bool idle_single = inflight.empty() && ready.size() == 1 && waiting.empty();
-      const bool solo = !batched || idle_single ||
+      // A lone request (nothing else admitted or waiting) runs at once as its own bulk
+      // call: there is nothing to pack it with, and the plain launch has the shortest path
+      // to the device.  Batches form from the requests that queue up while earlier work
+      // is on the device.
+      const bool lone = ready.size() == 1 && waiting.empty();
+      const bool solo = !batched || lone ||
                         (cfg->solo_min_keys && reqs[ready.front()].work.n >= cfg->solo_min_keys);
       if (!solo) {
         batch.clear();

@@ -318,12 +318,9 @@ __device__ __forceinline__ void sv_retrieve_range(const TableDesc& t, const KIn*
       if (bm) {
         if (ln.r == 0) emit(pos, true, hit, hidx);
         act = false;
-      } else if (be) {
-        if (ln.r == 0) emit(pos, false, hit, hidx);
-        act = false;
-      } else if (Steps<H>::more(h)) {
+      } else if (!be && Steps<H>::more(h)) {
         ++h;  // the rest of this window
-      } else if (!ovf_bit(fw, w, tag) || ++j >= t.p) {
+      } else if (be || !ovf_bit(fw, w, tag) || ++j >= t.p) {
         if (ln.r == 0) emit(pos, false, hit, hidx);
         act = false;
       } else {
@@ -415,12 +412,9 @@ __device__ __forceinline__ void sv_retrieve_range_k(const TableDesc& t, const KI
         if (bm) {
           if (ln.r == 0) emit(pos[q], true, hit, hidx);
           act[q] = false;
-        } else if (be) {
-          if (ln.r == 0) emit(pos[q], false, hit, hidx);
-          act[q] = false;
-        } else if (Steps<H>::more(h[q])) {
+        } else if (!be && Steps<H>::more(h[q])) {
           ++h[q];  // the rest of this window
-        } else if (!ovf_bit(fw, w[q], tag[q]) || ++j[q] >= t.p) {
+        } else if (be || !ovf_bit(fw, w[q], tag[q]) || ++j[q] >= t.p) {
           if (ln.r == 0) emit(pos[q], false, hit, hidx);
           act[q] = false;
         } else {
@@ -786,12 +780,10 @@ __device__ __forceinline__ void sv_erase_range(const TableDesc& t, const KIn* __
           act = false;
         }
         // else: another erase of the same key won; read the window again
-      } else if (be) {
-        act = false;  // absent: nothing to erase
-      } else if (Steps<H>::more(h)) {
+      } else if (!be && Steps<H>::more(h)) {
         ++h;  // the rest of this window
-      } else if (!ovf_bit(fw, w, tag) || ++j >= t.p) {
-        act = false;
+      } else if (be || !ovf_bit(fw, w, tag) || ++j >= t.p) {
+        act = false;  // absent: nothing to erase
       } else {
         h = 0;
         w = probe_next(w, step, t.p);

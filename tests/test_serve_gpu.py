@@ -137,6 +137,7 @@ def test_served_workload_at_its_own_scale(env):
         assert dt.sizes() == sizes
         if mode == 0:
             assert serve.wc_executor_get_status(ex, clear=True) == 0
-            assert st["launches"] < nreq  # requests were coalesced
+            if not arr.any():
+                assert st["launches"] < nreq  # all at once: requests were coalesced
     serve.wc_executor_destroy(ex)
     dt.close()
