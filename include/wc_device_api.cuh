@@ -28,6 +28,7 @@
 
 #include <cooperative_groups.h>
 #include <cooperative_groups/reduce.h>
+#include <cooperative_groups/scan.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -641,6 +642,27 @@ __device__ __forceinline__ void store_release(unsigned long long* p, uint64_t x)
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(x) : "memory");
 }
 
+// `n` elements of the pool cursor for every converged thread at once: one atomic per
+// coalesced group (the threads that reach the allocation together), each thread's share by
+// an exclusive scan -- hot appends would otherwise serialise on the one cursor.
+__device__ __forceinline__ uint64_t pool_alloc(const wc_device_view& t, uint64_t n) {
+  namespace cg = cooperative_groups;
+  cg::coalesced_group g = cg::coalesced_threads();
+  const unsigned long long before = cg::exclusive_scan(g, static_cast<unsigned long long>(n));
+  unsigned long long base = 0;
+  if (g.thread_rank() == g.size() - 1) base = atomicAdd(t.pool_cursor, before + n);
+  base = g.shfl(base, g.size() - 1);
+  return base + before;
+}
+
+// Distinct-key count update aggregated over the converged threads.
+__device__ __forceinline__ void add_keys(const wc_device_view& t, unsigned long long d) {
+  namespace cg = cooperative_groups;
+  cg::coalesced_group g = cg::coalesced_threads();
+  const unsigned long long sum = cg::reduce(g, d, cg::plus<unsigned long long>());
+  if (g.thread_rank() == 0 && sum != 0) atomicAdd(t.num_keys, sum);
+}
+
 // The key's slot in the key store (windows of W 16-byte slots, the probing sequence of
 // the bulk calls), inserted with handle 0 (no bucket) when absent: the earliest empty or
 // tombstoned slot of the walk, claimed with one 128-bit CAS.  -1 with the flag set when
@@ -672,7 +694,7 @@ __device__ int64_t key_slot(const wc_device_view& t, unsigned long long key, uin
     if (empty || j + 1 == t.windows) {
       if (have_t) {
         if (S::cas(t.slots, t_slot, t_word, key, 0ull)) {
-          atomicAdd(t.num_keys, 1ull);
+          add_keys(t, 1ull);
           return static_cast<int64_t>(t_slot);
         }
         have_t = false;  // the tombstone was taken: walk again from the start
@@ -689,7 +711,7 @@ __device__ int64_t key_slot(const wc_device_view& t, unsigned long long key, uin
       for (int q = 1; q < W; ++q)
         if (q == free_q) fw = win.slot(q);
       if (S::cas(t.slots, base + free_q, fw, key, 0ull)) {
-        atomicAdd(t.num_keys, 1ull);
+        add_keys(t, 1ull);
         return static_cast<int64_t>(base + free_q);
       }
       continue;  // the slot was taken (maybe by this key): read the window again
@@ -747,7 +769,7 @@ __device__ uint32_t append_w(const wc_device_view& t, unsigned long long key, V 
       // room in the newest bucket: take value number c
       if (atomicCAS(handle, h, h + 1) == h) {
         put_value<V>(t, offset(h), newest, c, value);
-        atomicAdd(t.size, 1ull);
+        add_size(t, 1);
         return 0;
       }
     } else if (!blocked) {
@@ -755,7 +777,7 @@ __device__ uint32_t append_w(const wc_device_view& t, unsigned long long key, V 
       if (atomicCAS(handle, h, h | kBlocked) == h) {
         const int64_t b = newest + 1;
         const uint64_t foot = cum_foot(t, b) - cum_foot(t, b - 1);
-        const uint64_t off = atomicAdd(t.pool_cursor, foot);
+        const uint64_t off = pool_alloc(t, foot);
         if (off + foot > t.pool_capacity) {
           store_release(handle, h);  // unblock, unchanged
           flags |= WC_FLAG_POOL_EXHAUSTED;
@@ -767,7 +789,7 @@ __device__ uint32_t append_w(const wc_device_view& t, unsigned long long key, V 
         }
         put_value<V>(t, off, b, c, value);
         store_release(handle, make(off, c + 1, b > 0));
-        atomicAdd(t.size, 1ull);
+        add_size(t, 1);
         return 0;
       }
     } else {
