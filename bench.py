@@ -976,25 +976,28 @@ def run_served(args, dev):
     for _ in range(max(1, args.warmup)):
         run(1, zero)
         run(0, zero)
+    # batched mode: requests of 2^20 keys or more go as their own bulk calls (the per-call
+    # path splits large inserts by table region) and so does a lone request; the rest queue
+    # up while earlier work runs and are packed into executor batches.  The "all_in_executor"
+    # runs pack every request (no solo calls), for comparison.
+    solo = 1 << 20
     runs = {}
     with ClockSampler(dev.index) as clk:
         runs["per_call_closed"] = run(1, zero)
-        runs["batched_closed"] = run(0, zero)
-        # requests of 2^20 keys or more go as their own bulk calls (the per-call path splits
-        # large inserts by table region), the rest are packed into executor batches
-        runs["batched_solo_closed"] = run(0, zero, solo=1 << 20)
-        runs["batched_small_batches_closed"] = run(0, zero, solo=1 << 20, max_keys=1 << 22)
+        runs["batched_closed"] = run(0, zero, solo=solo)
+        runs["batched_all_in_executor_closed"] = run(0, zero)
+        runs["batched_small_batches_closed"] = run(0, zero, solo=solo, max_keys=1 << 22)
         sat = nreq / (runs["per_call_closed"]["wall_ms"] * 1e-3)
         for f in (0.5, 0.8, 0.95):
             arr = wc_inputs.poisson_arrivals(0x57C00005 + int(f * 100), nreq, f * sat)
             runs["per_call_%.2f" % f] = run(1, arr)
-            runs["batched_%.2f" % f] = run(0, arr)
-            runs["batched_solo_%.2f" % f] = run(0, arr, solo=1 << 20)
+            runs["batched_%.2f" % f] = run(0, arr, solo=solo)
+            runs["batched_all_in_executor_%.2f" % f] = run(0, arr)
     b, p = runs["batched_closed"], runs["per_call_closed"]
     _common(args, "served_64tables_%dreq" % nreq, "G keys/s served (batched, closed loop)", b["throughput_gkeys"],
             "G keys/s", b["wall_ms"], "u32", {"tables": 64, "requests": nreq, "keys": keys_total,
                                               "per_call_saturation_req_per_s": sat, "hbm_budget_bytes": budget,
-                                              "executor_groups": groups,
+                                              "executor_groups": groups, "solo_min_keys": solo,
                                               "resident_table_bytes": resident}, clk,
             b["launches"], {"runs": runs, "batched_over_per_call": b["throughput_gkeys"] / p["throughput_gkeys"]})
     serve.wc_executor_destroy(ex)
