@@ -525,7 +525,9 @@ def apply_groups(api, wc, h, spec: str, kif: str = "0"):
         gs = gs * 3
     for op, g in zip((wc.WC_OP_INSERT, wc.WC_OP_RETRIEVE, wc.WC_OP_ERASE), gs):
         if g:
-            api.wc_table_set_launch(h, op, g)
+            lc = api.wc_table_get_launch(h, op)
+            api.wc_table_set_launch(h, op, g, lc["block_threads"], lc["blocks_per_sm"], lc["scheme"], lc["region_mib"],
+                                    lc["keys_in_flight"])
     ks = [int(x) for x in str(kif).split(",") if x.strip()]
     ops = (wc.WC_OP_RETRIEVE,) if len(ks) == 1 else (wc.WC_OP_INSERT, wc.WC_OP_RETRIEVE)
     for op, k in zip(ops, ks):

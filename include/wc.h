@@ -191,7 +191,7 @@ typedef struct {
  * keys_in_flight = keys each group probes at once (1 or 2; 0 = 1): with 2, every trip of
  * a group loads the windows of two keys, so twice as many random window reads are in
  * flight per warp (single-value retrieves of up to 32 bytes of window per lane; elsewhere
- * it is taken as 1). */
+ * it is taken as 1).  Default 2 for lookups of 4+4-byte single-value tables, else 1. */
 typedef struct {
   int32_t group_size;
   int32_t block_threads;

@@ -479,6 +479,9 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
     t->launch[op].region_mib = 0;
     t->launch[op].keys_in_flight = 1;
   }
+  // lookups of packed 4+4-byte single-value tables keep two keys per group in flight
+  // (2^27 keys at load 0.9: 28.0 against 27.2 G lookups/s; +4 % at loads 0.5 and 0.99)
+  if (cfg->kind == WC_SINGLE_VALUE && !soa && slot_bytes == 8) t->launch[WC_OP_RETRIEVE].keys_in_flight = 2;
   if (mv) {
     t->launch[WC_OP_INSERT].block_threads = 256;
     t->launch[WC_OP_INSERT].group_size = 1;

@@ -90,10 +90,11 @@ def tune_table(h: int, keys: torch.Tensor, values: torch.Tensor, queries: torch.
     out = torch.empty(queries.numel(), dtype=torch.int32 if vb == 4 else torch.int64, device=keys.device)
     found = torch.empty(queries.numel(), dtype=torch.uint8, device=keys.device)
     for opname, op in (("insert", WC_OP_INSERT), ("retrieve", WC_OP_RETRIEVE), ("erase", WC_OP_ERASE)):
+        kif = api.wc_table_get_launch(h, op)["keys_in_flight"]  # kept as the table has it
         key = cache_key(kb, vb, W, alpha, n, opname)
         if key in cache:
             c = cache[key]
-            api.wc_table_set_launch(h, op, c["group"], c["block"], 0, c["scheme"], 0)
+            api.wc_table_set_launch(h, op, c["group"], c["block"], 0, c["scheme"], 0, kif)
             best[opname] = dict(c, cached=True)
             continue
         schemes = [WC_SCHEME_DIRECT, WC_SCHEME_BLOCKED] if opname == "insert" else [WC_SCHEME_DIRECT]
@@ -101,7 +102,7 @@ def tune_table(h: int, keys: torch.Tensor, values: torch.Tensor, queries: torch.
         for G in SHAPES[sb][W]:
             for blk in BLOCKS:
                 for sc in schemes:
-                    api.wc_table_set_launch(h, op, G, blk, 0, sc, 0)
+                    api.wc_table_set_launch(h, op, G, blk, 0, sc, 0, kif)
                     if opname == "insert":
                         def f():
                             api.wc_table_clear(h, s)
@@ -122,7 +123,7 @@ def tune_table(h: int, keys: torch.Tensor, values: torch.Tensor, queries: torch.
                         report(r)
         # erase candidates include the insert; the differences are the erase's
         b = min(results, key=lambda r: r["ms"])
-        api.wc_table_set_launch(h, op, b["group"], b["block"], 0, b["scheme"], 0)
+        api.wc_table_set_launch(h, op, b["group"], b["block"], 0, b["scheme"], 0, kif)
         best[opname] = {"group": b["group"], "block": b["block"], "scheme": b["scheme"], "ms": b["ms"]}
         cache[key] = best[opname]
         if opname == "insert":  # later ops need the table filled with the best insert
