@@ -251,6 +251,10 @@ def random_probe(dev, table_bytes: int):
         r = R.best_rate(buf, ab, mode, accesses=1 << 26)
         out[key] = r["accesses_per_s"] / 1e9
         out[key.replace("_gps", "_shape")] = {"in_flight": r["in_flight"], "lanes": r["lanes"]}
+    # read + CAS inside one 32 MiB region (L2-resident): what the region-split insert claims in
+    r = R.best_rate(buf, 64, 1, accesses=1 << 26, buffer_bytes=32 << 20)
+    out["rmw64_region_gps"] = r["accesses_per_s"] / 1e9
+    out["rmw64_region_shape"] = {"in_flight": r["in_flight"], "lanes": r["lanes"]}
     del buf
     torch.cuda.empty_cache()
     return out
@@ -505,13 +509,22 @@ def run_wc(args, rank, world, local_rank):
         # report the query rate against the random-window read rate of the same buffer
         ret_bound = random_bound(9, pr["rd64_gps"], peak)
         ins_bound = random_bound(8, pr["rmw64_gps"], peak)
+        # the region-split insert: streamed passes (histogram 4 B, split 8 B in + 8 B out,
+        # sweep 8 B in per pair) and the table read and written back once, region by region,
+        # plus one read + CAS per pair inside an L2-resident region
+        tbl = 2 * info["table_bytes"] / n
+        split_bound = random_bound(28 + tbl, pr["rmw64_region_gps"], peak)
         res["random_roofline"] = dict(pr, retrieve_bound_gops=ret_bound, insert_bound_gops=ins_bound,
                                       retrieve_frac_of_rd64=res["retrieve_gops"] / pr["rd64_gps"],
                                       insert_frac_of_rmw64=res["insert_gops"] / pr["rmw64_gps"],
                                       retrieve_frac_of_bound=res["retrieve_gops"] / ret_bound,
                                       insert_frac_of_bound=res["insert_gops"] / ins_bound,
+                                      insert_region_split_bound_gops=split_bound,
+                                      insert_frac_of_region_split_bound=res["insert_gops"] / split_bound,
                                       formula="1 / (stream_B / BW + 1 / R_window): retrieve 9 B streamed + one 64 B "
-                                              "random read, insert 8 B + one 64 B random read + CAS")
+                                              "random read; insert 8 B + one 64 B random read + CAS; region-split "
+                                              "insert 28 B + 2 x table bytes per pair streamed + one 64 B read + CAS "
+                                              "in a 32 MiB region")
     print(json.dumps(res), flush=True)
     api.wc_table_destroy(h)
 
