@@ -851,7 +851,7 @@ def run_device_api(args, dev):
 
     import paper_2009_07914_gb300 as wc
     from paper_2009_07914_gb300 import api
-    from paper_2009_07914_gb300.roofline import wc_bench_device_api
+    from paper_2009_07914_gb300.roofline import wc_bench_device_api, wc_bench_device_api_group
     from paper_2009_07914_gb300.table import to_device
     n = 1 << args.log2n
     seed = 0x2468ACE1
@@ -883,6 +883,22 @@ def run_device_api(args, dev):
                 assert api.wc_size(h) == nv and int(found.sum()) == nv
             if i >= args.warmup:
                 ev.append((t0, t1, t2, t3))
+    # the group-cooperative forms: tiles of G threads per key
+    grp = {}
+    for G in (2, 4):
+        gev = []
+        for i in range(args.warmup + args.steps):
+            api.wc_table_clear(h, s)
+            sink.zero_()
+            t0 = timed(s, lambda: wc_bench_device_api_group(h, 0, G, n, seed, None, s))
+            t1 = timed(s, lambda: wc_bench_device_api_group(h, 1, G, n, seed, sink, s))
+            if i == 0:
+                assert api.wc_size(h) == nv and int(sink.item()) & 0x7FFFFFFFFFFFFFFF == want
+            if i >= args.warmup:
+                gev.append((t0, t1))
+        gi, gl = (statistics.median(e[j] for e in gev) for j in range(2))
+        grp["group%d_insert_gops" % G] = n / gi / 1e6
+        grp["group%d_lookup_gops" % G] = n / gl / 1e6
     fi, fl, bi, br = (statistics.median(e[j] for e in ev) for j in range(4))
     _common(args, "device_api_u32_n2^%d_alpha%.2f" % (args.log2n, args.alpha),
             "G ops/s (device-API fused insert + lookup)", 2 * n / ((fi + fl) * 1e-3) / 1e9, "G ops/s", fi + fl, "u32",
@@ -891,7 +907,7 @@ def run_device_api(args, dev):
              "l2": "no flush: table 1.19 GB"}, clk, 2 * args.steps,
             {"fused_insert_gops": n / fi / 1e6, "fused_lookup_gops": n / fl / 1e6,
              "bulk_insert_gops": n / bi / 1e6, "bulk_retrieve_gops": n / br / 1e6,
-             "fused_insert_ms": fi, "fused_lookup_ms": fl, "bulk_insert_ms": bi, "bulk_retrieve_ms": br})
+             "fused_insert_ms": fi, "fused_lookup_ms": fl, "bulk_insert_ms": bi, "bulk_retrieve_ms": br, **grp})
     api.wc_table_destroy(h)
 
 

@@ -326,6 +326,155 @@ __device__ bool erase_w(const wc_device_view& t, K key) {
   return false;
 }
 
+// ---- group-cooperative operations (Sec. IV-B2: a cooperative group probes each window) --
+//
+// The G threads of a tile (cooperative_groups::thread_block_tile<G>) serve ONE key together,
+// every thread of the tile passing the same key (and value): thread r reads slots
+// [r * W/G, (r + 1) * W/G) of each window, votes run over the tile, and one thread claims.
+// This is the paper's device-side interface (a group per operation); with G > 1 a window
+// is read by G threads with one load request, and the walk's control is shared.
+
+// The S consecutive slot words of one thread (S words of 8 bytes for 4+4-byte pairs, of 16
+// for 8+8), loaded with one vector load of up to 32 bytes per instruction.
+template <class K, int S>
+struct LaneSlots {
+  using Sl = Slots<K>;
+  static constexpr int kWords = S * static_cast<int>(sizeof(K) == 4 ? 1 : 2);
+  unsigned long long u[kWords];
+  __device__ __forceinline__ void load(const void* slots, uint64_t first) {
+    const unsigned long long* p = static_cast<const unsigned long long*>(slots) + first * (sizeof(K) == 4 ? 1 : 2);
+    if constexpr (kWords == 1) {
+      asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(u[0]) : "l"(p));
+    } else if constexpr (kWords == 2) {
+      asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(u[0]), "=l"(u[1]) : "l"(p));
+    } else {
+#pragma unroll
+      for (int i = 0; i < kWords; i += 4)
+        asm volatile("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];"
+                     : "=l"(u[i]), "=l"(u[i + 1]), "=l"(u[i + 2]), "=l"(u[i + 3])
+                     : "l"(p + i));
+    }
+  }
+  __device__ __forceinline__ typename Sl::Word slot(int q) const {
+    if constexpr (sizeof(K) == 4) {
+      return typename Sl::Word{u[q]};
+    } else {
+      return typename Sl::Word{u[2 * q], u[2 * q + 1]};
+    }
+  }
+};
+
+template <class K, int W, int G>
+__device__ bool retrieve_group(const cooperative_groups::thread_block_tile<G>& g, const wc_device_view& t, K key,
+                               typename Slots<K>::V& value) {
+  using Sl = Slots<K>;
+  constexpr int S = W / G;
+  static_assert(S >= 1 && W % G == 0, "a window is split evenly over the tile");
+  const int r = static_cast<int>(g.thread_rank());
+  uint32_t w, step, tag;
+  probe_init(static_cast<uint64_t>(key), t.seed, t.windows, w, step, tag);
+  for (uint32_t j = 0; j < t.windows; ++j) {
+    LaneSlots<K, S> ls;
+    ls.load(t.slots, static_cast<uint64_t>(w) * W + r * S);
+    int hit_q = -1;
+    bool empty = false;
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      const K k = Sl::key(ls.slot(q));
+      if (k == key && hit_q < 0) hit_q = q;
+      empty |= k == K(0);
+    }
+    const unsigned hm = g.ballot(hit_q >= 0);
+    if (hm) {
+      typename Sl::V v = 0;
+#pragma unroll
+      for (int q = 0; q < S; ++q)
+        if (q == hit_q) v = Sl::val(ls.slot(q));
+      value = g.shfl(v, __ffs(hm) - 1);
+      return true;
+    }
+    if (g.any(empty) || overflow_clear(t, w, tag)) return false;
+    w = probe_next(w, step, t.windows);
+  }
+  return false;
+}
+
+template <class K, int W, int G>
+__device__ uint32_t insert_group(const cooperative_groups::thread_block_tile<G>& g, const wc_device_view& t, K key,
+                                 typename Slots<K>::V value) {
+  using Sl = Slots<K>;
+  using Word = typename Sl::Word;
+  constexpr int S = W / G;
+  static_assert(S >= 1 && W % G == 0, "a window is split evenly over the tile");
+  const int r = static_cast<int>(g.thread_rank());
+  uint32_t w0, step, tag;
+  probe_init(static_cast<uint64_t>(key), t.seed, t.windows, w0, step, tag);
+  uint32_t w = w0, j = 0;
+  bool have_t = false;  // first tombstone of the walk (the same on every thread of the tile)
+  uint64_t t_slot = 0;
+  Word t_word{};
+  while (j < t.windows) {
+    LaneSlots<K, S> ls;
+    const uint64_t mine = static_cast<uint64_t>(w) * W + r * S;
+    ls.load(t.slots, mine);
+    int match_q = -1, free_q = -1;
+    bool empty = false;
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      const K k = Sl::key(ls.slot(q));
+      if (k == key && match_q < 0) match_q = q;
+      const bool is_empty = k == K(0);
+      empty |= is_empty;
+      if ((is_empty || k == K(~K(0))) && free_q < 0) free_q = q;
+    }
+    Word fw = ls.slot(0);
+#pragma unroll
+    for (int q = 1; q < S; ++q)
+      if (q == free_q) fw = ls.slot(q);
+    const unsigned mm = g.ballot(match_q >= 0);
+    if (mm) {  // the key is present: its value is replaced (Sec. IV-B3)
+      if (r == __ffs(mm) - 1) Sl::set_val(t.slots, mine + match_q, value);
+      if (r == 0) raise(t, WC_FLAG_DUPLICATE_KEY);
+      return WC_FLAG_DUPLICATE_KEY;
+    }
+    const unsigned fm = g.ballot(free_q >= 0);
+    if (g.any(empty) || j + 1 == t.windows) {  // absent: claim the earliest candidate
+      bool ok = false;
+      if (have_t) {
+        if (r == 0) ok = Sl::cas(t.slots, t_slot, t_word, key, value);
+        if (g.shfl(ok, 0)) break;
+        have_t = false;  // the tombstone was taken: walk again from the start
+        w = w0;
+        j = 0;
+        continue;
+      }
+      if (!fm) {
+        if (r == 0) raise(t, WC_FLAG_PROBE_LIMIT);
+        return WC_FLAG_PROBE_LIMIT;
+      }
+      const int src = __ffs(fm) - 1;
+      if (r == src) ok = Sl::cas(t.slots, mine + free_q, fw, key, value);
+      if (g.shfl(ok, src)) break;
+      continue;  // lost the slot: read the window again
+    }
+    if (fm && !have_t) {  // a full window: its free slots are tombstones
+      const int src = __ffs(fm) - 1;
+      have_t = true;
+      t_slot = g.shfl(mine + static_cast<uint64_t>(free_q < 0 ? 0 : free_q), src);
+      if constexpr (sizeof(K) == 4) {
+        t_word = Word{g.shfl(fw.w, src)};
+      } else {
+        t_word = Word{g.shfl(fw.k, src), g.shfl(fw.v, src)};
+      }
+    }
+    if (t.overflow_bits && r == 0) atomicOr(t.overflow_bits + (w >> 2), 1u << overflow_shift(w, tag));
+    w = probe_next(w, step, t.windows);
+    ++j;
+  }
+  if (r == 0) add_size(t, 1);
+  return 0;
+}
+
 // insert_w / retrieve_w / erase_w take the table's window width W as a template argument
 // (it must equal view.window_width): a kernel that knows W keeps one window in registers
 // instead of the widest one.  insert / retrieve / erase below pick W at run time.

@@ -52,6 +52,12 @@ wc_status wc_bench_random_access(void* d_buffer, const wc_rand_access_config* cf
 wc_status wc_bench_device_api(wc_table* t, int32_t mode, uint64_t n, uint32_t key_seed, uint64_t* d_sink,
                               void* stream);
 
+/* The same fused producer with the device API's group-cooperative operations: tiles of
+ * `group` threads (1, 2 or 4; W 8 or 16) produce one key each and insert it (mode 0) or look
+ * it up (mode 1) together -- one window read per tile, votes over the tile. */
+wc_status wc_bench_device_api_group(wc_table* t, int32_t mode, int32_t group, uint64_t n, uint32_t key_seed,
+                                    uint64_t* d_sink, void* stream);
+
 /* Device-API probe of the bucket list (include/wc_device_api.cuh, wc_dev::append): one
  * thread per pair appends (d_keys[i], d_values[i]) -- device arrays of the table's key and
  * value widths -- to a bucket multi-value table created with a growth strategy, every pair

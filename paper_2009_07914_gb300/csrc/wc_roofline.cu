@@ -1,4 +1,5 @@
 // Random-access roofline probes (include/wc_roofline.h).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -187,6 +188,31 @@ void dev_probe(const wc_device_view& v, int mode, uint64_t n, uint32_t seed, uns
   }
 }
 
+// The fused producer with tiles of G threads per key (the device API's group-cooperative
+// insert and lookup).
+template <int W, int G>
+__global__ void __launch_bounds__(256) k_dev_group(wc_device_view v, int mode, uint64_t n, uint32_t seed,
+                                                   unsigned long long* sink) {
+  namespace cg = cooperative_groups;
+  const auto tile = cg::tiled_partition<G>(cg::this_thread_block());
+  const uint64_t tiles = static_cast<uint64_t>(gridDim.x) * blockDim.x / G;
+  unsigned long long acc = 0;
+  for (uint64_t i = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / G; i < n; i += tiles) {
+    const uint32_t k = static_cast<uint32_t>(i * 2654435761ull) ^ seed;
+    if (wc_dev::is_sentinel(k)) continue;
+    if (mode == 0) {
+      wc_dev::insert_group<uint32_t, W, G>(tile, v, k, static_cast<uint32_t>(i));
+    } else {
+      uint32_t x;
+      if (wc_dev::retrieve_group<uint32_t, W, G>(tile, v, k, x) && tile.thread_rank() == 0) acc += x;
+    }
+  }
+  if (mode != 0) {
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(sink, acc);
+  }
+}
+
 // One thread per pair appends (keys[i], values[i]) to a bucket multi-value table with the
 // device API's per-element append (the concurrent bucket-list insert).
 template <class K, class V>
@@ -201,6 +227,31 @@ __global__ void __launch_bounds__(256) k_dev_append(wc_device_view v, const K* _
 }  // namespace wc
 
 extern "C" {
+
+wc_status wc_bench_device_api_group(wc_table* t, int32_t mode, int32_t group, uint64_t n, uint32_t key_seed,
+                                    uint64_t* d_sink, void* stream) {
+  if (t == nullptr || (mode != 0 && mode != 1) || (mode == 1 && d_sink == nullptr)) return WC_ERR_INVALID_ARG;
+  wc_device_view v;
+  const wc_status st = wc_table_device_view(t, &v);
+  if (st != WC_OK) return st;
+  if (v.kind != WC_SINGLE_VALUE || v.key_bytes != 4) return WC_ERR_UNSUPPORTED;
+  if (n == 0) return WC_OK;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != t->device) return WC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto* sink = reinterpret_cast<unsigned long long*>(d_sink);
+  const int sms = wc::sm_count_of(t->device);
+#define WC_GRP(Wv, Gv)                                                                                   \
+  if (static_cast<int>(v.window_width) == (Wv) && group == (Gv)) {                                       \
+    const int bps = wc::occupancy(wc::k_dev_group<Wv, Gv>, 256);                                         \
+    wc::k_dev_group<Wv, Gv><<<bps * sms, 256, 0, s>>>(v, mode, n, key_seed, sink);                      \
+    return cudaGetLastError() == cudaSuccess ? WC_OK : WC_ERR_CUDA;                                    \
+  }
+  WC_GRP(8, 1) WC_GRP(8, 2) WC_GRP(8, 4) WC_GRP(16, 2) WC_GRP(16, 4)
+#undef WC_GRP
+  return WC_ERR_INVALID_ARG;
+}
 
 wc_status wc_bench_mv_append(wc_table* t, const void* d_keys, const void* d_values, uint64_t n, void* stream) {
   if (t == nullptr || (n > 0 && (d_keys == nullptr || d_values == nullptr))) return WC_ERR_INVALID_ARG;

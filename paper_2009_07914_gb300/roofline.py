@@ -24,7 +24,17 @@ B.extra_signatures({
                                            ctypes.c_void_p, ctypes.c_void_p]),
     "wc_bench_mv_append": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                           ctypes.c_void_p]),
+    "wc_bench_device_api_group": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                                 ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
 })
+
+
+def wc_bench_device_api_group(table: int, mode: int, group: int, n: int, key_seed: int,
+                              sink: torch.Tensor | None = None, stream=None):
+    """Device-API probe with tiles of `group` threads per key: mode 0 insert, 1 lookup."""
+    B.check(B.lib().wc_bench_device_api_group(table, mode, group, n, key_seed & 0xFFFFFFFF,
+                                              None if sink is None else B.ptr(sink), B.stream_handle(stream)),
+            "wc_bench_device_api_group")
 
 
 def wc_bench_mv_append(table: int, keys: torch.Tensor, values: torch.Tensor, n: int | None = None, stream=None):

@@ -1,6 +1,7 @@
 // A user's program of the device API (include/wc_device_api.cuh): its own kernels insert,
 // look up and erase single elements, and call for_each / for_all with device lambdas.
 // Test infrastructure: built by tests/test_device_api_gpu.py, called through ctypes.
+#include <cooperative_groups.h>
 #include <cstdint>
 
 #include "wc_device_api.cuh"
@@ -92,6 +93,36 @@ __global__ void k_count_get(wc_device_view v, const K* keys, uint64_t n, K* out,
   }
 }
 
+// Group-cooperative inserts and lookups: each tile of G threads serves one key.
+template <class K, int W, int G>
+__global__ void k_group_op(wc_device_view v, int op, const K* keys, const K* vals, uint64_t n, K* out, uint8_t* found,
+                           uint32_t* flags) {
+  namespace cg = cooperative_groups;
+  const auto tile = cg::tiled_partition<G>(cg::this_thread_block());
+  const uint64_t i = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / G;
+  if (i >= n) return;  // whole tiles leave together (n is counted in tiles)
+  if (op == 0) {
+    const uint32_t f = wc_dev::insert_group<K, W, G>(tile, v, keys[i], vals[i]);
+    if (f && tile.thread_rank() == 0) atomicOr(flags, f);
+  } else {
+    K x = K(~K(0));
+    const bool hit = wc_dev::retrieve_group<K, W, G>(tile, v, keys[i], x);
+    if (tile.thread_rank() == 0) {
+      out[i] = hit ? x : K(~K(0));
+      found[i] = hit ? 1 : 0;
+    }
+  }
+}
+
+template <class K, int W, int G>
+int launch_group(const wc_device_view& v, int op, const void* keys, const void* vals, uint64_t n, void* out,
+                 uint8_t* found, uint32_t* flags) {
+  const uint64_t threads = n * G;
+  k_group_op<K, W, G><<<static_cast<unsigned>((threads + 255) / 256), 256>>>(
+      v, op, static_cast<const K*>(keys), static_cast<const K*>(vals), n, static_cast<K*>(out), found, flags);
+  return static_cast<int>(cudaDeviceSynchronize());
+}
+
 unsigned grid(uint64_t n) { return static_cast<unsigned>((n + 255) / 256); }
 
 }  // namespace
@@ -176,6 +207,23 @@ int wcu_count_get(const wc_device_view* v, const void* keys, uint64_t n, void* o
     k_count_get<unsigned long long><<<grid(n), 256>>>(*v, static_cast<const unsigned long long*>(keys), n,
                                                      static_cast<unsigned long long*>(out), found);
   return static_cast<int>(cudaDeviceSynchronize());
+}
+
+// Group-cooperative op (0 insert, 1 lookup) with tiles of G threads; (key width, W, G) as
+// the tests use them.
+int wcu_group_op(const wc_device_view* v, int op, int G, const void* keys, const void* vals, uint64_t n, void* out,
+                 uint8_t* found, uint32_t* flags) {
+  if (n == 0) return 0;
+  const int W = static_cast<int>(v->window_width);
+#define WCU_G(K, Wv, Gv) \
+  if (W == (Wv) && G == (Gv)) return launch_group<K, Wv, Gv>(*v, op, keys, vals, n, out, found, flags);
+  if (v->key_bytes == 4) {
+    WCU_G(uint32_t, 8, 1) WCU_G(uint32_t, 8, 2) WCU_G(uint32_t, 8, 4) WCU_G(uint32_t, 16, 4) WCU_G(uint32_t, 32, 8)
+  } else {
+    WCU_G(unsigned long long, 4, 2) WCU_G(unsigned long long, 8, 4) WCU_G(unsigned long long, 2, 2)
+  }
+#undef WCU_G
+  return -1;
 }
 
 // Write one 8-byte word of device memory from the host (the tests' way to leave a list

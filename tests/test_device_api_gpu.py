@@ -45,6 +45,7 @@ def env(tmp_path_factory):
     lib.wcu_for_all.argtypes = [V, vp]
     lib.wcu_mv_append.argtypes = [V, vp, vp, u64, vp]
     lib.wcu_set_op.argtypes = [V, ctypes.c_int, vp, u64, vp, vp]
+    lib.wcu_group_op.argtypes = [V, ctypes.c_int, ctypes.c_int, vp, vp, u64, vp, vp, vp]
     lib.wcu_count_add.argtypes = [V, vp, vp, u64, vp]
     lib.wcu_count_get.argtypes = [V, vp, u64, vp, vp]
     lib.wcu_poke_u64.argtypes = [vp, u64]
@@ -406,3 +407,63 @@ def test_device_count_add_matches_the_oracle(env, kb, W):
     bo, bf, _ = t.retrieve(q)  # the bulk lookup reads the same counts
     np.testing.assert_array_equal(bf, ef)
     np.testing.assert_array_equal(bo[ef == 1], eo[ef == 1])
+
+
+
+# ---- group-cooperative device operations (a tile of G threads per key, Sec. IV-B2) ------
+
+@pytest.mark.parametrize("opt", [0, 1], ids=["plain", "overflow_bits"])
+@pytest.mark.parametrize("kb,W,G", [(4, 8, 1), (4, 8, 2), (4, 8, 4), (4, 16, 4), (4, 32, 8), (8, 4, 2), (8, 8, 4),
+                                    (8, 2, 2)])
+def test_group_device_ops_match_the_oracle(env, kb, W, G, opt):
+    """Tiles of G threads insert (with repeats of stored keys, after erases that leave
+    tombstones) and look up keys together; crossed with the bulk calls; every value and
+    found bit equals the oracle's and the slot dump passes the invariant checker."""
+    wc, torch, lib = env
+    n = 50_000
+    allk = wc_inputs.distinct_u32(0x6A + W * 8 + G, 2 * n) if kb == 4 else wc_inputs.distinct_u64(0x6A + W * 8 + G,
+                                                                                                 2 * n)
+    vals = (wc_inputs.uniform_u32(G, 2 * n) if kb == 4 else wc_inputs.uniform_u64(G, 2 * n))
+    t = wc.SingleValueTable(kb, kb, min_capacity=int(n / 0.9) + 1, window_width=W, seed=SEED, options=opt)
+    o = oracle.SingleValue(kb, kb)
+    v = _view(wc, t)
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    wdt = torch.int32 if kb == 4 else torch.int64
+
+    def ins(k, x):
+        assert lib.wcu_group_op(ctypes.byref(v), 0, G, dev(torch, k, kb).data_ptr(), dev(torch, x, kb).data_ptr(),
+                                k.size, None, None, flags.data_ptr()) == 0
+
+    def look(k):
+        out = torch.empty(k.size, dtype=wdt, device="cuda")
+        fnd = torch.empty(k.size, dtype=torch.uint8, device="cuda")
+        assert lib.wcu_group_op(ctypes.byref(v), 1, G, dev(torch, k, kb).data_ptr(), None, k.size, out.data_ptr(),
+                                fnd.data_ptr(), flags.data_ptr()) == 0
+        return host(out, kb), fnd.cpu().numpy()
+
+    ins(allk[:n], vals[:n])
+    o.insert(allk[:n], vals[:n])
+    assert int(flags.item()) == 0 and t.size() == o.size() == n
+    q = allk[wc_inputs.shuffle_index(5, allk.size)]
+    go, gf = look(q)
+    eo, ef, _ = o.retrieve(q)
+    np.testing.assert_array_equal(gf, ef)
+    np.testing.assert_array_equal(go[ef == 1], eo[ef == 1])
+    bo, bf, _ = t.retrieve(q)  # the bulk lookup finds the group inserts
+    np.testing.assert_array_equal(bf, ef)
+    np.testing.assert_array_equal(bo, eo)
+    drop = allk[: n // 3]
+    t.erase(drop)
+    o.erase(drop)
+    again = np.concatenate([drop[::2], allk[n // 2: n // 2 + 300]])  # tombstones reused, duplicates
+    ins(again, vals[n: n + again.size])
+    o.insert(again, vals[n: n + again.size])
+    assert int(flags.item()) == wc.WC_FLAG_DUPLICATE_KEY and t.size() == o.size()
+    go, gf = look(q)
+    eo, ef, _ = o.retrieve(q)
+    np.testing.assert_array_equal(gf, ef)
+    np.testing.assert_array_equal(go[ef == 1], eo[ef == 1])
+    info = t.info
+    r = oracle.check_slots(wc.api.wc_table_dump_slots(t.handle), info["windows"], info["window_width"],
+                           info["slot_bytes"], SEED, True, wc.api.wc_table_dump_overflow_bits(t.handle) if opt else None)
+    assert r["dups"] == 0 and r["unreachable"] == 0 and r["live"] == o.size()
