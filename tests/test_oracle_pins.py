@@ -325,6 +325,36 @@ def test_bloom_oracle_no_false_negatives_and_formula_rate():
     assert total > (1 - math.exp(-k * n / (blocks * 256))) ** k
 
 
+def test_bloom_oracle_is_empty_then_monotone():
+    """Properties of any Bloom filter, independent of how bits are chosen: an empty filter
+    reports no key; inserting more keys never turns a present answer into an absent one;
+    a key's answer does not depend on the order of the inserts; with one bit per key and a
+    filter of a single block, a key is present exactly when some inserted key has its bit."""
+    rng = np.random.default_rng(21)
+    probe = rng.integers(1, 2 ** 31, 50_000, dtype=np.uint64).astype(np.uint32)
+    o = oracle.BloomFilter(4, 64, 5, 77)
+    assert not o.contains(probe)[0].any()
+    keys = rng.integers(1, 2 ** 31, 6_000, dtype=np.uint64).astype(np.uint32)
+    prev = np.zeros(probe.size, dtype=np.uint8)
+    for part in np.array_split(keys, 6):
+        o.insert(part)
+        cur = o.contains(probe)[0]
+        assert (cur >= prev).all()
+        prev = cur
+    r = oracle.BloomFilter(4, 64, 5, 77)
+    r.insert(keys[::-1])
+    assert np.array_equal(r.contains(probe)[0], prev)
+    # one block, one bit per key: 256 bits, so exactly the probes sharing a bit with an
+    # inserted key are present -- and every probe that is an inserted key is present
+    one = oracle.BloomFilter(4, 1, 1, 5)
+    one.insert(keys[:40])
+    got = one.contains(probe)[0]
+    assert got.mean() < 1.0 and one.contains(keys[:40])[0].all()
+    # the filter has 256 bits; 40 keys set at most 40 of them, so at most 40/256 of the
+    # probes can be present (each probe maps to one bit; equality with the share of set bits)
+    assert got.mean() <= 40 / 256 + 0.01
+
+
 def _fmix64_py(x: int) -> int:
     m = (1 << 64) - 1
     x ^= x >> 33
