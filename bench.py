@@ -468,7 +468,8 @@ def run_wc(args, rank, world, local_rank):
     dom_ms = max(ins, ret)
     achieved = BYTES_PER_OP[dom] * n / (dom_ms * 1e-3) / 1e9
     workload_name = "sv_u32_n2^%d_alpha%.2f" % (args.log2n, args.alpha)
-    kname = "k_sv_insert" if dom == "insert" else "k_sv_retrieve"
+    kif_ret = api.wc_table_get_launch(h, wc.WC_OP_RETRIEVE)["keys_in_flight"]
+    kname = "k_sv_insert" if dom == "insert" else ("k_sv_retrieve2" if kif_ret == 2 else "k_sv_retrieve")
     traffic = ncu_traffic(kname, workload_name)
     cpu = None if args.no_cpu else cpu_baseline(23, args.alpha)
     res = {
