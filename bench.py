@@ -362,6 +362,15 @@ def run_wc(args, rank, world, local_rank):
     h = api.wc_table_create(wc.WC_SINGLE_VALUE, 4, 4, int(np.ceil(n / args.alpha)), args.window, 0,
                             0x5EEDC0DE + rank, local_rank, options=opts)
     info = api.wc_table_get_info(h)
+    tuning = None
+    if args.window == 0 and not args.soa and os.environ.get("WC_AUTOTUNE", "1") != "0":
+        # window_width 0: the create took the library autotuner's choice; read it back
+        ns = api.wc_autotune_sample_keys(wc.WC_SINGLE_VALUE, 4, 4, int(np.ceil(n / args.alpha)), opts)
+        tu = api.wc_autotune(wc.WC_SINGLE_VALUE, 4, 4, load=0.9, sample_keys=ns, options=opts, use_cache=True,
+                             device=local_rank)
+        tuning = {"by": "wc_autotune (window_width 0)", "sample_keys": tu["sample_keys"], "load": tu["load"],
+                  "candidates": tu["candidates"], "window_width": tu["window_width"],
+                  "sample_ms": [round(x, 4) for x in tu["ms"]]}
     apply_groups(api, wc, h, args.group, args.kif)
     g_ins = api.wc_table_get_launch(h, wc.WC_OP_INSERT)["group_size"]
     g_ret = api.wc_table_get_launch(h, wc.WC_OP_RETRIEVE)["group_size"]
@@ -478,7 +487,8 @@ def run_wc(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": workload_name, "n": n, "queries": n, "present_fraction": 0.5,
                    "capacity": info["capacity"], "achieved_alpha": n / info["capacity"],
-                   "window_slots": info["window_width"], "group_insert": g_ins, "group_retrieve": g_ret,
+                   "window_slots": info["window_width"], "tuning": tuning, "group_insert": g_ins,
+                   "group_retrieve": g_ret,
                    "insert_keys_in_flight": api.wc_table_get_launch(h, wc.WC_OP_INSERT)["keys_in_flight"],
                    "retrieve_keys_in_flight": api.wc_table_get_launch(h, wc.WC_OP_RETRIEVE)["keys_in_flight"],
                    "table_bytes": info["table_bytes"], "overflow_bits": bool(info["options"] & 1),

@@ -99,9 +99,14 @@ enum { WC_SINGLE_VALUE = 0, WC_MULTI_VALUE = 1, WC_MULTI_VALUE_OA = 2, WC_HASH_S
  *                        next to a handle to their values, Sec. IV-C).
  *   window_width         slots per probing window W (the inner linear-probing window of
  *                        the cooperative probing scheme, Sec. IV-B2).  Windows are
- *                        aligned to W slots.  0 = the library default for the widths.
- *                        Allowed: 4, 8, 16, 32 (8-byte slots); 2, 4, 8, 16 (16-byte slots);
- *                        2, 4, 8 (bucket multi-value key store).
+ *                        aligned to W slots.  0 = autotuned: single-value, counting and
+ *                        hash-set tables in packed slots take the window width and launch
+ *                        shapes the library's autotuner measures fastest for their kind,
+ *                        widths and options at load 0.9 (wc_tune.h; once per process and
+ *                        size class, synchronous); other tables, or with the environment
+ *                        variable WC_AUTOTUNE=0, 64-byte windows (W = 64 / slot bytes).
+ *                        Allowed: 8, 16, 32 (4-byte slots); 4, 8, 16, 32 (8-byte slots);
+ *                        2, 4, 8, 16 (16-byte slots); 2, 4, 8 (bucket multi-value key store).
  *   min_capacity         requested slots (key-store slots for multi-value).  The table
  *                        holds capacity = p * W slots with p the smallest prime
  *                        >= ceil(min_capacity / W), so the outer double-hashing sequence

@@ -95,6 +95,64 @@ def wc_table_get_launch(t: int, op: int) -> dict:
     return {f: getattr(lc, f) for f, _ in WcLaunch._fields_}
 
 
+class WcTuning(ctypes.Structure):
+    """include/wc_tune.h wc_tuning."""
+    _fields_ = [("window_width", ctypes.c_int32), ("candidates", ctypes.c_int32), ("from_cache", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("launch", WcLaunch * 3), ("ms", ctypes.c_double * 3),
+                ("sample_keys", ctypes.c_uint64), ("load", ctypes.c_double)]
+
+
+B.extra_signatures({
+    "wc_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64, ctypes.c_int32,
+                                   ctypes.c_void_p]),
+    "wc_table_apply_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "wc_autotune_sample_keys": (ctypes.c_uint64, [ctypes.c_void_p]),
+})
+
+
+def _tuning_dict(tu: WcTuning) -> dict:
+    return {"window_width": tu.window_width, "candidates": tu.candidates, "from_cache": tu.from_cache,
+            "launch": [{f: getattr(tu.launch[i], f) for f, _ in WcLaunch._fields_} for i in range(3)],
+            "ms": [tu.ms[i] for i in range(3)], "sample_keys": tu.sample_keys, "load": tu.load}
+
+
+def wc_autotune(kind: int = WC_SINGLE_VALUE, key_bytes: int = 4, value_bytes: int = 4, window_width: int = 0,
+                load: float = 0.9, sample_keys: int = 1 << 20, options: int = 0, use_cache: bool = True,
+                device: int | None = None, seed: int = 0x5EED_C0DE) -> dict:
+    """Time the library's kernels on a synthetic sample and return the chosen window width
+    and launch shapes (wc_tune.h); launch[i] is for op i (insert, retrieve, erase)."""
+    if device is None:
+        device = torch.cuda.current_device()
+    cfg = WcTableConfig(kind=kind, key_bytes=key_bytes, value_bytes=value_bytes, window_width=window_width,
+                        device=device, l2_persist=0, options=int(options), reserved=0, min_capacity=0,
+                        value_pool_capacity=0, seed=int(seed) & (2 ** 64 - 1), bucket_first_size=0,
+                        bucket_growth=1.0)
+    tu = WcTuning()
+    check(lib().wc_autotune(ctypes.byref(cfg), float(load), int(sample_keys), 1 if use_cache else 0,
+                            ctypes.byref(tu)), "wc_autotune")
+    return _tuning_dict(tu)
+
+
+def wc_autotune_sample_keys(kind: int = WC_SINGLE_VALUE, key_bytes: int = 4, value_bytes: int = 4,
+                            min_capacity: int = 1024, options: int = 0) -> int:
+    """Sample size wc_table_create tunes on for window_width = 0 (at load 0.9)."""
+    cfg = WcTableConfig(kind=kind, key_bytes=key_bytes, value_bytes=value_bytes, window_width=0, device=0,
+                        l2_persist=0, options=int(options), reserved=0, min_capacity=int(min_capacity),
+                        value_pool_capacity=0, seed=0, bucket_first_size=0, bucket_growth=1.0)
+    return int(lib().wc_autotune_sample_keys(ctypes.byref(cfg)))
+
+
+def wc_table_apply_tuning(t: int, tuning: dict):
+    tu = WcTuning(window_width=tuning["window_width"], candidates=tuning.get("candidates", 0),
+                  from_cache=tuning.get("from_cache", 0), reserved=0, sample_keys=tuning.get("sample_keys", 0),
+                  load=tuning.get("load", 0.0))
+    for i in range(3):
+        for f, _ in WcLaunch._fields_:
+            setattr(tu.launch[i], f, int(tuning["launch"][i][f]))
+        tu.ms[i] = float(tuning.get("ms", [0, 0, 0])[i])
+    check(lib().wc_table_apply_tuning(t, ctypes.byref(tu)), "wc_table_apply_tuning")
+
+
 def wc_insert(t: int, keys, values, n: int | None = None, stream=None):
     """values may be None for counting tables (every key counts 1)."""
     n = _n_of(n, keys)

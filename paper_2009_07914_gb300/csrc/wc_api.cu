@@ -16,6 +16,7 @@
 
 #include "wc.h"
 #include "wc_internal.h"
+#include "wc_tune.h"
 
 namespace wc {
 
@@ -363,12 +364,23 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   const bool bloom = cfg->kind == WC_BLOOM_FILTER;
   int W = cfg->window_width;
   int bloom_k = 0;
+  wc_tuning tuning;
+  bool tuned = false;
   if (bloom) {  // window_width carries k, the bits per key; a block is the unit of probing
     bloom_k = W == 0 ? 8 : W;
     if (bloom_k < 1 || bloom_k > 16) return WC_ERR_INVALID_ARG;
     W = 1;
+  } else if (W == 0) {
+    // autotuned (wc_tune.h) for the kinds the single-value engine serves in packed slots,
+    // else (or when tuning is off or fails) the 64-byte window
+    const bool tunable = (cfg->kind == WC_SINGLE_VALUE || cfg->kind == WC_COUNTING || cfg->kind == WC_HASH_SET) &&
+                         !(cfg->options & WC_OPT_SOA);
+    if (tunable && autotune_enabled() &&
+        wc_autotune(cfg, 0.9, autotune_sample_for(*cfg), 1, &tuning) == WC_OK)
+      tuned = true;
+    W = tuned ? tuning.window_width : static_cast<int>(64 / slot_bytes);
+    if (!window_ok(cfg->kind, slot_bytes, W)) return WC_ERR_INVALID_ARG;
   } else {
-    if (W == 0) W = slot_bytes == 4 ? 16 : (slot_bytes == 8 ? 8 : 4);  // 64-byte windows
     if (!window_ok(cfg->kind, slot_bytes, W)) return WC_ERR_INVALID_ARG;
   }
   int ndev = 0;
@@ -482,6 +494,10 @@ wc_status wc_table_create(wc_table** out, const wc_table_config* cfg) {
   // lookups of packed 4+4-byte single-value tables keep two keys per group in flight
   // (2^27 keys at load 0.9: 28.0 against 27.2 G lookups/s; +4 % at loads 0.5 and 0.99)
   if (cfg->kind == WC_SINGLE_VALUE && !soa && slot_bytes == 8) t->launch[WC_OP_RETRIEVE].keys_in_flight = 2;
+  if (tuned) {
+    for (int op = 0; op < 3; ++op)
+      if (shape_ok(t, op, tuning.launch[op].group_size)) t->launch[op] = tuning.launch[op];
+  }
   if (mv) {
     t->launch[WC_OP_INSERT].block_threads = 256;
     t->launch[WC_OP_INSERT].group_size = 1;

@@ -181,6 +181,11 @@ void host_pipe_free(wc_table* t);
 // Device bytes of the table's host-buffer staging (0 before the first host-buffer call).
 uint64_t host_pipe_bytes(const wc_table* t);
 
+// window_width = 0 at table creation (wc_tune.cu): the sample size the autotuner runs for a
+// table of this configuration, and whether tuning is on (environment WC_AUTOTUNE != 0).
+uint64_t autotune_sample_for(const wc_table_config& cfg);
+bool autotune_enabled();
+
 // Scheme the table uses for `op` on a batch of n keys.
 int scheme_for(const wc_table* t, int op, uint64_t n);
 

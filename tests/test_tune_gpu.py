@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+import wc_inputs
 
 pytestmark = pytest.mark.gpu
 
@@ -79,3 +80,120 @@ def test_executor_runs_the_tuned_lane_shapes(tmp_path, monkeypatch, W):
         dt.close()
     with pytest.raises(Exception):
         serve.wc_executor_create(0, W, group_insert=8, group_retrieve=8)
+
+
+# ---- the library's own autotuner (include/wc_tune.h) and window_width = 0 ------------------
+
+SIZES = {(0, 4, 4): 8, (0, 8, 8): 16, (4, 4, 4): 8, (4, 8, 8): 16, (3, 4, 0): 4, (3, 8, 0): 8}  # slot bytes
+WIDTHS = {4: (8, 16, 32), 8: (4, 8, 16), 16: (2, 4, 8)}
+
+
+def test_native_autotune_picks_valid_shapes_and_caches():
+    """wc_autotune times every window width and group size on its own sample: the choice
+    is a valid shape of an allowed width, a second call with the cache is answered from it
+    unchanged, and a table of the chosen width accepts the shapes."""
+    from paper_2009_07914_gb300 import build
+    build.build()
+    from paper_2009_07914_gb300 import api
+    a = api.wc_autotune(0, 4, 4, load=0.9, sample_keys=1 << 16, use_cache=False)
+    assert a["from_cache"] == 0 and a["window_width"] in WIDTHS[8]
+    assert a["candidates"] >= 3 * 3 and all(ms > 0 for ms in a["ms"]) and a["sample_keys"] == 1 << 16
+    b = api.wc_autotune(0, 4, 4, load=0.9, sample_keys=1 << 16, use_cache=True)
+    c = api.wc_autotune(0, 4, 4, load=0.9, sample_keys=1 << 16, use_cache=True)
+    assert b["from_cache"] == 0 and c["from_cache"] == 1
+    assert {k: v for k, v in c.items() if k != "from_cache"} == {k: v for k, v in b.items() if k != "from_cache"}
+    h = api.wc_table_create(0, 4, 4, 1 << 12, a["window_width"], 0, 0x5EED, 0)
+    api.wc_table_apply_tuning(h, a)
+    for op in range(3):
+        assert api.wc_table_get_launch(h, op) == a["launch"][op]
+    api.wc_table_destroy(h)
+    # a fixed width is kept; unsupported kinds and bad arguments are refused
+    f = api.wc_autotune(0, 8, 8, window_width=4, load=0.8, sample_keys=1 << 14, use_cache=False)
+    assert f["window_width"] == 4
+    for bad in (dict(kind=1), dict(load=1.0), dict(sample_keys=100), dict(options=2)):
+        args = dict(kind=0, key_bytes=4, value_bytes=4, load=0.9, sample_keys=1 << 14, use_cache=False)
+        args.update(bad)
+        with pytest.raises(Exception):
+            api.wc_autotune(**args)
+    h = api.wc_table_create(0, 4, 4, 1 << 12, 16, 0, 0x5EED, 0)
+    with pytest.raises(Exception):  # a tuning for another window width
+        api.wc_table_apply_tuning(h, dict(a, window_width=8 if a["window_width"] != 8 else 4))
+    api.wc_table_destroy(h)
+
+
+@pytest.mark.parametrize("kind,kb,vb", sorted(SIZES))
+def test_window_zero_tables_are_tuned_and_match_the_oracle(kind, kb, vb):
+    """window_width = 0: the table takes the width and shapes of the cached tuning for its
+    kind and widths (small tables: a 2^20-key sample at load 0.9), and the tuned table
+    gives the oracle's results for insert, lookup and erase."""
+    from paper_2009_07914_gb300 import build
+    build.build()
+    import paper_2009_07914_gb300 as wc
+    from paper_2009_07914_gb300 import api
+    n = 30000
+    seed = 7000 + 10 * kind + kb
+    keys = (wc_inputs.distinct_u32(seed, 2 * n) if kb == 4 else wc_inputs.distinct_u64(seed, 2 * n))
+    ins, absent = keys[:n], keys[n:]
+    q = np.concatenate([ins[::2], absent[: n // 2]])
+    if kind == 3:
+        t = wc.HashSetTable(kb, min_capacity=int(n / 0.85))
+        o = oracle.HashSet(kb)
+    elif kind == 4:
+        t = wc.CountingTable(kb, min_capacity=int(n / 0.85))
+        o = oracle.Counting(kb)
+    else:
+        t = wc.SingleValueTable(kb, vb, min_capacity=int(n / 0.85))
+        o = oracle.SingleValue(kb, vb)
+    tu = api.wc_autotune(kind, kb, vb, load=0.9, sample_keys=1 << 20, use_cache=True)
+    assert tu["from_cache"] == 1  # the create above tuned and cached it
+    assert t.info["window_width"] == tu["window_width"] in WIDTHS[SIZES[(kind, kb, vb)]]
+    for op in range(3):
+        assert api.wc_table_get_launch(t.handle, op) == tu["launch"][op]
+    if kind == 3:
+        assert t.insert(ins) == 0
+        o.insert(ins)
+        got, _ = t.contains(q)
+        np.testing.assert_array_equal(got, o.contains(q)[0])
+        t.erase(ins[: n // 3])
+        o.erase(ins[: n // 3])
+        got, _ = t.contains(q)
+        np.testing.assert_array_equal(got, o.contains(q)[0])
+    else:
+        vals = (np.arange(n, dtype=np.uint64) * 2654435761 + 1).astype(np.uint32 if vb == 4 else np.uint64)
+        if kind == 4:
+            t.insert(ins, vals)
+            o.insert(ins, vals)
+        else:
+            assert t.insert(ins, vals) == 0
+            o.insert(ins, vals)
+        out, found, _ = t.retrieve(q)
+        eo, ef, _ = o.retrieve(q)
+        np.testing.assert_array_equal(found, ef)
+        np.testing.assert_array_equal(out, eo)
+        t.erase(ins[: n // 3])
+        o.erase(ins[: n // 3])
+        out, found, _ = t.retrieve(q)
+        eo, ef, _ = o.retrieve(q)
+        np.testing.assert_array_equal(found, ef)
+        np.testing.assert_array_equal(out, eo)
+    assert t.size() == o.size()
+    t.close()
+
+
+def test_window_zero_without_tuning_is_the_64_byte_window(monkeypatch):
+    """WC_AUTOTUNE=0: window_width = 0 gives W = 64 / slot bytes and the fixed default shapes,
+    and bucket multi-value tables are never tuned."""
+    from paper_2009_07914_gb300 import build
+    build.build()
+    import paper_2009_07914_gb300 as wc
+    monkeypatch.setenv("WC_AUTOTUNE", "0")
+    for (kind, kb, vb), sb in sorted(SIZES.items()):
+        t = (wc.HashSetTable(kb, min_capacity=4096) if kind == 3 else
+             wc.CountingTable(kb, min_capacity=4096) if kind == 4 else
+             wc.SingleValueTable(kb, vb, min_capacity=4096))
+        assert t.info["window_width"] == 64 // sb
+        t.close()
+    monkeypatch.delenv("WC_AUTOTUNE")
+    m = wc.MultiValueTable(4, 4, min_capacity=4096, value_pool_capacity=1 << 14)
+    assert m.info["window_width"] == 4
+    m.close()
