@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access roofline probe")
     ap.add_argument("--kif", default="0",
                     help="sv32: keys in flight per group (1, 2; 0 = default): K for the lookups, or K_insert,K_lookup")
+    ap.add_argument("--retrieve-scheme", type=int, default=0,
+                    help="sv32: lookup scheme (0 = the table's, 1 direct, 2 region split, 3 grouped duplicates)")
     ap.add_argument("--alphas", default="0.5,0.8,0.9,0.95,0.99",
                     help="sv32: target loads of the density sweep reported beside the headline ('' = none)")
     ap.add_argument("--soa", action="store_true", help="sv32: struct-of-arrays table (keys and values in two arrays)")
@@ -371,7 +373,7 @@ def run_wc(args, rank, world, local_rank):
         tuning = {"by": "wc_autotune (window_width 0)", "sample_keys": tu["sample_keys"], "load": tu["load"],
                   "candidates": tu["candidates"], "window_width": tu["window_width"],
                   "sample_ms": [round(x, 4) for x in tu["ms"]]}
-    apply_groups(api, wc, h, args.group, args.kif)
+    apply_groups(api, wc, h, args.group, args.kif, args.retrieve_scheme)
     g_ins = api.wc_table_get_launch(h, wc.WC_OP_INSERT)["group_size"]
     g_ret = api.wc_table_get_launch(h, wc.WC_OP_RETRIEVE)["group_size"]
     s = torch.cuda.current_stream()
@@ -491,6 +493,8 @@ def run_wc(args, rank, world, local_rank):
                    "group_retrieve": g_ret,
                    "insert_keys_in_flight": api.wc_table_get_launch(h, wc.WC_OP_INSERT)["keys_in_flight"],
                    "retrieve_keys_in_flight": api.wc_table_get_launch(h, wc.WC_OP_RETRIEVE)["keys_in_flight"],
+                   "retrieve_scheme": {0: "auto (direct)", 1: "direct", 2: "region split", 3: "grouped duplicates"}[
+                       api.wc_table_get_launch(h, wc.WC_OP_RETRIEVE)["scheme"]],
                    "table_bytes": info["table_bytes"], "overflow_bits": bool(info["options"] & 1),
                    "layout": "struct of arrays" if info["options"] & 2 else "packed 64-bit slots",
                    "l2": "no flush: inputs and table larger than L2 (table %.2f GB, keys %.2f GB)"
@@ -540,10 +544,11 @@ def run_wc(args, rank, world, local_rank):
     api.wc_table_destroy(h)
 
 
-def apply_groups(api, wc, h, spec: str, kif: str = "0"):
+def apply_groups(api, wc, h, spec: str, kif: str = "0", retrieve_scheme: int = 0):
     """--group: one lane count for every operation, or one per operation (insert,
     retrieve[, erase]); 0 keeps the table's default.  kif: keys in flight per group, for
-    the lookups alone ("2") or for insert and lookups ("2,2"); 0 keeps the default."""
+    the lookups alone ("2") or for insert and lookups ("2,2"); 0 keeps the default.
+    retrieve_scheme: the lookups' WC_SCHEME_* (0 keeps the default)."""
     gs = [int(x) for x in str(spec).split(",") if x.strip()]
     if len(gs) == 1:
         gs = gs * 3
@@ -559,6 +564,10 @@ def apply_groups(api, wc, h, spec: str, kif: str = "0"):
             lc = api.wc_table_get_launch(h, op)
             api.wc_table_set_launch(h, op, lc["group_size"], lc["block_threads"], lc["blocks_per_sm"], lc["scheme"],
                                     lc["region_mib"], k)
+    if retrieve_scheme:
+        lc = api.wc_table_get_launch(h, wc.WC_OP_RETRIEVE)
+        api.wc_table_set_launch(h, wc.WC_OP_RETRIEVE, lc["group_size"], lc["block_threads"], lc["blocks_per_sm"],
+                                retrieve_scheme, lc["region_mib"], lc["keys_in_flight"])
 
 
 def load_sweep(args, api, wc, h_main, keys, vals, qk, out, found, n, s, peak, rank, local_rank):
@@ -574,7 +583,7 @@ def load_sweep(args, api, wc, h_main, keys, vals, qk, out, found, n, s, peak, ra
     for a in (float(x) for x in args.alphas.split(",") if x.strip()):
         h = api.wc_table_create(wc.WC_SINGLE_VALUE, 4, 4, int(np.ceil(n / a)), args.window, 0, 0x5EEDC0DE + rank,
                                 local_rank, options=info_main["options"])
-        apply_groups(api, wc, h, args.group, args.kif)
+        apply_groups(api, wc, h, args.group, args.kif, args.retrieve_scheme)
         info = api.wc_table_get_info(h)
         ins, ret = [], []
         for i in range(2 + steps):
