@@ -192,7 +192,8 @@ typedef struct {
  * insert: 256 or 512, the block of its aggregation passes, default 256, with tiles of four
  * keys per thread); blocks_per_sm = resident blocks per SM the grid is
  * sized for (0 = the occupancy limit); scheme = how a bulk call visits the table
- * (WC_SCHEME_*); region_mib = table bytes per region of the blocked scheme (0 = 32);
+ * (WC_SCHEME_*); region_mib = table MiB per region of the blocked scheme (0 = 32; a region
+ * holds a power of two of windows, the most that fit in region_mib MiB);
  * keys_in_flight = keys each group probes at once (1 or 2; 0 = 1): with 2, every trip of
  * a group loads the windows of two keys, so twice as many random window reads are in
  * flight per warp (single-value retrieves of up to 32 bytes of window per lane; elsewhere

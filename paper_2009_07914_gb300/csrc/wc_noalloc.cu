@@ -95,14 +95,7 @@ cudaError_t run(const wc_table* t, const void* keys, const void* vals, uint64_t 
   using Key = typename L::Key;
   using Val = typename L::Val;
   const wc_launch& lc = t->launch[WC_OP_INSERT];
-  RegionMap m;
-  m.seed = t->cfg.seed;
-  m.p = static_cast<uint32_t>(t->windows);
-  const uint64_t region_bytes = static_cast<uint64_t>(lc.region_mib > 0 ? lc.region_mib : 32) << 20;
-  uint64_t wpr = std::max<uint64_t>(1, region_bytes / (t->W * t->slot_bytes));
-  if ((t->windows + wpr - 1) / wpr > static_cast<uint64_t>(kMaxRegions)) wpr = (t->windows + kMaxRegions - 1) / kMaxRegions;
-  m.wpr = static_cast<uint32_t>(wpr);
-  m.R = static_cast<uint32_t>((t->windows + wpr - 1) / wpr);
+  const RegionMap m = region_map(t, lc.region_mib);
   auto* hist = reinterpret_cast<unsigned int*>(sc);
   auto* cursor = reinterpret_cast<unsigned long long*>(sc + kCursorOff);
   auto* work = reinterpret_cast<unsigned long long*>(sc + kWorkOff);

@@ -24,17 +24,34 @@ constexpr int kMaxRegions = 1024;
 
 struct RegionMap {
   uint64_t seed;
-  uint32_t p;    // windows of the table
-  uint32_t wpr;  // windows per region
-  uint32_t R;    // regions
+  uint32_t p;      // windows of the table
+  uint32_t shift;  // 2^shift windows per region
+  uint32_t R;      // regions
   template <class K>
   __device__ __forceinline__ uint32_t of(K key) const {
     uint32_t w, step;
     probe_init(static_cast<uint64_t>(key), seed, p, w, step);
-    const uint32_t r = w / wpr;
+    const uint32_t r = w >> shift;
     return r < R ? r : R - 1;
   }
 };
+
+// Regions of a table: a power of two of windows each (a shift instead of a division per
+// key), the largest one within region_mib MiB (0 = 32), doubled until there are at most
+// kMaxRegions of them.
+inline RegionMap region_map(const wc_table* t, int region_mib) {
+  const uint64_t region_bytes = static_cast<uint64_t>(region_mib > 0 ? region_mib : 32) << 20;
+  const uint64_t window_bytes = t->W * t->slot_bytes;
+  uint32_t shift = 0;
+  while ((window_bytes << (shift + 1)) <= region_bytes && shift < 31) ++shift;
+  while (((t->windows + (1ull << shift) - 1) >> shift) > static_cast<uint64_t>(kMaxRegions)) ++shift;
+  RegionMap m;
+  m.seed = t->cfg.seed;
+  m.p = static_cast<uint32_t>(t->windows);
+  m.shift = shift;
+  m.R = static_cast<uint32_t>((t->windows + (1ull << shift) - 1) >> shift);
+  return m;
+}
 
 // Region of an output position: `per` consecutive positions per region.  Bit 31 of the
 // word carries a flag (the found bit of a retrieve result) and is not part of the
@@ -279,21 +296,14 @@ struct RegionSplit {
 
 inline uint64_t align256(uint64_t x) { return (x + 255) / 256 * 256; }
 
-// Regions of about region_mib MiB of slots (at most kMaxRegions of them).  Scratch layout:
+// Regions of region_map(t, region_mib).  Scratch layout:
 // [header kSplitHeader B | keys | vals | extra], grown on demand.  kVals: where the values
 // come from (kValsIota: the input positions as uint32; kValsOne: all 1).
 template <class K, class V, int kVals = kValsRead>
 cudaError_t region_split(const wc_table* t, int region_mib, const K* keys, const V* vals, uint64_t n, cudaStream_t s,
                          RegionSplit<K, V>& out, uint64_t extra = 0) {
   static_assert(kMaxRegions * sizeof(unsigned long long) <= kSplitCnt - kSplitCursor, "cursor area");
-  RegionMap m;
-  m.seed = t->cfg.seed;
-  m.p = static_cast<uint32_t>(t->windows);
-  const uint64_t region_bytes = static_cast<uint64_t>(region_mib > 0 ? region_mib : 32) << 20;
-  uint64_t wpr = std::max<uint64_t>(1, region_bytes / (t->W * t->slot_bytes));
-  if ((t->windows + wpr - 1) / wpr > static_cast<uint64_t>(kMaxRegions)) wpr = (t->windows + kMaxRegions - 1) / kMaxRegions;
-  m.wpr = static_cast<uint32_t>(wpr);
-  m.R = static_cast<uint32_t>((t->windows + wpr - 1) / wpr);
+  const RegionMap m = region_map(t, region_mib);
   const uint64_t keys_off = kSplitHeader;
   const uint64_t vals_off = keys_off + align256(n * sizeof(K));
   const uint64_t extra_off = vals_off + align256(n * sizeof(V));
