@@ -257,7 +257,15 @@ def random_probe(dev, table_bytes: int):
     r = R.best_rate(buf, 64, 1, accesses=1 << 26, buffer_bytes=32 << 20)
     out["rmw64_region_gps"] = r["accesses_per_s"] / 1e9
     out["rmw64_region_shape"] = {"in_flight": r["in_flight"], "lanes": r["lanes"]}
+    # the random 32 B sector rates R_rd and R_rmw over 8 GiB (HBM) and over 32 MiB (L2)
     del buf
+    torch.cuda.empty_cache()
+    big = torch.zeros(8 << 30, dtype=torch.uint8, device=dev)
+    for mib, tag in ((8192, "8g"), (32, "l2")):
+        for mode, key in ((0, "rd32"), (1, "rmw32")):
+            r = R.best_rate(big, 32, mode, accesses=1 << 26, buffer_bytes=mib << 20)
+            out["%s_%s_gps" % (key, tag)] = r["accesses_per_s"] / 1e9
+    del big
     torch.cuda.empty_cache()
     return out
 
@@ -502,6 +510,7 @@ def run_wc(args, rank, world, local_rank):
                    "parallelism": "replicas (independent table per GPU)"},
         "insert_gops": n / (ins * 1e-3) / 1e9, "retrieve_gops": n / (ret * 1e-3) / 1e9,
         "clear_ms": statistics.median(clear_ms), "insert_ms": ins, "retrieve_ms": ret,
+        "insert_ms_mean": statistics.mean(ins_ms), "retrieve_ms_mean": statistics.mean(ret_ms),
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "bytes_per_op": BYTES_PER_OP[dom], "traffic": traffic,
@@ -534,6 +543,11 @@ def run_wc(args, rank, world, local_rank):
                                       insert_frac_of_rmw64=res["insert_gops"] / pr["rmw64_gps"],
                                       retrieve_frac_of_bound=res["retrieve_gops"] / ret_bound,
                                       insert_frac_of_bound=res["insert_gops"] / ins_bound,
+                                      theoretical_sector_gps=peak / 32,
+                                      retrieve_frac_of_theoretical_sectors=res["retrieve_gops"] / (peak / 32),
+                                      insert_frac_of_theoretical_sectors=2 * res["insert_gops"] / (peak / 32),
+                                      retrieve_frac_of_rd32_8g=res["retrieve_gops"] / pr["rd32_8g_gps"],
+                                      insert_frac_of_rmw32_8g=res["insert_gops"] / pr["rmw32_8g_gps"],
                                       insert_region_split_bound_gops=split_bound,
                                       insert_frac_of_region_split_bound=res["insert_gops"] / split_bound,
                                       formula="1 / (stream_B / BW + 1 / R_window): retrieve 9 B streamed + one 64 B "
