@@ -20,8 +20,8 @@ cudaError_t insert_passes(const wc_table* t, const void* keys, const void* vals,
   auto scatter = k_mv_aggregate<KIn, VB, W, true, kThreads>;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(count, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(A::smem_bytes(false)));
-    cudaFuncSetAttribute(scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(A::smem_bytes(true)));
+    cudaFuncSetAttribute(count, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(A::smem_bytes(false, sizeof(KIn))));
+    cudaFuncSetAttribute(scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(A::smem_bytes(true, sizeof(KIn))));
     attr_done = true;
   }
   // Large batches into a key store larger than L2 are first split by key-store region
@@ -39,20 +39,20 @@ cudaError_t insert_passes(const wc_table* t, const void* keys, const void* vals,
     counters = sp.counters;
   }
   const uint64_t ntiles = (n + A::kTile - 1) / A::kTile;
-  const int bps_c = occupancy_smem(count, kThreads, A::smem_bytes(false));
-  const int bps_s = occupancy_smem(scatter, kThreads, A::smem_bytes(true));
+  const int bps_c = occupancy_smem(count, kThreads, A::smem_bytes(false, sizeof(KIn)));
+  const int bps_s = occupancy_smem(scatter, kThreads, A::smem_bytes(true, sizeof(KIn)));
   const unsigned g_c = static_cast<unsigned>(std::min<uint64_t>(ntiles, static_cast<uint64_t>(bps_c) * t->sm_count));
   const unsigned g_s = static_cast<unsigned>(std::min<uint64_t>(ntiles, static_cast<uint64_t>(bps_s) * t->sm_count));
   e = cudaMemsetAsync(pd.pending, 0, t->capacity * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  e = launch_k(t, count, g_c, kThreads, A::smem_bytes(false), s, d, pd, k, vals, n, counters);
+  e = launch_k(t, count, g_c, kThreads, A::smem_bytes(false, sizeof(KIn)), s, d, pd, k, vals, n, counters);
   if (e != cudaSuccess) return e;
   const uint64_t per_block = static_cast<uint64_t>(kAllocThreads) * kAllocItems;
   const unsigned g_a = static_cast<unsigned>((t->capacity + per_block - 1) / per_block);
   e = launch_k(t, t->growth == kGrowExact ? k_mv_alloc<VB> : k_mv_alloc_growth<VB>, g_a, kAllocThreads, 0, s, d, pd,
                t->capacity);
   if (e != cudaSuccess) return e;
-  return launch_k(t, scatter, g_s, kThreads, A::smem_bytes(true), s, d, pd, k, vals, n,
+  return launch_k(t, scatter, g_s, kThreads, A::smem_bytes(true, sizeof(KIn)), s, d, pd, k, vals, n,
                   counters ? counters + 1 : counters);
 }
 

@@ -23,6 +23,7 @@
 
 #include "wc_device.cuh"
 #include "wc_internal.h"
+#include "wc_partition.cuh"
 #include "wc_sv_kernels.cuh"
 
 namespace wc {
@@ -146,10 +147,13 @@ template <int kThreads>
 struct Agg {
   static constexpr int kTile = kThreads * kAggPerThread;  // batch elements per tile
   static constexpr int kSlots = 2 * kTile;
-  static constexpr size_t smem_bytes(bool scatter) {
+  // the tile's hash table (keys, counts, list; bases in the scatter pass), then the next
+  // tile's input keys (key_bytes each), copied in while the current tile is processed
+  static constexpr size_t table_bytes(bool scatter) {
     return (scatter ? 2 : 1) * kSlots * sizeof(unsigned long long) + kSlots * sizeof(uint32_t) +
            kSlots * sizeof(unsigned short);
   }
+  static constexpr size_t smem_bytes(bool scatter, size_t key_bytes) { return table_bytes(scatter) + kTile * key_bytes; }
 };
 
 template <int kSlots>
@@ -313,30 +317,57 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
   using V = typename PoolT<VB>::T;
   constexpr int kAggTile = Agg<kAggThreads>::kTile;
   constexpr int kAggSlots = Agg<kAggThreads>::kSlots;
-  extern __shared__ unsigned long long agg_smem[];  // Agg<kAggThreads>::smem_bytes(kScatter) bytes
+  extern __shared__ unsigned long long agg_smem[];  // Agg<kAggThreads>::smem_bytes(kScatter, sizeof(KIn)) bytes
   unsigned long long* s_key = agg_smem;
   unsigned long long* s_base = agg_smem + kAggSlots;
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(agg_smem + (kScatter ? 2 : 1) * kAggSlots);
   unsigned short* s_list = reinterpret_cast<unsigned short*>(s_cnt + kAggSlots);
+  KIn* s_in = reinterpret_cast<KIn*>(reinterpret_cast<char*>(agg_smem) + Agg<kAggThreads>::table_bytes(kScatter));
   __shared__ uint32_t s_wsum[kAggThreads / 32];
   __shared__ uint32_t s_len, s_next;
   const int lane = threadIdx.x & 31;
   const uint64_t ntiles = (n + kAggTile - 1) / kAggTile;
   uint32_t flags = 0;
   long long created = 0;
-  __shared__ unsigned long long s_tile;
+  __shared__ unsigned long long s_tile, s_ntile;
+  // the keys of tile `tl` go to s_in asynchronously (cp.async) while the block works on
+  // the tile before it, so a tile starts without a wait on HBM
+  auto prefetch = [&](uint64_t tl) {
+    const uint64_t b = tl * kAggTile;
+    const uint32_t cnt = static_cast<uint32_t>(n - b < kAggTile ? n - b : kAggTile);
+    for (uint32_t i = threadIdx.x; i < cnt; i += kAggThreads) cp_async_elem(s_in + i, keys + b + i);
+  };
   uint64_t tile = blockIdx.x;
   if (tile_counter != nullptr) {
     if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1ull);
     __syncthreads();
     tile = s_tile;
   }
+  if (tile < ntiles) prefetch(tile);
   while (tile < ntiles) {
+    // the next tile: taken now, so that its keys can be copied in during this one
+    uint64_t next = tile + gridDim.x;
+    if (tile_counter != nullptr) {
+      if (threadIdx.x == 0) s_ntile = atomicAdd(tile_counter, 1ull);
+    }
     for (int e = threadIdx.x; e < kAggSlots; e += kAggThreads) {
       s_key[e] = 0ull;
       s_cnt[e] = 0u;
     }
+    cp_async_wait_all();
     __syncthreads();
+    if (tile_counter != nullptr) next = s_ntile;
+    KIn kin_t[kAggPerThread];
+    V vin_t[kAggPerThread];
+#pragma unroll
+    for (int k = 0; k < kAggPerThread; ++k) {
+      const uint64_t e = tile * kAggTile + static_cast<uint64_t>(k) * kAggThreads + threadIdx.x;
+      kin_t[k] = e < n ? s_in[k * kAggThreads + threadIdx.x] : KIn(0);
+      // values are consumed at the end of the tile: their loads overlap the tile's work
+      if constexpr (kScatter) vin_t[k] = e < n ? static_cast<const V*>(vals)[e] : V(0);
+    }
+    __syncthreads();  // s_in is free again
+    if (next < ntiles) prefetch(next);
     int my_slot[kAggPerThread];
     uint32_t my_rank[kAggPerThread];
 #pragma unroll
@@ -345,7 +376,7 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
       unsigned long long key = 0ull;
       bool valid = false;
       if (e < n) {
-        const KIn kin = keys[e];
+        const KIn kin = kin_t[k];
         valid = !is_sentinel(kin);
         if (valid) key = static_cast<unsigned long long>(kin);
         else flags |= kFlagInvalid;
@@ -387,28 +418,21 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
     if constexpr (kScatter) {
       __syncthreads();
       V* pool = static_cast<V*>(pd.pool);
-      const V* vin = static_cast<const V*>(vals);
 #pragma unroll
       for (int k = 0; k < kAggPerThread; ++k) {
-        const uint64_t e = tile * kAggTile + static_cast<uint64_t>(k) * kAggThreads + threadIdx.x;
         if (my_slot[k] < 0) continue;
         const unsigned long long b = s_base[my_slot[k]];
         if (b == ~0ull) continue;
         if (pd.growth == kGrowExact)
-          pool[b + my_rank[k]] = vin[e];
+          pool[b + my_rank[k]] = vin_t[k];
         else
-          pool[g_value_index<VB>(pd, s_key[my_slot[k]], s_cnt[my_slot[k]], b + my_rank[k])] = vin[e];
+          pool[g_value_index<VB>(pd, s_key[my_slot[k]], s_cnt[my_slot[k]], b + my_rank[k])] = vin_t[k];
       }
     }
     __syncthreads();
-    if (tile_counter != nullptr) {
-      if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1ull);
-      __syncthreads();
-      tile = s_tile;
-    } else {
-      tile += gridDim.x;
-    }
+    tile = next;
   }
+  cp_async_wait_all();
   flush_flags(t.status, flags);
   if constexpr (!kScatter) flush_delta(t.nkeys, created);
 }
