@@ -17,43 +17,57 @@ cudaError_t insert_passes(const wc_table* t, const void* keys, const void* vals,
   const PoolDesc pd = pool_of(t);
   const KIn* k = static_cast<const KIn*>(keys);
   auto count = k_mv_aggregate<KIn, VB, W, false, kThreads>;
-  auto scatter = k_mv_aggregate<KIn, VB, W, true, kThreads>;
+  auto place = k_mv_place<VB, kThreads>;
+  const size_t smem_c = A::smem_bytes(false, sizeof(KIn));
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(count, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(A::smem_bytes(false, sizeof(KIn))));
-    cudaFuncSetAttribute(scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(A::smem_bytes(true, sizeof(KIn))));
+    cudaFuncSetAttribute(count, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_c));
     attr_done = true;
   }
+  // The counting pass's record for the placing pass (TileRecord): a (slot, count) entry
+  // per distinct key of a tile and one word per element.
+  const uint64_t ntiles = (n + A::kTile - 1) / A::kTile;
+  const uint64_t list_bytes = align256(ntiles * A::kTile * sizeof(uint2));
+  const uint64_t elem_bytes = align256(n * sizeof(uint32_t));
+  const uint64_t rec_bytes = list_bytes + elem_bytes + align256(ntiles * sizeof(uint32_t));
   // Large batches into a key store larger than L2 are first split by key-store region
   // (the region split of the single-value insert): the passes then probe one L2-resident
   // region of the key store at a time, and pass 3 writes one range of the pool at a time
   // (pass 2 lays buckets out in key-store order).
   unsigned long long* counters = nullptr;
+  char* rec_base = nullptr;
   cudaError_t e = cudaSuccess;
   if (n >= (1ull << 20) && t->table_bytes > (64ull << 20)) {
     RegionSplit<KIn, V> sp;
-    e = region_split(t, 32, k, static_cast<const V*>(vals), n, s, sp);
+    e = region_split(t, 32, k, static_cast<const V*>(vals), n, s, sp, rec_bytes);
     if (e != cudaSuccess) return e;
     k = sp.keys;
     vals = sp.vals;
     counters = sp.counters;
+    rec_base = sp.extra;
+  } else {
+    e = ensure_scratch(t, rec_bytes, s);
+    if (e != cudaSuccess) return e;
+    rec_base = static_cast<char*>(t->d_scratch);
   }
-  const uint64_t ntiles = (n + A::kTile - 1) / A::kTile;
-  const int bps_c = occupancy_smem(count, kThreads, A::smem_bytes(false, sizeof(KIn)));
-  const int bps_s = occupancy_smem(scatter, kThreads, A::smem_bytes(true, sizeof(KIn)));
+  TileRecord rec;
+  rec.list = reinterpret_cast<uint2*>(rec_base);
+  rec.elem = reinterpret_cast<uint32_t*>(rec_base + list_bytes);
+  rec.len = reinterpret_cast<uint32_t*>(rec_base + list_bytes + elem_bytes);
+  const int bps_c = occupancy_smem(count, kThreads, smem_c);
+  const int bps_p = occupancy(place, kThreads);
   const unsigned g_c = static_cast<unsigned>(std::min<uint64_t>(ntiles, static_cast<uint64_t>(bps_c) * t->sm_count));
-  const unsigned g_s = static_cast<unsigned>(std::min<uint64_t>(ntiles, static_cast<uint64_t>(bps_s) * t->sm_count));
+  const unsigned g_p = static_cast<unsigned>(std::min<uint64_t>(ntiles, static_cast<uint64_t>(bps_p) * t->sm_count));
   e = cudaMemsetAsync(pd.pending, 0, t->capacity * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  e = launch_k(t, count, g_c, kThreads, A::smem_bytes(false, sizeof(KIn)), s, d, pd, k, vals, n, counters);
+  e = launch_k(t, count, g_c, kThreads, smem_c, s, d, pd, k, vals, n, counters, rec);
   if (e != cudaSuccess) return e;
   const uint64_t per_block = static_cast<uint64_t>(kAllocThreads) * kAllocItems;
   const unsigned g_a = static_cast<unsigned>((t->capacity + per_block - 1) / per_block);
   e = launch_k(t, t->growth == kGrowExact ? k_mv_alloc<VB> : k_mv_alloc_growth<VB>, g_a, kAllocThreads, 0, s, d, pd,
                t->capacity);
   if (e != cudaSuccess) return e;
-  return launch_k(t, scatter, g_s, kThreads, A::smem_bytes(true, sizeof(KIn)), s, d, pd, k, vals, n,
-                  counters ? counters + 1 : counters);
+  return launch_k(t, place, g_p, kThreads, 0, s, d, pd, rec, vals, n, counters ? counters + 1 : counters);
 }
 
 // The aggregation passes run blocks of the insert launch's block_threads (256 or 512;

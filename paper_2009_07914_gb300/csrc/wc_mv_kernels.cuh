@@ -147,13 +147,25 @@ template <int kThreads>
 struct Agg {
   static constexpr int kTile = kThreads * kAggPerThread;  // batch elements per tile
   static constexpr int kSlots = 2 * kTile;
-  // the tile's hash table (keys, counts, list; bases in the scatter pass), then the next
-  // tile's input keys (key_bytes each), copied in while the current tile is processed
+  // the tile's hash table (keys, counts, list; bases in the scatter pass; key-store slots
+  // and list positions in the counting pass), then the next tile's input keys (key_bytes
+  // each), copied in while the current tile is processed
   static constexpr size_t table_bytes(bool scatter) {
     return (scatter ? 2 : 1) * kSlots * sizeof(unsigned long long) + kSlots * sizeof(uint32_t) +
-           kSlots * sizeof(unsigned short);
+           kSlots * sizeof(unsigned short) + (scatter ? 0 : kSlots * (sizeof(uint32_t) + sizeof(unsigned short)));
   }
   static constexpr size_t smem_bytes(bool scatter, size_t key_bytes) { return table_bytes(scatter) + kTile * key_bytes; }
+};
+
+// What the counting pass leaves for the placing pass (k_mv_place), per tile of the batch:
+// the tile's distinct keys as (key-store slot, count) at list[tile * kTile ..] (slot all
+// ones: the key could not be stored), their number at len[tile], and for every element
+// elem[e] = (position of its key in the list) << 16 | (its rank among the tile's elements
+// of that key), or all ones for a sentinel key.
+struct TileRecord {
+  uint2* list;
+  uint32_t* elem;
+  uint32_t* len;
 };
 
 template <int kSlots>
@@ -198,12 +210,14 @@ __device__ __forceinline__ uint32_t block_exclusive_u32(uint32_t x, uint32_t& to
 // in -- or, in the counting pass, inserted into -- the key store with one lane per key.
 // The loop is warp-uniform: each trip loads one window for every lane holding a key,
 // so a warp's window loads are in flight together, and a lane that finishes takes the
-// next key of the list.  Counting pass: pending[slot] += the key's tile count.  Scatter
-// pass: reserve the key's run in its bucket (s_base[e] = first pool index, or all ones).
+// next key of the list.  Counting pass: pending[slot] += the key's tile count, and
+// s_ks[e] = slot (when s_ks is given).  Scatter pass: reserve the key's run in its bucket
+// (s_base[e] = first pool index, or all ones).
 template <int W, bool kScatter, int VB>
 __device__ __forceinline__ void ks_global_phase(const TableDesc& t, const PoolDesc& pd,
                                                 unsigned long long* s_key, uint32_t* s_cnt,
-                                                unsigned long long* s_base, const unsigned short* s_list,
+                                                unsigned long long* s_base, uint32_t* s_ks,
+                                                const unsigned short* s_list,
                                                 uint32_t len, uint32_t* s_next, uint32_t& flags,
                                                 long long& created) {
   KsSlot* slots = static_cast<KsSlot*>(t.slots);
@@ -289,6 +303,7 @@ __device__ __forceinline__ void ks_global_phase(const TableDesc& t, const PoolDe
       if (slot >= 0) {
         if constexpr (!kScatter) {
           atomicAdd(pd.pending + slot, s_cnt[e]);
+          if (s_ks != nullptr) s_ks[e] = static_cast<uint32_t>(slot);
         } else {
           const uint32_t old = atomicAdd(pd.pending + slot, s_cnt[e]);
           if (pd.growth == kGrowExact) {
@@ -313,7 +328,7 @@ template <class KIn, int VB, int W, bool kScatter, int kAggThreads>
 // one range of the value pool at a time); otherwise tiles are strided over the grid.
 __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolDesc pd, const KIn* __restrict__ keys,
                                                               const void* __restrict__ vals, uint64_t n,
-                                                              unsigned long long* tile_counter) {
+                                                              unsigned long long* tile_counter, TileRecord rec) {
   using V = typename PoolT<VB>::T;
   constexpr int kAggTile = Agg<kAggThreads>::kTile;
   constexpr int kAggSlots = Agg<kAggThreads>::kSlots;
@@ -322,6 +337,9 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
   unsigned long long* s_base = agg_smem + kAggSlots;
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(agg_smem + (kScatter ? 2 : 1) * kAggSlots);
   unsigned short* s_list = reinterpret_cast<unsigned short*>(s_cnt + kAggSlots);
+  // counting pass with a record: key-store slot and list position of every table entry
+  uint32_t* s_ks = (!kScatter && rec.elem != nullptr) ? reinterpret_cast<uint32_t*>(s_list + kAggSlots) : nullptr;
+  unsigned short* s_pos = reinterpret_cast<unsigned short*>(reinterpret_cast<uint32_t*>(s_list + kAggSlots) + kAggSlots);
   KIn* s_in = reinterpret_cast<KIn*>(reinterpret_cast<char*>(agg_smem) + Agg<kAggThreads>::table_bytes(kScatter));
   __shared__ uint32_t s_wsum[kAggThreads / 32];
   __shared__ uint32_t s_len, s_next;
@@ -353,6 +371,7 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
     for (int e = threadIdx.x; e < kAggSlots; e += kAggThreads) {
       s_key[e] = 0ull;
       s_cnt[e] = 0u;
+      if (s_ks != nullptr) s_ks[e] = ~0u;
     }
     cp_async_wait_all();
     __syncthreads();
@@ -407,14 +426,36 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
       uint32_t pos = block_exclusive_u32<kAggThreads>(c, total, s_wsum);
 #pragma unroll
       for (int i = 0; i < kPer; ++i)
-        if (s_key[e0 + i] != 0ull) s_list[pos++] = static_cast<unsigned short>(e0 + i);
+        if (s_key[e0 + i] != 0ull) {
+          if (s_ks != nullptr) s_pos[e0 + i] = static_cast<unsigned short>(pos);
+          s_list[pos++] = static_cast<unsigned short>(e0 + i);
+        }
       if (threadIdx.x == 0) {
         s_len = total;
         s_next = 0;
       }
       __syncthreads();
     }
-    ks_global_phase<W, kScatter, VB>(t, pd, s_key, s_cnt, s_base, s_list, s_len, &s_next, flags, created);
+    if (s_ks != nullptr) {
+      // the record of this tile for the placing pass: element words now (the list
+      // positions are known), the (slot, count) list after the key-store phase
+#pragma unroll
+      for (int k = 0; k < kAggPerThread; ++k) {
+        const uint64_t e = tile * kAggTile + static_cast<uint64_t>(k) * kAggThreads + threadIdx.x;
+        if (e < n)
+          rec.elem[e] = my_slot[k] < 0 ? ~0u : (static_cast<uint32_t>(s_pos[my_slot[k]]) << 16) | my_rank[k];
+      }
+    }
+    ks_global_phase<W, kScatter, VB>(t, pd, s_key, s_cnt, s_base, s_ks, s_list, s_len, &s_next, flags, created);
+    if (s_ks != nullptr) {
+      __syncthreads();
+      const uint32_t len = s_len;
+      for (uint32_t i = threadIdx.x; i < len; i += kAggThreads) {
+        const int e = s_list[i];
+        rec.list[tile * kAggTile + i] = make_uint2(s_ks[e], s_cnt[e]);
+      }
+      if (threadIdx.x == 0) rec.len[tile] = len;
+    }
     if constexpr (kScatter) {
       __syncthreads();
       V* pool = static_cast<V*>(pd.pool);
@@ -435,6 +476,92 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
   cp_async_wait_all();
   flush_flags(t.status, flags);
   if constexpr (!kScatter) flush_delta(t.nkeys, created);
+}
+
+// ---- pass 3: placing the values ------------------------------------------------------------
+// With the counting pass's record of every tile (TileRecord), no key is looked up again:
+// per tile, each distinct key reserves its run in its bucket with one atomic on the
+// pending counter that pass 2 reset (Sec. IV-C's per-key cursor), and every element writes
+// its value at run start + its rank.  Tiles are taken in increasing order from
+// tile_counter when given (a region-split batch: the pool is written range by range),
+// else strided over the grid.  Element words and values are loaded at the start of a tile,
+// so their loads overlap the reservations.
+template <int VB, int kThreads>
+__global__ void __launch_bounds__(kThreads) k_mv_place(TableDesc t, PoolDesc pd, TileRecord rec,
+                                                       const void* __restrict__ vals, uint64_t n,
+                                                       unsigned long long* tile_counter) {
+  using V = typename PoolT<VB>::T;
+  constexpr int kTile = Agg<kThreads>::kTile;
+  constexpr int kPer = kTile / kThreads;  // list entries and elements per thread
+  __shared__ unsigned long long s_b[kTile];  // run start of each distinct key (all ones: none)
+  __shared__ unsigned long long s_h[kTile];  // growth strategy: the key's handle
+  __shared__ uint32_t s_c[kTile];            // growth strategy: the key's count before the call
+  __shared__ unsigned long long s_tile, s_ntile;
+  const KsSlot* slots = static_cast<const KsSlot*>(t.slots);
+  V* pool = static_cast<V*>(pd.pool);
+  const V* vin = static_cast<const V*>(vals);
+  const uint64_t ntiles = (n + kTile - 1) / kTile;
+  uint64_t tile = blockIdx.x;
+  if (tile_counter != nullptr) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1ull);
+    __syncthreads();
+    tile = s_tile;
+  }
+  while (tile < ntiles) {
+    uint32_t ew[kPer];
+    V v[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint64_t e = tile * kTile + static_cast<uint64_t>(k) * kThreads + threadIdx.x;
+      ew[k] = e < n ? rec.elem[e] : ~0u;
+      v[k] = e < n ? vin[e] : V(0);
+    }
+    const uint32_t len = rec.len[tile];
+    uint2 r[kPer];
+    uint32_t old[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint32_t i = static_cast<uint32_t>(k) * kThreads + threadIdx.x;
+      r[k] = i < len ? rec.list[tile * kTile + i] : make_uint2(~0u, 0u);
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) old[k] = r[k].x != ~0u ? atomicAdd(pd.pending + r[k].x, r[k].y) : kPoison;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint32_t i = static_cast<uint32_t>(k) * kThreads + threadIdx.x;
+      if (i >= len) continue;
+      if (old[k] & kPoison) {  // no stored key, or no bucket was allocated for it
+        s_b[i] = ~0ull;
+        continue;
+      }
+      const uint64_t handle = slots[r[k].x].v;
+      if (pd.growth == kGrowExact) {
+        s_b[i] = h_offset(handle) + (h_prev(handle) ? Hdr<VB>::kElems : 0) + old[k];
+      } else {
+        // growth: `old` is the value number of the run's first value; the handle and the
+        // key's count before the call give each value's place
+        s_b[i] = old[k];
+        s_h[i] = handle;
+        s_c[i] = pd.base[r[k].x];
+      }
+    }
+    if (tile_counter != nullptr && threadIdx.x == 0) s_ntile = atomicAdd(tile_counter, 1ull);
+    __syncthreads();
+    const uint64_t next = tile_counter != nullptr ? s_ntile : tile + gridDim.x;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      if (ew[k] == ~0u) continue;
+      const uint32_t i = ew[k] >> 16, rank = ew[k] & 0xffffu;
+      const unsigned long long b = s_b[i];
+      if (b == ~0ull) continue;
+      if (pd.growth == kGrowExact)
+        pool[b + rank] = v[k];
+      else
+        pool[g_value_index<VB>(pd, s_h[i], s_c[i], b + rank)] = v[k];
+    }
+    __syncthreads();
+    tile = next;
+  }
 }
 
 // ---- pass 2: bucket allocation ----------------------------------------------------------
