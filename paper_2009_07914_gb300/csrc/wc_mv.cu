@@ -1,4 +1,4 @@
-// Multi-value bulk insert: dispatch of the count / allocate / scatter passes.
+// Multi-value bulk insert: dispatch of the count / allocate / place passes.
 #include <algorithm>
 
 #include "wc_launch.cuh"
@@ -16,9 +16,9 @@ cudaError_t insert_passes(const wc_table* t, const void* keys, const void* vals,
   const TableDesc d = desc_of(t);
   const PoolDesc pd = pool_of(t);
   const KIn* k = static_cast<const KIn*>(keys);
-  auto count = k_mv_aggregate<KIn, VB, W, false, kThreads>;
+  auto count = k_mv_aggregate<KIn, W, kThreads>;
   auto place = k_mv_place<VB, kThreads>;
-  const size_t smem_c = A::smem_bytes(false, sizeof(KIn));
+  const size_t smem_c = A::smem_bytes(sizeof(KIn));
   static bool attr_done = false;
   if (!attr_done) {
     cudaFuncSetAttribute(count, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_c));
@@ -60,7 +60,7 @@ cudaError_t insert_passes(const wc_table* t, const void* keys, const void* vals,
   const unsigned g_p = static_cast<unsigned>(std::min<uint64_t>(ntiles, static_cast<uint64_t>(bps_p) * t->sm_count));
   e = cudaMemsetAsync(pd.pending, 0, t->capacity * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  e = launch_k(t, count, g_c, kThreads, smem_c, s, d, pd, k, vals, n, counters, rec);
+  e = launch_k(t, count, g_c, kThreads, smem_c, s, d, pd, k, n, counters, rec);
   if (e != cudaSuccess) return e;
   const uint64_t per_block = static_cast<uint64_t>(kAllocThreads) * kAllocItems;
   const unsigned g_a = static_cast<unsigned>((t->capacity + per_block - 1) / per_block);

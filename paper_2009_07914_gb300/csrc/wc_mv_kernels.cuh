@@ -12,11 +12,14 @@
 // Bulk insert = three passes over the batch (plus a clear of the per-slot counters):
 //   1. count: aggregate the batch tile by tile in shared memory (a hot key costs one
 //      global probe and one atomic per tile instead of one per occurrence), insert each
-//      distinct key into the key store, add its tile count to pending[slot];
+//      distinct key into the key store, add its tile count to pending[slot], and record
+//      per tile the distinct keys' slots and counts and per element its key's list
+//      position and its rank among the tile's copies of the key (TileRecord);
 //   2. allocate: one pass over the key store reserves every key's bucket from the pool
 //      (block-aggregated bump allocation) and rewrites its handle;
-//   3. scatter: aggregate again, reserve each tile's run inside the key's bucket with one
-//      atomic on pending[slot], and write the values.
+//   3. place: from the record, reserve each tile's run inside each key's bucket with one
+//      atomic on pending[slot] and write every value at run start + rank (no key is
+//      hashed or looked up again).
 // Within a bucket the order of values is unspecified (the paper's multi-value semantics
 // do not order values).
 #pragma once
@@ -147,14 +150,12 @@ template <int kThreads>
 struct Agg {
   static constexpr int kTile = kThreads * kAggPerThread;  // batch elements per tile
   static constexpr int kSlots = 2 * kTile;
-  // the tile's hash table (keys, counts, list; bases in the scatter pass; key-store slots
-  // and list positions in the counting pass), then the next tile's input keys (key_bytes
-  // each), copied in while the current tile is processed
-  static constexpr size_t table_bytes(bool scatter) {
-    return (scatter ? 2 : 1) * kSlots * sizeof(unsigned long long) + kSlots * sizeof(uint32_t) +
-           kSlots * sizeof(unsigned short) + (scatter ? 0 : kSlots * (sizeof(uint32_t) + sizeof(unsigned short)));
+  // the tile's hash table (keys, counts, list, key-store slots, list positions), then the
+  // next tile's input keys (key_bytes each), copied in while the current tile is processed
+  static constexpr size_t table_bytes() {
+    return kSlots * (sizeof(unsigned long long) + 2 * sizeof(uint32_t) + 2 * sizeof(unsigned short));
   }
-  static constexpr size_t smem_bytes(bool scatter, size_t key_bytes) { return table_bytes(scatter) + kTile * key_bytes; }
+  static constexpr size_t smem_bytes(size_t key_bytes) { return table_bytes() + kTile * key_bytes; }
 };
 
 // What the counting pass leaves for the placing pass (k_mv_place), per tile of the batch:
@@ -207,16 +208,15 @@ __device__ __forceinline__ uint32_t block_exclusive_u32(uint32_t x, uint32_t& to
 }
 
 // The global phase of one tile: every distinct key of the tile (s_list[0..len)) is found
-// in -- or, in the counting pass, inserted into -- the key store with one lane per key.
+// in or inserted into the key store with one lane per key.
 // The loop is warp-uniform: each trip loads one window for every lane holding a key,
 // so a warp's window loads are in flight together, and a lane that finishes takes the
-// next key of the list.  Counting pass: pending[slot] += the key's tile count, and
-// s_ks[e] = slot (when s_ks is given).  Scatter pass: reserve the key's run in its bucket
-// (s_base[e] = first pool index, or all ones).
-template <int W, bool kScatter, int VB>
+// next key of the list.  pending[slot] += the key's tile count, and s_ks[e] = slot (it
+// stays all ones for a key the key store could not take).
+template <int W>
 __device__ __forceinline__ void ks_global_phase(const TableDesc& t, const PoolDesc& pd,
                                                 unsigned long long* s_key, uint32_t* s_cnt,
-                                                unsigned long long* s_base, uint32_t* s_ks,
+                                                uint32_t* s_ks,
                                                 const unsigned short* s_list,
                                                 uint32_t len, uint32_t* s_next, uint32_t& flags,
                                                 long long& created) {
@@ -256,11 +256,9 @@ __device__ __forceinline__ void ks_global_phase(const TableDesc& t, const PoolDe
       uint32_t mm, me, mt;
       classify<KsL, W>(sl, k, mm, me, mt);
       int64_t slot = -1;
-      uint64_t handle = 0;
       if (mm) {
         slot = static_cast<int64_t>(b + __ffs(mm) - 1);
-        handle = pick<KsL, W>(sl, __ffs(mm) - 1).v;
-      } else if constexpr (!kScatter) {
+      } else {
         const bool last = j + 1 >= t.p;
         if (me || last) {
           if (have_t) {
@@ -292,55 +290,32 @@ __device__ __forceinline__ void ks_global_phase(const TableDesc& t, const PoolDe
           ++j;
           w = probe_next(w, step, t.p);
         }
-      } else {
-        if (me || ++j >= t.p) {
-          s_base[e] = ~0ull;  // absent: the counting pass could not store it
-          act = false;
-        } else {
-          w = probe_next(w, step, t.p);
-        }
       }
       if (slot >= 0) {
-        if constexpr (!kScatter) {
-          atomicAdd(pd.pending + slot, s_cnt[e]);
-          if (s_ks != nullptr) s_ks[e] = static_cast<uint32_t>(slot);
-        } else {
-          const uint32_t old = atomicAdd(pd.pending + slot, s_cnt[e]);
-          if (pd.growth == kGrowExact) {
-            s_base[e] = (old & kPoison) ? ~0ull : h_offset(handle) + (h_prev(handle) ? Hdr<VB>::kElems : 0) + old;
-          } else {
-            // growth: `old` is the value number of the run's first value; keep the handle
-            // and the key's count before the call for the per-value placement
-            s_base[e] = (old & kPoison) ? ~0ull : old;
-            s_key[e] = handle;
-            s_cnt[e] = pd.base[slot];
-          }
-        }
+        atomicAdd(pd.pending + slot, s_cnt[e]);
+        s_ks[e] = static_cast<uint32_t>(slot);
         act = false;
       }
     }
   }
 }
 
-template <class KIn, int VB, int W, bool kScatter, int kAggThreads>
+template <class KIn, int W, int kAggThreads>
 // tile_counter != nullptr: blocks take tiles in increasing order from it (the batch is
 // sorted by key-store region, so the active tiles touch one region of the key store and
 // one range of the value pool at a time); otherwise tiles are strided over the grid.
 __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolDesc pd, const KIn* __restrict__ keys,
-                                                              const void* __restrict__ vals, uint64_t n,
-                                                              unsigned long long* tile_counter, TileRecord rec) {
-  using V = typename PoolT<VB>::T;
+                                                              uint64_t n, unsigned long long* tile_counter,
+                                                              TileRecord rec) {
   constexpr int kAggTile = Agg<kAggThreads>::kTile;
   constexpr int kAggSlots = Agg<kAggThreads>::kSlots;
-  extern __shared__ unsigned long long agg_smem[];  // Agg<kAggThreads>::smem_bytes(kScatter, sizeof(KIn)) bytes
+  extern __shared__ unsigned long long agg_smem[];  // Agg<kAggThreads>::smem_bytes(sizeof(KIn)) bytes
   unsigned long long* s_key = agg_smem;
-  unsigned long long* s_base = agg_smem + kAggSlots;
-  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(agg_smem + (kScatter ? 2 : 1) * kAggSlots);
-  unsigned short* s_list = reinterpret_cast<unsigned short*>(s_cnt + kAggSlots);
-  // counting pass with a record: key-store slot and list position of every table entry
-  uint32_t* s_ks = (!kScatter && rec.elem != nullptr) ? reinterpret_cast<uint32_t*>(s_list + kAggSlots) : nullptr;
-  unsigned short* s_pos = reinterpret_cast<unsigned short*>(reinterpret_cast<uint32_t*>(s_list + kAggSlots) + kAggSlots);
-  KIn* s_in = reinterpret_cast<KIn*>(reinterpret_cast<char*>(agg_smem) + Agg<kAggThreads>::table_bytes(kScatter));
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(agg_smem + kAggSlots);
+  uint32_t* s_ks = s_cnt + kAggSlots;  // key-store slot of every table entry
+  unsigned short* s_list = reinterpret_cast<unsigned short*>(s_ks + kAggSlots);
+  unsigned short* s_pos = s_list + kAggSlots;  // list position of every table entry
+  KIn* s_in = reinterpret_cast<KIn*>(reinterpret_cast<char*>(agg_smem) + Agg<kAggThreads>::table_bytes());
   __shared__ uint32_t s_wsum[kAggThreads / 32];
   __shared__ uint32_t s_len, s_next;
   const int lane = threadIdx.x & 31;
@@ -371,19 +346,16 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
     for (int e = threadIdx.x; e < kAggSlots; e += kAggThreads) {
       s_key[e] = 0ull;
       s_cnt[e] = 0u;
-      if (s_ks != nullptr) s_ks[e] = ~0u;
+      s_ks[e] = ~0u;
     }
     cp_async_wait_all();
     __syncthreads();
     if (tile_counter != nullptr) next = s_ntile;
     KIn kin_t[kAggPerThread];
-    V vin_t[kAggPerThread];
 #pragma unroll
     for (int k = 0; k < kAggPerThread; ++k) {
       const uint64_t e = tile * kAggTile + static_cast<uint64_t>(k) * kAggThreads + threadIdx.x;
       kin_t[k] = e < n ? s_in[k * kAggThreads + threadIdx.x] : KIn(0);
-      // values are consumed at the end of the tile: their loads overlap the tile's work
-      if constexpr (kScatter) vin_t[k] = e < n ? static_cast<const V*>(vals)[e] : V(0);
     }
     __syncthreads();  // s_in is free again
     if (next < ntiles) prefetch(next);
@@ -427,7 +399,7 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
 #pragma unroll
       for (int i = 0; i < kPer; ++i)
         if (s_key[e0 + i] != 0ull) {
-          if (s_ks != nullptr) s_pos[e0 + i] = static_cast<unsigned short>(pos);
+          s_pos[e0 + i] = static_cast<unsigned short>(pos);
           s_list[pos++] = static_cast<unsigned short>(e0 + i);
         }
       if (threadIdx.x == 0) {
@@ -436,7 +408,7 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
       }
       __syncthreads();
     }
-    if (s_ks != nullptr) {
+    {
       // the record of this tile for the placing pass: element words now (the list
       // positions are known), the (slot, count) list after the key-store phase
 #pragma unroll
@@ -446,8 +418,8 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
           rec.elem[e] = my_slot[k] < 0 ? ~0u : (static_cast<uint32_t>(s_pos[my_slot[k]]) << 16) | my_rank[k];
       }
     }
-    ks_global_phase<W, kScatter, VB>(t, pd, s_key, s_cnt, s_base, s_ks, s_list, s_len, &s_next, flags, created);
-    if (s_ks != nullptr) {
+    ks_global_phase<W>(t, pd, s_key, s_cnt, s_ks, s_list, s_len, &s_next, flags, created);
+    {
       __syncthreads();
       const uint32_t len = s_len;
       for (uint32_t i = threadIdx.x; i < len; i += kAggThreads) {
@@ -456,26 +428,12 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
       }
       if (threadIdx.x == 0) rec.len[tile] = len;
     }
-    if constexpr (kScatter) {
-      __syncthreads();
-      V* pool = static_cast<V*>(pd.pool);
-#pragma unroll
-      for (int k = 0; k < kAggPerThread; ++k) {
-        if (my_slot[k] < 0) continue;
-        const unsigned long long b = s_base[my_slot[k]];
-        if (b == ~0ull) continue;
-        if (pd.growth == kGrowExact)
-          pool[b + my_rank[k]] = vin_t[k];
-        else
-          pool[g_value_index<VB>(pd, s_key[my_slot[k]], s_cnt[my_slot[k]], b + my_rank[k])] = vin_t[k];
-      }
-    }
     __syncthreads();
     tile = next;
   }
   cp_async_wait_all();
   flush_flags(t.status, flags);
-  if constexpr (!kScatter) flush_delta(t.nkeys, created);
+  flush_delta(t.nkeys, created);
 }
 
 // ---- pass 3: placing the values ------------------------------------------------------------
