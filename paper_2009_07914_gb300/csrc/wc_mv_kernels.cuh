@@ -387,20 +387,26 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
       my_rank[k] = base + __popc(peers & ((1u << lane) - 1u));
     }
     __syncthreads();
-    // compact the tile's distinct keys into a list, then probe them warp-uniformly
+    // compact the tile's distinct keys into a list, then probe them warp-uniformly; a
+    // thread takes every kAggThreads-th table entry, so a warp reads consecutive entries
+    // (the list order is of no consequence)
     {
       constexpr int kPer = kAggSlots / kAggThreads;
-      const int e0 = threadIdx.x * kPer;
       uint32_t c = 0;
+      bool used[kPer];
 #pragma unroll
-      for (int i = 0; i < kPer; ++i) c += s_key[e0 + i] != 0ull;
+      for (int i = 0; i < kPer; ++i) {
+        used[i] = s_key[i * kAggThreads + threadIdx.x] != 0ull;
+        c += used[i];
+      }
       uint32_t total = 0;
       uint32_t pos = block_exclusive_u32<kAggThreads>(c, total, s_wsum);
 #pragma unroll
       for (int i = 0; i < kPer; ++i)
-        if (s_key[e0 + i] != 0ull) {
-          s_pos[e0 + i] = static_cast<unsigned short>(pos);
-          s_list[pos++] = static_cast<unsigned short>(e0 + i);
+        if (used[i]) {
+          const int e = i * kAggThreads + threadIdx.x;
+          s_pos[e] = static_cast<unsigned short>(pos);
+          s_list[pos++] = static_cast<unsigned short>(e);
         }
       if (threadIdx.x == 0) {
         s_len = total;
@@ -482,8 +488,16 @@ __global__ void __launch_bounds__(kThreads) k_mv_place(TableDesc t, PoolDesc pd,
       const uint32_t i = static_cast<uint32_t>(k) * kThreads + threadIdx.x;
       r[k] = i < len ? rec.list[tile * kTile + i] : make_uint2(~0u, 0u);
     }
+    // the reservations and the handle loads of all the thread's keys go out together
+    uint64_t handle[kPer];
+    uint32_t c0[kPer];
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) old[k] = r[k].x != ~0u ? atomicAdd(pd.pending + r[k].x, r[k].y) : kPoison;
+    for (int k = 0; k < kPer; ++k) {
+      const bool ok = r[k].x != ~0u;
+      old[k] = ok ? atomicAdd(pd.pending + r[k].x, r[k].y) : kPoison;
+      handle[k] = ok ? slots[r[k].x].v : 0ull;
+      c0[k] = ok && pd.growth != kGrowExact ? pd.base[r[k].x] : 0u;
+    }
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const uint32_t i = static_cast<uint32_t>(k) * kThreads + threadIdx.x;
@@ -492,15 +506,14 @@ __global__ void __launch_bounds__(kThreads) k_mv_place(TableDesc t, PoolDesc pd,
         s_b[i] = ~0ull;
         continue;
       }
-      const uint64_t handle = slots[r[k].x].v;
       if (pd.growth == kGrowExact) {
-        s_b[i] = h_offset(handle) + (h_prev(handle) ? Hdr<VB>::kElems : 0) + old[k];
+        s_b[i] = h_offset(handle[k]) + (h_prev(handle[k]) ? Hdr<VB>::kElems : 0) + old[k];
       } else {
         // growth: `old` is the value number of the run's first value; the handle and the
         // key's count before the call give each value's place
         s_b[i] = old[k];
-        s_h[i] = handle;
-        s_c[i] = pd.base[r[k].x];
+        s_h[i] = handle[k];
+        s_c[i] = c0[k];
       }
     }
     if (tile_counter != nullptr && threadIdx.x == 0) s_ntile = atomicAdd(tile_counter, 1ull);
