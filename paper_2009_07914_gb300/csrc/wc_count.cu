@@ -79,11 +79,12 @@ __global__ void __launch_bounds__(kCntThreads) k_count_aggregate(const K* __rest
       atomicAdd(s_sum + h, wt);
     }
     __syncthreads();
-    // compact: thread t owns slots [t * per, (t + 1) * per)
+    // compact: thread t owns slots t, t + kCntThreads, ... (a warp reads consecutive slots;
+    // the order of the aggregated keys is of no consequence)
     constexpr int per = kCntSlots / kCntThreads;
     uint32_t c = 0;
 #pragma unroll
-    for (int q = 0; q < per; ++q) c += s_key[threadIdx.x * per + q] != K(0);
+    for (int q = 0; q < per; ++q) c += s_key[q * kCntThreads + threadIdx.x] != K(0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t inc = c;
 #pragma unroll
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(kCntThreads) k_count_aggregate(const K* __rest
     }
 #pragma unroll
     for (int q = 0; q < per; ++q) {
-      const int e = threadIdx.x * per + q;
+      const int e = q * kCntThreads + threadIdx.x;
       if (s_key[e] != K(0)) {
         ok[t0 + pos] = s_key[e];
         ov[t0 + pos] = s_sum[e];
