@@ -153,7 +153,8 @@ struct Agg {
   // the tile's hash table (keys, counts, list, key-store slots, list positions), then the
   // next tile's input keys (key_bytes each), copied in while the current tile is processed
   static constexpr size_t table_bytes() {
-    return kSlots * (sizeof(unsigned long long) + 2 * sizeof(uint32_t) + 2 * sizeof(unsigned short));
+    return kSlots * (sizeof(unsigned long long) + sizeof(uint32_t) + sizeof(unsigned short)) +
+           kTile * (sizeof(uint32_t) + sizeof(unsigned short));
   }
   static constexpr size_t smem_bytes(size_t key_bytes) { return table_bytes() + kTile * key_bytes; }
 };
@@ -211,8 +212,8 @@ __device__ __forceinline__ uint32_t block_exclusive_u32(uint32_t x, uint32_t& to
 // in or inserted into the key store with one lane per key.
 // The loop is warp-uniform: each trip loads one window for every lane holding a key,
 // so a warp's window loads are in flight together, and a lane that finishes takes the
-// next key of the list.  pending[slot] += the key's tile count, and s_ks[e] = slot (it
-// stays all ones for a key the key store could not take).
+// next key of the list.  pending[slot] += the key's tile count, and s_ks[i] = slot for
+// the key at list position i (it stays all ones for a key the key store could not take).
 template <int W>
 __device__ __forceinline__ void ks_global_phase(const TableDesc& t, const PoolDesc& pd,
                                                 unsigned long long* s_key, uint32_t* s_cnt,
@@ -223,7 +224,7 @@ __device__ __forceinline__ void ks_global_phase(const TableDesc& t, const PoolDe
   KsSlot* slots = static_cast<KsSlot*>(t.slots);
   const int lane = threadIdx.x & 31;
   bool act = false, more = true;
-  uint32_t e = 0, w = 0, step = 0, j = 0;
+  uint32_t e = 0, w = 0, step = 0, j = 0, li = 0;
   unsigned long long k = 0;
   bool have_t = false;
   uint64_t t_slot = 0;
@@ -236,6 +237,7 @@ __device__ __forceinline__ void ks_global_phase(const TableDesc& t, const PoolDe
       base = __shfl_sync(kFull, base, 0);
       const uint32_t mine = base + __popc(idle & ((1u << lane) - 1u));
       if (!act && mine < len) {
+        li = mine;
         e = s_list[mine];
         k = s_key[e];
         act = true;
@@ -293,7 +295,7 @@ __device__ __forceinline__ void ks_global_phase(const TableDesc& t, const PoolDe
       }
       if (slot >= 0) {
         atomicAdd(pd.pending + slot, s_cnt[e]);
-        s_ks[e] = static_cast<uint32_t>(slot);
+        s_ks[li] = static_cast<uint32_t>(slot);
         act = false;
       }
     }
@@ -304,7 +306,7 @@ template <class KIn, int W, int kAggThreads>
 // tile_counter != nullptr: blocks take tiles in increasing order from it (the batch is
 // sorted by key-store region, so the active tiles touch one region of the key store and
 // one range of the value pool at a time); otherwise tiles are strided over the grid.
-__global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolDesc pd, const KIn* __restrict__ keys,
+__global__ void __launch_bounds__(kAggThreads, W <= 4 ? 1280 / kAggThreads : 1) k_mv_aggregate(TableDesc t, PoolDesc pd, const KIn* __restrict__ keys,
                                                               uint64_t n, unsigned long long* tile_counter,
                                                               TileRecord rec) {
   constexpr int kAggTile = Agg<kAggThreads>::kTile;
@@ -312,9 +314,9 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
   extern __shared__ unsigned long long agg_smem[];  // Agg<kAggThreads>::smem_bytes(sizeof(KIn)) bytes
   unsigned long long* s_key = agg_smem;
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(agg_smem + kAggSlots);
-  uint32_t* s_ks = s_cnt + kAggSlots;  // key-store slot of every table entry
-  unsigned short* s_list = reinterpret_cast<unsigned short*>(s_ks + kAggSlots);
-  unsigned short* s_pos = s_list + kAggSlots;  // list position of every table entry
+  uint32_t* s_ks = s_cnt + kAggSlots;  // key-store slot of every list entry (kAggTile)
+  unsigned short* s_pos = reinterpret_cast<unsigned short*>(s_ks + kAggTile);  // list position of every table entry
+  unsigned short* s_list = s_pos + kAggSlots;  // the tile's distinct keys (table entries), kAggTile
   KIn* s_in = reinterpret_cast<KIn*>(reinterpret_cast<char*>(agg_smem) + Agg<kAggThreads>::table_bytes());
   __shared__ uint32_t s_wsum[kAggThreads / 32];
   __shared__ uint32_t s_len, s_next;
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
     for (int e = threadIdx.x; e < kAggSlots; e += kAggThreads) {
       s_key[e] = 0ull;
       s_cnt[e] = 0u;
-      s_ks[e] = ~0u;
+      if (e < kAggTile) s_ks[e] = ~0u;
     }
     cp_async_wait_all();
     __syncthreads();
@@ -429,8 +431,7 @@ __global__ void __launch_bounds__(kAggThreads) k_mv_aggregate(TableDesc t, PoolD
       __syncthreads();
       const uint32_t len = s_len;
       for (uint32_t i = threadIdx.x; i < len; i += kAggThreads) {
-        const int e = s_list[i];
-        rec.list[tile * kAggTile + i] = make_uint2(s_ks[e], s_cnt[e]);
+        rec.list[tile * kAggTile + i] = make_uint2(s_ks[i], s_cnt[s_list[i]]);
       }
       if (threadIdx.x == 0) rec.len[tile] = len;
     }
