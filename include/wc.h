@@ -247,8 +247,8 @@ wc_status wc_table_clear(wc_table* t, void* stream);
 
 wc_status wc_table_get_info(const wc_table* t, wc_table_info* h_out);
 
-/* Override the launch shape of one operation class (see wc_launch); the autotuner in
- * the Python package calls this.  group_size must divide W and give 8..64 bytes per lane
+/* Override the launch shape of one operation class (see wc_launch); the autotuners
+ * (wc_tune.h and the Python package's) call this.  group_size must divide W and give 8..64 bytes per lane
  * (or be 1..32 with W / group_size slots per lane <= 8).  Host only. */
 wc_status wc_table_set_launch(wc_table* t, int32_t op, const wc_launch* launch);
 wc_status wc_table_get_launch(const wc_table* t, int32_t op, wc_launch* h_out);
@@ -265,7 +265,10 @@ wc_status wc_table_get_launch(const wc_table* t, int32_t op, wc_launch* h_out);
  * batch, the stored value is one of that batch's values for it.  Multi-value: every
  * pair is appended (Sec. IV-B4); values of one call are stored contiguously per key in
  * the value pool (a bucket of exactly that call's count, linked to the key's earlier
- * buckets, Sec. IV-C with lambda = 1, s0 = count).  n < 2^32. */
+ * buckets, Sec. IV-C with lambda = 1, s0 = count).  A multi-value insert keeps per-tile
+ * records of its counting pass in the table's scratch (12 bytes per pair, plus the region
+ * split's key + value bytes per pair for batches of 2^20 or more into key stores over
+ * 64 MiB), grown on demand and held until wc_table_destroy.  n < 2^32. */
 wc_status wc_insert(wc_table* t, const void* d_keys, const void* d_values, uint64_t n,
                     void* stream);
 
