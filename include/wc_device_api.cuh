@@ -204,8 +204,9 @@ __device__ __forceinline__ bool overflow_clear(const wc_device_view& t, uint32_t
 }
 
 // kAdd: a counting table -- a stored key gets the value added to its count (no warning),
-// an absent one is stored with the value as its count.
-template <class K, int W, bool kAdd = false>
+// an absent one is stored with the value as its count.  kSize = false: a new key leaves
+// the table's size to the caller (see insert_uncounted).
+template <class K, int W, bool kAdd = false, bool kSize = true>
 __device__ uint32_t insert_w(const wc_device_view& t, K key, typename Slots<K>::V value) {
   using S = Slots<K>;
   using Word = typename S::Word;
@@ -270,7 +271,7 @@ __device__ uint32_t insert_w(const wc_device_view& t, K key, typename Slots<K>::
     w = probe_next(w, step, t.windows);
     ++j;
   }
-  add_size(t, 1);
+  if constexpr (kSize) add_size(t, 1);
   return 0;
 }
 
@@ -399,7 +400,7 @@ __device__ bool retrieve_group(const cooperative_groups::thread_block_tile<G>& g
   return false;
 }
 
-template <class K, int W, int G>
+template <class K, int W, int G, bool kSize = true>
 __device__ uint32_t insert_group(const cooperative_groups::thread_block_tile<G>& g, const wc_device_view& t, K key,
                                  typename Slots<K>::V value) {
   using Sl = Slots<K>;
@@ -471,7 +472,9 @@ __device__ uint32_t insert_group(const cooperative_groups::thread_block_tile<G>&
     w = probe_next(w, step, t.windows);
     ++j;
   }
-  if (r == 0) add_size(t, 1);
+  if constexpr (kSize) {
+    if (r == 0) add_size(t, 1);
+  }
   return 0;
 }
 
@@ -508,6 +511,21 @@ __device__ uint32_t insert(const wc_device_view& t, K key, typename Slots<K>::V 
     return WC_FLAG_INVALID_KEY;
   }
 #define WC_DEV_CALL(Wv) insert_w<K, Wv>(t, key, value)
+  WC_DEV_DISPATCH(K, WC_DEV_CALL)
+#undef WC_DEV_CALL
+}
+
+// insert, except that a new key does not update the table's size: it returns 0 for a new
+// key, and the caller adds the number of them with add_size(view, n) -- once per thread or
+// warp instead of once per element, which keeps a kernel that inserts many keys off the
+// one size counter.  The size is right once every such count has been added.
+template <class K>
+__device__ uint32_t insert_uncounted(const wc_device_view& t, K key, typename Slots<K>::V value) {
+  if (is_sentinel(key)) {
+    raise(t, WC_FLAG_INVALID_KEY);
+    return WC_FLAG_INVALID_KEY;
+  }
+#define WC_DEV_CALL(Wv) insert_w<K, Wv, false, false>(t, key, value)
   WC_DEV_DISPATCH(K, WC_DEV_CALL)
 #undef WC_DEV_CALL
 }

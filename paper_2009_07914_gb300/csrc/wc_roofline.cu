@@ -156,10 +156,13 @@ cudaError_t run(void* buf, const wc_rand_access_config& c, uint64_t* sink, cudaS
 template <int W>
 __global__ void __launch_bounds__(256) k_dev_insert(wc_device_view v, uint64_t n, uint32_t seed) {
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  long long added = 0;  // new keys of this thread, added to the size once at the end
   for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
     const uint32_t k = static_cast<uint32_t>(i * 2654435761ull) ^ seed;
-    if (!wc_dev::is_sentinel(k)) wc_dev::insert_w<uint32_t, W>(v, k, static_cast<uint32_t>(i));
+    if (!wc_dev::is_sentinel(k) && wc_dev::insert_w<uint32_t, W, false, false>(v, k, static_cast<uint32_t>(i)) == 0)
+      ++added;
   }
+  wc_dev::add_size(v, added);
 }
 
 template <int W>
@@ -197,11 +200,13 @@ __global__ void __launch_bounds__(256) k_dev_group(wc_device_view v, int mode, u
   const auto tile = cg::tiled_partition<G>(cg::this_thread_block());
   const uint64_t tiles = static_cast<uint64_t>(gridDim.x) * blockDim.x / G;
   unsigned long long acc = 0;
+  long long added = 0;  // new keys stored by this tile (its rank-0 thread), added once at the end
   for (uint64_t i = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / G; i < n; i += tiles) {
     const uint32_t k = static_cast<uint32_t>(i * 2654435761ull) ^ seed;
     if (wc_dev::is_sentinel(k)) continue;
     if (mode == 0) {
-      wc_dev::insert_group<uint32_t, W, G>(tile, v, k, static_cast<uint32_t>(i));
+      if (wc_dev::insert_group<uint32_t, W, G, false>(tile, v, k, static_cast<uint32_t>(i)) == 0 && tile.thread_rank() == 0)
+        ++added;
     } else {
       uint32_t x;
       if (wc_dev::retrieve_group<uint32_t, W, G>(tile, v, k, x) && tile.thread_rank() == 0) acc += x;
@@ -210,6 +215,8 @@ __global__ void __launch_bounds__(256) k_dev_group(wc_device_view v, int mode, u
   if (mode != 0) {
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(sink, acc);
+  } else {
+    wc_dev::add_size(v, added);
   }
 }
 

@@ -22,6 +22,21 @@ __global__ void k_insert(wc_device_view v, const K* keys, const K* vals, uint64_
   }
 }
 
+// Grid-stride inserts that count their new keys per thread and add them to the size once.
+template <class K>
+__global__ void k_insert_uncounted(wc_device_view v, const K* keys, const K* vals, uint64_t n, uint32_t* flags) {
+  long long added = 0;
+  uint32_t f = 0;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const uint32_t r = wc_dev::insert_uncounted<K>(v, keys[i], vals[i]);
+    if (r == 0) ++added;
+    f |= r;
+  }
+  wc_dev::add_size(v, added);
+  if (f) atomicOr(flags, f);
+}
+
 template <class K>
 __global__ void k_retrieve(wc_device_view v, const K* keys, uint64_t n, K* out, uint8_t* found) {
   const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -137,6 +152,17 @@ int wcu_insert(const wc_device_view* v, const void* keys, const void* vals, uint
   else
     k_insert<unsigned long long><<<grid(n), 256>>>(*v, static_cast<const unsigned long long*>(keys),
                                                   static_cast<const unsigned long long*>(vals), n, flags);
+  return static_cast<int>(cudaDeviceSynchronize());
+}
+
+int wcu_insert_uncounted(const wc_device_view* v, const void* keys, const void* vals, uint64_t n, uint32_t* flags) {
+  if (n == 0) return 0;
+  if (v->key_bytes == 4)
+    k_insert_uncounted<uint32_t><<<64, 256>>>(*v, static_cast<const uint32_t*>(keys), static_cast<const uint32_t*>(vals),
+                                             n, flags);
+  else
+    k_insert_uncounted<unsigned long long><<<64, 256>>>(*v, static_cast<const unsigned long long*>(keys),
+                                                       static_cast<const unsigned long long*>(vals), n, flags);
   return static_cast<int>(cudaDeviceSynchronize());
 }
 

@@ -38,6 +38,7 @@ def env(tmp_path_factory):
     vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
     V = ctypes.POINTER(wc._binding.WcDeviceView)
     lib.wcu_insert.argtypes = [V, vp, vp, u64, vp]
+    lib.wcu_insert_uncounted.argtypes = [V, vp, vp, u64, vp]
     lib.wcu_retrieve.argtypes = [V, vp, u64, vp, vp]
     lib.wcu_erase.argtypes = [V, vp, u64, vp]
     lib.wcu_fused_insert.argtypes = [V, u64, u32, vp]
@@ -467,3 +468,31 @@ def test_group_device_ops_match_the_oracle(env, kb, W, G, opt):
     r = oracle.check_slots(wc.api.wc_table_dump_slots(t.handle), info["windows"], info["window_width"],
                            info["slot_bytes"], SEED, True, wc.api.wc_table_dump_overflow_bits(t.handle) if opt else None)
     assert r["dups"] == 0 and r["unreachable"] == 0 and r["live"] == o.size()
+
+
+@pytest.mark.parametrize("kb", [4, 8])
+def test_uncounted_inserts_add_their_size_once(env, kb):
+    """insert_uncounted in a grid-stride kernel that adds its count of new keys to the size
+    once per thread: the same table, flags and size as the oracle's, duplicates and
+    sentinels included."""
+    wc, torch, lib = env
+    n = 40000
+    keys = wc_inputs.distinct_u32(31 + kb, n) if kb == 4 else wc_inputs.distinct_u64(31 + kb, n)
+    vals = (np.arange(n, dtype=np.uint64) * 7 + 3).astype(keys.dtype)
+    batch_k = np.concatenate([keys, keys[:3000], np.array([0], dtype=keys.dtype)])
+    batch_v = np.concatenate([vals, vals[:3000], np.array([1], dtype=keys.dtype)])
+    t = wc.SingleValueTable(kb, kb, min_capacity=int(n / 0.9), window_width=8 if kb == 4 else 4, seed=SEED,
+                            options=wc.WC_OPT_OVERFLOW_BITS)
+    v = wc.api.wc_table_device_view(t.handle)
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert lib.wcu_insert_uncounted(ctypes.byref(v), dev(torch, batch_k, kb).data_ptr(),
+                                    dev(torch, batch_v, kb).data_ptr(), batch_k.size, flags.data_ptr()) == 0
+    o = oracle.SingleValue(kb, kb)
+    of = o.insert(batch_k, batch_v)
+    assert int(flags.item()) == of
+    assert t.size() == o.size() == n
+    out, found, _ = t.retrieve(keys[3000:])
+    eo, ef, _ = o.retrieve(keys[3000:])
+    np.testing.assert_array_equal(found, ef)
+    np.testing.assert_array_equal(out, eo)
+    t.close()
