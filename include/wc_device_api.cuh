@@ -21,7 +21,11 @@
  * probing sequence window by window (W slots each) -- the paper's cooperative group of
  * one thread.  Status conditions (DUPLICATE_KEY, INVALID_KEY, PROBE_LIMIT) are returned
  * and also OR-ed into the table's status word; the pair count is updated with one atomic
- * per converged group of threads.
+ * per converged group of threads.  insert_group / retrieve_group spread one element over
+ * a tile of G threads (one window load per tile).  A kernel of many inserts or appends
+ * should use insert_uncounted / append_uncounted and add its counts once per thread
+ * (add_size, add_counts): the table's pair and key counters are single words, and one
+ * atomic on them per element (or per warp) bounds such a kernel.
  */
 #ifndef WC_DEVICE_API_CUH_
 #define WC_DEVICE_API_CUH_
@@ -834,8 +838,10 @@ __device__ __forceinline__ void add_keys(const wc_device_view& t, unsigned long 
 // the bulk calls), inserted with handle 0 (no bucket) when absent: the earliest empty or
 // tombstoned slot of the walk, claimed with one 128-bit CAS.  -1 with the flag set when
 // the key store is full.
+// new_keys != nullptr: a key it stores is counted there instead of in the table.
 template <int W>
-__device__ int64_t key_slot(const wc_device_view& t, unsigned long long key, uint32_t& flags) {
+__device__ int64_t key_slot(const wc_device_view& t, unsigned long long key, uint32_t& flags,
+                            unsigned long long* new_keys = nullptr) {
   using S = Slots<unsigned long long>;
   using Word = typename S::Word;
   uint32_t w0, step;
@@ -861,7 +867,8 @@ __device__ int64_t key_slot(const wc_device_view& t, unsigned long long key, uin
     if (empty || j + 1 == t.windows) {
       if (have_t) {
         if (S::cas(t.slots, t_slot, t_word, key, 0ull)) {
-          add_keys(t, 1ull);
+          if (new_keys) ++*new_keys;
+          else add_keys(t, 1ull);
           return static_cast<int64_t>(t_slot);
         }
         have_t = false;  // the tombstone was taken: walk again from the start
@@ -878,7 +885,8 @@ __device__ int64_t key_slot(const wc_device_view& t, unsigned long long key, uin
       for (int q = 1; q < W; ++q)
         if (q == free_q) fw = win.slot(q);
       if (S::cas(t.slots, base + free_q, fw, key, 0ull)) {
-        add_keys(t, 1ull);
+        if (new_keys) ++*new_keys;
+        else add_keys(t, 1ull);
         return static_cast<int64_t>(base + free_q);
       }
       continue;  // the slot was taken (maybe by this key): read the window again
@@ -911,10 +919,16 @@ __device__ __forceinline__ void put_value(const wc_device_view& t, uint64_t star
   put<V>(t, start + (b > 0 ? hdr : 0) + (c - cum_size(t, b - 1)), value);
 }
 
+// Counts of appends that leave the table's counters to their caller (append_uncounted).
+struct Counts {
+  unsigned long long values = 0, keys = 0;
+};
+
+// counts != nullptr: the appended value and a new key are counted there, not in the table.
 template <int W, class V>
-__device__ uint32_t append_w(const wc_device_view& t, unsigned long long key, V value) {
+__device__ uint32_t append_w(const wc_device_view& t, unsigned long long key, V value, Counts* counts = nullptr) {
   uint32_t flags = 0;
-  const int64_t slot = key_slot<W>(t, key, flags);
+  const int64_t slot = key_slot<W>(t, key, flags, counts ? &counts->keys : nullptr);
   if (slot < 0) {
     atomicOr(t.status, flags);
     return flags;
@@ -936,7 +950,8 @@ __device__ uint32_t append_w(const wc_device_view& t, unsigned long long key, V 
       // room in the newest bucket: take value number c
       if (atomicCAS(handle, h, h + 1) == h) {
         put_value<V>(t, offset(h), newest, c, value);
-        add_size(t, 1);
+        if (counts) ++counts->values;
+        else add_size(t, 1);
         return 0;
       }
     } else if (!blocked) {
@@ -956,7 +971,8 @@ __device__ uint32_t append_w(const wc_device_view& t, unsigned long long key, V 
         }
         put_value<V>(t, off, b, c, value);
         store_release(handle, make(off, c + 1, b > 0));
-        add_size(t, 1);
+        if (counts) ++counts->values;
+        else add_size(t, 1);
         return 0;
       }
     } else {
@@ -1002,6 +1018,28 @@ __device__ uint32_t append(const wc_device_view& t, K key, V value) {
     case 4: return bl::append_w<4, V>(t, k, value);
     default: return bl::append_w<8, V>(t, k, value);
   }
+}
+
+// append, except that the table's pair and key counters are left to the caller: the value
+// and a new key are counted in c, and add_counts(view, c) adds them -- once per thread
+// instead of once per element, which keeps a kernel of many appends off the two counters.
+template <class K, class V>
+__device__ uint32_t append_uncounted(const wc_device_view& t, K key, V value, bl::Counts& c) {
+  if (is_sentinel(key)) {
+    atomicOr(t.status, static_cast<uint32_t>(WC_FLAG_INVALID_KEY));
+    return WC_FLAG_INVALID_KEY;
+  }
+  const unsigned long long k = static_cast<unsigned long long>(key);
+  switch (t.window_width) {
+    case 2: return bl::append_w<2, V>(t, k, value, &c);
+    case 4: return bl::append_w<4, V>(t, k, value, &c);
+    default: return bl::append_w<8, V>(t, k, value, &c);
+  }
+}
+
+__device__ __forceinline__ void add_counts(const wc_device_view& t, const bl::Counts& c) {
+  add_size(t, static_cast<long long>(c.values));
+  bl::add_keys(t, c.keys);
 }
 
 // ---- higher-order bulk calls ----------------------------------------------------------

@@ -226,8 +226,10 @@ template <class K, class V>
 __global__ void __launch_bounds__(256) k_dev_append(wc_device_view v, const K* __restrict__ keys,
                                                     const V* __restrict__ vals, uint64_t n) {
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  wc_dev::bl::Counts c;  // the thread's appended values and new keys, added once at the end
   for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
-    wc_dev::append<K, V>(v, keys[i], vals[i]);
+    wc_dev::append_uncounted<K, V>(v, keys[i], vals[i], c);
+  wc_dev::add_counts(v, c);
 }
 
 }  // namespace

@@ -63,6 +63,18 @@ __global__ void k_fused_insert(wc_device_view v, uint64_t n, uint32_t seed, uint
 }
 
 // Per-element appends to a bucket multi-value table, all in one launch (concurrent).
+// Grid-stride appends that count values and new keys per thread and add them once.
+template <class K, class V>
+__global__ void k_mv_append_uncounted(wc_device_view v, const K* keys, const V* vals, uint64_t n, uint32_t* flags) {
+  wc_dev::bl::Counts c;
+  uint32_t f = 0;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+    f |= wc_dev::append_uncounted<K, V>(v, keys[i], vals[i], c);
+  wc_dev::add_counts(v, c);
+  if (f) atomicOr(flags, f);
+}
+
 template <class K, class V>
 __global__ void k_mv_append(wc_device_view v, const K* keys, const V* vals, uint64_t n, uint32_t* flags) {
   const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -200,6 +212,23 @@ int wcu_mv_append(const wc_device_view* v, const void* keys, const void* vals, u
   else
     k_mv_append<uint32_t, unsigned long long><<<grid(n), 256>>>(*v, static_cast<const uint32_t*>(keys),
                                                                 static_cast<const unsigned long long*>(vals), n, flags);
+  return static_cast<int>(cudaDeviceSynchronize());
+}
+
+int wcu_mv_append_uncounted(const wc_device_view* v, const void* keys, const void* vals, uint64_t n, uint32_t* flags) {
+  if (n == 0) return 0;
+  if (v->key_bytes == 4 && v->value_bytes == 4)
+    k_mv_append_uncounted<uint32_t, uint32_t><<<128, 256>>>(*v, static_cast<const uint32_t*>(keys),
+                                                           static_cast<const uint32_t*>(vals), n, flags);
+  else if (v->key_bytes == 8 && v->value_bytes == 4)
+    k_mv_append_uncounted<unsigned long long, uint32_t><<<128, 256>>>(
+        *v, static_cast<const unsigned long long*>(keys), static_cast<const uint32_t*>(vals), n, flags);
+  else if (v->key_bytes == 8)
+    k_mv_append_uncounted<unsigned long long, unsigned long long><<<128, 256>>>(
+        *v, static_cast<const unsigned long long*>(keys), static_cast<const unsigned long long*>(vals), n, flags);
+  else
+    k_mv_append_uncounted<uint32_t, unsigned long long><<<128, 256>>>(
+        *v, static_cast<const uint32_t*>(keys), static_cast<const unsigned long long*>(vals), n, flags);
   return static_cast<int>(cudaDeviceSynchronize());
 }
 

@@ -45,6 +45,7 @@ def env(tmp_path_factory):
     lib.wcu_for_each.argtypes = [V, vp, u64, vp, vp]
     lib.wcu_for_all.argtypes = [V, vp]
     lib.wcu_mv_append.argtypes = [V, vp, vp, u64, vp]
+    lib.wcu_mv_append_uncounted.argtypes = [V, vp, vp, u64, vp]
     lib.wcu_set_op.argtypes = [V, ctypes.c_int, vp, u64, vp, vp]
     lib.wcu_group_op.argtypes = [V, ctypes.c_int, ctypes.c_int, vp, vp, u64, vp, vp, vp]
     lib.wcu_count_add.argtypes = [V, vp, vp, u64, vp]
@@ -217,11 +218,13 @@ def _mv_check(t, o, queries):
 
 @pytest.mark.parametrize("kb,vb", [(4, 4), (8, 4), (8, 8)])
 @pytest.mark.parametrize("s0,lam", [(1, 1.1), (4, 1.0), (1, 2.0)])
-def test_device_appends_build_the_bucket_lists(env, kb, vb, s0, lam):
+@pytest.mark.parametrize("counted", [True, False], ids=["append", "append_uncounted"])
+def test_device_appends_build_the_bucket_lists(env, kb, vb, s0, lam, counted):
     """Concurrent per-element appends of hot keys (2^18 values over 1000 keys, every key's
     copies spread over the launch) against the multiset oracle, then a bulk insert into
     the same lists and appends again: counts, offsets and sorted values per key equal the
-    oracle's; the size counts every value, the key count every distinct key."""
+    oracle's; the size counts every value, the key count every distinct key (with
+    append_uncounted, once each thread has added its counts)."""
     wc, torch, lib = env
     n, nk = 1 << 18, 1000
     kdt = np.uint32 if kb == 4 else np.uint64
@@ -239,7 +242,8 @@ def test_device_appends_build_the_bucket_lists(env, kb, vb, s0, lam):
         keys = uni[rng.integers(0, nk, n)]
         vals = rng.integers(0, 1 << (8 * vb - 1), n, dtype=np.uint64).astype(vdt)
         dk, dv = dev(torch, keys, kb), dev(torch, vals, vb)
-        assert lib.wcu_mv_append(ctypes.byref(v), dk.data_ptr(), dv.data_ptr(), n, flags.data_ptr()) == 0
+        fn = lib.wcu_mv_append if counted else lib.wcu_mv_append_uncounted
+        assert fn(ctypes.byref(v), dk.data_ptr(), dv.data_ptr(), n, flags.data_ptr()) == 0
         o.insert(keys, vals)
         assert int(flags.item()) == 0 and t.status(clear=True) == 0
         assert t.size() == o.size() and t.num_keys() == nk
