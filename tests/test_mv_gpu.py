@@ -299,3 +299,34 @@ def test_growth_parameters_are_validated(wc):
             wc.MultiValueTable(8, 4, min_capacity=64, value_pool_capacity=64, **kw)
     with pytest.raises(wc.WcError):  # single-value tables have no buckets
         wc.SingleValueTable(4, 4, min_capacity=64, bucket_first_size=1, bucket_growth=2.0)
+
+
+def test_mv_full_key_store_keeps_whole_keys(wc):
+    """More distinct keys than key-store slots, spread over many tiles: PROBE_LIMIT is
+    raised and a key is either stored with every one of its values (those of all tiles
+    it occurs in) or not at all; the key count and the size agree with what is stored."""
+    t = make_mv(wc, 8, 4, 64, 1 << 16)
+    cap = t.capacity
+    rng = np.random.default_rng(5)
+    uni = np.arange(1, 4 * cap + 1, dtype=np.uint64) * np.uint64(0x9E3779B1)
+    keys = uni[rng.integers(0, uni.size, 20000)]
+    vals = np.arange(keys.size, dtype=np.uint32)
+    o = oracle.MultiValue(8, 4)
+    o.insert(keys, vals)
+    f = t.insert(keys, vals)
+    assert f & wc.WC_FLAG_PROBE_LIMIT
+    offs, _ = t.count_values(uni)
+    got = np.diff(offs.astype(np.int64))
+    want, _ = o.count_values(uni)
+    want = np.diff(want.astype(np.int64))
+    stored = got > 0
+    np.testing.assert_array_equal(got[stored], want[stored])
+    assert 0 < stored.sum() <= cap and t.num_keys() == stored.sum()
+    assert t.size() == int(offs[-1]) == int(want[stored].sum())
+    q = uni[stored]
+    qo, _ = t.count_values(q)
+    v, _ = t.retrieve_multi(q, qo)
+    eo, _ = o.count_values(q)
+    ev, _ = o.retrieve_multi(q, eo)
+    np.testing.assert_array_equal(qo, eo)
+    np.testing.assert_array_equal(oracle.sorted_segments(v, qo), oracle.sorted_segments(ev, eo))
