@@ -717,7 +717,10 @@ def run_sv64_zipf(args, dev):
     _common(args, "sv_u64_n2^%d_alpha0.90_zipf1.1" % log2n, "G ops/s (insert + Zipf retrieve)",
             2 * n / ((ins + ret) * 1e-3) / 1e9, "G ops/s", ins + ret, "u64",
             {"n": n, "capacity": info["capacity"], "table_bytes": info["table_bytes"],
-             "window_slots": info["window_width"], "l2": "no flush: table 4.8 GB"}, clk,
+             "window_slots": info["window_width"], "launch": {
+                 op: {k: lc_[k] for k in ("group_size", "keys_in_flight", "scheme")}
+                 for op, lc_ in (("insert", api.wc_table_get_launch(h, wc.WC_OP_INSERT)), ("retrieve", lc))},
+             "l2": "no flush: table 4.8 GB"}, clk,
             (insert_launches(api, h, n) + 1) * args.steps,
             {"insert_gops": n / ins / 1e6, "retrieve_gops": n / ret / 1e6, "insert_ms": ins, "retrieve_ms": ret,
              "retrieve_dedup_gops": n / ret_dedup / 1e6, "retrieve_dedup_ms": ret_dedup,

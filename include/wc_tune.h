@@ -10,9 +10,12 @@
  * (or the one the caller fixes), a table of the caller's kind, widths and options is
  * filled to the given load with `sample_keys` distinct keys, and every valid group size
  * of insert, retrieve (and keys in flight 1 or 2 where the lookup kernel supports it) and
- * erase is timed with CUDA events (best of three calls).  W is the one with the smallest
- * insert + retrieve time.  A shape replaces the library's default only when it is more
- * than 2 % faster, so noise does not flip the choice.
+ * erase is timed with CUDA events (best of three calls).  A lookup is timed on two query
+ * streams: uniform keys, half of them absent (bound by HBM), and queries over a hot 1/64 of
+ * the keys (bound by L2, as a skewed stream's hot keys are); a shape has to serve both.
+ * W is the one with the smallest insert + retrieve time.  A shape replaces the library's default only when it is more
+ * than 10 % faster: the sample stands for tables of other sizes and query streams, and only
+ * clear wins on it carry over to them.
  *
  * wc_table_create uses it for window_width = 0 (wc.h): single-value, counting and
  * hash-set tables in packed slots are created with the tuned W and shapes for load 0.9,
@@ -41,8 +44,8 @@ typedef struct {
   int32_t reserved;
   wc_launch launch[3];     /* the chosen shapes of WC_OP_INSERT, WC_OP_RETRIEVE, WC_OP_ERASE */
   double ms[3];            /* their best time on the sample: insert of sample_keys pairs,
-                              lookup of sample_keys queries (half of them absent), erase of
-                              the sample_keys keys */
+                              lookup of sample_keys uniform queries (half of them absent)
+                              plus sample_keys hot ones, erase of the sample_keys keys */
   uint64_t sample_keys;
   double load;
 } wc_tuning;

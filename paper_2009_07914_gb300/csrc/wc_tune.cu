@@ -13,21 +13,46 @@
 #include <vector>
 
 #include "wc.h"
+#include "wc_device_api.cuh"
 #include "wc_internal.h"
 #include "wc_tune.h"
 
 namespace {
 
-// The sample: keys 1..n (distinct, never a sentinel), values 1..n, and n queries of which
-// the even positions hold present keys and the odd ones keys above n (absent).  The
-// table hashes every key, so consecutive keys land on random windows like any others.
+// The sample: key j = mix(j) for j = 1..n, values 1..n, n queries of which the even
+// positions hold present keys and the odd ones the keys mix(n + 1 + i) (absent), and n "hot"
+// queries over the first n / 64 keys only -- a set whose windows stay in L2, as the hot
+// keys of a skewed query stream do.  mix is an invertible finalizer (MurmurHash3's fmix64 /
+// fmix32, public domain), so the keys are distinct and look random in value and order (a
+// sample of sequential keys measured a different best lookup shape than random keys do);
+// mix(0) = 0, and the one j whose mix is all ones takes mix(3n + 7) instead, which no other
+// sample key has.
+__device__ __forceinline__ uint32_t tune_mix(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ uint64_t tune_mix(uint64_t h) { return wc_dev::fmix64(h); }
+
+template <class K>
+__device__ __forceinline__ K tune_key(uint64_t j, uint64_t n) {
+  K x = tune_mix(static_cast<K>(j));
+  if (x == K(~K(0))) x = tune_mix(static_cast<K>(3 * n + 7));
+  return x;
+}
+
 template <class K, class V>
-__global__ void k_tune_fill(K* keys, V* vals, K* queries, uint64_t n) {
+__global__ void k_tune_fill(K* keys, V* vals, K* queries, K* hot, uint64_t n) {
+  const uint64_t hot_n = n / 64 > 0 ? n / 64 : 1;
   for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-    keys[i] = static_cast<K>(i + 1);
+    keys[i] = tune_key<K>(i + 1, n);
     if (vals != nullptr) vals[i] = static_cast<V>(i + 1);
-    queries[i] = static_cast<K>((i & 1) ? n + 1 + i : i + 1);
+    queries[i] = tune_key<K>((i & 1) ? n + 1 + i : i + 1, n);
+    hot[i] = tune_key<K>((i * 2654435761ull) % hot_n + 1, n);
   }
 }
 
@@ -39,12 +64,14 @@ struct Buffers {
   void* keys = nullptr;
   void* vals = nullptr;
   void* queries = nullptr;
+  void* hot = nullptr;
   void* out = nullptr;
   uint8_t* found = nullptr;
   ~Buffers() {
     cudaFree(keys);
     cudaFree(vals);
     cudaFree(queries);
+    cudaFree(hot);
     cudaFree(out);
     cudaFree(found);
   }
@@ -77,8 +104,14 @@ int slot_bytes_of(const wc_table_config& c) {
   return c.key_bytes + c.value_bytes;
 }
 
+// A shape or window width replaces the library's default only when it is more than 10 %
+// faster on the sample: the sample is smaller than most tables it stands for (a 256 MiB
+// table for tables of gigabytes), and smaller margins measured on it did not carry over
+// (2^27 keys: a 32-byte window 2-4 % ahead on the sample was 4 % behind on the table).
+constexpr double kReplace = 0.90;
+
 // One window width: the best shape of each operation, with the library default kept
-// unless another shape is more than 2 % faster.
+// unless another shape is more than 10 % faster.
 struct WindowResult {
   bool ok = false;
   wc_launch launch[3];
@@ -117,9 +150,15 @@ class Tuner {
   int slot_bytes() const { return slot_bytes_of(cfg_); }
 
   wc_status insert(wc_table* t) { return wc_insert(t, b_.keys, is_set() ? nullptr : b_.vals, n_, s_); }
+  // a lookup is timed on both kinds of query stream: the uniform one (HBM-bound) and the
+  // hot one (L2-bound), so a shape that only wins one of them does not take the table
   wc_status lookup(wc_table* t) {
-    if (is_set()) return wc_contains(t, b_.queries, n_, b_.found, s_);
-    return wc_retrieve(t, b_.queries, n_, b_.out, b_.found, s_);
+    for (const void* q : {b_.queries, b_.hot}) {
+      const wc_status st = is_set() ? wc_contains(t, q, n_, b_.found, s_)
+                                    : wc_retrieve(t, q, n_, b_.out, b_.found, s_);
+      if (st != WC_OK) return st;
+    }
+    return WC_OK;
   }
   wc_status erase(wc_table* t) { return wc_erase(t, b_.keys, n_, s_); }
 
@@ -150,7 +189,7 @@ class Tuner {
 
   // Time the table's default shape of `op` and every other valid group size (and, for
   // lookups whose lanes hold at most 32 bytes of window, two keys in flight); keep the
-  // default unless the fastest other shape beats it by more than 2 %.
+  // default unless the fastest other shape beats it by more than 10 %.
   template <class Prep, class Op>
   wc_status sweep(wc_table* t, int W, int op, Prep prep, Op timed, WindowResult& r) {
     wc_launch def{};
@@ -185,7 +224,7 @@ class Tuner {
         best = cands[i];
       }
     }
-    const bool keep = !(best_ms < 0.98 * def_ms);
+    const bool keep = !(best_ms < kReplace * def_ms);
     r.launch[op] = keep ? def : best;
     r.ms[op] = keep ? def_ms : best_ms;
     return wc_table_set_launch(t, op, &r.launch[op]);
@@ -211,7 +250,7 @@ template <class K, class V>
 cudaError_t fill_sample(Buffers& b, uint64_t n, cudaStream_t s) {
   const unsigned grid = static_cast<unsigned>(std::min<uint64_t>((n + 255) / 256, 4096));
   k_tune_fill<K, V><<<grid, 256, 0, s>>>(static_cast<K*>(b.keys), static_cast<V*>(b.vals), static_cast<K*>(b.queries),
-                                         n);
+                                         static_cast<K*>(b.hot), n);
   return cudaGetLastError();
 }
 
@@ -231,6 +270,7 @@ wc_status autotune_uncached(const wc_table_config& cfg, double load, uint64_t n,
   };
   const uint64_t vbytes = vb > 0 ? static_cast<uint64_t>(vb) : 4;
   if (cudaMalloc(&b.keys, n * kb) != cudaSuccess || cudaMalloc(&b.queries, n * kb) != cudaSuccess ||
+      cudaMalloc(&b.hot, n * kb) != cudaSuccess ||
       cudaMalloc(&b.out, n * vbytes) != cudaSuccess || cudaMalloc(&b.found, n) != cudaSuccess ||
       (vb > 0 && cudaMalloc(&b.vals, n * vbytes) != cudaSuccess))
     return done(WC_ERR_OUT_OF_MEMORY);
@@ -243,7 +283,7 @@ wc_status autotune_uncached(const wc_table_config& cfg, double load, uint64_t n,
   Tuner tuner(cfg, load, n, s, b);
   int candidates = 0;
   // the default window width is kept unless another one's insert + lookup time beats it
-  // by more than 2 %
+  // by more than 10 %
   bool have = false, have_def = false;
   double best = 1e30, def_score = 0;
   WindowResult pick, def_r;
@@ -266,7 +306,7 @@ wc_status autotune_uncached(const wc_table_config& cfg, double load, uint64_t n,
       have = true;
     }
   }
-  if (have_def && !(have && best < 0.98 * def_score)) {
+  if (have_def && !(have && best < kReplace * def_score)) {
     pick = def_r;
     pick_w = wdef;
     have = true;
