@@ -686,6 +686,8 @@ def run_sv64_zipf(args, dev):
     s = torch.cuda.current_stream()
     h = api.wc_table_create(0, 8, 8, int(np.ceil(n / 0.9)), args.window, 0, 0x5EEDC0DE, dev.index)
     info = api.wc_table_get_info(h)
+    import paper_2009_07914_gb300 as wc
+    apply_groups(api, wc, h, args.group, args.kif, args.retrieve_scheme)
     ev = []
 
     def step(rec):
