@@ -148,6 +148,7 @@ cudaError_t dispatch(const wc_table* t, const void* keys, const void* vals, uint
   } else {
     WC_NA_CASE(LayoutP64, 2, 1) WC_NA_CASE(LayoutP64, 2, 2)
     WC_NA_CASE(LayoutP64, 4, 1) WC_NA_CASE(LayoutP64, 4, 2) WC_NA_CASE(LayoutP64, 4, 4)
+    WC_NA_CASE_H(LayoutP64, 8, 1, 2)
     WC_NA_CASE(LayoutP64, 8, 2) WC_NA_CASE(LayoutP64, 8, 4) WC_NA_CASE(LayoutP64, 8, 8)
     WC_NA_CASE(LayoutP64, 16, 4) WC_NA_CASE(LayoutP64, 16, 8) WC_NA_CASE(LayoutP64, 16, 16)
   }

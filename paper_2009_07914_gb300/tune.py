@@ -28,7 +28,7 @@ from ._binding import WC_OP_ERASE, WC_OP_INSERT, WC_OP_RETRIEVE, WC_SCHEME_BLOCK
 
 SHAPES = {  # slot bytes -> W -> valid lanes per key
     8: {4: [1, 2, 4], 8: [1, 2, 4, 8], 16: [1, 2, 4, 8, 16], 32: [4, 8, 16, 32]},
-    16: {2: [1, 2], 4: [1, 2, 4], 8: [2, 4, 8], 16: [4, 8, 16]},
+    16: {2: [1, 2], 4: [1, 2, 4], 8: [1, 2, 4, 8], 16: [4, 8, 16]},
 }
 BLOCKS = (256, 128)
 

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 W_G_P32 = [(4, 1), (4, 2), (4, 4), (8, 1), (8, 2), (8, 4), (8, 8), (16, 1), (16, 2), (16, 4), (16, 8), (16, 16),
            (32, 4), (32, 8), (32, 16), (32, 32)]
-W_G_P64 = [(2, 1), (2, 2), (4, 1), (4, 2), (4, 4), (8, 2), (8, 4), (8, 8), (16, 4), (16, 8), (16, 16)]
+W_G_P64 = [(2, 1), (2, 2), (4, 1), (4, 2), (4, 4), (8, 1), (8, 2), (8, 4), (8, 8), (16, 4), (16, 8), (16, 16)]
 
 
 @pytest.fixture(scope="module")
