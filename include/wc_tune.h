@@ -13,9 +13,9 @@
  * erase is timed with CUDA events (best of three calls).  A lookup is timed on two query
  * streams: uniform keys, half of them absent (bound by HBM), and queries over a hot 1/64 of
  * the keys (bound by L2, as a skewed stream's hot keys are); a shape has to serve both.
- * W is the one with the smallest insert + retrieve time.  A shape replaces the library's default only when it is more
- * than 10 % faster: the sample stands for tables of other sizes and query streams, and only
- * clear wins on it carry over to them.
+ * W is the one with the smallest insert + retrieve time.  A shape or width replaces the
+ * library's default only when it is more than 10 % faster: the sample stands for tables of
+ * other sizes and query streams, and only clear wins on it carry over to them.
  *
  * wc_table_create uses it for window_width = 0 (wc.h): single-value, counting and
  * hash-set tables in packed slots are created with the tuned W and shapes for load 0.9,

@@ -128,3 +128,26 @@ def test_device_api_header_compiles_for_sm103a(tmp_path):
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-3000:]
     assert os.path.getsize(out) > 0
+
+
+def test_autotune_sample_sizes_and_refusals(lib):
+    """Host-side parts of the autotuner: the sample wc_table_create tunes on for
+    window_width = 0 (2^20 keys for tables of up to 32 MiB of slots, else a 256 MiB table
+    at load 0.9), and the argument checks that refuse a call before any device work."""
+    from paper_2009_07914_gb300 import api
+    assert api.wc_autotune_sample_keys(0, 4, 4, 1 << 20) == 1 << 20          # 8 MiB of 8-byte slots
+    assert api.wc_autotune_sample_keys(0, 4, 4, 4 << 20) == 1 << 20          # 32 MiB: still L2-sized
+    big = api.wc_autotune_sample_keys(0, 4, 4, (4 << 20) + 1)
+    assert big == ((256 << 20) // 8 * 9 // 10) & ~1023 and big * 8 / 0.9 > 200 << 20
+    assert api.wc_autotune_sample_keys(0, 8, 8, 1 << 30) == ((256 << 20) // 16 * 9 // 10) & ~1023
+    assert api.wc_autotune_sample_keys(3, 4, 0, 1 << 30) == ((256 << 20) // 4 * 9 // 10) & ~1023
+    for bad in (dict(load=1.0), dict(load=0.01), dict(sample_keys=100), dict(sample_keys=1 << 27)):
+        args = dict(kind=0, key_bytes=4, value_bytes=4, load=0.9, sample_keys=1 << 14, use_cache=False, device=0)
+        args.update(bad)
+        with pytest.raises(Exception) as e:
+            api.wc_autotune(**args)
+        assert getattr(e.value, "code", None) == 1  # WC_ERR_INVALID_ARG
+    for kind, kb, vb, opt in ((1, 4, 4, 0), (2, 4, 4, 0), (5, 4, 0, 0), (0, 4, 4, 2)):
+        with pytest.raises(Exception) as e:
+            api.wc_autotune(kind, kb, vb, load=0.9, sample_keys=1 << 14, options=opt, use_cache=False, device=0)
+        assert getattr(e.value, "code", None) == 6  # WC_ERR_UNSUPPORTED
